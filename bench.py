@@ -1,0 +1,375 @@
+"""Benchmark of the EDA hot path on GB300: member solves/s to relative residual
+1e-6 and Hessian-vector products/s, mixed precision against the plain FP64
+GPU path, with the roofline of the dominant kernel and the CPU oracle timed
+beside it.
+
+One step = the whole path on one synthetic EDA of the n=4096, 64-step,
+51-member Lorenz-96 workload: nonlinear trajectories, innovations and
+right-hand sides of all members, the Gamma sketch of the control Hessian,
+the Nystrom factorisation and LMP, and the batched PCG of all 51 members to
+relative residual 1e-6.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torch.distributed.run) every rank runs an
+independent replica on its own GPU (the path has no data exchange between
+EDA problems); value = member solves of all ranks / max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import eda_synth as S  # noqa: E402
+
+METRIC = "EDA member solves/s to rel-res 1e-6 & Hv products/s vs plain FP64 GPU path"
+UNIT = "member solves/s"
+TOL = 1e-6
+MAXIT = 6000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_%d.csv" % gpu_index)
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- workload
+def workload(seed):
+    spec = S.spec_batched(seed=seed)
+    dr = S.draws(spec)
+    return spec, dr
+
+
+def cpu_oracle_step(spec, xb, y, taps, iters_per_member, sample_iters=30):
+    """The oracle on a bounded sample of one step: setup, RHS, Gamma sketch and
+    LMP of every member, then ``sample_iters`` PCG iterations of one member;
+    the full step is extrapolated with ``iters_per_member`` (the iteration
+    count each member needs to reach the tolerance)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    traj = O.member_trajectories(spec, xb)
+    d = O.innovations(spec, traj, y)
+    b = O.rhs(spec, traj, d, taps)
+    ctrl = traj[0:1]
+
+    def apply_ctrl(block):
+        tr = np.broadcast_to(ctrl, (block.shape[1],) + ctrl.shape[1:])
+        return O.apply_A(spec, tr, block.T.copy(), taps).T
+
+    Sk, D, _ = O.nystrom(apply_ctrl, O.gamma(b)[:, : spec.ell], spec.k)
+    theta = O.theta_value(spec.theta_mode, D, spec.theta)
+    c = O.lmp_coeffs(D, theta)
+    t1 = time.perf_counter()
+    O.pcg(lambda V: O.hvp(spec, traj[:1], V, taps), b[:1], lambda R: O.lmp_apply(Sk, c, R),
+          tol=0.0, maxit=sample_iters, fixed_iters=sample_iters)
+    t2 = time.perf_counter()
+    t_iter = (t2 - t1) / sample_iters
+    full = (t1 - t0) + t_iter * float(np.sum(iters_per_member))
+    return {"t_setup_sketch_lmp_s": t1 - t0, "t_iter_s": t_iter, "t_full_step_s": full,
+            "sample": "numpy FP64 oracle: setup, RHS, Gamma sketch and LMP of all %d members "
+                      "(%.1f s) plus %d PCG iterations of one member (%.3f s each), extrapolated "
+                      "to the %d PCG iterations (summed over members) the step needs"
+                      % (spec.n_members, t1 - t0, sample_iters, t_iter, int(np.sum(iters_per_member)))}
+
+
+def oracle_iters_per_member(spec):
+    """PCG iterations per member of the oracle on this workload (committed
+    fixture written by tests/golden/write_oracle_iters.py from the oracle)."""
+    path = os.path.join(ROOT, "tests", "golden", "oracle_pcg_iters_n4096.json")
+    d = json.load(open(path))
+    return np.full(spec.n_members, float(np.mean(d["iters"])))
+
+
+def run_reference(args):
+    """The oracle (the only reference: the paper ships no code) on the host."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle as O
+    spec, dr = workload(args.seed)
+    taps = O.bhalf_taps(spec.n, spec.length_scale, spec.sigma_b)
+    _, xb, y = O.twin(spec, dr, taps)
+    iters = oracle_iters_per_member(spec)
+    for _ in range(args.warmup):
+        cpu_oracle_step(spec, xb, y, taps, iters, sample_iters=5)
+    times = []
+    r = None
+    for _ in range(args.steps):
+        r = cpu_oracle_step(spec, xb, y, taps, iters)
+        times.append(r["t_full_step_s"])
+    t = float(np.sum(times))
+    value = spec.n_members * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": spec.name, "n": spec.n, "window": spec.nsteps,
+                                            "members": spec.n_members, "ell": spec.ell, "k": spec.k},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": r["sample"] + " (iteration count: the oracle's own, "
+                                       "tests/golden/oracle_pcg_iters_n4096.json)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2605_23571_gb300 as P
+    P.build()
+    spec, dr = workload(args.seed + rank)
+    taps = P.bhalf_gaussian(spec.n, spec.length_scale, spec.sigma_b)
+    M, n, p = spec.n_members, spec.n, spec.p
+    stream = torch.cuda.current_stream(dev)
+
+    # synthetic identical twin generated on the GPU by the library
+    hgen = P.Handle.from_spec(spec, taps, precision=P.EDA_FP64)
+    xb = torch.empty(M, n, dtype=torch.float64, device=dev)
+    y = torch.empty(M, p, dtype=torch.float64, device=dev)
+    x_spin0 = torch.tensor(spec.F + spec.spin_sigma * dr.eta_spin, device=dev)
+    hgen.eda_twin(x_spin0, spec.spinup, torch.tensor(dr.eta_b, device=dev),
+                  torch.tensor(dr.eta_o, device=dev), xb, y)
+    hgen.close()
+
+    dz = torch.empty(M, n, dtype=torch.float64, device=dev)
+    iters = torch.empty(M, dtype=torch.int32, device=dev)
+    relres = torch.empty(M, dtype=torch.float64, device=dev)
+    status = torch.empty(M, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
+
+    def step(h, xb_, y_, dz_, it_, rr_, st_):
+        h.eda_set_trajectory(xb_, y_)
+        h.eda_sketch()
+        h.eda_build_lmp()
+        h.eda_solve_batch(TOL, MAXIT, None, True, dz_, it_, rr_, st_)
+
+    def timed_steps(h, k, warm):
+        for _ in range(warm):
+            step(h, xb, y, dz, iters, relres, status)
+        torch.cuda.synchronize()
+        tot = 0.0
+        its = []
+        for _ in range(k):
+            flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(h, xb, y, dz, iters, relres, status)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1) / 1e3
+            its.append(iters.cpu().numpy().copy())
+        return tot, its
+
+    hm = P.Handle.from_spec(spec, taps, precision=P.EDA_MIXED)
+    h64 = P.Handle.from_spec(spec, taps, precision=P.EDA_FP64)
+    # setup (untimed): the autotuner picks the sweep tilings on this workload
+    hm.eda_set_trajectory(xb, y)
+    tuned_ms_mixed = hm.eda_autotune(0)
+    h64.eda_set_trajectory(xb, y)
+    tuned_ms_64 = h64.eda_autotune(0)
+
+    # ---- timed region (headline: mixed precision)
+    for _ in range(args.warmup):
+        step(hm, xb, y, dz, iters, relres, status)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches0 = P.kernel_launches()
+    with Clocks(local) as clk:
+        t_mixed, its_mixed = timed_steps(hm, args.steps, 0)
+    launches = P.kernel_launches() - launches0
+    st_mixed = status.cpu().numpy()
+    rr_mixed = relres.cpu().numpy()
+    dz_mixed = dz.cpu().numpy()
+    if world > 1:
+        tt = torch.tensor([t_mixed], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_mixed = float(tt.item())
+    value = world * M * args.steps / t_mixed
+
+    # ---- plain FP64 GPU path (comparison)
+    t64, its64 = timed_steps(h64, max(1, args.fp64_steps), 1)
+    dz64 = dz.cpu().numpy()
+    value64 = M * max(1, args.fp64_steps) / t64
+
+    # ---- Hessian-vector products/s and the roofline of the dominant kernel
+    ms32 = hm.eda_time_hvp_sweep(reps=20)
+    ms64 = h64.eda_time_hvp_sweep(reps=3)
+    hvps32 = M / (ms32 / 1e3)
+    hvps64 = M / (ms64 / 1e3)
+    bytes_per_launch = M * 4 * n * (2 * spec.nsteps + 2)  # trajectory + vectors, FP32
+    achieved = bytes_per_launch / (ms32 / 1e3) / 1e9
+    peak, peak_kind = measured_peaks()
+
+    # ---- end to end through the C ABI with host buffers
+    xb_h = xb.cpu().pin_memory().numpy()
+    y_h = y.cpu().pin_memory().numpy()
+    dz_h = torch.empty(M, n, dtype=torch.float64).pin_memory().numpy()
+    it_h = torch.empty(M, dtype=torch.int32).pin_memory().numpy()
+    rr_h = torch.empty(M, dtype=torch.float64).pin_memory().numpy()
+    st_h = torch.empty(M, dtype=torch.int32).pin_memory().numpy()
+    step(hm, xb_h, y_h, dz_h, it_h, rr_h, st_h)
+    torch.cuda.synchronize()
+    te = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(hm, xb_h, y_h, dz_h, it_h, rr_h, st_h)
+        torch.cuda.synchronize()
+        te += time.perf_counter() - t0
+    e2e = {"value": M * args.steps / te, "unit": UNIT,
+           "h2d_bytes_per_step": int(xb_h.nbytes + y_h.nbytes),
+           "d2h_bytes_per_step": int(dz_h.nbytes + it_h.nbytes + rr_h.nbytes + st_h.nbytes)}
+
+    # ---- CPU oracle baseline (rank 0, N = 1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = cpu_oracle_step(spec, xb.cpu().numpy(), y.cpu().numpy(), taps, its64[-1])
+        cpu = {"value": M / r["t_full_step_s"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": r["sample"] + " (iteration counts: the FP64 GPU path's, same algorithm)"}
+
+    hm.close()
+    h64.close()
+    if rank == 0:
+        its_m = np.concatenate(its_mixed)
+        its_d = np.concatenate(its64)
+        diff64 = float(np.max(np.linalg.norm(dz_mixed - dz64, axis=1) / np.linalg.norm(dz64, axis=1)))
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_mixed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": spec.name, "n": n, "window": spec.nsteps, "members": M,
+                       "ell": spec.ell, "k": spec.k, "obs_per_step": int(p // len(spec.obs_steps)),
+                       "obs_steps": int(len(spec.obs_steps)), "tol": TOL, "precision": "mixed",
+                       "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "fp64_path": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * t64 / max(1, args.fp64_steps),
+                          "speedup_mixed_over_fp64": value / world / value64,
+                          "iters_median": float(np.median(its_d))},
+            "hv_per_s": {"mixed_fp32_sweep": hvps32, "fp64_sweep": hvps64,
+                         "ms_per_batched_launch_fp32": ms32, "ms_per_batched_launch_fp64": ms64},
+            "solve": {"iters_min": int(its_m.min()), "iters_median": float(np.median(its_m)),
+                      "iters_max": int(its_m.max()), "all_converged": bool((st_mixed == 0).all()),
+                      "true_relres_max": float(rr_mixed.max()),
+                      "rel_diff_mixed_vs_fp64_max": diff64},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "sweep_kernel<float,8> (batched member HVP, 51 columns)",
+                         "peak_kind": peak_kind},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,265 @@
+/*
+ * eda.h — C ABI of the GB300 (sm_103a) ensemble-of-4D-Var solver library
+ * (libeda.so).
+ *
+ * The library solves, for every member j of an ensemble data assimilation
+ * (EDA) with a Lorenz-96 model, the incremental strong-constraint 4D-Var
+ * system in the control variable (Section 2.3, Eq. (system with CVT)):
+ *
+ *     (I + A_j) dz_j = b_j,   A_j = U_B^T G_j^T R^{-1} G_j U_B,
+ *                             b_j = U_B^T G_j^T R^{-1} d_j,
+ *
+ * with a second-level scaled spectral LMP (Section 3.1) built from a Nystrom
+ * approximation (Section 3.2.3, Algorithm 1) of the control member's A,
+ * sketched with the matrix of right-hand-side differences Gamma
+ * (Section 3.2.2, Eq. (Gamma)), and batched preconditioned CG.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an eda_status.  EDA_OK is 0; on any other value
+ *   eda_last_error() returns a message.  A member that does not converge is
+ *   NOT an error: it is reported in status_out of eda_solve_batch.
+ * - Vectors are FP64, member-major: member (or column) c occupies elements
+ *   [c*n, (c+1)*n).  Observation-space arrays are FP64, member-major with
+ *   p = obs_ptr[n_obs_times] entries per member, ordered by observation step
+ *   then by the order of obs_idx.
+ * - Array arguments may be HOST or DEVICE memory (the library asks the CUDA
+ *   runtime which).  Device arrays are used in place on the handle's stream.
+ *   Host arrays are copied through the handle's staging buffers on that
+ *   stream; a call that writes a host array synchronises the stream before
+ *   returning.  The caller owns every argument array; the handle owns its
+ *   internal buffers (trajectory store, right-hand sides, sketch, LMP).
+ * - Calls on one handle are not thread-safe; distinct handles are
+ *   independent.
+ */
+#ifndef EDA_H
+#define EDA_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define EDA_API __attribute__((visibility("default")))
+#else
+#define EDA_API
+#endif
+
+typedef enum {
+  EDA_OK = 0,
+  EDA_ERR_INVALID = 1,  /* a size, pointer or option is out of range        */
+  EDA_ERR_CUDA = 2,     /* a CUDA runtime call failed                         */
+  EDA_ERR_NUMERIC = 3,  /* NaN/Inf in an input, or Cholesky failure after the
+                           Appendix B shift retry                             */
+  EDA_ERR_TIMEOUT = 4,  /* a bounded device-side wait gave up                 */
+  EDA_ERR_STATE = 5     /* calls out of order (e.g. solve before set_trajectory) */
+} eda_status;
+
+/* precision */
+enum { EDA_FP64 = 0, EDA_MIXED = 1 };
+/* theta_mode: the scaling of the spectral LMP (Section 3.1) */
+enum { EDA_THETA_GIVEN = 0, EDA_THETA_LAMBDA_K = 1, EDA_THETA_MID = 2 };
+/* per-member solve status */
+enum { EDA_CONVERGED = 0, EDA_MAXIT = 1, EDA_NAN = 2, EDA_BREAKDOWN = 3 };
+
+typedef struct eda_handle eda_handle;
+
+/*
+ * Problem definition.  All pointers in this struct are HOST pointers; the
+ * library copies what it needs during eda_create.
+ *
+ *  n, nsteps       state size (n >= 4) and window length N (N >= 1):
+ *                  states x_0 .. x_N (Section 2.1).
+ *  F, dt           Lorenz-96 forcing and RK4 step (Section 4: F = 8,
+ *                  dt = 0.025).
+ *  n_obs_times     number of observation steps (>= 1).
+ *  obs_steps       [n_obs_times] strictly increasing steps in [0, N].
+ *  obs_ptr         [n_obs_times+1] CSR offsets into obs_idx (obs_ptr[0] = 0).
+ *  obs_idx         [p] observed variable indices in [0, n), strictly
+ *                  increasing within each step: H_t selects them.
+ *  rinv            [p] diagonal of R^{-1} (R = sigma_o^2 I in Section 4).
+ *  bhalf_w, bhalf_coef
+ *                  U_B = U_B^T as the banded symmetric circulant
+ *                  (U_B v)_i = sum_{|d|<=w} coef[|d|] v_{(i+d) mod n},
+ *                  0 <= w <= (n-1)/2, coef has w+1 entries.
+ *  n_members       L + 1 (member 0 is the control, Section 2.2), >= 1.
+ *  ell, k          sketch columns (1 <= ell <= L) and LMP rank (1 <= k <= ell)
+ *                  (Algorithm 1).  ell = 0 disables the LMP.
+ *  theta_mode, theta   EDA_THETA_GIVEN uses theta; EDA_THETA_LAMBDA_K uses
+ *                  lambda_k(I+A); EDA_THETA_MID uses (lambda_k(I+A)+1)/2
+ *                  (Section 3.1).
+ *  precision       EDA_FP64: every sweep, vector and scalar in FP64.
+ *                  EDA_MIXED: tangent-linear/adjoint sweeps and LMP apply in
+ *                  FP32, CG scalars, residual norms and the small Nystrom
+ *                  factorisations in FP64, FP64 residual replacement.
+ *  ckpt_every      0 stores the whole trajectory; c > 0 stores every c-th
+ *                  state and recomputes the segments in the adjoint sweep.
+ *  stream          a cudaStream_t (NULL = the legacy default stream).
+ */
+typedef struct {
+  int n;
+  int nsteps;
+  double F;
+  double dt;
+  int n_obs_times;
+  const int* obs_steps;
+  const int* obs_ptr;
+  const int* obs_idx;
+  const double* rinv;
+  int bhalf_w;
+  const double* bhalf_coef;
+  int n_members;
+  int ell;
+  int k;
+  int theta_mode;
+  double theta;
+  int precision;
+  int ckpt_every;
+  void* stream;
+} eda_config;
+
+/* Library version string (static storage). */
+EDA_API const char* eda_version(void);
+
+/* Message of the last error on this handle; with h == NULL, of the last
+ * failed eda_create or handle-less call on this thread.  Static or
+ * handle-owned storage, valid until the next call on the handle. */
+EDA_API const char* eda_last_error(const eda_handle* h);
+
+/*
+ * Creates a handle for one EDA problem (Section 2.2: L perturbed members and
+ * a control) on the current CUDA device.  Validates the configuration
+ * (EDA_ERR_INVALID on any out-of-range value or unsorted observation list),
+ * copies the observation network and U_B taps to the device and allocates
+ * the trajectory store.  *out receives the handle (NULL on failure).
+ */
+EDA_API int eda_create(const eda_config* cfg, eda_handle** out);
+
+/* Releases every device buffer of the handle.  NULL is accepted. */
+EDA_API int eda_destroy(eda_handle* h);
+
+/*
+ * Identical-twin generator (Section 4): spins up x_spin0 [n] for `spinup`
+ * RK4 steps to the truth x^t_0, integrates the truth over the window and
+ * observes it, and forms
+ *   x_b,0 = x^t_0 + U_B eta_b[0],      y_0 = H x^t + R^{1/2} eta_o[0],
+ *   x_b,j = x_b,0 + U_B eta_b[j],      y_j = y_0 + R^{1/2} eta_o[j]
+ * (Section 2.2) for j = 1..L.  eta_b is [(L+1) x n], eta_o [(L+1) x p],
+ * standard-normal draws supplied by the caller.  Outputs xb_out
+ * [(L+1) x n] and y_out [(L+1) x p]; xt0_out [n] may be NULL.  FP64.
+ */
+EDA_API int eda_twin(eda_handle* h, const double* x_spin0, int spinup,
+                     const double* eta_b, const double* eta_o,
+                     double* xb_out, double* y_out, double* xt0_out);
+
+/*
+ * Setup of every member (Section 2.1 and 2.2): integrates the nonlinear
+ * model from each background xb [(L+1) x n] in FP64, stores the trajectory
+ * (or its checkpoints), forms the innovations d_j = y_j - G(x_b,j) from
+ * y [(L+1) x p], and the right-hand sides b_j = U_B^T G_j^T R^{-1} d_j by one
+ * adjoint sweep per member (FP64).  rhs_out [(L+1) x n] may be NULL.
+ * Invalidates any previous sketch and LMP.
+ */
+EDA_API int eda_set_trajectory(eda_handle* h, const double* xb, const double* y,
+                               double* rhs_out);
+
+/*
+ * Sketch Y = A Phi of the control member's Hessian (Algorithm 1, first
+ * step, with q-1 further power passes when q > 1).  phi [n x ell] is
+ * column-major (column c at [c*n, (c+1)*n)); phi == NULL uses
+ * Gamma = [b_1 - b_0, ..., b_ell - b_0] (Section 3.2.2, Eq. (Gamma)).
+ * y_out [n x ell] (may be NULL) receives A Phi of the last pass.  Requires
+ * eda_set_trajectory.  Sweeps in FP64 (EDA_FP64) or FP32 (EDA_MIXED).
+ */
+EDA_API int eda_sketch(eda_handle* h, const double* phi, int q, double* y_out);
+
+/*
+ * Rest of Algorithm 1 in FP64 on the stored sketch: economic QR of Y
+ * (CholeskyQR2), W = Phi^T Y, W = C^T C (with the Appendix B shift
+ * nu = eps ||Y||_F if the factorisation breaks down), T = R_Y C^{-1}, SVD
+ * T = U_T Sigma V_T^T, S = Q_Y U_T, D = Sigma^2, truncated to k; then the
+ * LMP coefficients c_i = theta / (1 + D_i) - 1 (Section 3.1).
+ * eigvals_out [k] (may be NULL) receives lambda_i(I + A) = 1 + D_i in
+ * descending order; s_out [n x k] column-major (may be NULL) receives S_k.
+ * EDA_ERR_NUMERIC if the shifted factorisation also fails.
+ */
+EDA_API int eda_build_lmp(eda_handle* h, double* eigvals_out, double* s_out);
+
+/*
+ * Loads a spectral LMP built elsewhere (another process, a previous cycle, a
+ * test): s_in [n x k] column-major with orthonormal columns approximating
+ * eigenvectors of A, eigvals_in [k] the matching lambda_i(I + A) >= 1 in
+ * descending order.  theta follows the handle's theta_mode (Section 3.1).
+ * Replaces any LMP from eda_build_lmp.  EDA_ERR_INVALID on a non-finite or
+ * out-of-order eigenvalue.
+ */
+EDA_API int eda_set_lmp(eda_handle* h, const double* s_in, const double* eigvals_in);
+
+/*
+ * Batched PCG (Section 2.3) on (I + A_j) dz_j = b_j for every member j, each
+ * with its own Hessian, preconditioned by the control member's LMP when
+ * use_lmp != 0 (requires eda_build_lmp).  Stops member j when
+ * ||r_j|| / ||b_j|| <= tol on the recurrence residual (tol = 0 runs exactly
+ * maxit iterations), or after maxit iterations.  x0 [(L+1) x n] is the
+ * initial guess (NULL = 0).  Outputs: dz_out [(L+1) x n], iters_out
+ * [L+1] (int), relres_out [L+1] (the FP64 recurrence residual at exit; in
+ * EDA_MIXED the FP64 true residual), status_out [L+1] (EDA_CONVERGED,
+ * EDA_MAXIT, EDA_NAN, EDA_BREAKDOWN).  Any output may be NULL except dz_out.
+ */
+EDA_API int eda_solve_batch(eda_handle* h, double tol, int maxit, const double* x0,
+                            int use_lmp, double* dz_out, int* iters_out,
+                            double* relres_out, int* status_out);
+
+/*
+ * Batched Hessian-vector products (Section 2.3, Eq. (system with CVT)):
+ * HV[c] = (include_identity ? V[c] : 0) + A_{m(c)} V[c] for c < ncol, with
+ * m(c) = member_of_col[c] in [0, L] choosing the trajectory (the
+ * linearisation state).  V, HV are [ncol x n].  Requires
+ * eda_set_trajectory.  Sweeps in FP64 (EDA_FP64) or FP32 (EDA_MIXED).
+ */
+EDA_API int eda_hvp(eda_handle* h, const int* member_of_col, int ncol, const double* V,
+                    double* HV, int include_identity);
+
+/*
+ * Autotuner of the sweep tiling: for the stored trajectories, times the
+ * batched member Hessian-vector sweep (all L+1 members) for every tiling
+ * that fits -- thread-block cluster size 1..8 (CTAs per vector) and halo
+ * refresh period K in {2, 4, 8, 16} steps -- and keeps the fastest for all
+ * later sweeps of the handle.  which: bit 0 tunes the FP64 sweep, bit 1 the
+ * FP32 sweep (EDA_MIXED only); 0 = the sweeps of the handle's precision.
+ * *best_ms_out (may be NULL) = sum of the chosen tilings' mean times (ms).
+ * Requires eda_set_trajectory.  Synchronises the stream.
+ */
+EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out);
+
+/*
+ * Tracing: process-wide number of CUDA kernels the library has launched
+ * (every handle, every entry point) since it was loaded.  No device work.
+ */
+EDA_API long long eda_kernel_launches(void);
+
+/*
+ * Tracing: times `reps` launches of the batched Hessian-vector sweep that the
+ * PCG of eda_solve_batch issues (all L+1 members, each on its own
+ * trajectory, inputs from the handle's current direction vectors) with CUDA
+ * events on the handle's stream, after one untimed launch.  fp64 != 0 times
+ * the FP64 sweep, otherwise the sweep of the handle's precision.
+ * *ms_out = mean milliseconds per launch.  Requires eda_set_trajectory.
+ * Synchronises the stream.
+ */
+EDA_API int eda_time_hvp_sweep(eda_handle* h, int reps, int fp64, double* ms_out);
+
+/*
+ * Host helper: taps of U_B for a Gaussian correlation
+ * B = sigma_b^2 exp(-d^2 / (2 L^2)) on the circle of n points:
+ * coef[d] = sigma_b (2 / (pi L^2))^{1/4} exp(-d^2 / L^2) for
+ * d <= w = min((n-1)/2, floor(L sqrt(ln 1e17))).  Writes w+1 taps to
+ * taps_out (capacity max_taps) and w to *w_out.  No device work.
+ */
+EDA_API int eda_bhalf_gaussian(int n, double length_scale, double sigma_b,
+                               double* taps_out, int max_taps, int* w_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EDA_H */

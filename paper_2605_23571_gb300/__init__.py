@@ -1,0 +1,269 @@
+"""GB300-native (sm_103a) ensemble-of-4D-Var solver with a randomized spectral
+LMP: Python binding of the C ABI in ``include/eda.h`` (``libeda.so``).
+
+The binding only marshals arguments: every step of the path (trajectories,
+tangent-linear/adjoint Hessian-vector products, Nystrom approximation, LMP,
+batched PCG) runs in the library's CUDA kernels.  There is no CPU fallback:
+importing works without a GPU, but creating a handle needs the CUDA library
+and a device, and fails loudly otherwise.
+
+Array arguments may be torch tensors (CUDA or CPU) or numpy arrays; they must
+be contiguous and FP64 (vectors) or int32 (indices).  Host arrays are staged
+by the library through device buffers (see ``include/eda.h``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libeda.so")
+
+EDA_OK, EDA_ERR_INVALID, EDA_ERR_CUDA, EDA_ERR_NUMERIC, EDA_ERR_TIMEOUT, EDA_ERR_STATE = range(6)
+EDA_FP64, EDA_MIXED = 0, 1
+EDA_THETA_GIVEN, EDA_THETA_LAMBDA_K, EDA_THETA_MID = 0, 1, 2
+EDA_CONVERGED, EDA_MAXIT, EDA_NAN, EDA_BREAKDOWN = 0, 1, 2, 3
+
+# every symbol the header declares
+EXPORTS = ["eda_version", "eda_last_error", "eda_create", "eda_destroy", "eda_twin",
+           "eda_set_trajectory", "eda_sketch", "eda_build_lmp", "eda_set_lmp", "eda_solve_batch", "eda_hvp",
+           "eda_bhalf_gaussian", "eda_kernel_launches", "eda_time_hvp_sweep", "eda_autotune"]
+
+
+class EdaError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("eda error %d: %s" % (code, msg))
+        self.code = code
+
+
+class EdaConfig(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int), ("nsteps", ctypes.c_int), ("F", ctypes.c_double), ("dt", ctypes.c_double),
+        ("n_obs_times", ctypes.c_int), ("obs_steps", ctypes.c_void_p), ("obs_ptr", ctypes.c_void_p),
+        ("obs_idx", ctypes.c_void_p), ("rinv", ctypes.c_void_p), ("bhalf_w", ctypes.c_int),
+        ("bhalf_coef", ctypes.c_void_p), ("n_members", ctypes.c_int), ("ell", ctypes.c_int),
+        ("k", ctypes.c_int), ("theta_mode", ctypes.c_int), ("theta", ctypes.c_double),
+        ("precision", ctypes.c_int), ("ckpt_every", ctypes.c_int), ("stream", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def build() -> str:
+    """Compiles libeda.so in-tree (nvcc, sm_103a)."""
+    from . import nvcc_build
+    return nvcc_build.build()
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libeda.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libeda.so not built (run paper_2605_23571_gb300.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.eda_version.restype = ctypes.c_char_p
+    L.eda_version.argtypes = []
+    L.eda_last_error.restype = ctypes.c_char_p
+    L.eda_last_error.argtypes = [vp]
+    L.eda_create.restype = i
+    L.eda_create.argtypes = [ctypes.POINTER(EdaConfig), ctypes.POINTER(vp)]
+    L.eda_destroy.restype = i
+    L.eda_destroy.argtypes = [vp]
+    L.eda_twin.restype = i
+    L.eda_twin.argtypes = [vp, vp, i, vp, vp, vp, vp, vp]
+    L.eda_set_trajectory.restype = i
+    L.eda_set_trajectory.argtypes = [vp, vp, vp, vp]
+    L.eda_sketch.restype = i
+    L.eda_sketch.argtypes = [vp, vp, i, vp]
+    L.eda_build_lmp.restype = i
+    L.eda_build_lmp.argtypes = [vp, vp, vp]
+    L.eda_set_lmp.restype = i
+    L.eda_set_lmp.argtypes = [vp, vp, vp]
+    L.eda_solve_batch.restype = i
+    L.eda_solve_batch.argtypes = [vp, d, i, vp, i, vp, vp, vp, vp]
+    L.eda_hvp.restype = i
+    L.eda_hvp.argtypes = [vp, vp, i, vp, vp, i]
+    L.eda_kernel_launches.restype = ctypes.c_longlong
+    L.eda_kernel_launches.argtypes = []
+    L.eda_autotune.restype = i
+    L.eda_autotune.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double)]
+    L.eda_time_hvp_sweep.restype = i
+    L.eda_time_hvp_sweep.argtypes = [vp, i, i, ctypes.POINTER(ctypes.c_double)]
+    L.eda_bhalf_gaussian.restype = i
+    L.eda_bhalf_gaussian.argtypes = [i, d, d, vp, i, ctypes.POINTER(ctypes.c_int)]
+    _lib = L
+    return L
+
+
+def _ptr(a, dtype, count: Optional[int] = None, name: str = "array"):
+    """Address of a contiguous torch tensor or numpy array of the given dtype."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError("%s must be a contiguous %s numpy array" % (name, np.dtype(dtype)))
+        if count is not None and a.size < count:
+            raise ValueError("%s has %d elements, needs %d" % (name, a.size, count))
+        return a.ctypes.data
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        tdt = {np.float64: torch.float64, np.int32: torch.int32}[np.dtype(dtype).type]
+        if a.dtype != tdt or not a.is_contiguous():
+            raise TypeError("%s must be a contiguous %s tensor" % (name, tdt))
+        if count is not None and a.numel() < count:
+            raise ValueError("%s has %d elements, needs %d" % (name, a.numel(), count))
+        return a.data_ptr()
+    raise TypeError("%s must be a numpy array or torch tensor" % name)
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process so far."""
+    return int(lib().eda_kernel_launches())
+
+
+def bhalf_gaussian(n: int, length_scale: float, sigma_b: float = 1.0) -> np.ndarray:
+    """Taps of U_B for a Gaussian correlation of length L (library host helper)."""
+    L = lib()
+    cap = n // 2 + 2
+    out = np.zeros(cap)
+    w = ctypes.c_int(0)
+    rc = L.eda_bhalf_gaussian(int(n), float(length_scale), float(sigma_b), out.ctypes.data, cap,
+                              ctypes.byref(w))
+    if rc != EDA_OK:
+        raise EdaError(rc, L.eda_last_error(None).decode())
+    return out[: w.value + 1].copy()
+
+
+class Handle:
+    """One EDA problem on the current CUDA device (wraps ``eda_handle``).
+
+    Methods carry the C names and arguments of ``include/eda.h``.
+    """
+
+    def __init__(self, n, nsteps, obs_steps, obs_ptr, obs_idx, rinv, bhalf_coef, n_members,
+                 ell, k, theta_mode=EDA_THETA_MID, theta=1.0, precision=EDA_FP64, ckpt_every=0,
+                 F=8.0, dt=0.025, stream=None):
+        self._L = lib()
+        self.n, self.nsteps, self.M = int(n), int(nsteps), int(n_members)
+        self._keep = [np.ascontiguousarray(obs_steps, dtype=np.int32),
+                      np.ascontiguousarray(obs_ptr, dtype=np.int32),
+                      np.ascontiguousarray(obs_idx, dtype=np.int32),
+                      np.ascontiguousarray(rinv, dtype=np.float64),
+                      np.ascontiguousarray(bhalf_coef, dtype=np.float64)]
+        steps, ptr, idx, rv, coef = self._keep
+        self.p = int(ptr[-1])
+        self.ell, self.k = int(ell), int(k)
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except ImportError:  # pragma: no cover
+                stream = 0
+        cfg = EdaConfig(n=self.n, nsteps=self.nsteps, F=float(F), dt=float(dt),
+                        n_obs_times=len(steps), obs_steps=steps.ctypes.data,
+                        obs_ptr=ptr.ctypes.data, obs_idx=idx.ctypes.data, rinv=rv.ctypes.data,
+                        bhalf_w=len(coef) - 1, bhalf_coef=coef.ctypes.data, n_members=self.M,
+                        ell=self.ell, k=self.k, theta_mode=int(theta_mode), theta=float(theta),
+                        precision=int(precision), ckpt_every=int(ckpt_every),
+                        stream=ctypes.c_void_p(int(stream)))
+        h = ctypes.c_void_p(None)
+        rc = self._L.eda_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc != EDA_OK:
+            raise EdaError(rc, self._L.eda_last_error(None).decode())
+        self._h = h
+
+    @classmethod
+    def from_spec(cls, spec, taps, precision=EDA_FP64, stream=None, **kw):
+        args = dict(n=spec.n, nsteps=spec.nsteps, obs_steps=spec.obs_steps, obs_ptr=spec.obs_ptr,
+                    obs_idx=spec.obs_idx, rinv=spec.rinv, bhalf_coef=taps,
+                    n_members=spec.n_members, ell=spec.ell, k=spec.k, theta_mode=spec.theta_mode,
+                    theta=spec.theta, precision=precision, ckpt_every=spec.ckpt_every, F=spec.F,
+                    dt=spec.dt, stream=stream)
+        args.update(kw)
+        return cls(**args)
+
+    def _check(self, rc):
+        if rc != EDA_OK:
+            raise EdaError(rc, self._L.eda_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._L.eda_destroy(self._h)
+            self._h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ----------------------------------------------------------------- calls
+    def eda_twin(self, x_spin0, spinup, eta_b, eta_o, xb_out, y_out, xt0_out=None):
+        n, M, p = self.n, self.M, self.p
+        self._check(self._L.eda_twin(
+            self._h, _ptr(x_spin0, np.float64, n, "x_spin0"), int(spinup),
+            _ptr(eta_b, np.float64, M * n, "eta_b"), _ptr(eta_o, np.float64, M * p, "eta_o"),
+            _ptr(xb_out, np.float64, M * n, "xb_out"), _ptr(y_out, np.float64, M * p, "y_out"),
+            _ptr(xt0_out, np.float64, n, "xt0_out")))
+
+    def eda_set_trajectory(self, xb, y, rhs_out=None):
+        n, M, p = self.n, self.M, self.p
+        self._check(self._L.eda_set_trajectory(
+            self._h, _ptr(xb, np.float64, M * n, "xb"), _ptr(y, np.float64, M * p, "y"),
+            _ptr(rhs_out, np.float64, M * n, "rhs_out")))
+
+    def eda_sketch(self, phi=None, q=1, y_out=None):
+        n, ell = self.n, self.ell
+        self._check(self._L.eda_sketch(self._h, _ptr(phi, np.float64, ell * n, "phi"), int(q),
+                                       _ptr(y_out, np.float64, ell * n, "y_out")))
+
+    def eda_build_lmp(self, eigvals_out=None, s_out=None):
+        self._check(self._L.eda_build_lmp(self._h, _ptr(eigvals_out, np.float64, self.k, "eigvals_out"),
+                                          _ptr(s_out, np.float64, self.k * self.n, "s_out")))
+
+    def eda_set_lmp(self, s_in, eigvals_in):
+        self._check(self._L.eda_set_lmp(self._h, _ptr(s_in, np.float64, self.k * self.n, "s_in"),
+                                        _ptr(eigvals_in, np.float64, self.k, "eigvals_in")))
+
+    def eda_solve_batch(self, tol, maxit, x0, use_lmp, dz_out, iters_out=None, relres_out=None,
+                        status_out=None):
+        n, M = self.n, self.M
+        self._check(self._L.eda_solve_batch(
+            self._h, float(tol), int(maxit), _ptr(x0, np.float64, M * n, "x0"), 1 if use_lmp else 0,
+            _ptr(dz_out, np.float64, M * n, "dz_out"), _ptr(iters_out, np.int32, M, "iters_out"),
+            _ptr(relres_out, np.float64, M, "relres_out"), _ptr(status_out, np.int32, M, "status_out")))
+
+    def eda_autotune(self, which=0):
+        """Times the sweep tilings on the stored trajectories, keeps the fastest."""
+        ms = ctypes.c_double(0.0)
+        self._check(self._L.eda_autotune(self._h, int(which), ctypes.byref(ms)))
+        return ms.value
+
+    def eda_time_hvp_sweep(self, reps=10, fp64=False):
+        """Mean milliseconds per launch of the batched member HVP sweep."""
+        ms = ctypes.c_double(0.0)
+        self._check(self._L.eda_time_hvp_sweep(self._h, int(reps), 1 if fp64 else 0, ctypes.byref(ms)))
+        return ms.value
+
+    def eda_hvp(self, member_of_col, V, HV, include_identity=True):
+        ncol = int(np.asarray(member_of_col.shape[0] if hasattr(member_of_col, "shape") else len(member_of_col)))
+        n = self.n
+        self._check(self._L.eda_hvp(self._h, _ptr(member_of_col, np.int32, ncol, "member_of_col"), ncol,
+                                    _ptr(V, np.float64, ncol * n, "V"), _ptr(HV, np.float64, ncol * n, "HV"),
+                                    1 if include_identity else 0))

@@ -1,0 +1,1212 @@
+// C ABI of libeda.so: the EDA handle and the orchestration of the sweeps,
+// the Nystrom/LMP build and the batched PCG on one CUDA stream.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dense.h"
+#include "eda_internal.h"
+
+namespace eda {
+namespace {
+std::atomic<long long> g_launches{0};
+}
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+}  // namespace eda
+
+using eda::PcgScalars;
+using eda::SweepArgs;
+using eda::SweepPlan;
+
+struct eda_handle {
+  // problem
+  int n = 0, N = 0, M = 0, p = 0, nos = 0, w = 0, ell = 0, k = 0;
+  int theta_mode = 0, precision = 0, ckpt = 0;
+  double F = 8.0, dt = 0.025, theta_given = 1.0;
+  cudaStream_t st = nullptr;
+  std::string err;
+  std::vector<int> h_obs_of_t;
+  // device: problem definition
+  int* obs_of_t = nullptr;
+  int* obs_ptr = nullptr;
+  int* obs_idx = nullptr;
+  double* rinv = nullptr;
+  float* rinv32 = nullptr;
+  double* bcoef = nullptr;
+  float* bcoef32 = nullptr;
+  // device: setup products
+  double* traj = nullptr;
+  float* traj32 = nullptr;
+  double* d = nullptr;
+  double* rd = nullptr;
+  double* b = nullptr;
+  // device: sketch and LMP
+  double* Phi = nullptr;
+  double* Y = nullptr;
+  float* V32a = nullptr;  // ell x n scratch (FP32 sweeps)
+  float* V32b = nullptr;
+  double* Q1 = nullptr;
+  double* Q = nullptr;
+  double* G = nullptr;
+  double* R1 = nullptr;
+  double* R1i = nullptr;
+  double* R2 = nullptr;
+  double* R2i = nullptr;
+  double* RY = nullptr;
+  double* W = nullptr;
+  double* UT = nullptr;
+  double* Dv = nullptr;
+  double* cv = nullptr;
+  double* theta = nullptr;
+  int* dstatus = nullptr;
+  double* S = nullptr;
+  float* S32 = nullptr;
+  double* lmpW = nullptr;  // k x M
+  // device: PCG
+  double *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr;
+  float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
+  PcgScalars* sc = nullptr;
+  int* active = nullptr;
+  int* nactive = nullptr;
+  int* cols = nullptr;  // identity member map 0..max(M, ell)-1
+  int* zeros = nullptr; // member map of zeros (control trajectory)
+  int* hflag = nullptr; // pinned host int
+  // stash
+  double* stash = nullptr;
+  float* stash32 = nullptr;
+  int stash_cols = 0;
+  // state
+  bool have_traj = false, have_sketch = false, have_lmp = false;
+  double shift_used = 0.0;
+  SweepPlan plan64{}, plan32{};
+  int* tab64 = nullptr;  // per-CTA observation ranges of plan64 / plan32
+  int* tab32 = nullptr;
+  bool tab64_ok = false, tab32_ok = false;
+  std::vector<int> h_obs_ptr, h_obs_idx;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(eda_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  g_err = msg;
+  return code;
+}
+
+#define CU(h, ...)                                                                               \
+  do {                                                                                           \
+    cudaError_t e__ = (__VA_ARGS__);                                                             \
+    if (e__ != cudaSuccess) {                                                                    \
+      return fail((h), EDA_ERR_CUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e__)); \
+    }                                                                                            \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(eda_handle* h, T** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaSuccess) h->allocs.push_back((void*)*p);
+  return e;
+}
+
+bool is_device_ptr(const void* ptr) {
+  if (ptr == nullptr) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// An input array given as host or device memory, seen as device memory.
+struct In {
+  const void* dev = nullptr;
+  void* tmp = nullptr;
+  cudaStream_t st = nullptr;
+  cudaError_t init(const void* p, size_t bytes, cudaStream_t s) {
+    st = s;
+    if (p == nullptr || is_device_ptr(p)) {
+      dev = p;
+      return cudaSuccess;
+    }
+    cudaError_t e = cudaMallocAsync(&tmp, bytes ? bytes : 1, s);
+    if (e != cudaSuccess) return e;
+    dev = tmp;
+    return cudaMemcpyAsync(tmp, p, bytes, cudaMemcpyHostToDevice, s);
+  }
+  ~In() {
+    if (tmp) cudaFreeAsync(tmp, st);
+  }
+};
+
+// An output array given as host or device memory.
+struct Out {
+  void* host = nullptr;
+  void* dev = nullptr;
+  void* tmp = nullptr;
+  size_t bytes = 0;
+  cudaStream_t st = nullptr;
+  cudaError_t init(void* p, size_t nbytes, cudaStream_t s) {
+    st = s;
+    bytes = nbytes;
+    if (p == nullptr || is_device_ptr(p)) {
+      dev = p;
+      return cudaSuccess;
+    }
+    host = p;
+    cudaError_t e = cudaMallocAsync(&tmp, nbytes ? nbytes : 1, s);
+    dev = tmp;
+    return e;
+  }
+  cudaError_t finish() {
+    if (!host) return cudaSuccess;
+    return cudaMemcpyAsync(host, tmp, bytes, cudaMemcpyDeviceToHost, st);
+  }
+  ~Out() {
+    if (tmp) cudaFreeAsync(tmp, st);
+  }
+};
+
+// ----------------------------------------------------------------- small kernels
+__global__ void count_nonfinite_kernel(long long count, const double* v, int* flag) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(v[i])) atomicAdd(flag, 1);
+}
+
+__global__ void gamma_kernel(int n, int ell, const double* b, double* Phi) {
+  const long long total = (long long)ell * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int g = (int)(i % n);
+    const long long c = i / n;
+    Phi[i] = b[(c + 1) * n + g] - b[g];
+  }
+}
+
+__global__ void axpy_kernel(long long count, double alpha, const double* xv, double* yv) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    yv[i] += alpha * xv[i];
+}
+
+template <typename T>
+__global__ void sub_kernel(long long count, const double* a, const T* bq, T* out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = (T)(a[i] - (double)bq[i]);
+}
+
+__global__ void bhalf_apply_kernel(int n, int w, const double* coef, int ncol, const double* V, double* out) {
+  const long long total = (long long)ncol * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int g = (int)(i % n);
+    const double* v = V + (i / n) * n;
+    double acc = coef[0] * v[g];
+    for (int dd = 1; dd <= w; ++dd) {
+      int gm = g - dd;
+      if (gm < 0) gm += n;
+      int gq = g + dd;
+      if (gq >= n) gq -= n;
+      acc += coef[dd] * (v[gm] + v[gq]);
+    }
+    out[i] = acc;
+  }
+}
+
+// xb_j = xt + U_B(eta_0 + eta_j) -- the sum is formed first by twin_sum_kernel
+__global__ void twin_sum_kernel(int n, int M, const double* eta, double* out) {
+  const long long total = (long long)M * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long j = i / n;
+    const int g = (int)(i % n);
+    out[i] = eta[g] + (j > 0 ? eta[i] : 0.0);
+  }
+}
+
+__global__ void twin_x_kernel(int n, int M, const double* xt, double* xb) {
+  const long long total = (long long)M * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    xb[i] += xt[i % n];
+}
+
+__global__ void twin_y_kernel(int p, int M, const double* ytrue, const double* rinv, const double* eta,
+                              double* y) {
+  const long long total = (long long)M * p;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long j = i / p;
+    const int kk = (int)(i % p);
+    const double e = eta[kk] + (j > 0 ? eta[i] : 0.0);
+    y[i] = ytrue[kk] + e / sqrt(rinv[kk]);
+  }
+}
+
+__global__ void iota_kernel(int count, int* v, int value_mode) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x)
+    v[i] = value_mode ? i : 0;
+}
+
+__global__ void export_kernel(int M, const PcgScalars* sc, int* iters, double* relres, int* status) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
+    if (iters) iters[j] = sc[j].iters;
+    if (relres) relres[j] = sc[j].relres;
+    if (status) status[j] = sc[j].status;
+  }
+}
+
+__global__ void eig_kernel(int k, const double* D, double* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) out[i] = 1.0 + D[i];
+}
+
+// true-residual bookkeeping of the mixed solve
+__global__ void true_res_kernel(int n, const double* b, const double* hx, float* r32, PcgScalars* sc,
+                                int* active, double tol, int* nactive, int* need) {
+  __shared__ double red[32];
+  const int j = blockIdx.x;
+  const double* bj = b + (long long)j * n;
+  const double* hj = hx + (long long)j * n;
+  float* rj = r32 + (long long)j * n;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < n; g += blockDim.x) {
+    const double rv = bj[g] - hj[g];
+    rj[g] = (float)rv;
+    s += rv * rv;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    const double bn = sc[j].bnorm;
+    const double rel = bn > 0.0 ? sqrt(t) / bn : 0.0;
+    sc[j].relres = rel;
+    const bool ok = (bn == 0.0) || (rel <= tol);
+    if (sc[j].status == EDA_CONVERGED && !ok) {
+      // recurrence said converged, the FP64 residual disagrees: continue
+      sc[j].status = EDA_MAXIT;
+      active[j] = 1;
+      atomicAdd(nactive, 1);
+      atomicAdd(need, 1);
+    }
+  }
+}
+
+inline unsigned grid_for(long long count) {
+  long long g = (count + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > 8192) g = 8192;
+  return (unsigned)g;
+}
+
+// ------------------------------------------------------------- sweep helpers
+template <typename T>
+SweepArgs<T> base_args(eda_handle* h) {
+  SweepArgs<T> a{};
+  a.n = h->n;
+  a.N = h->N;
+  a.F = (T)h->F;
+  a.dt = (T)h->dt;
+  a.obs_of_t = h->obs_of_t;
+  a.obs_ptr = h->obs_ptr;
+  a.obs_idx = h->obs_idx;
+  a.p = h->p;
+  a.w = h->w;
+  a.nos = h->nos;
+  if constexpr (sizeof(T) == 8) {
+    a.traj = h->traj;
+    a.rinv = h->rinv;
+    a.bcoef = h->bcoef;
+    a.obs_tab = h->tab64_ok ? h->tab64 : nullptr;
+  } else {
+    a.traj = h->traj32;
+    a.rinv = h->rinv32;
+    a.bcoef = h->bcoef32;
+    a.obs_tab = h->tab32_ok ? h->tab32 : nullptr;
+  }
+  a.traj_mstride = (long long)(h->N + 1) * h->n;
+  return a;
+}
+
+int ensure_stash(eda_handle* h, int ncol) {
+  if (ncol <= h->stash_cols) return EDA_OK;
+  if (h->stash) cudaFree(h->stash);
+  if (h->stash32) cudaFree(h->stash32);
+  h->stash = nullptr;
+  h->stash32 = nullptr;
+  for (auto& p : h->allocs)
+    if (p == (void*)h->stash || p == (void*)h->stash32) p = nullptr;
+  const size_t cnt = (size_t)ncol * (size_t)(h->p > 0 ? h->p : 1);
+  CU(h, cudaMalloc((void**)&h->stash, cnt * sizeof(double)));
+  CU(h, cudaMalloc((void**)&h->stash32, cnt * sizeof(float)));
+  h->stash_cols = ncol;
+  return EDA_OK;
+}
+
+// Installs a sweep tiling and its observation table.
+int set_plan(eda_handle* h, bool fp64, const SweepPlan& pl) {
+  std::vector<int> tab((size_t)pl.CS * h->nos * 8);
+  bool ok = false;
+  eda::obs_table(pl, h->n, h->nos, h->h_obs_ptr.data(), h->h_obs_idx.data(), tab.data(), &ok);
+  int*& dt = fp64 ? h->tab64 : h->tab32;
+  if (dt) {
+    CU(h, cudaStreamSynchronize(h->st));
+    CU(h, cudaFree(dt));
+    dt = nullptr;
+  }
+  if (ok) {
+    CU(h, cudaMalloc((void**)&dt, tab.size() * sizeof(int)));
+    CU(h, cudaMemcpy(dt, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  if (fp64) {
+    h->plan64 = pl;
+    h->tab64_ok = ok;
+  } else {
+    h->plan32 = pl;
+    h->tab32_ok = ok;
+  }
+  return EDA_OK;
+}
+
+// HV = (ident ? V : 0) + A_{m(c)} V for ncol columns, device pointers, FP64 at
+// the interface; FP32 sweeps in EDA_MIXED unless force64.
+int hvp_dev(eda_handle* h, const int* dcols, int ncol, const double* V, double* HV, int ident, bool force64,
+            const int* active) {
+  if (ncol <= 0) return EDA_OK;
+  int rc = ensure_stash(h, ncol);
+  if (rc) return rc;
+  if (h->precision == EDA_FP64 || force64) {
+    SweepArgs<double> a = base_args<double>(h);
+    a.mode = eda::MODE_HVP;
+    a.ncol = ncol;
+    a.col_member = dcols;
+    a.col_active = active;
+    a.V = V;
+    a.v_stride = h->n;
+    a.OUT = HV;
+    a.out_stride = h->n;
+    a.stash = h->stash;
+    a.stash_stride = h->p;
+    a.include_identity = ident;
+    CU(h, eda::launch_sweep<double>(a, h->plan64, h->st));
+    return EDA_OK;
+  }
+  // FP32 sweeps through scratch vectors
+  float *v32 = nullptr, *o32 = nullptr;
+  const size_t cnt = (size_t)ncol * h->n;
+  CU(h, cudaMallocAsync((void**)&v32, cnt * sizeof(float), h->st));
+  CU(h, cudaMallocAsync((void**)&o32, cnt * sizeof(float), h->st));
+  CU(h, eda::convert<double, float>((long long)cnt, V, v32, h->st));
+  SweepArgs<float> a = base_args<float>(h);
+  a.mode = eda::MODE_HVP;
+  a.ncol = ncol;
+  a.col_member = dcols;
+  a.col_active = active;
+  a.V = v32;
+  a.v_stride = h->n;
+  a.OUT = o32;
+  a.out_stride = h->n;
+  a.stash = h->stash32;
+  a.stash_stride = h->p;
+  a.include_identity = ident;
+  CU(h, eda::launch_sweep<float>(a, h->plan32, h->st));
+  CU(h, eda::convert<float, double>((long long)cnt, o32, HV, h->st));
+  CU(h, cudaFreeAsync(v32, h->st));
+  CU(h, cudaFreeAsync(o32, h->st));
+  return EDA_OK;
+}
+
+// FP32 HVP on FP32 vectors (the mixed PCG), active mask.
+int hvp32_dev(eda_handle* h, const float* V, float* HV, const int* active) {
+  int rc = ensure_stash(h, h->M);
+  if (rc) return rc;
+  SweepArgs<float> a = base_args<float>(h);
+  a.mode = eda::MODE_HVP;
+  a.ncol = h->M;
+  a.col_member = h->cols;
+  a.col_active = active;
+  a.V = V;
+  a.v_stride = h->n;
+  a.OUT = HV;
+  a.out_stride = h->n;
+  a.stash = h->stash32;
+  a.stash_stride = h->p;
+  a.include_identity = 1;
+  CU(h, eda::launch_sweep<float>(a, h->plan32, h->st));
+  return EDA_OK;
+}
+
+int read_flag(eda_handle* h, const int* dflag, int* out) {
+  CU(h, cudaMemcpyAsync(h->hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CU(h, cudaStreamSynchronize(h->st));
+  *out = *h->hflag;
+  return EDA_OK;
+}
+
+// CholeskyQR2 of Y (ell columns): Q (n x ell) and R_Y = R2 R1 (ell x ell).
+// Falls back to a shifted first pass when the Gram matrix is not positive
+// definite to working precision.
+int cholqr2(eda_handle* h, const double* Yin, double* Qout) {
+  const int n = h->n, m = h->ell;
+  int st = 0;
+  CU(h, eda::gemm_tn<double, double>(n, Yin, m, Yin, m, h->G, m, nullptr, true, h->st));
+  CU(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
+  CU(h, eda::chol_inv(h->G, m, 0.0, h->R1, h->R1i, h->dstatus, h->st));
+  int rc = read_flag(h, h->dstatus, &st);
+  if (rc) return rc;
+  if (st) {
+    // shifted CholeskyQR: G + s I with s proportional to u * ||Y||_F^2
+    std::vector<double> Gh((size_t)m * m);
+    CU(h, cudaMemcpyAsync(Gh.data(), h->G, Gh.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CU(h, cudaStreamSynchronize(h->st));
+    double tr = 0.0;
+    for (int i = 0; i < m; ++i) tr += Gh[(size_t)i * m + i];
+    const double shift = 11.0 * ((double)n * m + (double)m * (m + 1)) * 1.1102230246251565e-16 * tr;
+    CU(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
+    CU(h, eda::chol_inv(h->G, m, shift, h->R1, h->R1i, h->dstatus, h->st));
+    rc = read_flag(h, h->dstatus, &st);
+    if (rc) return rc;
+    if (st) return fail(h, EDA_ERR_NUMERIC, "sketch QR: Gram matrix not positive definite even after shift");
+  }
+  CU(h, eda::gemm_nn<double, double>(n, Yin, m, m, h->R1i, nullptr, nullptr, h->Q1, nullptr, h->st));
+  CU(h, eda::gemm_tn<double, double>(n, h->Q1, m, h->Q1, m, h->G, m, nullptr, true, h->st));
+  CU(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
+  CU(h, eda::chol_inv(h->G, m, 0.0, h->R2, h->R2i, h->dstatus, h->st));
+  rc = read_flag(h, h->dstatus, &st);
+  if (rc) return rc;
+  if (st) return fail(h, EDA_ERR_NUMERIC, "sketch QR: second CholeskyQR pass failed");
+  CU(h, eda::gemm_nn<double, double>(n, h->Q1, m, m, h->R2i, nullptr, nullptr, Qout, nullptr, h->st));
+  CU(h, eda::tri_mul(h->R2, h->R1, h->RY, m, h->st));
+  return EDA_OK;
+}
+
+// z = P r for active members (or z = r without the LMP).
+template <typename T>
+int lmp_apply_dev(eda_handle* h, const T* r, T* z, bool use_lmp) {
+  const int n = h->n, M = h->M;
+  if (!use_lmp) {
+    CU(h, cudaMemcpyAsync(z, r, (size_t)M * n * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
+    return EDA_OK;
+  }
+  const T* Sx;
+  if constexpr (sizeof(T) == 8)
+    Sx = h->S;
+  else
+    Sx = h->S32;
+  CU(h, eda::gemm_tn<T, T>(n, Sx, h->k, r, M, h->lmpW, h->k, h->active, false, h->st));
+  CU(h, eda::gemm_nn<T, T>(n, Sx, h->k, M, h->lmpW, h->cv, r, z, h->active, h->st));
+  return EDA_OK;
+}
+
+int check_finite(eda_handle* h, const double* v, long long count, const char* what) {
+  CU(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
+  eda::count_launch();
+  count_nonfinite_kernel<<<grid_for(count), 256, 0, h->st>>>(count, v, h->dstatus);
+  CU(h, cudaGetLastError());
+  int bad = 0;
+  int rc = read_flag(h, h->dstatus, &bad);
+  if (rc) return rc;
+  if (bad) return fail(h, EDA_ERR_NUMERIC, std::string("non-finite values in ") + what);
+  return EDA_OK;
+}
+
+int env_int(const char* name, int dflt) {
+  const char* s = std::getenv(name);
+  return (s && *s) ? std::atoi(s) : dflt;
+}
+
+}  // namespace
+
+// =========================================================================
+// C ABI
+// =========================================================================
+
+extern "C" {
+
+EDA_API const char* eda_version(void) { return "eda-gb300 0.1 (sm_103a)"; }
+
+EDA_API long long eda_kernel_launches(void) { return eda::g_launches.load(std::memory_order_relaxed); }
+
+EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (!h->have_traj) return fail(h, EDA_ERR_STATE, "eda_autotune before eda_set_trajectory");
+  if (which == 0) which = (h->precision == EDA_FP64) ? 1 : 3;
+  const size_t cnt = (size_t)h->M * h->n;
+  cudaEvent_t e0, e1;
+  CU(h, cudaEventCreate(&e0));
+  CU(h, cudaEventCreate(&e1));
+  const int Ks[] = {2, 4, 8, 16};
+  double best_total = 0.0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool fp64 = (pass == 0);
+    if (!(which & (fp64 ? 1 : 2))) continue;
+    if (!fp64 && h->precision != EDA_MIXED) continue;
+    if (fp64) {
+      CU(h, cudaMemcpyAsync(h->pv, h->b, cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    } else {
+      CU(h, eda::convert<double, float>((long long)cnt, h->b, h->p32, h->st));
+    }
+    const SweepPlan keep = fp64 ? h->plan64 : h->plan32;
+    SweepPlan best = keep;
+    float best_ms = 1e30f;
+    const int reps = fp64 ? 1 : 3;
+    for (int CS = 1; CS <= 8; ++CS) {
+      for (int K : Ks) {
+        SweepPlan pl;
+        if (!eda::plan_sweep_exact(h->n, fp64 ? 8 : 4, h->w, CS, K, &pl)) continue;
+        if (pl.HL > h->n && CS > 1) continue;
+        int rc = set_plan(h, fp64, pl);
+        if (rc) return rc;
+        float ms = 0.f;
+        for (int rep = -1; rep < reps; ++rep) {
+          if (rep == 0) CU(h, cudaEventRecord(e0, h->st));
+          rc = fp64 ? hvp_dev(h, h->cols, h->M, h->pv, h->q, 1, true, nullptr) : hvp32_dev(h, h->p32, h->q32, nullptr);
+          if (rc) return rc;
+        }
+        CU(h, cudaEventRecord(e1, h->st));
+        CU(h, cudaEventSynchronize(e1));
+        CU(h, cudaEventElapsedTime(&ms, e0, e1));
+        ms /= reps;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = pl;
+        }
+      }
+    }
+    int rc = set_plan(h, fp64, best);
+    if (rc) return rc;
+    best_total += best_ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best_ms_out) *best_ms_out = best_total;
+  return EDA_OK;
+}
+
+EDA_API int eda_time_hvp_sweep(eda_handle* h, int reps, int fp64, double* ms_out) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (!h->have_traj) return fail(h, EDA_ERR_STATE, "eda_time_hvp_sweep before eda_set_trajectory");
+  if (reps < 1 || !ms_out) return fail(h, EDA_ERR_INVALID, "eda_time_hvp_sweep: invalid argument");
+  const bool use64 = fp64 || h->precision == EDA_FP64;
+  const size_t cnt = (size_t)h->M * h->n;
+  if (use64) {
+    CU(h, cudaMemcpyAsync(h->pv, h->b, cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  } else {
+    CU(h, eda::convert<double, float>((long long)cnt, h->b, h->p32, h->st));
+  }
+  cudaEvent_t e0, e1;
+  CU(h, cudaEventCreate(&e0));
+  CU(h, cudaEventCreate(&e1));
+  int rc = EDA_OK;
+  float ms = 0.f;
+  for (int rep = -1; rep < reps && rc == EDA_OK; ++rep) {
+    if (rep == 0) CU(h, cudaEventRecord(e0, h->st));
+    rc = use64 ? hvp_dev(h, h->cols, h->M, h->pv, h->q, 1, true, nullptr) : hvp32_dev(h, h->p32, h->q32, nullptr);
+  }
+  CU(h, cudaEventRecord(e1, h->st));
+  CU(h, cudaEventSynchronize(e1));
+  CU(h, cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  *ms_out = (double)ms / reps;
+  return EDA_OK;
+}
+
+EDA_API const char* eda_last_error(const eda_handle* h) { return h ? h->err.c_str() : g_err.c_str(); }
+
+EDA_API int eda_bhalf_gaussian(int n, double length_scale, double sigma_b, double* taps_out, int max_taps,
+                               int* w_out) {
+  if (n < 1 || !(length_scale > 0.0) || !(sigma_b > 0.0) || !taps_out || max_taps < 1 || !w_out)
+    return fail(nullptr, EDA_ERR_INVALID, "eda_bhalf_gaussian: invalid argument");
+  const double L = length_scale;
+  int wcut = (int)std::floor(L * std::sqrt(-std::log(1e-17)));
+  int w = (n - 1) / 2;
+  if (wcut < w) w = wcut;
+  if (w < 0) w = 0;
+  if (w + 1 > max_taps) return fail(nullptr, EDA_ERR_INVALID, "eda_bhalf_gaussian: max_taps too small");
+  const double c0 = sigma_b * std::pow(2.0 / (M_PI * L * L), 0.25);
+  for (int dd = 0; dd <= w; ++dd) taps_out[dd] = c0 * std::exp(-(double)dd * dd / (L * L));
+  *w_out = w;
+  return EDA_OK;
+}
+
+EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
+  if (!out) return fail(nullptr, EDA_ERR_INVALID, "eda_create: out is NULL");
+  *out = nullptr;
+  if (!cfg) return fail(nullptr, EDA_ERR_INVALID, "eda_create: cfg is NULL");
+  const eda_config& c = *cfg;
+  if (c.n < 4) return fail(nullptr, EDA_ERR_INVALID, "n must be >= 4");
+  if (c.nsteps < 1) return fail(nullptr, EDA_ERR_INVALID, "nsteps must be >= 1");
+  if (!std::isfinite(c.F) || !(c.dt > 0.0) || !std::isfinite(c.dt))
+    return fail(nullptr, EDA_ERR_INVALID, "F and dt must be finite, dt > 0");
+  if (c.n_obs_times < 1 || !c.obs_steps || !c.obs_ptr || !c.obs_idx || !c.rinv)
+    return fail(nullptr, EDA_ERR_INVALID, "observation network missing");
+  if (c.n_members < 1) return fail(nullptr, EDA_ERR_INVALID, "n_members must be >= 1");
+  if (c.bhalf_w < 0 || c.bhalf_w > (c.n - 1) / 2 || !c.bhalf_coef)
+    return fail(nullptr, EDA_ERR_INVALID, "bhalf_w must be in [0, (n-1)/2] with coefficients");
+  if (c.ell < 0 || c.ell > c.n_members - 1 || c.ell > 88 || c.ell > c.n)
+    return fail(nullptr, EDA_ERR_INVALID, "ell must be in [0, min(L, 88, n)]");
+  if (c.ell > 0 && (c.k < 1 || c.k > c.ell)) return fail(nullptr, EDA_ERR_INVALID, "k must be in [1, ell]");
+  if (c.theta_mode < 0 || c.theta_mode > 2) return fail(nullptr, EDA_ERR_INVALID, "bad theta_mode");
+  if (c.theta_mode == EDA_THETA_GIVEN && !(c.theta > 0.0)) return fail(nullptr, EDA_ERR_INVALID, "theta must be > 0");
+  if (c.precision != EDA_FP64 && c.precision != EDA_MIXED) return fail(nullptr, EDA_ERR_INVALID, "bad precision");
+  if (c.ckpt_every != 0) return fail(nullptr, EDA_ERR_INVALID, "ckpt_every > 0 is not supported by this build");
+  // observation network
+  int prev = -1;
+  for (int j = 0; j < c.n_obs_times; ++j) {
+    if (c.obs_steps[j] <= prev || c.obs_steps[j] < 0 || c.obs_steps[j] > c.nsteps)
+      return fail(nullptr, EDA_ERR_INVALID, "obs_steps must be strictly increasing in [0, nsteps]");
+    prev = c.obs_steps[j];
+  }
+  if (c.obs_ptr[0] != 0) return fail(nullptr, EDA_ERR_INVALID, "obs_ptr[0] must be 0");
+  for (int j = 0; j < c.n_obs_times; ++j) {
+    if (c.obs_ptr[j + 1] < c.obs_ptr[j]) return fail(nullptr, EDA_ERR_INVALID, "obs_ptr must be non-decreasing");
+    int last = -1;
+    for (int kk = c.obs_ptr[j]; kk < c.obs_ptr[j + 1]; ++kk) {
+      if (c.obs_idx[kk] <= last || c.obs_idx[kk] >= c.n)
+        return fail(nullptr, EDA_ERR_INVALID, "obs_idx must be strictly increasing in [0, n) per step");
+      last = c.obs_idx[kk];
+      if (!(c.rinv[kk] > 0.0) || !std::isfinite(c.rinv[kk]))
+        return fail(nullptr, EDA_ERR_INVALID, "rinv must be positive and finite");
+    }
+  }
+  const int p = c.obs_ptr[c.n_obs_times];
+  if (p < 1) return fail(nullptr, EDA_ERR_INVALID, "no observations");
+  for (int dd = 0; dd <= c.bhalf_w; ++dd)
+    if (!std::isfinite(c.bhalf_coef[dd])) return fail(nullptr, EDA_ERR_INVALID, "bhalf_coef not finite");
+
+  eda_handle* h = new eda_handle();
+  h->n = c.n;
+  h->N = c.nsteps;
+  h->M = c.n_members;
+  h->p = p;
+  h->nos = c.n_obs_times;
+  h->w = c.bhalf_w;
+  h->ell = c.ell;
+  h->k = c.ell > 0 ? c.k : 0;
+  h->theta_mode = c.theta_mode;
+  h->theta_given = c.theta;
+  h->precision = c.precision;
+  h->ckpt = c.ckpt_every;
+  h->F = c.F;
+  h->dt = c.dt;
+  h->st = (cudaStream_t)c.stream;
+
+  auto bail = [&](int code) {
+    eda_destroy(h);
+    return code;
+  };
+#define CUC(...)                                                                                 \
+  do {                                                                                           \
+    cudaError_t e__ = (__VA_ARGS__);                                                             \
+    if (e__ != cudaSuccess) {                                                                    \
+      fail(nullptr, EDA_ERR_CUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e__));   \
+      return bail(EDA_ERR_CUDA);                                                                 \
+    }                                                                                            \
+  } while (0)
+
+  const int Kh = env_int("EDA_SWEEP_K", 0);
+  const int cs64 = env_int("EDA_SWEEP_CS64", 1), cs32 = env_int("EDA_SWEEP_CS32", 1);
+  if (!eda::plan_sweep(h->n, 8, h->w, cs64, Kh, &h->plan64) || !eda::plan_sweep(h->n, 4, h->w, cs32, Kh, &h->plan32)) {
+    fail(nullptr, EDA_ERR_INVALID, "state size too large for the sweep tiling");
+    return bail(EDA_ERR_INVALID);
+  }
+
+  h->h_obs_ptr.assign(c.obs_ptr, c.obs_ptr + h->nos + 1);
+  h->h_obs_idx.assign(c.obs_idx, c.obs_idx + p);
+  h->h_obs_of_t.assign(h->N + 1, -1);
+  for (int j = 0; j < c.n_obs_times; ++j) h->h_obs_of_t[c.obs_steps[j]] = j;
+  const int n = h->n, N = h->N, M = h->M, ell = h->ell, kk = h->k;
+  const int mcols = std::max(M, std::max(ell, 1));
+  CUC(dalloc(h, &h->obs_of_t, N + 1));
+  CUC(dalloc(h, &h->obs_ptr, h->nos + 1));
+  CUC(dalloc(h, &h->obs_idx, p));
+  CUC(dalloc(h, &h->rinv, p));
+  CUC(dalloc(h, &h->rinv32, p));
+  CUC(dalloc(h, &h->bcoef, h->w + 1));
+  CUC(dalloc(h, &h->bcoef32, h->w + 1));
+  CUC(dalloc(h, &h->traj, (size_t)M * (N + 1) * n));
+  if (h->precision == EDA_MIXED) CUC(dalloc(h, &h->traj32, (size_t)M * (N + 1) * n));
+  CUC(dalloc(h, &h->d, (size_t)M * p));
+  CUC(dalloc(h, &h->rd, (size_t)M * p));
+  CUC(dalloc(h, &h->b, (size_t)M * n));
+  const int me = std::max(ell, 1);
+  CUC(dalloc(h, &h->Phi, (size_t)me * n));
+  CUC(dalloc(h, &h->Y, (size_t)me * n));
+  CUC(dalloc(h, &h->Q1, (size_t)me * n));
+  CUC(dalloc(h, &h->Q, (size_t)me * n));
+  CUC(dalloc(h, &h->G, (size_t)me * me));
+  CUC(dalloc(h, &h->R1, (size_t)me * me));
+  CUC(dalloc(h, &h->R1i, (size_t)me * me));
+  CUC(dalloc(h, &h->R2, (size_t)me * me));
+  CUC(dalloc(h, &h->R2i, (size_t)me * me));
+  CUC(dalloc(h, &h->RY, (size_t)me * me));
+  CUC(dalloc(h, &h->W, (size_t)me * me));
+  CUC(dalloc(h, &h->UT, (size_t)me * me));
+  CUC(dalloc(h, &h->Dv, me));
+  CUC(dalloc(h, &h->cv, me));
+  CUC(dalloc(h, &h->theta, 1));
+  CUC(dalloc(h, &h->dstatus, 1));
+  CUC(dalloc(h, &h->S, (size_t)std::max(kk, 1) * n));
+  CUC(dalloc(h, &h->S32, (size_t)std::max(kk, 1) * n));
+  CUC(dalloc(h, &h->lmpW, (size_t)std::max(kk, 1) * M));
+  CUC(dalloc(h, &h->x, (size_t)M * n));
+  CUC(dalloc(h, &h->r, (size_t)M * n));
+  CUC(dalloc(h, &h->z, (size_t)M * n));
+  CUC(dalloc(h, &h->pv, (size_t)M * n));
+  CUC(dalloc(h, &h->q, (size_t)M * n));
+  if (h->precision == EDA_MIXED) {
+    CUC(dalloc(h, &h->r32, (size_t)M * n));
+    CUC(dalloc(h, &h->z32, (size_t)M * n));
+    CUC(dalloc(h, &h->p32, (size_t)M * n));
+    CUC(dalloc(h, &h->q32, (size_t)M * n));
+  }
+  CUC(dalloc(h, &h->sc, M));
+  CUC(dalloc(h, &h->active, M));
+  CUC(dalloc(h, &h->nactive, 1));
+  CUC(dalloc(h, &h->cols, mcols));
+  CUC(dalloc(h, &h->zeros, mcols));
+  CUC(cudaMallocHost((void**)&h->hflag, sizeof(int)));
+
+  std::vector<float> tmp32(std::max(p, h->w + 1));
+  CUC(cudaMemcpyAsync(h->obs_of_t, h->h_obs_of_t.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CUC(cudaMemcpyAsync(h->obs_ptr, c.obs_ptr, (h->nos + 1) * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CUC(cudaMemcpyAsync(h->obs_idx, c.obs_idx, p * sizeof(int), cudaMemcpyHostToDevice, h->st));
+  CUC(cudaMemcpyAsync(h->rinv, c.rinv, p * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  CUC(cudaMemcpyAsync(h->bcoef, c.bhalf_coef, (h->w + 1) * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  CUC(eda::convert<double, float>(p, h->rinv, h->rinv32, h->st));
+  CUC(eda::convert<double, float>(h->w + 1, h->bcoef, h->bcoef32, h->st));
+  eda::count_launch();
+  iota_kernel<<<grid_for(mcols), 256, 0, h->st>>>(mcols, h->cols, 1);
+  eda::count_launch();
+  iota_kernel<<<grid_for(mcols), 256, 0, h->st>>>(mcols, h->zeros, 0);
+  CUC(cudaGetLastError());
+  CUC(cudaStreamSynchronize(h->st));
+  {
+    const SweepPlan p64 = h->plan64, p32 = h->plan32;
+    if (set_plan(h, true, p64) != EDA_OK || set_plan(h, false, p32) != EDA_OK) {
+      g_err = h->err;
+      return bail(EDA_ERR_CUDA);
+    }
+  }
+#undef CUC
+  *out = h;
+  return EDA_OK;
+}
+
+EDA_API int eda_destroy(eda_handle* h) {
+  if (!h) return EDA_OK;
+  if (h->st) cudaStreamSynchronize(h->st);
+  for (void* p : h->allocs)
+    if (p) cudaFree(p);
+  if (h->stash) cudaFree(h->stash);
+  if (h->stash32) cudaFree(h->stash32);
+  if (h->tab64) cudaFree(h->tab64);
+  if (h->tab32) cudaFree(h->tab32);
+  if (h->hflag) cudaFreeHost(h->hflag);
+  delete h;
+  return EDA_OK;
+}
+
+EDA_API int eda_twin(eda_handle* h, const double* x_spin0, int spinup, const double* eta_b,
+                     const double* eta_o, double* xb_out, double* y_out, double* xt0_out) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (!x_spin0 || !eta_b || !eta_o || !xb_out || !y_out || spinup < 0)
+    return fail(h, EDA_ERR_INVALID, "eda_twin: invalid argument");
+  const int n = h->n, M = h->M, p = h->p;
+  In xs, eb, eo;
+  CU(h, xs.init(x_spin0, (size_t)n * sizeof(double), h->st));
+  CU(h, eb.init(eta_b, (size_t)M * n * sizeof(double), h->st));
+  CU(h, eo.init(eta_o, (size_t)M * p * sizeof(double), h->st));
+  Out oxb, oy, oxt;
+  CU(h, oxb.init(xb_out, (size_t)M * n * sizeof(double), h->st));
+  CU(h, oy.init(y_out, (size_t)M * p * sizeof(double), h->st));
+  CU(h, oxt.init(xt0_out, (size_t)n * sizeof(double), h->st));
+  double *xt = nullptr, *ytrue = nullptr, *tmp = nullptr;
+  int* nobs = nullptr;
+  CU(h, cudaMallocAsync((void**)&xt, (size_t)n * sizeof(double), h->st));
+  CU(h, cudaMallocAsync((void**)&ytrue, (size_t)p * sizeof(double), h->st));
+  CU(h, cudaMallocAsync((void**)&tmp, (size_t)M * n * sizeof(double), h->st));
+  CU(h, cudaMallocAsync((void**)&nobs, (size_t)(spinup + 1) * sizeof(int), h->st));
+  // spin-up: no observations
+  if (spinup > 0) {
+    CU(h, cudaMemsetAsync(nobs, 0xFF, (size_t)(spinup + 1) * sizeof(int), h->st));
+    SweepArgs<double> a = base_args<double>(h);
+    a.mode = eda::MODE_NL;
+    a.N = spinup;
+    a.obs_of_t = nobs;
+    a.ncol = 1;
+    a.x0 = (const double*)xs.dev;
+    a.x0_stride = n;
+    a.final_out = xt;
+    CU(h, eda::launch_sweep<double>(a, h->plan64, h->st));
+  } else {
+    CU(h, cudaMemcpyAsync(xt, xs.dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  }
+  // truth over the window, observed
+  {
+    SweepArgs<double> a = base_args<double>(h);
+    a.mode = eda::MODE_NL;
+    a.ncol = 1;
+    a.x0 = xt;
+    a.x0_stride = n;
+    a.d_out = ytrue;
+    CU(h, eda::launch_sweep<double>(a, h->plan64, h->st));
+  }
+  eda::count_launch();
+  twin_sum_kernel<<<grid_for((long long)M * n), 256, 0, h->st>>>(n, M, (const double*)eb.dev, tmp);
+  eda::count_launch();
+  bhalf_apply_kernel<<<grid_for((long long)M * n), 256, 0, h->st>>>(n, h->w, h->bcoef, M, tmp, (double*)oxb.dev);
+  eda::count_launch();
+  twin_x_kernel<<<grid_for((long long)M * n), 256, 0, h->st>>>(n, M, xt, (double*)oxb.dev);
+  eda::count_launch();
+  twin_y_kernel<<<grid_for((long long)M * p), 256, 0, h->st>>>(p, M, ytrue, h->rinv, (const double*)eo.dev,
+                                                               (double*)oy.dev);
+  CU(h, cudaGetLastError());
+  if (oxt.dev) CU(h, cudaMemcpyAsync(oxt.dev, xt, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  CU(h, cudaFreeAsync(xt, h->st));
+  CU(h, cudaFreeAsync(ytrue, h->st));
+  CU(h, cudaFreeAsync(tmp, h->st));
+  CU(h, cudaFreeAsync(nobs, h->st));
+  CU(h, oxb.finish());
+  CU(h, oy.finish());
+  CU(h, oxt.finish());
+  if (oxb.host || oy.host || oxt.host) CU(h, cudaStreamSynchronize(h->st));
+  return EDA_OK;
+}
+
+EDA_API int eda_set_trajectory(eda_handle* h, const double* xb, const double* y, double* rhs_out) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (!xb || !y) return fail(h, EDA_ERR_INVALID, "eda_set_trajectory: xb and y are required");
+  const int n = h->n, M = h->M, p = h->p, N = h->N;
+  In ixb, iy;
+  CU(h, ixb.init(xb, (size_t)M * n * sizeof(double), h->st));
+  CU(h, iy.init(y, (size_t)M * p * sizeof(double), h->st));
+  int rc = check_finite(h, (const double*)ixb.dev, (long long)M * n, "xb");
+  if (rc) return rc;
+  rc = check_finite(h, (const double*)iy.dev, (long long)M * p, "y");
+  if (rc) return rc;
+  h->have_traj = h->have_sketch = h->have_lmp = false;
+  // nonlinear trajectories and innovations (FP64)
+  {
+    SweepArgs<double> a = base_args<double>(h);
+    a.mode = eda::MODE_NL;
+    a.ncol = M;
+    a.x0 = (const double*)ixb.dev;
+    a.x0_stride = n;
+    a.traj_out = h->traj;
+    a.traj_out_mstride = (long long)(N + 1) * n;
+    a.yobs = (const double*)iy.dev;
+    a.d_out = h->d;
+    a.rd_out = h->rd;
+    CU(h, eda::launch_sweep<double>(a, h->plan64, h->st));
+  }
+  if (h->precision == EDA_MIXED)
+    CU(h, eda::convert<double, float>((long long)M * (N + 1) * n, h->traj, h->traj32, h->st));
+  // right-hand sides b_j = U_B^T G_j^T R^{-1} d_j (FP64 adjoint sweep)
+  {
+    SweepArgs<double> a = base_args<double>(h);
+    a.mode = eda::MODE_RHS;
+    a.ncol = M;
+    a.stash = h->rd;
+    a.stash_stride = p;
+    a.OUT = h->b;
+    a.out_stride = n;
+    CU(h, eda::launch_sweep<double>(a, h->plan64, h->st));
+  }
+  Out orhs;
+  CU(h, orhs.init(rhs_out, (size_t)M * n * sizeof(double), h->st));
+  if (orhs.dev)
+    CU(h, cudaMemcpyAsync(orhs.dev, h->b, (size_t)M * n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  CU(h, orhs.finish());
+  if (orhs.host) CU(h, cudaStreamSynchronize(h->st));
+  h->have_traj = true;
+  return EDA_OK;
+}
+
+EDA_API int eda_hvp(eda_handle* h, const int* member_of_col, int ncol, const double* V, double* HV,
+                    int include_identity) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (!h->have_traj) return fail(h, EDA_ERR_STATE, "eda_hvp before eda_set_trajectory");
+  if (ncol < 0 || (ncol > 0 && (!member_of_col || !V || !HV))) return fail(h, EDA_ERR_INVALID, "eda_hvp: invalid argument");
+  if (ncol == 0) return EDA_OK;
+  const int n = h->n;
+  std::vector<int> hm;
+  const int* mptr = member_of_col;
+  if (!is_device_ptr(member_of_col)) {
+    for (int c = 0; c < ncol; ++c)
+      if (member_of_col[c] < 0 || member_of_col[c] >= h->M) return fail(h, EDA_ERR_INVALID, "member_of_col out of range");
+  }
+  In im, iv;
+  CU(h, im.init(mptr, (size_t)ncol * sizeof(int), h->st));
+  CU(h, iv.init(V, (size_t)ncol * n * sizeof(double), h->st));
+  Out o;
+  CU(h, o.init(HV, (size_t)ncol * n * sizeof(double), h->st));
+  int rc = hvp_dev(h, (const int*)im.dev, ncol, (const double*)iv.dev, (double*)o.dev, include_identity ? 1 : 0,
+                   false, nullptr);
+  if (rc) return rc;
+  CU(h, o.finish());
+  if (o.host) CU(h, cudaStreamSynchronize(h->st));
+  return EDA_OK;
+}
+
+EDA_API int eda_sketch(eda_handle* h, const double* phi, int q, double* y_out) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (!h->have_traj) return fail(h, EDA_ERR_STATE, "eda_sketch before eda_set_trajectory");
+  if (h->ell < 1) return fail(h, EDA_ERR_INVALID, "eda_sketch: ell = 0");
+  if (q < 1) return fail(h, EDA_ERR_INVALID, "eda_sketch: q must be >= 1");
+  const int n = h->n, ell = h->ell;
+  In iphi;
+  CU(h, iphi.init(phi, (size_t)ell * n * sizeof(double), h->st));
+  if (phi) {
+    CU(h, cudaMemcpyAsync(h->Phi, iphi.dev, (size_t)ell * n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  } else {
+    eda::count_launch();
+    gamma_kernel<<<grid_for((long long)ell * n), 256, 0, h->st>>>(n, ell, h->b, h->Phi);
+    CU(h, cudaGetLastError());
+  }
+  h->have_sketch = h->have_lmp = false;
+  for (int pass = 1; pass <= q; ++pass) {
+    int rc = hvp_dev(h, h->zeros, ell, h->Phi, h->Y, 0, false, nullptr);
+    if (rc) return rc;
+    if (pass < q) {
+      rc = cholqr2(h, h->Y, h->Phi);  // Phi = Q_Y (Algorithm 1, power loop)
+      if (rc) return rc;
+    }
+  }
+  Out oy;
+  CU(h, oy.init(y_out, (size_t)ell * n * sizeof(double), h->st));
+  if (oy.dev) CU(h, cudaMemcpyAsync(oy.dev, h->Y, (size_t)ell * n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  CU(h, oy.finish());
+  if (oy.host) CU(h, cudaStreamSynchronize(h->st));
+  h->have_sketch = true;
+  return EDA_OK;
+}
+
+EDA_API int eda_build_lmp(eda_handle* h, double* eigvals_out, double* s_out) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (!h->have_sketch) return fail(h, EDA_ERR_STATE, "eda_build_lmp before eda_sketch");
+  const int n = h->n, m = h->ell, kk = h->k;
+  double nu = 0.0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    int rc = cholqr2(h, h->Y, h->Q);
+    if (rc) return rc;
+    CU(h, eda::gemm_tn<double, double>(n, h->Phi, m, h->Y, m, h->W, m, nullptr, false, h->st));
+    CU(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
+    CU(h, eda::nystrom_core(h->W, h->RY, m, kk, nu, h->theta_mode, h->theta_given, h->UT, h->Dv, h->cv, h->theta,
+                            h->dstatus, h->st));
+    int st = 0;
+    rc = read_flag(h, h->dstatus, &st);
+    if (rc) return rc;
+    if (!st) break;
+    if (attempt == 1) return fail(h, EDA_ERR_NUMERIC, "Nystrom: Cholesky of Phi^T Y failed after the shift");
+    // Appendix B: shift nu = eps ||Y||_F, Y <- Y + nu Phi
+    CU(h, eda::gemm_tn<double, double>(n, h->Y, m, h->Y, m, h->G, m, nullptr, true, h->st));
+    std::vector<double> Gh((size_t)m * m);
+    CU(h, cudaMemcpyAsync(Gh.data(), h->G, Gh.size() * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CU(h, cudaStreamSynchronize(h->st));
+    double tr = 0.0;
+    for (int i = 0; i < m; ++i) tr += Gh[(size_t)i * m + i];
+    nu = 2.220446049250313e-16 * std::sqrt(tr);
+    eda::count_launch();
+    axpy_kernel<<<grid_for((long long)m * n), 256, 0, h->st>>>((long long)m * n, nu, h->Phi, h->Y);
+    CU(h, cudaGetLastError());
+  }
+  h->shift_used = nu;
+  // S = Q_Y U_T(:, 1:k)
+  CU(h, eda::gemm_nn<double, double>(n, h->Q, m, kk, h->UT, nullptr, nullptr, h->S, nullptr, h->st));
+  if (h->precision == EDA_MIXED) CU(h, eda::convert<double, float>((long long)kk * n, h->S, h->S32, h->st));
+  Out oe, os;
+  CU(h, oe.init(eigvals_out, (size_t)kk * sizeof(double), h->st));
+  CU(h, os.init(s_out, (size_t)kk * n * sizeof(double), h->st));
+  if (oe.dev) {
+    eda::count_launch();
+    eig_kernel<<<1, 128, 0, h->st>>>(kk, h->Dv, (double*)oe.dev);
+    CU(h, cudaGetLastError());
+  }
+  if (os.dev) CU(h, cudaMemcpyAsync(os.dev, h->S, (size_t)kk * n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  CU(h, oe.finish());
+  CU(h, os.finish());
+  if (oe.host || os.host) CU(h, cudaStreamSynchronize(h->st));
+  h->have_lmp = true;
+  return EDA_OK;
+}
+
+EDA_API int eda_set_lmp(eda_handle* h, const double* s_in, const double* eigvals_in) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (h->k < 1) return fail(h, EDA_ERR_INVALID, "eda_set_lmp: the handle has no LMP rank (ell = 0)");
+  if (!s_in || !eigvals_in) return fail(h, EDA_ERR_INVALID, "eda_set_lmp: invalid argument");
+  const int n = h->n, kk = h->k;
+  std::vector<double> ev(kk);
+  if (is_device_ptr(eigvals_in)) {
+    CU(h, cudaMemcpyAsync(ev.data(), eigvals_in, kk * sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CU(h, cudaStreamSynchronize(h->st));
+  } else {
+    std::memcpy(ev.data(), eigvals_in, kk * sizeof(double));
+  }
+  std::vector<double> D(kk), c(kk);
+  for (int i = 0; i < kk; ++i) {
+    if (!std::isfinite(ev[i]) || ev[i] < 1.0 || (i > 0 && ev[i] > ev[i - 1]))
+      return fail(h, EDA_ERR_INVALID, "eda_set_lmp: eigenvalues must be finite, >= 1 and descending");
+    D[i] = ev[i] - 1.0;
+  }
+  const double lamk = ev[kk - 1];
+  double th = h->theta_given;
+  if (h->theta_mode == EDA_THETA_LAMBDA_K) th = lamk;
+  if (h->theta_mode == EDA_THETA_MID) th = 0.5 * (lamk + 1.0);
+  for (int i = 0; i < kk; ++i) c[i] = th / (1.0 + D[i]) - 1.0;
+  In is;
+  CU(h, is.init(s_in, (size_t)kk * n * sizeof(double), h->st));
+  CU(h, cudaMemcpyAsync(h->S, is.dev, (size_t)kk * n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  CU(h, cudaMemcpyAsync(h->Dv, D.data(), kk * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  CU(h, cudaMemcpyAsync(h->cv, c.data(), kk * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  CU(h, cudaMemcpyAsync(h->theta, &th, sizeof(double), cudaMemcpyHostToDevice, h->st));
+  if (h->precision == EDA_MIXED) CU(h, eda::convert<double, float>((long long)kk * n, h->S, h->S32, h->st));
+  CU(h, cudaStreamSynchronize(h->st));
+  h->have_lmp = true;
+  return EDA_OK;
+}
+
+namespace {
+
+// FP64 PCG iterations from the current (x, r) state; the caller has run
+// pcg_start.  Returns the number of iterations done.
+int pcg_loop64(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done) {
+  const int n = h->n, M = h->M;
+  const int fixed = (tol > 0.0) ? 0 : maxit;
+  int rc = lmp_apply_dev<double>(h, h->r, h->z, use_lmp);
+  if (rc) return rc;
+  CU(h, eda::pcg_first_dir<double>(n, M, h->r, h->z, h->pv, h->sc, h->active, h->st));
+  int it = it0;
+  while (it < maxit) {
+    ++it;
+    rc = hvp_dev(h, h->cols, M, h->pv, h->q, 1, true, h->active);
+    if (rc) return rc;
+    CU(h, eda::pcg_update<double, double>(n, M, it, h->pv, h->q, h->x, h->r, h->sc, h->active, tol, h->nactive,
+                                          fixed, h->st));
+    rc = lmp_apply_dev<double>(h, h->r, h->z, use_lmp);
+    if (rc) return rc;
+    CU(h, eda::pcg_dir<double>(n, M, h->r, h->z, h->pv, h->sc, h->active, h->st));
+    int na = 0;
+    rc = read_flag(h, h->nactive, &na);
+    if (rc) return rc;
+    if (na == 0) break;
+  }
+  *it_done = it;
+  return EDA_OK;
+}
+
+// Mixed PCG iterations: FP32 vectors and sweeps, FP64 x and scalars.
+int pcg_loop32(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done) {
+  const int n = h->n, M = h->M;
+  const int fixed = (tol > 0.0) ? 0 : maxit;
+  int rc = lmp_apply_dev<float>(h, h->r32, h->z32, use_lmp);
+  if (rc) return rc;
+  CU(h, eda::pcg_first_dir<float>(n, M, h->r32, h->z32, h->p32, h->sc, h->active, h->st));
+  int it = it0;
+  while (it < maxit) {
+    ++it;
+    rc = hvp32_dev(h, h->p32, h->q32, h->active);
+    if (rc) return rc;
+    CU(h, eda::pcg_update<float, double>(n, M, it, h->p32, h->q32, h->x, h->r32, h->sc, h->active, tol,
+                                         h->nactive, fixed, h->st));
+    rc = lmp_apply_dev<float>(h, h->r32, h->z32, use_lmp);
+    if (rc) return rc;
+    CU(h, eda::pcg_dir<float>(n, M, h->r32, h->z32, h->p32, h->sc, h->active, h->st));
+    int na = 0;
+    rc = read_flag(h, h->nactive, &na);
+    if (rc) return rc;
+    if (na == 0) break;
+  }
+  *it_done = it;
+  return EDA_OK;
+}
+
+}  // namespace
+
+EDA_API int eda_solve_batch(eda_handle* h, double tol, int maxit, const double* x0, int use_lmp, double* dz_out,
+                            int* iters_out, double* relres_out, int* status_out) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (!h->have_traj) return fail(h, EDA_ERR_STATE, "eda_solve_batch before eda_set_trajectory");
+  if (use_lmp && !h->have_lmp) return fail(h, EDA_ERR_STATE, "eda_solve_batch with use_lmp before eda_build_lmp");
+  if (!dz_out || maxit < 0 || !(tol >= 0.0)) return fail(h, EDA_ERR_INVALID, "eda_solve_batch: invalid argument");
+  const int n = h->n, M = h->M;
+  const size_t vb = (size_t)M * n * sizeof(double);
+  In ix0;
+  CU(h, ix0.init(x0, vb, h->st));
+  CU(h, cudaMemsetAsync(h->nactive, 0, sizeof(int), h->st));
+  // x = x0 (or 0), r = b - H x0
+  if (x0) {
+    CU(h, cudaMemcpyAsync(h->x, ix0.dev, vb, cudaMemcpyDeviceToDevice, h->st));
+    int rc = hvp_dev(h, h->cols, M, h->x, h->q, 1, true, nullptr);
+    if (rc) return rc;
+    eda::count_launch();
+    sub_kernel<double><<<grid_for((long long)M * n), 256, 0, h->st>>>((long long)M * n, h->b, h->q, h->r);
+  } else {
+    CU(h, cudaMemsetAsync(h->x, 0, vb, h->st));
+    CU(h, cudaMemcpyAsync(h->r, h->b, vb, cudaMemcpyDeviceToDevice, h->st));
+  }
+  CU(h, cudaGetLastError());
+  CU(h, eda::pcg_start<double>(n, M, h->b, h->r, h->sc, h->active, tol, h->nactive, h->st));
+  const bool lmp = use_lmp != 0;
+  int it = 0;
+  if (h->precision == EDA_FP64) {
+    int rc = pcg_loop64(h, tol, maxit, 0, lmp, &it);
+    if (rc) return rc;
+  } else {
+    CU(h, eda::convert<double, float>((long long)M * n, h->r, h->r32, h->st));
+    int rc = pcg_loop32(h, tol, maxit, 0, lmp, &it);
+    if (rc) return rc;
+    // FP64 residual replacement: true residual with FP64 sweeps; members whose
+    // true residual misses the tolerance restart from it.
+    for (int rep = 0; rep < 8; ++rep) {
+      rc = hvp_dev(h, h->cols, M, h->x, h->q, 1, true, nullptr);
+      if (rc) return rc;
+      CU(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
+      eda::count_launch();
+      true_res_kernel<<<M, 256, 0, h->st>>>(n, h->b, h->q, h->r32, h->sc, h->active, tol > 0.0 ? tol : 1e300,
+                                           h->nactive, h->dstatus);
+      CU(h, cudaGetLastError());
+      int need = 0;
+      rc = read_flag(h, h->dstatus, &need);
+      if (rc) return rc;
+      if (need == 0 || it >= maxit || tol <= 0.0) break;
+      rc = pcg_loop32(h, tol, maxit, it, lmp, &it);
+      if (rc) return rc;
+    }
+  }
+  Out odz, oit, orr, ost;
+  CU(h, odz.init(dz_out, vb, h->st));
+  CU(h, oit.init(iters_out, (size_t)M * sizeof(int), h->st));
+  CU(h, orr.init(relres_out, (size_t)M * sizeof(double), h->st));
+  CU(h, ost.init(status_out, (size_t)M * sizeof(int), h->st));
+  CU(h, cudaMemcpyAsync(odz.dev, h->x, vb, cudaMemcpyDeviceToDevice, h->st));
+  eda::count_launch();
+  export_kernel<<<1, 256, 0, h->st>>>(M, h->sc, (int*)oit.dev, (double*)orr.dev, (int*)ost.dev);
+  CU(h, cudaGetLastError());
+  CU(h, odz.finish());
+  CU(h, oit.finish());
+  CU(h, orr.finish());
+  CU(h, ost.finish());
+  if (odz.host || oit.host || orr.host || ost.host) CU(h, cudaStreamSynchronize(h->st));
+  return EDA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,47 @@
+// Launchers of the dense kernels (dense.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/eda.h"
+#include "eda_internal.h"
+
+namespace eda {
+
+// Per-member CG scalars (FP64 recurrences, Section 2.3).
+struct PcgScalars {
+  double rz;      // r . z of the current iterate
+  double bnorm;   // ||b||
+  double relres;  // ||r|| / ||b||
+  int iters;
+  int status;
+};
+
+template <typename TA, typename TB>
+cudaError_t gemm_tn(int n, const TA* A, int ka, const TB* B, int mb, double* Cm, int ldc,
+                    const int* active_cols, bool sym, cudaStream_t s);
+template <typename TA, typename TZ>
+cudaError_t gemm_nn(int n, const TA* A, int k, int m, const double* Bs, const double* scale, const TZ* R,
+                    TZ* Z, const int* active_cols, cudaStream_t s);
+cudaError_t chol_inv(const double* G, int m, double shift, double* R, double* Rinv, int* status,
+                     cudaStream_t s);
+cudaError_t tri_mul(const double* A, const double* B, double* P, int m, cudaStream_t s);
+cudaError_t nystrom_core(const double* W, const double* RY, int m, int k, double nu, int theta_mode,
+                         double theta_given, double* UT, double* D, double* cvec, double* theta_out,
+                         int* status, cudaStream_t s);
+template <typename T>
+cudaError_t pcg_start(int n, int m, const double* b, const T* r, PcgScalars* sc, int* active, double tol,
+                      int* nactive, cudaStream_t s);
+template <typename T>
+cudaError_t pcg_first_dir(int n, int m, const T* r, const T* z, T* p, PcgScalars* sc, const int* active,
+                          cudaStream_t s);
+template <typename T, typename TX>
+cudaError_t pcg_update(int n, int m, int it, const T* p, const T* q, TX* x, T* r, PcgScalars* sc, int* active,
+                       double tol, int* nactive, int fixed_iters, cudaStream_t s);
+template <typename T>
+cudaError_t pcg_dir(int n, int m, const T* r, const T* z, T* p, PcgScalars* sc, const int* active,
+                    cudaStream_t s);
+template <typename TS, typename TD>
+cudaError_t convert(long long count, const TS* src, TD* dst, cudaStream_t s);
+
+}  // namespace eda

@@ -1,0 +1,93 @@
+// Internal declarations shared by the translation units of libeda.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/eda.h"
+
+namespace eda {
+
+// Process-wide count of kernel launches (tracing).
+void count_launch(int k = 1);
+
+enum SweepMode { MODE_HVP = 0, MODE_RHS = 1, MODE_NL = 2 };
+
+// Arguments of one launch of the Lorenz-96 sweep kernel.  One "column" is one
+// vector processed on the trajectory of member col_member[col]; it is split
+// over CS CTAs (a thread-block cluster), CTA r owning global indices
+// [r*Ttile, min((r+1)*Ttile, n)) and computing redundantly on the extended
+// region of E = A*C elements starting HL to the left of its tile.  The halo is
+// refreshed from its owners every K steps.
+template <typename T>
+struct SweepArgs {
+  int n, N;
+  T F, dt;
+  // trajectory store, states 0..N of each member (MODE_HVP / MODE_RHS)
+  const T* traj;
+  long long traj_mstride;
+  // observation network
+  const int* obs_of_t;   // [N+1]: observation-step index at step t, or -1
+  const int* obs_tab;    // [CS][nos][8] observation ranges per CTA (or nullptr)
+  int nos;
+  const int* obs_ptr;    // [n_obs_times + 1]
+  const int* obs_idx;    // [p]
+  const T* rinv;         // [p]
+  int p;
+  // U_B taps
+  int w;
+  const T* bcoef;        // [w+1]
+  // columns
+  int ncol;
+  const int* col_member; // [ncol] or nullptr (= column index)
+  const int* col_active; // [ncol] or nullptr (= all active)
+  const T* V;            // MODE_HVP input vectors [ncol][v_stride]
+  long long v_stride;
+  T* OUT;                // MODE_HVP / MODE_RHS outputs
+  long long out_stride;
+  T* stash;              // MODE_HVP: per-column obs stash [ncol][stash_stride]
+                         // MODE_RHS: per-member forcing R^{-1} d [member][stash_stride]
+  long long stash_stride;
+  int include_identity;
+  int mode;
+  // MODE_NL
+  const T* x0;           // [col][x0_stride] initial states
+  long long x0_stride;
+  T* traj_out;           // [member][N+1][n] or nullptr
+  long long traj_out_mstride;
+  T* final_out;          // [col][n] final state or nullptr
+  const T* yobs;         // [col][p] or nullptr (then d = H x)
+  T* d_out;              // [col][p] or nullptr
+  T* rd_out;             // [col][p] or nullptr: R^{-1} d
+  // plan
+  int CS, Ttile, HL, E, K;
+};
+
+struct SweepPlan {
+  int CS, C, A, E, Ttile, HL, K;
+  size_t smem;
+};
+
+// Picks the tiling of a sweep for state size n (elem_bytes = sizeof(T)):
+// the smallest cluster size >= min_cs whose tile fits one CTA.  K_hint > 0
+// fixes the halo refresh period.  Returns false if no plan fits.
+bool plan_sweep(int n, int elem_bytes, int w, int min_cs, int K_hint, SweepPlan* out);
+
+// The plan with exactly cluster size CS and refresh period K, if it fits.
+bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* out);
+
+// Per-CTA observation ranges of a plan: for CTA r and observation step j,
+// tab[(r*nos + j)*8 + 0..1] = [k0, k1) of the observations of the owned tile,
+// [2..4] and [5..7] = (k0, k1, base) of the (at most two) index ranges of the
+// extended region, local position = obs_idx[k] - base.  Empty when the
+// extended region is longer than n (then the kernel scans every observation).
+void obs_table(const SweepPlan& p, int n, int nos, const int* obs_ptr, const int* obs_idx,
+               int* tab /* [CS*nos*8] */, bool* usable);
+
+// Launches the sweep for `ncol` columns.  Returns a cudaError_t.
+template <typename T>
+cudaError_t launch_sweep(const SweepArgs<T>& a, const SweepPlan& plan, cudaStream_t s);
+
+}  // namespace eda

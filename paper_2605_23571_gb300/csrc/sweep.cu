@@ -1,0 +1,791 @@
+// Lorenz-96 sweeps on sm_103a: nonlinear trajectory with innovations, the
+// tangent-linear/adjoint Hessian-vector product (I + A) v, and the adjoint
+// right-hand side U_B^T G^T R^{-1} d (Section 2.3, Eq. (system with CVT);
+// the model and RK4 step of Section 4).
+//
+// Layout of one column (one vector on one member's trajectory):
+//  * the column is split over a thread-block cluster of CS CTAs; CTA r owns
+//    the global indices [r*Ttile, min((r+1)*Ttile, n));
+//  * each CTA computes on an extended region of E = A*C consecutive (periodic)
+//    indices starting HL before its tile; thread t keeps elements
+//    [t*C, t*C + C) of that region in registers;
+//  * a stage of RK4 needs the neighbours i-2, i-1, i+1, i+2 of a thread's
+//    run: threads publish the first two and last two values of their run to
+//    a shared-memory edge buffer and read their neighbours' after a barrier;
+//  * the stencil wraps inside the extended region, so values within 8 s + 8
+//    of its ends are wrong after s steps; every K steps the halo is reloaded
+//    from its owners (distributed shared memory inside the cluster), and
+//    HL = 8K + 8 keeps the owned tile exact (for CS = 1 the owner is the CTA
+//    itself and the reload implements the periodic boundary);
+//  * trajectory states x_t are streamed from HBM into a double-buffered
+//    shared-memory stage (coalesced loads issued one step ahead).
+//
+// The tangent linear is the exact derivative of the discrete RK4 step and
+// the adjoint its exact transpose, computed stage by stage in reverse.
+#include <cooperative_groups.h>
+
+#include "eda_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace eda {
+namespace {
+
+constexpr int kNumEdge = 6;
+constexpr int kMaxThreads = 512;
+
+template <typename T, int C>
+struct Run {
+  T v[C];
+  T m2, m1, p1, p2;
+  // Element j of the run, j in [-2, C+1]; j is a compile-time constant after
+  // unrolling so this folds to a register.
+  __device__ __forceinline__ T at(int j) const {
+    return j == -2 ? m2
+                   : (j == -1 ? m1
+                              : (j == C ? p1 : (j == C + 1 ? p2 : v[j < 0 ? 0 : (j >= C ? C - 1 : j)])));
+  }
+};
+
+// Lorenz-96 tendency f_j = (x_{j+1} - x_{j-2}) x_{j-1} - x_j + F.
+template <typename T, int C>
+__device__ __forceinline__ T tend(const Run<T, C>& X, int j, T F) {
+  return (X.at(j + 1) - X.at(j - 2)) * X.at(j - 1) - X.at(j) + F;
+}
+// (J(X) e)_j = (e_{j+1} - e_{j-2}) X_{j-1} + (X_{j+1} - X_{j-2}) e_{j-1} - e_j.
+template <typename T, int C>
+__device__ __forceinline__ T jvp(const Run<T, C>& X, const Run<T, C>& e, int j) {
+  return (e.at(j + 1) - e.at(j - 2)) * X.at(j - 1) + (X.at(j + 1) - X.at(j - 2)) * e.at(j - 1) - e.at(j);
+}
+// (J(X)^T w)_j = X_{j-2} w_{j-1} + (X_{j+2} - X_{j-1}) w_{j+1} - X_{j+1} w_{j+2} - w_j.
+template <typename T, int C>
+__device__ __forceinline__ T jtvp(const Run<T, C>& X, const Run<T, C>& w, int j) {
+  return X.at(j - 2) * w.at(j - 1) + (X.at(j + 2) - X.at(j - 1)) * w.at(j + 1) - X.at(j + 1) * w.at(j + 2) -
+         w.at(j);
+}
+
+struct Geo {
+  int n, E, A, tid, tl, tr, l0, HL, Ttile, Town, a0, gbase, CS, rank;
+};
+
+template <typename T, int C>
+__device__ __forceinline__ void publish(T* eb, const Geo& g, const T (&v)[C]) {
+  eb[g.tid] = v[0];
+  eb[g.A + g.tid] = v[1];
+  eb[2 * g.A + g.tid] = v[C - 2];
+  eb[3 * g.A + g.tid] = v[C - 1];
+}
+
+template <typename T, int C>
+__device__ __forceinline__ void fetch(const T* eb, const Geo& g, Run<T, C>& r) {
+  r.m2 = eb[2 * g.A + g.tl];
+  r.m1 = eb[3 * g.A + g.tl];
+  r.p1 = eb[g.tr];
+  r.p2 = eb[g.A + g.tr];
+}
+
+// Run of the stage buffer xs (whole extended region resident in smem).
+template <typename T, int C>
+__device__ __forceinline__ void run_from_smem(const T* xs, const Geo& g, Run<T, C>& r) {
+#pragma unroll
+  for (int c = 0; c < C; ++c) r.v[c] = xs[g.l0 + c];
+  r.m2 = xs[g.l0 >= 2 ? g.l0 - 2 : g.l0 - 2 + g.E];
+  r.m1 = xs[g.l0 >= 1 ? g.l0 - 1 : g.l0 - 1 + g.E];
+  r.p1 = xs[g.l0 + C < g.E ? g.l0 + C : g.l0 + C - g.E];
+  r.p2 = xs[g.l0 + C + 1 < g.E ? g.l0 + C + 1 : g.l0 + C + 1 - g.E];
+}
+
+__device__ __forceinline__ void sync_cluster_or_block(bool cluster) {
+  if (cluster) {
+    cg::this_cluster().sync();
+  } else {
+    __syncthreads();
+  }
+}
+
+// Reads the halo elements of v (positions outside the owned tile) from their
+// owners' mirrors.  The caller has written every thread's v to its own
+// mirror and passed a cluster (or block) barrier.
+template <typename T, int C>
+__device__ __forceinline__ void read_halo(T (&v)[C], T* mir, const Geo& g) {
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    const int l = g.l0 + c;
+    if (l < g.HL || l >= g.HL + g.Town) {
+      const int gi = (g.gbase + l) % g.n;
+      const int r2 = gi / g.Ttile;
+      const int ll = g.HL + gi - r2 * g.Ttile;
+      if (g.CS == 1 || r2 == g.rank) {
+        v[c] = mir[ll];
+      } else {
+        const T* rem = cg::this_cluster().map_shared_rank(mir, r2);
+        v[c] = rem[ll];
+      }
+    }
+  }
+}
+
+// Observation k-ranges of this CTA at observation step oj (see obs_table).
+__device__ __forceinline__ const int* obs_ranges(const int* tab, int nos, int rank, int oj) {
+  return tab + ((long long)rank * nos + oj) * 8;
+}
+
+template <typename T, int C>
+__device__ __forceinline__ void write_mirror(T* mir, const Geo& g, const T (&v)[C]) {
+#pragma unroll
+  for (int c = 0; c < C; ++c) mir[g.l0 + c] = v[c];
+}
+
+// out[c] = sum_{|d|<=w} cf[|d|] src[base + w + c + d] for c < C: the banded
+// symmetric circulant on C consecutive outputs with a sliding register window
+// (3 shared-memory loads per tap).  src holds the input with a w-halo.
+template <typename T, int C>
+__device__ __forceinline__ void conv_run(const T* src, int base, int w, const T* cf, T (&out)[C]) {
+  T Lw[C], Rw[C];
+  const T c0 = cf[0];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    Lw[c] = src[base + w + c];
+    Rw[c] = Lw[c];
+    out[c] = c0 * Lw[c];
+  }
+  for (int d = 1; d <= w; ++d) {
+#pragma unroll
+    for (int c = C - 1; c > 0; --c) Lw[c] = Lw[c - 1];
+    Lw[0] = src[base + w - d];
+#pragma unroll
+    for (int c = 0; c < C - 1; ++c) Rw[c] = Rw[c + 1];
+    Rw[C - 1] = src[base + w + C - 1 + d];
+    const T cd = cf[d];
+#pragma unroll
+    for (int c = 0; c < C; ++c) out[c] += cd * (Lw[c] + Rw[c]);
+  }
+}
+
+// U_B lambda on the owned tile from the mirrors of the cluster (+ v if ident);
+// thread t produces outputs [t*C, t*C + C) of the tile.  stage has room for
+// E + 2w values.
+template <typename T, int C>
+__device__ void bhalf_from_mirrors(const SweepArgs<T>& a, const Geo& g, T* mir, T* stage, const T* cf,
+                                   T* out, const T* ident) {
+  const int w = a.w;
+  const int cnt = g.Town + 2 * w;
+  for (int j = g.tid; j < cnt; j += g.A) {
+    int gi = (g.a0 - w + j) % g.n;
+    if (gi < 0) gi += g.n;
+    const int r2 = gi / g.Ttile;
+    const int ll = g.HL + gi - r2 * g.Ttile;
+    if (g.CS == 1 || r2 == g.rank) {
+      stage[j] = mir[ll];
+    } else {
+      const T* rem = cg::this_cluster().map_shared_rank(mir, r2);
+      stage[j] = rem[ll];
+    }
+  }
+  // every remote read of this cluster's mirrors is complete after this barrier
+  sync_cluster_or_block(g.CS > 1);
+  const int j0 = g.tid * C;
+  if (j0 < g.Town) {
+    T o[C];
+    conv_run<T, C>(stage, j0, w, cf, o);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      if (j0 + c < g.Town) {
+        T v = o[c];
+        if (ident) v += ident[g.a0 + j0 + c];
+        out[g.a0 + j0 + c] = v;
+      }
+    }
+  }
+}
+
+// stash[k] = R^{-1}_k delta_t[obs_idx[k]] for the observations of the owned
+// tile at observation step oj; the owned values are in the mirror.
+template <typename T>
+__device__ __forceinline__ void gather_obs(const SweepArgs<T>& a, const Geo& g, int oj, const T* mir, T* stash) {
+  int k0 = a.obs_ptr[oj], k1 = a.obs_ptr[oj + 1];
+  if (a.obs_tab != nullptr) {
+    const int* tb = obs_ranges(a.obs_tab, a.nos, g.rank, oj);
+    k0 = tb[0];
+    k1 = tb[1];
+    for (int k = k0 + g.tid; k < k1; k += g.A) stash[k] = a.rinv[k] * mir[g.HL + a.obs_idx[k] - g.a0];
+  } else {
+    for (int k = k0 + g.tid; k < k1; k += g.A) {
+      const int gi = a.obs_idx[k];
+      if (gi >= g.a0 && gi < g.a0 + g.Town) stash[k] = a.rinv[k] * mir[g.HL + gi - g.a0];
+    }
+  }
+}
+
+template <typename T, int C>
+__global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+
+  Geo g;
+  g.CS = a.CS;
+  g.rank = (a.CS > 1) ? (int)cg::this_cluster().block_rank() : 0;
+  const int col = blockIdx.x / a.CS;
+  if (col >= a.ncol) return;
+  if (a.col_active != nullptr && a.col_active[col] == 0) return;  // uniform over the cluster
+  const int member = a.col_member ? a.col_member[col] : col;
+
+  g.n = a.n;
+  g.E = a.E;
+  g.A = blockDim.x;
+  g.tid = threadIdx.x;
+  g.tl = (g.tid + g.A - 1) % g.A;
+  g.tr = (g.tid + 1) % g.A;
+  g.l0 = g.tid * C;
+  g.HL = a.HL;
+  g.Ttile = a.Ttile;
+  g.a0 = g.rank * a.Ttile;
+  g.Town = min(a.Ttile, a.n - g.a0);
+  g.gbase = ((g.a0 - a.HL) % a.n + a.n) % a.n;
+
+  const int w = a.w;
+  const int xsz = max(max(2 * g.E, g.E + 2 * w + 2), a.Ttile + 2 * w + 2);
+  T* xs0 = sm;
+  T* xs1 = sm + g.E;
+  T* mir = sm + xsz;
+  T* eb[kNumEdge];
+#pragma unroll
+  for (int i = 0; i < kNumEdge; ++i) eb[i] = mir + g.E + i * 4 * g.A;
+  T* cf = mir + g.E + kNumEdge * 4 * g.A;  // U_B taps, w+1 values
+
+  // global index of staging position tid + j*A (coalesced order)
+  int gp[C];
+#pragma unroll
+  for (int j = 0; j < C; ++j) gp[j] = (g.gbase + g.tid + j * g.A) % g.n;
+
+  const T F = a.F, h = a.dt;
+  const T h2 = h * T(0.5), h6 = h / T(6), h3 = h / T(3);
+  const int N = a.N;
+  const bool clus = a.CS > 1;
+
+  if (a.mode == MODE_NL) {
+    // ---------------------------------------------------------------- nonlinear
+    const T* x0 = a.x0 + (long long)col * a.x0_stride;
+#pragma unroll
+    for (int j = 0; j < C; ++j) xs0[g.tid + j * g.A] = x0[gp[j]];
+    __syncthreads();
+    T x[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) x[c] = xs0[g.l0 + c];
+    T* tout = a.traj_out ? a.traj_out + (long long)member * a.traj_out_mstride : nullptr;
+    for (int t = 0; t <= N; ++t) {
+      if (t > 0) {
+        Run<T, C> X;
+        T X1[C], acc[C], Xs[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) X1[c] = x[c];
+        // stage 1
+#pragma unroll
+        for (int c = 0; c < C; ++c) X.v[c] = x[c];
+        fetch(eb[0], g, X);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const T k = tend(X, c, F);
+          acc[c] = k;
+          Xs[c] = X1[c] + h2 * k;
+        }
+        publish(eb[1], g, Xs);
+        __syncthreads();
+        // stage 2
+#pragma unroll
+        for (int c = 0; c < C; ++c) X.v[c] = Xs[c];
+        fetch(eb[1], g, X);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const T k = tend(X, c, F);
+          acc[c] += T(2) * k;
+          Xs[c] = X1[c] + h2 * k;
+        }
+        publish(eb[2], g, Xs);
+        __syncthreads();
+        // stage 3
+#pragma unroll
+        for (int c = 0; c < C; ++c) X.v[c] = Xs[c];
+        fetch(eb[2], g, X);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const T k = tend(X, c, F);
+          acc[c] += T(2) * k;
+          Xs[c] = X1[c] + h * k;
+        }
+        publish(eb[1], g, Xs);
+        __syncthreads();
+        // stage 4
+#pragma unroll
+        for (int c = 0; c < C; ++c) X.v[c] = Xs[c];
+        fetch(eb[1], g, X);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const T k = tend(X, c, F);
+          acc[c] += k;
+          x[c] = X1[c] + h6 * acc[c];
+        }
+      }
+      const int oj = a.obs_of_t[t];
+      const bool refresh = (t > 0) && (t % a.K == 0) && (t < N);
+      const bool store = (tout != nullptr) || (t == N && a.final_out != nullptr);
+      if (oj >= 0 || refresh || store) {
+        write_mirror(mir, g, x);
+        sync_cluster_or_block(refresh && clus);
+        if (tout != nullptr) {
+          T* dst = tout + (long long)t * a.n + g.a0;
+          for (int j = g.tid; j < g.Town; j += g.A) dst[j] = mir[g.HL + j];
+        }
+        if (t == N && a.final_out != nullptr) {
+          T* dst = a.final_out + (long long)col * a.n + g.a0;
+          for (int j = g.tid; j < g.Town; j += g.A) dst[j] = mir[g.HL + j];
+        }
+        if (oj >= 0) {
+          int k0 = a.obs_ptr[oj], k1 = a.obs_ptr[oj + 1];
+          if (a.obs_tab != nullptr) {
+            const int* tb = obs_ranges(a.obs_tab, a.nos, g.rank, oj);
+            k0 = tb[0];
+            k1 = tb[1];
+          }
+          for (int k = k0 + g.tid; k < k1; k += g.A) {
+            const int gi = a.obs_idx[k];
+            if (gi >= g.a0 && gi < g.a0 + g.Town) {
+              const T hx = mir[g.HL + gi - g.a0];
+              const T d = a.yobs ? a.yobs[(long long)col * a.p + k] - hx : hx;
+              if (a.d_out) a.d_out[(long long)col * a.p + k] = d;
+              if (a.rd_out) a.rd_out[(long long)col * a.p + k] = a.rinv[k] * d;
+            }
+          }
+        }
+        if (refresh) {
+          read_halo(x, mir, g);
+          sync_cluster_or_block(clus);
+        }
+      }
+      publish(eb[0], g, x);
+      __syncthreads();
+    }
+    return;
+  }
+
+  // ------------------------------------------------------------------ HVP / RHS
+  const T* trj = a.traj + (long long)member * a.traj_mstride;
+  const T* V = (a.mode == MODE_HVP) ? a.V + (long long)col * a.v_stride : nullptr;
+  T* stash = (a.mode == MODE_HVP) ? a.stash + (long long)col * a.stash_stride
+                                  : a.stash + (long long)member * a.stash_stride;
+
+  if (a.mode == MODE_HVP) {
+    // delta_0 = U_B v on the extended region (v staged with a w-halo)
+    {
+      T* vs = sm;
+      const int cnt = g.E + 2 * w;
+      for (int j = g.tid; j < cnt; j += g.A) {
+        int gi = (g.gbase - w + j) % g.n;
+        if (gi < 0) gi += g.n;
+        vs[j] = V[gi];
+      }
+      for (int j = g.tid; j <= w; j += g.A) cf[j] = a.bcoef[j];
+      __syncthreads();
+    }
+    T dl[C];
+    conv_run<T, C>(sm, g.l0, w, cf, dl);
+    __syncthreads();
+    // x_0 into the stage buffer
+#pragma unroll
+    for (int j = 0; j < C; ++j) xs0[g.tid + j * g.A] = trj[gp[j]];
+    if (a.obs_of_t[0] >= 0) {
+      const int oj = a.obs_of_t[0];
+      write_mirror(mir, g, dl);
+      __syncthreads();
+      gather_obs(a, g, oj, mir, stash);
+    }
+    publish(eb[0], g, dl);
+    __syncthreads();
+
+    // ------------------------------------------------ tangent linear, forward
+    for (int t = 0; t < N; ++t) {
+      const T* cur = (t & 1) ? xs1 : xs0;
+      T* nxt = (t & 1) ? xs0 : xs1;
+      T pf[C];
+      if (t + 1 < N) {
+        const T* src = trj + (long long)(t + 1) * a.n;
+#pragma unroll
+        for (int j = 0; j < C; ++j) pf[j] = src[gp[j]];
+      }
+      Run<T, C> X, e;
+      T X1[C], Xs[C], es[C], acc[C];
+      // stage 1: slopes at X1 = x_t
+      run_from_smem(cur, g, X);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        X1[c] = X.v[c];
+        e.v[c] = dl[c];
+      }
+      fetch(eb[0], g, e);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const T k = tend(X, c, F);
+        const T dk = jvp(X, e, c);
+        Xs[c] = X1[c] + h2 * k;
+        acc[c] = dk;
+        es[c] = dl[c] + h2 * dk;
+      }
+      publish(eb[1], g, Xs);
+      publish(eb[3], g, es);
+      __syncthreads();
+      // stage 2
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        X.v[c] = Xs[c];
+        e.v[c] = es[c];
+      }
+      fetch(eb[1], g, X);
+      fetch(eb[3], g, e);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const T k = tend(X, c, F);
+        const T dk = jvp(X, e, c);
+        Xs[c] = X1[c] + h2 * k;
+        acc[c] += T(2) * dk;
+        es[c] = dl[c] + h2 * dk;
+      }
+      publish(eb[2], g, Xs);
+      publish(eb[4], g, es);
+      __syncthreads();
+      // stage 3
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        X.v[c] = Xs[c];
+        e.v[c] = es[c];
+      }
+      fetch(eb[2], g, X);
+      fetch(eb[4], g, e);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const T k = tend(X, c, F);
+        const T dk = jvp(X, e, c);
+        Xs[c] = X1[c] + h * k;
+        acc[c] += T(2) * dk;
+        es[c] = dl[c] + h * dk;
+      }
+      publish(eb[1], g, Xs);
+      publish(eb[3], g, es);
+      __syncthreads();
+      // stage 4
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        X.v[c] = Xs[c];
+        e.v[c] = es[c];
+      }
+      fetch(eb[1], g, X);
+      fetch(eb[3], g, e);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const T dk = jvp(X, e, c);
+        acc[c] += dk;
+        dl[c] += h6 * acc[c];
+      }
+      if (t + 1 < N) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) nxt[g.tid + j * g.A] = pf[j];
+      }
+      const int oj = a.obs_of_t[t + 1];
+      const bool refresh = ((t + 1) % a.K == 0) && (t + 1 < N);
+      if (oj >= 0 || refresh) {
+        write_mirror(mir, g, dl);
+        sync_cluster_or_block(refresh && clus);
+        if (oj >= 0) gather_obs(a, g, oj, mir, stash);
+        if (refresh) {
+          read_halo(dl, mir, g);
+          sync_cluster_or_block(clus);
+        }
+      }
+      publish(eb[0], g, dl);
+      __syncthreads();
+    }
+    // the stash written by every CTA of the cluster must be visible to all
+    if (clus) cg::this_cluster().sync();
+  }
+
+  // ------------------------------------------------------ adjoint, backward
+  T lam[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) lam[c] = T(0);
+
+  auto inject = [&](int oj) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) mir[g.l0 + c] = T(0);
+    __syncthreads();
+    if (a.obs_tab != nullptr) {
+      const int* tb = obs_ranges(a.obs_tab, a.nos, g.rank, oj);
+#pragma unroll
+      for (int sgm = 0; sgm < 2; ++sgm) {
+        const int k0 = tb[2 + 3 * sgm], k1 = tb[3 + 3 * sgm], base = tb[4 + 3 * sgm];
+        for (int k = k0 + g.tid; k < k1; k += g.A) mir[a.obs_idx[k] - base] = stash[k];
+      }
+    } else {
+      const int k0 = a.obs_ptr[oj], k1 = a.obs_ptr[oj + 1];
+      for (int k = k0 + g.tid; k < k1; k += g.A) {
+        const int gi = a.obs_idx[k];
+        const T val = stash[k];
+        int l = ((gi - g.gbase) % g.n + g.n) % g.n;
+        for (; l < g.E; l += g.n) mir[l] = val;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < C; ++c) lam[c] += mir[g.l0 + c];
+  };
+
+  if (a.obs_of_t[N] >= 0) inject(a.obs_of_t[N]);
+  {
+    T* dst = ((N - 1) & 1) ? xs1 : xs0;
+    const T* src = trj + (long long)(N - 1) * a.n;
+#pragma unroll
+    for (int j = 0; j < C; ++j) dst[g.tid + j * g.A] = src[gp[j]];
+    __syncthreads();
+  }
+  for (int t = N - 1; t >= 0; --t) {
+    const T* cur = (t & 1) ? xs1 : xs0;
+    T* nxt = (t & 1) ? xs0 : xs1;
+    T pf[C];
+    if (t > 0) {
+      const T* src = trj + (long long)(t - 1) * a.n;
+#pragma unroll
+      for (int j = 0; j < C; ++j) pf[j] = src[gp[j]];
+    }
+    Run<T, C> X, wv;
+    T X1[C], X2[C], X3[C], X4[C], ln[C], ad[C];
+    // forward recomputation of the stage states
+    run_from_smem(cur, g, X);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      X1[c] = X.v[c];
+      X2[c] = X1[c] + h2 * tend(X, c, F);
+      ad[c] = h6 * lam[c];
+    }
+    publish(eb[1], g, X2);
+    publish(eb[3], g, ad);
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < C; ++c) X.v[c] = X2[c];
+    fetch(eb[1], g, X);
+#pragma unroll
+    for (int c = 0; c < C; ++c) X3[c] = X1[c] + h2 * tend(X, c, F);
+    publish(eb[2], g, X3);
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < C; ++c) X.v[c] = X3[c];
+    fetch(eb[2], g, X);
+#pragma unroll
+    for (int c = 0; c < C; ++c) X4[c] = X1[c] + h * tend(X, c, F);
+    publish(eb[5], g, X4);
+    __syncthreads();
+    // reverse stage 4: g4 = J4^T a4, a4 = h/6 lam
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      X.v[c] = X4[c];
+      wv.v[c] = ad[c];
+    }
+    fetch(eb[5], g, X);
+    fetch(eb[3], g, wv);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const T gg = jtvp(X, wv, c);
+      ln[c] = lam[c] + gg;
+      ad[c] = h3 * lam[c] + h * gg;  // a3
+    }
+    publish(eb[4], g, ad);
+    __syncthreads();
+    // reverse stage 3
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      X.v[c] = X3[c];
+      wv.v[c] = ad[c];
+    }
+    fetch(eb[2], g, X);
+    fetch(eb[4], g, wv);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const T gg = jtvp(X, wv, c);
+      ln[c] += gg;
+      ad[c] = h3 * lam[c] + h2 * gg;  // a2
+    }
+    publish(eb[3], g, ad);
+    __syncthreads();
+    // reverse stage 2
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      X.v[c] = X2[c];
+      wv.v[c] = ad[c];
+    }
+    fetch(eb[1], g, X);
+    fetch(eb[3], g, wv);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const T gg = jtvp(X, wv, c);
+      ln[c] += gg;
+      ad[c] = h6 * lam[c] + h2 * gg;  // a1
+    }
+    publish(eb[4], g, ad);
+    __syncthreads();
+    // reverse stage 1
+    run_from_smem(cur, g, X);
+#pragma unroll
+    for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
+    fetch(eb[4], g, wv);
+#pragma unroll
+    for (int c = 0; c < C; ++c) lam[c] = ln[c] + jtvp(X, wv, c);
+    if (t > 0) {
+#pragma unroll
+      for (int j = 0; j < C; ++j) nxt[g.tid + j * g.A] = pf[j];
+    }
+    const int oj = a.obs_of_t[t];
+    if (oj >= 0) inject(oj);
+    const bool refresh = ((N - t) % a.K == 0) && (t > 0);
+    if (refresh) {
+      write_mirror(mir, g, lam);
+      sync_cluster_or_block(clus);
+      read_halo(lam, mir, g);
+      sync_cluster_or_block(clus);
+    }
+    __syncthreads();
+  }
+
+  // ---------------------------------------------- output U_B lambda_0 (+ v)
+  for (int j = g.tid; j <= w; j += g.A) cf[j] = a.bcoef[j];
+  write_mirror(mir, g, lam);
+  sync_cluster_or_block(clus);
+  T* out = a.OUT + (long long)col * a.out_stride;
+  const T* ident = (a.mode == MODE_HVP && a.include_identity) ? V : nullptr;
+  bhalf_from_mirrors<T, C>(a, g, mir, sm, cf, out, ident);
+}
+
+template <typename T, int C>
+cudaError_t launch_impl(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t s) {
+  auto kern = sweep_kernel<T, C>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
+  if (err != cudaSuccess) return err;
+  if (p.CS > 8) {
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (err != cudaSuccess) return err;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.ncol * p.CS), 1, 1);
+  cfg.blockDim = dim3((unsigned)p.A, 1, 1);
+  cfg.dynamicSmemBytes = p.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (p.CS > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)p.CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
+}  // namespace
+
+bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* out) {
+  const int C = (elem_bytes == 8) ? 4 : 8;
+  if (CS < 1 || CS > 16 || K < 1) return false;
+  const int Ttile = (n + CS - 1) / CS;
+  if ((CS - 1) * Ttile >= n) return false;
+  const int HL = 8 * K + 8;
+  const int need = Ttile + 2 * HL;
+  int A = (need + C - 1) / C;
+  A = ((A + 31) / 32) * 32;
+  if (A > kMaxThreads) return false;
+  const int E = A * C;
+  int xsz = 2 * E;
+  if (E + 2 * w + 2 > xsz) xsz = E + 2 * w + 2;
+  if (Ttile + 2 * w + 2 > xsz) xsz = Ttile + 2 * w + 2;
+  const size_t elems = (size_t)xsz + (size_t)E + (size_t)kNumEdge * 4 * A + (size_t)(w + 1);
+  const size_t smem = elems * (size_t)elem_bytes;
+  if (smem > 227 * 1024) return false;
+  out->CS = CS;
+  out->C = C;
+  out->A = A;
+  out->E = E;
+  out->Ttile = Ttile;
+  out->HL = HL;
+  out->K = K;
+  out->smem = smem;
+  return true;
+}
+
+bool plan_sweep(int n, int elem_bytes, int w, int min_cs, int K_hint, SweepPlan* out) {
+  for (int CS = (min_cs > 1 ? min_cs : 1); CS <= 16; ++CS) {
+    const int K = K_hint > 0 ? K_hint : (CS == 1 ? 4 : 8);
+    if (plan_sweep_exact(n, elem_bytes, w, CS, K, out)) return true;
+  }
+  return false;
+}
+
+void obs_table(const SweepPlan& p, int n, int nos, const int* obs_ptr, const int* obs_idx, int* tab,
+               bool* usable) {
+  *usable = p.E <= n;
+  if (!*usable) return;
+  auto lower = [&](int j, int g) {
+    int lo = obs_ptr[j], hi = obs_ptr[j + 1];
+    while (lo < hi) {
+      const int mid = (lo + hi) / 2;
+      if (obs_idx[mid] < g)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    return lo;
+  };
+  for (int r = 0; r < p.CS; ++r) {
+    const int a0 = r * p.Ttile;
+    const int town = (p.Ttile < n - a0) ? p.Ttile : n - a0;
+    const int gbase = ((a0 - p.HL) % n + n) % n;
+    for (int j = 0; j < nos; ++j) {
+      int* t = tab + ((long long)r * nos + j) * 8;
+      t[0] = lower(j, a0);
+      t[1] = lower(j, a0 + town);
+      if (gbase + p.E <= n) {
+        t[2] = lower(j, gbase);
+        t[3] = lower(j, gbase + p.E);
+        t[4] = gbase;
+        t[5] = t[6] = 0;
+        t[7] = 0;
+      } else {
+        t[2] = lower(j, gbase);
+        t[3] = obs_ptr[j + 1];
+        t[4] = gbase;
+        t[5] = obs_ptr[j];
+        t[6] = lower(j, gbase + p.E - n);
+        t[7] = gbase - n;
+      }
+    }
+  }
+}
+
+template <typename T>
+cudaError_t launch_sweep(const SweepArgs<T>& a0, const SweepPlan& p, cudaStream_t s) {
+  SweepArgs<T> a = a0;
+  a.CS = p.CS;
+  a.Ttile = p.Ttile;
+  a.HL = p.HL;
+  a.E = p.E;
+  a.K = p.K;
+  if (a.ncol <= 0) return cudaSuccess;
+  if constexpr (sizeof(T) == 8) {
+    if (p.C != 4) return cudaErrorInvalidValue;
+    return launch_impl<T, 4>(a, p, s);
+  } else {
+    if (p.C != 8) return cudaErrorInvalidValue;
+    return launch_impl<T, 8>(a, p, s);
+  }
+}
+
+template cudaError_t launch_sweep<double>(const SweepArgs<double>&, const SweepPlan&, cudaStream_t);
+template cudaError_t launch_sweep<float>(const SweepArgs<float>&, const SweepPlan&, cudaStream_t);
+
+}  // namespace eda

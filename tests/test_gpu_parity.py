@@ -1,0 +1,285 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Inputs come from the seeded draws and the oracle's identical twin; expected
+values from the oracle.  FP64 path: 1e-10 relative (Hessian products,
+right-hand sides, solutions at equal iteration counts); mixed path: the error
+against the oracle is reported and bounded.
+"""
+from dataclasses import replace
+
+import numpy as np
+import pytest
+
+import eda_synth as S
+import oracle as O
+from helpers import env, problem, rel, rowrel
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2605_23571_gb300")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    P.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def make(spec, taps, precision=P.EDA_FP64, **kw):
+    return P.Handle.from_spec(spec, taps, precision=precision, **kw)
+
+
+def oracle_setup(spec, taps, xb, y):
+    traj = O.member_trajectories(spec, xb)
+    d = O.innovations(spec, traj, y)
+    b = O.rhs(spec, traj, d, taps)
+    return traj, d, b
+
+
+SMALL = [
+    S.spec_small(40, 20, 11, every_step=4, length_scale=2.0),   # the n=40 tiny workload
+    S.spec_small(97, 13, 5, every_var=3, every_step=3, length_scale=3.0, seed=1),  # ragged
+    S.spec_small(5, 6, 3, every_var=1, every_step=1, length_scale=0.7, seed=2),    # minimal n
+    S.spec_small(300, 16, 7, every_var=2, every_step=2, length_scale=8.0, seed=3),
+]
+
+
+@pytest.mark.parametrize("spec", SMALL, ids=lambda s: s.name)
+def test_twin_matches_oracle_without_spinup(spec):
+    spec = replace(spec, spinup=3)
+    taps = O.bhalf_taps(spec.n, spec.length_scale, spec.sigma_b)
+    dr = S.draws(spec)
+    _, xb_o, y_o = O.twin(spec, dr, taps)
+    x_spin0 = spec.F + spec.spin_sigma * dr.eta_spin
+    with make(spec, taps) as h:
+        xb = np.zeros((spec.n_members, spec.n))
+        y = np.zeros((spec.n_members, spec.p))
+        h.eda_twin(np.ascontiguousarray(x_spin0), spec.spinup, dr.eta_b, dr.eta_o, xb, y)
+    assert rel(xb, xb_o) < 1e-13
+    assert rel(y, y_o) < 1e-13
+
+
+@pytest.mark.parametrize("spec", SMALL, ids=lambda s: s.name)
+def test_rhs_and_hvp_fp64(spec):
+    taps, xb, y = problem(spec)
+    traj, d, b = oracle_setup(spec, taps, xb, y)
+    rng = np.random.default_rng(7)
+    ncol = 2 * spec.n_members + 1
+    cols = rng.integers(0, spec.n_members, ncol).astype(np.int32)
+    V = rng.standard_normal((ncol, spec.n))
+    ref = O.hvp(spec, traj[cols], V, taps)
+    refA = O.hvp(spec, traj[cols], V, taps, identity=False)
+    with make(spec, taps) as h:
+        rhs = np.zeros_like(b)
+        h.eda_set_trajectory(xb, y, rhs)
+        assert rowrel(rhs, b).max() < 1e-11
+        HV = np.zeros_like(V)
+        h.eda_hvp(cols, V, HV, True)
+        assert rowrel(HV, ref).max() < 1e-11
+        h.eda_hvp(cols, V, HV, False)
+        assert rowrel(HV, refA).max() < 1e-10
+
+
+@pytest.mark.parametrize("cs", [2, 3, 5])
+def test_hvp_fp64_cluster_split(cs):
+    # the same column split over a cluster of CTAs exchanging halos
+    spec = S.spec_small(600, 24, 4, every_var=2, every_step=3, length_scale=4.0, seed=5)
+    taps, xb, y = problem(spec)
+    traj, d, b = oracle_setup(spec, taps, xb, y)
+    rng = np.random.default_rng(cs)
+    cols = np.array([0, 1, 2, 3, 0], dtype=np.int32)
+    V = rng.standard_normal((len(cols), spec.n))
+    ref = O.hvp(spec, traj[cols], V, taps)
+    for K in (1, 3, 8):
+        with env(EDA_SWEEP_CS64=cs, EDA_SWEEP_K=K):
+            with make(spec, taps) as h:
+                rhs = np.zeros_like(b)
+                h.eda_set_trajectory(xb, y, rhs)
+                assert rowrel(rhs, b).max() < 1e-11, (cs, K)
+                HV = np.zeros_like(V)
+                h.eda_hvp(cols, V, HV, True)
+                assert rowrel(HV, ref).max() < 1e-11, (cs, K)
+
+
+def test_hvp_obs_at_window_ends():
+    # observations at t = 0 and t = N exercise the first gather and the first
+    # injection of the sweeps
+    n, N = 64, 9
+    steps = np.array([0, 4, 9], dtype=np.int32)
+    idx1 = np.arange(0, n, 3, dtype=np.int32)
+    spec = S.Spec(n=n, nsteps=N, obs_steps=steps,
+                  obs_ptr=(np.arange(4) * len(idx1)).astype(np.int32),
+                  obs_idx=np.tile(idx1, 3), sigma_o=0.5, sigma_b=1.0, length_scale=2.5,
+                  n_members=3, ell=2, k=2)
+    taps, xb, y = problem(spec)
+    traj, d, b = oracle_setup(spec, taps, xb, y)
+    V = np.random.default_rng(1).standard_normal((3, n))
+    cols = np.arange(3, dtype=np.int32)
+    with make(spec, taps) as h:
+        rhs = np.zeros_like(b)
+        h.eda_set_trajectory(xb, y, rhs)
+        assert rowrel(rhs, b).max() < 1e-11
+        HV = np.zeros_like(V)
+        h.eda_hvp(cols, V, HV, True)
+        assert rowrel(HV, O.hvp(spec, traj, V, taps)).max() < 1e-11
+
+
+def test_sketch_lmp_and_solve_fp64_tiny():
+    spec = S.spec_tiny(seed=4)
+    taps, xb, y = problem(spec)
+    # equal iteration counts: the fewest iterations any member needs to reach
+    # 1e-6, so that no member is iterating on rounding noise
+    K = int(O.eda_pipeline(spec, xb, y, taps, tol=1e-6, maxit=100)["iters"].min())
+    ref = O.eda_pipeline(spec, xb, y, taps, tol=0, maxit=K, fixed_iters=K)
+    with make(spec, taps) as h:
+        rhs = np.zeros_like(ref["b"])
+        h.eda_set_trajectory(xb, y, rhs)
+        Yg = np.zeros((spec.ell, spec.n))
+        h.eda_sketch(None, 1, Yg)
+        assert rel(Yg, ref["Y"].T) < 1e-11
+        ev = np.zeros(spec.k)
+        Sg = np.zeros((spec.k, spec.n))
+        h.eda_build_lmp(ev, Sg)
+        np.testing.assert_allclose(ev, 1 + ref["D"], rtol=1e-9)
+        # LMP action (sign/rotation invariant): S diag(c) S^T
+        Pg = (Sg.T * ref["c"]) @ Sg
+        Po = (ref["S"] * ref["c"]) @ ref["S"].T
+        assert np.linalg.norm(Pg - Po) <= 1e-8 * np.linalg.norm(Po)
+        dz = np.zeros_like(ref["b"])
+        it = np.zeros(spec.n_members, np.int32)
+        rr = np.zeros(spec.n_members)
+        st = np.zeros(spec.n_members, np.int32)
+        # PCG parity with one preconditioner on both sides: the Nystrom
+        # factors agree only to ~eps * cond(Phi^T A Phi) ~ 1e-8, and CG
+        # amplifies preconditioner differences, so the oracle's LMP is loaded
+        h.eda_set_lmp(np.ascontiguousarray(ref["S"].T), 1 + ref["D"])
+        h.eda_solve_batch(0.0, K, None, True, dz, it, rr, st)
+        assert (it == K).all()
+        assert rowrel(dz, ref["x"]).max() < 1e-10
+        np.testing.assert_allclose(rr, ref["relres"], rtol=1e-7)
+
+
+def test_solve_tolerance_stopped_fp64_tiny():
+    spec = S.spec_tiny(seed=5)
+    taps, xb, y = problem(spec)
+    ref = O.eda_pipeline(spec, xb, y, taps, tol=1e-6, maxit=100)
+    exact = O.eda_pipeline(spec, xb, y, taps, tol=1e-13, maxit=300)["x"]
+    with make(spec, taps) as h:
+        h.eda_set_trajectory(xb, y)
+        h.eda_set_lmp(np.ascontiguousarray(ref["S"].T), 1 + ref["D"])
+        dz = np.zeros_like(ref["b"])
+        it = np.zeros(spec.n_members, np.int32)
+        rr = np.zeros(spec.n_members)
+        st = np.zeros(spec.n_members, np.int32)
+        h.eda_solve_batch(1e-6, 100, None, True, dz, it, rr, st)
+        assert (st == P.EDA_CONVERGED).all()
+        assert np.abs(it - ref["iters"]).max() <= 1
+        assert (rr <= 1e-6).all()
+        # and with the LMP the library builds itself: converged, error bound
+        h.eda_sketch()
+        h.eda_build_lmp()
+        h.eda_solve_batch(1e-6, 100, None, True, dz, it, rr, st)
+    assert (st == P.EDA_CONVERGED).all()
+    assert np.abs(it - ref["iters"]).max() <= 3
+    assert (rr <= 1e-6).all()
+    # ||dz - dz*|| <= ||r|| since lambda_min(I + A) >= 1
+    err = np.linalg.norm(dz - exact, axis=1)
+    assert (err <= rr * np.linalg.norm(ref["b"], axis=1) * (1 + 1e-6) + 1e-12).all()
+
+
+def test_solve_without_lmp_and_with_x0():
+    spec = S.spec_small(97, 13, 5, every_var=3, every_step=3, length_scale=3.0, seed=6)
+    taps, xb, y = problem(spec)
+    traj, d, b = oracle_setup(spec, taps, xb, y)
+    x0 = np.random.default_rng(3).standard_normal(b.shape) * 0.1
+    ref = O.pcg(lambda V: O.hvp(spec, traj, V, taps), b, tol=0, maxit=9, x0=x0, fixed_iters=9)
+    with make(spec, taps) as h:
+        h.eda_set_trajectory(xb, y)
+        dz = np.zeros_like(b)
+        h.eda_solve_batch(0.0, 9, x0, False, dz)
+    assert rowrel(dz, ref["x"]).max() < 1e-10
+
+
+def test_mixed_precision_tiny_reports_error():
+    spec = S.spec_tiny(seed=6)
+    taps, xb, y = problem(spec)
+    exact = O.eda_pipeline(spec, xb, y, taps, tol=1e-13, maxit=300)
+    with make(spec, taps, precision=P.EDA_MIXED) as h:
+        h.eda_set_trajectory(xb, y)
+        h.eda_sketch()
+        h.eda_build_lmp()
+        dz = np.zeros_like(exact["b"])
+        it = np.zeros(spec.n_members, np.int32)
+        rr = np.zeros(spec.n_members)
+        st = np.zeros(spec.n_members, np.int32)
+        h.eda_solve_batch(1e-6, 200, None, True, dz, it, rr, st)
+    err = rowrel(dz, exact["x"])
+    print("mixed tiny: max rel err %.3e, iters %s, true relres max %.3e" % (err.max(), it, rr.max()))
+    assert (st == P.EDA_CONVERGED).all()
+    assert (rr <= 1e-6).all()
+    # the FP64 true residual bounds the error: ||e|| <= ||r|| (lambda_min >= 1)
+    bn = np.linalg.norm(exact["b"], axis=1)
+    assert (np.linalg.norm(dz - exact["x"], axis=1) <= rr * bn * (1 + 1e-6) + 1e-12).all()
+
+
+def test_hvp_device_tensors_and_empty_batch():
+    import torch
+    spec = S.spec_small(40, 20, 3, every_step=4)
+    taps, xb, y = problem(spec)
+    traj, d, b = oracle_setup(spec, taps, xb, y)
+    dev = torch.device("cuda:0")
+    with make(spec, taps) as h:
+        h.eda_set_trajectory(torch.tensor(xb, device=dev), torch.tensor(y, device=dev))
+        V = torch.randn(4, spec.n, dtype=torch.float64, device=dev)
+        HV = torch.empty_like(V)
+        cols = torch.tensor([2, 0, 1, 2], dtype=torch.int32, device=dev)
+        h.eda_hvp(cols, V, HV, True)
+        torch.cuda.synchronize()
+        ref = O.hvp(spec, traj[[2, 0, 1, 2]], V.cpu().numpy(), taps)
+        assert rowrel(HV.cpu().numpy(), ref).max() < 1e-11
+        h.eda_hvp(np.zeros(0, np.int32), np.zeros((0, spec.n)), np.zeros((0, spec.n)), True)
+
+
+def test_errors_are_reported():
+    spec = S.spec_small(40, 20, 3, every_step=4)
+    taps, xb, y = problem(spec)
+    with make(spec, taps) as h:
+        with pytest.raises(P.EdaError) as e:
+            h.eda_sketch()
+        assert e.value.code == P.EDA_ERR_STATE
+        bad = xb.copy()
+        bad[1, 3] = np.nan
+        with pytest.raises(P.EdaError) as e:
+            h.eda_set_trajectory(bad, y)
+        assert e.value.code == P.EDA_ERR_NUMERIC
+    with pytest.raises(P.EdaError) as e:
+        P.Handle.from_spec(spec, taps, n=3)
+    assert e.value.code == P.EDA_ERR_INVALID
+
+
+def test_full_size_batched_hvp_and_rhs_fp64():
+    # the n=4096, 64-step, 51-member workload: RHS of every member and one
+    # batched product (members' own trajectories) against the oracle
+    spec = replace(S.spec_batched(seed=0), spinup=200)
+    taps, xb, y = problem(spec)
+    traj, d, b = oracle_setup(spec, taps, xb, y)
+    rng = np.random.default_rng(11)
+    cols = np.arange(spec.n_members, dtype=np.int32)
+    V = rng.standard_normal((spec.n_members, spec.n))
+    ref = O.hvp(spec, traj, V, taps)
+    with make(spec, taps) as h:
+        rhs = np.zeros_like(b)
+        h.eda_set_trajectory(xb, y, rhs)
+        assert rowrel(rhs, b).max() < 1e-10
+        HV = np.zeros_like(V)
+        h.eda_hvp(cols, V, HV, True)
+        assert rowrel(HV, ref).max() < 1e-10
+    with make(spec, taps, precision=P.EDA_MIXED) as h:
+        h.eda_set_trajectory(xb, y)
+        HV = np.zeros_like(V)
+        h.eda_hvp(cols, V, HV, True)
+        e32 = rowrel(HV, ref).max()
+        print("FP32 sweep HVP rel err at n=4096, N=64: %.3e" % e32)
+        assert e32 < 1e-4
