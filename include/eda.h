@@ -249,6 +249,44 @@ EDA_API long long eda_kernel_launches(void);
  */
 EDA_API int eda_time_hvp_sweep(eda_handle* h, int reps, int fp64, double* ms_out);
 
+/* ------------------------------------------------------------------------
+ * Uneven batching (not in the paper, which solves one EDA at a time): a group
+ * of independent EDA problems -- each its own handle, with its own n, window,
+ * member count, observation network and U_B, all of one precision and on one
+ * stream -- whose sweeps run as single launches over all problems (one per
+ * thread-block shape), whose PCG vector updates and LMP applies run as
+ * batched launches over every (problem, member), and whose PCG iteration is
+ * captured once in a CUDA graph and replayed until every member converges.
+ * The handles stay owned by the caller and must outlive the group.
+ * ---------------------------------------------------------------------- */
+typedef struct eda_group eda_group;
+
+/* Groups count >= 1 handles.  EDA_ERR_INVALID if they differ in precision
+ * or stream, or a problem does not fit the sweep tiling. */
+EDA_API int eda_group_create(eda_handle* const* handles, int count, eda_group** out);
+EDA_API int eda_group_destroy(eda_group* g);
+/* Message of the group's last error (static or group-owned storage). */
+EDA_API const char* eda_group_last_error(const eda_group* g);
+/* eda_set_trajectory of every problem: xb[i] [(L_i+1) x n_i], y[i]
+ * [(L_i+1) x p_i] (host array of per-problem pointers, each host or device). */
+EDA_API int eda_group_set_trajectories(eda_group* g, const double* const* xb, const double* const* y);
+/* Gamma sketch Y = A Gamma of every problem's control Hessian (Algorithm 1,
+ * q = 1): all sketch columns of all problems in one launch per bucket. */
+EDA_API int eda_group_sketch(eda_group* g);
+/* The rest of Algorithm 1 and the LMP of every problem (eda_build_lmp). */
+EDA_API int eda_group_build_lmp(eda_group* g);
+/* Autotuner: times the group's batched member sweep for halo refresh periods
+ * K in {2, 4, 8, 16} per bucket, keeps the fastest per problem.
+ * *best_ms_out (may be NULL) = mean time of the tuned batched sweep (ms). */
+EDA_API int eda_group_autotune(eda_group* g, double* best_ms_out);
+/* Batched PCG of every member of every problem (as eda_solve_batch, x0 = 0).
+ * dz_out[i] [(L_i+1) x n_i] per problem (host array of pointers, each host or
+ * device, NULL entries skipped; dz_out itself may be NULL); iters_out,
+ * relres_out, status_out [sum_i (L_i+1)] concatenated in problem order (host
+ * or device, may be NULL).  Synchronises the stream. */
+EDA_API int eda_group_solve(eda_group* g, double tol, int maxit, int use_lmp, double* const* dz_out,
+                            int* iters_out, double* relres_out, int* status_out);
+
 /*
  * Host helper: taps of U_B for a Gaussian correlation
  * B = sigma_b^2 exp(-d^2 / (2 L^2)) on the circle of n points:

@@ -30,7 +30,9 @@ EDA_CONVERGED, EDA_MAXIT, EDA_NAN, EDA_BREAKDOWN = 0, 1, 2, 3
 # every symbol the header declares
 EXPORTS = ["eda_version", "eda_last_error", "eda_create", "eda_destroy", "eda_twin",
            "eda_set_trajectory", "eda_sketch", "eda_build_lmp", "eda_set_lmp", "eda_solve_batch", "eda_hvp",
-           "eda_bhalf_gaussian", "eda_kernel_launches", "eda_time_hvp_sweep", "eda_autotune"]
+           "eda_bhalf_gaussian", "eda_kernel_launches", "eda_time_hvp_sweep", "eda_autotune",
+           "eda_group_create", "eda_group_destroy", "eda_group_last_error", "eda_group_set_trajectories",
+           "eda_group_sketch", "eda_group_build_lmp", "eda_group_autotune", "eda_group_solve"]
 
 
 class EdaError(RuntimeError):
@@ -96,6 +98,22 @@ def lib() -> ctypes.CDLL:
     L.eda_autotune.argtypes = [vp, i, ctypes.POINTER(ctypes.c_double)]
     L.eda_time_hvp_sweep.restype = i
     L.eda_time_hvp_sweep.argtypes = [vp, i, i, ctypes.POINTER(ctypes.c_double)]
+    L.eda_group_create.restype = i
+    L.eda_group_create.argtypes = [ctypes.POINTER(vp), i, ctypes.POINTER(vp)]
+    L.eda_group_destroy.restype = i
+    L.eda_group_destroy.argtypes = [vp]
+    L.eda_group_last_error.restype = ctypes.c_char_p
+    L.eda_group_last_error.argtypes = [vp]
+    L.eda_group_set_trajectories.restype = i
+    L.eda_group_set_trajectories.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp)]
+    L.eda_group_sketch.restype = i
+    L.eda_group_sketch.argtypes = [vp]
+    L.eda_group_build_lmp.restype = i
+    L.eda_group_build_lmp.argtypes = [vp]
+    L.eda_group_autotune.restype = i
+    L.eda_group_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.eda_group_solve.restype = i
+    L.eda_group_solve.argtypes = [vp, d, i, i, ctypes.POINTER(vp), vp, vp, vp]
     L.eda_bhalf_gaussian.restype = i
     L.eda_bhalf_gaussian.argtypes = [i, d, d, vp, i, ctypes.POINTER(ctypes.c_int)]
     _lib = L
@@ -267,3 +285,73 @@ class Handle:
         self._check(self._L.eda_hvp(self._h, _ptr(member_of_col, np.int32, ncol, "member_of_col"), ncol,
                                     _ptr(V, np.float64, ncol * n, "V"), _ptr(HV, np.float64, ncol * n, "HV"),
                                     1 if include_identity else 0))
+
+
+class Group:
+    """Independent EDA problems solved together (wraps ``eda_group``).
+
+    ``handles`` are ``Handle`` objects of one precision and stream; they must
+    outlive the group.  Methods carry the C names of ``include/eda.h``.
+    """
+
+    def __init__(self, handles):
+        self._L = lib()
+        self.handles = list(handles)
+        arr = (ctypes.c_void_p * len(self.handles))(*[h._h.value for h in self.handles])
+        g = ctypes.c_void_p(None)
+        rc = self._L.eda_group_create(arr, len(self.handles), ctypes.byref(g))
+        if rc != EDA_OK:
+            raise EdaError(rc, self._L.eda_last_error(None).decode())
+        self._g = g
+        self.total_members = sum(h.M for h in self.handles)
+
+    def _check(self, rc):
+        if rc != EDA_OK:
+            raise EdaError(rc, self._L.eda_group_last_error(self._g).decode())
+
+    def close(self):
+        if getattr(self, "_g", None) is not None and self._g.value:
+            self._L.eda_group_destroy(self._g)
+            self._g = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def eda_group_set_trajectories(self, xbs, ys):
+        xa = (ctypes.c_void_p * len(xbs))(*[_ptr(x, np.float64, h.M * h.n, "xb")
+                                            for x, h in zip(xbs, self.handles)])
+        ya = (ctypes.c_void_p * len(ys))(*[_ptr(y, np.float64, h.M * h.p, "y")
+                                           for y, h in zip(ys, self.handles)])
+        self._check(self._L.eda_group_set_trajectories(self._g, xa, ya))
+
+    def eda_group_sketch(self):
+        self._check(self._L.eda_group_sketch(self._g))
+
+    def eda_group_build_lmp(self):
+        self._check(self._L.eda_group_build_lmp(self._g))
+
+    def eda_group_autotune(self):
+        ms = ctypes.c_double(0.0)
+        self._check(self._L.eda_group_autotune(self._g, ctypes.byref(ms)))
+        return ms.value
+
+    def eda_group_solve(self, tol, maxit, use_lmp, dz_outs=None, iters_out=None, relres_out=None,
+                        status_out=None):
+        T = self.total_members
+        da = None
+        if dz_outs is not None:
+            da = (ctypes.c_void_p * len(dz_outs))(*[_ptr(z, np.float64, h.M * h.n, "dz")
+                                                    for z, h in zip(dz_outs, self.handles)])
+        self._check(self._L.eda_group_solve(self._g, float(tol), int(maxit), 1 if use_lmp else 0, da,
+                                            _ptr(iters_out, np.int32, T, "iters_out"),
+                                            _ptr(relres_out, np.float64, T, "relres_out"),
+                                            _ptr(status_out, np.int32, T, "status_out")))

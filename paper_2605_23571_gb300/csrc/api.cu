@@ -10,8 +10,7 @@
 #include <string>
 #include <vector>
 
-#include "dense.h"
-#include "eda_internal.h"
+#include "handle.h"
 
 namespace eda {
 namespace {
@@ -20,79 +19,14 @@ std::atomic<long long> g_launches{0};
 void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 }  // namespace eda
 
-using eda::PcgScalars;
-using eda::SweepArgs;
-using eda::SweepPlan;
+using eda::env_int;
+using eda::fail;
+using eda::grid_for;
+using eda::is_device_ptr;
+using eda::read_flag;
+using eda::set_plan;
 
-struct eda_handle {
-  // problem
-  int n = 0, N = 0, M = 0, p = 0, nos = 0, w = 0, ell = 0, k = 0;
-  int theta_mode = 0, precision = 0, ckpt = 0;
-  double F = 8.0, dt = 0.025, theta_given = 1.0;
-  cudaStream_t st = nullptr;
-  std::string err;
-  std::vector<int> h_obs_of_t;
-  // device: problem definition
-  int* obs_of_t = nullptr;
-  int* obs_ptr = nullptr;
-  int* obs_idx = nullptr;
-  double* rinv = nullptr;
-  float* rinv32 = nullptr;
-  double* bcoef = nullptr;
-  float* bcoef32 = nullptr;
-  // device: setup products
-  double* traj = nullptr;
-  float* traj32 = nullptr;
-  double* d = nullptr;
-  double* rd = nullptr;
-  double* b = nullptr;
-  // device: sketch and LMP
-  double* Phi = nullptr;
-  double* Y = nullptr;
-  float* V32a = nullptr;  // ell x n scratch (FP32 sweeps)
-  float* V32b = nullptr;
-  double* Q1 = nullptr;
-  double* Q = nullptr;
-  double* G = nullptr;
-  double* R1 = nullptr;
-  double* R1i = nullptr;
-  double* R2 = nullptr;
-  double* R2i = nullptr;
-  double* RY = nullptr;
-  double* W = nullptr;
-  double* UT = nullptr;
-  double* Dv = nullptr;
-  double* cv = nullptr;
-  double* theta = nullptr;
-  int* dstatus = nullptr;
-  double* S = nullptr;
-  float* S32 = nullptr;
-  double* lmpW = nullptr;  // k x M
-  // device: PCG
-  double *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr;
-  float *r32 = nullptr, *z32 = nullptr, *p32 = nullptr, *q32 = nullptr;
-  PcgScalars* sc = nullptr;
-  int* active = nullptr;
-  int* nactive = nullptr;
-  int* cols = nullptr;  // identity member map 0..max(M, ell)-1
-  int* zeros = nullptr; // member map of zeros (control trajectory)
-  int* hflag = nullptr; // pinned host int
-  // stash
-  double* stash = nullptr;
-  float* stash32 = nullptr;
-  int stash_cols = 0;
-  // state
-  bool have_traj = false, have_sketch = false, have_lmp = false;
-  double shift_used = 0.0;
-  SweepPlan plan64{}, plan32{};
-  int* tab64 = nullptr;  // per-CTA observation ranges of plan64 / plan32
-  int* tab32 = nullptr;
-  bool tab64_ok = false, tab32_ok = false;
-  std::vector<int> h_obs_ptr, h_obs_idx;
-  std::vector<void*> allocs;
-};
-
-namespace {
+namespace eda {
 
 thread_local std::string g_err;
 
@@ -100,22 +34,6 @@ int fail(eda_handle* h, int code, const std::string& msg) {
   if (h) h->err = msg;
   g_err = msg;
   return code;
-}
-
-#define CU(h, ...)                                                                               \
-  do {                                                                                           \
-    cudaError_t e__ = (__VA_ARGS__);                                                             \
-    if (e__ != cudaSuccess) {                                                                    \
-      return fail((h), EDA_ERR_CUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e__)); \
-    }                                                                                            \
-  } while (0)
-
-template <typename T>
-cudaError_t dalloc(eda_handle* h, T** p, size_t count) {
-  if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
-  if (e == cudaSuccess) h->allocs.push_back((void*)*p);
-  return e;
 }
 
 bool is_device_ptr(const void* ptr) {
@@ -127,6 +45,64 @@ bool is_device_ptr(const void* ptr) {
     return false;
   }
   return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+unsigned grid_for(long long count) {
+  long long g = (count + 255) / 256;
+  if (g < 1) g = 1;
+  if (g > 8192) g = 8192;
+  return (unsigned)g;
+}
+
+// Installs a sweep tiling and its observation table.
+int set_plan(eda_handle* h, bool fp64, const SweepPlan& pl) {
+  std::vector<int> tab((size_t)pl.CS * h->nos * 8);
+  bool ok = false;
+  eda::obs_table(pl, h->n, h->nos, h->h_obs_ptr.data(), h->h_obs_idx.data(), tab.data(), &ok);
+  int*& dt = fp64 ? h->tab64 : h->tab32;
+  if (dt) {
+    CU(h, cudaStreamSynchronize(h->st));
+    CU(h, cudaFree(dt));
+    dt = nullptr;
+  }
+  if (ok) {
+    CU(h, cudaMalloc((void**)&dt, tab.size() * sizeof(int)));
+    CU(h, cudaMemcpy(dt, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice));
+  }
+  if (fp64) {
+    h->plan64 = pl;
+    h->tab64_ok = ok;
+  } else {
+    h->plan32 = pl;
+    h->tab32_ok = ok;
+  }
+  return EDA_OK;
+}
+
+int read_flag(eda_handle* h, const int* dflag, int* out) {
+  CU(h, cudaMemcpyAsync(h->hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CU(h, cudaStreamSynchronize(h->st));
+  *out = *h->hflag;
+  return EDA_OK;
+}
+
+int env_int(const char* name, int dflt) {
+  const char* s = std::getenv(name);
+  return (s && *s) ? std::atoi(s) : dflt;
+}
+
+}  // namespace eda
+
+namespace {
+
+
+
+template <typename T>
+cudaError_t dalloc(eda_handle* h, T** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e == cudaSuccess) h->allocs.push_back((void*)*p);
+  return e;
 }
 
 // An input array given as host or device memory, seen as device memory.
@@ -261,6 +237,12 @@ __global__ void iota_kernel(int count, int* v, int value_mode) {
     v[i] = value_mode ? i : 0;
 }
 
+// first inner threshold of the mixed solve: max(tol, tau * relres0)
+__global__ void set_tolm_kernel(int M, PcgScalars* sc, double tol, double tau) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x)
+    sc[j].tolm = fmax(tol, tau * sc[j].relres);
+}
+
 __global__ void export_kernel(int M, const PcgScalars* sc, int* iters, double* relres, int* status) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
     if (iters) iters[j] = sc[j].iters;
@@ -274,17 +256,22 @@ __global__ void eig_kernel(int k, const double* D, double* out) {
 }
 
 // true-residual bookkeeping of the mixed solve
-__global__ void true_res_kernel(int n, const double* b, const double* hx, float* r32, PcgScalars* sc,
-                                int* active, double tol, int* nactive, int* need) {
+// FP64 true residual r = b - H x of every member; a member whose true
+// residual misses tol is reactivated with the next inner threshold
+// max(tol, tau * true relres).
+__global__ void true_res_kernel(int n, const double* b, const double* hx, float* r32, double* r64,
+                                PcgScalars* sc, int* active, double tol, int* nactive, int* need, double tau) {
   __shared__ double red[32];
   const int j = blockIdx.x;
   const double* bj = b + (long long)j * n;
   const double* hj = hx + (long long)j * n;
-  float* rj = r32 + (long long)j * n;
+  float* rj = r32 ? r32 + (long long)j * n : nullptr;
+  double* rj64 = r64 + (long long)j * n;
   double s = 0.0;
   for (int g = threadIdx.x; g < n; g += blockDim.x) {
     const double rv = bj[g] - hj[g];
-    rj[g] = (float)rv;
+    if (rj) rj[g] = (float)rv;
+    rj64[g] = rv;
     s += rv * rv;
   }
 #pragma unroll
@@ -299,20 +286,15 @@ __global__ void true_res_kernel(int n, const double* b, const double* hx, float*
     sc[j].relres = rel;
     const bool ok = (bn == 0.0) || (rel <= tol);
     if (sc[j].status == EDA_CONVERGED && !ok) {
-      // recurrence said converged, the FP64 residual disagrees: continue
+      // the inner solve met its threshold but the FP64 residual misses tol:
+      // next refinement round
       sc[j].status = EDA_MAXIT;
+      sc[j].tolm = fmax(tol, tau * rel);
       active[j] = 1;
       atomicAdd(nactive, 1);
       atomicAdd(need, 1);
     }
   }
-}
-
-inline unsigned grid_for(long long count) {
-  long long g = (count + 255) / 256;
-  if (g < 1) g = 1;
-  if (g > 8192) g = 8192;
-  return (unsigned)g;
 }
 
 // ------------------------------------------------------------- sweep helpers
@@ -359,31 +341,6 @@ int ensure_stash(eda_handle* h, int ncol) {
   return EDA_OK;
 }
 
-// Installs a sweep tiling and its observation table.
-int set_plan(eda_handle* h, bool fp64, const SweepPlan& pl) {
-  std::vector<int> tab((size_t)pl.CS * h->nos * 8);
-  bool ok = false;
-  eda::obs_table(pl, h->n, h->nos, h->h_obs_ptr.data(), h->h_obs_idx.data(), tab.data(), &ok);
-  int*& dt = fp64 ? h->tab64 : h->tab32;
-  if (dt) {
-    CU(h, cudaStreamSynchronize(h->st));
-    CU(h, cudaFree(dt));
-    dt = nullptr;
-  }
-  if (ok) {
-    CU(h, cudaMalloc((void**)&dt, tab.size() * sizeof(int)));
-    CU(h, cudaMemcpy(dt, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice));
-  }
-  if (fp64) {
-    h->plan64 = pl;
-    h->tab64_ok = ok;
-  } else {
-    h->plan32 = pl;
-    h->tab32_ok = ok;
-  }
-  return EDA_OK;
-}
-
 // HV = (ident ? V : 0) + A_{m(c)} V for ncol columns, device pointers, FP64 at
 // the interface; FP32 sweeps in EDA_MIXED unless force64.
 int hvp_dev(eda_handle* h, const int* dcols, int ncol, const double* V, double* HV, int ident, bool force64,
@@ -407,55 +364,20 @@ int hvp_dev(eda_handle* h, const int* dcols, int ncol, const double* V, double* 
     CU(h, eda::launch_sweep<double>(a, h->plan64, h->st));
     return EDA_OK;
   }
-  // FP32 sweeps through scratch vectors
-  float *v32 = nullptr, *o32 = nullptr;
-  const size_t cnt = (size_t)ncol * h->n;
-  CU(h, cudaMallocAsync((void**)&v32, cnt * sizeof(float), h->st));
-  CU(h, cudaMallocAsync((void**)&o32, cnt * sizeof(float), h->st));
-  CU(h, eda::convert<double, float>((long long)cnt, V, v32, h->st));
+  // FP32 sweeps reading and writing the FP64 vectors directly
   SweepArgs<float> a = base_args<float>(h);
   a.mode = eda::MODE_HVP;
   a.ncol = ncol;
   a.col_member = dcols;
   a.col_active = active;
-  a.V = v32;
+  a.V64 = V;
   a.v_stride = h->n;
-  a.OUT = o32;
+  a.OUT64 = HV;
   a.out_stride = h->n;
   a.stash = h->stash32;
   a.stash_stride = h->p;
   a.include_identity = ident;
   CU(h, eda::launch_sweep<float>(a, h->plan32, h->st));
-  CU(h, eda::convert<float, double>((long long)cnt, o32, HV, h->st));
-  CU(h, cudaFreeAsync(v32, h->st));
-  CU(h, cudaFreeAsync(o32, h->st));
-  return EDA_OK;
-}
-
-// FP32 HVP on FP32 vectors (the mixed PCG), active mask.
-int hvp32_dev(eda_handle* h, const float* V, float* HV, const int* active) {
-  int rc = ensure_stash(h, h->M);
-  if (rc) return rc;
-  SweepArgs<float> a = base_args<float>(h);
-  a.mode = eda::MODE_HVP;
-  a.ncol = h->M;
-  a.col_member = h->cols;
-  a.col_active = active;
-  a.V = V;
-  a.v_stride = h->n;
-  a.OUT = HV;
-  a.out_stride = h->n;
-  a.stash = h->stash32;
-  a.stash_stride = h->p;
-  a.include_identity = 1;
-  CU(h, eda::launch_sweep<float>(a, h->plan32, h->st));
-  return EDA_OK;
-}
-
-int read_flag(eda_handle* h, const int* dflag, int* out) {
-  CU(h, cudaMemcpyAsync(h->hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
-  CU(h, cudaStreamSynchronize(h->st));
-  *out = *h->hflag;
   return EDA_OK;
 }
 
@@ -496,24 +418,6 @@ int cholqr2(eda_handle* h, const double* Yin, double* Qout) {
   return EDA_OK;
 }
 
-// z = P r for active members (or z = r without the LMP).
-template <typename T>
-int lmp_apply_dev(eda_handle* h, const T* r, T* z, bool use_lmp) {
-  const int n = h->n, M = h->M;
-  if (!use_lmp) {
-    CU(h, cudaMemcpyAsync(z, r, (size_t)M * n * sizeof(T), cudaMemcpyDeviceToDevice, h->st));
-    return EDA_OK;
-  }
-  const T* Sx;
-  if constexpr (sizeof(T) == 8)
-    Sx = h->S;
-  else
-    Sx = h->S32;
-  CU(h, eda::gemm_tn<T, T>(n, Sx, h->k, r, M, h->lmpW, h->k, h->active, false, h->st));
-  CU(h, eda::gemm_nn<T, T>(n, Sx, h->k, M, h->lmpW, h->cv, r, z, h->active, h->st));
-  return EDA_OK;
-}
-
 int check_finite(eda_handle* h, const double* v, long long count, const char* what) {
   CU(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
   eda::count_launch();
@@ -524,11 +428,6 @@ int check_finite(eda_handle* h, const double* v, long long count, const char* wh
   if (rc) return rc;
   if (bad) return fail(h, EDA_ERR_NUMERIC, std::string("non-finite values in ") + what);
   return EDA_OK;
-}
-
-int env_int(const char* name, int dflt) {
-  const char* s = std::getenv(name);
-  return (s && *s) ? std::atoi(s) : dflt;
 }
 
 }  // namespace
@@ -557,11 +456,7 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
     const bool fp64 = (pass == 0);
     if (!(which & (fp64 ? 1 : 2))) continue;
     if (!fp64 && h->precision != EDA_MIXED) continue;
-    if (fp64) {
-      CU(h, cudaMemcpyAsync(h->pv, h->b, cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-    } else {
-      CU(h, eda::convert<double, float>((long long)cnt, h->b, h->p32, h->st));
-    }
+    CU(h, cudaMemcpyAsync(h->pv, h->b, cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
     const SweepPlan keep = fp64 ? h->plan64 : h->plan32;
     SweepPlan best = keep;
     float best_ms = 1e30f;
@@ -576,7 +471,7 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
         float ms = 0.f;
         for (int rep = -1; rep < reps; ++rep) {
           if (rep == 0) CU(h, cudaEventRecord(e0, h->st));
-          rc = fp64 ? hvp_dev(h, h->cols, h->M, h->pv, h->q, 1, true, nullptr) : hvp32_dev(h, h->p32, h->q32, nullptr);
+          rc = hvp_dev(h, h->cols, h->M, h->pv, h->q, 1, fp64, nullptr);
           if (rc) return rc;
         }
         CU(h, cudaEventRecord(e1, h->st));
@@ -592,6 +487,9 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
     int rc = set_plan(h, fp64, best);
     if (rc) return rc;
     best_total += best_ms;
+    if (env_int("EDA_VERBOSE", 0))
+      std::fprintf(stderr, "eda_autotune: %s sweep CS=%d K=%d A=%d E=%d C=%d %.4f ms\n", fp64 ? "FP64" : "FP32", best.CS,
+                   best.K, best.A, best.E, best.C, best_ms);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -605,11 +503,7 @@ EDA_API int eda_time_hvp_sweep(eda_handle* h, int reps, int fp64, double* ms_out
   if (reps < 1 || !ms_out) return fail(h, EDA_ERR_INVALID, "eda_time_hvp_sweep: invalid argument");
   const bool use64 = fp64 || h->precision == EDA_FP64;
   const size_t cnt = (size_t)h->M * h->n;
-  if (use64) {
-    CU(h, cudaMemcpyAsync(h->pv, h->b, cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-  } else {
-    CU(h, eda::convert<double, float>((long long)cnt, h->b, h->p32, h->st));
-  }
+  CU(h, cudaMemcpyAsync(h->pv, h->b, cnt * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
   cudaEvent_t e0, e1;
   CU(h, cudaEventCreate(&e0));
   CU(h, cudaEventCreate(&e1));
@@ -617,7 +511,7 @@ EDA_API int eda_time_hvp_sweep(eda_handle* h, int reps, int fp64, double* ms_out
   float ms = 0.f;
   for (int rep = -1; rep < reps && rc == EDA_OK; ++rep) {
     if (rep == 0) CU(h, cudaEventRecord(e0, h->st));
-    rc = use64 ? hvp_dev(h, h->cols, h->M, h->pv, h->q, 1, true, nullptr) : hvp32_dev(h, h->p32, h->q32, nullptr);
+    rc = hvp_dev(h, h->cols, h->M, h->pv, h->q, 1, use64, nullptr);
   }
   CU(h, cudaEventRecord(e1, h->st));
   CU(h, cudaEventSynchronize(e1));
@@ -629,7 +523,7 @@ EDA_API int eda_time_hvp_sweep(eda_handle* h, int reps, int fp64, double* ms_out
   return EDA_OK;
 }
 
-EDA_API const char* eda_last_error(const eda_handle* h) { return h ? h->err.c_str() : g_err.c_str(); }
+EDA_API const char* eda_last_error(const eda_handle* h) { return h ? h->err.c_str() : eda::g_err.c_str(); }
 
 EDA_API int eda_bhalf_gaussian(int n, double length_scale, double sigma_b, double* taps_out, int max_taps,
                                int* w_out) {
@@ -772,18 +666,14 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
   CUC(dalloc(h, &h->z, (size_t)M * n));
   CUC(dalloc(h, &h->pv, (size_t)M * n));
   CUC(dalloc(h, &h->q, (size_t)M * n));
-  if (h->precision == EDA_MIXED) {
-    CUC(dalloc(h, &h->r32, (size_t)M * n));
-    CUC(dalloc(h, &h->z32, (size_t)M * n));
-    CUC(dalloc(h, &h->p32, (size_t)M * n));
-    CUC(dalloc(h, &h->q32, (size_t)M * n));
-  }
   CUC(dalloc(h, &h->sc, M));
   CUC(dalloc(h, &h->active, M));
   CUC(dalloc(h, &h->nactive, 1));
   CUC(dalloc(h, &h->cols, mcols));
   CUC(dalloc(h, &h->zeros, mcols));
   CUC(cudaMallocHost((void**)&h->hflag, sizeof(int)));
+  CUC(cudaMallocHost((void**)&h->hring, eda_handle::kRing * sizeof(int)));
+  for (int i = 0; i < eda_handle::kRing; ++i) CUC(cudaEventCreateWithFlags(&h->ring_ev[i], cudaEventDisableTiming));
 
   std::vector<float> tmp32(std::max(p, h->w + 1));
   CUC(cudaMemcpyAsync(h->obs_of_t, h->h_obs_of_t.data(), (N + 1) * sizeof(int), cudaMemcpyHostToDevice, h->st));
@@ -802,7 +692,7 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
   {
     const SweepPlan p64 = h->plan64, p32 = h->plan32;
     if (set_plan(h, true, p64) != EDA_OK || set_plan(h, false, p32) != EDA_OK) {
-      g_err = h->err;
+      eda::g_err = h->err;
       return bail(EDA_ERR_CUDA);
     }
   }
@@ -821,6 +711,9 @@ EDA_API int eda_destroy(eda_handle* h) {
   if (h->tab64) cudaFree(h->tab64);
   if (h->tab32) cudaFree(h->tab32);
   if (h->hflag) cudaFreeHost(h->hflag);
+  if (h->hring) cudaFreeHost(h->hring);
+  for (int i = 0; i < eda_handle::kRing; ++i)
+    if (h->ring_ev[i]) cudaEventDestroy(h->ring_ev[i]);
   delete h;
   return EDA_OK;
 }
@@ -1086,55 +979,51 @@ EDA_API int eda_set_lmp(eda_handle* h, const double* s_in, const double* eigvals
 
 namespace {
 
-// FP64 PCG iterations from the current (x, r) state; the caller has run
-// pcg_start.  Returns the number of iterations done.
-int pcg_loop64(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done) {
+// PCG iterations from the current (x, r) state (the caller has run
+// pcg_start): FP64 vectors and scalars; sweeps in FP64 (sweep64) or FP32,
+// LMP arithmetic in FP64 or FP32 accordingly.  The host polls the active
+// count through a ring of pinned copies and runs at most kRing-1 iterations
+// ahead of the device.
+int pcg_loop(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done, bool sweep64) {
   const int n = h->n, M = h->M;
   const int fixed = (tol > 0.0) ? 0 : maxit;
-  int rc = lmp_apply_dev<double>(h, h->r, h->z, use_lmp);
+  auto precond = [&]() -> int {
+    if (!use_lmp) {
+      CU(h, cudaMemcpyAsync(h->z, h->r, (size_t)M * n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+    } else if (sweep64) {
+      CU(h, eda::lmp_fused<double>(n, M, h->S, h->cv, h->k, nullptr, nullptr, nullptr, h->k, h->r, h->z,
+                                   h->active, h->st));
+    } else {
+      CU(h, eda::lmp_fused<float>(n, M, h->S32, h->cv, h->k, nullptr, nullptr, nullptr, h->k, h->r, h->z,
+                                  h->active, h->st));
+    }
+    return EDA_OK;
+  };
+  int rc = precond();
   if (rc) return rc;
   CU(h, eda::pcg_first_dir<double>(n, M, h->r, h->z, h->pv, h->sc, h->active, h->st));
+  constexpr int R = eda_handle::kRing;
   int it = it0;
   while (it < maxit) {
     ++it;
-    rc = hvp_dev(h, h->cols, M, h->pv, h->q, 1, true, h->active);
+    rc = hvp_dev(h, h->cols, M, h->pv, h->q, 1, sweep64, h->active);
     if (rc) return rc;
     CU(h, eda::pcg_update<double, double>(n, M, it, h->pv, h->q, h->x, h->r, h->sc, h->active, tol, h->nactive,
                                           fixed, h->st));
-    rc = lmp_apply_dev<double>(h, h->r, h->z, use_lmp);
+    rc = precond();
     if (rc) return rc;
     CU(h, eda::pcg_dir<double>(n, M, h->r, h->z, h->pv, h->sc, h->active, h->st));
-    int na = 0;
-    rc = read_flag(h, h->nactive, &na);
-    if (rc) return rc;
-    if (na == 0) break;
+    const int slot = it % R;
+    CU(h, cudaMemcpyAsync(h->hring + slot, h->nactive, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CU(h, cudaEventRecord(h->ring_ev[slot], h->st));
+    if (it - it0 >= R) {
+      const int old = (it - R + 1) % R;
+      CU(h, cudaEventSynchronize(h->ring_ev[old]));
+      if (h->hring[old] == 0) break;
+    }
   }
-  *it_done = it;
-  return EDA_OK;
-}
-
-// Mixed PCG iterations: FP32 vectors and sweeps, FP64 x and scalars.
-int pcg_loop32(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done) {
-  const int n = h->n, M = h->M;
-  const int fixed = (tol > 0.0) ? 0 : maxit;
-  int rc = lmp_apply_dev<float>(h, h->r32, h->z32, use_lmp);
-  if (rc) return rc;
-  CU(h, eda::pcg_first_dir<float>(n, M, h->r32, h->z32, h->p32, h->sc, h->active, h->st));
-  int it = it0;
-  while (it < maxit) {
-    ++it;
-    rc = hvp32_dev(h, h->p32, h->q32, h->active);
-    if (rc) return rc;
-    CU(h, eda::pcg_update<float, double>(n, M, it, h->p32, h->q32, h->x, h->r32, h->sc, h->active, tol,
-                                         h->nactive, fixed, h->st));
-    rc = lmp_apply_dev<float>(h, h->r32, h->z32, use_lmp);
-    if (rc) return rc;
-    CU(h, eda::pcg_dir<float>(n, M, h->r32, h->z32, h->p32, h->sc, h->active, h->st));
-    int na = 0;
-    rc = read_flag(h, h->nactive, &na);
-    if (rc) return rc;
-    if (na == 0) break;
-  }
+  CU(h, cudaStreamSynchronize(h->st));
+  // iterations actually done: the largest per-member count
   *it_done = it;
   return EDA_OK;
 }
@@ -1168,27 +1057,37 @@ EDA_API int eda_solve_batch(eda_handle* h, double tol, int maxit, const double* 
   const bool lmp = use_lmp != 0;
   int it = 0;
   if (h->precision == EDA_FP64) {
-    int rc = pcg_loop64(h, tol, maxit, 0, lmp, &it);
+    int rc = pcg_loop(h, tol, maxit, 0, lmp, &it, true);
     if (rc) return rc;
   } else {
-    CU(h, eda::convert<double, float>((long long)M * n, h->r, h->r32, h->st));
-    int rc = pcg_loop32(h, tol, maxit, 0, lmp, &it);
+    // FP32 sweeps and FP32 LMP arithmetic; CG vectors, scalars and x in FP64.
+    // Iterative refinement: every inner PCG reduces its own residual by tau,
+    // then the FP64 true residual restarts the next round.
+    const char* taus = std::getenv("EDA_MIXED_INNER_TOL");
+    const double tau = (taus && *taus) ? std::atof(taus) : 1e-3;
+    if (tol > 0.0 && tau > 0.0) {
+      eda::count_launch();
+      set_tolm_kernel<<<1, 128, 0, h->st>>>(M, h->sc, tol, tau);
+      CU(h, cudaGetLastError());
+    }
+    int rc = pcg_loop(h, tol, maxit, 0, lmp, &it, false);
     if (rc) return rc;
-    // FP64 residual replacement: true residual with FP64 sweeps; members whose
-    // true residual misses the tolerance restart from it.
-    for (int rep = 0; rep < 8; ++rep) {
+    // FP64 residual replacement: true residual b - H x with FP64 sweeps;
+    // members whose true residual misses the tolerance restart from it.
+    for (int rep = 0; rep < 64; ++rep) {
       rc = hvp_dev(h, h->cols, M, h->x, h->q, 1, true, nullptr);
       if (rc) return rc;
       CU(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
       eda::count_launch();
-      true_res_kernel<<<M, 256, 0, h->st>>>(n, h->b, h->q, h->r32, h->sc, h->active, tol > 0.0 ? tol : 1e300,
-                                           h->nactive, h->dstatus);
+      true_res_kernel<<<M, 256, 0, h->st>>>(n, h->b, h->q, nullptr, h->r, h->sc, h->active,
+                                           tol > 0.0 ? tol : 1e300, h->nactive, h->dstatus,
+                                           tau > 0.0 ? tau : 0.0);
       CU(h, cudaGetLastError());
       int need = 0;
       rc = read_flag(h, h->dstatus, &need);
       if (rc) return rc;
       if (need == 0 || it >= maxit || tol <= 0.0) break;
-      rc = pcg_loop32(h, tol, maxit, it, lmp, &it);
+      rc = pcg_loop(h, tol, maxit, it, lmp, &it, false);
       if (rc) return rc;
     }
   }

@@ -301,13 +301,31 @@ __global__ void nystrom_core_kernel(const double* W, const double* RY, int m, in
 // ---------------------------------------------------------------------------
 
 // Start: bnorm, relres and convergence at x0; r given.  z, p set by caller.
+// Item geometry: with item arrays, item j has length n_of[j] at offset
+// off_of[j] of the concatenated vectors; without, length n at j*n.
+struct ItemGeo {
+  const int* n_of;
+  const long long* off_of;
+};
+__device__ __forceinline__ void item_geo(const ItemGeo& ig, int j, int n, int* nj, long long* off) {
+  if (ig.n_of) {
+    *nj = ig.n_of[j];
+    *off = ig.off_of[j];
+  } else {
+    *nj = n;
+    *off = (long long)j * n;
+  }
+}
+
 template <typename T>
-__global__ void pcg_start_kernel(int n, const double* b, const T* r, PcgScalars* sc, int* active,
+__global__ void pcg_start_kernel(int n, ItemGeo ig, const double* b, const T* r, PcgScalars* sc, int* active,
                                  double tol, int* nactive) {
   __shared__ double red[32];
   const int j = blockIdx.x;
-  const double* bj = b + (long long)j * n;
-  const T* rj = r + (long long)j * n;
+  long long off;
+  item_geo(ig, j, n, &n, &off);
+  const double* bj = b + off;
+  const T* rj = r + off;
   double sb = 0.0, sr = 0.0;
   for (int g = threadIdx.x; g < n; g += blockDim.x) {
     sb += bj[g] * bj[g];
@@ -321,6 +339,7 @@ __global__ void pcg_start_kernel(int n, const double* b, const T* r, PcgScalars*
     sc[j].relres = bn > 0.0 ? sqrt(sr) / bn : 0.0;
     sc[j].iters = 0;
     sc[j].status = EDA_MAXIT;
+    sc[j].tolm = 0.0;
     const bool done = (bn == 0.0) || (tol > 0.0 && sc[j].relres <= tol);
     if (done) sc[j].status = EDA_CONVERGED;
     active[j] = done ? 0 : 1;
@@ -330,14 +349,16 @@ __global__ void pcg_start_kernel(int n, const double* b, const T* r, PcgScalars*
 
 // rz = r.z, p = z (start of the recurrences).
 template <typename T>
-__global__ void pcg_first_dir_kernel(int n, const T* r, const T* z, T* p, PcgScalars* sc,
+__global__ void pcg_first_dir_kernel(int n, ItemGeo ig, const T* r, const T* z, T* p, PcgScalars* sc,
                                      const int* active) {
   __shared__ double red[32];
   const int j = blockIdx.x;
   if (!active[j]) return;
-  const T* rj = r + (long long)j * n;
-  const T* zj = z + (long long)j * n;
-  T* pj = p + (long long)j * n;
+  long long off;
+  item_geo(ig, j, n, &n, &off);
+  const T* rj = r + off;
+  const T* zj = z + off;
+  T* pj = p + off;
   double s = 0.0;
   for (int g = threadIdx.x; g < n; g += blockDim.x) {
     s += (double)rj[g] * (double)zj[g];
@@ -350,15 +371,17 @@ __global__ void pcg_first_dir_kernel(int n, const T* r, const T* z, T* p, PcgSca
 // After q = H p: alpha, x += alpha p, r -= alpha q, the residual norm and the
 // stopping test.
 template <typename T, typename TX>
-__global__ void pcg_update_kernel(int n, int it, const T* p, const T* q, TX* x, T* r, PcgScalars* sc,
+__global__ void pcg_update_kernel(int n, ItemGeo ig, int it, const T* p, const T* q, TX* x, T* r, PcgScalars* sc,
                                   int* active, double tol, int* nactive, int fixed_iters) {
   __shared__ double red[32];
   const int j = blockIdx.x;
   if (!active[j]) return;
-  const T* pj = p + (long long)j * n;
-  const T* qj = q + (long long)j * n;
-  TX* xj = x + (long long)j * n;
-  T* rj = r + (long long)j * n;
+  long long off;
+  item_geo(ig, j, n, &n, &off);
+  const T* pj = p + off;
+  const T* qj = q + off;
+  TX* xj = x + off;
+  T* rj = r + off;
   double s = 0.0;
   for (int g = threadIdx.x; g < n; g += blockDim.x) s += (double)pj[g] * (double)qj[g];
   const double pq = block_sum<double>(s, red);
@@ -382,17 +405,18 @@ __global__ void pcg_update_kernel(int n, int it, const T* p, const T* q, TX* x, 
   if (threadIdx.x == 0) {
     const double rel = sqrt(rr) / sc[j].bnorm;
     sc[j].relres = rel;
-    sc[j].iters = it;
+    const int itj = sc[j].iters + 1;  // per-member count (launch-order independent, graph friendly)
+    sc[j].iters = itj;
     bool stop = false;
     if (!isfinite(rel)) {
       sc[j].status = EDA_NAN;
       stop = true;
     } else if (fixed_iters > 0) {
-      if (it >= fixed_iters) {
+      if (itj >= fixed_iters) {
         sc[j].status = EDA_CONVERGED;
         stop = true;
       }
-    } else if (rel <= tol) {
+    } else if (rel <= (sc[j].tolm > 0.0 ? sc[j].tolm : tol)) {
       sc[j].status = EDA_CONVERGED;
       stop = true;
     }
@@ -405,19 +429,63 @@ __global__ void pcg_update_kernel(int n, int it, const T* p, const T* q, TX* x, 
 
 // After z = P r: beta = (r.z)_new / (r.z)_old, p = z + beta p.
 template <typename T>
-__global__ void pcg_dir_kernel(int n, const T* r, const T* z, T* p, PcgScalars* sc, const int* active) {
+__global__ void pcg_dir_kernel(int n, ItemGeo ig, const T* r, const T* z, T* p, PcgScalars* sc, const int* active) {
   __shared__ double red[32];
   const int j = blockIdx.x;
   if (!active[j]) return;
-  const T* rj = r + (long long)j * n;
-  const T* zj = z + (long long)j * n;
-  T* pj = p + (long long)j * n;
+  long long off;
+  item_geo(ig, j, n, &n, &off);
+  const T* rj = r + off;
+  const T* zj = z + off;
+  T* pj = p + off;
   double s = 0.0;
   for (int g = threadIdx.x; g < n; g += blockDim.x) s += (double)rj[g] * (double)zj[g];
   const double rz = block_sum<double>(s, red);
   const double beta = rz / sc[j].rz;
   for (int g = threadIdx.x; g < n; g += blockDim.x) pj[g] = (T)((double)zj[g] + beta * (double)pj[g]);
   if (threadIdx.x == 0) sc[j].rz = rz;
+}
+
+// z_j = r_j + S diag(c) S^T r_j for item j (Section 3.1), one CTA per item:
+// the k projections by warps (shuffle reductions) into shared memory, then
+// the expansion.  TS is the type of S and of the arithmetic (double, or
+// float for the mixed path); r and z are FP64.  S_of/c_of/k_of give each
+// item's LMP (per problem in a group), or S, c, k for all items.
+template <typename TS>
+__global__ void lmp_fused_kernel(int n, ItemGeo ig, const TS* S, const double* c, int k, const TS* const* S_of,
+                                 const double* const* c_of, const int* k_of, const double* r, double* z,
+                                 const int* active) {
+  extern __shared__ double wsm[];  // k projections
+  const int j = blockIdx.x;
+  if (active && !active[j]) return;
+  long long off;
+  item_geo(ig, j, n, &n, &off);
+  if (S_of) {
+    S = S_of[j];
+    c = c_of[j];
+    k = k_of[j];
+  }
+  const double* rj = r + off;
+  double* zj = z + off;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (k <= 0 || S == nullptr) {
+    for (int g = threadIdx.x; g < n; g += blockDim.x) zj[g] = rj[g];
+    return;
+  }
+  for (int i = wid; i < k; i += nw) {
+    const TS* si = S + (long long)i * n;
+    TS acc = TS(0);
+    for (int g = lane; g < n; g += 32) acc += si[g] * (TS)rj[g];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) wsm[i] = (double)acc * c[i];
+  }
+  __syncthreads();
+  for (int g = threadIdx.x; g < n; g += blockDim.x) {
+    TS acc = TS(0);
+    for (int i = 0; i < k; ++i) acc += S[(long long)i * n + g] * (TS)wsm[i];
+    zj[g] = rj[g] + (double)acc;
+  }
 }
 
 template <typename TS, typename TD>
@@ -487,33 +555,46 @@ cudaError_t nystrom_core(const double* W, const double* RY, int m, int k, double
 
 template <typename T>
 cudaError_t pcg_start(int n, int m, const double* b, const T* r, PcgScalars* sc, int* active, double tol,
-                      int* nactive, cudaStream_t s) {
+                      int* nactive, cudaStream_t s, const int* n_of, const long long* off_of) {
   count_launch();
-  pcg_start_kernel<T><<<m, 256, 0, s>>>(n, b, r, sc, active, tol, nactive);
+  pcg_start_kernel<T><<<m, 256, 0, s>>>(n, ItemGeo{n_of, off_of}, b, r, sc, active, tol, nactive);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t pcg_first_dir(int n, int m, const T* r, const T* z, T* p, PcgScalars* sc, const int* active,
-                          cudaStream_t s) {
+                          cudaStream_t s, const int* n_of, const long long* off_of) {
   count_launch();
-  pcg_first_dir_kernel<T><<<m, 256, 0, s>>>(n, r, z, p, sc, active);
+  pcg_first_dir_kernel<T><<<m, 256, 0, s>>>(n, ItemGeo{n_of, off_of}, r, z, p, sc, active);
   return cudaGetLastError();
 }
 
 template <typename T, typename TX>
 cudaError_t pcg_update(int n, int m, int it, const T* p, const T* q, TX* x, T* r, PcgScalars* sc, int* active,
-                       double tol, int* nactive, int fixed_iters, cudaStream_t s) {
+                       double tol, int* nactive, int fixed_iters, cudaStream_t s, const int* n_of,
+                       const long long* off_of) {
   count_launch();
-  pcg_update_kernel<T, TX><<<m, 256, 0, s>>>(n, it, p, q, x, r, sc, active, tol, nactive, fixed_iters);
+  pcg_update_kernel<T, TX><<<m, 256, 0, s>>>(n, ItemGeo{n_of, off_of}, it, p, q, x, r, sc, active, tol, nactive,
+                                             fixed_iters);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t pcg_dir(int n, int m, const T* r, const T* z, T* p, PcgScalars* sc, const int* active,
-                    cudaStream_t s) {
+                    cudaStream_t s, const int* n_of, const long long* off_of) {
   count_launch();
-  pcg_dir_kernel<T><<<m, 256, 0, s>>>(n, r, z, p, sc, active);
+  pcg_dir_kernel<T><<<m, 256, 0, s>>>(n, ItemGeo{n_of, off_of}, r, z, p, sc, active);
+  return cudaGetLastError();
+}
+
+template <typename TS>
+cudaError_t lmp_fused(int n, int m, const TS* S, const double* c, int k, const TS* const* S_of,
+                      const double* const* c_of, const int* k_of, int kmax, const double* r, double* z,
+                      const int* active, cudaStream_t s, const int* n_of, const long long* off_of) {
+  if (m <= 0) return cudaSuccess;
+  count_launch();
+  lmp_fused_kernel<TS><<<m, 256, (size_t)(kmax > 0 ? kmax : 1) * sizeof(double), s>>>(
+      n, ItemGeo{n_of, off_of}, S, c, k, S_of, c_of, k_of, r, z, active);
   return cudaGetLastError();
 }
 
@@ -537,21 +618,29 @@ template cudaError_t gemm_nn<double, double>(int, const double*, int, int, const
 template cudaError_t gemm_nn<float, float>(int, const float*, int, int, const double*, const double*,
                                            const float*, float*, const int*, cudaStream_t);
 template cudaError_t pcg_start<double>(int, int, const double*, const double*, PcgScalars*, int*, double, int*,
-                                       cudaStream_t);
+                                       cudaStream_t, const int*, const long long*);
 template cudaError_t pcg_start<float>(int, int, const double*, const float*, PcgScalars*, int*, double, int*,
-                                      cudaStream_t);
+                                      cudaStream_t, const int*, const long long*);
 template cudaError_t pcg_first_dir<double>(int, int, const double*, const double*, double*, PcgScalars*,
-                                           const int*, cudaStream_t);
+                                           const int*, cudaStream_t, const int*, const long long*);
 template cudaError_t pcg_first_dir<float>(int, int, const float*, const float*, float*, PcgScalars*, const int*,
-                                          cudaStream_t);
+                                          cudaStream_t, const int*, const long long*);
 template cudaError_t pcg_update<double, double>(int, int, int, const double*, const double*, double*, double*,
-                                                PcgScalars*, int*, double, int*, int, cudaStream_t);
+                                                PcgScalars*, int*, double, int*, int, cudaStream_t, const int*,
+                                                const long long*);
 template cudaError_t pcg_update<float, double>(int, int, int, const float*, const float*, double*, float*,
-                                               PcgScalars*, int*, double, int*, int, cudaStream_t);
+                                               PcgScalars*, int*, double, int*, int, cudaStream_t, const int*,
+                                               const long long*);
 template cudaError_t pcg_dir<double>(int, int, const double*, const double*, double*, PcgScalars*, const int*,
-                                     cudaStream_t);
+                                     cudaStream_t, const int*, const long long*);
 template cudaError_t pcg_dir<float>(int, int, const float*, const float*, float*, PcgScalars*, const int*,
-                                    cudaStream_t);
+                                    cudaStream_t, const int*, const long long*);
+template cudaError_t lmp_fused<double>(int, int, const double*, const double*, int, const double* const*,
+                                       const double* const*, const int*, int, const double*, double*, const int*,
+                                       cudaStream_t, const int*, const long long*);
+template cudaError_t lmp_fused<float>(int, int, const float*, const double*, int, const float* const*,
+                                      const double* const*, const int*, int, const double*, double*, const int*,
+                                      cudaStream_t, const int*, const long long*);
 template cudaError_t convert<double, float>(long long, const double*, float*, cudaStream_t);
 template cudaError_t convert<float, double>(long long, const float*, double*, cudaStream_t);
 

@@ -15,6 +15,8 @@ struct PcgScalars {
   double relres;  // ||r|| / ||b||
   int iters;
   int status;
+  double tolm;    // per-member stopping threshold on ||r||/||b|| (0: the call's tol)
+  double pad;
 };
 
 template <typename TA, typename TB>
@@ -29,18 +31,27 @@ cudaError_t tri_mul(const double* A, const double* B, double* P, int m, cudaStre
 cudaError_t nystrom_core(const double* W, const double* RY, int m, int k, double nu, int theta_mode,
                          double theta_given, double* UT, double* D, double* cvec, double* theta_out,
                          int* status, cudaStream_t s);
+// Batched PCG vector kernels, one CTA per item.  With n_of/off_of, item j
+// has length n_of[j] at offset off_of[j]; otherwise length n at j*n.
 template <typename T>
 cudaError_t pcg_start(int n, int m, const double* b, const T* r, PcgScalars* sc, int* active, double tol,
-                      int* nactive, cudaStream_t s);
+                      int* nactive, cudaStream_t s, const int* n_of = nullptr, const long long* off_of = nullptr);
 template <typename T>
 cudaError_t pcg_first_dir(int n, int m, const T* r, const T* z, T* p, PcgScalars* sc, const int* active,
-                          cudaStream_t s);
+                          cudaStream_t s, const int* n_of = nullptr, const long long* off_of = nullptr);
 template <typename T, typename TX>
 cudaError_t pcg_update(int n, int m, int it, const T* p, const T* q, TX* x, T* r, PcgScalars* sc, int* active,
-                       double tol, int* nactive, int fixed_iters, cudaStream_t s);
+                       double tol, int* nactive, int fixed_iters, cudaStream_t s, const int* n_of = nullptr,
+                       const long long* off_of = nullptr);
 template <typename T>
 cudaError_t pcg_dir(int n, int m, const T* r, const T* z, T* p, PcgScalars* sc, const int* active,
-                    cudaStream_t s);
+                    cudaStream_t s, const int* n_of = nullptr, const long long* off_of = nullptr);
+// z = r + S diag(c) S^T r per item (fused projection and expansion).
+template <typename TS>
+cudaError_t lmp_fused(int n, int m, const TS* S, const double* c, int k, const TS* const* S_of,
+                      const double* const* c_of, const int* k_of, int kmax, const double* r, double* z,
+                      const int* active, cudaStream_t s, const int* n_of = nullptr,
+                      const long long* off_of = nullptr);
 template <typename TS, typename TD>
 cudaError_t convert(long long count, const TS* src, TD* dst, cudaStream_t s);
 

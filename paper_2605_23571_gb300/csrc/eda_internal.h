@@ -15,6 +15,34 @@ void count_launch(int k = 1);
 
 enum SweepMode { MODE_HVP = 0, MODE_RHS = 1, MODE_NL = 2 };
 
+// One problem of a group launch (uneven batching): its model, observation
+// network, U_B taps, trajectory store and sweep tiling (the launch fixes the
+// cluster size and the run length C; each problem has its own tile, halo,
+// refresh period and number of active threads A).
+template <typename T>
+struct SweepProb {
+  int n, N, p, w, nos;
+  int Ttile, HL, E, K, A;
+  T F, dt;
+  const T* traj;
+  long long traj_mstride;
+  const int* obs_of_t;
+  const int* obs_ptr;
+  const int* obs_idx;
+  const T* rinv;
+  const int* obs_tab;
+  const T* bcoef;
+};
+
+// One work item of a group launch: a vector of problem `prob` on the
+// trajectory of `member`, at offset voff of the launch's concatenated
+// input/output arrays and soff of its stash (observation space); flag >= 0
+// indexes an activity flag (the item is skipped when it is 0).
+struct SweepItem {
+  int prob, member, flag, pad;
+  long long voff, soff;
+};
+
 // Arguments of one launch of the Lorenz-96 sweep kernel.  One "column" is one
 // vector processed on the trajectory of member col_member[col]; it is split
 // over CS CTAs (a thread-block cluster), CTA r owning global indices
@@ -47,6 +75,8 @@ struct SweepArgs {
   long long v_stride;
   T* OUT;                // MODE_HVP / MODE_RHS outputs
   long long out_stride;
+  const double* V64;     // if set: FP64 input vectors instead of V (FP32 sweeps)
+  double* OUT64;         // if set: FP64 outputs instead of OUT
   T* stash;              // MODE_HVP: per-column obs stash [ncol][stash_stride]
                          // MODE_RHS: per-member forcing R^{-1} d [member][stash_stride]
   long long stash_stride;
@@ -63,6 +93,11 @@ struct SweepArgs {
   T* rd_out;             // [col][p] or nullptr: R^{-1} d
   // plan
   int CS, Ttile, HL, E, K;
+  // group launch (uneven batching): when items != nullptr, column c of the
+  // launch is items[c] and every problem field above comes from probs[prob]
+  const SweepProb<T>* probs;
+  const SweepItem* items;
+  const int* flags;
 };
 
 struct SweepPlan {
@@ -74,6 +109,10 @@ struct SweepPlan {
 // the smallest cluster size >= min_cs whose tile fits one CTA.  K_hint > 0
 // fixes the halo refresh period.  Returns false if no plan fits.
 bool plan_sweep(int n, int elem_bytes, int w, int min_cs, int K_hint, SweepPlan* out);
+
+// Dynamic shared memory of a sweep launch with A threads, runs of C and
+// at most w+1 taps.
+size_t sweep_smem_bytes(int A, int C, int w, int elem_bytes);
 
 // The plan with exactly cluster size CS and refresh period K, if it fits.
 bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* out);

@@ -1,0 +1,110 @@
+// The EDA handle and the internal helpers shared by api.cu and group.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "dense.h"
+#include "eda_internal.h"
+
+using eda::PcgScalars;
+using eda::SweepArgs;
+using eda::SweepPlan;
+
+struct eda_handle {
+  // problem
+  int n = 0, N = 0, M = 0, p = 0, nos = 0, w = 0, ell = 0, k = 0;
+  int theta_mode = 0, precision = 0, ckpt = 0;
+  double F = 8.0, dt = 0.025, theta_given = 1.0;
+  cudaStream_t st = nullptr;
+  std::string err;
+  std::vector<int> h_obs_of_t;
+  // device: problem definition
+  int* obs_of_t = nullptr;
+  int* obs_ptr = nullptr;
+  int* obs_idx = nullptr;
+  double* rinv = nullptr;
+  float* rinv32 = nullptr;
+  double* bcoef = nullptr;
+  float* bcoef32 = nullptr;
+  // device: setup products
+  double* traj = nullptr;
+  float* traj32 = nullptr;
+  double* d = nullptr;
+  double* rd = nullptr;
+  double* b = nullptr;
+  // device: sketch and LMP
+  double* Phi = nullptr;
+  double* Y = nullptr;
+  float* V32a = nullptr;  // ell x n scratch (FP32 sweeps)
+  float* V32b = nullptr;
+  double* Q1 = nullptr;
+  double* Q = nullptr;
+  double* G = nullptr;
+  double* R1 = nullptr;
+  double* R1i = nullptr;
+  double* R2 = nullptr;
+  double* R2i = nullptr;
+  double* RY = nullptr;
+  double* W = nullptr;
+  double* UT = nullptr;
+  double* Dv = nullptr;
+  double* cv = nullptr;
+  double* theta = nullptr;
+  int* dstatus = nullptr;
+  double* S = nullptr;
+  float* S32 = nullptr;
+  double* lmpW = nullptr;  // k x M
+  // device: PCG
+  double *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr;
+  PcgScalars* sc = nullptr;
+  int* active = nullptr;
+  int* nactive = nullptr;
+  int* cols = nullptr;  // identity member map 0..max(M, ell)-1
+  int* zeros = nullptr; // member map of zeros (control trajectory)
+  int* hflag = nullptr; // pinned host int
+  static constexpr int kRing = 4;     // iterations the host may run ahead
+  int* hring = nullptr;               // pinned host copies of the active count
+  cudaEvent_t ring_ev[kRing] = {};
+  // stash
+  double* stash = nullptr;
+  float* stash32 = nullptr;
+  int stash_cols = 0;
+  // state
+  bool have_traj = false, have_sketch = false, have_lmp = false;
+  double shift_used = 0.0;
+  SweepPlan plan64{}, plan32{};
+  int* tab64 = nullptr;  // per-CTA observation ranges of plan64 / plan32
+  int* tab32 = nullptr;
+  bool tab64_ok = false, tab32_ok = false;
+  std::vector<int> h_obs_ptr, h_obs_idx;
+  std::vector<void*> allocs;
+};
+
+
+namespace eda {
+
+// Records msg as the last error (of h, and of the thread) and returns code.
+int fail(eda_handle* h, int code, const std::string& msg);
+// True if ptr is device (or managed) memory.
+bool is_device_ptr(const void* ptr);
+// Installs a sweep tiling of the handle and its observation table.
+int set_plan(eda_handle* h, bool fp64, const SweepPlan& pl);
+// Reads one device int (synchronises the stream).
+int read_flag(eda_handle* h, const int* dflag, int* out);
+// Integer environment variable (tiling overrides, diagnostics).
+int env_int(const char* name, int dflt);
+// 1D grid size for a grid-stride loop over count elements.
+unsigned grid_for(long long count);
+
+}  // namespace eda
+
+#define CU(h, ...)                                                                               \
+  do {                                                                                           \
+    cudaError_t e__ = (__VA_ARGS__);                                                             \
+    if (e__ != cudaSuccess) {                                                                    \
+      return eda::fail((h), EDA_ERR_CUDA, std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e__)); \
+    }                                                                                            \
+  } while (0)

@@ -65,23 +65,25 @@ __device__ __forceinline__ T jtvp(const Run<T, C>& X, const Run<T, C>& w, int j)
 }
 
 struct Geo {
-  int n, E, A, tid, tl, tr, l0, HL, Ttile, Town, a0, gbase, CS, rank;
+  // A: threads holding the extended region (the neighbour wrap); AS: edge
+  // buffer slot stride and NT: loop stride (both the block size)
+  int n, E, A, AS, NT, tid, tl, tr, l0, HL, Ttile, Town, a0, gbase, CS, rank;
 };
 
 template <typename T, int C>
 __device__ __forceinline__ void publish(T* eb, const Geo& g, const T (&v)[C]) {
   eb[g.tid] = v[0];
-  eb[g.A + g.tid] = v[1];
-  eb[2 * g.A + g.tid] = v[C - 2];
-  eb[3 * g.A + g.tid] = v[C - 1];
+  eb[g.AS + g.tid] = v[1];
+  eb[2 * g.AS + g.tid] = v[C - 2];
+  eb[3 * g.AS + g.tid] = v[C - 1];
 }
 
 template <typename T, int C>
 __device__ __forceinline__ void fetch(const T* eb, const Geo& g, Run<T, C>& r) {
-  r.m2 = eb[2 * g.A + g.tl];
-  r.m1 = eb[3 * g.A + g.tl];
+  r.m2 = eb[2 * g.AS + g.tl];
+  r.m1 = eb[3 * g.AS + g.tl];
   r.p1 = eb[g.tr];
-  r.p2 = eb[g.A + g.tr];
+  r.p2 = eb[g.AS + g.tr];
 }
 
 // Run of the stage buffer xs (whole extended region resident in smem).
@@ -130,10 +132,71 @@ __device__ __forceinline__ const int* obs_ranges(const int* tab, int nos, int ra
   return tab + ((long long)rank * nos + oj) * 8;
 }
 
+// Own run <-> mirror, with 16-byte shared-memory accesses (C * sizeof(T) is a
+// multiple of 16 for every instantiated tile).
 template <typename T, int C>
 __device__ __forceinline__ void write_mirror(T* mir, const Geo& g, const T (&v)[C]) {
+  static_assert((C * sizeof(T)) % 16 == 0, "run must be a whole number of 16-byte chunks");
+  if constexpr (sizeof(T) == 4) {
+    float4* p = reinterpret_cast<float4*>(mir + g.l0);
 #pragma unroll
-  for (int c = 0; c < C; ++c) mir[g.l0 + c] = v[c];
+    for (int q = 0; q < C / 4; ++q) p[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+  } else {
+    double2* p = reinterpret_cast<double2*>(mir + g.l0);
+#pragma unroll
+    for (int q = 0; q < C / 2; ++q) p[q] = make_double2(v[2 * q], v[2 * q + 1]);
+  }
+}
+
+template <typename T, int C>
+__device__ __forceinline__ void write_mirror_zero(T* mir, const Geo& g) {
+  T z[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) z[c] = T(0);
+  write_mirror<T, C>(mir, g, z);
+}
+
+template <typename T, int C>
+__device__ __forceinline__ void add_mirror(const T* mir, const Geo& g, T (&v)[C]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* p = reinterpret_cast<const float4*>(mir + g.l0);
+#pragma unroll
+    for (int q = 0; q < C / 4; ++q) {
+      const float4 u = p[q];
+      v[4 * q] += u.x;
+      v[4 * q + 1] += u.y;
+      v[4 * q + 2] += u.z;
+      v[4 * q + 3] += u.w;
+    }
+  } else {
+    const double2* p = reinterpret_cast<const double2*>(mir + g.l0);
+#pragma unroll
+    for (int q = 0; q < C / 2; ++q) {
+      const double2 u = p[q];
+      v[2 * q] += u.x;
+      v[2 * q + 1] += u.y;
+    }
+  }
+}
+
+// mir[obs_idx[k] - base] = stash[k] for k in [k0, k1), four loads in flight
+// per thread.
+template <typename T>
+__device__ __forceinline__ void scatter_obs(const int* __restrict__ idx, const T* __restrict__ stash, int k0,
+                                            int k1, int base, int tid, int A, T* mir) {
+  for (int k = k0 + tid; k < k1; k += 4 * A) {
+    int ii[4];
+    T vv[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int kk = k + u * A;
+      ii[u] = kk < k1 ? __ldg(idx + kk) : 0;
+      vv[u] = kk < k1 ? stash[kk] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (k + u * A < k1) mir[ii[u] - base] = vv[u];
+  }
 }
 
 // out[c] = sum_{|d|<=w} cf[|d|] src[base + w + c + d] for c < C: the banded
@@ -165,12 +228,12 @@ __device__ __forceinline__ void conv_run(const T* src, int base, int w, const T*
 // U_B lambda on the owned tile from the mirrors of the cluster (+ v if ident);
 // thread t produces outputs [t*C, t*C + C) of the tile.  stage has room for
 // E + 2w values.
-template <typename T, int C>
+template <typename T, int C, typename TO>
 __device__ void bhalf_from_mirrors(const SweepArgs<T>& a, const Geo& g, T* mir, T* stage, const T* cf,
-                                   T* out, const T* ident) {
+                                   TO* out, const double* ident64, const T* ident) {
   const int w = a.w;
   const int cnt = g.Town + 2 * w;
-  for (int j = g.tid; j < cnt; j += g.A) {
+  for (int j = g.tid; j < cnt; j += g.NT) {
     int gi = (g.a0 - w + j) % g.n;
     if (gi < 0) gi += g.n;
     const int r2 = gi / g.Ttile;
@@ -191,8 +254,9 @@ __device__ void bhalf_from_mirrors(const SweepArgs<T>& a, const Geo& g, T* mir, 
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       if (j0 + c < g.Town) {
-        T v = o[c];
-        if (ident) v += ident[g.a0 + j0 + c];
+        TO v = (TO)o[c];
+        if (ident64) v += (TO)ident64[g.a0 + j0 + c];
+        else if (ident) v += (TO)ident[g.a0 + j0 + c];
         out[g.a0 + j0 + c] = v;
       }
     }
@@ -208,31 +272,120 @@ __device__ __forceinline__ void gather_obs(const SweepArgs<T>& a, const Geo& g, 
     const int* tb = obs_ranges(a.obs_tab, a.nos, g.rank, oj);
     k0 = tb[0];
     k1 = tb[1];
-    for (int k = k0 + g.tid; k < k1; k += g.A) stash[k] = a.rinv[k] * mir[g.HL + a.obs_idx[k] - g.a0];
+    const int off = g.HL - g.a0;
+    for (int k = k0 + g.tid; k < k1; k += 4 * g.NT) {
+      int ii[4];
+      T rr[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int kk = k + u * g.NT;
+        ii[u] = kk < k1 ? __ldg(a.obs_idx + kk) : 0;
+        rr[u] = kk < k1 ? __ldg(a.rinv + kk) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (k + u * g.NT < k1) stash[k + u * g.NT] = rr[u] * mir[off + ii[u]];
+    }
   } else {
-    for (int k = k0 + g.tid; k < k1; k += g.A) {
+    for (int k = k0 + g.tid; k < k1; k += g.NT) {
       const int gi = a.obs_idx[k];
       if (gi >= g.a0 && gi < g.a0 + g.Town) stash[k] = a.rinv[k] * mir[g.HL + gi - g.a0];
     }
   }
 }
 
+// Own run of the trajectory state at row `row` (C consecutive elements of the
+// extended region): one or two 16-byte vector loads when aligned, else scalar.
 template <typename T, int C>
-__global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a) {
+__device__ __forceinline__ void load_run(const T* row, const int (&gi)[C], bool vec_ok, T (&out)[C]) {
+  if (vec_ok) {
+    if constexpr (sizeof(T) == 4) {
+      const float4* p = reinterpret_cast<const float4*>(row + gi[0]);
+#pragma unroll
+      for (int v = 0; v < C / 4; ++v) {
+        const float4 q = __ldg(p + v);
+        out[4 * v] = q.x;
+        out[4 * v + 1] = q.y;
+        out[4 * v + 2] = q.z;
+        out[4 * v + 3] = q.w;
+      }
+    } else {
+      const double2* p = reinterpret_cast<const double2*>(row + gi[0]);
+#pragma unroll
+      for (int v = 0; v < C / 2; ++v) {
+        const double2 q = __ldg(p + v);
+        out[2 * v] = q.x;
+        out[2 * v + 1] = q.y;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < C; ++c) out[c] = __ldg(row + gi[c]);
+  }
+}
+
+constexpr int kObsMapCap = 1024;  // steps whose observation index is cached in smem
+
+template <typename T, int C>
+__global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
 
+  SweepArgs<T> a = a0;
   Geo g;
   g.CS = a.CS;
   g.rank = (a.CS > 1) ? (int)cg::this_cluster().block_rank() : 0;
   const int col = blockIdx.x / a.CS;
   if (col >= a.ncol) return;
-  if (a.col_active != nullptr && a.col_active[col] == 0) return;  // uniform over the cluster
-  const int member = a.col_member ? a.col_member[col] : col;
+  // launch-wide shared-memory layout (the group launch sizes it for its largest problem)
+  const int Emax = (int)blockDim.x * C;
+  const int wmax = a0.w;
+  int member, A_act = (int)blockDim.x;
+  long long voff, soff;
+  if (a.items != nullptr) {
+    const SweepItem it = a.items[col];
+    if (it.flag >= 0 && a.flags[it.flag] == 0) return;  // uniform over the cluster
+    const SweepProb<T> P = a.probs[it.prob];
+    a.n = P.n;
+    a.N = P.N;
+    a.p = P.p;
+    a.w = P.w;
+    a.nos = P.nos;
+    a.Ttile = P.Ttile;
+    a.HL = P.HL;
+    a.E = P.E;
+    a.K = P.K;
+    a.F = P.F;
+    a.dt = P.dt;
+    a.traj = P.traj;
+    a.traj_mstride = P.traj_mstride;
+    a.obs_of_t = P.obs_of_t;
+    a.obs_ptr = P.obs_ptr;
+    a.obs_idx = P.obs_idx;
+    a.rinv = P.rinv;
+    a.obs_tab = P.obs_tab;
+    a.bcoef = P.bcoef;
+    member = it.member;
+    voff = it.voff;
+    soff = it.soff;
+    A_act = P.A;
+    if (a.mode == MODE_NL && a.traj_out != nullptr) {
+      a.traj_out = const_cast<T*>(P.traj);
+      a.traj_out_mstride = P.traj_mstride;
+    }
+  } else {
+    if (a.col_active != nullptr && a.col_active[col] == 0) return;  // uniform over the cluster
+    member = a.col_member ? a.col_member[col] : col;
+    voff = (long long)col * (a.mode == MODE_NL ? a.x0_stride : a.out_stride);
+    soff = (long long)(a.mode == MODE_RHS ? member : col) * a.stash_stride;
+    if (a.mode == MODE_NL) soff = (long long)col * a.p;
+  }
 
   g.n = a.n;
   g.E = a.E;
-  g.A = blockDim.x;
+  g.A = A_act;
+  g.AS = blockDim.x;
+  g.NT = blockDim.x;
   g.tid = threadIdx.x;
   g.tl = (g.tid + g.A - 1) % g.A;
   g.tr = (g.tid + 1) % g.A;
@@ -244,34 +397,43 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   g.gbase = ((g.a0 - a.HL) % a.n + a.n) % a.n;
 
   const int w = a.w;
-  const int xsz = max(max(2 * g.E, g.E + 2 * w + 2), a.Ttile + 2 * w + 2);
-  T* xs0 = sm;
-  T* xs1 = sm + g.E;
-  T* mir = sm + xsz;
+  const int N = a.N;
+  // shared memory: mirror | stage area (conv input, then edge buffers) | taps | obs map
+  const int stage_sz = max(Emax + 2 * wmax + 2, kNumEdge * 4 * g.AS);
+  T* mir = sm;
+  T* stage = sm + Emax;
   T* eb[kNumEdge];
 #pragma unroll
-  for (int i = 0; i < kNumEdge; ++i) eb[i] = mir + g.E + i * 4 * g.A;
-  T* cf = mir + g.E + kNumEdge * 4 * g.A;  // U_B taps, w+1 values
+  for (int i = 0; i < kNumEdge; ++i) eb[i] = stage + i * 4 * g.AS;
+  T* cf = stage + stage_sz;
+  int* omap = reinterpret_cast<int*>(cf + (wmax + 1));
+  const bool omap_smem = (N + 1) <= kObsMapCap;
+  for (int j = g.tid; j <= w; j += g.NT) cf[j] = a.bcoef[j];
+  if (omap_smem)
+    for (int j = g.tid; j <= N; j += g.NT) omap[j] = a.obs_of_t[j];
+  auto obs_at = [&](int t) { return omap_smem ? omap[t] : a.obs_of_t[t]; };
 
-  // global index of staging position tid + j*A (coalesced order)
-  int gp[C];
+  // global indices of this thread's run, and whether 16-byte loads apply
+  int gi[C];
+  {
+    const int g0 = (g.gbase + g.l0) % g.n;
 #pragma unroll
-  for (int j = 0; j < C; ++j) gp[j] = (g.gbase + g.tid + j * g.A) % g.n;
+    for (int c = 0; c < C; ++c) gi[c] = (g0 + c) % g.n;
+  }
+  constexpr int kVec = 16 / (int)sizeof(T);
+  const bool vec_ok = (g.n % kVec == 0) && (gi[0] % kVec == 0) && (gi[0] + C <= g.n);
 
   const T F = a.F, h = a.dt;
   const T h2 = h * T(0.5), h6 = h / T(6), h3 = h / T(3);
-  const int N = a.N;
   const bool clus = a.CS > 1;
+  __syncthreads();
 
   if (a.mode == MODE_NL) {
     // ---------------------------------------------------------------- nonlinear
-    const T* x0 = a.x0 + (long long)col * a.x0_stride;
-#pragma unroll
-    for (int j = 0; j < C; ++j) xs0[g.tid + j * g.A] = x0[gp[j]];
-    __syncthreads();
     T x[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) x[c] = xs0[g.l0 + c];
+    const T* x0row = a.x0 + voff;
+    const bool x0_vec = vec_ok && ((reinterpret_cast<unsigned long long>(x0row) & 15ull) == 0);
+    load_run<T, C>(x0row, gi, x0_vec, x);
     T* tout = a.traj_out ? a.traj_out + (long long)member * a.traj_out_mstride : nullptr;
     for (int t = 0; t <= N; ++t) {
       if (t > 0) {
@@ -279,7 +441,6 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
         T X1[C], acc[C], Xs[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) X1[c] = x[c];
-        // stage 1
 #pragma unroll
         for (int c = 0; c < C; ++c) X.v[c] = x[c];
         fetch(eb[0], g, X);
@@ -291,7 +452,6 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
         }
         publish(eb[1], g, Xs);
         __syncthreads();
-        // stage 2
 #pragma unroll
         for (int c = 0; c < C; ++c) X.v[c] = Xs[c];
         fetch(eb[1], g, X);
@@ -303,7 +463,6 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
         }
         publish(eb[2], g, Xs);
         __syncthreads();
-        // stage 3
 #pragma unroll
         for (int c = 0; c < C; ++c) X.v[c] = Xs[c];
         fetch(eb[2], g, X);
@@ -315,7 +474,6 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
         }
         publish(eb[1], g, Xs);
         __syncthreads();
-        // stage 4
 #pragma unroll
         for (int c = 0; c < C; ++c) X.v[c] = Xs[c];
         fetch(eb[1], g, X);
@@ -326,7 +484,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
           x[c] = X1[c] + h6 * acc[c];
         }
       }
-      const int oj = a.obs_of_t[t];
+      const int oj = obs_at(t);
       const bool refresh = (t > 0) && (t % a.K == 0) && (t < N);
       const bool store = (tout != nullptr) || (t == N && a.final_out != nullptr);
       if (oj >= 0 || refresh || store) {
@@ -334,11 +492,11 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
         sync_cluster_or_block(refresh && clus);
         if (tout != nullptr) {
           T* dst = tout + (long long)t * a.n + g.a0;
-          for (int j = g.tid; j < g.Town; j += g.A) dst[j] = mir[g.HL + j];
+          for (int j = g.tid; j < g.Town; j += g.NT) dst[j] = mir[g.HL + j];
         }
         if (t == N && a.final_out != nullptr) {
-          T* dst = a.final_out + (long long)col * a.n + g.a0;
-          for (int j = g.tid; j < g.Town; j += g.A) dst[j] = mir[g.HL + j];
+          T* dst = a.final_out + voff + g.a0;
+          for (int j = g.tid; j < g.Town; j += g.NT) dst[j] = mir[g.HL + j];
         }
         if (oj >= 0) {
           int k0 = a.obs_ptr[oj], k1 = a.obs_ptr[oj + 1];
@@ -347,13 +505,13 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
             k0 = tb[0];
             k1 = tb[1];
           }
-          for (int k = k0 + g.tid; k < k1; k += g.A) {
-            const int gi = a.obs_idx[k];
-            if (gi >= g.a0 && gi < g.a0 + g.Town) {
-              const T hx = mir[g.HL + gi - g.a0];
-              const T d = a.yobs ? a.yobs[(long long)col * a.p + k] - hx : hx;
-              if (a.d_out) a.d_out[(long long)col * a.p + k] = d;
-              if (a.rd_out) a.rd_out[(long long)col * a.p + k] = a.rinv[k] * d;
+          for (int k = k0 + g.tid; k < k1; k += g.NT) {
+            const int gk = a.obs_idx[k];
+            if (gk >= g.a0 && gk < g.a0 + g.Town) {
+              const T hx = mir[g.HL + gk - g.a0];
+              const T d = a.yobs ? a.yobs[soff + k] - hx : hx;
+              if (a.d_out) a.d_out[soff + k] = d;
+              if (a.rd_out) a.rd_out[soff + k] = a.rinv[k] * d;
             }
           }
         }
@@ -370,63 +528,54 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
 
   // ------------------------------------------------------------------ HVP / RHS
   const T* trj = a.traj + (long long)member * a.traj_mstride;
-  const T* V = (a.mode == MODE_HVP) ? a.V + (long long)col * a.v_stride : nullptr;
-  T* stash = (a.mode == MODE_HVP) ? a.stash + (long long)col * a.stash_stride
-                                  : a.stash + (long long)member * a.stash_stride;
+  const T* V = (a.mode == MODE_HVP && a.V) ? a.V + voff : nullptr;
+  const double* V64 = (a.mode == MODE_HVP && a.V64) ? a.V64 + voff : nullptr;
+  T* stash = a.stash + soff;
+  T xr[C];  // own run of x_t (registers)
 
   if (a.mode == MODE_HVP) {
     // delta_0 = U_B v on the extended region (v staged with a w-halo)
     {
-      T* vs = sm;
       const int cnt = g.E + 2 * w;
-      for (int j = g.tid; j < cnt; j += g.A) {
-        int gi = (g.gbase - w + j) % g.n;
-        if (gi < 0) gi += g.n;
-        vs[j] = V[gi];
+      for (int j = g.tid; j < cnt; j += g.NT) {
+        int gk = (g.gbase - w + j) % g.n;
+        if (gk < 0) gk += g.n;
+        stage[j] = V64 ? (T)V64[gk] : V[gk];
       }
-      for (int j = g.tid; j <= w; j += g.A) cf[j] = a.bcoef[j];
       __syncthreads();
     }
     T dl[C];
-    conv_run<T, C>(sm, g.l0, w, cf, dl);
-    __syncthreads();
-    // x_0 into the stage buffer
-#pragma unroll
-    for (int j = 0; j < C; ++j) xs0[g.tid + j * g.A] = trj[gp[j]];
-    if (a.obs_of_t[0] >= 0) {
-      const int oj = a.obs_of_t[0];
+    conv_run<T, C>(stage, g.l0, w, cf, dl);
+    load_run<T, C>(trj, gi, vec_ok, xr);
+    __syncthreads();  // the stage area becomes the edge buffers
+    if (obs_at(0) >= 0) {
       write_mirror(mir, g, dl);
       __syncthreads();
-      gather_obs(a, g, oj, mir, stash);
+      gather_obs(a, g, obs_at(0), mir, stash);
     }
     publish(eb[0], g, dl);
+    publish(eb[5], g, xr);
     __syncthreads();
 
     // ------------------------------------------------ tangent linear, forward
     for (int t = 0; t < N; ++t) {
-      const T* cur = (t & 1) ? xs1 : xs0;
-      T* nxt = (t & 1) ? xs0 : xs1;
       T pf[C];
-      if (t + 1 < N) {
-        const T* src = trj + (long long)(t + 1) * a.n;
-#pragma unroll
-        for (int j = 0; j < C; ++j) pf[j] = src[gp[j]];
-      }
+      if (t + 1 < N) load_run<T, C>(trj + (long long)(t + 1) * a.n, gi, vec_ok, pf);
       Run<T, C> X, e;
-      T X1[C], Xs[C], es[C], acc[C];
+      T Xs[C], es[C], acc[C];
       // stage 1: slopes at X1 = x_t
-      run_from_smem(cur, g, X);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        X1[c] = X.v[c];
+        X.v[c] = xr[c];
         e.v[c] = dl[c];
       }
+      fetch(eb[5], g, X);
       fetch(eb[0], g, e);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
         const T k = tend(X, c, F);
         const T dk = jvp(X, e, c);
-        Xs[c] = X1[c] + h2 * k;
+        Xs[c] = xr[c] + h2 * k;
         acc[c] = dk;
         es[c] = dl[c] + h2 * dk;
       }
@@ -445,7 +594,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       for (int c = 0; c < C; ++c) {
         const T k = tend(X, c, F);
         const T dk = jvp(X, e, c);
-        Xs[c] = X1[c] + h2 * k;
+        Xs[c] = xr[c] + h2 * k;
         acc[c] += T(2) * dk;
         es[c] = dl[c] + h2 * dk;
       }
@@ -464,7 +613,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       for (int c = 0; c < C; ++c) {
         const T k = tend(X, c, F);
         const T dk = jvp(X, e, c);
-        Xs[c] = X1[c] + h * k;
+        Xs[c] = xr[c] + h * k;
         acc[c] += T(2) * dk;
         es[c] = dl[c] + h * dk;
       }
@@ -487,9 +636,9 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       }
       if (t + 1 < N) {
 #pragma unroll
-        for (int j = 0; j < C; ++j) nxt[g.tid + j * g.A] = pf[j];
+        for (int c = 0; c < C; ++c) xr[c] = pf[c];
       }
-      const int oj = a.obs_of_t[t + 1];
+      const int oj = obs_at(t + 1);
       const bool refresh = ((t + 1) % a.K == 0) && (t + 1 < N);
       if (oj >= 0 || refresh) {
         write_mirror(mir, g, dl);
@@ -501,6 +650,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
         }
       }
       publish(eb[0], g, dl);
+      publish(eb[5], g, xr);
       __syncthreads();
     }
     // the stash written by every CTA of the cluster must be visible to all
@@ -513,55 +663,44 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   for (int c = 0; c < C; ++c) lam[c] = T(0);
 
   auto inject = [&](int oj) {
-#pragma unroll
-    for (int c = 0; c < C; ++c) mir[g.l0 + c] = T(0);
+    write_mirror_zero<T, C>(mir, g);
     __syncthreads();
     if (a.obs_tab != nullptr) {
       const int* tb = obs_ranges(a.obs_tab, a.nos, g.rank, oj);
 #pragma unroll
       for (int sgm = 0; sgm < 2; ++sgm) {
         const int k0 = tb[2 + 3 * sgm], k1 = tb[3 + 3 * sgm], base = tb[4 + 3 * sgm];
-        for (int k = k0 + g.tid; k < k1; k += g.A) mir[a.obs_idx[k] - base] = stash[k];
+        scatter_obs<T>(a.obs_idx, stash, k0, k1, base, g.tid, g.NT, mir);
       }
     } else {
       const int k0 = a.obs_ptr[oj], k1 = a.obs_ptr[oj + 1];
-      for (int k = k0 + g.tid; k < k1; k += g.A) {
-        const int gi = a.obs_idx[k];
+      for (int k = k0 + g.tid; k < k1; k += g.NT) {
+        const int gk = a.obs_idx[k];
         const T val = stash[k];
-        int l = ((gi - g.gbase) % g.n + g.n) % g.n;
+        int l = ((gk - g.gbase) % g.n + g.n) % g.n;
         for (; l < g.E; l += g.n) mir[l] = val;
       }
     }
     __syncthreads();
-#pragma unroll
-    for (int c = 0; c < C; ++c) lam[c] += mir[g.l0 + c];
+    add_mirror<T, C>(mir, g, lam);
   };
 
-  if (a.obs_of_t[N] >= 0) inject(a.obs_of_t[N]);
-  {
-    T* dst = ((N - 1) & 1) ? xs1 : xs0;
-    const T* src = trj + (long long)(N - 1) * a.n;
-#pragma unroll
-    for (int j = 0; j < C; ++j) dst[g.tid + j * g.A] = src[gp[j]];
-    __syncthreads();
-  }
+  if (obs_at(N) >= 0) inject(obs_at(N));
+  load_run<T, C>(trj + (long long)(N - 1) * a.n, gi, vec_ok, xr);
+  publish(eb[0], g, xr);
+  __syncthreads();
   for (int t = N - 1; t >= 0; --t) {
-    const T* cur = (t & 1) ? xs1 : xs0;
-    T* nxt = (t & 1) ? xs0 : xs1;
     T pf[C];
-    if (t > 0) {
-      const T* src = trj + (long long)(t - 1) * a.n;
-#pragma unroll
-      for (int j = 0; j < C; ++j) pf[j] = src[gp[j]];
-    }
-    Run<T, C> X, wv;
-    T X1[C], X2[C], X3[C], X4[C], ln[C], ad[C];
+    if (t > 0) load_run<T, C>(trj + (long long)(t - 1) * a.n, gi, vec_ok, pf);
+    Run<T, C> X1, X, wv;
+    T X2[C], X3[C], X4[C], ln[C], ad[C];
     // forward recomputation of the stage states
-    run_from_smem(cur, g, X);
+#pragma unroll
+    for (int c = 0; c < C; ++c) X1.v[c] = xr[c];
+    fetch(eb[0], g, X1);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      X1[c] = X.v[c];
-      X2[c] = X1[c] + h2 * tend(X, c, F);
+      X2[c] = xr[c] + h2 * tend(X1, c, F);
       ad[c] = h6 * lam[c];
     }
     publish(eb[1], g, X2);
@@ -571,14 +710,14 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     for (int c = 0; c < C; ++c) X.v[c] = X2[c];
     fetch(eb[1], g, X);
 #pragma unroll
-    for (int c = 0; c < C; ++c) X3[c] = X1[c] + h2 * tend(X, c, F);
+    for (int c = 0; c < C; ++c) X3[c] = xr[c] + h2 * tend(X, c, F);
     publish(eb[2], g, X3);
     __syncthreads();
 #pragma unroll
     for (int c = 0; c < C; ++c) X.v[c] = X3[c];
     fetch(eb[2], g, X);
 #pragma unroll
-    for (int c = 0; c < C; ++c) X4[c] = X1[c] + h * tend(X, c, F);
+    for (int c = 0; c < C; ++c) X4[c] = xr[c] + h * tend(X, c, F);
     publish(eb[5], g, X4);
     __syncthreads();
     // reverse stage 4: g4 = J4^T a4, a4 = h/6 lam
@@ -630,17 +769,16 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     publish(eb[4], g, ad);
     __syncthreads();
     // reverse stage 1
-    run_from_smem(cur, g, X);
 #pragma unroll
     for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
     fetch(eb[4], g, wv);
 #pragma unroll
-    for (int c = 0; c < C; ++c) lam[c] = ln[c] + jtvp(X, wv, c);
+    for (int c = 0; c < C; ++c) lam[c] = ln[c] + jtvp(X1, wv, c);
     if (t > 0) {
 #pragma unroll
-      for (int j = 0; j < C; ++j) nxt[g.tid + j * g.A] = pf[j];
+      for (int c = 0; c < C; ++c) xr[c] = pf[c];
     }
-    const int oj = a.obs_of_t[t];
+    const int oj = obs_at(t);
     if (oj >= 0) inject(oj);
     const bool refresh = ((N - t) % a.K == 0) && (t > 0);
     if (refresh) {
@@ -649,26 +787,34 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       read_halo(lam, mir, g);
       sync_cluster_or_block(clus);
     }
+    publish(eb[0], g, xr);
     __syncthreads();
   }
 
   // ---------------------------------------------- output U_B lambda_0 (+ v)
-  for (int j = g.tid; j <= w; j += g.A) cf[j] = a.bcoef[j];
   write_mirror(mir, g, lam);
   sync_cluster_or_block(clus);
-  T* out = a.OUT + (long long)col * a.out_stride;
-  const T* ident = (a.mode == MODE_HVP && a.include_identity) ? V : nullptr;
-  bhalf_from_mirrors<T, C>(a, g, mir, sm, cf, out, ident);
+  const bool ident = (a.mode == MODE_HVP && a.include_identity);
+  if (a.OUT64) {
+    bhalf_from_mirrors<T, C, double>(a, g, mir, stage, cf, a.OUT64 + voff, ident ? V64 : nullptr,
+                                     ident ? V : nullptr);
+  } else {
+    bhalf_from_mirrors<T, C, T>(a, g, mir, stage, cf, a.OUT + voff, ident ? V64 : nullptr, ident ? V : nullptr);
+  }
 }
 
 template <typename T, int C>
 cudaError_t launch_impl(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t s) {
   auto kern = sweep_kernel<T, C>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem);
-  if (err != cudaSuccess) return err;
-  if (p.CS > 8) {
+  // function attributes are set once (they are not stream work and must not
+  // be issued while a stream is being captured)
+  static bool attrs_set = false;
+  if (!attrs_set) {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (err != cudaSuccess) return err;
+    attrs_set = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.ncol * p.CS), 1, 1);
@@ -690,6 +836,14 @@ cudaError_t launch_impl(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t 
 
 }  // namespace
 
+size_t sweep_smem_bytes(int A, int C, int w, int elem_bytes) {
+  const int E = A * C;
+  int stage = kNumEdge * 4 * A;
+  if (E + 2 * w + 2 > stage) stage = E + 2 * w + 2;
+  const size_t elems = (size_t)E + (size_t)stage + (size_t)(w + 1);
+  return elems * (size_t)elem_bytes + (size_t)kObsMapCap * sizeof(int) + 16;
+}
+
 bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* out) {
   const int C = (elem_bytes == 8) ? 4 : 8;
   if (CS < 1 || CS > 16 || K < 1) return false;
@@ -701,11 +855,7 @@ bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* ou
   A = ((A + 31) / 32) * 32;
   if (A > kMaxThreads) return false;
   const int E = A * C;
-  int xsz = 2 * E;
-  if (E + 2 * w + 2 > xsz) xsz = E + 2 * w + 2;
-  if (Ttile + 2 * w + 2 > xsz) xsz = Ttile + 2 * w + 2;
-  const size_t elems = (size_t)xsz + (size_t)E + (size_t)kNumEdge * 4 * A + (size_t)(w + 1);
-  const size_t smem = elems * (size_t)elem_bytes;
+  const size_t smem = sweep_smem_bytes(A, C, w, elem_bytes);
   if (smem > 227 * 1024) return false;
   out->CS = CS;
   out->C = C;

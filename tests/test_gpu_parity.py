@@ -126,14 +126,25 @@ def test_hvp_obs_at_window_ends():
         assert rowrel(HV, O.hvp(spec, traj, V, taps)).max() < 1e-11
 
 
+def oracle_self_sensitivity(spec, traj, b, taps, S_, c_, K, seed=0):
+    """How far the oracle's own K-iteration PCG iterate moves when b is
+    perturbed by 1e-16 relative: CG amplifies rounding on some members, and
+    two correct FP64 implementations cannot agree below this level."""
+    P_ = lambda R: O.lmp_apply(S_, c_, R)
+    a = O.pcg(lambda V: O.hvp(spec, traj, V, taps), b, P_, tol=0, maxit=K, fixed_iters=K)
+    bp = b * (1 + 1e-16 * np.random.default_rng(seed).standard_normal(b.shape))
+    c = O.pcg(lambda V: O.hvp(spec, traj, V, taps), bp, P_, tol=0, maxit=K, fixed_iters=K)
+    return rowrel(c["x"], a["x"])
+
+
 def test_sketch_lmp_and_solve_fp64_tiny():
     spec = S.spec_tiny(seed=4)
     taps, xb, y = problem(spec)
-    # equal iteration counts: the fewest iterations any member needs to reach
-    # 1e-6, so that no member is iterating on rounding noise
-    K = int(O.eda_pipeline(spec, xb, y, taps, tol=1e-6, maxit=100)["iters"].min())
-    ref = O.eda_pipeline(spec, xb, y, taps, tol=0, maxit=K, fixed_iters=K)
+    # equal iteration counts no larger than the fewest any member needs to
+    # reach 1e-6, so that no member is iterating on rounding noise
+    Kmin = int(O.eda_pipeline(spec, xb, y, taps, tol=1e-6, maxit=100)["iters"].min())
     with make(spec, taps) as h:
+        ref = O.eda_pipeline(spec, xb, y, taps, tol=0, maxit=Kmin, fixed_iters=Kmin)
         rhs = np.zeros_like(ref["b"])
         h.eda_set_trajectory(xb, y, rhs)
         Yg = np.zeros((spec.ell, spec.n))
@@ -147,18 +158,26 @@ def test_sketch_lmp_and_solve_fp64_tiny():
         Pg = (Sg.T * ref["c"]) @ Sg
         Po = (ref["S"] * ref["c"]) @ ref["S"].T
         assert np.linalg.norm(Pg - Po) <= 1e-8 * np.linalg.norm(Po)
-        dz = np.zeros_like(ref["b"])
-        it = np.zeros(spec.n_members, np.int32)
-        rr = np.zeros(spec.n_members)
-        st = np.zeros(spec.n_members, np.int32)
         # PCG parity with one preconditioner on both sides: the Nystrom
         # factors agree only to ~eps * cond(Phi^T A Phi) ~ 1e-8, and CG
         # amplifies preconditioner differences, so the oracle's LMP is loaded
         h.eda_set_lmp(np.ascontiguousarray(ref["S"].T), 1 + ref["D"])
-        h.eda_solve_batch(0.0, K, None, True, dz, it, rr, st)
-        assert (it == K).all()
-        assert rowrel(dz, ref["x"]).max() < 1e-10
-        np.testing.assert_allclose(rr, ref["relres"], rtol=1e-7)
+        for K in (8, Kmin):
+            refK = O.pcg(lambda V: O.hvp(spec, ref["traj"], V, taps), ref["b"],
+                         lambda R: O.lmp_apply(ref["S"], ref["c"], R), tol=0, maxit=K, fixed_iters=K)
+            sens = oracle_self_sensitivity(spec, ref["traj"], ref["b"], taps, ref["S"], ref["c"], K)
+            dz = np.zeros_like(ref["b"])
+            it = np.zeros(spec.n_members, np.int32)
+            rr = np.zeros(spec.n_members)
+            st = np.zeros(spec.n_members, np.int32)
+            h.eda_solve_batch(0.0, K, None, True, dz, it, rr, st)
+            assert (it == K).all()
+            err = rowrel(dz, refK["x"])
+            bound = np.maximum(1e-10, 100.0 * sens)
+            assert (err <= bound).all(), (K, err, sens)
+            assert (err[sens < 1e-12] < 1e-10).all()
+            calm = sens < 1e-12
+            np.testing.assert_allclose(rr[calm], refK["relres"][calm], rtol=1e-6)
 
 
 def test_solve_tolerance_stopped_fp64_tiny():
@@ -175,8 +194,17 @@ def test_solve_tolerance_stopped_fp64_tiny():
         st = np.zeros(spec.n_members, np.int32)
         h.eda_solve_batch(1e-6, 100, None, True, dz, it, rr, st)
         assert (st == P.EDA_CONVERGED).all()
-        assert np.abs(it - ref["iters"]).max() <= 1
         assert (rr <= 1e-6).all()
+        # stopping counts: +-1 of the oracle's, widened on members whose own
+        # count moves when b is perturbed by 1e-16 (CG rounding sensitivity)
+        lo, hi = ref["iters"].copy(), ref["iters"].copy()
+        traj = ref["traj"]
+        for sd in range(10):
+            bp = ref["b"] * (1 + 1e-16 * np.random.default_rng(sd).standard_normal(ref["b"].shape))
+            c2 = O.pcg(lambda V: O.hvp(spec, traj, V, taps), bp,
+                       lambda R: O.lmp_apply(ref["S"], ref["c"], R), tol=1e-6, maxit=100)["iters"]
+            lo, hi = np.minimum(lo, c2), np.maximum(hi, c2)
+        assert ((it >= lo - 1) & (it <= hi + 1)).all(), (it, lo, hi)
         # and with the LMP the library builds itself: converged, error bound
         h.eda_sketch()
         h.eda_build_lmp()
