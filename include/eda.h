@@ -287,6 +287,54 @@ EDA_API int eda_group_autotune(eda_group* g, double* best_ms_out);
 EDA_API int eda_group_solve(eda_group* g, double tol, int maxit, int use_lmp, double* const* dz_out,
                             int* iters_out, double* relres_out, int* status_out);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start (not in the paper): a periodic 1-D convolutional
+ * network mapping (member right-hand side b_j, control solution dz_0) to a
+ * guess of the member solution dz_j, used only as the initial iterate x0 of
+ * eda_solve_batch, which still runs to the same tolerance (so the plain
+ * solve remains the judge of the error).
+ *
+ * Network: channels 2 -> H -> H -> H -> 1, kernel 5 with periodic wrap (tap t
+ * reads position i + t - 2 mod n), GELU (erf form) after layers 1-3; inputs
+ * [b_j / s_b, dz_0 / s_z] with s_b, s_z the training-set RMS of b and dz_0;
+ * guess = dz_0 + s_z * out.  Parameters: FP32 masters, flat, per layer the
+ * weights [out][in][5] then the biases; every product uses the weights
+ * rounded to BF16, activations and accumulation are FP32.  Training: mean
+ * squared error of (guess - dz_j) / s_z, AdamW (beta 0.9/0.999, eps 1e-8,
+ * decoupled weight decay).  Samples are [count x n] FP64 arrays (host or
+ * device).  Calls on one network are not thread-safe.
+ * ---------------------------------------------------------------------- */
+typedef struct eda_ws eda_ws;
+
+/* n >= 5 periodic points, 1 <= hidden <= 64 channels, max_batch samples per
+ * forward/backward pass; parameters start at zero (set them before use). */
+EDA_API int eda_ws_create(int n, int hidden, int max_batch, void* stream, eda_ws** out);
+EDA_API int eda_ws_destroy(eda_ws* w);
+EDA_API const char* eda_ws_last_error(const eda_ws* w);
+/* Number of FP32 parameters (0 for NULL). */
+EDA_API long long eda_ws_num_params(const eda_ws* w);
+/* Loads / stores the flat FP32 parameters (host or device); loading resets
+ * the AdamW moments.  Together with the scales this is the saved model. */
+EDA_API int eda_ws_set_params(eda_ws* w, const float* params);
+EDA_API int eda_ws_get_params(eda_ws* w, float* params);
+/* Input scales s_b, s_z (> 0); eda_ws_train sets them from its data when
+ * they are unset. */
+EDA_API int eda_ws_set_scales(eda_ws* w, double s_b, double s_z);
+EDA_API int eda_ws_get_scales(const eda_ws* w, double* s_b, double* s_z);
+/* Mean loss over count <= max_batch samples and its gradient w.r.t. the
+ * parameters (grad_out [num_params] FP32, host or device, may be NULL);
+ * no update.  Requires the scales. */
+EDA_API int eda_ws_loss_grad(eda_ws* w, const double* rhs, const double* ctrl, const double* sol, int count,
+                             double* loss_out, float* grad_out);
+/* epochs passes of AdamW over count samples in batches of <= max_batch; order
+ * [epochs x count] sample permutation (host or device; NULL = sequential).
+ * loss_out [epochs] (host, may be NULL) = mean batch loss per epoch. */
+EDA_API int eda_ws_train(eda_ws* w, const double* rhs, const double* ctrl, const double* sol, int count,
+                         int epochs, int batch, double lr, double weight_decay, const int* order,
+                         double* loss_out);
+/* out [count x n] = the network's guesses of dz_j (host or device). */
+EDA_API int eda_ws_infer(eda_ws* w, const double* rhs, const double* ctrl, int count, double* out);
+
 /*
  * Host helper: taps of U_B for a Gaussian correlation
  * B = sigma_b^2 exp(-d^2 / (2 L^2)) on the circle of n points:

@@ -32,7 +32,10 @@ EXPORTS = ["eda_version", "eda_last_error", "eda_create", "eda_destroy", "eda_tw
            "eda_set_trajectory", "eda_sketch", "eda_build_lmp", "eda_set_lmp", "eda_solve_batch", "eda_hvp",
            "eda_bhalf_gaussian", "eda_kernel_launches", "eda_time_hvp_sweep", "eda_autotune",
            "eda_group_create", "eda_group_destroy", "eda_group_last_error", "eda_group_set_trajectories",
-           "eda_group_sketch", "eda_group_build_lmp", "eda_group_autotune", "eda_group_solve"]
+           "eda_group_sketch", "eda_group_build_lmp", "eda_group_autotune", "eda_group_solve",
+           "eda_ws_create", "eda_ws_destroy", "eda_ws_last_error", "eda_ws_num_params", "eda_ws_set_params",
+           "eda_ws_get_params", "eda_ws_set_scales", "eda_ws_get_scales", "eda_ws_loss_grad", "eda_ws_train",
+           "eda_ws_infer"]
 
 
 class EdaError(RuntimeError):
@@ -114,6 +117,28 @@ def lib() -> ctypes.CDLL:
     L.eda_group_autotune.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.eda_group_solve.restype = i
     L.eda_group_solve.argtypes = [vp, d, i, i, ctypes.POINTER(vp), vp, vp, vp]
+    L.eda_ws_create.restype = i
+    L.eda_ws_create.argtypes = [i, i, i, vp, ctypes.POINTER(vp)]
+    L.eda_ws_destroy.restype = i
+    L.eda_ws_destroy.argtypes = [vp]
+    L.eda_ws_last_error.restype = ctypes.c_char_p
+    L.eda_ws_last_error.argtypes = [vp]
+    L.eda_ws_num_params.restype = ctypes.c_longlong
+    L.eda_ws_num_params.argtypes = [vp]
+    L.eda_ws_set_params.restype = i
+    L.eda_ws_set_params.argtypes = [vp, vp]
+    L.eda_ws_get_params.restype = i
+    L.eda_ws_get_params.argtypes = [vp, vp]
+    L.eda_ws_set_scales.restype = i
+    L.eda_ws_set_scales.argtypes = [vp, d, d]
+    L.eda_ws_get_scales.restype = i
+    L.eda_ws_get_scales.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    L.eda_ws_loss_grad.restype = i
+    L.eda_ws_loss_grad.argtypes = [vp, vp, vp, vp, i, ctypes.POINTER(ctypes.c_double), vp]
+    L.eda_ws_train.restype = i
+    L.eda_ws_train.argtypes = [vp, vp, vp, vp, i, i, i, d, d, vp, vp]
+    L.eda_ws_infer.restype = i
+    L.eda_ws_infer.argtypes = [vp, vp, vp, i, vp]
     L.eda_bhalf_gaussian.restype = i
     L.eda_bhalf_gaussian.argtypes = [i, d, d, vp, i, ctypes.POINTER(ctypes.c_int)]
     _lib = L
@@ -121,6 +146,11 @@ def lib() -> ctypes.CDLL:
 
 
 def _ptr(a, dtype, count: Optional[int] = None, name: str = "array"):
+    """Address of a contiguous torch tensor or numpy array of the given dtype."""
+    return _ptr_impl(a, dtype, count, name)
+
+
+def _ptr_impl(a, dtype, count, name):
     """Address of a contiguous torch tensor or numpy array of the given dtype."""
     if a is None:
         return None
@@ -135,7 +165,7 @@ def _ptr(a, dtype, count: Optional[int] = None, name: str = "array"):
     except ImportError:  # pragma: no cover
         torch = None
     if torch is not None and isinstance(a, torch.Tensor):
-        tdt = {np.float64: torch.float64, np.int32: torch.int32}[np.dtype(dtype).type]
+        tdt = {np.float64: torch.float64, np.int32: torch.int32, np.float32: torch.float32}[np.dtype(dtype).type]
         if a.dtype != tdt or not a.is_contiguous():
             raise TypeError("%s must be a contiguous %s tensor" % (name, tdt))
         if count is not None and a.numel() < count:
@@ -355,3 +385,91 @@ class Group:
                                             _ptr(iters_out, np.int32, T, "iters_out"),
                                             _ptr(relres_out, np.float64, T, "relres_out"),
                                             _ptr(status_out, np.int32, T, "status_out")))
+
+
+class WarmStart:
+    """The learned warm-start network (wraps ``eda_ws``); methods carry the C
+    names of ``include/eda.h``."""
+
+    def __init__(self, n, hidden=64, max_batch=64, stream=None):
+        self._L = lib()
+        if stream is None:
+            try:
+                import torch
+                stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+            except ImportError:  # pragma: no cover
+                stream = 0
+        w = ctypes.c_void_p(None)
+        rc = self._L.eda_ws_create(int(n), int(hidden), int(max_batch), ctypes.c_void_p(int(stream)),
+                                   ctypes.byref(w))
+        if rc != EDA_OK:
+            raise EdaError(rc, self._L.eda_last_error(None).decode())
+        self._w = w
+        self.n, self.hidden, self.max_batch = int(n), int(hidden), int(max_batch)
+        self.num_params = int(self._L.eda_ws_num_params(w))
+
+    def _check(self, rc):
+        if rc != EDA_OK:
+            raise EdaError(rc, self._L.eda_ws_last_error(self._w).decode())
+
+    def close(self):
+        if getattr(self, "_w", None) is not None and self._w.value:
+            self._L.eda_ws_destroy(self._w)
+            self._w = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def eda_ws_set_params(self, params):
+        self._check(self._L.eda_ws_set_params(self._w, _ptr(params, np.float32, self.num_params, "params")))
+
+    def eda_ws_get_params(self):
+        out = np.zeros(self.num_params, dtype=np.float32)
+        self._check(self._L.eda_ws_get_params(self._w, out.ctypes.data))
+        return out
+
+    def eda_ws_set_scales(self, s_b, s_z):
+        self._check(self._L.eda_ws_set_scales(self._w, float(s_b), float(s_z)))
+
+    def eda_ws_get_scales(self):
+        a, b = ctypes.c_double(0), ctypes.c_double(0)
+        self._check(self._L.eda_ws_get_scales(self._w, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def eda_ws_loss_grad(self, rhs, ctrl, sol):
+        count = int(rhs.shape[0])
+        loss = ctypes.c_double(0.0)
+        grad = np.zeros(self.num_params, dtype=np.float32)
+        n = self.n
+        self._check(self._L.eda_ws_loss_grad(self._w, _ptr(rhs, np.float64, count * n, "rhs"),
+                                             _ptr(ctrl, np.float64, count * n, "ctrl"),
+                                             _ptr(sol, np.float64, count * n, "sol"), count,
+                                             ctypes.byref(loss), grad.ctypes.data))
+        return loss.value, grad
+
+    def eda_ws_train(self, rhs, ctrl, sol, epochs, batch, lr, weight_decay=0.0, order=None):
+        count = int(rhs.shape[0])
+        n = self.n
+        losses = np.zeros(max(epochs, 1))
+        self._check(self._L.eda_ws_train(self._w, _ptr(rhs, np.float64, count * n, "rhs"),
+                                         _ptr(ctrl, np.float64, count * n, "ctrl"),
+                                         _ptr(sol, np.float64, count * n, "sol"), count, int(epochs),
+                                         int(batch), float(lr), float(weight_decay),
+                                         _ptr(order, np.int32, epochs * count, "order"), losses.ctypes.data))
+        return losses[:epochs]
+
+    def eda_ws_infer(self, rhs, ctrl, out):
+        count = int(rhs.shape[0])
+        n = self.n
+        self._check(self._L.eda_ws_infer(self._w, _ptr(rhs, np.float64, count * n, "rhs"),
+                                         _ptr(ctrl, np.float64, count * n, "ctrl"), count,
+                                         _ptr(out, np.float64, count * n, "out")))
