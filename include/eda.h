@@ -249,6 +249,32 @@ EDA_API long long eda_kernel_launches(void);
  */
 EDA_API int eda_time_hvp_sweep(eda_handle* h, int reps, int fp64, double* ms_out);
 
+/*
+ * eda_hvp for callers that must not allocate device memory while they run
+ * (the paper has no counterpart: it is an interface for callers).  Such
+ * callers include a host thread capturing a CUDA graph in global mode, where
+ * cudaMalloc is illegal; an assimilation cycle confined to a preallocated
+ * memory budget; a latency-critical loop that cannot afford the device
+ * synchronisation an allocation may cause.  eda_hvp may allocate (it grows
+ * the handle's observation stash and stages host arrays); this variant
+ * computes the same products with no allocation at all:
+ *  - member_of_col, V and HV must be device memory (EDA_ERR_INVALID otherwise);
+ *  - its scratch, the per-column observation stash, is a fixed 32 MiB
+ *    __device__ array compiled into the library (held by every device that
+ *    loads it until the process exits): ncol * p must not exceed
+ *    eda_hvp_noalloc_capacity(precision == EDA_FP64) entries, or the call
+ *    fails with EDA_ERR_INVALID before any work (split the columns);
+ *  - the first call on a device looks up the array's device address (no
+ *    allocation); make that first call before any stream capture;
+ *  - every call on a device shares the array: calls that overlap on the GPU
+ *    (other streams, other handles) race; calls on one stream do not.  The
+ *    stash needs no clearing (each entry is written before it is read).
+ */
+EDA_API int eda_hvp_noalloc(eda_handle* h, const int* member_of_col, int ncol, const double* V,
+                            double* HV, int include_identity);
+/* Stash entries the eda_hvp_noalloc scratch holds (FP64 if fp64 != 0, else FP32). */
+EDA_API long long eda_hvp_noalloc_capacity(int fp64);
+
 /* ------------------------------------------------------------------------
  * Uneven batching (not in the paper, which solves one EDA at a time): a group
  * of independent EDA problems -- each its own handle, with its own n, window,

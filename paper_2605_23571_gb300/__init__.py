@@ -35,7 +35,7 @@ EXPORTS = ["eda_version", "eda_last_error", "eda_create", "eda_destroy", "eda_tw
            "eda_group_sketch", "eda_group_build_lmp", "eda_group_autotune", "eda_group_solve",
            "eda_ws_create", "eda_ws_destroy", "eda_ws_last_error", "eda_ws_num_params", "eda_ws_set_params",
            "eda_ws_get_params", "eda_ws_set_scales", "eda_ws_get_scales", "eda_ws_loss_grad", "eda_ws_train",
-           "eda_ws_infer"]
+           "eda_ws_infer", "eda_hvp_noalloc", "eda_hvp_noalloc_capacity"]
 
 
 class EdaError(RuntimeError):
@@ -139,6 +139,10 @@ def lib() -> ctypes.CDLL:
     L.eda_ws_train.argtypes = [vp, vp, vp, vp, i, i, i, d, d, vp, vp]
     L.eda_ws_infer.restype = i
     L.eda_ws_infer.argtypes = [vp, vp, vp, i, vp]
+    L.eda_hvp_noalloc.restype = i
+    L.eda_hvp_noalloc.argtypes = [vp, vp, i, vp, vp, i]
+    L.eda_hvp_noalloc_capacity.restype = ctypes.c_longlong
+    L.eda_hvp_noalloc_capacity.argtypes = [i]
     L.eda_bhalf_gaussian.restype = i
     L.eda_bhalf_gaussian.argtypes = [i, d, d, vp, i, ctypes.POINTER(ctypes.c_int)]
     _lib = L
@@ -302,6 +306,15 @@ class Handle:
         ms = ctypes.c_double(0.0)
         self._check(self._L.eda_autotune(self._h, int(which), ctypes.byref(ms)))
         return ms.value
+
+    def eda_hvp_noalloc(self, member_of_col, V, HV, include_identity=True):
+        """eda_hvp without any device allocation (device arguments only, the
+        observation stash in the library's fixed scratch array)."""
+        ncol = int(member_of_col.shape[0])
+        n = self.n
+        self._check(self._L.eda_hvp_noalloc(self._h, _ptr(member_of_col, np.int32, ncol, "member_of_col"), ncol,
+                                            _ptr(V, np.float64, ncol * n, "V"),
+                                            _ptr(HV, np.float64, ncol * n, "HV"), 1 if include_identity else 0))
 
     def eda_time_hvp_sweep(self, reps=10, fp64=False):
         """Mean milliseconds per launch of the batched member HVP sweep."""
