@@ -160,9 +160,12 @@ def specs_uneven(count: int = 256, seed: int = 0, n_range=(40, 8192), w_range=(8
         density = float(rng.uniform(0.25, 0.5))
         lb = float(rng.uniform(2.0, 16.0))
         steps, ptr, idx = subset_obs(n, nsteps, density, 2, rng)
+        # k = members - 1 from an ell = members sketch; a sketch cannot have
+        # more columns than the state has variables, so ell <= n
+        ell = min(members, n)
         out.append(Spec(n=n, nsteps=nsteps, obs_steps=steps, obs_ptr=ptr, obs_idx=idx,
                         sigma_o=1.0, sigma_b=1.0, length_scale=lb,
-                        n_members=members + 1, ell=members, k=members - 1,
+                        n_members=members + 1, ell=ell, k=ell - 1,
                         seed=seed * 100003 + i, name="uneven_%d" % i))
     return out
 

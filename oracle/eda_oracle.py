@@ -315,13 +315,24 @@ def cost_J(Hx, x, b):
 # ---------------------------------------------------------------------------
 
 
-def nystrom(apply_a, Phi, k, q=1, shift_eps=np.finfo(np.float64).eps):
+def nystrom(apply_a, Phi, k, q=1, shift_eps=np.finfo(np.float64).eps, evd_rtol=1e-12):
     """Algorithm 1.  ``apply_a`` maps an (n, ell) block to A times it.
 
-    Returns (S_k (n, k), D_k (k,), info) with D_k descending.  If the
-    Cholesky factorisation of W breaks down, the algorithm is rerun on the
-    shifted matrix A + nu I with nu = eps ||A Phi||_F (Appendix B) and nu is
-    subtracted from the eigenvalues; ``info['shift']`` reports nu.
+    Returns (S_k (n, k), D_k (k,), info) with D_k descending.
+
+    The small matrix W = Phi^T A Phi is inverted through its Cholesky factor
+    (Algorithm 1).  If that breaks down, the algorithm is rerun on the
+    shifted matrix A + nu I with nu = eps ||A Phi||_F and nu is subtracted
+    from the eigenvalues (Appendix B, shift).  If the shifted factorisation
+    also breaks down -- Phi itself numerically rank deficient, e.g. when B
+    has few non-negligible eigenvalues -- W is inverted by a truncated
+    eigendecomposition (Appendix B, third variant): W^+ = V diag(1/mu) V^T
+    over the eigenvalues mu > evd_rtol * max(mu), T = R_Y V diag(mu^{-1/2}).
+    The approximation then has rank r = number of kept mu, so only
+    k_eff = min(k, r) modes carry information: columns k_eff..k-1 of S_k and
+    the matching entries of D_k are returned as zeros (the LMP acts as the
+    identity there).  ``info['path']`` is 'cholesky', 'shift' or 'evd' and
+    ``info['rank']`` is k_eff (k on the first two paths).
     """
     Phi = np.asarray(Phi, dtype=np.float64)
     Y = apply_a(Phi)
@@ -331,25 +342,42 @@ def nystrom(apply_a, Phi, k, q=1, shift_eps=np.finfo(np.float64).eps):
         Y = apply_a(Phi)
         Q, R = np.linalg.qr(Y)
     nu = 0.0
+    path = "cholesky"
     W = Phi.T @ Y
     W = 0.5 * (W + W.T)
     try:
         L = np.linalg.cholesky(W)
+        T = np.linalg.solve(L, R.T).T           # T = R_Y C^{-1}, C = L^T (W = C^T C)
     except np.linalg.LinAlgError:
         nu = shift_eps * np.linalg.norm(Y)
-        Y = Y + nu * Phi
-        Q, R = np.linalg.qr(Y)
-        W = Phi.T @ Y
-        W = 0.5 * (W + W.T)
-        L = np.linalg.cholesky(W)
-    C = L.T                                   # W = C^T C, C upper triangular
-    # T = R_Y C^{-1}  <=>  C^T T^T = R_Y^T (a lower-triangular solve)
-    T = np.linalg.solve(C.T, R.T).T
+        Ys = Y + nu * Phi
+        Qs, Rs = np.linalg.qr(Ys)
+        Ws = Phi.T @ Ys
+        Ws = 0.5 * (Ws + Ws.T)
+        try:
+            L = np.linalg.cholesky(Ws)
+            Y, Q, R = Ys, Qs, Rs
+            T = np.linalg.solve(L, R.T).T
+            path = "shift"
+        except np.linalg.LinAlgError:
+            nu = 0.0
+            path = "evd"
+            mu, V = np.linalg.eigh(W)
+            keep = mu > evd_rtol * max(mu.max(), 0.0)
+            f = np.zeros_like(mu)
+            f[keep] = 1.0 / np.sqrt(mu[keep])
+            T = R @ (V * f)                       # T T^T = R_Y W^+ R_Y^T
     U, s, _ = np.linalg.svd(T)
     S = Q @ U
     D = s * s - nu
     D = np.maximum(D, 0.0)
-    return S[:, :k].copy(), D[:k].copy(), {"shift": nu, "Y": Y, "Q": Q, "R": R}
+    S, D = S[:, :k].copy(), D[:k].copy()
+    rank = k
+    if path == "evd":
+        rank = min(k, int(keep.sum()))
+        S[:, rank:] = 0.0
+        D[rank:] = 0.0
+    return S, D, {"shift": nu, "path": path, "Y": Y, "Q": Q, "R": R, "rank": rank}
 
 
 # ---------------------------------------------------------------------------
@@ -359,10 +387,11 @@ def nystrom(apply_a, Phi, k, q=1, shift_eps=np.finfo(np.float64).eps):
 
 def theta_value(mode, D, theta_given=1.0):
     """theta: given, lambda_k(I+A), or (lambda_k(I+A) + lambda_n(I+A))/2 with
-    lambda_n(I+A) = 1 (Section 3.1)."""
+    lambda_n(I+A) = 1 (Section 3.1).  ``D`` holds the retained modes only
+    (an empty D, a sketch without information, gives lambda_k = 1)."""
     if mode == 0:
         return float(theta_given)
-    lam_k = 1.0 + float(D[-1])
+    lam_k = 1.0 + (float(D[-1]) if len(D) else 0.0)
     if mode == 1:
         return lam_k
     return 0.5 * (lam_k + 1.0)
@@ -484,8 +513,10 @@ def eda_pipeline(spec, xb, y, taps, tol=1e-6, maxit=500, use_lmp=True, fixed_ite
             return apply_A(spec, tr, block.T.copy(), taps).T
 
         S, D, info = nystrom(apply_ctrl, Phi, spec.k, q=q)
-        theta = theta_value(spec.theta_mode, D, spec.theta)
+        r = info["rank"]
+        theta = theta_value(spec.theta_mode, D[:r], spec.theta)
         c = lmp_coeffs(D, theta)
+        c[r:] = 0.0
         out.update(S=S, D=D, theta=theta, c=c, shift=info["shift"], Y=info["Y"])
         P = lambda R: lmp_apply(S, c, R)
     else:

@@ -266,3 +266,42 @@ def test_gamma_covariance_is_A_plus_A2_on_linear_twin():
     assert rel < 6.0 / np.sqrt(draws), rel
     # and the mean of gamma is zero to Monte-Carlo accuracy
     assert np.linalg.norm(G.mean(1)) < 6.0 * np.sqrt(np.trace(target) / draws)
+
+
+def test_nystrom_truncated_evd_when_the_sketch_is_rank_deficient():
+    # B with a length scale comparable to n has only a few non-negligible
+    # eigenvalues, so Gamma (in the range of U_B) is numerically rank
+    # deficient and no shift of A makes Phi^T A Phi definite; the truncated
+    # eigendecomposition variant (Appendix B) still returns the Nystrom
+    # approximation, which is exact on the span of the sketch:
+    # S D S^T = A Phi (Phi^T A Phi)^+ Phi^T A.
+    n, N = 41, 10
+    steps, ptr, idx = S.regular_obs(n, N, 3, 2)
+    spec = S.Spec(n=n, nsteps=N, obs_steps=steps, obs_ptr=ptr, obs_idx=idx, sigma_o=1.0,
+                  sigma_b=1.0, length_scale=7.6, n_members=33, ell=32, k=31, spinup=300)
+    taps = O.bhalf_taps(n, 7.6, 1.0)
+    _, xb, y = O.twin(spec, S.draws(spec), taps)
+    traj = O.member_trajectories(spec, xb)
+    b = O.rhs(spec, traj, O.innovations(spec, traj, y), taps)
+    Phi = O.gamma(b)[:, :32]
+    sv = np.linalg.svd(Phi, compute_uv=False)
+    assert sv[-1] < 1e-6 * sv[0]          # numerically rank deficient
+    f = control_apply(spec, traj, taps)
+    Sk, D, info = O.nystrom(f, Phi, 31, evd_rtol=1e-12)
+    assert info["path"] == "evd"
+    A = O.dense_A(spec, traj[0], taps)
+    Y = A @ Phi
+    W = Phi.T @ Y
+    mu, V = np.linalg.eigh(0.5 * (W + W.T))
+    keep = mu > 1e-12 * mu.max()
+    # rank r of the approximation < k: the first r columns are orthonormal
+    # eigenvectors, the remaining ones (and their D) are zero
+    r = info["rank"]
+    assert r == keep.sum() < 31
+    np.testing.assert_allclose(Sk[:, :r].T @ Sk[:, :r], np.eye(r), atol=1e-12)
+    assert not Sk[:, r:].any() and not D[r:].any()
+    AN = Y @ (V[:, keep] / mu[keep]) @ V[:, keep].T @ Y.T
+    np.testing.assert_allclose((Sk * D) @ Sk.T, AN, atol=1e-8 * np.abs(AN).max())
+    # and A_N <= A: no eigenvalue exceeds A's
+    lamA = np.sort(np.linalg.eigvalsh(0.5 * (A + A.T)))[::-1]
+    assert (D <= lamA[: len(D)] * (1 + 1e-8) + 1e-10 * lamA[0]).all()
