@@ -145,8 +145,8 @@ def cpu_oracle_step(spec, xb, y, taps, iters_per_member, sample_iters=30):
         tr = np.broadcast_to(ctrl, (block.shape[1],) + ctrl.shape[1:])
         return O.apply_A(spec, tr, block.T.copy(), taps).T
 
-    Sk, D, _ = O.nystrom(apply_ctrl, O.gamma(b)[:, : spec.ell], spec.k)
-    theta = O.theta_value(spec.theta_mode, D, spec.theta)
+    Sk, D, info = O.nystrom(apply_ctrl, O.gamma(b)[:, : spec.ell], spec.k)
+    theta = O.theta_value(spec.theta_mode, D[: info["rank"]], spec.theta)
     c = O.lmp_coeffs(D, theta)
     t1 = time.perf_counter()
     O.pcg(lambda V: O.hvp(spec, traj[:1], V, taps), b[:1], lambda R: O.lmp_apply(Sk, c, R),

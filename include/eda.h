@@ -83,7 +83,7 @@ typedef struct eda_handle eda_handle;
  *                  (U_B v)_i = sum_{|d|<=w} coef[|d|] v_{(i+d) mod n},
  *                  0 <= w <= (n-1)/2, coef has w+1 entries.
  *  n_members       L + 1 (member 0 is the control, Section 2.2), >= 1.
- *  ell, k          sketch columns (1 <= ell <= L) and LMP rank (1 <= k <= ell)
+ *  ell, k          sketch columns (1 <= ell <= min(L, 80, n)) and LMP rank (1 <= k <= ell)
  *                  (Algorithm 1).  ell = 0 disables the LMP.
  *  theta_mode, theta   EDA_THETA_GIVEN uses theta; EDA_THETA_LAMBDA_K uses
  *                  lambda_k(I+A); EDA_THETA_MID uses (lambda_k(I+A)+1)/2
@@ -178,12 +178,29 @@ EDA_API int eda_sketch(eda_handle* h, const double* phi, int q, double* y_out);
  * (CholeskyQR2), W = Phi^T Y, W = C^T C (with the Appendix B shift
  * nu = eps ||Y||_F if the factorisation breaks down), T = R_Y C^{-1}, SVD
  * T = U_T Sigma V_T^T, S = Q_Y U_T, D = Sigma^2, truncated to k; then the
- * LMP coefficients c_i = theta / (1 + D_i) - 1 (Section 3.1).
- * eigvals_out [k] (may be NULL) receives lambda_i(I + A) = 1 + D_i in
- * descending order; s_out [n x k] column-major (may be NULL) receives S_k.
- * EDA_ERR_NUMERIC if the shifted factorisation also fails.
+ * LMP coefficients c_i = theta / (1 + D_i) - 1 (Section 3.1).  If the
+ * shifted factorisation also breaks down (a numerically rank-deficient
+ * sketch), W = Phi^T Y is inverted by a truncated eigendecomposition over
+ * its eigenvalues above 1e-12 times the largest, and the range of Y taken
+ * from the eigendecomposition of Y^T Y (Appendix B).  That approximation
+ * has rank r = the number of eigenvalues kept, so only k_eff = min(k, r)
+ * modes are informative: columns k_eff..k-1 of S_k are zero, their D_i = 0
+ * and c_i = 0 (the LMP is the identity there), and theta is taken at mode
+ * k_eff.  eigvals_out [k] (may be NULL) receives lambda_i(I + A) = 1 + D_i
+ * in descending order; s_out [n x k] column-major (may be NULL) receives
+ * S_k.  EDA_ERR_NUMERIC if the last CholeskyQR pass of the truncated
+ * variant fails.
  */
 EDA_API int eda_build_lmp(eda_handle* h, double* eigvals_out, double* s_out);
+
+/*
+ * How the last eda_build_lmp went (host outputs, each may be NULL): *path =
+ * 0 (Cholesky of W), 1 (Appendix B shift) or 2 (truncated
+ * eigendecomposition); *rank = the number of informative LMP modes (k, or
+ * k_eff on path 2; k after eda_set_lmp); *shift = nu (0 unless path 1).
+ * EDA_ERR_STATE before any LMP.
+ */
+EDA_API int eda_lmp_info(eda_handle* h, int* path, int* rank, double* shift);
 
 /*
  * Loads a spectral LMP built elsewhere (another process, a previous cycle, a
@@ -200,7 +217,8 @@ EDA_API int eda_set_lmp(eda_handle* h, const double* s_in, const double* eigvals
  * with its own Hessian, preconditioned by the control member's LMP when
  * use_lmp != 0 (requires eda_build_lmp).  Stops member j when
  * ||r_j|| / ||b_j|| <= tol on the recurrence residual (tol = 0 runs exactly
- * maxit iterations), or after maxit iterations.  x0 [(L+1) x n] is the
+ * maxit iterations), or after its own maxit-th iteration (the budget is per
+ * member, refinement rounds included).  x0 [(L+1) x n] is the
  * initial guess (NULL = 0).  Outputs: dz_out [(L+1) x n], iters_out
  * [L+1] (int), relres_out [L+1] (the FP64 recurrence residual at exit; in
  * EDA_MIXED the FP64 true residual), status_out [L+1] (EDA_CONVERGED,
@@ -305,7 +323,9 @@ EDA_API int eda_group_build_lmp(eda_group* g);
  * K in {2, 4, 8, 16} per bucket, keeps the fastest per problem.
  * *best_ms_out (may be NULL) = mean time of the tuned batched sweep (ms). */
 EDA_API int eda_group_autotune(eda_group* g, double* best_ms_out);
-/* Batched PCG of every member of every problem (as eda_solve_batch, x0 = 0).
+/* Batched PCG of every member of every problem (as eda_solve_batch, x0 = 0;
+ * maxit is a budget per member, so one hard problem does not cut the others
+ * short).
  * dz_out[i] [(L_i+1) x n_i] per problem (host array of pointers, each host or
  * device, NULL entries skipped; dz_out itself may be NULL); iters_out,
  * relres_out, status_out [sum_i (L_i+1)] concatenated in problem order (host

@@ -35,7 +35,7 @@ EXPORTS = ["eda_version", "eda_last_error", "eda_create", "eda_destroy", "eda_tw
            "eda_group_sketch", "eda_group_build_lmp", "eda_group_autotune", "eda_group_solve",
            "eda_ws_create", "eda_ws_destroy", "eda_ws_last_error", "eda_ws_num_params", "eda_ws_set_params",
            "eda_ws_get_params", "eda_ws_set_scales", "eda_ws_get_scales", "eda_ws_loss_grad", "eda_ws_train",
-           "eda_ws_infer", "eda_hvp_noalloc", "eda_hvp_noalloc_capacity"]
+           "eda_ws_infer", "eda_hvp_noalloc", "eda_hvp_noalloc_capacity", "eda_lmp_info"]
 
 
 class EdaError(RuntimeError):
@@ -91,6 +91,8 @@ def lib() -> ctypes.CDLL:
     L.eda_build_lmp.argtypes = [vp, vp, vp]
     L.eda_set_lmp.restype = i
     L.eda_set_lmp.argtypes = [vp, vp, vp]
+    L.eda_lmp_info.restype = i
+    L.eda_lmp_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)]
     L.eda_solve_batch.restype = i
     L.eda_solve_batch.argtypes = [vp, d, i, vp, i, vp, vp, vp, vp]
     L.eda_hvp.restype = i
@@ -292,6 +294,13 @@ class Handle:
     def eda_set_lmp(self, s_in, eigvals_in):
         self._check(self._L.eda_set_lmp(self._h, _ptr(s_in, np.float64, self.k * self.n, "s_in"),
                                         _ptr(eigvals_in, np.float64, self.k, "eigvals_in")))
+
+    def eda_lmp_info(self):
+        """(path, rank, shift) of the current LMP: path 0 Cholesky, 1 shift,
+        2 truncated eigendecomposition; rank = informative modes."""
+        path, rank, shift = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+        self._check(self._L.eda_lmp_info(self._h, ctypes.byref(path), ctypes.byref(rank), ctypes.byref(shift)))
+        return path.value, rank.value, shift.value
 
     def eda_solve_batch(self, tol, maxit, x0, use_lmp, dz_out, iters_out=None, relres_out=None,
                         status_out=None):

@@ -79,6 +79,31 @@ int set_plan(eda_handle* h, bool fp64, const SweepPlan& pl) {
   return EDA_OK;
 }
 
+int ensure_ml(eda_handle* h, int ncol, bool fp64) {
+  const SweepPlan& pl = fp64 ? h->plan64 : h->plan32;
+  if (!pl.ml) return EDA_OK;
+  const long long need = (long long)ncol * h->n;
+  if (fp64 && need > h->ml64_cap) {
+    h->ml64_cap = 0;
+    for (int i = 0; i < 2; ++i) {
+      if (h->ml64[i]) cudaFree(h->ml64[i]);
+      h->ml64[i] = nullptr;
+      CU(h, cudaMalloc((void**)&h->ml64[i], need * sizeof(double)));
+    }
+    h->ml64_cap = need;
+  }
+  if (!fp64 && need > h->ml32_cap) {
+    h->ml32_cap = 0;
+    for (int i = 0; i < 2; ++i) {
+      if (h->ml32[i]) cudaFree(h->ml32[i]);
+      h->ml32[i] = nullptr;
+      CU(h, cudaMalloc((void**)&h->ml32[i], need * sizeof(float)));
+    }
+    h->ml32_cap = need;
+  }
+  return EDA_OK;
+}
+
 int read_flag(eda_handle* h, const int* dflag, int* out) {
   CU(h, cudaMemcpyAsync(h->hflag, dflag, sizeof(int), cudaMemcpyDeviceToHost, h->st));
   CU(h, cudaStreamSynchronize(h->st));
@@ -260,7 +285,8 @@ __global__ void eig_kernel(int k, const double* D, double* out) {
 // residual misses tol is reactivated with the next inner threshold
 // max(tol, tau * true relres).
 __global__ void true_res_kernel(int n, const double* b, const double* hx, float* r32, double* r64,
-                                PcgScalars* sc, int* active, double tol, int* nactive, int* need, double tau) {
+                                PcgScalars* sc, int* active, double tol, int* nactive, int* need, double tau,
+                                int maxit) {
   __shared__ double red[32];
   const int j = blockIdx.x;
   const double* bj = b + (long long)j * n;
@@ -287,12 +313,14 @@ __global__ void true_res_kernel(int n, const double* b, const double* hx, float*
     const bool ok = (bn == 0.0) || (rel <= tol);
     if (sc[j].status == EDA_CONVERGED && !ok) {
       // the inner solve met its threshold but the FP64 residual misses tol:
-      // next refinement round
+      // next refinement round, while the member has iterations left
       sc[j].status = EDA_MAXIT;
-      sc[j].tolm = fmax(tol, tau * rel);
-      active[j] = 1;
-      atomicAdd(nactive, 1);
-      atomicAdd(need, 1);
+      if (sc[j].iters < maxit) {
+        sc[j].tolm = fmax(tol, tau * rel);
+        active[j] = 1;
+        atomicAdd(nactive, 1);
+        atomicAdd(need, 1);
+      }
     }
   }
 }
@@ -361,7 +389,7 @@ int hvp_dev(eda_handle* h, const int* dcols, int ncol, const double* V, double* 
     a.stash = h->stash;
     a.stash_stride = h->p;
     a.include_identity = ident;
-    CU(h, eda::launch_sweep<double>(a, h->plan64, h->st));
+    CU(h, (eda::ensure_ml(h, a.ncol, true) == EDA_OK) ? eda::launch_sweep<double>(a, h->plan64, h->st, h->ml64[0], h->ml64[1]) : cudaErrorMemoryAllocation);
     return EDA_OK;
   }
   // FP32 sweeps reading and writing the FP64 vectors directly
@@ -377,7 +405,7 @@ int hvp_dev(eda_handle* h, const int* dcols, int ncol, const double* V, double* 
   a.stash = h->stash32;
   a.stash_stride = h->p;
   a.include_identity = ident;
-  CU(h, eda::launch_sweep<float>(a, h->plan32, h->st));
+  CU(h, (eda::ensure_ml(h, a.ncol, false) == EDA_OK) ? eda::launch_sweep<float>(a, h->plan32, h->st, h->ml32[0], h->ml32[1]) : cudaErrorMemoryAllocation);
   return EDA_OK;
 }
 
@@ -461,35 +489,45 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
     SweepPlan best = keep;
     float best_ms = 1e30f;
     const int reps = fp64 ? 1 : 3;
-    for (int CS = 1; CS <= 8; ++CS) {
+    // candidates: single-launch cluster plans (CS 1..8), then multi-launch
+    // plans where a column spans several tiles
+    std::vector<SweepPlan> cands;
+    for (int CS = 1; CS <= 8; ++CS)
       for (int K : Ks) {
         SweepPlan pl;
         if (!eda::plan_sweep_exact(h->n, fp64 ? 8 : 4, h->w, CS, K, &pl)) continue;
         if (pl.HL > h->n && CS > 1) continue;
-        int rc = set_plan(h, fp64, pl);
+        cands.push_back(pl);
+      }
+    for (int A : {128, 256, 512})
+      for (int K : Ks) {
+        SweepPlan pl;
+        if (eda::plan_sweep_ml(h->n, fp64 ? 8 : 4, h->w, 2 * K, A, &pl) && pl.CS >= 2) cands.push_back(pl);
+      }
+    for (const SweepPlan& pl : cands) {
+      int rc = set_plan(h, fp64, pl);
+      if (rc) return rc;
+      float ms = 0.f;
+      for (int rep = -1; rep < reps; ++rep) {
+        if (rep == 0) CU(h, cudaEventRecord(e0, h->st));
+        rc = hvp_dev(h, h->cols, h->M, h->pv, h->q, 1, fp64, nullptr);
         if (rc) return rc;
-        float ms = 0.f;
-        for (int rep = -1; rep < reps; ++rep) {
-          if (rep == 0) CU(h, cudaEventRecord(e0, h->st));
-          rc = hvp_dev(h, h->cols, h->M, h->pv, h->q, 1, fp64, nullptr);
-          if (rc) return rc;
-        }
-        CU(h, cudaEventRecord(e1, h->st));
-        CU(h, cudaEventSynchronize(e1));
-        CU(h, cudaEventElapsedTime(&ms, e0, e1));
-        ms /= reps;
-        if (ms < best_ms) {
-          best_ms = ms;
-          best = pl;
-        }
+      }
+      CU(h, cudaEventRecord(e1, h->st));
+      CU(h, cudaEventSynchronize(e1));
+      CU(h, cudaEventElapsedTime(&ms, e0, e1));
+      ms /= reps;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = pl;
       }
     }
     int rc = set_plan(h, fp64, best);
     if (rc) return rc;
     best_total += best_ms;
     if (env_int("EDA_VERBOSE", 0))
-      std::fprintf(stderr, "eda_autotune: %s sweep CS=%d K=%d A=%d E=%d C=%d %.4f ms\n", fp64 ? "FP64" : "FP32", best.CS,
-                   best.K, best.A, best.E, best.C, best_ms);
+      std::fprintf(stderr, "eda_autotune: %s sweep %s CS=%d K=%d A=%d E=%d C=%d %.4f ms\n", fp64 ? "FP64" : "FP32",
+                   best.ml ? "multi-launch" : "cluster", best.CS, best.K, best.A, best.E, best.C, best_ms);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -555,8 +593,8 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
   if (c.n_members < 1) return fail(nullptr, EDA_ERR_INVALID, "n_members must be >= 1");
   if (c.bhalf_w < 0 || c.bhalf_w > (c.n - 1) / 2 || !c.bhalf_coef)
     return fail(nullptr, EDA_ERR_INVALID, "bhalf_w must be in [0, (n-1)/2] with coefficients");
-  if (c.ell < 0 || c.ell > c.n_members - 1 || c.ell > 88 || c.ell > c.n)
-    return fail(nullptr, EDA_ERR_INVALID, "ell must be in [0, min(L, 88, n)]");
+  if (c.ell < 0 || c.ell > c.n_members - 1 || c.ell > 80 || c.ell > c.n)
+    return fail(nullptr, EDA_ERR_INVALID, "ell must be in [0, min(L, 80, n)]");
   if (c.ell > 0 && (c.k < 1 || c.k > c.ell)) return fail(nullptr, EDA_ERR_INVALID, "k must be in [1, ell]");
   if (c.theta_mode < 0 || c.theta_mode > 2) return fail(nullptr, EDA_ERR_INVALID, "bad theta_mode");
   if (c.theta_mode == EDA_THETA_GIVEN && !(c.theta > 0.0)) return fail(nullptr, EDA_ERR_INVALID, "theta must be > 0");
@@ -616,9 +654,19 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
     }                                                                                            \
   } while (0)
 
+  // Sweep tiling: a single-launch cluster plan where one fits, else the
+  // multi-launch plan.  EDA_SWEEP_K fixes the refresh period;
+  // EDA_SWEEP_CS64/CS32 the smallest cluster size; EDA_SWEEP_ML=<threads>
+  // forces multi-launch tiles of that many threads.
   const int Kh = env_int("EDA_SWEEP_K", 0);
   const int cs64 = env_int("EDA_SWEEP_CS64", 1), cs32 = env_int("EDA_SWEEP_CS32", 1);
-  if (!eda::plan_sweep(h->n, 8, h->w, cs64, Kh, &h->plan64) || !eda::plan_sweep(h->n, 4, h->w, cs32, Kh, &h->plan32)) {
+  const int mlA = env_int("EDA_SWEEP_ML", 0);
+  const bool planned =
+      mlA > 0 ? (eda::plan_sweep_ml(h->n, 8, h->w, Kh > 0 ? Kh : 16, mlA, &h->plan64) &&
+                 eda::plan_sweep_ml(h->n, 4, h->w, Kh > 0 ? Kh : 16, mlA, &h->plan32))
+              : (eda::plan_sweep(h->n, 8, h->w, cs64, Kh, &h->plan64) &&
+                 eda::plan_sweep(h->n, 4, h->w, cs32, Kh, &h->plan32));
+  if (!planned) {
     fail(nullptr, EDA_ERR_INVALID, "state size too large for the sweep tiling");
     return bail(EDA_ERR_INVALID);
   }
@@ -708,6 +756,10 @@ EDA_API int eda_destroy(eda_handle* h) {
     if (p) cudaFree(p);
   if (h->stash) cudaFree(h->stash);
   if (h->stash32) cudaFree(h->stash32);
+  for (int i = 0; i < 2; ++i) {
+    if (h->ml64[i]) cudaFree(h->ml64[i]);
+    if (h->ml32[i]) cudaFree(h->ml32[i]);
+  }
   if (h->tab64) cudaFree(h->tab64);
   if (h->tab32) cudaFree(h->tab32);
   if (h->hflag) cudaFreeHost(h->hflag);
@@ -749,7 +801,7 @@ EDA_API int eda_twin(eda_handle* h, const double* x_spin0, int spinup, const dou
     a.x0 = (const double*)xs.dev;
     a.x0_stride = n;
     a.final_out = xt;
-    CU(h, eda::launch_sweep<double>(a, h->plan64, h->st));
+    CU(h, (eda::ensure_ml(h, a.ncol, true) == EDA_OK) ? eda::launch_sweep<double>(a, h->plan64, h->st, h->ml64[0], h->ml64[1]) : cudaErrorMemoryAllocation);
   } else {
     CU(h, cudaMemcpyAsync(xt, xs.dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
   }
@@ -761,7 +813,7 @@ EDA_API int eda_twin(eda_handle* h, const double* x_spin0, int spinup, const dou
     a.x0 = xt;
     a.x0_stride = n;
     a.d_out = ytrue;
-    CU(h, eda::launch_sweep<double>(a, h->plan64, h->st));
+    CU(h, (eda::ensure_ml(h, a.ncol, true) == EDA_OK) ? eda::launch_sweep<double>(a, h->plan64, h->st, h->ml64[0], h->ml64[1]) : cudaErrorMemoryAllocation);
   }
   eda::count_launch();
   twin_sum_kernel<<<grid_for((long long)M * n), 256, 0, h->st>>>(n, M, (const double*)eb.dev, tmp);
@@ -809,7 +861,7 @@ EDA_API int eda_set_trajectory(eda_handle* h, const double* xb, const double* y,
     a.yobs = (const double*)iy.dev;
     a.d_out = h->d;
     a.rd_out = h->rd;
-    CU(h, eda::launch_sweep<double>(a, h->plan64, h->st));
+    CU(h, (eda::ensure_ml(h, a.ncol, true) == EDA_OK) ? eda::launch_sweep<double>(a, h->plan64, h->st, h->ml64[0], h->ml64[1]) : cudaErrorMemoryAllocation);
   }
   if (h->precision == EDA_MIXED)
     CU(h, eda::convert<double, float>((long long)M * (N + 1) * n, h->traj, h->traj32, h->st));
@@ -822,7 +874,7 @@ EDA_API int eda_set_trajectory(eda_handle* h, const double* xb, const double* y,
     a.stash_stride = p;
     a.OUT = h->b;
     a.out_stride = n;
-    CU(h, eda::launch_sweep<double>(a, h->plan64, h->st));
+    CU(h, (eda::ensure_ml(h, a.ncol, true) == EDA_OK) ? eda::launch_sweep<double>(a, h->plan64, h->st, h->ml64[0], h->ml64[1]) : cudaErrorMemoryAllocation);
   }
   Out orhs;
   CU(h, orhs.init(rhs_out, (size_t)M * n * sizeof(double), h->st));
@@ -898,8 +950,16 @@ EDA_API int eda_build_lmp(eda_handle* h, double* eigvals_out, double* s_out) {
   if (!h->have_sketch) return fail(h, EDA_ERR_STATE, "eda_build_lmp before eda_sketch");
   const int n = h->n, m = h->ell, kk = h->k;
   double nu = 0.0;
+  // Algorithm 1 with the Cholesky factor of W; on breakdown the Appendix B
+  // shift nu = eps ||Y||_F; if that also breaks down (the sketch is
+  // numerically rank deficient), the truncated-eigendecomposition variant.
+  bool robust = false;
   for (int attempt = 0; attempt < 2; ++attempt) {
     int rc = cholqr2(h, h->Y, h->Q);
+    if (rc == EDA_ERR_NUMERIC) {
+      robust = true;
+      break;
+    }
     if (rc) return rc;
     CU(h, eda::gemm_tn<double, double>(n, h->Phi, m, h->Y, m, h->W, m, nullptr, false, h->st));
     CU(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
@@ -909,7 +969,10 @@ EDA_API int eda_build_lmp(eda_handle* h, double* eigvals_out, double* s_out) {
     rc = read_flag(h, h->dstatus, &st);
     if (rc) return rc;
     if (!st) break;
-    if (attempt == 1) return fail(h, EDA_ERR_NUMERIC, "Nystrom: Cholesky of Phi^T Y failed after the shift");
+    if (attempt == 1) {
+      robust = true;
+      break;
+    }
     // Appendix B: shift nu = eps ||Y||_F, Y <- Y + nu Phi
     CU(h, eda::gemm_tn<double, double>(n, h->Y, m, h->Y, m, h->G, m, nullptr, true, h->st));
     std::vector<double> Gh((size_t)m * m);
@@ -922,9 +985,49 @@ EDA_API int eda_build_lmp(eda_handle* h, double* eigvals_out, double* s_out) {
     axpy_kernel<<<grid_for((long long)m * n), 256, 0, h->st>>>((long long)m * n, nu, h->Phi, h->Y);
     CU(h, cudaGetLastError());
   }
+  if (robust) {
+    if (nu != 0.0) {  // undo the shift of Y
+      eda::count_launch();
+      axpy_kernel<<<grid_for((long long)m * n), 256, 0, h->st>>>((long long)m * n, -nu, h->Phi, h->Y);
+      CU(h, cudaGetLastError());
+      nu = 0.0;
+    }
+    // W = Phi^T Y; M = U mu^{-1/2} (kept eigenvalues); Z = Y M (into Q);
+    // K = Z^T Z; SB = V D^{-1/2}; S' = Z SB (into pv); then one CholeskyQR
+    // pass on S' restores orthonormal columns.  Columns k_eff..k-1 of S are
+    // zero (c = 0 there: the LMP is the identity on them).
+    const double rtol = 1e-12;
+    CU(h, eda::gemm_tn<double, double>(n, h->Phi, m, h->Y, m, h->W, m, nullptr, false, h->st));
+    CU(h, eda::robust_winv(h->W, m, rtol, h->RY, h->st));
+    CU(h, eda::gemm_nn<double, double>(n, h->Y, m, m, h->RY, nullptr, nullptr, h->Q, nullptr, h->st));
+    CU(h, eda::gemm_tn<double, double>(n, h->Q, m, h->Q, m, h->G, m, nullptr, true, h->st));
+    CU(h, eda::robust_eig(h->G, m, kk, rtol, h->theta_mode, h->theta_given, h->UT, h->Dv, h->cv, h->theta,
+                          h->dstatus, h->st));
+    int ke = 0;
+    int rc = read_flag(h, h->dstatus, &ke);
+    if (rc) return rc;
+    if (ke < 0 || ke > kk) return fail(h, EDA_ERR_NUMERIC, "Nystrom: truncated-eigendecomposition variant failed");
+    if (ke > 0) {
+      CU(h, eda::gemm_nn<double, double>(n, h->Q, m, ke, h->UT, nullptr, nullptr, h->pv, nullptr, h->st));
+      CU(h, eda::gemm_tn<double, double>(n, h->pv, ke, h->pv, ke, h->G, ke, nullptr, true, h->st));
+      CU(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
+      CU(h, eda::chol_inv(h->G, ke, 0.0, h->R1, h->R1i, h->dstatus, h->st));
+      int st = 0;
+      rc = read_flag(h, h->dstatus, &st);
+      if (rc) return rc;
+      if (st) return fail(h, EDA_ERR_NUMERIC, "Nystrom: truncated-eigendecomposition variant failed");
+      CU(h, eda::gemm_nn<double, double>(n, h->pv, ke, ke, h->R1i, nullptr, nullptr, h->S, nullptr, h->st));
+    }
+    if (ke < kk) CU(h, cudaMemsetAsync(h->S + (size_t)ke * n, 0, (size_t)(kk - ke) * n * sizeof(double), h->st));
+    h->lmp_rank = ke;
+    h->nystrom_path = 2;
+  } else {
+    h->nystrom_path = (nu != 0.0) ? 1 : 0;
+    h->lmp_rank = kk;
+    // S = Q_Y U_T(:, 1:k)
+    CU(h, eda::gemm_nn<double, double>(n, h->Q, m, kk, h->UT, nullptr, nullptr, h->S, nullptr, h->st));
+  }
   h->shift_used = nu;
-  // S = Q_Y U_T(:, 1:k)
-  CU(h, eda::gemm_nn<double, double>(n, h->Q, m, kk, h->UT, nullptr, nullptr, h->S, nullptr, h->st));
   if (h->precision == EDA_MIXED) CU(h, eda::convert<double, float>((long long)kk * n, h->S, h->S32, h->st));
   Out oe, os;
   CU(h, oe.init(eigvals_out, (size_t)kk * sizeof(double), h->st));
@@ -973,7 +1076,19 @@ EDA_API int eda_set_lmp(eda_handle* h, const double* s_in, const double* eigvals
   CU(h, cudaMemcpyAsync(h->theta, &th, sizeof(double), cudaMemcpyHostToDevice, h->st));
   if (h->precision == EDA_MIXED) CU(h, eda::convert<double, float>((long long)kk * n, h->S, h->S32, h->st));
   CU(h, cudaStreamSynchronize(h->st));
+  h->nystrom_path = 0;
+  h->lmp_rank = h->k;
+  h->shift_used = 0.0;
   h->have_lmp = true;
+  return EDA_OK;
+}
+
+EDA_API int eda_lmp_info(eda_handle* h, int* path, int* rank, double* shift) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (!h->have_lmp) return fail(h, EDA_ERR_STATE, "eda_lmp_info before eda_build_lmp or eda_set_lmp");
+  if (path) *path = h->nystrom_path;
+  if (rank) *rank = h->lmp_rank;
+  if (shift) *shift = h->shift_used;
   return EDA_OK;
 }
 
@@ -1003,12 +1118,14 @@ int pcg_loop(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* i
   if (rc) return rc;
   CU(h, eda::pcg_first_dir<double>(n, M, h->r, h->z, h->pv, h->sc, h->active, h->st));
   constexpr int R = eda_handle::kRing;
+  // every member stops at convergence or at its own maxit-th iteration, so
+  // no loop needs more than maxit iterations
   int it = it0;
-  while (it < maxit) {
+  while (it - it0 < maxit) {
     ++it;
     rc = hvp_dev(h, h->cols, M, h->pv, h->q, 1, sweep64, h->active);
     if (rc) return rc;
-    CU(h, eda::pcg_update<double, double>(n, M, it, h->pv, h->q, h->x, h->r, h->sc, h->active, tol, h->nactive,
+    CU(h, eda::pcg_update<double, double>(n, M, maxit, h->pv, h->q, h->x, h->r, h->sc, h->active, tol, h->nactive,
                                           fixed, h->st));
     rc = precond();
     if (rc) return rc;
@@ -1081,12 +1198,12 @@ EDA_API int eda_solve_batch(eda_handle* h, double tol, int maxit, const double* 
       eda::count_launch();
       true_res_kernel<<<M, 256, 0, h->st>>>(n, h->b, h->q, nullptr, h->r, h->sc, h->active,
                                            tol > 0.0 ? tol : 1e300, h->nactive, h->dstatus,
-                                           tau > 0.0 ? tau : 0.0);
+                                           tau > 0.0 ? tau : 0.0, maxit);
       CU(h, cudaGetLastError());
       int need = 0;
       rc = read_flag(h, h->dstatus, &need);
       if (rc) return rc;
-      if (need == 0 || it >= maxit || tol <= 0.0) break;
+      if (need == 0 || tol <= 0.0) break;
       rc = pcg_loop(h, tol, maxit, it, lmp, &it, false);
       if (rc) return rc;
     }

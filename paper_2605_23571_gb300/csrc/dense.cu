@@ -296,6 +296,105 @@ __global__ void nystrom_core_kernel(const double* W, const double* RY, int m, in
   }
 }
 
+// Eigendecomposition of a symmetric PSD m x m matrix held in M (one-sided
+// Jacobi: columns of M V become v_i mu_i); on return M's columns are the
+// unit eigenvectors scaled by f(mu_i) and mu[] the eigenvalues, where
+// f(mu) = mu^{pw} if mu > rtol * max(mu) else 0.
+__device__ void psd_eig_scaled(double* M, int m, double* mu, double pw, double rtol, int* rotated) {
+  jacobi_columns(M, m, rotated, 60);
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s += M[i + j * m] * M[i + j * m];
+    mu[j] = sqrt(s);
+  }
+  __syncthreads();
+  double mx = 0.0;
+  for (int j = 0; j < m; ++j) mx = fmax(mx, mu[j]);
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int j = idx / m;
+    const double u = mu[j];
+    const double f = (u > rtol * mx && u > 0.0) ? pow(u, pw) / u : 0.0;  // unit vector times u^pw
+    M[idx] *= f;
+  }
+  __syncthreads();
+}
+
+// Robust core of Algorithm 1 for a numerically rank-deficient sketch
+// (Appendix B, truncated eigendecomposition), in two one-CTA steps around
+// two tall-skinny GEMMs done by the caller:
+//   (1) W = U mu U^T (symmetrised W = Phi^T Y); M = U mu^{-1/2} over the
+//       eigenvalues mu > rtol * max(mu), zero columns elsewhere, so that
+//       A_N = Y W^+ Y^T = Z Z^T with Z = Y M;
+//   (2) K = Z^T Z = V D V^T; the eigenvectors of A_N are S = Z V D^{-1/2}
+//       and its eigenvalues D.  Only modes with D > rtol * max(D) carry
+//       information, so k_eff = min(k, their count); SB (m x k) = V D^{-1/2}
+//       for the first k_eff modes (descending D) and zero beyond, D and c
+//       zero beyond k_eff, theta taken at mode k_eff (lambda = 1 if k_eff =
+//       0); *rank_out = k_eff.
+// Working from Z rather than from the Gram matrix Y^T Y keeps the small
+// modes: Y^T Y squares the condition number of Y and loses every singular
+// value below sqrt(eps) of the largest.
+__global__ void robust_winv_kernel(const double* W, int m, double rtol, double* M) {
+  extern __shared__ double sm[];
+  double* Ms = sm;           // m x m
+  double* mu = sm + m * m;   // m
+  __shared__ int rotated;
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int i = idx % m, j = idx / m;
+    Ms[idx] = 0.5 * (W[idx] + W[j + i * m]);
+  }
+  __syncthreads();
+  psd_eig_scaled(Ms, m, mu, -0.5, rtol, &rotated);
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) M[idx] = Ms[idx];
+}
+
+__global__ void robust_eig_kernel(const double* K, int m, int k, double rtol, int theta_mode, double theta_given,
+                                  double* SB, double* D, double* cvec, double* theta_out, int* rank_out) {
+  extern __shared__ double sm[];
+  double* Ms = sm;           // m x m: K -> V D^{-1/2}
+  double* ev = sm + m * m;   // m
+  int* order = reinterpret_cast<int*>(ev + m);
+  __shared__ int rotated;
+  __shared__ int keff;
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int i = idx % m, j = idx / m;
+    Ms[idx] = 0.5 * (K[idx] + K[j + i * m]);
+  }
+  __syncthreads();
+  psd_eig_scaled(Ms, m, ev, -0.5, rtol, &rotated);
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    int r = 0;
+    for (int i = 0; i < m; ++i) r += (ev[i] > ev[j]) || (ev[i] == ev[j] && i < j);
+    order[r] = j;
+  }
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    for (int j = 0; j < m; ++j) mx = fmax(mx, ev[j]);
+    int r = 0;
+    for (int j = 0; j < m; ++j) r += (ev[j] > rtol * mx && ev[j] > 0.0);
+    keff = r < k ? r : k;
+  }
+  __syncthreads();
+  const int ke = keff;
+  for (int idx = threadIdx.x; idx < m * k; idx += blockDim.x) {
+    const int i = idx % m, r = idx / m;
+    SB[i + (long long)r * m] = (r < ke) ? Ms[i + order[r] * m] : 0.0;
+  }
+  if (threadIdx.x == 0) {
+    double lamk = 1.0;
+    for (int r = 0; r < k; ++r) {
+      D[r] = (r < ke) ? ev[order[r]] : 0.0;
+      if (r == ke - 1) lamk = 1.0 + D[r];
+    }
+    double th = theta_given;
+    if (theta_mode == EDA_THETA_LAMBDA_K) th = lamk;
+    if (theta_mode == EDA_THETA_MID) th = 0.5 * (lamk + 1.0);
+    *theta_out = th;
+    for (int r = 0; r < k; ++r) cvec[r] = (r < ke) ? th / (1.0 + D[r]) - 1.0 : 0.0;
+    *rank_out = ke;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Batched PCG vector kernels: one CTA per member (column).
 // ---------------------------------------------------------------------------
@@ -371,7 +470,7 @@ __global__ void pcg_first_dir_kernel(int n, ItemGeo ig, const T* r, const T* z, 
 // After q = H p: alpha, x += alpha p, r -= alpha q, the residual norm and the
 // stopping test.
 template <typename T, typename TX>
-__global__ void pcg_update_kernel(int n, ItemGeo ig, int it, const T* p, const T* q, TX* x, T* r, PcgScalars* sc,
+__global__ void pcg_update_kernel(int n, ItemGeo ig, int maxit, const T* p, const T* q, TX* x, T* r, PcgScalars* sc,
                                   int* active, double tol, int* nactive, int fixed_iters) {
   __shared__ double red[32];
   const int j = blockIdx.x;
@@ -418,6 +517,9 @@ __global__ void pcg_update_kernel(int n, ItemGeo ig, int it, const T* p, const T
       }
     } else if (rel <= (sc[j].tolm > 0.0 ? sc[j].tolm : tol)) {
       sc[j].status = EDA_CONVERGED;
+      stop = true;
+    } else if (maxit > 0 && itj >= maxit) {  // this member's own budget
+      sc[j].status = EDA_MAXIT;
       stop = true;
     }
     if (stop) {
@@ -553,6 +655,25 @@ cudaError_t nystrom_core(const double* W, const double* RY, int m, int k, double
   return cudaGetLastError();
 }
 
+cudaError_t robust_winv(const double* W, int m, double rtol, double* M, cudaStream_t s) {
+  const size_t smem = ((size_t)m * m + m) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(robust_winv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  robust_winv_kernel<<<1, 1024, smem, s>>>(W, m, rtol, M);
+  return cudaGetLastError();
+}
+
+cudaError_t robust_eig(const double* K, int m, int k, double rtol, int theta_mode, double theta_given, double* SB,
+                       double* D, double* cvec, double* theta_out, int* rank_out, cudaStream_t s) {
+  const size_t smem = ((size_t)m * m + m) * sizeof(double) + (size_t)m * sizeof(int);
+  cudaError_t e = cudaFuncSetAttribute(robust_eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  robust_eig_kernel<<<1, 1024, smem, s>>>(K, m, k, rtol, theta_mode, theta_given, SB, D, cvec, theta_out, rank_out);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t pcg_start(int n, int m, const double* b, const T* r, PcgScalars* sc, int* active, double tol,
                       int* nactive, cudaStream_t s, const int* n_of, const long long* off_of) {
@@ -570,11 +691,11 @@ cudaError_t pcg_first_dir(int n, int m, const T* r, const T* z, T* p, PcgScalars
 }
 
 template <typename T, typename TX>
-cudaError_t pcg_update(int n, int m, int it, const T* p, const T* q, TX* x, T* r, PcgScalars* sc, int* active,
+cudaError_t pcg_update(int n, int m, int maxit, const T* p, const T* q, TX* x, T* r, PcgScalars* sc, int* active,
                        double tol, int* nactive, int fixed_iters, cudaStream_t s, const int* n_of,
                        const long long* off_of) {
   count_launch();
-  pcg_update_kernel<T, TX><<<m, 256, 0, s>>>(n, ItemGeo{n_of, off_of}, it, p, q, x, r, sc, active, tol, nactive,
+  pcg_update_kernel<T, TX><<<m, 256, 0, s>>>(n, ItemGeo{n_of, off_of}, maxit, p, q, x, r, sc, active, tol, nactive,
                                              fixed_iters);
   return cudaGetLastError();
 }

@@ -31,6 +31,15 @@ cudaError_t tri_mul(const double* A, const double* B, double* P, int m, cudaStre
 cudaError_t nystrom_core(const double* W, const double* RY, int m, int k, double nu, int theta_mode,
                          double theta_given, double* UT, double* D, double* cvec, double* theta_out,
                          int* status, cudaStream_t s);
+// Algorithm 1 core for a numerically rank-deficient sketch (truncated
+// eigendecompositions, Appendix B), around two caller GEMMs:
+// robust_winv: M [m x m] = U mu^{-1/2} over W's eigenvalues above rtol*max
+// (zero columns elsewhere); the caller forms Z = Y M and K = Z^T Z;
+// robust_eig: SB [m x k] = V D^{-1/2} for the first k_eff modes of K =
+// V D V^T (S = Z SB), D, c, theta, *rank_out = k_eff.
+cudaError_t robust_winv(const double* W, int m, double rtol, double* M, cudaStream_t s);
+cudaError_t robust_eig(const double* K, int m, int k, double rtol, int theta_mode, double theta_given, double* SB,
+                       double* D, double* cvec, double* theta_out, int* rank_out, cudaStream_t s);
 // Batched PCG vector kernels, one CTA per item.  With n_of/off_of, item j
 // has length n_of[j] at offset off_of[j]; otherwise length n at j*n.
 template <typename T>
@@ -39,8 +48,9 @@ cudaError_t pcg_start(int n, int m, const double* b, const T* r, PcgScalars* sc,
 template <typename T>
 cudaError_t pcg_first_dir(int n, int m, const T* r, const T* z, T* p, PcgScalars* sc, const int* active,
                           cudaStream_t s, const int* n_of = nullptr, const long long* off_of = nullptr);
+// maxit > 0: a member stops (status EDA_MAXIT) once its own count reaches it.
 template <typename T, typename TX>
-cudaError_t pcg_update(int n, int m, int it, const T* p, const T* q, TX* x, T* r, PcgScalars* sc, int* active,
+cudaError_t pcg_update(int n, int m, int maxit, const T* p, const T* q, TX* x, T* r, PcgScalars* sc, int* active,
                        double tol, int* nactive, int fixed_iters, cudaStream_t s, const int* n_of = nullptr,
                        const long long* off_of = nullptr);
 template <typename T>

@@ -93,6 +93,13 @@ struct SweepArgs {
   T* rd_out;             // [col][p] or nullptr: R^{-1} d
   // plan
   int CS, Ttile, HL, E, K;
+  // multi-launch mode (n too large for one cluster): CS tiles per column
+  // without a cluster, this launch runs forward steps [f0, f1) and backward
+  // steps b1-1 down to b0, loading the state of its extended region from
+  // st_in [col][n] and storing its owned tile to st_out [col][n]
+  int ml, f0, f1, b1, b0;
+  const T* st_in;
+  T* st_out;
   // group launch (uneven batching): when items != nullptr, column c of the
   // launch is items[c] and every problem field above comes from probs[prob]
   const SweepProb<T>* probs;
@@ -103,6 +110,7 @@ struct SweepArgs {
 struct SweepPlan {
   int CS, C, A, E, Ttile, HL, K;
   size_t smem;
+  int ml;  // 1: multi-launch tiles of K steps (no cluster), CS = tiles per column
 };
 
 // Picks the tiling of a sweep for state size n (elem_bytes = sizeof(T)):
@@ -113,6 +121,11 @@ bool plan_sweep(int n, int elem_bytes, int w, int min_cs, int K_hint, SweepPlan*
 // Dynamic shared memory of a sweep launch with A threads, runs of C and
 // at most w+1 taps.
 size_t sweep_smem_bytes(int A, int C, int w, int elem_bytes);
+
+// A multi-launch plan: tiles of A*C - 2HL owned points, K steps per launch,
+// A threads per CTA (A = 0: 512 for FP64, 256 for FP32; else a multiple of
+// 32 up to 512).
+bool plan_sweep_ml(int n, int elem_bytes, int w, int K, int A, SweepPlan* out);
 
 // The plan with exactly cluster size CS and refresh period K, if it fits.
 bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* out);
@@ -125,8 +138,10 @@ bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* ou
 void obs_table(const SweepPlan& p, int n, int nos, const int* obs_ptr, const int* obs_idx,
                int* tab /* [CS*nos*8] */, bool* usable);
 
-// Launches the sweep for `ncol` columns.  Returns a cudaError_t.
+// Launches the sweep for `ncol` columns.  Returns a cudaError_t.  A
+// multi-launch plan needs ml_buf: two state buffers of ncol * n values.
 template <typename T>
-cudaError_t launch_sweep(const SweepArgs<T>& a, const SweepPlan& plan, cudaStream_t s);
+cudaError_t launch_sweep(const SweepArgs<T>& a, const SweepPlan& plan, cudaStream_t s, T* ml_buf0 = nullptr,
+                         T* ml_buf1 = nullptr);
 
 }  // namespace eda

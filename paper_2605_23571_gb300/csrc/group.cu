@@ -80,6 +80,8 @@ struct eda_group {
   // captured PCG iteration
   cudaGraphExec_t gexec = nullptr;
   int g_key = -1;
+  double g_tol = -1.0;
+  int g_maxit = -1;
   std::vector<void*> allocs;
 };
 
@@ -119,7 +121,7 @@ int leave(eda_group* g) {
 // ---------------------------------------------------------------- kernels
 __global__ void g_true_res_kernel(const int* n_of, const long long* off_of, const double* b, const double* hx,
                                   double* r, PcgScalars* sc, int* active, double tol, int* nactive, int* need,
-                                  double tau) {
+                                  double tau, int maxit) {
   __shared__ double red[32];
   const int j = blockIdx.x;
   const int n = n_of[j];
@@ -143,10 +145,12 @@ __global__ void g_true_res_kernel(const int* n_of, const long long* off_of, cons
     const bool ok = (bn == 0.0) || (rel <= tol);
     if (sc[j].status == EDA_CONVERGED && !ok) {
       sc[j].status = EDA_MAXIT;
-      sc[j].tolm = fmax(tol, tau * rel);
-      active[j] = 1;
-      atomicAdd(nactive, 1);
-      atomicAdd(need, 1);
+      if (sc[j].iters < maxit) {  // next refinement round, within the member's budget
+        sc[j].tolm = fmax(tol, tau * rel);
+        active[j] = 1;
+        atomicAdd(nactive, 1);
+        atomicAdd(need, 1);
+      }
     }
   }
 }
@@ -219,6 +223,10 @@ int plan_group(eda_group* g, bool fp64, const std::vector<int>& Kp) {
     for (int CS = 1; CS <= 16 && !ok; ++CS) ok = eda::plan_sweep_exact(h->n, eb, h->w, CS, Kp[pi], &pl);
     if (!ok && !eda::plan_sweep(h->n, eb, h->w, 1, 0, &pl))
       return gfail(g, EDA_ERR_INVALID, "group: a problem does not fit the sweep tiling");
+    if (pl.ml)
+      return gfail(g, EDA_ERR_INVALID,
+                   "group: problem " + std::to_string(pi) + " (n = " + std::to_string(h->n) +
+                       ") needs multi-launch sweeps; solve it on its own handle");
     plans[pi] = pl;
     int Ab = 32;
     while (Ab < pl.A) Ab *= 2;
@@ -378,10 +386,10 @@ int group_sweep(eda_group* g, bool fp64, const double* V, double* HV, int ident,
 }
 
 // The work of one PCG iteration of the whole group (captured into a graph).
-int group_iteration(eda_group* g, bool sweep64, bool use_lmp, double tol, int fixed) {
+int group_iteration(eda_group* g, bool sweep64, bool use_lmp, double tol, int maxit, int fixed) {
   int rc = group_sweep(g, sweep64, g->p, g->q, 1, false);
   if (rc) return rc;
-  GCU(g, eda::pcg_update<double, double>(0, g->T, 0, g->p, g->q, g->x, g->r, g->sc, g->active, tol, g->nactive,
+  GCU(g, eda::pcg_update<double, double>(0, g->T, maxit, g->p, g->q, g->x, g->r, g->sc, g->active, tol, g->nactive,
                                          fixed, g->st, g->d_n_of, g->d_off_of));
   if (use_lmp) {
     if (sweep64)
@@ -419,31 +427,36 @@ int group_pcg_loop(eda_group* g, bool sweep64, bool use_lmp, double tol, int max
   GCU(g, eda::pcg_first_dir<double>(0, g->T, g->r, g->z, g->p, g->sc, g->active, g->st, g->d_n_of, g->d_off_of));
   const int key = (sweep64 ? 1 : 0) + (use_lmp ? 2 : 0) + (fixed ? 4 : 0);
   const bool use_graph = eda::env_int("EDA_GROUP_GRAPH", 1) != 0 && fixed == 0;
-  if (use_graph && (g->gexec == nullptr || g->g_key != key)) {
+  // the graph bakes in tol and maxit as kernel arguments
+  if (use_graph && (g->gexec == nullptr || g->g_key != key || g->g_tol != tol || g->g_maxit != maxit)) {
     if (g->gexec) {
       cudaGraphExecDestroy(g->gexec);
       g->gexec = nullptr;
     }
     cudaGraph_t graph;
     GCU(g, cudaStreamBeginCapture(g->st, cudaStreamCaptureModeRelaxed));
-    rc = group_iteration(g, sweep64, use_lmp, tol, fixed);
+    rc = group_iteration(g, sweep64, use_lmp, tol, maxit, fixed);
     cudaError_t ce = cudaStreamEndCapture(g->st, &graph);
     if (rc) return rc;
     GCU(g, ce);
     GCU(g, cudaGraphInstantiate(&g->gexec, graph, 0));
     cudaGraphDestroy(graph);
     g->g_key = key;
+    g->g_tol = tol;
+    g->g_maxit = maxit;
   }
   constexpr int R = 4;
+  // every member stops at convergence or at its own maxit-th iteration, so
+  // no loop needs more than maxit iterations
   int it = *it_io;
   const int it0 = it;
-  while (it < maxit) {
+  while (it - it0 < maxit) {
     ++it;
     if (use_graph) {
       eda::count_launch(3 + (int)(sweep64 ? g->b64.size() : g->b32.size()));
       GCU(g, cudaGraphLaunch(g->gexec, g->st));
     } else {
-      rc = group_iteration(g, sweep64, use_lmp, tol, fixed);
+      rc = group_iteration(g, sweep64, use_lmp, tol, maxit, fixed);
       if (rc) return rc;
     }
     const int slot = it % R;
@@ -753,13 +766,14 @@ EDA_API int eda_group_solve(eda_group* g, double tol, int maxit, int use_lmp, do
       GCU(g, cudaMemsetAsync(g->active, 0, (size_t)g->T * sizeof(int), g->st));
       eda::count_launch();
       g_true_res_kernel<<<g->T, 256, 0, g->st>>>(g->d_n_of, g->d_off_of, g->b, g->q, g->r, g->sc, g->active,
-                                                 tol > 0.0 ? tol : 1e300, g->nactive, g->dflag, tau > 0.0 ? tau : 0.0);
+                                                 tol > 0.0 ? tol : 1e300, g->nactive, g->dflag, tau > 0.0 ? tau : 0.0,
+                                                 maxit);
       GCU(g, cudaGetLastError());
       int need = 0;
       GCU(g, cudaMemcpyAsync(g->hring, g->dflag, sizeof(int), cudaMemcpyDeviceToHost, g->st));
       GCU(g, cudaStreamSynchronize(g->st));
       need = g->hring[0];
-      if (need == 0 || it >= maxit || tol <= 0.0) break;
+      if (need == 0 || tol <= 0.0) break;
       rc = group_pcg_loop(g, false, use_lmp != 0, tol, maxit, &it);
       if (rc) return rc;
     }

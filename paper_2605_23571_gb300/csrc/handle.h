@@ -74,7 +74,13 @@ struct eda_handle {
   int stash_cols = 0;
   // state
   bool have_traj = false, have_sketch = false, have_lmp = false;
+  // state buffers of multi-launch sweeps (n too large for one cluster)
+  double* ml64[2] = {nullptr, nullptr};
+  float* ml32[2] = {nullptr, nullptr};
+  long long ml64_cap = 0, ml32_cap = 0;
   double shift_used = 0.0;
+  int nystrom_path = 0;  // 0 Cholesky, 1 Appendix B shift, 2 truncated eigendecomposition
+  int lmp_rank = 0;      // informative LMP modes (k, or k_eff on path 2)
   SweepPlan plan64{}, plan32{};
   int* tab64 = nullptr;  // per-CTA observation ranges of plan64 / plan32
   int* tab32 = nullptr;
@@ -92,6 +98,9 @@ int fail(eda_handle* h, int code, const std::string& msg);
 bool is_device_ptr(const void* ptr);
 // Installs a sweep tiling of the handle and its observation table.
 int set_plan(eda_handle* h, bool fp64, const SweepPlan& pl);
+// State buffers for a multi-launch sweep of ncol columns (no-op for
+// cluster plans); grows the handle's buffers when needed.
+int ensure_ml(eda_handle* h, int ncol, bool fp64);
 // Reads one device int (synchronises the stream).
 int read_flag(eda_handle* h, const int* dflag, int* out);
 // Integer environment variable (tiling overrides, diagnostics).

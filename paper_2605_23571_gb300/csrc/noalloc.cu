@@ -48,6 +48,9 @@ EDA_API int eda_hvp_noalloc(eda_handle* h, const int* member_of_col, int ncol, c
   if (!eda::is_device_ptr(member_of_col) || !eda::is_device_ptr(V) || !eda::is_device_ptr(HV))
     return eda::fail(h, EDA_ERR_INVALID, "eda_hvp_noalloc: member_of_col, V and HV must be device memory");
   const bool fp64 = (h->precision == EDA_FP64);
+  if ((fp64 ? h->plan64 : h->plan32).ml)
+    return eda::fail(h, EDA_ERR_INVALID,
+                     "eda_hvp_noalloc: this state size needs multi-launch sweeps with state buffers; use eda_hvp");
   const long long need = (long long)ncol * (long long)h->p;  // stash entries
   if (need > eda_hvp_noalloc_capacity(fp64 ? 1 : 0))
     return eda::fail(h, EDA_ERR_INVALID,

@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   SweepArgs<T> a = a0;
   Geo g;
   g.CS = a.CS;
-  g.rank = (a.CS > 1) ? (int)cg::this_cluster().block_rank() : 0;
+  g.rank = (a.CS > 1) ? (a.ml ? (int)(blockIdx.x % a.CS) : (int)cg::this_cluster().block_rank()) : 0;
   const int col = blockIdx.x / a.CS;
   if (col >= a.ncol) return;
   // launch-wide shared-memory layout (the group launch sizes it for its largest problem)
@@ -425,18 +425,33 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
 
   const T F = a.F, h = a.dt;
   const T h2 = h * T(0.5), h6 = h / T(6), h3 = h / T(3);
-  const bool clus = a.CS > 1;
+  const bool clus = a.CS > 1 && !a.ml;
+  const int f0 = a.ml ? a.f0 : 0, f1 = a.ml ? a.f1 : N;
+  const int b0 = a.ml ? a.b0 : 0, b1 = a.ml ? a.b1 : N;
+  // owned tile of a register run -> row[a0 .. a0 + Town) (through the mirror)
+  auto store_owned = [&](const T (&v)[C], T* row) {
+    write_mirror(mir, g, v);
+    __syncthreads();
+    for (int j = g.tid; j < g.Town; j += g.NT) row[g.a0 + j] = mir[g.HL + j];
+    __syncthreads();
+  };
   __syncthreads();
 
   if (a.mode == MODE_NL) {
     // ---------------------------------------------------------------- nonlinear
     T x[C];
-    const T* x0row = a.x0 + voff;
-    const bool x0_vec = vec_ok && ((reinterpret_cast<unsigned long long>(x0row) & 15ull) == 0);
-    load_run<T, C>(x0row, gi, x0_vec, x);
     T* tout = a.traj_out ? a.traj_out + (long long)member * a.traj_out_mstride : nullptr;
-    for (int t = 0; t <= N; ++t) {
-      if (t > 0) {
+    {
+      // x_f0: the initial state, or (later launches of a multi-launch sweep)
+      // the state the previous launch stored in the trajectory
+      const T* x0row = (f0 == 0)        ? a.x0 + voff
+                       : (tout != nullptr) ? tout + (long long)f0 * a.n
+                                           : a.st_in + (long long)col * a.n;
+      const bool x0_vec = vec_ok && ((reinterpret_cast<unsigned long long>(x0row) & 15ull) == 0);
+      load_run<T, C>(x0row, gi, x0_vec, x);
+    }
+    for (int t = f0; t <= f1; ++t) {
+      if (t > f0) {
         Run<T, C> X;
         T X1[C], acc[C], Xs[C];
 #pragma unroll
@@ -484,9 +499,10 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
           x[c] = X1[c] + h6 * acc[c];
         }
       }
-      const int oj = obs_at(t);
+      const bool fresh = (t > f0) || (f0 == 0);  // x_t not yet stored / observed
+      const int oj = fresh ? obs_at(t) : -1;
       const bool refresh = (t > 0) && (t % a.K == 0) && (t < N);
-      const bool store = (tout != nullptr) || (t == N && a.final_out != nullptr);
+      const bool store = fresh && ((tout != nullptr) || (t == N && a.final_out != nullptr));
       if (oj >= 0 || refresh || store) {
         write_mirror(mir, g, x);
         sync_cluster_or_block(refresh && clus);
@@ -523,6 +539,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       publish(eb[0], g, x);
       __syncthreads();
     }
+    if (a.ml && tout == nullptr && f1 < N) store_owned(x, a.st_out + (long long)col * a.n);
     return;
   }
 
@@ -533,7 +550,9 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   T* stash = a.stash + soff;
   T xr[C];  // own run of x_t (registers)
 
-  if (a.mode == MODE_HVP) {
+  if (a.mode == MODE_HVP && f1 > f0) {
+    T dl[C];
+    if (f0 == 0) {
     // delta_0 = U_B v on the extended region (v staged with a w-halo)
     {
       const int cnt = g.E + 2 * w;
@@ -544,7 +563,6 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       }
       __syncthreads();
     }
-    T dl[C];
     conv_run<T, C>(stage, g.l0, w, cf, dl);
     load_run<T, C>(trj, gi, vec_ok, xr);
     __syncthreads();  // the stage area becomes the edge buffers
@@ -553,14 +571,19 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       __syncthreads();
       gather_obs(a, g, obs_at(0), mir, stash);
     }
+    } else {
+      // later launch of a multi-launch sweep: the state of the extended region
+      load_run<T, C>(a.st_in + (long long)col * a.n, gi, vec_ok, dl);
+      load_run<T, C>(trj + (long long)f0 * a.n, gi, vec_ok, xr);
+    }
     publish(eb[0], g, dl);
     publish(eb[5], g, xr);
     __syncthreads();
 
     // ------------------------------------------------ tangent linear, forward
-    for (int t = 0; t < N; ++t) {
+    for (int t = f0; t < f1; ++t) {
       T pf[C];
-      if (t + 1 < N) load_run<T, C>(trj + (long long)(t + 1) * a.n, gi, vec_ok, pf);
+      if (t + 1 < f1) load_run<T, C>(trj + (long long)(t + 1) * a.n, gi, vec_ok, pf);
       Run<T, C> X, e;
       T Xs[C], es[C], acc[C];
       // stage 1: slopes at X1 = x_t
@@ -634,7 +657,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
         acc[c] += dk;
         dl[c] += h6 * acc[c];
       }
-      if (t + 1 < N) {
+      if (t + 1 < f1) {
 #pragma unroll
         for (int c = 0; c < C; ++c) xr[c] = pf[c];
       }
@@ -655,7 +678,9 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     }
     // the stash written by every CTA of the cluster must be visible to all
     if (clus) cg::this_cluster().sync();
+    if (a.ml && f1 < N) store_owned(dl, a.st_out + (long long)col * a.n);
   }
+  if (b1 <= b0) return;  // a forward-only launch of a multi-launch sweep
 
   // ------------------------------------------------------ adjoint, backward
   T lam[C];
@@ -685,13 +710,17 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     add_mirror<T, C>(mir, g, lam);
   };
 
-  if (obs_at(N) >= 0) inject(obs_at(N));
-  load_run<T, C>(trj + (long long)(N - 1) * a.n, gi, vec_ok, xr);
+  if (b1 == N) {
+    if (obs_at(N) >= 0) inject(obs_at(N));
+  } else {
+    load_run<T, C>(a.st_in + (long long)col * a.n, gi, vec_ok, lam);
+  }
+  load_run<T, C>(trj + (long long)(b1 - 1) * a.n, gi, vec_ok, xr);
   publish(eb[0], g, xr);
   __syncthreads();
-  for (int t = N - 1; t >= 0; --t) {
+  for (int t = b1 - 1; t >= b0; --t) {
     T pf[C];
-    if (t > 0) load_run<T, C>(trj + (long long)(t - 1) * a.n, gi, vec_ok, pf);
+    if (t > b0) load_run<T, C>(trj + (long long)(t - 1) * a.n, gi, vec_ok, pf);
     Run<T, C> X1, X, wv;
     T X2[C], X3[C], X4[C], ln[C], ad[C];
     // forward recomputation of the stage states
@@ -774,7 +803,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     fetch(eb[4], g, wv);
 #pragma unroll
     for (int c = 0; c < C; ++c) lam[c] = ln[c] + jtvp(X1, wv, c);
-    if (t > 0) {
+    if (t > b0) {
 #pragma unroll
       for (int c = 0; c < C; ++c) xr[c] = pf[c];
     }
@@ -791,6 +820,10 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     __syncthreads();
   }
 
+  if (a.ml) {  // multi-launch: the state goes to global memory; U_B follows in its own kernel
+    store_owned(lam, a.st_out + (long long)col * a.n);
+    return;
+  }
   // ---------------------------------------------- output U_B lambda_0 (+ v)
   write_mirror(mir, g, lam);
   sync_cluster_or_block(clus);
@@ -800,6 +833,30 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
                                      ident ? V : nullptr);
   } else {
     bhalf_from_mirrors<T, C, T>(a, g, mir, stage, cf, a.OUT + voff, ident ? V64 : nullptr, ident ? V : nullptr);
+  }
+}
+
+// out[col][i] = (ident ? v[col][i] : 0) + sum_{|d|<=w} coef[|d|] lam[col][(i+d) mod n]
+// (the last step of a multi-launch Hessian product or right-hand side).
+template <typename T, typename TO>
+__global__ void bhalf_out_kernel(int n, int w, const T* __restrict__ coef, int ncol, const T* __restrict__ lam,
+                                 const double* v64, const T* v, TO* out, int ident) {
+  const long long total = (long long)ncol * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(e % n);
+    const T* row = lam + (e - i);
+    T acc = coef[0] * row[i];
+    for (int d = 1; d <= w; ++d) {
+      int im = i - d;
+      if (im < 0) im += n;
+      int ip = i + d;
+      if (ip >= n) ip -= n;
+      acc += coef[d] * (row[im] + row[ip]);
+    }
+    TO o = (TO)acc;
+    if (ident) o += v64 ? (TO)v64[e] : (TO)v[e];
+    out[e] = o;
   }
 }
 
@@ -822,7 +879,7 @@ cudaError_t launch_impl(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t 
   cfg.dynamicSmemBytes = p.smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
-  if (p.CS > 1) {
+  if (p.CS > 1 && !p.ml) {
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)p.CS;
     attr[0].val.clusterDim.y = 1;
@@ -846,6 +903,7 @@ size_t sweep_smem_bytes(int A, int C, int w, int elem_bytes) {
 
 bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* out) {
   const int C = (elem_bytes == 8) ? 4 : 8;
+  out->ml = 0;
   if (CS < 1 || CS > 16 || K < 1) return false;
   const int Ttile = (n + CS - 1) / CS;
   if ((CS - 1) * Ttile >= n) return false;
@@ -868,12 +926,37 @@ bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* ou
   return true;
 }
 
+bool plan_sweep_ml(int n, int elem_bytes, int w, int K, int A, SweepPlan* out) {
+  const int C = (elem_bytes == 8) ? 4 : 8;
+  if (A <= 0) A = (elem_bytes == 8) ? 512 : 256;
+  if (A % 32 != 0 || A > kMaxThreads) return false;
+  const int E = A * C;
+  const int HL = 8 * K + 8;
+  const int Ttile = E - 2 * HL;
+  if (K < 1 || Ttile < 64) return false;
+  const size_t smem = sweep_smem_bytes(A, C, w, elem_bytes);
+  if (smem > 227 * 1024) return false;
+  out->CS = (n + Ttile - 1) / Ttile;
+  out->C = C;
+  out->A = A;
+  out->E = E;
+  out->Ttile = Ttile;
+  out->HL = HL;
+  out->K = K;
+  out->smem = smem;
+  out->ml = 1;
+  return true;
+}
+
 bool plan_sweep(int n, int elem_bytes, int w, int min_cs, int K_hint, SweepPlan* out) {
   for (int CS = (min_cs > 1 ? min_cs : 1); CS <= 16; ++CS) {
     const int K = K_hint > 0 ? K_hint : (CS == 1 ? 4 : 8);
-    if (plan_sweep_exact(n, elem_bytes, w, CS, K, out)) return true;
+    if (plan_sweep_exact(n, elem_bytes, w, CS, K, out)) {
+      out->ml = 0;
+      return true;
+    }
   }
-  return false;
+  return plan_sweep_ml(n, elem_bytes, w, K_hint > 0 ? K_hint : 16, 0, out);
 }
 
 void obs_table(const SweepPlan& p, int n, int nos, const int* obs_ptr, const int* obs_idx, int* tab,
@@ -918,14 +1001,7 @@ void obs_table(const SweepPlan& p, int n, int nos, const int* obs_ptr, const int
 }
 
 template <typename T>
-cudaError_t launch_sweep(const SweepArgs<T>& a0, const SweepPlan& p, cudaStream_t s) {
-  SweepArgs<T> a = a0;
-  a.CS = p.CS;
-  a.Ttile = p.Ttile;
-  a.HL = p.HL;
-  a.E = p.E;
-  a.K = p.K;
-  if (a.ncol <= 0) return cudaSuccess;
+cudaError_t launch_one(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t s) {
   if constexpr (sizeof(T) == 8) {
     if (p.C != 4) return cudaErrorInvalidValue;
     return launch_impl<T, 4>(a, p, s);
@@ -935,7 +1011,81 @@ cudaError_t launch_sweep(const SweepArgs<T>& a0, const SweepPlan& p, cudaStream_
   }
 }
 
-template cudaError_t launch_sweep<double>(const SweepArgs<double>&, const SweepPlan&, cudaStream_t);
-template cudaError_t launch_sweep<float>(const SweepArgs<float>&, const SweepPlan&, cudaStream_t);
+template <typename T>
+cudaError_t launch_sweep(const SweepArgs<T>& a0, const SweepPlan& p, cudaStream_t s, T* ml_buf0, T* ml_buf1) {
+  SweepArgs<T> a = a0;
+  a.CS = p.CS;
+  a.Ttile = p.Ttile;
+  a.HL = p.HL;
+  a.E = p.E;
+  a.K = p.K;
+  if (a.ncol <= 0) return cudaSuccess;
+  if (!p.ml) {
+    a.ml = 0;
+    return launch_one<T>(a, p, s);
+  }
+  // multi-launch: chunks of K steps, the state of every column through two
+  // global buffers (the launch boundary replaces the halo exchange)
+  if (a.items != nullptr || ml_buf0 == nullptr || ml_buf1 == nullptr) return cudaErrorInvalidValue;
+  // the closing U_B kernel indexes vectors as contiguous [col][n] rows
+  if (a.mode != MODE_NL && (a.out_stride != a.n || (a.mode == MODE_HVP && a.v_stride != a.n)))
+    return cudaErrorInvalidValue;
+  a.ml = 1;
+  a.K = 1 << 30;  // no in-launch refresh
+  const int N = a.N, K = p.K;
+  T* buf[2] = {ml_buf0, ml_buf1};
+  int cur = 0;
+  if (a.mode == MODE_NL) {
+    for (int t0 = 0; t0 < N; t0 += K) {
+      a.f0 = t0;
+      a.f1 = (t0 + K < N) ? t0 + K : N;
+      a.b0 = a.b1 = 0;
+      a.st_in = buf[cur];
+      a.st_out = buf[1 - cur];
+      cudaError_t e = launch_one<T>(a, p, s);
+      if (e != cudaSuccess) return e;
+      cur = 1 - cur;
+    }
+    return cudaSuccess;
+  }
+  if (a.mode == MODE_HVP) {
+    for (int t0 = 0; t0 < N; t0 += K) {
+      a.f0 = t0;
+      a.f1 = (t0 + K < N) ? t0 + K : N;
+      a.b0 = a.b1 = 0;
+      a.st_in = buf[cur];
+      a.st_out = buf[1 - cur];
+      cudaError_t e = launch_one<T>(a, p, s);
+      if (e != cudaSuccess) return e;
+      cur = 1 - cur;
+    }
+  }
+  for (int t1 = N; t1 > 0; t1 -= K) {
+    a.f0 = a.f1 = 0;
+    a.b1 = t1;
+    a.b0 = (t1 - K > 0) ? t1 - K : 0;
+    a.st_in = buf[cur];
+    a.st_out = buf[1 - cur];
+    cudaError_t e = launch_one<T>(a, p, s);
+    if (e != cudaSuccess) return e;
+    cur = 1 - cur;
+  }
+  // U_B lambda_0 (+ v)
+  const long long total = (long long)a.ncol * a.n;
+  long long blocks = (total + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  const int ident = (a.mode == MODE_HVP && a.include_identity) ? 1 : 0;
+  count_launch();
+  if (a.OUT64)
+    bhalf_out_kernel<T, double><<<(unsigned)blocks, 256, 0, s>>>(a.n, a.w, a.bcoef, a.ncol, buf[cur], a.V64, a.V,
+                                                                  a.OUT64, ident);
+  else
+    bhalf_out_kernel<T, T><<<(unsigned)blocks, 256, 0, s>>>(a.n, a.w, a.bcoef, a.ncol, buf[cur], a.V64, a.V, a.OUT,
+                                                            ident);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_sweep<double>(const SweepArgs<double>&, const SweepPlan&, cudaStream_t, double*, double*);
+template cudaError_t launch_sweep<float>(const SweepArgs<float>&, const SweepPlan&, cudaStream_t, float*, float*);
 
 }  // namespace eda

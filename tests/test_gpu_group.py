@@ -106,3 +106,42 @@ def test_group_mixed_precision_converges():
         ref = O.pcg(lambda V: O.hvp(s_, traj, V, taps), b, tol=1e-13, maxit=5000)["x"]
         e = np.linalg.norm(z - ref, axis=1)
         assert (e <= 1.01e-6 * np.linalg.norm(b, axis=1) + 1e-12).all()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_group_maxit_is_a_budget_per_member(precision):
+    # an easy problem (short window) and a hard one (long window, larger
+    # Hessian eigenvalues) in one group: with a budget the hard problem
+    # cannot meet, the easy problem's members must still converge, and every
+    # member's count stays within the budget
+    easy = S.spec_small(64, 6, 4, every_var=2, every_step=2, length_scale=2.0, seed=1)
+    hard = S.spec_small(200, 60, 4, every_var=1, every_step=1, length_scale=6.0, seed=2)
+    specs = [easy, hard]
+    for s_ in specs:
+        s_.spinup = 300
+    probs = [problem(s_) for s_ in specs]
+    prec = P.EDA_FP64 if precision == "fp64" else P.EDA_MIXED
+    hs = [P.Handle.from_spec(s_, taps, precision=prec) for s_, (taps, _, _) in zip(specs, probs)]
+    # each problem alone: the budget lies between what they need
+    need = []
+    for s_, (taps, xb, y) in zip(specs, probs):
+        with P.Handle.from_spec(s_, taps, precision=prec) as h:
+            h.eda_set_trajectory(xb, y)
+            itk = np.zeros(s_.n_members, np.int32)
+            h.eda_solve_batch(1e-8, 20000, None, False, np.zeros((s_.n_members, s_.n)), itk)
+            need.append(int(itk.max()))
+    assert need[1] > need[0] + 10, need
+    budget = (need[0] + need[1]) // 2
+    with P.Group(hs) as g:
+        g.eda_group_set_trajectories([xb for _, xb, _ in probs], [y for _, _, y in probs])
+        T = g.total_members
+        it = np.zeros(T, np.int32)
+        rr = np.zeros(T)
+        st = np.zeros(T, np.int32)
+        g.eda_group_solve(1e-8, budget, False, None, it, rr, st)
+    for h in hs:
+        h.close()
+    m0 = easy.n_members
+    assert (st[m0:] == P.EDA_MAXIT).any(), "the hard problem should not converge within the budget"
+    assert (st[:m0] == P.EDA_CONVERGED).all() and (rr[:m0] <= 1e-8).all(), (st, rr, it, budget)
+    assert (it <= budget).all()

@@ -103,6 +103,100 @@ def test_hvp_fp64_cluster_split(cs):
                 assert rowrel(HV, ref).max() < 1e-11, (cs, K)
 
 
+def _ml_spec(n, seed):
+    # observations at t = 0 and t = N as well as inside the window
+    N = 13
+    steps = np.array([0, 3, 6, 9, 12, 13], dtype=np.int32)
+    idx1 = np.arange(0, n, 2, dtype=np.int32)
+    return S.Spec(n=n, nsteps=N, obs_steps=steps,
+                  obs_ptr=(np.arange(len(steps) + 1) * len(idx1)).astype(np.int32),
+                  obs_idx=np.tile(idx1, len(steps)), sigma_o=1.0, sigma_b=1.0,
+                  length_scale=4.0, n_members=5, ell=4, k=4, spinup=5, seed=seed,
+                  name="l96_n%d_w13_m5" % n)
+
+
+# (n, threads per CTA, launch length K): FP64 tiles of 256 - 2(8K + 8) and
+# FP32 tiles of 512 - 2(8K + 8) owned points, so that one column spans 2 to 6
+# tiles with a ragged last tile; n = 997 also disables the 16-byte loads
+ML_CASES = [(600, 64, 2), (997, 64, 3), (1000, 128, 1)]
+
+
+@pytest.mark.parametrize("n,threads,K", ML_CASES)
+def test_multi_launch_sweeps_match_oracle(n, threads, K):
+    # sweeps of states too large for one cluster run as chains of K-step
+    # launches whose state passes through global memory; forced here at
+    # small n: twin (spin-up and trajectories), right-hand sides, products
+    # with and without the identity, the sketch and the LMP
+    spec = _ml_spec(n, seed=n)
+    taps = O.bhalf_taps(spec.n, spec.length_scale, spec.sigma_b)
+    dr = S.draws(spec)
+    _, xb, y = O.twin(spec, dr, taps)
+    traj, d, b = oracle_setup(spec, taps, xb, y)
+    rng = np.random.default_rng(n)
+    cols = np.array([0, 3, 1, 4, 2, 0, 3], dtype=np.int32)
+    V = rng.standard_normal((len(cols), spec.n))
+    ref = O.hvp(spec, traj[cols], V, taps)
+    refA = O.hvp(spec, traj[cols], V, taps, identity=False)
+    with env(EDA_SWEEP_ML=threads, EDA_SWEEP_K=K):
+        with make(spec, taps) as h:
+            xb_g = np.zeros((spec.n_members, spec.n))
+            y_g = np.zeros((spec.n_members, spec.p))
+            h.eda_twin(np.ascontiguousarray(spec.F + spec.spin_sigma * dr.eta_spin), spec.spinup,
+                       dr.eta_b, dr.eta_o, xb_g, y_g)
+            assert rel(xb_g, xb) < 1e-13 and rel(y_g, y) < 1e-13
+            rhs = np.zeros_like(b)
+            h.eda_set_trajectory(xb, y, rhs)
+            assert rowrel(rhs, b).max() < 1e-11
+            HV = np.zeros_like(V)
+            h.eda_hvp(cols, V, HV, True)
+            assert rowrel(HV, ref).max() < 1e-11
+            h.eda_hvp(cols, V, HV, False)
+            assert rowrel(HV, refA).max() < 1e-10
+            h.eda_sketch()
+            ev = np.zeros(spec.k)
+            h.eda_build_lmp(ev)
+            ro = O.eda_pipeline(spec, xb, y, taps, tol=1e-6, maxit=200)
+            np.testing.assert_allclose(ev, 1 + ro["D"], rtol=1e-9)
+        with make(spec, taps, precision=P.EDA_MIXED) as h:
+            h.eda_set_trajectory(xb, y)
+            HV = np.zeros_like(V)
+            h.eda_hvp(cols, V, HV, True)
+            assert rowrel(HV, ref).max() < 1e-4
+            h.eda_sketch()
+            h.eda_build_lmp()
+            dz = np.zeros_like(b)
+            rr = np.zeros(spec.n_members)
+            st = np.zeros(spec.n_members, np.int32)
+            h.eda_solve_batch(1e-8, 500, None, True, dz, None, rr, st)
+            assert (st == P.EDA_CONVERGED).all() and (rr <= 1e-8).all()
+            exact = O.eda_pipeline(spec, xb, y, taps, tol=1e-13, maxit=500)["x"]
+            bn = np.linalg.norm(b, axis=1)
+            assert (np.linalg.norm(dz - exact, axis=1) <= rr * bn * (1 + 1e-6) + 1e-12).all()
+
+
+def test_autotuned_tiling_keeps_parity():
+    # the autotuner times cluster and multi-launch tilings and keeps the
+    # fastest; whichever it keeps must give the same products
+    spec = S.spec_small(2500, 16, 6, every_var=2, every_step=2, length_scale=6.0, seed=9)
+    taps, xb, y = problem(spec)
+    traj, d, b = oracle_setup(spec, taps, xb, y)
+    cols = np.arange(spec.n_members, dtype=np.int32)
+    V = np.random.default_rng(2).standard_normal((spec.n_members, spec.n))
+    ref = O.hvp(spec, traj, V, taps)
+    with make(spec, taps, precision=P.EDA_MIXED) as h:
+        h.eda_set_trajectory(xb, y)
+        assert h.eda_autotune(3) > 0
+        HV = np.zeros_like(V)
+        h.eda_hvp(cols, V, HV, True)
+        assert rowrel(HV, ref).max() < 1e-4
+    with make(spec, taps) as h:
+        h.eda_set_trajectory(xb, y)
+        assert h.eda_autotune(1) > 0
+        HV = np.zeros_like(V)
+        h.eda_hvp(cols, V, HV, True)
+        assert rowrel(HV, ref).max() < 1e-11
+
+
 def test_hvp_obs_at_window_ends():
     # observations at t = 0 and t = N exercise the first gather and the first
     # injection of the sweeps
@@ -311,3 +405,54 @@ def test_full_size_batched_hvp_and_rhs_fp64():
         e32 = rowrel(HV, ref).max()
         print("FP32 sweep HVP rel err at n=4096, N=64: %.3e" % e32)
         assert e32 < 1e-4
+
+
+def test_rank_deficient_sketch_uses_the_truncated_eigendecomposition():
+    # a length scale comparable to n leaves B, and so Gamma, numerically rank
+    # deficient: Cholesky and the shift both break down and Algorithm 1 is
+    # completed with truncated eigendecompositions (Appendix B).  The
+    # approximation A_N = Y W^+ Y^T must match the oracle's on its
+    # significant part, and the preconditioned solve still converges.
+    n, N = 41, 10
+    steps, ptr, idx = S.regular_obs(n, N, 3, 2)
+    spec = S.Spec(n=n, nsteps=N, obs_steps=steps, obs_ptr=ptr, obs_idx=idx, sigma_o=1.0,
+                  sigma_b=1.0, length_scale=7.6, n_members=33, ell=32, k=31, spinup=300)
+    taps, xb, y = problem(spec)
+    ref = O.eda_pipeline(spec, xb, y, taps, tol=1e-6, maxit=500)
+    with make(spec, taps) as h:
+        h.eda_set_trajectory(xb, y)
+        h.eda_sketch()
+        ev = np.zeros(spec.k)
+        Sg = np.zeros((spec.k, spec.n))
+        h.eda_build_lmp(ev, Sg)
+        path, rank, shift = h.eda_lmp_info()
+        assert path == 2 and shift == 0.0
+        # the approximation's rank is below k: orthonormal eigenvectors up to
+        # it, zero columns (lambda = 1) beyond
+        r = int((ref["D"] > 0).sum())
+        assert rank < spec.k and abs(rank - r) <= 1
+        np.testing.assert_allclose(Sg[:rank] @ Sg[:rank].T, np.eye(rank), atol=1e-10)
+        assert not Sg[rank:].any() and (ev[rank:] == 1.0).all()
+        # a truncated pseudo-inverse amplifies rounding by 1/mu: the oracle's
+        # own small modes move under a 1e-16 perturbation of b, and two
+        # correct implementations agree only to that level (times a margin)
+        traj = ref["traj"]
+        f = lambda B_: O.apply_A(spec, np.broadcast_to(traj[0:1], (B_.shape[1],) + traj.shape[1:]),
+                                 B_.T.copy(), taps).T
+        sens = np.zeros(r)
+        for sd in range(4):
+            bp = ref["b"] * (1 + 1e-16 * np.random.default_rng(sd).standard_normal(ref["b"].shape))
+            Dp = O.nystrom(f, O.gamma(bp)[:, : spec.ell], spec.k)[1]
+            sens = np.maximum(sens, np.abs(Dp[:r] - ref["D"][:r]) / ref["D"][:r])
+        D = ev - 1
+        m = min(r, rank)
+        err = np.abs(D[:m] - ref["D"][:m]) / ref["D"][:m]
+        assert (err <= np.maximum(1e-9, 10.0 * sens[:m])).all(), (err, sens)
+        AN_g = (Sg.T * D) @ Sg
+        AN_o = (ref["S"] * ref["D"]) @ ref["S"].T
+        assert np.linalg.norm(AN_g - AN_o) <= 1e-6 * np.linalg.norm(AN_o)
+        dz = np.zeros((spec.n_members, spec.n))
+        st = np.zeros(spec.n_members, np.int32)
+        rr = np.zeros(spec.n_members)
+        h.eda_solve_batch(1e-6, 500, None, True, dz, None, rr, st)
+    assert (st == P.EDA_CONVERGED).all() and (rr <= 1e-6).all()

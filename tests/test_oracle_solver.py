@@ -297,7 +297,7 @@ def test_nystrom_truncated_evd_when_the_sketch_is_rank_deficient():
     # rank r of the approximation < k: the first r columns are orthonormal
     # eigenvectors, the remaining ones (and their D) are zero
     r = info["rank"]
-    assert r == keep.sum() < 31
+    assert r <= keep.sum() < 31 and D[r - 1] > 1e-12 * D[0]
     np.testing.assert_allclose(Sk[:, :r].T @ Sk[:, :r], np.eye(r), atol=1e-12)
     assert not Sk[:, r:].any() and not D[r:].any()
     AN = Y @ (V[:, keep] / mu[keep]) @ V[:, keep].T @ Y.T

@@ -73,3 +73,21 @@ def test_noalloc_rejects_host_memory_and_oversized_batches():
             h.eda_hvp_noalloc(cb, Vb, torch.empty_like(Vb), True)
         assert e.value.code == P.EDA_ERR_INVALID
         assert "exceed" in str(e.value)
+
+
+def test_noalloc_rejects_multi_launch_tilings():
+    # multi-launch sweeps pass their state through buffers the handle
+    # allocates, so the allocation-free entry point refuses them
+    import torch
+    from helpers import env
+    dev = torch.device("cuda:0")
+    spec = S.spec_small(600, 8, 3, every_var=2, every_step=2, length_scale=3.0, seed=3)
+    taps, xb, y = problem(spec)
+    with env(EDA_SWEEP_ML=64, EDA_SWEEP_K=2):
+        with P.Handle.from_spec(spec, taps, precision=P.EDA_FP64) as h:
+            h.eda_set_trajectory(xb, y)
+            cols = torch.zeros(2, dtype=torch.int32, device=dev)
+            V = torch.zeros(2, spec.n, dtype=torch.float64, device=dev)
+            with pytest.raises(P.EdaError) as e:
+                h.eda_hvp_noalloc(cols, V, torch.empty_like(V), True)
+            assert e.value.code == P.EDA_ERR_INVALID and "multi-launch" in str(e.value)
