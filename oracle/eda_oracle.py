@@ -328,10 +328,11 @@ def nystrom(apply_a, Phi, k, q=1, shift_eps=np.finfo(np.float64).eps, evd_rtol=1
     has few non-negligible eigenvalues -- W is inverted by a truncated
     eigendecomposition (Appendix B, third variant): W^+ = V diag(1/mu) V^T
     over the eigenvalues mu > evd_rtol * max(mu), T = R_Y V diag(mu^{-1/2}).
-    The approximation then has rank r = number of kept mu, so only
-    k_eff = min(k, r) modes carry information: columns k_eff..k-1 of S_k and
-    the matching entries of D_k are returned as zeros (the LMP acts as the
-    identity there).  ``info['path']`` is 'cholesky', 'shift' or 'evd' and
+    The approximation then has rank r at most the number of kept mu, and
+    only its modes with D > evd_rtol * max(D) carry information, so
+    k_eff = min(k, their count): columns k_eff..k-1 of S_k and the matching
+    entries of D_k are returned as zeros (the LMP acts as the identity
+    there).  ``info['path']`` is 'cholesky', 'shift' or 'evd' and
     ``info['rank']`` is k_eff (k on the first two paths).
     """
     Phi = np.asarray(Phi, dtype=np.float64)
@@ -374,7 +375,7 @@ def nystrom(apply_a, Phi, k, q=1, shift_eps=np.finfo(np.float64).eps, evd_rtol=1
     S, D = S[:, :k].copy(), D[:k].copy()
     rank = k
     if path == "evd":
-        rank = min(k, int(keep.sum()))
+        rank = min(k, int(keep.sum()), int(np.sum(D > evd_rtol * max(D.max(), 0.0))))
         S[:, rank:] = 0.0
         D[rank:] = 0.0
     return S, D, {"shift": nu, "path": path, "Y": Y, "Q": Q, "R": R, "rank": rank}
