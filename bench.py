@@ -18,12 +18,19 @@ EDA problems); value = member solves of all ranks / max time over ranks.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
 import time
+
+# the CPU oracle baseline reports the threads it uses: one (numpy's BLAS
+# pinned to a single thread before numpy loads)
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 import numpy as np
 
@@ -120,6 +127,25 @@ def measured_peaks():
         d = json.load(open(path))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+SWEEP_SRC = os.path.join(ROOT, "paper_2605_23571_gb300", "csrc", "sweep.cu")
+SWEEP_PROFILE = os.path.join(ROOT, "profiles", "sweep_kernel_f32_member_hvp_l96_n4096_w64_m51.md")
+
+
+def sweep_traffic_per_launch():
+    """DRAM bytes (read + write) per launch of the FP32 member-HVP sweep from
+    the committed ncu summary, or None when the sweep source has changed
+    since those counters were taken (or there is no summary)."""
+    if not os.path.exists(SWEEP_PROFILE):
+        return None
+    txt = open(SWEEP_PROFILE).read()
+    m_sha = re.search(r"sweep\.cu sha256: ([0-9a-f]{64})", txt)
+    m_b = re.search(r"dram bytes per launch \(read \+ write\): ([0-9.eE+]+)", txt)
+    if not (m_sha and m_b):
+        return None
+    sha = hashlib.sha256(open(SWEEP_SRC, "rb").read()).hexdigest()
+    return float(m_b.group(1)) if sha == m_sha.group(1) else None
 
 
 # ---------------------------------------------------------------- workload
@@ -270,9 +296,14 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     launches0 = P.kernel_launches()
+    hm.eda_trace(True)  # event-timed sweeps inside the timed steps (roofline)
+    torch.cuda.profiler.start()  # ncu --profile-from-start off captures from here
     with Clocks(local) as clk:
         t_mixed, its_mixed = timed_steps(hm, args.steps, 0)
+    torch.cuda.profiler.stop()
+    hm.eda_trace(False)
     launches = P.kernel_launches() - launches0
+    sw_calls, sw_cols, sw_ms = hm.eda_trace_read(fp64=False)
     st_mixed = status.cpu().numpy()
     rr_mixed = relres.cpu().numpy()
     dz_mixed = dz.cpu().numpy()
@@ -292,9 +323,14 @@ def run_ours(args):
     ms64 = h64.eda_time_hvp_sweep(reps=3)
     hvps32 = M / (ms32 / 1e3)
     hvps64 = M / (ms64 / 1e3)
-    bytes_per_launch = M * 4 * n * (2 * spec.nsteps + 2)  # trajectory + vectors, FP32
-    achieved = bytes_per_launch / (ms32 / 1e3) / 1e9
+    # roofline of the FP32 sweep from the timed steps: algorithmic bytes per
+    # member-column HVP s*n*(2N+2) (trajectory forward and backward, vector
+    # in and out), times the columns each traced launch computed, over the
+    # event-timed launch durations
+    bytes_per_col = 4 * n * (2 * spec.nsteps + 2)
+    achieved = bytes_per_col * sw_cols / (sw_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
+    traffic = sweep_traffic_per_launch()
 
     # ---- end to end through the C ABI with host buffers
     xb_h = xb.cpu().pin_memory().numpy()
@@ -349,9 +385,12 @@ def run_ours(args):
                       "true_relres_max": float(rr_mixed.max()),
                       "rel_diff_mixed_vs_fp64_max": diff64},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "sweep_kernel<float,8> (batched member HVP, 51 columns)",
-                         "peak_kind": peak_kind},
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "sweep_kernel<float,8> (FP32 Hessian-product sweeps of the timed steps)",
+                         "launches_timed": sw_calls, "columns": sw_cols,
+                         "ms_per_launch": sw_ms / max(1, sw_calls),
+                         "bytes_per_launch": bytes_per_col * sw_cols / max(1, sw_calls),
+                         "peak_kind": peak_kind + " (MEASURED_PEAKS hbm_gbs, burst copy)"},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": int(launches),

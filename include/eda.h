@@ -257,6 +257,24 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out);
 EDA_API long long eda_kernel_launches(void);
 
 /*
+ * Tracing of the Hessian-product sweeps of one handle (eda_hvp, the sketch,
+ * the PCG of eda_solve_batch, the FP64 true residuals): with enable != 0,
+ * every later sweep is bracketed by a pair of CUDA events on the handle's
+ * stream and the columns it computed (the active members, counted on the
+ * device) are summed.  eda_trace(h, 1) starts a new record (zeroing the
+ * totals); eda_trace(h, 0) stops recording and keeps them.  Each sweep adds
+ * one one-thread kernel and two event records to the stream.
+ */
+EDA_API int eda_trace(eda_handle* h, int enable);
+/*
+ * Totals of the record (host outputs, each may be NULL): for the FP64
+ * sweeps (fp64 != 0) or the FP32 sweeps, *sweeps = sweeps recorded,
+ * *columns = columns they computed, *ms = summed event time.  Synchronises
+ * the stream.
+ */
+EDA_API int eda_trace_read(eda_handle* h, int fp64, long long* sweeps, long long* columns, double* ms);
+
+/*
  * Tracing: times `reps` launches of the batched Hessian-vector sweep that the
  * PCG of eda_solve_batch issues (all L+1 members, each on its own
  * trajectory, inputs from the handle's current direction vectors) with CUDA

@@ -35,7 +35,8 @@ EXPORTS = ["eda_version", "eda_last_error", "eda_create", "eda_destroy", "eda_tw
            "eda_group_sketch", "eda_group_build_lmp", "eda_group_autotune", "eda_group_solve",
            "eda_ws_create", "eda_ws_destroy", "eda_ws_last_error", "eda_ws_num_params", "eda_ws_set_params",
            "eda_ws_get_params", "eda_ws_set_scales", "eda_ws_get_scales", "eda_ws_loss_grad", "eda_ws_train",
-           "eda_ws_infer", "eda_hvp_noalloc", "eda_hvp_noalloc_capacity", "eda_lmp_info"]
+           "eda_ws_infer", "eda_hvp_noalloc", "eda_hvp_noalloc_capacity", "eda_lmp_info",
+           "eda_trace", "eda_trace_read"]
 
 
 class EdaError(RuntimeError):
@@ -91,6 +92,11 @@ def lib() -> ctypes.CDLL:
     L.eda_build_lmp.argtypes = [vp, vp, vp]
     L.eda_set_lmp.restype = i
     L.eda_set_lmp.argtypes = [vp, vp, vp]
+    L.eda_trace.restype = i
+    L.eda_trace.argtypes = [vp, i]
+    L.eda_trace_read.restype = i
+    L.eda_trace_read.argtypes = [vp, i, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                 ctypes.POINTER(d)]
     L.eda_lmp_info.restype = i
     L.eda_lmp_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)]
     L.eda_solve_batch.restype = i
@@ -294,6 +300,17 @@ class Handle:
     def eda_set_lmp(self, s_in, eigvals_in):
         self._check(self._L.eda_set_lmp(self._h, _ptr(s_in, np.float64, self.k * self.n, "s_in"),
                                         _ptr(eigvals_in, np.float64, self.k, "eigvals_in")))
+
+    def eda_trace(self, enable=True):
+        """Starts (enable) or stops the sweep trace of this handle."""
+        self._check(self._L.eda_trace(self._h, 1 if enable else 0))
+
+    def eda_trace_read(self, fp64=False):
+        """(sweeps, columns, ms) recorded for the FP64 or the FP32 sweeps."""
+        a, b, c = ctypes.c_longlong(0), ctypes.c_longlong(0), ctypes.c_double(0.0)
+        self._check(self._L.eda_trace_read(self._h, 1 if fp64 else 0, ctypes.byref(a), ctypes.byref(b),
+                                           ctypes.byref(c)))
+        return a.value, b.value, c.value
 
     def eda_lmp_info(self):
         """(path, rank, shift) of the current LMP: path 0 Cholesky, 1 shift,

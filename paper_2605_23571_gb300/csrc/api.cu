@@ -369,14 +369,76 @@ int ensure_stash(eda_handle* h, int ncol) {
   return EDA_OK;
 }
 
+__global__ void trace_cols_kernel(unsigned long long* acc, const int* nactive, int ncol) {
+  *acc += (unsigned long long)(nactive ? *nactive : ncol);
+}
+
+// Adds the completed event pairs of the trace pool to the totals.
+int trace_drain(eda_handle* h) {
+  if (h->trace_used == 0) return EDA_OK;
+  CU(h, cudaEventSynchronize(h->trace_ev[2 * (h->trace_used - 1) + 1]));
+  for (int i = 0; i < h->trace_used; ++i) {
+    float ms = 0.f;
+    CU(h, cudaEventElapsedTime(&ms, h->trace_ev[2 * i], h->trace_ev[2 * i + 1]));
+    h->trace_ms[h->trace_kind[i]] += ms;
+    h->trace_calls[h->trace_kind[i]] += 1;
+  }
+  h->trace_used = 0;
+  return EDA_OK;
+}
+
+// Opens a traced sweep: column count and the first event of a pair.
+int trace_begin(eda_handle* h, int kind, const int* active, int ncol) {
+  constexpr int kPairs = 1024;
+  if (h->trace_ev.empty()) {
+    h->trace_ev.resize(2 * kPairs);
+    h->trace_kind.resize(kPairs);
+    for (auto& e : h->trace_ev) CU(h, cudaEventCreate(&e));
+  }
+  if (h->trace_used == kPairs) {
+    int rc = trace_drain(h);
+    if (rc) return rc;
+  }
+  eda::count_launch();
+  trace_cols_kernel<<<1, 1, 0, h->st>>>(h->trace_cols + kind, active ? h->nactive : nullptr, ncol);
+  CU(h, cudaGetLastError());
+  h->trace_kind[h->trace_used] = kind;
+  CU(h, cudaEventRecord(h->trace_ev[2 * h->trace_used], h->st));
+  return EDA_OK;
+}
+
+int trace_end(eda_handle* h) {
+  CU(h, cudaEventRecord(h->trace_ev[2 * h->trace_used + 1], h->st));
+  ++h->trace_used;
+  return EDA_OK;
+}
+
+int hvp_launch(eda_handle* h, const int* dcols, int ncol, const double* V, double* HV, int ident, bool sw64,
+               const int* active, double* dot);
+
 // HV = (ident ? V : 0) + A_{m(c)} V for ncol columns, device pointers, FP64 at
-// the interface; FP32 sweeps in EDA_MIXED unless force64.
+// the interface; FP32 sweeps in EDA_MIXED unless force64.  With tracing on,
+// the sweep is bracketed by an event pair (active columns counted on the
+// device from the active count).  dot (PCG accumulators) != nullptr: the
+// sweep also adds v . (H v) of every active column to them.
 int hvp_dev(eda_handle* h, const int* dcols, int ncol, const double* V, double* HV, int ident, bool force64,
-            const int* active) {
+            const int* active, double* dot = nullptr) {
   if (ncol <= 0) return EDA_OK;
   int rc = ensure_stash(h, ncol);
   if (rc) return rc;
-  if (h->precision == EDA_FP64 || force64) {
+  const bool sw64 = (h->precision == EDA_FP64 || force64);
+  if (h->trace_on) {
+    rc = trace_begin(h, sw64 ? 0 : 1, active, ncol);
+    if (rc) return rc;
+  }
+  rc = hvp_launch(h, dcols, ncol, V, HV, ident, sw64, active, dot);
+  if (rc) return rc;
+  return h->trace_on ? trace_end(h) : EDA_OK;
+}
+
+int hvp_launch(eda_handle* h, const int* dcols, int ncol, const double* V, double* HV, int ident, bool sw64,
+               const int* active, double* dot) {
+  if (sw64) {
     SweepArgs<double> a = base_args<double>(h);
     a.mode = eda::MODE_HVP;
     a.ncol = ncol;
@@ -389,6 +451,8 @@ int hvp_dev(eda_handle* h, const int* dcols, int ncol, const double* V, double* 
     a.stash = h->stash;
     a.stash_stride = h->p;
     a.include_identity = ident;
+    a.dot_out = dot;
+    a.dot_stride = eda::kPcgAccStride;
     CU(h, (eda::ensure_ml(h, a.ncol, true) == EDA_OK) ? eda::launch_sweep<double>(a, h->plan64, h->st, h->ml64[0], h->ml64[1]) : cudaErrorMemoryAllocation);
     return EDA_OK;
   }
@@ -405,6 +469,8 @@ int hvp_dev(eda_handle* h, const int* dcols, int ncol, const double* V, double* 
   a.stash = h->stash32;
   a.stash_stride = h->p;
   a.include_identity = ident;
+  a.dot_out = dot;
+  a.dot_stride = eda::kPcgAccStride;
   CU(h, (eda::ensure_ml(h, a.ncol, false) == EDA_OK) ? eda::launch_sweep<float>(a, h->plan32, h->st, h->ml32[0], h->ml32[1]) : cudaErrorMemoryAllocation);
   return EDA_OK;
 }
@@ -469,6 +535,33 @@ extern "C" {
 EDA_API const char* eda_version(void) { return "eda-gb300 0.1 (sm_103a)"; }
 
 EDA_API long long eda_kernel_launches(void) { return eda::g_launches.load(std::memory_order_relaxed); }
+
+EDA_API int eda_trace(eda_handle* h, int enable) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (enable) {
+    int rc = trace_drain(h);
+    if (rc) return rc;
+    h->trace_ms[0] = h->trace_ms[1] = 0.0;
+    h->trace_calls[0] = h->trace_calls[1] = 0;
+    CU(h, cudaMemsetAsync(h->trace_cols, 0, 2 * sizeof(unsigned long long), h->st));
+  }
+  h->trace_on = enable != 0;
+  return EDA_OK;
+}
+
+EDA_API int eda_trace_read(eda_handle* h, int fp64, long long* sweeps, long long* columns, double* ms) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  int rc = trace_drain(h);
+  if (rc) return rc;
+  const int kind = fp64 ? 0 : 1;
+  unsigned long long cols = 0;
+  CU(h, cudaMemcpyAsync(&cols, h->trace_cols + kind, sizeof(cols), cudaMemcpyDeviceToHost, h->st));
+  CU(h, cudaStreamSynchronize(h->st));
+  if (sweeps) *sweeps = h->trace_calls[kind];
+  if (columns) *columns = (long long)cols;
+  if (ms) *ms = h->trace_ms[kind];
+  return EDA_OK;
+}
 
 EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
   if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
@@ -717,6 +810,26 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
   CUC(dalloc(h, &h->sc, M));
   CUC(dalloc(h, &h->active, M));
   CUC(dalloc(h, &h->nactive, 1));
+  CUC(dalloc(h, &h->trace_cols, 2));
+  CUC(dalloc(h, &h->acc, M));
+  CUC(dalloc(h, &h->Wk, (size_t)M * std::max(kk, 1)));
+  {
+    std::vector<eda::PcgTask> tasks;
+    eda::pcg_tasks(&n, 1, &tasks);
+    h->ntasks = (int)tasks.size();
+    CUC(dalloc(h, &h->tasks, tasks.size()));
+    CUC(cudaMemcpy(h->tasks, tasks.data(), tasks.size() * sizeof(eda::PcgTask), cudaMemcpyHostToDevice));
+    eda::PcgProb pr{};
+    pr.n = n;
+    pr.M = M;
+    pr.k = kk;
+    pr.item0 = 0;
+    pr.off0 = 0;
+    pr.S = (h->precision == EDA_MIXED) ? (const void*)h->S32 : (const void*)h->S;
+    pr.c = h->cv;
+    CUC(dalloc(h, &h->probs, 1));
+    CUC(cudaMemcpy(h->probs, &pr, sizeof(pr), cudaMemcpyHostToDevice));
+  }
   CUC(dalloc(h, &h->cols, mcols));
   CUC(dalloc(h, &h->zeros, mcols));
   CUC(cudaMallocHost((void**)&h->hflag, sizeof(int)));
@@ -762,6 +875,8 @@ EDA_API int eda_destroy(eda_handle* h) {
   }
   if (h->tab64) cudaFree(h->tab64);
   if (h->tab32) cudaFree(h->tab32);
+  for (cudaEvent_t e : h->trace_ev)
+    if (e) cudaEventDestroy(e);
   if (h->hflag) cudaFreeHost(h->hflag);
   if (h->hring) cudaFreeHost(h->hring);
   for (int i = 0; i < eda_handle::kRing; ++i)
@@ -1092,44 +1207,47 @@ EDA_API int eda_lmp_info(eda_handle* h, int* path, int* rank, double* shift) {
   return EDA_OK;
 }
 
+}  // extern "C"
+
 namespace {
 
 // PCG iterations from the current (x, r) state (the caller has run
 // pcg_start): FP64 vectors and scalars; sweeps in FP64 (sweep64) or FP32,
-// LMP arithmetic in FP64 or FP32 accordingly.  The host polls the active
-// count through a ring of pinned copies and runs at most kRing-1 iterations
-// ahead of the device.
-int pcg_loop(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done, bool sweep64) {
-  const int n = h->n, M = h->M;
+// LMP arithmetic in FP64 or FP32 accordingly.  One iteration is the sweep
+// (with p.q in its epilogue) and the update, precond and dir launches over
+// row chunks of all members (pcg.h).  The host polls the active count
+// through a ring of pinned copies and runs at most kRing-1 iterations ahead
+// of the device.
+template <typename TS>
+int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done, bool sweep64) {
+  const int M = h->M;
   const int fixed = (tol > 0.0) ? 0 : maxit;
-  auto precond = [&]() -> int {
-    if (!use_lmp) {
-      CU(h, cudaMemcpyAsync(h->z, h->r, (size_t)M * n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
-    } else if (sweep64) {
-      CU(h, eda::lmp_fused<double>(n, M, h->S, h->cv, h->k, nullptr, nullptr, nullptr, h->k, h->r, h->z,
-                                   h->active, h->st));
-    } else {
-      CU(h, eda::lmp_fused<float>(n, M, h->S32, h->cv, h->k, nullptr, nullptr, nullptr, h->k, h->r, h->z,
-                                  h->active, h->st));
-    }
-    return EDA_OK;
-  };
-  int rc = precond();
-  if (rc) return rc;
-  CU(h, eda::pcg_first_dir<double>(n, M, h->r, h->z, h->pv, h->sc, h->active, h->st));
+  const int lmp = use_lmp ? 1 : 0;
+  const int kmax = std::max(h->k, 1);
+  TS* Wk = reinterpret_cast<TS*>(h->Wk);
+  // start: z = P r, p = z, r.z
+  CU(h, eda::pcg2_reset(h->acc, M, Wk, (size_t)M * kmax * sizeof(TS), h->st));
+  CU(h, eda::pcg2_update<TS>(h->tasks, h->ntasks, h->probs, kmax, h->pv, h->q, h->x, h->r, h->sc, h->acc, h->active,
+                             Wk, 0, 0, lmp, h->nactive, h->st));
+  CU(h, eda::pcg2_precond<TS>(h->tasks, h->ntasks, h->probs, kmax, h->r, h->z, h->pv, h->sc, h->acc, h->active, Wk,
+                              0, tol, maxit, fixed, lmp, 1, h->nactive, h->st));
+  // the first update accumulates the projections of r_1 from zero
+  CU(h, cudaMemsetAsync(Wk, 0, (size_t)M * kmax * sizeof(TS), h->st));
   constexpr int R = eda_handle::kRing;
   // every member stops at convergence or at its own maxit-th iteration, so
   // no loop needs more than maxit iterations
   int it = it0;
   while (it - it0 < maxit) {
+    const int par = (it - it0) & 1;
     ++it;
-    rc = hvp_dev(h, h->cols, M, h->pv, h->q, 1, sweep64, h->active);
+    int rc = hvp_dev(h, h->cols, M, h->pv, h->q, 1, sweep64, h->active, reinterpret_cast<double*>(h->acc));
     if (rc) return rc;
-    CU(h, eda::pcg_update<double, double>(n, M, maxit, h->pv, h->q, h->x, h->r, h->sc, h->active, tol, h->nactive,
-                                          fixed, h->st));
-    rc = precond();
-    if (rc) return rc;
-    CU(h, eda::pcg_dir<double>(n, M, h->r, h->z, h->pv, h->sc, h->active, h->st));
+    CU(h, eda::pcg2_update<TS>(h->tasks, h->ntasks, h->probs, kmax, h->pv, h->q, h->x, h->r, h->sc, h->acc,
+                               h->active, Wk, par, 1, lmp, h->nactive, h->st));
+    CU(h, eda::pcg2_precond<TS>(h->tasks, h->ntasks, h->probs, kmax, h->r, h->z, h->pv, h->sc, h->acc, h->active,
+                                Wk, par, tol, maxit, fixed, lmp, 0, h->nactive, h->st));
+    CU(h, eda::pcg2_dir<TS>(h->tasks, h->ntasks, h->probs, kmax, h->z, h->pv, h->sc, h->acc, h->active, Wk, par,
+                            h->st));
     const int slot = it % R;
     CU(h, cudaMemcpyAsync(h->hring + slot, h->nactive, sizeof(int), cudaMemcpyDeviceToHost, h->st));
     CU(h, cudaEventRecord(h->ring_ev[slot], h->st));
@@ -1140,12 +1258,19 @@ int pcg_loop(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* i
     }
   }
   CU(h, cudaStreamSynchronize(h->st));
-  // iterations actually done: the largest per-member count
   *it_done = it;
   return EDA_OK;
 }
 
+int pcg_loop(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done, bool sweep64) {
+  // the LMP arithmetic follows the sweeps: FP64, or FP32 with the FP32 copy of S
+  if (sweep64) return pcg_loop_t<double>(h, tol, maxit, it0, use_lmp, it_done, true);
+  return pcg_loop_t<float>(h, tol, maxit, it0, use_lmp, it_done, false);
+}
+
 }  // namespace
+
+extern "C" {
 
 EDA_API int eda_solve_batch(eda_handle* h, double tol, int maxit, const double* x0, int use_lmp, double* dz_out,
                             int* iters_out, double* relres_out, int* status_out) {

@@ -446,149 +446,6 @@ __global__ void pcg_start_kernel(int n, ItemGeo ig, const double* b, const T* r,
   }
 }
 
-// rz = r.z, p = z (start of the recurrences).
-template <typename T>
-__global__ void pcg_first_dir_kernel(int n, ItemGeo ig, const T* r, const T* z, T* p, PcgScalars* sc,
-                                     const int* active) {
-  __shared__ double red[32];
-  const int j = blockIdx.x;
-  if (!active[j]) return;
-  long long off;
-  item_geo(ig, j, n, &n, &off);
-  const T* rj = r + off;
-  const T* zj = z + off;
-  T* pj = p + off;
-  double s = 0.0;
-  for (int g = threadIdx.x; g < n; g += blockDim.x) {
-    s += (double)rj[g] * (double)zj[g];
-    pj[g] = zj[g];
-  }
-  s = block_sum<double>(s, red);
-  if (threadIdx.x == 0) sc[j].rz = s;
-}
-
-// After q = H p: alpha, x += alpha p, r -= alpha q, the residual norm and the
-// stopping test.
-template <typename T, typename TX>
-__global__ void pcg_update_kernel(int n, ItemGeo ig, int maxit, const T* p, const T* q, TX* x, T* r, PcgScalars* sc,
-                                  int* active, double tol, int* nactive, int fixed_iters) {
-  __shared__ double red[32];
-  const int j = blockIdx.x;
-  if (!active[j]) return;
-  long long off;
-  item_geo(ig, j, n, &n, &off);
-  const T* pj = p + off;
-  const T* qj = q + off;
-  TX* xj = x + off;
-  T* rj = r + off;
-  double s = 0.0;
-  for (int g = threadIdx.x; g < n; g += blockDim.x) s += (double)pj[g] * (double)qj[g];
-  const double pq = block_sum<double>(s, red);
-  if (!(pq > 0.0)) {
-    if (threadIdx.x == 0) {
-      sc[j].status = isfinite(pq) ? EDA_BREAKDOWN : EDA_NAN;
-      active[j] = 0;
-      atomicSub(nactive, 1);
-    }
-    return;
-  }
-  const double alpha = sc[j].rz / pq;
-  double rr = 0.0;
-  for (int g = threadIdx.x; g < n; g += blockDim.x) {
-    xj[g] = (TX)((double)xj[g] + alpha * (double)pj[g]);
-    const double rv = (double)rj[g] - alpha * (double)qj[g];
-    rj[g] = (T)rv;
-    rr += rv * rv;
-  }
-  rr = block_sum<double>(rr, red);
-  if (threadIdx.x == 0) {
-    const double rel = sqrt(rr) / sc[j].bnorm;
-    sc[j].relres = rel;
-    const int itj = sc[j].iters + 1;  // per-member count (launch-order independent, graph friendly)
-    sc[j].iters = itj;
-    bool stop = false;
-    if (!isfinite(rel)) {
-      sc[j].status = EDA_NAN;
-      stop = true;
-    } else if (fixed_iters > 0) {
-      if (itj >= fixed_iters) {
-        sc[j].status = EDA_CONVERGED;
-        stop = true;
-      }
-    } else if (rel <= (sc[j].tolm > 0.0 ? sc[j].tolm : tol)) {
-      sc[j].status = EDA_CONVERGED;
-      stop = true;
-    } else if (maxit > 0 && itj >= maxit) {  // this member's own budget
-      sc[j].status = EDA_MAXIT;
-      stop = true;
-    }
-    if (stop) {
-      active[j] = 0;
-      atomicSub(nactive, 1);
-    }
-  }
-}
-
-// After z = P r: beta = (r.z)_new / (r.z)_old, p = z + beta p.
-template <typename T>
-__global__ void pcg_dir_kernel(int n, ItemGeo ig, const T* r, const T* z, T* p, PcgScalars* sc, const int* active) {
-  __shared__ double red[32];
-  const int j = blockIdx.x;
-  if (!active[j]) return;
-  long long off;
-  item_geo(ig, j, n, &n, &off);
-  const T* rj = r + off;
-  const T* zj = z + off;
-  T* pj = p + off;
-  double s = 0.0;
-  for (int g = threadIdx.x; g < n; g += blockDim.x) s += (double)rj[g] * (double)zj[g];
-  const double rz = block_sum<double>(s, red);
-  const double beta = rz / sc[j].rz;
-  for (int g = threadIdx.x; g < n; g += blockDim.x) pj[g] = (T)((double)zj[g] + beta * (double)pj[g]);
-  if (threadIdx.x == 0) sc[j].rz = rz;
-}
-
-// z_j = r_j + S diag(c) S^T r_j for item j (Section 3.1), one CTA per item:
-// the k projections by warps (shuffle reductions) into shared memory, then
-// the expansion.  TS is the type of S and of the arithmetic (double, or
-// float for the mixed path); r and z are FP64.  S_of/c_of/k_of give each
-// item's LMP (per problem in a group), or S, c, k for all items.
-template <typename TS>
-__global__ void lmp_fused_kernel(int n, ItemGeo ig, const TS* S, const double* c, int k, const TS* const* S_of,
-                                 const double* const* c_of, const int* k_of, const double* r, double* z,
-                                 const int* active) {
-  extern __shared__ double wsm[];  // k projections
-  const int j = blockIdx.x;
-  if (active && !active[j]) return;
-  long long off;
-  item_geo(ig, j, n, &n, &off);
-  if (S_of) {
-    S = S_of[j];
-    c = c_of[j];
-    k = k_of[j];
-  }
-  const double* rj = r + off;
-  double* zj = z + off;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  if (k <= 0 || S == nullptr) {
-    for (int g = threadIdx.x; g < n; g += blockDim.x) zj[g] = rj[g];
-    return;
-  }
-  for (int i = wid; i < k; i += nw) {
-    const TS* si = S + (long long)i * n;
-    TS acc = TS(0);
-    for (int g = lane; g < n; g += 32) acc += si[g] * (TS)rj[g];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) wsm[i] = (double)acc * c[i];
-  }
-  __syncthreads();
-  for (int g = threadIdx.x; g < n; g += blockDim.x) {
-    TS acc = TS(0);
-    for (int i = 0; i < k; ++i) acc += S[(long long)i * n + g] * (TS)wsm[i];
-    zj[g] = rj[g] + (double)acc;
-  }
-}
 
 template <typename TS, typename TD>
 __global__ void convert_kernel(long long count, const TS* s, TD* d) {
@@ -682,43 +539,6 @@ cudaError_t pcg_start(int n, int m, const double* b, const T* r, PcgScalars* sc,
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t pcg_first_dir(int n, int m, const T* r, const T* z, T* p, PcgScalars* sc, const int* active,
-                          cudaStream_t s, const int* n_of, const long long* off_of) {
-  count_launch();
-  pcg_first_dir_kernel<T><<<m, 256, 0, s>>>(n, ItemGeo{n_of, off_of}, r, z, p, sc, active);
-  return cudaGetLastError();
-}
-
-template <typename T, typename TX>
-cudaError_t pcg_update(int n, int m, int maxit, const T* p, const T* q, TX* x, T* r, PcgScalars* sc, int* active,
-                       double tol, int* nactive, int fixed_iters, cudaStream_t s, const int* n_of,
-                       const long long* off_of) {
-  count_launch();
-  pcg_update_kernel<T, TX><<<m, 256, 0, s>>>(n, ItemGeo{n_of, off_of}, maxit, p, q, x, r, sc, active, tol, nactive,
-                                             fixed_iters);
-  return cudaGetLastError();
-}
-
-template <typename T>
-cudaError_t pcg_dir(int n, int m, const T* r, const T* z, T* p, PcgScalars* sc, const int* active,
-                    cudaStream_t s, const int* n_of, const long long* off_of) {
-  count_launch();
-  pcg_dir_kernel<T><<<m, 256, 0, s>>>(n, ItemGeo{n_of, off_of}, r, z, p, sc, active);
-  return cudaGetLastError();
-}
-
-template <typename TS>
-cudaError_t lmp_fused(int n, int m, const TS* S, const double* c, int k, const TS* const* S_of,
-                      const double* const* c_of, const int* k_of, int kmax, const double* r, double* z,
-                      const int* active, cudaStream_t s, const int* n_of, const long long* off_of) {
-  if (m <= 0) return cudaSuccess;
-  count_launch();
-  lmp_fused_kernel<TS><<<m, 256, (size_t)(kmax > 0 ? kmax : 1) * sizeof(double), s>>>(
-      n, ItemGeo{n_of, off_of}, S, c, k, S_of, c_of, k_of, r, z, active);
-  return cudaGetLastError();
-}
-
 template <typename TS, typename TD>
 cudaError_t convert(long long count, const TS* src, TD* dst, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
@@ -741,26 +561,6 @@ template cudaError_t gemm_nn<float, float>(int, const float*, int, int, const do
 template cudaError_t pcg_start<double>(int, int, const double*, const double*, PcgScalars*, int*, double, int*,
                                        cudaStream_t, const int*, const long long*);
 template cudaError_t pcg_start<float>(int, int, const double*, const float*, PcgScalars*, int*, double, int*,
-                                      cudaStream_t, const int*, const long long*);
-template cudaError_t pcg_first_dir<double>(int, int, const double*, const double*, double*, PcgScalars*,
-                                           const int*, cudaStream_t, const int*, const long long*);
-template cudaError_t pcg_first_dir<float>(int, int, const float*, const float*, float*, PcgScalars*, const int*,
-                                          cudaStream_t, const int*, const long long*);
-template cudaError_t pcg_update<double, double>(int, int, int, const double*, const double*, double*, double*,
-                                                PcgScalars*, int*, double, int*, int, cudaStream_t, const int*,
-                                                const long long*);
-template cudaError_t pcg_update<float, double>(int, int, int, const float*, const float*, double*, float*,
-                                               PcgScalars*, int*, double, int*, int, cudaStream_t, const int*,
-                                               const long long*);
-template cudaError_t pcg_dir<double>(int, int, const double*, const double*, double*, PcgScalars*, const int*,
-                                     cudaStream_t, const int*, const long long*);
-template cudaError_t pcg_dir<float>(int, int, const float*, const float*, float*, PcgScalars*, const int*,
-                                    cudaStream_t, const int*, const long long*);
-template cudaError_t lmp_fused<double>(int, int, const double*, const double*, int, const double* const*,
-                                       const double* const*, const int*, int, const double*, double*, const int*,
-                                       cudaStream_t, const int*, const long long*);
-template cudaError_t lmp_fused<float>(int, int, const float*, const double*, int, const float* const*,
-                                      const double* const*, const int*, int, const double*, double*, const int*,
                                       cudaStream_t, const int*, const long long*);
 template cudaError_t convert<double, float>(long long, const double*, float*, cudaStream_t);
 template cudaError_t convert<float, double>(long long, const float*, double*, cudaStream_t);

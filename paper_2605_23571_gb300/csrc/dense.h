@@ -10,7 +10,7 @@ namespace eda {
 
 // Per-member CG scalars (FP64 recurrences, Section 2.3).
 struct PcgScalars {
-  double rz;      // r . z of the current iterate
+  double rz;      // (unused: r . z lives in the iteration accumulators)
   double bnorm;   // ||b||
   double relres;  // ||r|| / ||b||
   int iters;
@@ -40,28 +40,13 @@ cudaError_t nystrom_core(const double* W, const double* RY, int m, int k, double
 cudaError_t robust_winv(const double* W, int m, double rtol, double* M, cudaStream_t s);
 cudaError_t robust_eig(const double* K, int m, int k, double rtol, int theta_mode, double theta_given, double* SB,
                        double* D, double* cvec, double* theta_out, int* rank_out, cudaStream_t s);
-// Batched PCG vector kernels, one CTA per item.  With n_of/off_of, item j
-// has length n_of[j] at offset off_of[j]; otherwise length n at j*n.
+// Start of the batched PCG, one CTA per item: ||b||, the relative residual
+// of the initial r, statuses and the active set.  With n_of/off_of, item j
+// has length n_of[j] at offset off_of[j]; otherwise length n at j*n.  The
+// iterations are in pcg.h.
 template <typename T>
 cudaError_t pcg_start(int n, int m, const double* b, const T* r, PcgScalars* sc, int* active, double tol,
                       int* nactive, cudaStream_t s, const int* n_of = nullptr, const long long* off_of = nullptr);
-template <typename T>
-cudaError_t pcg_first_dir(int n, int m, const T* r, const T* z, T* p, PcgScalars* sc, const int* active,
-                          cudaStream_t s, const int* n_of = nullptr, const long long* off_of = nullptr);
-// maxit > 0: a member stops (status EDA_MAXIT) once its own count reaches it.
-template <typename T, typename TX>
-cudaError_t pcg_update(int n, int m, int maxit, const T* p, const T* q, TX* x, T* r, PcgScalars* sc, int* active,
-                       double tol, int* nactive, int fixed_iters, cudaStream_t s, const int* n_of = nullptr,
-                       const long long* off_of = nullptr);
-template <typename T>
-cudaError_t pcg_dir(int n, int m, const T* r, const T* z, T* p, PcgScalars* sc, const int* active,
-                    cudaStream_t s, const int* n_of = nullptr, const long long* off_of = nullptr);
-// z = r + S diag(c) S^T r per item (fused projection and expansion).
-template <typename TS>
-cudaError_t lmp_fused(int n, int m, const TS* S, const double* c, int k, const TS* const* S_of,
-                      const double* const* c_of, const int* k_of, int kmax, const double* r, double* z,
-                      const int* active, cudaStream_t s, const int* n_of = nullptr,
-                      const long long* off_of = nullptr);
 template <typename TS, typename TD>
 cudaError_t convert(long long count, const TS* src, TD* dst, cudaStream_t s);
 

@@ -81,6 +81,10 @@ struct SweepArgs {
                          // MODE_RHS: per-member forcing R^{-1} d [member][stash_stride]
   long long stash_stride;
   int include_identity;
+  // MODE_HVP with include_identity: if set, dot_out[item * dot_stride] +=
+  // v . (H v) over the column (item = column, or the group item's flag)
+  double* dot_out;
+  int dot_stride;
   int mode;
   // MODE_NL
   const T* x0;           // [col][x0_stride] initial states

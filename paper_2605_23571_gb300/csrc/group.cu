@@ -59,6 +59,11 @@ struct eda_group {
   double* stash64 = nullptr;
   float* stash32 = nullptr;
   PcgScalars* sc = nullptr;
+  eda::PcgAcc* acc = nullptr;     // per-item accumulators of an iteration
+  double* Wk = nullptr;           // T x max(kmax,1) LMP projections
+  eda::PcgTask* tasks = nullptr;  // row chunks of every problem
+  int ntasks = 0;
+  eda::PcgProb* probs = nullptr;  // per problem: sizes, items, S (of the group's precision), c
   int* active = nullptr;
   int* nactive = nullptr;
   int* dflag = nullptr;
@@ -339,7 +344,8 @@ int set_items(eda_group* g, bool fp64, bool sketch) {
 }
 
 // One launch per bucket: HV = V + A V (ident) or A V for the current items.
-int group_sweep(eda_group* g, bool fp64, const double* V, double* HV, int ident, bool sketch) {
+int group_sweep(eda_group* g, bool fp64, const double* V, double* HV, int ident, bool sketch,
+                double* dot = nullptr) {
   std::vector<Bucket>& bs = fp64 ? g->b64 : g->b32;
   for (Bucket& b : bs) {
     if (b.items.empty()) continue;
@@ -364,6 +370,8 @@ int group_sweep(eda_group* g, bool fp64, const double* V, double* HV, int ident,
       a.probs = g->d_prob64;
       a.items = b.d_items;
       a.flags = g->active;
+      a.dot_out = dot;
+      a.dot_stride = eda::kPcgAccStride;
       a.n = 1;
       GCU(g, eda::launch_sweep<double>(a, pl, g->st));
     } else {
@@ -378,6 +386,8 @@ int group_sweep(eda_group* g, bool fp64, const double* V, double* HV, int ident,
       a.probs = g->d_prob32;
       a.items = b.d_items;
       a.flags = g->active;
+      a.dot_out = dot;
+      a.dot_stride = eda::kPcgAccStride;
       a.n = 1;
       GCU(g, eda::launch_sweep<float>(a, pl, g->st));
     }
@@ -385,48 +395,51 @@ int group_sweep(eda_group* g, bool fp64, const double* V, double* HV, int ident,
   return EDA_OK;
 }
 
-// The work of one PCG iteration of the whole group (captured into a graph).
-int group_iteration(eda_group* g, bool sweep64, bool use_lmp, double tol, int maxit, int fixed) {
-  int rc = group_sweep(g, sweep64, g->p, g->q, 1, false);
+// The work of one PCG iteration of the whole group (iteration parity par):
+// the batched sweeps with p.q in their epilogue, then the update, precond and
+// dir launches over row chunks of every problem (pcg.h).
+template <typename TS>
+int group_iteration(eda_group* g, bool sweep64, bool use_lmp, double tol, int maxit, int fixed, int par) {
+  const int kmax = std::max(g->kmax, 1);
+  const int lmp = use_lmp ? 1 : 0;
+  TS* Wk = reinterpret_cast<TS*>(g->Wk);
+  int rc = group_sweep(g, sweep64, g->p, g->q, 1, false, reinterpret_cast<double*>(g->acc));
   if (rc) return rc;
-  GCU(g, eda::pcg_update<double, double>(0, g->T, maxit, g->p, g->q, g->x, g->r, g->sc, g->active, tol, g->nactive,
-                                         fixed, g->st, g->d_n_of, g->d_off_of));
-  if (use_lmp) {
-    if (sweep64)
-      GCU(g, eda::lmp_fused<double>(0, g->T, nullptr, nullptr, 0, g->d_S_of, g->d_c_of, g->d_k_of, g->kmax, g->r,
-                                    g->z, g->active, g->st, g->d_n_of, g->d_off_of));
-    else
-      GCU(g, eda::lmp_fused<float>(0, g->T, nullptr, nullptr, 0, g->d_S32_of, g->d_c_of, g->d_k_of, g->kmax, g->r,
-                                   g->z, g->active, g->st, g->d_n_of, g->d_off_of));
-  } else {
-    GCU(g, cudaMemcpyAsync(g->z, g->r, (size_t)g->vtot * sizeof(double), cudaMemcpyDeviceToDevice, g->st));
-  }
-  GCU(g, eda::pcg_dir<double>(0, g->T, g->r, g->z, g->p, g->sc, g->active, g->st, g->d_n_of, g->d_off_of));
+  GCU(g, eda::pcg2_update<TS>(g->tasks, g->ntasks, g->probs, kmax, g->p, g->q, g->x, g->r, g->sc, g->acc, g->active,
+                              Wk, par, 1, lmp, g->nactive, g->st));
+  GCU(g, eda::pcg2_precond<TS>(g->tasks, g->ntasks, g->probs, kmax, g->r, g->z, g->p, g->sc, g->acc, g->active, Wk,
+                               par, tol, maxit, fixed, lmp, 0, g->nactive, g->st));
+  GCU(g, eda::pcg2_dir<TS>(g->tasks, g->ntasks, g->probs, kmax, g->z, g->p, g->sc, g->acc, g->active, Wk, par,
+                           g->st));
   return EDA_OK;
 }
 
-int group_precond(eda_group* g, bool sweep64, bool use_lmp) {
-  if (!use_lmp) {
-    GCU(g, cudaMemcpyAsync(g->z, g->r, (size_t)g->vtot * sizeof(double), cudaMemcpyDeviceToDevice, g->st));
-  } else if (sweep64) {
-    GCU(g, eda::lmp_fused<double>(0, g->T, nullptr, nullptr, 0, g->d_S_of, g->d_c_of, g->d_k_of, g->kmax, g->r, g->z,
-                                  g->active, g->st, g->d_n_of, g->d_off_of));
-  } else {
-    GCU(g, eda::lmp_fused<float>(0, g->T, nullptr, nullptr, 0, g->d_S32_of, g->d_c_of, g->d_k_of, g->kmax, g->r,
-                                 g->z, g->active, g->st, g->d_n_of, g->d_off_of));
-  }
+// Start of a PCG loop: z = P r, p = z, r.z for the active items.
+template <typename TS>
+int group_start(eda_group* g, bool use_lmp, double tol, int maxit, int fixed) {
+  const int kmax = std::max(g->kmax, 1);
+  const int lmp = use_lmp ? 1 : 0;
+  TS* Wk = reinterpret_cast<TS*>(g->Wk);
+  GCU(g, eda::pcg2_reset(g->acc, g->T, Wk, (size_t)g->T * kmax * sizeof(TS), g->st));
+  GCU(g, eda::pcg2_update<TS>(g->tasks, g->ntasks, g->probs, kmax, g->p, g->q, g->x, g->r, g->sc, g->acc, g->active,
+                              Wk, 0, 0, lmp, g->nactive, g->st));
+  GCU(g, eda::pcg2_precond<TS>(g->tasks, g->ntasks, g->probs, kmax, g->r, g->z, g->p, g->sc, g->acc, g->active, Wk,
+                               0, tol, maxit, fixed, lmp, 1, g->nactive, g->st));
+  // the first update accumulates the projections of r_1 from zero
+  GCU(g, cudaMemsetAsync(Wk, 0, (size_t)g->T * kmax * sizeof(TS), g->st));
   return EDA_OK;
 }
 
-// PCG iterations of the group from the current (x, r): graph replay with the
-// active count polled through a ring of pinned copies.
-int group_pcg_loop(eda_group* g, bool sweep64, bool use_lmp, double tol, int maxit, int* it_io) {
+// PCG iterations of the group from the current (x, r): replay of a graph of
+// two iterations (parities 0 and 1) with the active count polled through a
+// ring of pinned copies.
+template <typename TS>
+int group_pcg_loop_t(eda_group* g, bool sweep64, bool use_lmp, double tol, int maxit, int* it_io) {
   const int fixed = tol > 0.0 ? 0 : maxit;
-  int rc = group_precond(g, sweep64, use_lmp);
+  int rc = group_start<TS>(g, use_lmp, tol, maxit, fixed);
   if (rc) return rc;
-  GCU(g, eda::pcg_first_dir<double>(0, g->T, g->r, g->z, g->p, g->sc, g->active, g->st, g->d_n_of, g->d_off_of));
   const int key = (sweep64 ? 1 : 0) + (use_lmp ? 2 : 0) + (fixed ? 4 : 0);
-  const bool use_graph = eda::env_int("EDA_GROUP_GRAPH", 1) != 0 && fixed == 0;
+  const bool use_graph = eda::env_int("EDA_GROUP_GRAPH", 1) != 0;
   // the graph bakes in tol and maxit as kernel arguments
   if (use_graph && (g->gexec == nullptr || g->g_key != key || g->g_tol != tol || g->g_maxit != maxit)) {
     if (g->gexec) {
@@ -435,7 +448,8 @@ int group_pcg_loop(eda_group* g, bool sweep64, bool use_lmp, double tol, int max
     }
     cudaGraph_t graph;
     GCU(g, cudaStreamBeginCapture(g->st, cudaStreamCaptureModeRelaxed));
-    rc = group_iteration(g, sweep64, use_lmp, tol, maxit, fixed);
+    rc = group_iteration<TS>(g, sweep64, use_lmp, tol, maxit, fixed, 0);
+    if (!rc) rc = group_iteration<TS>(g, sweep64, use_lmp, tol, maxit, fixed, 1);
     cudaError_t ce = cudaStreamEndCapture(g->st, &graph);
     if (rc) return rc;
     GCU(g, ce);
@@ -447,23 +461,27 @@ int group_pcg_loop(eda_group* g, bool sweep64, bool use_lmp, double tol, int max
   }
   constexpr int R = 4;
   // every member stops at convergence or at its own maxit-th iteration, so
-  // no loop needs more than maxit iterations
+  // no loop needs more than maxit iterations (one more at most: the graph
+  // runs iterations in pairs, and a member past its budget is inactive)
   int it = *it_io;
   const int it0 = it;
+  int polls = 0;
   while (it - it0 < maxit) {
-    ++it;
     if (use_graph) {
-      eda::count_launch(3 + (int)(sweep64 ? g->b64.size() : g->b32.size()));
+      eda::count_launch(2 * (4 + (int)(sweep64 ? g->b64.size() : g->b32.size())));
       GCU(g, cudaGraphLaunch(g->gexec, g->st));
     } else {
-      rc = group_iteration(g, sweep64, use_lmp, tol, maxit, fixed);
+      rc = group_iteration<TS>(g, sweep64, use_lmp, tol, maxit, fixed, 0);
+      if (!rc) rc = group_iteration<TS>(g, sweep64, use_lmp, tol, maxit, fixed, 1);
       if (rc) return rc;
     }
-    const int slot = it % R;
+    it += 2;
+    ++polls;
+    const int slot = polls % R;
     GCU(g, cudaMemcpyAsync(g->hring + slot, g->nactive, sizeof(int), cudaMemcpyDeviceToHost, g->st));
     GCU(g, cudaEventRecord(g->ev[slot], g->st));
-    if (it - it0 >= R) {
-      const int old = (it - R + 1) % R;
+    if (polls >= R) {
+      const int old = (polls - R + 1) % R;
       GCU(g, cudaEventSynchronize(g->ev[old]));
       if (g->hring[old] == 0) break;
     }
@@ -471,6 +489,12 @@ int group_pcg_loop(eda_group* g, bool sweep64, bool use_lmp, double tol, int max
   GCU(g, cudaStreamSynchronize(g->st));
   *it_io = it;
   return EDA_OK;
+}
+
+int group_pcg_loop(eda_group* g, bool sweep64, bool use_lmp, double tol, int maxit, int* it_io) {
+  // the LMP arithmetic follows the sweeps: FP64, or FP32 with the FP32 copies of S
+  if (sweep64) return group_pcg_loop_t<double>(g, true, use_lmp, tol, maxit, it_io);
+  return group_pcg_loop_t<float>(g, false, use_lmp, tol, maxit, it_io);
 }
 
 }  // namespace
@@ -538,7 +562,9 @@ EDA_API int eda_group_create(eda_handle* const* handles, int count, eda_group** 
       galloc(g, &g->b, voff) || galloc(g, &g->x, voff) || galloc(g, &g->r, voff) || galloc(g, &g->z, voff) ||
       galloc(g, &g->p, voff) || galloc(g, &g->q, voff) || galloc(g, &g->stash64, soff) ||
       galloc(g, &g->stash32, soff) || galloc(g, &g->sc, T) || galloc(g, &g->active, T) ||
-      galloc(g, &g->nactive, 1) || galloc(g, &g->dflag, 1) || galloc(g, &g->Phi, koff) || galloc(g, &g->Y, koff)) {
+      galloc(g, &g->nactive, 1) || galloc(g, &g->dflag, 1) || galloc(g, &g->Phi, koff) || galloc(g, &g->Y, koff) ||
+      galloc(g, &g->acc, T) || galloc(g, &g->Wk, (long long)T * std::max(g->kmax, 1)) ||
+      galloc(g, &g->probs, count)) {
     eda::fail(nullptr, EDA_ERR_CUDA, "eda_group_create: out of device memory");
     return bail(EDA_ERR_CUDA);
   }
@@ -554,6 +580,30 @@ EDA_API int eda_group_create(eda_handle* const* handles, int count, eda_group** 
   if (!e) e = cudaMemcpy(g->d_S32_of, S32_of.data(), T * sizeof(void*), cudaMemcpyHostToDevice);
   if (!e) e = cudaMemcpy(g->d_c_of, c_of.data(), T * sizeof(void*), cudaMemcpyHostToDevice);
   if (!e) e = cudaMemcpy(g->d_k_of, k_of.data(), T * sizeof(int), cudaMemcpyHostToDevice);
+  {
+    // the problems as one PCG batch: row-chunk tasks and per-problem records
+    std::vector<eda::PcgProb> pr(count);
+    std::vector<int> n_of(count);
+    int item = 0;
+    for (int pi = 0; pi < count; ++pi) {
+      eda_handle* h = handles[pi];
+      pr[pi].n = h->n;
+      pr[pi].M = h->M;
+      pr[pi].k = h->k;
+      pr[pi].item0 = item;
+      pr[pi].off0 = g->item_off[item];
+      pr[pi].S = (h->k > 0) ? ((prec == EDA_MIXED) ? (const void*)h->S32 : (const void*)h->S) : nullptr;
+      pr[pi].c = h->cv;
+      n_of[pi] = h->n;
+      item += h->M;
+    }
+    std::vector<eda::PcgTask> tasks;
+    eda::pcg_tasks(n_of.data(), count, &tasks);
+    g->ntasks = (int)tasks.size();
+    if (!e) e = galloc(g, &g->tasks, tasks.size());
+    if (!e) e = cudaMemcpy(g->tasks, tasks.data(), tasks.size() * sizeof(eda::PcgTask), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(g->probs, pr.data(), pr.size() * sizeof(eda::PcgProb), cudaMemcpyHostToDevice);
+  }
   if (!e) e = cudaMallocHost((void**)&g->hring, 4 * sizeof(int));
   for (int i = 0; i < 4 && !e; ++i) e = cudaEventCreateWithFlags(&g->ev[i], cudaEventDisableTiming);
   if (e) {

@@ -8,6 +8,7 @@
 
 #include "dense.h"
 #include "eda_internal.h"
+#include "pcg.h"
 
 using eda::PcgScalars;
 using eda::SweepArgs;
@@ -60,6 +61,11 @@ struct eda_handle {
   // device: PCG
   double *x = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr;
   PcgScalars* sc = nullptr;
+  eda::PcgAcc* acc = nullptr;      // per-member accumulators of an iteration
+  double* Wk = nullptr;            // M x max(k,1) LMP projections (FP64, or FP32 in the mixed solve)
+  eda::PcgTask* tasks = nullptr;   // row chunks of the state
+  int ntasks = 0;
+  eda::PcgProb* probs = nullptr;   // the handle as a one-problem batch
   int* active = nullptr;
   int* nactive = nullptr;
   int* cols = nullptr;  // identity member map 0..max(M, ell)-1
@@ -87,6 +93,16 @@ struct eda_handle {
   bool tab64_ok = false, tab32_ok = false;
   std::vector<int> h_obs_ptr, h_obs_idx;
   std::vector<void*> allocs;
+  // tracing of the Hessian-product sweeps ([0] FP64 sweeps, [1] FP32):
+  // event pairs around each sweep on the handle's stream, drained into the
+  // totals when the pool is full or on read; column counts on the device
+  bool trace_on = false;
+  std::vector<cudaEvent_t> trace_ev;      // 2 per pair
+  std::vector<int> trace_kind;            // precision index per pair
+  int trace_used = 0;
+  double trace_ms[2] = {0.0, 0.0};
+  long long trace_calls[2] = {0, 0};
+  unsigned long long* trace_cols = nullptr;  // device [2]
 };
 
 

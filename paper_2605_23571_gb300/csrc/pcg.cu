@@ -1,0 +1,329 @@
+// Row-chunk kernels of the batched PCG iteration (see pcg.h).
+#include <vector>
+
+#include "eda_internal.h"
+#include "pcg.h"
+
+namespace eda {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Row stride of the transposed S chunk in the precond kernel: odd, so that
+// 32 lanes reading one column of 32 consecutive rows hit 32 banks.
+__host__ __device__ __forceinline__ int odd_stride(int k) { return k | 1; }
+
+template <typename TS>
+__global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* tasks, const PcgProb* probs, int kmax,
+                                                               const double* p, const double* q, double* x,
+                                                               double* r, PcgScalars* sc, PcgAcc* acc, int* active,
+                                                               TS* Wk, int par, int update, int use_lmp,
+                                                               int* nactive) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int RBP = kPcgRows + 1;  // S chunk [c][RBP]: lane c reads column c
+  const PcgTask tk = tasks[blockIdx.x];
+  const PcgProb P = probs[tk.prob];
+  const int k = use_lmp ? P.k : 0;
+  TS* Ssm = reinterpret_cast<TS*>(smraw);
+  TS* rsm = Ssm + (size_t)kmax * RBP;  // [kWarps][kPcgRows]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const TS* S = static_cast<const TS*>(P.S);
+  for (int idx = threadIdx.x; idx < k * tk.rows; idx += kThreads) {
+    const int c = idx / tk.rows, i = idx - c * tk.rows;
+    Ssm[c * RBP + i] = S[(long long)c * P.n + tk.row0 + i];
+  }
+  // slot par^1 collects r.z in the precond launch that follows
+  if (update && tk.first)
+    for (int m = threadIdx.x; m < P.M; m += kThreads) acc[P.item0 + m].rz[par ^ 1] = 0.0;
+  __syncthreads();
+  TS* rw = rsm + wid * kPcgRows;
+  for (int m = wid; m < P.M; m += kWarps) {
+    const int item = P.item0 + m;
+    if (!active[item]) continue;
+    const long long off = P.off0 + (long long)m * P.n + tk.row0;
+    if (update) {
+      const double pq = acc[item].pq;
+      if (!(pq > 0.0)) {  // breakdown (or NaN): every CTA skips the member
+        if (tk.first && lane == 0) {
+          sc[item].status = isfinite(pq) ? EDA_BREAKDOWN : EDA_NAN;
+          active[item] = 0;
+          atomicSub(nactive, 1);
+        }
+        continue;
+      }
+      const double alpha = acc[item].rz[par] / pq;
+      double rr = 0.0;
+      for (int i = lane; i < tk.rows; i += 32) {
+        const double pv = p[off + i], qv = q[off + i];
+        x[off + i] += alpha * pv;
+        const double rv = r[off + i] - alpha * qv;
+        r[off + i] = rv;
+        rr += rv * rv;
+        rw[i] = (TS)rv;
+      }
+      rr = warp_sum(rr);
+      if (lane == 0) atomicAdd(&acc[item].rr, rr);
+    } else {
+      for (int i = lane; i < tk.rows; i += 32) rw[i] = (TS)r[off + i];
+    }
+    __syncwarp();
+    for (int c = lane; c < k; c += 32) {
+      const TS* Sc = Ssm + c * RBP;
+      TS s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      int i = 0;
+      for (; i + 4 <= tk.rows; i += 4) {
+        s0 += Sc[i] * rw[i];
+        s1 += Sc[i + 1] * rw[i + 1];
+        s2 += Sc[i + 2] * rw[i + 2];
+        s3 += Sc[i + 3] * rw[i + 3];
+      }
+      for (; i < tk.rows; ++i) s0 += Sc[i] * rw[i];
+      atomicAdd(&Wk[(long long)item * kmax + c], (s0 + s1) + (s2 + s3));
+    }
+    __syncwarp();
+  }
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* tasks, const PcgProb* probs, int kmax,
+                                                                const double* r, double* z, double* p,
+                                                                PcgScalars* sc, PcgAcc* acc, int* active,
+                                                                const TS* Wk, int par, double tol, int maxit,
+                                                                int fixed, int use_lmp, int init, int* nactive) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const PcgTask tk = tasks[blockIdx.x];
+  const PcgProb P = probs[tk.prob];
+  const int k = use_lmp ? P.k : 0;
+  const int KP = odd_stride(k);
+  TS* Ssm = reinterpret_cast<TS*>(smraw);  // [row][KP]: lane = row reads a row
+  TS* wsm = Ssm + (size_t)kPcgRows * KP;   // [kWarps][kmax]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const TS* S = static_cast<const TS*>(P.S);
+  for (int idx = threadIdx.x; idx < k * tk.rows; idx += kThreads) {
+    const int c = idx / tk.rows, i = idx - c * tk.rows;
+    Ssm[i * KP + c] = S[(long long)c * P.n + tk.row0 + i];
+  }
+  // p^T q of the next sweep accumulates from zero
+  if (tk.first)
+    for (int m = threadIdx.x; m < P.M; m += kThreads) acc[P.item0 + m].pq = 0.0;
+  __syncthreads();
+  const int slot = init ? 0 : (par ^ 1);
+  TS* wc = wsm + wid * kmax;
+  for (int m = wid; m < P.M; m += kWarps) {
+    const int item = P.item0 + m;
+    if (!active[item]) continue;
+    if (!init) {
+      // the stopping test, from values no CTA of this launch writes
+      const double bn = sc[item].bnorm;
+      const double rel = bn > 0.0 ? sqrt(acc[item].rr) / bn : 0.0;
+      const int itj = sc[item].iters + 1;
+      const double tolm = sc[item].tolm;
+      bool stop = false;
+      int st = EDA_MAXIT;
+      if (!isfinite(rel)) {
+        st = EDA_NAN;
+        stop = true;
+      } else if (fixed > 0) {
+        if (itj >= fixed) {
+          st = EDA_CONVERGED;
+          stop = true;
+        }
+      } else if (rel <= (tolm > 0.0 ? tolm : tol)) {
+        st = EDA_CONVERGED;
+        stop = true;
+      } else if (maxit > 0 && itj >= maxit) {
+        stop = true;
+      }
+      if (tk.first && lane == 0) {
+        sc[item].relres = rel;
+        acc[item].inc = 1;
+        if (stop) {
+          sc[item].status = st;
+          active[item] = 0;
+          atomicSub(nactive, 1);
+        }
+      }
+      if (stop) continue;
+    }
+    for (int c = lane; c < k; c += 32) wc[c] = (TS)(P.c[c] * (double)Wk[(long long)item * kmax + c]);
+    __syncwarp();
+    const long long off = P.off0 + (long long)m * P.n + tk.row0;
+    double rz = 0.0;
+    for (int i = lane; i < tk.rows; i += 32) {
+      const double rv = r[off + i];
+      double zv = rv;
+      if (k > 0) {
+        const TS* Srow = Ssm + i * KP;
+        TS s0 = 0, s1 = 0;
+        int c = 0;
+        for (; c + 2 <= k; c += 2) {
+          s0 += Srow[c] * wc[c];
+          s1 += Srow[c + 1] * wc[c + 1];
+        }
+        if (c < k) s0 += Srow[c] * wc[c];
+        zv += (double)(s0 + s1);
+      }
+      z[off + i] = zv;
+      if (init) p[off + i] = zv;
+      rz += rv * zv;
+    }
+    rz = warp_sum(rz);
+    if (lane == 0) atomicAdd(&acc[item].rz[slot], rz);
+    __syncwarp();
+  }
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(kThreads) pcg2_dir_kernel(const PcgTask* tasks, const PcgProb* probs, int kmax,
+                                                            const double* z, double* p, PcgScalars* sc, PcgAcc* acc,
+                                                            const int* active, TS* Wk, int par) {
+  const PcgTask tk = tasks[blockIdx.x];
+  const PcgProb P = probs[tk.prob];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (tk.first) {
+    // bookkeeping of the problem: iteration counts, and the accumulators
+    // the next update launch fills
+    for (int m = threadIdx.x; m < P.M; m += kThreads) {
+      const int item = P.item0 + m;
+      if (acc[item].inc) {
+        sc[item].iters += 1;
+        acc[item].inc = 0;
+      }
+      acc[item].rr = 0.0;
+    }
+    for (int idx = threadIdx.x; idx < P.M * kmax; idx += kThreads)
+      Wk[(long long)P.item0 * kmax + idx] = TS(0);
+  }
+  for (int m = wid; m < P.M; m += kWarps) {
+    const int item = P.item0 + m;
+    if (!active[item]) continue;
+    const double beta = acc[item].rz[par ^ 1] / acc[item].rz[par];
+    const long long off = P.off0 + (long long)m * P.n + tk.row0;
+    for (int i = lane; i < tk.rows; i += 32) p[off + i] = z[off + i] + beta * p[off + i];
+  }
+}
+
+__global__ void pcg2_reset_kernel(PcgAcc* acc, int T) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < T; j += gridDim.x * blockDim.x) {
+    PcgAcc a;
+    a.pq = a.rr = a.rz[0] = a.rz[1] = 0.0;
+    a.inc = a.pad = 0;
+    acc[j] = a;
+  }
+}
+
+__global__ void pcg2_col_dot_kernel(int n, const double* v, const double* hv, const int* active, PcgAcc* acc) {
+  __shared__ double red[kWarps];
+  const int col = blockIdx.y;
+  if (active && !active[col]) return;
+  const long long base = (long long)col * n;
+  double s = 0.0;
+  for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) s += v[base + i] * hv[base + i];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kWarps; ++w) t += red[w];
+    atomicAdd(&acc[col].pq, t);
+  }
+}
+
+template <typename K>
+cudaError_t set_smem(K kern, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace
+
+void pcg_tasks(const int* n_of, int nprob, std::vector<PcgTask>* out) {
+  out->clear();
+  for (int pi = 0; pi < nprob; ++pi)
+    for (int r0 = 0; r0 < n_of[pi]; r0 += kPcgRows) {
+      const int rows = (n_of[pi] - r0 < kPcgRows) ? n_of[pi] - r0 : kPcgRows;
+      out->push_back(PcgTask{pi, r0, rows, r0 == 0 ? 1 : 0});
+    }
+}
+
+cudaError_t pcg2_reset(PcgAcc* acc, int T, void* Wk, size_t wk_bytes, cudaStream_t s) {
+  if (T <= 0) return cudaSuccess;
+  count_launch();
+  pcg2_reset_kernel<<<(T + 255) / 256, 256, 0, s>>>(acc, T);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || wk_bytes == 0) return e;
+  return cudaMemsetAsync(Wk, 0, wk_bytes, s);
+}
+
+template <typename TS>
+cudaError_t pcg2_update(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, const double* p,
+                        const double* q, double* x, double* r, PcgScalars* sc, PcgAcc* acc, int* active, TS* Wk,
+                        int par, int update, int use_lmp, int* nactive, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  const size_t smem = ((size_t)kmax * (kPcgRows + 1) + (size_t)kWarps * kPcgRows) * sizeof(TS);
+  cudaError_t e = set_smem(pcg2_update_kernel<TS>, smem);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  pcg2_update_kernel<TS><<<ntasks, kThreads, smem, s>>>(tasks, probs, kmax, p, q, x, r, sc, acc, active, Wk, par,
+                                                        update, use_lmp, nactive);
+  return cudaGetLastError();
+}
+
+template <typename TS>
+cudaError_t pcg2_precond(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, const double* r,
+                         double* z, double* p, PcgScalars* sc, PcgAcc* acc, int* active, const TS* Wk, int par,
+                         double tol, int maxit, int fixed, int use_lmp, int init, int* nactive, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  const size_t smem = ((size_t)kPcgRows * odd_stride(kmax) + (size_t)kWarps * (kmax > 0 ? kmax : 1)) * sizeof(TS);
+  cudaError_t e = set_smem(pcg2_precond_kernel<TS>, smem);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  pcg2_precond_kernel<TS><<<ntasks, kThreads, smem, s>>>(tasks, probs, kmax, r, z, p, sc, acc, active, Wk, par, tol,
+                                                         maxit, fixed, use_lmp, init, nactive);
+  return cudaGetLastError();
+}
+
+template <typename TS>
+cudaError_t pcg2_dir(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, const double* z, double* p,
+                     PcgScalars* sc, PcgAcc* acc, const int* active, TS* Wk, int par, cudaStream_t s) {
+  if (ntasks <= 0) return cudaSuccess;
+  count_launch();
+  pcg2_dir_kernel<TS><<<ntasks, kThreads, 0, s>>>(tasks, probs, kmax, z, p, sc, acc, active, Wk, par);
+  return cudaGetLastError();
+}
+
+cudaError_t pcg2_col_dot(int n, int ncol, const double* v, const double* hv, const int* active, PcgAcc* acc,
+                         cudaStream_t s) {
+  if (ncol <= 0) return cudaSuccess;
+  int bx = (n + kThreads * 4 - 1) / (kThreads * 4);
+  if (bx > 64) bx = 64;
+  count_launch();
+  pcg2_col_dot_kernel<<<dim3(bx, ncol), kThreads, 0, s>>>(n, v, hv, active, acc);
+  return cudaGetLastError();
+}
+
+template cudaError_t pcg2_update<double>(const PcgTask*, int, const PcgProb*, int, const double*, const double*,
+                                         double*, double*, PcgScalars*, PcgAcc*, int*, double*, int, int, int, int*,
+                                         cudaStream_t);
+template cudaError_t pcg2_update<float>(const PcgTask*, int, const PcgProb*, int, const double*, const double*,
+                                        double*, double*, PcgScalars*, PcgAcc*, int*, float*, int, int, int, int*,
+                                        cudaStream_t);
+template cudaError_t pcg2_precond<double>(const PcgTask*, int, const PcgProb*, int, const double*, double*, double*,
+                                          PcgScalars*, PcgAcc*, int*, const double*, int, double, int, int, int,
+                                          int, int*, cudaStream_t);
+template cudaError_t pcg2_precond<float>(const PcgTask*, int, const PcgProb*, int, const double*, double*, double*,
+                                         PcgScalars*, PcgAcc*, int*, const float*, int, double, int, int, int, int,
+                                         int*, cudaStream_t);
+template cudaError_t pcg2_dir<double>(const PcgTask*, int, const PcgProb*, int, const double*, double*, PcgScalars*,
+                                      PcgAcc*, const int*, double*, int, cudaStream_t);
+template cudaError_t pcg2_dir<float>(const PcgTask*, int, const PcgProb*, int, const double*, double*, PcgScalars*,
+                                     PcgAcc*, const int*, float*, int, cudaStream_t);
+
+}  // namespace eda

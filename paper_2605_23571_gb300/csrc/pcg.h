@@ -1,0 +1,88 @@
+// Batched preconditioned CG (Section 2.3) with the scaled spectral LMP
+// (Section 3.1), one iteration as four launches over row chunks of all
+// members of all problems:
+//   sweep   q = H p, with p^T q accumulated per member in its epilogue;
+//   update  alpha = r.z / p.q, x += alpha p, r -= alpha q, ||r||^2 and the
+//           LMP projections w = S^T r (split over row chunks);
+//   precond the per-member stopping test, z = r + S diag(c) w, r.z;
+//   dir     beta = (r.z)_new / (r.z)_old, p = z + beta p.
+// Reductions over rows go to per-member accumulators with atomics.  r.z is
+// double-buffered by iteration parity and every accumulator is zeroed by a
+// launch that does not read it, so no launch reads a value that another CTA
+// of the same launch writes.  The per-member stopping test is taken by every
+// CTA from values no CTA of that launch writes; the CTA of a problem's first
+// row chunk records it.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "dense.h"
+
+namespace eda {
+
+// Per-member accumulators of one iteration (40 bytes: pq is the first
+// double, so the sweep epilogue adds p^T q at acc + 5 * member).
+struct PcgAcc {
+  double pq;     // p^T q of this iteration (sweep epilogue)
+  double rr;     // ||r||^2 after the update
+  double rz[2];  // r^T z by iteration parity
+  int inc;       // 1: the member iterated (set by precond, counted by dir)
+  int pad;
+};
+constexpr int kPcgAccStride = (int)(sizeof(PcgAcc) / sizeof(double));
+
+// One problem of the batch: members item0 .. item0+M-1, member m's vectors
+// at off0 + m * n of the concatenated layout; S is k x n column-major (TS),
+// c the k LMP coefficients (k = 0: no LMP).
+struct PcgProb {
+  int n, M, k, item0;
+  long long off0;
+  const void* S;
+  const double* c;
+};
+
+// A chunk of rows [row0, row0 + rows) of one problem (rows <= kPcgRows);
+// first = 1 for the chunk with row0 = 0, whose CTA does the problem's
+// per-member bookkeeping.
+struct PcgTask {
+  int prob, row0, rows, first;
+};
+constexpr int kPcgRows = 64;
+
+// Builds the row-chunk tasks of the given problem sizes.
+void pcg_tasks(const int* n_of, int nprob, std::vector<PcgTask>* out);
+
+// Zeroes the accumulators of every member and its projections (start of a
+// PCG loop).
+cudaError_t pcg2_reset(PcgAcc* acc, int T, void* Wk, size_t wk_bytes, cudaStream_t s);
+
+// update = 1: the CG update and the projections of the new r.
+// update = 0: projections of the current r only (start of a loop).
+// use_lmp = 0: no projections.
+template <typename TS>
+cudaError_t pcg2_update(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, const double* p,
+                        const double* q, double* x, double* r, PcgScalars* sc, PcgAcc* acc, int* active, TS* Wk,
+                        int par, int update, int use_lmp, int* nactive, cudaStream_t s);
+
+// init = 0: stopping test (tol, maxit, fixed), then z and r.z into slot
+// par^1 for the members that go on.  init = 1 (start of a loop): no test;
+// z, p = z and r.z into slot 0; the caller then clears the projections
+// before the first update.
+template <typename TS>
+cudaError_t pcg2_precond(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, const double* r,
+                         double* z, double* p, PcgScalars* sc, PcgAcc* acc, int* active, const TS* Wk, int par,
+                         double tol, int maxit, int fixed, int use_lmp, int init, int* nactive, cudaStream_t s);
+
+// p = z + beta p; counts the iteration and clears rr and the projections.
+template <typename TS>
+cudaError_t pcg2_dir(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, const double* z, double* p,
+                     PcgScalars* sc, PcgAcc* acc, const int* active, TS* Wk, int par, cudaStream_t s);
+
+// acc[col].pq += v_col . hv_col for active columns of an [ncol][n] batch
+// (used where the sweep epilogue cannot accumulate it).
+cudaError_t pcg2_col_dot(int n, int ncol, const double* v, const double* hv, const int* active, PcgAcc* acc,
+                         cudaStream_t s);
+
+}  // namespace eda

@@ -25,6 +25,7 @@
 #include <cooperative_groups.h>
 
 #include "eda_internal.h"
+#include "pcg.h"
 
 namespace cg = cooperative_groups;
 
@@ -230,7 +231,7 @@ __device__ __forceinline__ void conv_run(const T* src, int base, int w, const T*
 // E + 2w values.
 template <typename T, int C, typename TO>
 __device__ void bhalf_from_mirrors(const SweepArgs<T>& a, const Geo& g, T* mir, T* stage, const T* cf,
-                                   TO* out, const double* ident64, const T* ident) {
+                                   TO* out, const double* ident64, const T* ident, double* dot) {
   const int w = a.w;
   const int cnt = g.Town + 2 * w;
   for (int j = g.tid; j < cnt; j += g.NT) {
@@ -248,6 +249,7 @@ __device__ void bhalf_from_mirrors(const SweepArgs<T>& a, const Geo& g, T* mir, 
   // every remote read of this cluster's mirrors is complete after this barrier
   sync_cluster_or_block(g.CS > 1);
   const int j0 = g.tid * C;
+  double part = 0.0;  // v . (H v) over this thread's outputs
   if (j0 < g.Town) {
     T o[C];
     conv_run<T, C>(stage, j0, w, cf, o);
@@ -255,10 +257,27 @@ __device__ void bhalf_from_mirrors(const SweepArgs<T>& a, const Geo& g, T* mir, 
     for (int c = 0; c < C; ++c) {
       if (j0 + c < g.Town) {
         TO v = (TO)o[c];
-        if (ident64) v += (TO)ident64[g.a0 + j0 + c];
-        else if (ident) v += (TO)ident[g.a0 + j0 + c];
+        double in = 0.0;
+        if (ident64) in = ident64[g.a0 + j0 + c];
+        else if (ident) in = (double)ident[g.a0 + j0 + c];
+        if (ident64 || ident) v += (TO)in;
         out[g.a0 + j0 + c] = v;
+        part += in * (double)v;
       }
+    }
+  }
+  if (dot != nullptr) {  // uniform over the CTA
+    // the mirror is free here: every remote read of it ended at the cluster
+    // barrier above, and the outputs were taken from the stage area
+    double* red = reinterpret_cast<double*>(mir);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((g.tid & 31) == 0) red[g.tid >> 5] = part;
+    __syncthreads();
+    if (g.tid == 0) {
+      double t = 0.0;
+      for (int i = 0; i < g.NT / 32; ++i) t += red[i];
+      atomicAdd(dot, t);
     }
   }
 }
@@ -341,9 +360,11 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   const int Emax = (int)blockDim.x * C;
   const int wmax = a0.w;
   int member, A_act = (int)blockDim.x;
+  int item = col;  // accumulator index of the column (dot_out)
   long long voff, soff;
   if (a.items != nullptr) {
     const SweepItem it = a.items[col];
+    item = it.flag;
     if (it.flag >= 0 && a.flags[it.flag] == 0) return;  // uniform over the cluster
     const SweepProb<T> P = a.probs[it.prob];
     a.n = P.n;
@@ -828,11 +849,13 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   write_mirror(mir, g, lam);
   sync_cluster_or_block(clus);
   const bool ident = (a.mode == MODE_HVP && a.include_identity);
+  double* dot = (ident && a.dot_out != nullptr) ? a.dot_out + (long long)item * a.dot_stride : nullptr;
   if (a.OUT64) {
     bhalf_from_mirrors<T, C, double>(a, g, mir, stage, cf, a.OUT64 + voff, ident ? V64 : nullptr,
-                                     ident ? V : nullptr);
+                                     ident ? V : nullptr, dot);
   } else {
-    bhalf_from_mirrors<T, C, T>(a, g, mir, stage, cf, a.OUT + voff, ident ? V64 : nullptr, ident ? V : nullptr);
+    bhalf_from_mirrors<T, C, T>(a, g, mir, stage, cf, a.OUT + voff, ident ? V64 : nullptr, ident ? V : nullptr,
+                                dot);
   }
 }
 
@@ -1082,7 +1105,18 @@ cudaError_t launch_sweep(const SweepArgs<T>& a0, const SweepPlan& p, cudaStream_
   else
     bhalf_out_kernel<T, T><<<(unsigned)blocks, 256, 0, s>>>(a.n, a.w, a.bcoef, a.ncol, buf[cur], a.V64, a.V, a.OUT,
                                                             ident);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !(ident && a.dot_out != nullptr)) return e;
+  // v . (H v) per column (the cluster epilogue accumulates it in place);
+  // column c of a multi-launch sweep is accumulator c
+  const double* vin = a.V64;
+  const double* vout = a.OUT64;
+  if constexpr (sizeof(T) == 8) {
+    if (vin == nullptr) vin = a.V;
+    if (vout == nullptr) vout = a.OUT;
+  }
+  if (vin == nullptr || vout == nullptr || a.dot_stride != kPcgAccStride) return cudaErrorInvalidValue;
+  return pcg2_col_dot(a.n, a.ncol, vin, vout, a.col_active, reinterpret_cast<PcgAcc*>(a.dot_out), s);
 }
 
 template cudaError_t launch_sweep<double>(const SweepArgs<double>&, const SweepPlan&, cudaStream_t, double*, double*);
