@@ -582,16 +582,17 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
     SweepPlan best = keep;
     float best_ms = 1e30f;
     const int reps = fp64 ? 1 : 3;
-    // candidates: single-launch cluster plans (CS 1..8), then multi-launch
-    // plans where a column spans several tiles
+    // candidates: single-launch cluster plans (CS 1..8, two run lengths),
+    // then multi-launch plans where a column spans several tiles
     std::vector<SweepPlan> cands;
-    for (int CS = 1; CS <= 8; ++CS)
-      for (int K : Ks) {
-        SweepPlan pl;
-        if (!eda::plan_sweep_exact(h->n, fp64 ? 8 : 4, h->w, CS, K, &pl)) continue;
-        if (pl.HL > h->n && CS > 1) continue;
-        cands.push_back(pl);
-      }
+    for (int C : {fp64 ? 4 : 8, fp64 ? 2 : 4})  // values per thread
+      for (int CS = 1; CS <= 8; ++CS)
+        for (int K : Ks) {
+          SweepPlan pl;
+          if (!eda::plan_sweep_exact(h->n, fp64 ? 8 : 4, h->w, CS, K, &pl, C)) continue;
+          if (pl.HL > h->n && CS > 1) continue;
+          cands.push_back(pl);
+        }
     for (int A : {128, 256, 512})
       for (int K : Ks) {
         SweepPlan pl;
@@ -749,16 +750,18 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
 
   // Sweep tiling: a single-launch cluster plan where one fits, else the
   // multi-launch plan.  EDA_SWEEP_K fixes the refresh period;
-  // EDA_SWEEP_CS64/CS32 the smallest cluster size; EDA_SWEEP_ML=<threads>
-  // forces multi-launch tiles of that many threads.
+  // EDA_SWEEP_CS64/CS32 the smallest cluster size; EDA_SWEEP_C64/C32 the
+  // values per thread; EDA_SWEEP_ML=<threads> forces multi-launch tiles of
+  // that many threads.
   const int Kh = env_int("EDA_SWEEP_K", 0);
   const int cs64 = env_int("EDA_SWEEP_CS64", 1), cs32 = env_int("EDA_SWEEP_CS32", 1);
   const int mlA = env_int("EDA_SWEEP_ML", 0);
+  const int c64 = env_int("EDA_SWEEP_C64", 0), c32 = env_int("EDA_SWEEP_C32", 0);
   const bool planned =
       mlA > 0 ? (eda::plan_sweep_ml(h->n, 8, h->w, Kh > 0 ? Kh : 16, mlA, &h->plan64) &&
                  eda::plan_sweep_ml(h->n, 4, h->w, Kh > 0 ? Kh : 16, mlA, &h->plan32))
-              : (eda::plan_sweep(h->n, 8, h->w, cs64, Kh, &h->plan64) &&
-                 eda::plan_sweep(h->n, 4, h->w, cs32, Kh, &h->plan32));
+              : (eda::plan_sweep(h->n, 8, h->w, cs64, Kh, &h->plan64, c64) &&
+                 eda::plan_sweep(h->n, 4, h->w, cs32, Kh, &h->plan32, c32));
   if (!planned) {
     fail(nullptr, EDA_ERR_INVALID, "state size too large for the sweep tiling");
     return bail(EDA_ERR_INVALID);
@@ -1227,9 +1230,9 @@ int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int*
   TS* Wk = reinterpret_cast<TS*>(h->Wk);
   // start: z = P r, p = z, r.z
   CU(h, eda::pcg2_reset(h->acc, M, Wk, (size_t)M * kmax * sizeof(TS), h->st));
-  CU(h, eda::pcg2_update<TS>(h->tasks, h->ntasks, h->probs, kmax, h->pv, h->q, h->x, h->r, h->sc, h->acc, h->active,
+  CU(h, eda::pcg2_update<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->pv, h->q, h->x, h->r, h->sc, h->acc, h->active,
                              Wk, 0, 0, lmp, h->nactive, h->st));
-  CU(h, eda::pcg2_precond<TS>(h->tasks, h->ntasks, h->probs, kmax, h->r, h->z, h->pv, h->sc, h->acc, h->active, Wk,
+  CU(h, eda::pcg2_precond<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->r, h->z, h->pv, h->sc, h->acc, h->active, Wk,
                               0, tol, maxit, fixed, lmp, 1, h->nactive, h->st));
   // the first update accumulates the projections of r_1 from zero
   CU(h, cudaMemsetAsync(Wk, 0, (size_t)M * kmax * sizeof(TS), h->st));
@@ -1242,11 +1245,11 @@ int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int*
     ++it;
     int rc = hvp_dev(h, h->cols, M, h->pv, h->q, 1, sweep64, h->active, reinterpret_cast<double*>(h->acc));
     if (rc) return rc;
-    CU(h, eda::pcg2_update<TS>(h->tasks, h->ntasks, h->probs, kmax, h->pv, h->q, h->x, h->r, h->sc, h->acc,
+    CU(h, eda::pcg2_update<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->pv, h->q, h->x, h->r, h->sc, h->acc,
                                h->active, Wk, par, 1, lmp, h->nactive, h->st));
-    CU(h, eda::pcg2_precond<TS>(h->tasks, h->ntasks, h->probs, kmax, h->r, h->z, h->pv, h->sc, h->acc, h->active,
+    CU(h, eda::pcg2_precond<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->r, h->z, h->pv, h->sc, h->acc, h->active,
                                 Wk, par, tol, maxit, fixed, lmp, 0, h->nactive, h->st));
-    CU(h, eda::pcg2_dir<TS>(h->tasks, h->ntasks, h->probs, kmax, h->z, h->pv, h->sc, h->acc, h->active, Wk, par,
+    CU(h, eda::pcg2_dir<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->z, h->pv, h->sc, h->acc, h->active, Wk, par,
                             h->st));
     const int slot = it % R;
     CU(h, cudaMemcpyAsync(h->hring + slot, h->nactive, sizeof(int), cudaMemcpyDeviceToHost, h->st));

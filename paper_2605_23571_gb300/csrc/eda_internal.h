@@ -119,8 +119,9 @@ struct SweepPlan {
 
 // Picks the tiling of a sweep for state size n (elem_bytes = sizeof(T)):
 // the smallest cluster size >= min_cs whose tile fits one CTA.  K_hint > 0
-// fixes the halo refresh period.  Returns false if no plan fits.
-bool plan_sweep(int n, int elem_bytes, int w, int min_cs, int K_hint, SweepPlan* out);
+// fixes the halo refresh period, C > 0 the values per thread (as in
+// plan_sweep_exact).  Returns false if no plan fits.
+bool plan_sweep(int n, int elem_bytes, int w, int min_cs, int K_hint, SweepPlan* out, int C = 0);
 
 // Dynamic shared memory of a sweep launch with A threads, runs of C and
 // at most w+1 taps.
@@ -131,8 +132,10 @@ size_t sweep_smem_bytes(int A, int C, int w, int elem_bytes);
 // 32 up to 512).
 bool plan_sweep_ml(int n, int elem_bytes, int w, int K, int A, SweepPlan* out);
 
-// The plan with exactly cluster size CS and refresh period K, if it fits.
-bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* out);
+// The plan with exactly cluster size CS, refresh period K and C values per
+// thread (C = 0: 4 for FP64, 8 for FP32; else FP64 2 or 4, FP32 4 or 8), if
+// it fits.
+bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* out, int C = 0);
 
 // Per-CTA observation ranges of a plan: for CTA r and observation step j,
 // tab[(r*nos + j)*8 + 0..1] = [k0, k1) of the observations of the owned tile,

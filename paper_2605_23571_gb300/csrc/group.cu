@@ -54,6 +54,7 @@ struct eda_group {
   const double** d_c_of = nullptr;
   int* d_k_of = nullptr;
   int kmax = 0;
+  int mmax = 0;  // largest member count of the problems
   long long vtot = 0, stot = 0;
   double *b = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
   double* stash64 = nullptr;
@@ -405,11 +406,11 @@ int group_iteration(eda_group* g, bool sweep64, bool use_lmp, double tol, int ma
   TS* Wk = reinterpret_cast<TS*>(g->Wk);
   int rc = group_sweep(g, sweep64, g->p, g->q, 1, false, reinterpret_cast<double*>(g->acc));
   if (rc) return rc;
-  GCU(g, eda::pcg2_update<TS>(g->tasks, g->ntasks, g->probs, kmax, g->p, g->q, g->x, g->r, g->sc, g->acc, g->active,
+  GCU(g, eda::pcg2_update<TS>(g->tasks, g->ntasks, g->probs, kmax, g->mmax, g->p, g->q, g->x, g->r, g->sc, g->acc, g->active,
                               Wk, par, 1, lmp, g->nactive, g->st));
-  GCU(g, eda::pcg2_precond<TS>(g->tasks, g->ntasks, g->probs, kmax, g->r, g->z, g->p, g->sc, g->acc, g->active, Wk,
+  GCU(g, eda::pcg2_precond<TS>(g->tasks, g->ntasks, g->probs, kmax, g->mmax, g->r, g->z, g->p, g->sc, g->acc, g->active, Wk,
                                par, tol, maxit, fixed, lmp, 0, g->nactive, g->st));
-  GCU(g, eda::pcg2_dir<TS>(g->tasks, g->ntasks, g->probs, kmax, g->z, g->p, g->sc, g->acc, g->active, Wk, par,
+  GCU(g, eda::pcg2_dir<TS>(g->tasks, g->ntasks, g->probs, kmax, g->mmax, g->z, g->p, g->sc, g->acc, g->active, Wk, par,
                            g->st));
   return EDA_OK;
 }
@@ -421,9 +422,9 @@ int group_start(eda_group* g, bool use_lmp, double tol, int maxit, int fixed) {
   const int lmp = use_lmp ? 1 : 0;
   TS* Wk = reinterpret_cast<TS*>(g->Wk);
   GCU(g, eda::pcg2_reset(g->acc, g->T, Wk, (size_t)g->T * kmax * sizeof(TS), g->st));
-  GCU(g, eda::pcg2_update<TS>(g->tasks, g->ntasks, g->probs, kmax, g->p, g->q, g->x, g->r, g->sc, g->acc, g->active,
+  GCU(g, eda::pcg2_update<TS>(g->tasks, g->ntasks, g->probs, kmax, g->mmax, g->p, g->q, g->x, g->r, g->sc, g->acc, g->active,
                               Wk, 0, 0, lmp, g->nactive, g->st));
-  GCU(g, eda::pcg2_precond<TS>(g->tasks, g->ntasks, g->probs, kmax, g->r, g->z, g->p, g->sc, g->acc, g->active, Wk,
+  GCU(g, eda::pcg2_precond<TS>(g->tasks, g->ntasks, g->probs, kmax, g->mmax, g->r, g->z, g->p, g->sc, g->acc, g->active, Wk,
                                0, tol, maxit, fixed, lmp, 1, g->nactive, g->st));
   // the first update accumulates the projections of r_1 from zero
   GCU(g, cudaMemsetAsync(Wk, 0, (size_t)g->T * kmax * sizeof(TS), g->st));
@@ -546,6 +547,7 @@ EDA_API int eda_group_create(eda_handle* const* handles, int count, eda_group** 
       c_of.push_back(h->cv);
       k_of.push_back(h->k);
       g->kmax = std::max(g->kmax, h->k);
+      g->mmax = std::max(g->mmax, h->M);
       voff += h->n;
       soff += h->p;
     }

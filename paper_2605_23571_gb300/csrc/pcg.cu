@@ -40,13 +40,15 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* ta
     Ssm[c * RBP + i] = S[(long long)c * P.n + tk.row0 + i];
   }
   // slot par^1 collects r.z in the precond launch that follows
-  if (update && tk.first)
+  if (update && tk.first && blockIdx.y == 0)
     for (int m = threadIdx.x; m < P.M; m += kThreads) acc[P.item0 + m].rz[par ^ 1] = 0.0;
   __syncthreads();
   TS* rw = rsm + wid * kPcgRows;
-  for (int m = wid; m < P.M; m += kWarps) {
+  {
+    const int m = blockIdx.y * kWarps + wid;  // one member per warp
+    if (m >= P.M) return;
     const int item = P.item0 + m;
-    if (!active[item]) continue;
+    if (!active[item]) return;
     const long long off = P.off0 + (long long)m * P.n + tk.row0;
     if (update) {
       const double pq = acc[item].pq;
@@ -56,7 +58,7 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* ta
           active[item] = 0;
           atomicSub(nactive, 1);
         }
-        continue;
+        return;
       }
       const double alpha = acc[item].rz[par] / pq;
       double rr = 0.0;
@@ -87,7 +89,6 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* ta
       for (; i < tk.rows; ++i) s0 += Sc[i] * rw[i];
       atomicAdd(&Wk[(long long)item * kmax + c], (s0 + s1) + (s2 + s3));
     }
-    __syncwarp();
   }
 }
 
@@ -111,14 +112,16 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
     Ssm[i * KP + c] = S[(long long)c * P.n + tk.row0 + i];
   }
   // p^T q of the next sweep accumulates from zero
-  if (tk.first)
+  if (tk.first && blockIdx.y == 0)
     for (int m = threadIdx.x; m < P.M; m += kThreads) acc[P.item0 + m].pq = 0.0;
   __syncthreads();
   const int slot = init ? 0 : (par ^ 1);
   TS* wc = wsm + wid * kmax;
-  for (int m = wid; m < P.M; m += kWarps) {
+  {
+    const int m = blockIdx.y * kWarps + wid;  // one member per warp
+    if (m >= P.M) return;
     const int item = P.item0 + m;
-    if (!active[item]) continue;
+    if (!active[item]) return;
     if (!init) {
       // the stopping test, from values no CTA of this launch writes
       const double bn = sc[item].bnorm;
@@ -150,7 +153,7 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
           atomicSub(nactive, 1);
         }
       }
-      if (stop) continue;
+      if (stop) return;
     }
     for (int c = lane; c < k; c += 32) wc[c] = (TS)(P.c[c] * (double)Wk[(long long)item * kmax + c]);
     __syncwarp();
@@ -176,7 +179,6 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
     }
     rz = warp_sum(rz);
     if (lane == 0) atomicAdd(&acc[item].rz[slot], rz);
-    __syncwarp();
   }
 }
 
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(kThreads) pcg2_dir_kernel(const PcgTask* tasks
   const PcgTask tk = tasks[blockIdx.x];
   const PcgProb P = probs[tk.prob];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (tk.first) {
+  if (tk.first && blockIdx.y == 0) {
     // bookkeeping of the problem: iteration counts, and the accumulators
     // the next update launch fills
     for (int m = threadIdx.x; m < P.M; m += kThreads) {
@@ -201,9 +203,11 @@ __global__ void __launch_bounds__(kThreads) pcg2_dir_kernel(const PcgTask* tasks
     for (int idx = threadIdx.x; idx < P.M * kmax; idx += kThreads)
       Wk[(long long)P.item0 * kmax + idx] = TS(0);
   }
-  for (int m = wid; m < P.M; m += kWarps) {
+  {
+    const int m = blockIdx.y * kWarps + wid;  // one member per warp
+    if (m >= P.M) return;
     const int item = P.item0 + m;
-    if (!active[item]) continue;
+    if (!active[item]) return;
     const double beta = acc[item].rz[par ^ 1] / acc[item].rz[par];
     const long long off = P.off0 + (long long)m * P.n + tk.row0;
     for (int i = lane; i < tk.rows; i += 32) p[off + i] = z[off + i] + beta * p[off + i];
@@ -263,39 +267,39 @@ cudaError_t pcg2_reset(PcgAcc* acc, int T, void* Wk, size_t wk_bytes, cudaStream
 }
 
 template <typename TS>
-cudaError_t pcg2_update(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, const double* p,
+cudaError_t pcg2_update(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* p,
                         const double* q, double* x, double* r, PcgScalars* sc, PcgAcc* acc, int* active, TS* Wk,
                         int par, int update, int use_lmp, int* nactive, cudaStream_t s) {
-  if (ntasks <= 0) return cudaSuccess;
+  if (ntasks <= 0 || mmax <= 0) return cudaSuccess;
   const size_t smem = ((size_t)kmax * (kPcgRows + 1) + (size_t)kWarps * kPcgRows) * sizeof(TS);
   cudaError_t e = set_smem(pcg2_update_kernel<TS>, smem);
   if (e != cudaSuccess) return e;
   count_launch();
-  pcg2_update_kernel<TS><<<ntasks, kThreads, smem, s>>>(tasks, probs, kmax, p, q, x, r, sc, acc, active, Wk, par,
+  pcg2_update_kernel<TS><<<dim3(ntasks, (mmax + kWarps - 1) / kWarps), kThreads, smem, s>>>(tasks, probs, kmax, p, q, x, r, sc, acc, active, Wk, par,
                                                         update, use_lmp, nactive);
   return cudaGetLastError();
 }
 
 template <typename TS>
-cudaError_t pcg2_precond(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, const double* r,
+cudaError_t pcg2_precond(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* r,
                          double* z, double* p, PcgScalars* sc, PcgAcc* acc, int* active, const TS* Wk, int par,
                          double tol, int maxit, int fixed, int use_lmp, int init, int* nactive, cudaStream_t s) {
-  if (ntasks <= 0) return cudaSuccess;
+  if (ntasks <= 0 || mmax <= 0) return cudaSuccess;
   const size_t smem = ((size_t)kPcgRows * odd_stride(kmax) + (size_t)kWarps * (kmax > 0 ? kmax : 1)) * sizeof(TS);
   cudaError_t e = set_smem(pcg2_precond_kernel<TS>, smem);
   if (e != cudaSuccess) return e;
   count_launch();
-  pcg2_precond_kernel<TS><<<ntasks, kThreads, smem, s>>>(tasks, probs, kmax, r, z, p, sc, acc, active, Wk, par, tol,
+  pcg2_precond_kernel<TS><<<dim3(ntasks, (mmax + kWarps - 1) / kWarps), kThreads, smem, s>>>(tasks, probs, kmax, r, z, p, sc, acc, active, Wk, par, tol,
                                                          maxit, fixed, use_lmp, init, nactive);
   return cudaGetLastError();
 }
 
 template <typename TS>
-cudaError_t pcg2_dir(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, const double* z, double* p,
+cudaError_t pcg2_dir(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* z, double* p,
                      PcgScalars* sc, PcgAcc* acc, const int* active, TS* Wk, int par, cudaStream_t s) {
-  if (ntasks <= 0) return cudaSuccess;
+  if (ntasks <= 0 || mmax <= 0) return cudaSuccess;
   count_launch();
-  pcg2_dir_kernel<TS><<<ntasks, kThreads, 0, s>>>(tasks, probs, kmax, z, p, sc, acc, active, Wk, par);
+  pcg2_dir_kernel<TS><<<dim3(ntasks, (mmax + kWarps - 1) / kWarps), kThreads, 0, s>>>(tasks, probs, kmax, z, p, sc, acc, active, Wk, par);
   return cudaGetLastError();
 }
 
@@ -309,21 +313,21 @@ cudaError_t pcg2_col_dot(int n, int ncol, const double* v, const double* hv, con
   return cudaGetLastError();
 }
 
-template cudaError_t pcg2_update<double>(const PcgTask*, int, const PcgProb*, int, const double*, const double*,
+template cudaError_t pcg2_update<double>(const PcgTask*, int, const PcgProb*, int, int, const double*, const double*,
                                          double*, double*, PcgScalars*, PcgAcc*, int*, double*, int, int, int, int*,
                                          cudaStream_t);
-template cudaError_t pcg2_update<float>(const PcgTask*, int, const PcgProb*, int, const double*, const double*,
+template cudaError_t pcg2_update<float>(const PcgTask*, int, const PcgProb*, int, int, const double*, const double*,
                                         double*, double*, PcgScalars*, PcgAcc*, int*, float*, int, int, int, int*,
                                         cudaStream_t);
-template cudaError_t pcg2_precond<double>(const PcgTask*, int, const PcgProb*, int, const double*, double*, double*,
+template cudaError_t pcg2_precond<double>(const PcgTask*, int, const PcgProb*, int, int, const double*, double*, double*,
                                           PcgScalars*, PcgAcc*, int*, const double*, int, double, int, int, int,
                                           int, int*, cudaStream_t);
-template cudaError_t pcg2_precond<float>(const PcgTask*, int, const PcgProb*, int, const double*, double*, double*,
+template cudaError_t pcg2_precond<float>(const PcgTask*, int, const PcgProb*, int, int, const double*, double*, double*,
                                          PcgScalars*, PcgAcc*, int*, const float*, int, double, int, int, int, int,
                                          int*, cudaStream_t);
-template cudaError_t pcg2_dir<double>(const PcgTask*, int, const PcgProb*, int, const double*, double*, PcgScalars*,
+template cudaError_t pcg2_dir<double>(const PcgTask*, int, const PcgProb*, int, int, const double*, double*, PcgScalars*,
                                       PcgAcc*, const int*, double*, int, cudaStream_t);
-template cudaError_t pcg2_dir<float>(const PcgTask*, int, const PcgProb*, int, const double*, double*, PcgScalars*,
+template cudaError_t pcg2_dir<float>(const PcgTask*, int, const PcgProb*, int, int, const double*, double*, PcgScalars*,
                                      PcgAcc*, const int*, float*, int, cudaStream_t);
 
 }  // namespace eda

@@ -49,9 +49,11 @@ struct PcgProb {
 struct PcgTask {
   int prob, row0, rows, first;
 };
-constexpr int kPcgRows = 64;
+constexpr int kPcgRows = 128;
 
-// Builds the row-chunk tasks of the given problem sizes.
+// Builds the row-chunk tasks of the given problem sizes.  Every kernel
+// below runs a grid of (tasks, ceil(mmax / 8)) CTAs of 8 warps, one member
+// per warp (mmax: the largest member count of the problems).
 void pcg_tasks(const int* n_of, int nprob, std::vector<PcgTask>* out);
 
 // Zeroes the accumulators of every member and its projections (start of a
@@ -62,7 +64,7 @@ cudaError_t pcg2_reset(PcgAcc* acc, int T, void* Wk, size_t wk_bytes, cudaStream
 // update = 0: projections of the current r only (start of a loop).
 // use_lmp = 0: no projections.
 template <typename TS>
-cudaError_t pcg2_update(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, const double* p,
+cudaError_t pcg2_update(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* p,
                         const double* q, double* x, double* r, PcgScalars* sc, PcgAcc* acc, int* active, TS* Wk,
                         int par, int update, int use_lmp, int* nactive, cudaStream_t s);
 
@@ -71,13 +73,13 @@ cudaError_t pcg2_update(const PcgTask* tasks, int ntasks, const PcgProb* probs, 
 // z, p = z and r.z into slot 0; the caller then clears the projections
 // before the first update.
 template <typename TS>
-cudaError_t pcg2_precond(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, const double* r,
+cudaError_t pcg2_precond(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* r,
                          double* z, double* p, PcgScalars* sc, PcgAcc* acc, int* active, const TS* Wk, int par,
                          double tol, int maxit, int fixed, int use_lmp, int init, int* nactive, cudaStream_t s);
 
 // p = z + beta p; counts the iteration and clears rr and the projections.
 template <typename TS>
-cudaError_t pcg2_dir(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, const double* z, double* p,
+cudaError_t pcg2_dir(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* z, double* p,
                      PcgScalars* sc, PcgAcc* acc, const int* active, TS* Wk, int par, cudaStream_t s);
 
 // acc[col].pq += v_col . hv_col for active columns of an [ncol][n] batch

@@ -924,8 +924,10 @@ size_t sweep_smem_bytes(int A, int C, int w, int elem_bytes) {
   return elems * (size_t)elem_bytes + (size_t)kObsMapCap * sizeof(int) + 16;
 }
 
-bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* out) {
-  const int C = (elem_bytes == 8) ? 4 : 8;
+bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* out, int C) {
+  if (C == 0) C = (elem_bytes == 8) ? 4 : 8;
+  // instantiated runs: FP64 2 or 4 values per thread, FP32 4 or 8
+  if (elem_bytes == 8 ? (C != 2 && C != 4) : (C != 4 && C != 8)) return false;
   out->ml = 0;
   if (CS < 1 || CS > 16 || K < 1) return false;
   const int Ttile = (n + CS - 1) / CS;
@@ -971,10 +973,10 @@ bool plan_sweep_ml(int n, int elem_bytes, int w, int K, int A, SweepPlan* out) {
   return true;
 }
 
-bool plan_sweep(int n, int elem_bytes, int w, int min_cs, int K_hint, SweepPlan* out) {
+bool plan_sweep(int n, int elem_bytes, int w, int min_cs, int K_hint, SweepPlan* out, int C) {
   for (int CS = (min_cs > 1 ? min_cs : 1); CS <= 16; ++CS) {
     const int K = K_hint > 0 ? K_hint : (CS == 1 ? 4 : 8);
-    if (plan_sweep_exact(n, elem_bytes, w, CS, K, out)) {
+    if (plan_sweep_exact(n, elem_bytes, w, CS, K, out, C)) {
       out->ml = 0;
       return true;
     }
@@ -1026,12 +1028,13 @@ void obs_table(const SweepPlan& p, int n, int nos, const int* obs_ptr, const int
 template <typename T>
 cudaError_t launch_one(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t s) {
   if constexpr (sizeof(T) == 8) {
-    if (p.C != 4) return cudaErrorInvalidValue;
-    return launch_impl<T, 4>(a, p, s);
+    if (p.C == 4) return launch_impl<T, 4>(a, p, s);
+    if (p.C == 2) return launch_impl<T, 2>(a, p, s);
   } else {
-    if (p.C != 8) return cudaErrorInvalidValue;
-    return launch_impl<T, 8>(a, p, s);
+    if (p.C == 8) return launch_impl<T, 8>(a, p, s);
+    if (p.C == 4) return launch_impl<T, 4>(a, p, s);
   }
+  return cudaErrorInvalidValue;
 }
 
 template <typename T>

@@ -103,6 +103,33 @@ def test_hvp_fp64_cluster_split(cs):
                 assert rowrel(HV, ref).max() < 1e-11, (cs, K)
 
 
+@pytest.mark.parametrize("c64,c32", [(2, 4), (4, 8)])
+def test_hvp_with_each_run_length(c64, c32):
+    # every instantiated run length (values per thread) of the sweep kernel,
+    # alone and split over a cluster, FP64 against the oracle and the FP32
+    # sweep within single-precision error
+    spec = S.spec_small(600, 24, 4, every_var=2, every_step=3, length_scale=4.0, seed=15)
+    taps, xb, y = problem(spec)
+    traj, d, b = oracle_setup(spec, taps, xb, y)
+    cols = np.array([0, 1, 2, 3, 2], dtype=np.int32)
+    V = np.random.default_rng(4).standard_normal((len(cols), spec.n))
+    ref = O.hvp(spec, traj[cols], V, taps)
+    for cs in (1, 3):
+        with env(EDA_SWEEP_C64=c64, EDA_SWEEP_C32=c32, EDA_SWEEP_CS64=cs, EDA_SWEEP_CS32=cs):
+            with make(spec, taps) as h:
+                rhs = np.zeros_like(b)
+                h.eda_set_trajectory(xb, y, rhs)
+                assert rowrel(rhs, b).max() < 1e-11, (c64, cs)
+                HV = np.zeros_like(V)
+                h.eda_hvp(cols, V, HV, True)
+                assert rowrel(HV, ref).max() < 1e-11, (c64, cs)
+            with make(spec, taps, precision=P.EDA_MIXED) as h:
+                h.eda_set_trajectory(xb, y)
+                HV = np.zeros_like(V)
+                h.eda_hvp(cols, V, HV, True)
+                assert rowrel(HV, ref).max() < 1e-4, (c32, cs)
+
+
 def _ml_spec(n, seed):
     # observations at t = 0 and t = N as well as inside the window
     N = 13
