@@ -79,6 +79,36 @@ int set_plan(eda_handle* h, bool fp64, const SweepPlan& pl) {
   return EDA_OK;
 }
 
+int set_warp_plan(eda_handle* h, bool fp64, const SweepPlan* pl) {
+  int*& dt = fp64 ? h->wtab64 : h->wtab32;
+  SweepPlan& wp = fp64 ? h->wplan64 : h->wplan32;
+  if (dt) {
+    CU(h, cudaStreamSynchronize(h->st));
+    CU(h, cudaFree(dt));
+    dt = nullptr;
+  }
+  wp = SweepPlan{};
+  if (pl == nullptr) return EDA_OK;
+  std::vector<int> tab((size_t)pl->CS * (pl->A / 32) * h->nos * 8);
+  eda::warp_obs_table(*pl, h->n, h->nos, h->h_obs_ptr.data(), h->h_obs_idx.data(), tab.data());
+  CU(h, cudaMalloc((void**)&dt, std::max<size_t>(tab.size(), 1) * sizeof(int)));
+  CU(h, cudaMemcpy(dt, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice));
+  wp = *pl;
+  return EDA_OK;
+}
+
+const SweepPlan& hvp_plan(const eda_handle* h, bool fp64, const int** obs_tab, const int** wtab) {
+  const SweepPlan& wp = fp64 ? h->wplan64 : h->wplan32;
+  if (wp.warp) {
+    *obs_tab = nullptr;
+    *wtab = fp64 ? h->wtab64 : h->wtab32;
+    return wp;
+  }
+  *wtab = nullptr;
+  *obs_tab = fp64 ? (h->tab64_ok ? h->tab64 : nullptr) : (h->tab32_ok ? h->tab32 : nullptr);
+  return fp64 ? h->plan64 : h->plan32;
+}
+
 int ensure_ml(eda_handle* h, int ncol, bool fp64) {
   const SweepPlan& pl = fp64 ? h->plan64 : h->plan32;
   if (!pl.ml) return EDA_OK;
@@ -453,7 +483,8 @@ int hvp_launch(eda_handle* h, const int* dcols, int ncol, const double* V, doubl
     a.include_identity = ident;
     a.dot_out = dot;
     a.dot_stride = eda::kPcgAccStride;
-    CU(h, (eda::ensure_ml(h, a.ncol, true) == EDA_OK) ? eda::launch_sweep<double>(a, h->plan64, h->st, h->ml64[0], h->ml64[1]) : cudaErrorMemoryAllocation);
+    const SweepPlan& pl = eda::hvp_plan(h, true, &a.obs_tab, &a.wtab);
+    CU(h, (eda::ensure_ml(h, a.ncol, true) == EDA_OK) ? eda::launch_sweep<double>(a, pl, h->st, h->ml64[0], h->ml64[1]) : cudaErrorMemoryAllocation);
     return EDA_OK;
   }
   // FP32 sweeps reading and writing the FP64 vectors directly
@@ -471,7 +502,8 @@ int hvp_launch(eda_handle* h, const int* dcols, int ncol, const double* V, doubl
   a.include_identity = ident;
   a.dot_out = dot;
   a.dot_stride = eda::kPcgAccStride;
-  CU(h, (eda::ensure_ml(h, a.ncol, false) == EDA_OK) ? eda::launch_sweep<float>(a, h->plan32, h->st, h->ml32[0], h->ml32[1]) : cudaErrorMemoryAllocation);
+  const SweepPlan& pl = eda::hvp_plan(h, false, &a.obs_tab, &a.wtab);
+  CU(h, (eda::ensure_ml(h, a.ncol, false) == EDA_OK) ? eda::launch_sweep<float>(a, pl, h->st, h->ml32[0], h->ml32[1]) : cudaErrorMemoryAllocation);
   return EDA_OK;
 }
 
@@ -598,8 +630,16 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
         SweepPlan pl;
         if (eda::plan_sweep_ml(h->n, fp64 ? 8 : 4, h->w, 2 * K, A, &pl) && pl.CS >= 2) cands.push_back(pl);
       }
+    // warp-tiled plans (Hessian-product sweeps only)
+    for (int C : {fp64 ? 4 : 8, fp64 ? 2 : 4})
+      for (int CS = 2; CS <= 16; ++CS)
+        for (int K : {4, 8, 16}) {
+          SweepPlan pl;
+          if (eda::plan_sweep_warp(h->n, fp64 ? 8 : 4, h->w, CS, K, C, &pl)) cands.push_back(pl);
+        }
     for (const SweepPlan& pl : cands) {
-      int rc = set_plan(h, fp64, pl);
+      int rc = eda::set_warp_plan(h, fp64, pl.warp ? &pl : nullptr);
+      if (!rc && !pl.warp) rc = set_plan(h, fp64, pl);
       if (rc) return rc;
       float ms = 0.f;
       for (int rep = -1; rep < reps; ++rep) {
@@ -616,12 +656,16 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
         best = pl;
       }
     }
-    int rc = set_plan(h, fp64, best);
+    // the general plan serves the other sweeps; a warp-tiled winner serves
+    // the Hessian products beside it
+    int rc = set_plan(h, fp64, best.warp ? keep : best);
+    if (!rc) rc = eda::set_warp_plan(h, fp64, best.warp ? &best : nullptr);
     if (rc) return rc;
     best_total += best_ms;
     if (env_int("EDA_VERBOSE", 0))
       std::fprintf(stderr, "eda_autotune: %s sweep %s CS=%d K=%d A=%d E=%d C=%d %.4f ms\n", fp64 ? "FP64" : "FP32",
-                   best.ml ? "multi-launch" : "cluster", best.CS, best.K, best.A, best.E, best.C, best_ms);
+                   best.warp ? "warp-tiled" : (best.ml ? "multi-launch" : "cluster"), best.CS, best.K, best.A, best.E,
+                   best.C, best_ms);
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -766,6 +810,18 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
     fail(nullptr, EDA_ERR_INVALID, "state size too large for the sweep tiling");
     return bail(EDA_ERR_INVALID);
   }
+  // EDA_SWEEP_WARP=1: warp-tiled Hessian-product sweeps (cluster size from
+  // EDA_SWEEP_CS64/CS32 upwards, refresh period EDA_SWEEP_K or 8, values per
+  // lane EDA_SWEEP_C64/C32), where such a tiling fits
+  SweepPlan wp64{}, wp32{};
+  bool want_w64 = false, want_w32 = false;
+  if (env_int("EDA_SWEEP_WARP", 0)) {
+    const int Kw = Kh > 0 ? Kh : 8;
+    for (int cs = std::max(cs64, 2); cs <= 16 && !want_w64; ++cs)
+      want_w64 = eda::plan_sweep_warp(h->n, 8, h->w, cs, Kw, c64 ? c64 : 4, &wp64);
+    for (int cs = std::max(cs32, 2); cs <= 16 && !want_w32; ++cs)
+      want_w32 = eda::plan_sweep_warp(h->n, 4, h->w, cs, Kw, c32 ? c32 : 8, &wp32);
+  }
 
   h->h_obs_ptr.assign(c.obs_ptr, c.obs_ptr + h->nos + 1);
   h->h_obs_idx.assign(c.obs_idx, c.obs_idx + p);
@@ -855,7 +911,9 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
   CUC(cudaStreamSynchronize(h->st));
   {
     const SweepPlan p64 = h->plan64, p32 = h->plan32;
-    if (set_plan(h, true, p64) != EDA_OK || set_plan(h, false, p32) != EDA_OK) {
+    if (set_plan(h, true, p64) != EDA_OK || set_plan(h, false, p32) != EDA_OK ||
+        (want_w64 && eda::set_warp_plan(h, true, &wp64) != EDA_OK) ||
+        (want_w32 && eda::set_warp_plan(h, false, &wp32) != EDA_OK)) {
       eda::g_err = h->err;
       return bail(EDA_ERR_CUDA);
     }
@@ -878,6 +936,8 @@ EDA_API int eda_destroy(eda_handle* h) {
   }
   if (h->tab64) cudaFree(h->tab64);
   if (h->tab32) cudaFree(h->tab32);
+  if (h->wtab64) cudaFree(h->wtab64);
+  if (h->wtab32) cudaFree(h->wtab32);
   for (cudaEvent_t e : h->trace_ev)
     if (e) cudaEventDestroy(e);
   if (h->hflag) cudaFreeHost(h->hflag);

@@ -104,6 +104,9 @@ struct SweepArgs {
   int ml, f0, f1, b1, b0;
   const T* st_in;
   T* st_out;
+  // warp-tiled plans: [CS][warps][nos][8] observation ranges of each warp
+  // (injection: k0, k1, offset for two segments; gather: k0, k1)
+  const int* wtab;
   // group launch (uneven batching): when items != nullptr, column c of the
   // launch is items[c] and every problem field above comes from probs[prob]
   const SweepProb<T>* probs;
@@ -114,7 +117,8 @@ struct SweepArgs {
 struct SweepPlan {
   int CS, C, A, E, Ttile, HL, K;
   size_t smem;
-  int ml;  // 1: multi-launch tiles of K steps (no cluster), CS = tiles per column
+  int ml;    // 1: multi-launch tiles of K steps (no cluster), CS = tiles per column
+  int warp;  // 1: warp-tiled Hessian-product kernel (MODE_HVP only; needs a warp table)
 };
 
 // Picks the tiling of a sweep for state size n (elem_bytes = sizeof(T)):
@@ -131,6 +135,16 @@ size_t sweep_smem_bytes(int A, int C, int w, int elem_bytes);
 // A threads per CTA (A = 0: 512 for FP64, 256 for FP32; else a multiple of
 // 32 up to 512).
 bool plan_sweep_ml(int n, int elem_bytes, int w, int K, int A, SweepPlan* out);
+
+// A warp-tiled Hessian-product plan with cluster size CS, refresh period K
+// and C values per lane (FP64 2 or 4, FP32 4 or 8): warps of 32*C points
+// owning all but a halo of 12 (C = 2, 4) or 16 (C = 8) at each end, at most
+// 16 warps per CTA, and a CTA region no longer than n.  False if it does
+// not fit.
+bool plan_sweep_warp(int n, int elem_bytes, int w, int CS, int K, int C, SweepPlan* out);
+
+// The observation table of a warp-tiled plan (see SweepArgs::wtab).
+void warp_obs_table(const SweepPlan& p, int n, int nos, const int* obs_ptr, const int* obs_idx, int* tab);
 
 // The plan with exactly cluster size CS, refresh period K and C values per
 // thread (C = 0: 4 for FP64, 8 for FP32; else FP64 2 or 4, FP32 4 or 8), if

@@ -88,6 +88,11 @@ struct eda_handle {
   int nystrom_path = 0;  // 0 Cholesky, 1 Appendix B shift, 2 truncated eigendecomposition
   int lmp_rank = 0;      // informative LMP modes (k, or k_eff on path 2)
   SweepPlan plan64{}, plan32{};
+  // warp-tiled plans of the Hessian-product sweeps (warp = 0: none; the
+  // plans above serve then) and their observation tables
+  SweepPlan wplan64{}, wplan32{};
+  int* wtab64 = nullptr;
+  int* wtab32 = nullptr;
   int* tab64 = nullptr;  // per-CTA observation ranges of plan64 / plan32
   int* tab32 = nullptr;
   bool tab64_ok = false, tab32_ok = false;
@@ -114,6 +119,11 @@ int fail(eda_handle* h, int code, const std::string& msg);
 bool is_device_ptr(const void* ptr);
 // Installs a sweep tiling of the handle and its observation table.
 int set_plan(eda_handle* h, bool fp64, const SweepPlan& pl);
+// Installs (pl != nullptr) or removes the warp-tiled Hessian-product plan.
+int set_warp_plan(eda_handle* h, bool fp64, const SweepPlan* pl);
+// The plan of the Hessian-product sweeps of one precision and its tables:
+// the warp-tiled plan if installed, else the general plan.
+const SweepPlan& hvp_plan(const eda_handle* h, bool fp64, const int** obs_tab, const int** wtab);
 // State buffers for a multi-launch sweep of ncol columns (no-op for
 // cluster plans); grows the handle's buffers when needed.
 int ensure_ml(eda_handle* h, int ncol, bool fp64);

@@ -48,7 +48,10 @@ EDA_API int eda_hvp_noalloc(eda_handle* h, const int* member_of_col, int ncol, c
   if (!eda::is_device_ptr(member_of_col) || !eda::is_device_ptr(V) || !eda::is_device_ptr(HV))
     return eda::fail(h, EDA_ERR_INVALID, "eda_hvp_noalloc: member_of_col, V and HV must be device memory");
   const bool fp64 = (h->precision == EDA_FP64);
-  if ((fp64 ? h->plan64 : h->plan32).ml)
+  const int* obs_tab = nullptr;
+  const int* wtab = nullptr;
+  const SweepPlan& plan = eda::hvp_plan(h, fp64, &obs_tab, &wtab);
+  if (plan.ml)
     return eda::fail(h, EDA_ERR_INVALID,
                      "eda_hvp_noalloc: this state size needs multi-launch sweeps with state buffers; use eda_hvp");
   const long long need = (long long)ncol * (long long)h->p;  // stash entries
@@ -85,7 +88,8 @@ EDA_API int eda_hvp_noalloc(eda_handle* h, const int* member_of_col, int ncol, c
     a.w = h->w;
     a.bcoef = h->bcoef;
     a.nos = h->nos;
-    a.obs_tab = h->tab64_ok ? h->tab64 : nullptr;
+    a.obs_tab = obs_tab;
+    a.wtab = wtab;
     a.mode = eda::MODE_HVP;
     a.ncol = ncol;
     a.col_member = member_of_col;
@@ -96,7 +100,7 @@ EDA_API int eda_hvp_noalloc(eda_handle* h, const int* member_of_col, int ncol, c
     a.stash = static_cast<double*>(scratch);
     a.stash_stride = h->p;
     a.include_identity = include_identity ? 1 : 0;
-    CU(h, eda::launch_sweep<double>(a, h->plan64, h->st));
+    CU(h, eda::launch_sweep<double>(a, plan, h->st));
   } else {
     SweepArgs<float> a{};
     a.n = h->n;
@@ -113,7 +117,8 @@ EDA_API int eda_hvp_noalloc(eda_handle* h, const int* member_of_col, int ncol, c
     a.w = h->w;
     a.bcoef = h->bcoef32;
     a.nos = h->nos;
-    a.obs_tab = h->tab32_ok ? h->tab32 : nullptr;
+    a.obs_tab = obs_tab;
+    a.wtab = wtab;
     a.mode = eda::MODE_HVP;
     a.ncol = ncol;
     a.col_member = member_of_col;
@@ -124,7 +129,7 @@ EDA_API int eda_hvp_noalloc(eda_handle* h, const int* member_of_col, int ncol, c
     a.stash = static_cast<float*>(scratch);
     a.stash_stride = h->p;
     a.include_identity = include_identity ? 1 : 0;
-    CU(h, eda::launch_sweep<float>(a, h->plan32, h->st));
+    CU(h, eda::launch_sweep<float>(a, plan, h->st));
   }
   return EDA_OK;
 }

@@ -883,6 +883,487 @@ __global__ void bhalf_out_kernel(int n, int w, const T* __restrict__ coef, int n
   }
 }
 
+// ---------------------------------------------------------------------------
+// Warp-tiled Hessian-vector sweep (MODE_HVP).  As above, one column per
+// cluster of CS CTAs, each CTA computing an extended region of E points with
+// a halo of 8K + 8 refreshed from the owners every K steps.  Inside the CTA
+// the region is split among warps: warp w owns E positions
+// [w*LW, (w+1)*LW) and computes on the 32*C points starting HW before them
+// (HW = warp_halo(C), LW = 32*C - 2*HW), lane l holding C consecutive
+// values.  Stencil neighbours come from warp shuffles; one RK4 step spreads
+// an edge error at most 11 points, so after every step each warp publishes
+// its owned values to a shared mirror (double-buffered by step parity) and
+// its edge lanes reload theirs after one block barrier.  Observation gather and
+// injection touch only the warp's own positions, through a per-(rank, warp,
+// observation step) table of index ranges.
+// ---------------------------------------------------------------------------
+// Positions a one-step error can travel from a tile edge: 8 (left) and 4
+// (right) in a tangent-linear RK4 step, 11 both ways in an adjoint step with
+// its stage recomputation.  A warp halo is the smallest whole number of runs
+// covering 11 points.
+__host__ __device__ constexpr int warp_halo(int C) { return ((11 + C - 1) / C) * C; }
+constexpr int kWarpMaxThreads = 512;
+
+template <typename T, int C>
+__device__ __forceinline__ void shfl_m2m1p1(Run<T, C>& r) {
+  r.m2 = __shfl_up_sync(0xffffffffu, r.v[C - 2], 1);
+  r.m1 = __shfl_up_sync(0xffffffffu, r.v[C - 1], 1);
+  r.p1 = __shfl_down_sync(0xffffffffu, r.v[0], 1);
+}
+template <typename T, int C>
+__device__ __forceinline__ void shfl_all(Run<T, C>& r) {
+  shfl_m2m1p1<T, C>(r);
+  r.p2 = __shfl_down_sync(0xffffffffu, r.v[1], 1);
+}
+template <typename T, int C>
+__device__ __forceinline__ void shfl_m1p1p2(Run<T, C>& r) {
+  r.m1 = __shfl_up_sync(0xffffffffu, r.v[C - 1], 1);
+  r.p1 = __shfl_down_sync(0xffffffffu, r.v[0], 1);
+  r.p2 = __shfl_down_sync(0xffffffffu, r.v[1], 1);
+}
+
+template <typename T, int C>
+__device__ __forceinline__ void run_to_smem(T* dst, const T (&v)[C]) {
+  if constexpr (sizeof(T) == 4) {
+    float4* q = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int i = 0; i < C / 4; ++i) q[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  } else {
+    double2* q = reinterpret_cast<double2*>(dst);
+#pragma unroll
+    for (int i = 0; i < C / 2; ++i) q[i] = make_double2(v[2 * i], v[2 * i + 1]);
+  }
+}
+template <typename T, int C>
+__device__ __forceinline__ void run_from_smem_vec(const T* src, T (&v)[C]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4* q = reinterpret_cast<const float4*>(src);
+#pragma unroll
+    for (int i = 0; i < C / 4; ++i) {
+      const float4 u = q[i];
+      v[4 * i] = u.x;
+      v[4 * i + 1] = u.y;
+      v[4 * i + 2] = u.z;
+      v[4 * i + 3] = u.w;
+    }
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(src);
+#pragma unroll
+    for (int i = 0; i < C / 2; ++i) {
+      const double2 u = q[i];
+      v[2 * i] = u.x;
+      v[2 * i + 1] = u.y;
+    }
+  }
+}
+
+template <typename T, int C>
+__global__ void __launch_bounds__(kWarpMaxThreads) wsweep_kernel(const SweepArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  constexpr int HW = warp_halo(C);
+  constexpr int HLN = HW / C;          // edge lanes on each side of a warp tile
+  constexpr int LW = 32 * C - 2 * HW;  // positions a warp owns
+  static_assert(HW % C == 0, "the warp halo must be whole runs");
+  const int nw = (int)(blockDim.x >> 5);
+  const int wid = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+
+  Geo g;
+  g.CS = a.CS;
+  g.rank = (a.CS > 1) ? (int)cg::this_cluster().block_rank() : 0;
+  const int col = blockIdx.x / a.CS;
+  if (col >= a.ncol) return;
+  if (a.col_active != nullptr && a.col_active[col] == 0) return;  // uniform over the cluster
+  const int member = a.col_member ? a.col_member[col] : col;
+  const long long voff = (long long)col * a.out_stride;
+  const long long soff = (long long)col * a.stash_stride;
+  g.n = a.n;
+  g.E = a.E;
+  g.A = g.AS = g.NT = (int)blockDim.x;
+  g.tid = (int)threadIdx.x;
+  g.tl = g.tr = g.l0 = 0;
+  g.HL = a.HL;
+  g.Ttile = a.Ttile;
+  g.a0 = g.rank * a.Ttile;
+  g.Town = min(a.Ttile, a.n - g.a0);
+  g.gbase = ((g.a0 - a.HL) % a.n + a.n) % a.n;
+  const int E = a.E, w = a.w, N = a.N;
+
+  // shared memory: mirrors [2][E] | stage [E + 2(HW + w)] | taps [w + 1] | obs-step map
+  T* mir0 = sm;
+  T* mir1 = sm + E;
+  T* stage = sm + 2 * E;
+  const int stage_sz = E + 2 * (HW + w);
+  T* cf = stage + stage_sz;
+  int* omap = reinterpret_cast<int*>(cf + (w + 1));
+  const bool omap_smem = (N + 1) <= kObsMapCap;
+  for (int j = g.tid; j <= w; j += g.NT) cf[j] = a.bcoef[j];
+  if (omap_smem)
+    for (int j = g.tid; j <= N; j += g.NT) omap[j] = a.obs_of_t[j];
+  auto obs_at = [&](int t) { return omap_smem ? omap[t] : a.obs_of_t[t]; };
+
+  const int p0 = wid * LW - HW + lane * C;  // E position of this lane's first value
+  int gi[C];
+  {
+    int g0 = (g.gbase + p0) % g.n;
+    if (g0 < 0) g0 += g.n;
+#pragma unroll
+    for (int c = 0; c < C; ++c) gi[c] = (g0 + c) % g.n;
+  }
+  constexpr int kVec = 16 / (int)sizeof(T);
+  const bool vec_ok = (g.n % kVec == 0) && (gi[0] % kVec == 0) && (gi[0] + C <= g.n);
+  const bool own = lane >= HLN && lane < 32 - HLN;
+  const bool in_E = p0 >= 0 && p0 + C <= E;
+  const T F = a.F, h = a.dt;
+  const T h2 = h * T(0.5), h6 = h / T(6), h3 = h / T(3);
+  const bool clus = a.CS > 1;
+  const T* trj = a.traj + (long long)member * a.traj_mstride;
+  const T* V = a.V ? a.V + voff : nullptr;
+  const double* V64 = a.V64 ? a.V64 + voff : nullptr;
+  T* stash = a.stash + soff;
+  // this warp's observation ranges at step oj: injection (owned positions,
+  // two segments) and gather (owned positions inside the CTA tile)
+  auto wtab = [&](int oj) { return a.wtab + (((long long)g.rank * nw + wid) * a.nos + oj) * 8; };
+
+  // Refresh after every lane wrote its owned values to mirror m (and a
+  // barrier): edge lanes reload from the neighbouring warps; every K steps
+  // all positions outside the CTA tile reload from their owners' mirrors.
+  auto read_halos = [&](T (&v)[C], T* m, bool cstep) {
+    if (cstep) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int p = p0 + c;
+        if (p < g.HL || p >= g.HL + g.Town) {
+          const int r2 = gi[c] / g.Ttile;
+          const int ll = g.HL + gi[c] - r2 * g.Ttile;
+          if (!clus || r2 == g.rank) {
+            v[c] = m[ll];
+          } else {
+            const T* rem = cg::this_cluster().map_shared_rank(m, r2);
+            v[c] = rem[ll];
+          }
+        } else if (!own) {
+          v[c] = m[p];
+        }
+      }
+    } else if (!own && in_E) {
+      run_from_smem_vec<T, C>(m + p0, v);
+    }
+  };
+
+  // ------------------------------------------- delta_0 = U_B v (v staged with a halo)
+  for (int j = g.tid; j < stage_sz; j += g.NT) {
+    int gk = (g.gbase - HW - w + j) % g.n;
+    if (gk < 0) gk += g.n;
+    stage[j] = V64 ? (T)V64[gk] : V[gk];
+  }
+  __syncthreads();
+  T dl[C], xr[C];
+  conv_run<T, C>(stage, p0 + HW, w, cf, dl);
+  load_run<T, C>(trj, gi, vec_ok, xr);
+
+  auto gather = [&](int oj, const T* m) {
+    const int* tb = wtab(oj);
+    const int off = g.HL - g.a0;
+    for (int k = tb[6] + lane; k < tb[7]; k += 32) stash[k] = a.rinv[k] * m[a.obs_idx[k] + off];
+  };
+  {
+    const int oj = obs_at(0);
+    if (oj >= 0) {
+      if (own) run_to_smem<T, C>(mir0 + p0, dl);
+      __syncwarp();
+      gather(oj, mir0);
+    }
+  }
+
+  // ------------------------------------------------ tangent linear, forward
+  // observations per lane loaded a step ahead: with 8 values per lane the
+  // registers allow it and it hides the loads; shorter runs keep occupancy
+  constexpr int kObsPre = (C >= 8) ? 4 : 0;
+  for (int t = 0; t < N; ++t) {
+    T pf[C];
+    if (t + 1 < N) load_run<T, C>(trj + (long long)(t + 1) * g.n, gi, vec_ok, pf);
+    // this warp's gather at t + 1: indices and weights in flight during the step
+    const int ojn = obs_at(t + 1);
+    int gk0 = 0, gk1 = 0;
+    int gidx[kObsPre > 0 ? kObsPre : 1];
+    T grin[kObsPre > 0 ? kObsPre : 1];
+    if (kObsPre > 0 && ojn >= 0) {
+      const int* tb = wtab(ojn);
+      gk0 = tb[6];
+      gk1 = tb[7];
+#pragma unroll
+      for (int u = 0; u < kObsPre; ++u) {
+        const int k = gk0 + lane + 32 * u;
+        gidx[u] = k < gk1 ? __ldg(a.obs_idx + k) : 0;
+        grin[u] = k < gk1 ? __ldg(a.rinv + k) : T(0);
+      }
+    }
+    Run<T, C> X, e;
+    T Xs[C], es[C], acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      X.v[c] = xr[c];
+      e.v[c] = dl[c];
+    }
+    shfl_m2m1p1<T, C>(X);
+    shfl_m2m1p1<T, C>(e);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const T k = tend(X, c, F);
+      const T dk = jvp(X, e, c);
+      Xs[c] = xr[c] + h2 * k;
+      acc[c] = dk;
+      es[c] = dl[c] + h2 * dk;
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      X.v[c] = Xs[c];
+      e.v[c] = es[c];
+    }
+    shfl_m2m1p1<T, C>(X);
+    shfl_m2m1p1<T, C>(e);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const T k = tend(X, c, F);
+      const T dk = jvp(X, e, c);
+      Xs[c] = xr[c] + h2 * k;
+      acc[c] += T(2) * dk;
+      es[c] = dl[c] + h2 * dk;
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      X.v[c] = Xs[c];
+      e.v[c] = es[c];
+    }
+    shfl_m2m1p1<T, C>(X);
+    shfl_m2m1p1<T, C>(e);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const T k = tend(X, c, F);
+      const T dk = jvp(X, e, c);
+      Xs[c] = xr[c] + h * k;
+      acc[c] += T(2) * dk;
+      es[c] = dl[c] + h * dk;
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      X.v[c] = Xs[c];
+      e.v[c] = es[c];
+    }
+    shfl_m2m1p1<T, C>(X);
+    shfl_m2m1p1<T, C>(e);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      acc[c] += jvp(X, e, c);
+      dl[c] += h6 * acc[c];
+    }
+    if (t + 1 < N) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) xr[c] = pf[c];
+    }
+    // publish, gather, refresh
+    const int t1 = t + 1;
+    T* m = (t1 & 1) ? mir1 : mir0;
+    if (own) run_to_smem<T, C>(m + p0, dl);
+    if (ojn >= 0) {
+      __syncwarp();
+      if constexpr (kObsPre > 0) {
+        const int off = g.HL - g.a0;
+#pragma unroll
+        for (int u = 0; u < kObsPre; ++u) {
+          const int k = gk0 + lane + 32 * u;
+          if (k < gk1) stash[k] = grin[u] * m[gidx[u] + off];
+        }
+        for (int k = gk0 + lane + 32 * kObsPre; k < gk1; k += 32) stash[k] = a.rinv[k] * m[a.obs_idx[k] + off];
+      } else {
+        gather(ojn, m);
+      }
+    }
+    const bool cstep = (t1 % a.K == 0) && (t1 < N);
+    sync_cluster_or_block(cstep && clus);
+    if (t1 < N) read_halos(dl, m, cstep);
+    if (cstep && clus) cg::this_cluster().sync();  // remote reads of m end before it is rewritten
+  }
+  // every stash entry of the cluster is written before any CTA injects
+  sync_cluster_or_block(clus);
+
+  // ------------------------------------------------------ adjoint, backward
+  T lam[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) lam[c] = T(0);
+  // this warp's injection at step t: the two index segments as one list,
+  // the first kObsPre per lane loaded ahead (pre_*) by the caller
+  int ia0 = 0, na = 0, offa = 0, ib0 = 0, nb = 0, offb = 0;
+  int pidx[kObsPre > 0 ? kObsPre : 1];
+  T pval[kObsPre > 0 ? kObsPre : 1];
+  auto inject_prefetch = [&](int t) {
+    if constexpr (kObsPre == 0) return;
+    const int oj = obs_at(t);
+    na = nb = 0;
+    if (oj < 0) return;
+    const int* tb = wtab(oj);
+    ia0 = tb[0];
+    na = tb[1] - tb[0];
+    offa = tb[2];
+    ib0 = tb[3];
+    nb = tb[4] - tb[3];
+    offb = tb[5];
+#pragma unroll
+    for (int u = 0; u < kObsPre; ++u) {
+      const int f = lane + 32 * u;
+      const int k = f < na ? ia0 + f : ib0 + (f - na);
+      const bool ok = f < na + nb;
+      pidx[u] = ok ? __ldg(a.obs_idx + k) + (f < na ? offa : offb) : 0;
+      pval[u] = ok ? stash[k] : T(0);
+    }
+  };
+  auto inject_refresh = [&](int t) {
+    T* m = (t & 1) ? mir1 : mir0;
+    if (own) run_to_smem<T, C>(m + p0, lam);
+    if constexpr (kObsPre > 0) {
+      if (na + nb > 0) {
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < kObsPre; ++u)
+          if (lane + 32 * u < na + nb) m[pidx[u]] += pval[u];
+        for (int f = lane + 32 * kObsPre; f < na + nb; f += 32) {
+          const int k = f < na ? ia0 + f : ib0 + (f - na);
+          m[a.obs_idx[k] + (f < na ? offa : offb)] += stash[k];
+        }
+        __syncwarp();
+        if (own) run_from_smem_vec<T, C>(m + p0, lam);
+      }
+    } else {
+      const int oj = obs_at(t);
+      if (oj >= 0) {
+        __syncwarp();
+        const int* tb = wtab(oj);
+#pragma unroll
+        for (int sgm = 0; sgm < 2; ++sgm) {
+          const int k1 = tb[3 * sgm + 1], off = tb[3 * sgm + 2];
+          for (int k = tb[3 * sgm] + lane; k < k1; k += 32) m[a.obs_idx[k] + off] += stash[k];
+        }
+        __syncwarp();
+        if (own) run_from_smem_vec<T, C>(m + p0, lam);
+      }
+    }
+    const bool cstep = ((N - t) % a.K == 0) && (t > 0);
+    sync_cluster_or_block(cstep && clus);
+    if (t > 0) read_halos(lam, m, cstep);
+    if (cstep && clus) cg::this_cluster().sync();
+  };
+  inject_prefetch(N);
+  inject_refresh(N);
+  load_run<T, C>(trj + (long long)(N - 1) * g.n, gi, vec_ok, xr);
+  for (int t = N - 1; t >= 0; --t) {
+    T pf[C];
+    if (t > 0) load_run<T, C>(trj + (long long)(t - 1) * g.n, gi, vec_ok, pf);
+    inject_prefetch(t);
+    Run<T, C> X1, X2, X3, X4, wv;
+    T ln[C], ad[C];
+    // stage states of the step from x_t
+#pragma unroll
+    for (int c = 0; c < C; ++c) X1.v[c] = xr[c];
+    shfl_all<T, C>(X1);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      X2.v[c] = xr[c] + h2 * tend(X1, c, F);
+      ad[c] = h6 * lam[c];
+    }
+    shfl_all<T, C>(X2);
+#pragma unroll
+    for (int c = 0; c < C; ++c) X3.v[c] = xr[c] + h2 * tend(X2, c, F);
+    shfl_all<T, C>(X3);
+#pragma unroll
+    for (int c = 0; c < C; ++c) X4.v[c] = xr[c] + h * tend(X3, c, F);
+    shfl_all<T, C>(X4);
+    // reverse stage 4: g4 = J4^T a4, a4 = h/6 lam
+#pragma unroll
+    for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
+    shfl_m1p1p2<T, C>(wv);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const T gg = jtvp(X4, wv, c);
+      ln[c] = lam[c] + gg;
+      ad[c] = h3 * lam[c] + h * gg;  // a3
+    }
+    // reverse stage 3
+#pragma unroll
+    for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
+    shfl_m1p1p2<T, C>(wv);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const T gg = jtvp(X3, wv, c);
+      ln[c] += gg;
+      ad[c] = h3 * lam[c] + h2 * gg;  // a2
+    }
+    // reverse stage 2
+#pragma unroll
+    for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
+    shfl_m1p1p2<T, C>(wv);
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const T gg = jtvp(X2, wv, c);
+      ln[c] += gg;
+      ad[c] = h6 * lam[c] + h2 * gg;  // a1
+    }
+    // reverse stage 1
+#pragma unroll
+    for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
+    shfl_m1p1p2<T, C>(wv);
+#pragma unroll
+    for (int c = 0; c < C; ++c) lam[c] = ln[c] + jtvp(X1, wv, c);
+    if (t > 0) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) xr[c] = pf[c];
+    }
+    inject_refresh(t);
+  }
+
+  // ---------------------------------------------- output U_B lambda_0 (+ v)
+  // lambda_0 of every CTA's tile is in its mir0 (t = 0 has parity 0)
+  sync_cluster_or_block(clus);
+  const bool ident = a.include_identity != 0;
+  double* dot = (ident && a.dot_out != nullptr) ? a.dot_out + (long long)col * a.dot_stride : nullptr;
+  if (a.OUT64) {
+    bhalf_from_mirrors<T, C, double>(a, g, mir0, stage, cf, a.OUT64 + voff, ident ? V64 : nullptr,
+                                     ident ? V : nullptr, dot);
+  } else {
+    bhalf_from_mirrors<T, C, T>(a, g, mir0, stage, cf, a.OUT + voff, ident ? V64 : nullptr, ident ? V : nullptr,
+                                dot);
+  }
+}
+
+template <typename T, int C>
+cudaError_t launch_warp(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t s) {
+  auto kern = wsweep_kernel<T, C>;
+  static bool attrs_set = false;
+  if (!attrs_set) {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (err != cudaSuccess) return err;
+    attrs_set = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.ncol * p.CS), 1, 1);
+  cfg.blockDim = dim3((unsigned)p.A, 1, 1);
+  cfg.dynamicSmemBytes = p.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (p.CS > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)p.CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, kern, a);
+}
+
 template <typename T, int C>
 cudaError_t launch_impl(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t s) {
   auto kern = sweep_kernel<T, C>;
@@ -929,6 +1410,7 @@ bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* ou
   // instantiated runs: FP64 2 or 4 values per thread, FP32 4 or 8
   if (elem_bytes == 8 ? (C != 2 && C != 4) : (C != 4 && C != 8)) return false;
   out->ml = 0;
+  out->warp = 0;
   if (CS < 1 || CS > 16 || K < 1) return false;
   const int Ttile = (n + CS - 1) / CS;
   if ((CS - 1) * Ttile >= n) return false;
@@ -951,6 +1433,89 @@ bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* ou
   return true;
 }
 
+bool plan_sweep_warp(int n, int elem_bytes, int w, int CS, int K, int C, SweepPlan* out) {
+  if (elem_bytes == 8 ? (C != 2 && C != 4) : (C != 4 && C != 8)) return false;
+  if (CS < 1 || CS > 16 || K < 1) return false;
+  const int LW = 32 * C - 2 * warp_halo(C);
+  const int Ttile = (n + CS - 1) / CS;
+  if ((CS - 1) * Ttile >= n) return false;
+  const int HL = 8 * K + 8;
+  const int need = Ttile + 2 * HL;
+  const int nw = (need + LW - 1) / LW;
+  if (nw * 32 > kWarpMaxThreads) return false;
+  const int E = nw * LW;
+  if (E > n) return false;  // each warp's range maps to distinct points
+  const size_t smem = (size_t)(3 * E + 2 * (warp_halo(C) + w) + w + 1) * (size_t)elem_bytes +
+                      (size_t)kObsMapCap * sizeof(int) + 16;
+  if (smem > 227 * 1024) return false;
+  out->CS = CS;
+  out->C = C;
+  out->A = nw * 32;
+  out->E = E;
+  out->Ttile = Ttile;
+  out->HL = HL;
+  out->K = K;
+  out->smem = smem;
+  out->ml = 0;
+  out->warp = 1;
+  return true;
+}
+
+void warp_obs_table(const SweepPlan& p, int n, int nos, const int* obs_ptr, const int* obs_idx, int* tab) {
+  const int LW = 32 * p.C - 2 * warp_halo(p.C);
+  const int nw = p.A / 32;
+  auto lower = [&](int j, int g) {
+    int lo = obs_ptr[j], hi = obs_ptr[j + 1];
+    while (lo < hi) {
+      const int mid = (lo + hi) / 2;
+      if (obs_idx[mid] < g)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    return lo;
+  };
+  for (int r = 0; r < p.CS; ++r) {
+    const int a0 = r * p.Ttile;
+    const int town = (p.Ttile < n - a0) ? p.Ttile : n - a0;
+    const int gbase = ((a0 - p.HL) % n + n) % n;
+    for (int wi = 0; wi < nw; ++wi) {
+      const int e0 = wi * LW, e1 = e0 + LW;
+      const int g0 = gbase + e0, g1 = gbase + e1;  // g1 - g0 = LW <= n
+      // gather: owned positions inside the CTA tile [HL, HL + town)
+      const int ie0 = e0 > p.HL ? e0 : p.HL;
+      const int ie1 = e1 < p.HL + town ? e1 : p.HL + town;
+      for (int j = 0; j < nos; ++j) {
+        int* t = tab + (((long long)r * nw + wi) * nos + j) * 8;
+        t[3] = t[4] = 0;
+        t[5] = 0;
+        if (g1 <= n) {
+          t[0] = lower(j, g0);
+          t[1] = lower(j, g1);
+          t[2] = -gbase;
+        } else if (g0 >= n) {
+          t[0] = lower(j, g0 - n);
+          t[1] = lower(j, g1 - n);
+          t[2] = n - gbase;
+        } else {
+          t[0] = lower(j, g0);
+          t[1] = obs_ptr[j + 1];
+          t[2] = -gbase;
+          t[3] = obs_ptr[j];
+          t[4] = lower(j, g1 - n);
+          t[5] = n - gbase;
+        }
+        if (ie0 < ie1) {
+          t[6] = lower(j, a0 + ie0 - p.HL);
+          t[7] = lower(j, a0 + ie1 - p.HL);
+        } else {
+          t[6] = t[7] = 0;
+        }
+      }
+    }
+  }
+}
+
 bool plan_sweep_ml(int n, int elem_bytes, int w, int K, int A, SweepPlan* out) {
   const int C = (elem_bytes == 8) ? 4 : 8;
   if (A <= 0) A = (elem_bytes == 8) ? 512 : 256;
@@ -970,6 +1535,7 @@ bool plan_sweep_ml(int n, int elem_bytes, int w, int K, int A, SweepPlan* out) {
   out->K = K;
   out->smem = smem;
   out->ml = 1;
+  out->warp = 0;
   return true;
 }
 
@@ -1046,6 +1612,18 @@ cudaError_t launch_sweep(const SweepArgs<T>& a0, const SweepPlan& p, cudaStream_
   a.E = p.E;
   a.K = p.K;
   if (a.ncol <= 0) return cudaSuccess;
+  if (p.warp) {
+    if (a.mode != MODE_HVP || a.items != nullptr || a.wtab == nullptr) return cudaErrorInvalidValue;
+    a.ml = 0;
+    if constexpr (sizeof(T) == 8) {
+      if (p.C == 4) return launch_warp<T, 4>(a, p, s);
+      if (p.C == 2) return launch_warp<T, 2>(a, p, s);
+    } else {
+      if (p.C == 8) return launch_warp<T, 8>(a, p, s);
+      if (p.C == 4) return launch_warp<T, 4>(a, p, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   if (!p.ml) {
     a.ml = 0;
     return launch_one<T>(a, p, s);

@@ -201,6 +201,95 @@ def test_multi_launch_sweeps_match_oracle(n, threads, K):
             assert (np.linalg.norm(dz - exact, axis=1) <= rr * bn * (1 + 1e-6) + 1e-12).all()
 
 
+def _subset_spec(n, seed):
+    # a random subset of the variables observed (the same at every step), with
+    # observations at t = 0 and N as well
+    rng = np.random.default_rng(seed)
+    idx1 = np.sort(rng.choice(n, size=int(0.3 * n), replace=False)).astype(np.int32)
+    steps = np.array([0, 2, 4, 7, 9, 12, 13], dtype=np.int32)
+    return S.Spec(n=n, nsteps=13, obs_steps=steps,
+                  obs_ptr=(np.arange(len(steps) + 1) * len(idx1)).astype(np.int32),
+                  obs_idx=np.tile(idx1, len(steps)), sigma_o=0.7, sigma_b=1.0,
+                  length_scale=5.0, n_members=5, ell=4, k=4, spinup=5, seed=seed,
+                  name="l96_n%d_w13_m5_subset" % n)
+
+
+# (n, cluster size, refresh period, values per lane FP64, FP32, observation network)
+WARP_CASES = [(1000, 2, 8, 4, 8, "regular"), (1000, 3, 4, 2, 4, "regular"),
+              (997, 3, 8, 4, 4, "subset"), (2048, 5, 4, 2, 8, "subset")]
+
+
+@pytest.mark.parametrize("n,cs,K,c64,c32,net", WARP_CASES)
+def test_warp_tiled_sweeps_match_oracle(n, cs, K, c64, c32, net):
+    # the warp-tiled Hessian-product kernel (shuffle stencils, warp halos
+    # refreshed every step, cluster halos every K steps): products with and
+    # without the identity, the sketch and LMP, and a preconditioned solve
+    # whose p.q comes from the sweep epilogue
+    spec = _ml_spec(n, seed=n) if net == "regular" else _subset_spec(n, seed=n)
+    taps = O.bhalf_taps(spec.n, spec.length_scale, spec.sigma_b)
+    _, xb, y = O.twin(spec, S.draws(spec), taps)
+    traj, d, b = oracle_setup(spec, taps, xb, y)
+    cols = np.array([0, 3, 1, 4, 2, 0, 3], dtype=np.int32)
+    V = np.random.default_rng(n + cs).standard_normal((len(cols), spec.n))
+    ref = O.hvp(spec, traj[cols], V, taps)
+    refA = O.hvp(spec, traj[cols], V, taps, identity=False)
+    with env(EDA_SWEEP_WARP=1, EDA_SWEEP_CS64=cs, EDA_SWEEP_CS32=cs, EDA_SWEEP_K=K,
+             EDA_SWEEP_C64=c64, EDA_SWEEP_C32=c32):
+        with make(spec, taps) as h:
+            h.eda_set_trajectory(xb, y)
+            HV = np.zeros_like(V)
+            h.eda_hvp(cols, V, HV, True)
+            assert rowrel(HV, ref).max() < 1e-11
+            h.eda_hvp(cols, V, HV, False)
+            assert rowrel(HV, refA).max() < 1e-10
+            h.eda_sketch()
+            ev = np.zeros(spec.k)
+            h.eda_build_lmp(ev)
+            ro = O.eda_pipeline(spec, xb, y, taps, tol=1e-6, maxit=200)
+            np.testing.assert_allclose(ev, 1 + ro["D"], rtol=1e-9)
+            dz = np.zeros_like(b)
+            rr = np.zeros(spec.n_members)
+            st = np.zeros(spec.n_members, np.int32)
+            h.eda_solve_batch(1e-10, 500, None, True, dz, None, rr, st)
+            assert (st == P.EDA_CONVERGED).all()
+            exact = O.eda_pipeline(spec, xb, y, taps, tol=1e-13, maxit=500)["x"]
+            bn = np.linalg.norm(b, axis=1)
+            assert (np.linalg.norm(dz - exact, axis=1) <= 1.5e-10 * bn).all()
+        with make(spec, taps, precision=P.EDA_MIXED) as h:
+            h.eda_set_trajectory(xb, y)
+            HV = np.zeros_like(V)
+            h.eda_hvp(cols, V, HV, True)
+            assert rowrel(HV, ref).max() < 1e-4
+            h.eda_sketch()
+            h.eda_build_lmp()
+            dz = np.zeros_like(b)
+            rr = np.zeros(spec.n_members)
+            st = np.zeros(spec.n_members, np.int32)
+            h.eda_solve_batch(1e-8, 500, None, True, dz, None, rr, st)
+            assert (st == P.EDA_CONVERGED).all() and (rr <= 1e-8).all()
+
+
+def test_warp_tiled_full_size_batched_hvp():
+    # the n=4096, 64-step, 51-member workload on the warp-tiled kernel
+    spec = replace(S.spec_batched(seed=0), spinup=200)
+    taps, xb, y = problem(spec)
+    traj, d, b = oracle_setup(spec, taps, xb, y)
+    cols = np.arange(spec.n_members, dtype=np.int32)
+    V = np.random.default_rng(12).standard_normal((spec.n_members, spec.n))
+    ref = O.hvp(spec, traj, V, taps)
+    with env(EDA_SWEEP_WARP=1, EDA_SWEEP_CS64=5, EDA_SWEEP_CS32=5):
+        with make(spec, taps) as h:
+            h.eda_set_trajectory(xb, y)
+            HV = np.zeros_like(V)
+            h.eda_hvp(cols, V, HV, True)
+            assert rowrel(HV, ref).max() < 1e-10
+        with make(spec, taps, precision=P.EDA_MIXED) as h:
+            h.eda_set_trajectory(xb, y)
+            HV = np.zeros_like(V)
+            h.eda_hvp(cols, V, HV, True)
+            assert rowrel(HV, ref).max() < 1e-4
+
+
 def test_autotuned_tiling_keeps_parity():
     # the autotuner times cluster and multi-launch tilings and keeps the
     # fastest; whichever it keeps must give the same products
