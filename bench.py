@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the scale, uneven-batch and warm-start measurements")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
 
@@ -227,6 +229,187 @@ def run_reference(args):
     return 0
 
 
+# algorithmic FP32 operations per element-step of one member-column HVP: the
+# tangent-linear RK4 step (57) and the adjoint step with its stage
+# recomputation (60), counting each multiply and add (Lorenz-96 stencils of
+# the oracle's tl_step / adj_step)
+FLOPS_PER_ELEMENT_STEP = 117
+
+
+def fp32_peak_tflops(sm_mhz):
+    """FP32 FMA peak of a GB300: 152 SMs x 128 lanes x 2 flops per cycle."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def forms_scale(P, dev, hbm_peak):
+    """Scale workload (n=65536, 96-step window, 81 members): the batched
+    member HVP in FP32 and FP64 on the tuned tiling, with its HBM and FP32
+    ALU roofline fractions and the FP32 sweep's error against FP64."""
+    import torch
+    spec = S.spec_scale(seed=0)
+    spec.ckpt_every = 0
+    taps = P.bhalf_gaussian(spec.n, spec.length_scale, spec.sigma_b)
+    dr = S.draws(spec)
+    M, n, p, N = spec.n_members, spec.n, spec.p, spec.nsteps
+    hg = P.Handle.from_spec(spec, taps, precision=P.EDA_FP64)
+    xb = torch.empty(M, n, dtype=torch.float64, device=dev)
+    y = torch.empty(M, p, dtype=torch.float64, device=dev)
+    hg.eda_twin(torch.tensor(spec.F + spec.spin_sigma * dr.eta_spin, device=dev), spec.spinup,
+                torch.tensor(dr.eta_b, device=dev), torch.tensor(dr.eta_o, device=dev), xb, y)
+    hg.close()
+    cols = torch.arange(M, dtype=torch.int32, device=dev)
+    V = torch.tensor(S.gaussian_matrix(M, n, 31), device=dev)
+    out = {}
+    HV = {}
+    for prec, key in ((P.EDA_MIXED, "fp32"), (P.EDA_FP64, "fp64")):
+        with P.Handle.from_spec(spec, taps, precision=prec) as h:
+            h.eda_set_trajectory(xb, y)
+            h.eda_autotune(0)
+            ms = h.eda_time_hvp_sweep(reps=5 if key == "fp32" else 2, fp64=(key == "fp64"))
+            out["ms_per_batched_hvp_" + key] = ms
+            hv = torch.empty_like(V)
+            h.eda_hvp(cols, V, hv, True)
+            HV[key] = hv
+    torch.cuda.synchronize()
+    rel = (torch.linalg.norm(HV["fp32"] - HV["fp64"], dim=1) / torch.linalg.norm(HV["fp64"], dim=1)).max().item()
+    ms32 = out["ms_per_batched_hvp_fp32"]
+    bytes_launch = M * 4 * n * (2 * N + 2)
+    flops_launch = FLOPS_PER_ELEMENT_STEP * M * n * N
+    gbs = bytes_launch / (ms32 / 1e3) / 1e9
+    tfl = flops_launch / (ms32 / 1e3) / 1e12
+    peak_alu = fp32_peak_tflops(2070.0)
+    out.update({
+        "workload": spec.name, "columns": M, "trajectory_bytes_fp32": M * (N + 1) * n * 4,
+        "hv_per_s_fp32": M / (ms32 / 1e3),
+        "roofline_hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                         "bytes_per_launch": bytes_launch},
+        "roofline_alu": {"achieved": tfl, "peak": peak_alu, "unit": "TFLOP/s", "frac": tfl / peak_alu,
+                         "flops_per_launch": flops_launch,
+                         "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+        "fp32_vs_fp64_hvp_relerr_max": rel,
+    })
+    return out
+
+
+def forms_uneven(P, dev, count=256, maxit=3000):
+    """Uneven batch: 256 independent problems in one group (mixed precision,
+    graph-captured PCG, autotuned tiling), each member with a budget of
+    maxit iterations."""
+    import torch
+    specs = S.specs_uneven(count, seed=0)
+    hs, xbs, ys = [], [], []
+    for s_ in specs:
+        taps = P.bhalf_gaussian(s_.n, s_.length_scale, s_.sigma_b)
+        h = P.Handle.from_spec(s_, taps, precision=P.EDA_MIXED)
+        dr = S.draws(s_)
+        xb = torch.empty(s_.n_members, s_.n, dtype=torch.float64, device=dev)
+        y = torch.empty(s_.n_members, s_.p, dtype=torch.float64, device=dev)
+        h.eda_twin(torch.tensor(s_.F + s_.spin_sigma * dr.eta_spin, device=dev), s_.spinup,
+                   torch.tensor(dr.eta_b, device=dev), torch.tensor(dr.eta_o, device=dev), xb, y)
+        hs.append(h)
+        xbs.append(xb)
+        ys.append(y)
+    with P.Group(hs) as g:
+        g.eda_group_set_trajectories(xbs, ys)
+        g.eda_group_sketch()
+        g.eda_group_build_lmp()
+        g.eda_group_autotune()
+        T = g.total_members
+        it = np.zeros(T, np.int32)
+        rr = np.zeros(T)
+        st = np.zeros(T, np.int32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.eda_group_solve(TOL, maxit, True, None, it, rr, st)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+    for h in hs:
+        h.close()
+    conv = int((st == 0).sum())
+    return {"workload": "uneven_256_seed0", "problems": count, "member_solves": T, "converged": conv,
+            "budget_per_member": maxit, "seconds": t, "converged_solves_per_s": conv / t,
+            "iters_median": float(np.median(it)), "iters_p90": float(np.percentile(it, 90)),
+            "true_relres_max_converged": float(rr[st == 0].max()) if conv else None}
+
+
+def forms_warm(P, dev, train_edas=80, test_edas=2, epochs=3, hidden=64):
+    """Learned warm start (n=1024, 32-step window, 256 members): training
+    triples (member RHS, control solution, member solution) from the plain
+    solver, the network trained on the GPU by the library's kernels, then
+    held-out problems solved from zero and from the network's guess to the
+    same tolerance."""
+    import torch
+    n = 1024
+
+    def setup(seed):
+        spec = S.spec_warm(seed=seed)
+        M = spec.n_members
+        taps = P.bhalf_gaussian(n, spec.length_scale, spec.sigma_b)
+        h = P.Handle.from_spec(spec, taps, precision=P.EDA_MIXED)
+        dr = S.draws(spec)
+        xb = torch.empty(M, n, dtype=torch.float64, device=dev)
+        y = torch.empty(M, spec.p, dtype=torch.float64, device=dev)
+        h.eda_twin(torch.tensor(spec.F + spec.spin_sigma * dr.eta_spin, device=dev), spec.spinup,
+                   torch.tensor(dr.eta_b, device=dev), torch.tensor(dr.eta_o, device=dev), xb, y)
+        b = torch.empty(M, n, dtype=torch.float64, device=dev)
+        h.eda_set_trajectory(xb, y, b)
+        h.eda_sketch()
+        h.eda_build_lmp()
+        return h, b
+
+    def solve(h, M, x0=None):
+        dz = torch.empty(M, n, dtype=torch.float64, device=dev)
+        it = torch.empty(M, dtype=torch.int32, device=dev)
+        st = torch.empty(M, dtype=torch.int32, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.eda_solve_batch(TOL, 20000, x0, True, dz, it, None, st)
+        torch.cuda.synchronize()
+        return dz, it.cpu().numpy(), st.cpu().numpy(), time.perf_counter() - t0
+
+    R, Cc, Z = [], [], []
+    t0 = time.perf_counter()
+    for e in range(train_edas):
+        h, b = setup(10 ** 6 + e)
+        dz, _, _, _ = solve(h, b.shape[0])
+        R.append(b[1:])
+        Cc.append(dz[0:1].expand(dz.shape[0] - 1, -1))
+        Z.append(dz[1:])
+        h.close()
+    R, Cc, Z = (torch.cat(v).contiguous() for v in (R, Cc, Z))
+    t_data = time.perf_counter() - t0
+    ws = P.WarmStart(n, hidden, max_batch=64)
+    ws.eda_ws_init(S.gaussian_matrix(1, ws.num_params, 42)[0])
+    order = np.concatenate([np.random.default_rng(e).permutation(R.shape[0]) for e in range(epochs)]).astype(np.int32)
+    t0 = time.perf_counter()
+    losses = ws.eda_ws_train(R, Cc, Z, epochs=epochs, batch=64, lr=1e-3, weight_decay=0.0, order=order)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    zero_it, warm_it, zero_t, warm_t, ok = 0, 0, 0.0, 0.0, True
+    for e in range(test_edas):
+        h, b = setup(2 * 10 ** 6 + e)
+        M = b.shape[0]
+        dz, it0, st0, tz = solve(h, M)
+        guess = torch.empty(M - 1, n, dtype=torch.float64, device=dev)
+        ws.eda_ws_infer(b[1:].contiguous(), dz[0:1].expand(M - 1, -1).contiguous(), guess)
+        x0 = torch.cat([dz[0:1], guess]).contiguous()
+        _, itw, stw, tw = solve(h, M, x0=x0)
+        h.close()
+        zero_it += int(it0[1:].sum())
+        warm_it += int(itw[1:].sum())
+        zero_t += tz
+        warm_t += tw
+        ok = ok and bool((st0 == 0).all() and (stw == 0).all())
+    ws.close()
+    members = test_edas * 256
+    return {"workload": "l96_n1024_w32_m257", "training_triples": int(R.shape[0]), "data_s": t_data,
+            "train_s": t_train, "epochs": epochs, "loss_first_last": [float(losses[0]), float(losses[-1])],
+            "held_out_members": members, "iters_zero_start": zero_it, "iters_warm_start": warm_it,
+            "iterations_saved_frac": 1.0 - warm_it / max(1, zero_it),
+            "solves_per_s_zero": members / zero_t, "solves_per_s_warm": members / warm_t,
+            "all_converged": ok}
+
+
 def run_ours(args):
     import torch
     rank, world, local = dist_env()
@@ -362,6 +545,9 @@ def run_ours(args):
 
     hm.close()
     h64.close()
+    forms = None
+    if rank == 0 and not args.no_forms:
+        forms = {"scale": forms_scale(P, dev, peak), "uneven": forms_uneven(P, dev), "warm_start": forms_warm(P, dev)}
     if rank == 0:
         its_m = np.concatenate(its_mixed)
         its_d = np.concatenate(its64)
@@ -395,7 +581,13 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk.summary(),
+            "roofline_alu": {"achieved": FLOPS_PER_ELEMENT_STEP * spec.nsteps * n * sw_cols / (sw_ms / 1e3) / 1e12,
+                             "peak": fp32_peak_tflops(2070.0), "unit": "TFLOP/s",
+                             "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"},
+            "forms": forms,
         }
+        ra = line["roofline_alu"]
+        ra["frac"] = ra["achieved"] / ra["peak"]
         print(json.dumps(line))
     if world > 1:
         torch.distributed.barrier()

@@ -377,6 +377,11 @@ EDA_API int eda_ws_destroy(eda_ws* w);
 EDA_API const char* eda_ws_last_error(const eda_ws* w);
 /* Number of FP32 parameters (0 for NULL). */
 EDA_API long long eda_ws_num_params(const eda_ws* w);
+/* He initialisation from standard-normal draws [num_params] FP64 (host or
+ * device; one per parameter in the flat layout): weights of a layer with ci
+ * input channels = draw * sqrt(2 / (5 ci)), biases 0; resets the AdamW
+ * moments. */
+EDA_API int eda_ws_init(eda_ws* w, const double* draws);
 /* Loads / stores the flat FP32 parameters (host or device); loading resets
  * the AdamW moments.  Together with the scales this is the saved model. */
 EDA_API int eda_ws_set_params(eda_ws* w, const float* params);

@@ -36,7 +36,7 @@ EXPORTS = ["eda_version", "eda_last_error", "eda_create", "eda_destroy", "eda_tw
            "eda_ws_create", "eda_ws_destroy", "eda_ws_last_error", "eda_ws_num_params", "eda_ws_set_params",
            "eda_ws_get_params", "eda_ws_set_scales", "eda_ws_get_scales", "eda_ws_loss_grad", "eda_ws_train",
            "eda_ws_infer", "eda_hvp_noalloc", "eda_hvp_noalloc_capacity", "eda_lmp_info",
-           "eda_trace", "eda_trace_read"]
+           "eda_trace", "eda_trace_read", "eda_ws_init"]
 
 
 class EdaError(RuntimeError):
@@ -133,6 +133,8 @@ def lib() -> ctypes.CDLL:
     L.eda_ws_last_error.argtypes = [vp]
     L.eda_ws_num_params.restype = ctypes.c_longlong
     L.eda_ws_num_params.argtypes = [vp]
+    L.eda_ws_init.restype = i
+    L.eda_ws_init.argtypes = [vp, vp]
     L.eda_ws_set_params.restype = i
     L.eda_ws_set_params.argtypes = [vp, vp]
     L.eda_ws_get_params.restype = i
@@ -467,6 +469,10 @@ class WarmStart:
 
     def __exit__(self, *a):
         self.close()
+
+    def eda_ws_init(self, draws):
+        """He initialisation from num_params standard-normal draws (FP64)."""
+        self._check(self._L.eda_ws_init(self._w, _ptr(draws, np.float64, self.num_params, "draws")))
 
     def eda_ws_set_params(self, params):
         self._check(self._L.eda_ws_set_params(self._w, _ptr(params, np.float32, self.num_params, "params")))

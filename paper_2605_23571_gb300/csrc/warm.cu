@@ -252,6 +252,12 @@ __global__ void sumsq_kernel(long long count, const double* v, double* acc) {
 
 }  // namespace
 
+// theta = eta * scale (He-scaled weights from standard-normal draws).
+__global__ void he_init_kernel(long long count, const double* eta, float* theta, float scale) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count; i += (long long)gridDim.x * blockDim.x)
+    theta[i] = (float)eta[i] * scale;
+}
+
 struct eda_ws {
   int n = 0, H = 0, Bmax = 0;
   cudaStream_t st = nullptr;
@@ -418,6 +424,33 @@ EDA_API int eda_ws_destroy(eda_ws* w) {
 EDA_API const char* eda_ws_last_error(const eda_ws* w) { return w ? w->err.c_str() : eda_last_error(nullptr); }
 
 EDA_API long long eda_ws_num_params(const eda_ws* w) { return w ? w->nparam : 0; }
+
+EDA_API int eda_ws_init(eda_ws* w, const double* draws) {
+  if (!w || !draws) return wfail(w, EDA_ERR_INVALID, "eda_ws_init: invalid argument");
+  const double* eta = draws;
+  double* tmp = nullptr;
+  if (!eda::is_device_ptr(draws)) {
+    WCU(w, cudaMalloc((void**)&tmp, w->nparam * sizeof(double)));
+    WCU(w, cudaMemcpyAsync(tmp, draws, w->nparam * sizeof(double), cudaMemcpyHostToDevice, w->st));
+    eta = tmp;
+  }
+  for (int l = 0; l < 4; ++l) {
+    const long long nwt = (long long)w->cout_[l] * w->cin[l] * KS;
+    eda::count_launch();
+    he_init_kernel<<<eda::grid_for(nwt), 256, 0, w->st>>>(nwt, eta + w->woff[l], w->theta + w->woff[l],
+                                                          (float)std::sqrt(2.0 / (w->cin[l] * KS)));
+    WCU(w, cudaGetLastError());
+    WCU(w, cudaMemsetAsync(w->theta + w->boff[l], 0, w->cout_[l] * sizeof(float), w->st));
+  }
+  WCU(w, cudaMemsetAsync(w->m, 0, w->nparam * sizeof(float), w->st));
+  WCU(w, cudaMemsetAsync(w->v, 0, w->nparam * sizeof(float), w->st));
+  w->step = 0;
+  const int rc = refresh_bf16(w);
+  if (rc) return rc;
+  WCU(w, cudaStreamSynchronize(w->st));
+  if (tmp) cudaFree(tmp);
+  return EDA_OK;
+}
 
 EDA_API int eda_ws_set_params(eda_ws* w, const float* params) {
   if (!w || !params) return wfail(w, EDA_ERR_INVALID, "eda_ws_set_params: invalid argument");

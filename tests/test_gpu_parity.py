@@ -523,6 +523,35 @@ def test_full_size_batched_hvp_and_rhs_fp64():
         assert e32 < 1e-4
 
 
+@pytest.mark.slow
+def test_full_size_scale_hvp_sampled_columns():
+    # the n=65536, 96-step, 81-member workload (multi-launch tiling): products
+    # of a sample of members on their own trajectories against the oracle,
+    # column by column, and the right-hand sides of the same members
+    spec = replace(S.spec_scale(seed=0), ckpt_every=0, spinup=100)
+    taps, xb, y = problem(spec)
+    sample = np.array([0, 37, 80], dtype=np.int32)
+    traj = O.member_trajectories(spec, xb[sample])
+    d = O.innovations(spec, traj, y[sample])
+    b = O.rhs(spec, traj, d, taps)
+    V = np.random.default_rng(21).standard_normal((len(sample), spec.n))
+    ref = O.hvp(spec, traj, V, taps)
+    with make(spec, taps) as h:
+        rhs = np.zeros((spec.n_members, spec.n))
+        h.eda_set_trajectory(xb, y, rhs)
+        assert rowrel(rhs[sample], b).max() < 1e-10
+        HV = np.zeros_like(V)
+        h.eda_hvp(sample, V, HV, True)
+        assert rowrel(HV, ref).max() < 1e-10
+    with make(spec, taps, precision=P.EDA_MIXED) as h:
+        h.eda_set_trajectory(xb, y)
+        HV = np.zeros_like(V)
+        h.eda_hvp(sample, V, HV, True)
+        e32 = rowrel(HV, ref).max()
+        print("FP32 sweep HVP rel err at n=65536, N=96: %.3e" % e32)
+        assert e32 < 1e-3
+
+
 def test_rank_deficient_sketch_uses_the_truncated_eigendecomposition():
     # a length scale comparable to n leaves B, and so Gamma, numerically rank
     # deficient: Cholesky and the shift both break down and Algorithm 1 is

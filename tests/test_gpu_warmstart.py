@@ -85,3 +85,13 @@ def test_training_learns_a_periodic_convolution():
         ws.eda_ws_set_params(theta.astype(np.float32))
         losses = ws.eda_ws_train(rhs, ctrl, sol, epochs=300, batch=32, lr=3e-3)
     assert losses[-1] < 0.2 * losses[0], losses[[0, -1]]
+
+
+def test_he_initialisation_matches_oracle():
+    hidden, n = 16, 48
+    with P.WarmStart(n, hidden, max_batch=4) as ws:
+        eta = S.gaussian_matrix(1, ws.num_params, 7)[0]
+        ws.eda_ws_init(eta)
+        got = ws.eda_ws_get_params()
+    ref = W.init_params(hidden, eta)
+    np.testing.assert_allclose(got, ref.astype(np.float32), rtol=1e-6, atol=0)
