@@ -1282,7 +1282,8 @@ namespace {
 // through a ring of pinned copies and runs at most kRing-1 iterations ahead
 // of the device.
 template <typename TS>
-int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done, bool sweep64) {
+int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done, bool sweep64,
+               int replace_every) {
   const int M = h->M;
   const int fixed = (tol > 0.0) ? 0 : maxit;
   const int lmp = use_lmp ? 1 : 0;
@@ -1307,6 +1308,17 @@ int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int*
     if (rc) return rc;
     CU(h, eda::pcg2_update<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->pv, h->q, h->x, h->r, h->sc, h->acc,
                                h->active, Wk, par, 1, lmp, h->nactive, h->st));
+    if (replace_every > 0 && (it - it0) % replace_every == 0) {
+      // residual replacement: the recurrence residual gives way to the FP64
+      // true residual b - (I + A) x, and the projections follow it; CG goes
+      // on with the same direction
+      rc = hvp_dev(h, h->cols, M, h->x, h->q, 1, true, h->active);
+      if (rc) return rc;
+      CU(h, eda::pcg2_replace(h->tasks, h->ntasks, h->probs, M, h->b, h->q, h->r, h->acc, M, h->active, h->st));
+      CU(h, cudaMemsetAsync(Wk, 0, (size_t)M * kmax * sizeof(TS), h->st));
+      CU(h, eda::pcg2_update<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->pv, h->q, h->x, h->r, h->sc, h->acc,
+                                 h->active, Wk, par, 0, lmp, h->nactive, h->st));
+    }
     CU(h, eda::pcg2_precond<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->r, h->z, h->pv, h->sc, h->acc, h->active,
                                 Wk, par, tol, maxit, fixed, lmp, 0, h->nactive, h->st));
     CU(h, eda::pcg2_dir<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->z, h->pv, h->sc, h->acc, h->active, Wk, par,
@@ -1325,10 +1337,11 @@ int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int*
   return EDA_OK;
 }
 
-int pcg_loop(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done, bool sweep64) {
+int pcg_loop(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done, bool sweep64,
+             int replace_every = 0) {
   // the LMP arithmetic follows the sweeps: FP64, or FP32 with the FP32 copy of S
-  if (sweep64) return pcg_loop_t<double>(h, tol, maxit, it0, use_lmp, it_done, true);
-  return pcg_loop_t<float>(h, tol, maxit, it0, use_lmp, it_done, false);
+  if (sweep64) return pcg_loop_t<double>(h, tol, maxit, it0, use_lmp, it_done, true, 0);
+  return pcg_loop_t<float>(h, tol, maxit, it0, use_lmp, it_done, false, replace_every);
 }
 
 }  // namespace
@@ -1367,15 +1380,20 @@ EDA_API int eda_solve_batch(eda_handle* h, double tol, int maxit, const double* 
   } else {
     // FP32 sweeps and FP32 LMP arithmetic; CG vectors, scalars and x in FP64.
     // Iterative refinement: every inner PCG reduces its own residual by tau,
-    // then the FP64 true residual restarts the next round.
+    // then the FP64 true residual b - (I + A) x restarts the members that
+    // miss tol.  EDA_MIXED_REPLACE = r > 0 instead replaces the recurrence
+    // residual by the FP64 true one every r iterations without a restart;
+    // on the batched workload that needs as many iterations and costs the
+    // extra FP64 sweeps, so restarts are the default.
     const char* taus = std::getenv("EDA_MIXED_INNER_TOL");
     const double tau = (taus && *taus) ? std::atof(taus) : 1e-3;
-    if (tol > 0.0 && tau > 0.0) {
+    const int rep = env_int("EDA_MIXED_REPLACE", 0);
+    if (rep <= 0 && tol > 0.0 && tau > 0.0) {
       eda::count_launch();
       set_tolm_kernel<<<1, 128, 0, h->st>>>(M, h->sc, tol, tau);
       CU(h, cudaGetLastError());
     }
-    int rc = pcg_loop(h, tol, maxit, 0, lmp, &it, false);
+    int rc = pcg_loop(h, tol, maxit, 0, lmp, &it, false, rep);
     if (rc) return rc;
     // FP64 residual replacement: true residual b - H x with FP64 sweeps;
     // members whose true residual misses the tolerance restart from it.
@@ -1392,7 +1410,7 @@ EDA_API int eda_solve_batch(eda_handle* h, double tol, int maxit, const double* 
       rc = read_flag(h, h->dstatus, &need);
       if (rc) return rc;
       if (need == 0 || tol <= 0.0) break;
-      rc = pcg_loop(h, tol, maxit, it, lmp, &it, false);
+      rc = pcg_loop(h, tol, maxit, it, lmp, &it, false, rep);
       if (rc) return rc;
     }
   }

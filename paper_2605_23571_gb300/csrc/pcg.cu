@@ -214,6 +214,28 @@ __global__ void __launch_bounds__(kThreads) pcg2_dir_kernel(const PcgTask* tasks
   }
 }
 
+// r = b - hx and ||r||^2 for the active members (hx = (I + A) x).
+__global__ void __launch_bounds__(kThreads) pcg2_replace_kernel(const PcgTask* tasks, const PcgProb* probs,
+                                                                const double* b, const double* hx, double* r,
+                                                                PcgAcc* acc, const int* active) {
+  const PcgTask tk = tasks[blockIdx.x];
+  const PcgProb P = probs[tk.prob];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int m = blockIdx.y * kWarps + wid;
+  if (m >= P.M) return;
+  const int item = P.item0 + m;
+  if (!active[item]) return;
+  const long long off = P.off0 + (long long)m * P.n + tk.row0;
+  double rr = 0.0;
+  for (int i = lane; i < tk.rows; i += 32) {
+    const double rv = b[off + i] - hx[off + i];
+    r[off + i] = rv;
+    rr += rv * rv;
+  }
+  rr = warp_sum(rr);
+  if (lane == 0) atomicAdd(&acc[item].rr, rr);
+}
+
 __global__ void pcg2_reset_kernel(PcgAcc* acc, int T) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < T; j += gridDim.x * blockDim.x) {
     PcgAcc a;
@@ -300,6 +322,18 @@ cudaError_t pcg2_dir(const PcgTask* tasks, int ntasks, const PcgProb* probs, int
   if (ntasks <= 0 || mmax <= 0) return cudaSuccess;
   count_launch();
   pcg2_dir_kernel<TS><<<dim3(ntasks, (mmax + kWarps - 1) / kWarps), kThreads, 0, s>>>(tasks, probs, kmax, z, p, sc, acc, active, Wk, par);
+  return cudaGetLastError();
+}
+
+cudaError_t pcg2_replace(const PcgTask* tasks, int ntasks, const PcgProb* probs, int mmax, const double* b,
+                         const double* hx, double* r, PcgAcc* acc, int T, const int* active, cudaStream_t s) {
+  if (ntasks <= 0 || mmax <= 0) return cudaSuccess;
+  // ||r||^2 of the replaced residual accumulates from zero
+  cudaError_t e = cudaMemset2DAsync(&acc[0].rr, sizeof(PcgAcc), 0, sizeof(double), T, s);
+  if (e != cudaSuccess) return e;
+  count_launch();
+  pcg2_replace_kernel<<<dim3(ntasks, (mmax + kWarps - 1) / kWarps), kThreads, 0, s>>>(tasks, probs, b, hx, r, acc,
+                                                                                      active);
   return cudaGetLastError();
 }
 

@@ -82,6 +82,11 @@ template <typename TS>
 cudaError_t pcg2_dir(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* z, double* p,
                      PcgScalars* sc, PcgAcc* acc, const int* active, TS* Wk, int par, cudaStream_t s);
 
+// Residual replacement: r = b - hx (hx = (I + A) x from an accurate sweep)
+// and ||r||^2 (cleared first) for the active members of T.
+cudaError_t pcg2_replace(const PcgTask* tasks, int ntasks, const PcgProb* probs, int mmax, const double* b,
+                         const double* hx, double* r, PcgAcc* acc, int T, const int* active, cudaStream_t s);
+
 // acc[col].pq += v_col . hv_col for active columns of an [ncol][n] batch
 // (used where the sweep epilogue cannot accumulate it).
 cudaError_t pcg2_col_dot(int n, int ncol, const double* v, const double* hv, const int* active, PcgAcc* acc,
