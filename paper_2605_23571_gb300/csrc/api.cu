@@ -381,6 +381,8 @@ SweepArgs<T> base_args(eda_handle* h) {
     a.obs_tab = h->tab32_ok ? h->tab32 : nullptr;
   }
   a.traj_mstride = (long long)(h->N + 1) * h->n;
+  if constexpr (sizeof(T) == 8) a.stages = h->stg;
+  a.stage_astride = (long long)h->M * (h->N + 1) * h->n;
   return a;
 }
 
@@ -838,6 +840,11 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
   CUC(dalloc(h, &h->bcoef32, h->w + 1));
   CUC(dalloc(h, &h->traj, (size_t)M * (N + 1) * n));
   if (h->precision == EDA_MIXED) CUC(dalloc(h, &h->traj32, (size_t)M * (N + 1) * n));
+  // stage-state store for the FP64 sweeps, which are bound by the FP64 pipe
+  // and gain from not recomputing the stages (EDA_STAGE_STORE=0: recompute).
+  // FP32 sweeps always recompute: streaming three more arrays costs them more
+  // than the arithmetic saved.
+  if (env_int("EDA_STAGE_STORE", 1)) CUC(dalloc(h, &h->stg, (size_t)3 * M * (N + 1) * n));
   CUC(dalloc(h, &h->d, (size_t)M * p));
   CUC(dalloc(h, &h->rd, (size_t)M * p));
   CUC(dalloc(h, &h->b, (size_t)M * n));
@@ -1036,13 +1043,15 @@ EDA_API int eda_set_trajectory(eda_handle* h, const double* xb, const double* y,
     a.x0_stride = n;
     a.traj_out = h->traj;
     a.traj_out_mstride = (long long)(N + 1) * n;
+    a.stage_out = h->stg;
     a.yobs = (const double*)iy.dev;
     a.d_out = h->d;
     a.rd_out = h->rd;
     CU(h, (eda::ensure_ml(h, a.ncol, true) == EDA_OK) ? eda::launch_sweep<double>(a, h->plan64, h->st, h->ml64[0], h->ml64[1]) : cudaErrorMemoryAllocation);
   }
-  if (h->precision == EDA_MIXED)
+  if (h->precision == EDA_MIXED) {
     CU(h, eda::convert<double, float>((long long)M * (N + 1) * n, h->traj, h->traj32, h->st));
+  }
   // right-hand sides b_j = U_B^T G_j^T R^{-1} d_j (FP64 adjoint sweep)
   {
     SweepArgs<double> a = base_args<double>(h);

@@ -95,6 +95,14 @@ struct SweepArgs {
   const T* yobs;         // [col][p] or nullptr (then d = H x)
   T* d_out;              // [col][p] or nullptr
   T* rd_out;             // [col][p] or nullptr: R^{-1} d
+  // Nonlinear stage states X2, X3, X4 of every RK4 step t -> t+1 (rows
+  // t = 0..N-1) of each member: three arrays, array s at + s * stage_astride,
+  // member m at + m * traj_mstride (the trajectory's layout).  MODE_NL with
+  // stage_out writes them; MODE_HVP / MODE_RHS with stages read them instead
+  // of recomputing.
+  T* stage_out;
+  const T* stages;
+  long long stage_astride;
   // plan
   int CS, Ttile, HL, E, K;
   // multi-launch mode (n too large for one cluster): CS tiles per column

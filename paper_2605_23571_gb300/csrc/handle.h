@@ -33,6 +33,10 @@ struct eda_handle {
   // device: setup products
   double* traj = nullptr;
   float* traj32 = nullptr;
+  // stage states X2, X3, X4 of every RK4 step ([3][member][t][n], the
+  // trajectory's layout), written with the trajectory and read by the FP64
+  // sweeps; nullptr: recomputed
+  double* stg = nullptr;
   double* d = nullptr;
   double* rd = nullptr;
   double* b = nullptr;

@@ -345,7 +345,10 @@ __device__ __forceinline__ void load_run(const T* row, const int (&gi)[C], bool 
 
 constexpr int kObsMapCap = 1024;  // steps whose observation index is cached in smem
 
-template <typename T, int C>
+// STG: the kernel reads stored stage states when the arguments carry them
+// (instantiated for FP64 only: FP32 sweeps recompute, which costs them less
+// than streaming three more arrays).
+template <typename T, int C, bool STG>
 __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -471,6 +474,16 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       const bool x0_vec = vec_ok && ((reinterpret_cast<unsigned long long>(x0row) & 15ull) == 0);
       load_run<T, C>(x0row, gi, x0_vec, x);
     }
+    // owned positions of a run -> row of a stage array
+    T* sout = a.stage_out ? a.stage_out + (long long)member * a.traj_mstride : nullptr;
+    auto store_stage = [&](int s_, int row, const T (&v)[C]) {
+      T* dst = sout + (long long)s_ * a.stage_astride + (long long)row * a.n;
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const int l = g.l0 + c;
+        if (l >= g.HL && l < g.HL + g.Town) dst[gi[c]] = v[c];
+      }
+    };
     for (int t = f0; t <= f1; ++t) {
       if (t > f0) {
         Run<T, C> X;
@@ -486,6 +499,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
           acc[c] = k;
           Xs[c] = X1[c] + h2 * k;
         }
+        if (sout) store_stage(0, t - 1, Xs);
         publish(eb[1], g, Xs);
         __syncthreads();
 #pragma unroll
@@ -497,6 +511,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
           acc[c] += T(2) * k;
           Xs[c] = X1[c] + h2 * k;
         }
+        if (sout) store_stage(1, t - 1, Xs);
         publish(eb[2], g, Xs);
         __syncthreads();
 #pragma unroll
@@ -508,6 +523,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
           acc[c] += T(2) * k;
           Xs[c] = X1[c] + h * k;
         }
+        if (sout) store_stage(2, t - 1, Xs);
         publish(eb[1], g, Xs);
         __syncthreads();
 #pragma unroll
@@ -570,6 +586,24 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   const double* V64 = (a.mode == MODE_HVP && a.V64) ? a.V64 + voff : nullptr;
   T* stash = a.stash + soff;
   T xr[C];  // own run of x_t (registers)
+  // stored stage states of this member (or recomputation when absent)
+  const T* stg = nullptr;
+  if constexpr (STG) stg = a.stages ? a.stages + (long long)member * a.traj_mstride : nullptr;
+  int gh[4];  // global indices of the run's two left and two right neighbours
+  gh[0] = (gi[0] - 2 + g.n) % g.n;
+  gh[1] = (gi[0] - 1 + g.n) % g.n;
+  gh[2] = (gi[C - 1] + 1) % g.n;
+  gh[3] = (gi[C - 1] + 2) % g.n;
+  auto load_halo = [&](const T* row, Run<T, C>& X) {
+    X.m2 = row[gh[0]];
+    X.m1 = row[gh[1]];
+    X.p1 = row[gh[2]];
+    X.p2 = row[gh[3]];
+  };
+  auto load_sx = [&](const T* row, Run<T, C>& X) {
+    load_run<T, C>(row, gi, vec_ok, X.v);
+    load_halo(row, X);
+  };
 
   if (a.mode == MODE_HVP && f1 > f0) {
     T dl[C];
@@ -605,6 +639,58 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     for (int t = f0; t < f1; ++t) {
       T pf[C];
       if (t + 1 < f1) load_run<T, C>(trj + (long long)(t + 1) * a.n, gi, vec_ok, pf);
+      if (stg != nullptr) {
+        // stage states from the store: only delta's edges are exchanged
+        Run<T, C> X1, X2, X3, X4, e;
+        T es[C], acc[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) X1.v[c] = xr[c];
+        load_halo(trj + (long long)t * a.n, X1);
+        load_sx(stg + (long long)t * a.n, X2);
+        load_sx(stg + a.stage_astride + (long long)t * a.n, X3);
+        load_sx(stg + 2 * a.stage_astride + (long long)t * a.n, X4);
+#pragma unroll
+        for (int c = 0; c < C; ++c) e.v[c] = dl[c];
+        fetch(eb[0], g, e);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const T dk = jvp(X1, e, c);
+          acc[c] = dk;
+          es[c] = dl[c] + h2 * dk;
+        }
+        publish(eb[3], g, es);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < C; ++c) e.v[c] = es[c];
+        fetch(eb[3], g, e);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const T dk = jvp(X2, e, c);
+          acc[c] += T(2) * dk;
+          es[c] = dl[c] + h2 * dk;
+        }
+        publish(eb[4], g, es);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < C; ++c) e.v[c] = es[c];
+        fetch(eb[4], g, e);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const T dk = jvp(X3, e, c);
+          acc[c] += T(2) * dk;
+          es[c] = dl[c] + h * dk;
+        }
+        publish(eb[3], g, es);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < C; ++c) e.v[c] = es[c];
+        fetch(eb[3], g, e);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          acc[c] += jvp(X4, e, c);
+          dl[c] += h6 * acc[c];
+        }
+      } else {
       Run<T, C> X, e;
       T Xs[C], es[C], acc[C];
       // stage 1: slopes at X1 = x_t
@@ -678,6 +764,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
         acc[c] += dk;
         dl[c] += h6 * acc[c];
       }
+      }
       if (t + 1 < f1) {
 #pragma unroll
         for (int c = 0; c < C; ++c) xr[c] = pf[c];
@@ -742,6 +829,60 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   for (int t = b1 - 1; t >= b0; --t) {
     T pf[C];
     if (t > b0) load_run<T, C>(trj + (long long)(t - 1) * a.n, gi, vec_ok, pf);
+    if (stg != nullptr) {
+      // stage states from the store: only the adjoint weights' edges are
+      // exchanged, through edge buffers 3 and 4 in turn
+      Run<T, C> S1, S2, S3, S4, wv;
+      T ln[C], ad[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) S1.v[c] = xr[c];
+      load_halo(trj + (long long)t * a.n, S1);
+      load_sx(stg + (long long)t * a.n, S2);
+      load_sx(stg + a.stage_astride + (long long)t * a.n, S3);
+      load_sx(stg + 2 * a.stage_astride + (long long)t * a.n, S4);
+#pragma unroll
+      for (int c = 0; c < C; ++c) ad[c] = h6 * lam[c];  // a4
+      publish(eb[3], g, ad);
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
+      fetch(eb[3], g, wv);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const T gg = jtvp(S4, wv, c);
+        ln[c] = lam[c] + gg;
+        ad[c] = h3 * lam[c] + h * gg;  // a3
+      }
+      publish(eb[4], g, ad);
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
+      fetch(eb[4], g, wv);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const T gg = jtvp(S3, wv, c);
+        ln[c] += gg;
+        ad[c] = h3 * lam[c] + h2 * gg;  // a2
+      }
+      publish(eb[3], g, ad);
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
+      fetch(eb[3], g, wv);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        const T gg = jtvp(S2, wv, c);
+        ln[c] += gg;
+        ad[c] = h6 * lam[c] + h2 * gg;  // a1
+      }
+      publish(eb[4], g, ad);
+      __syncthreads();
+#pragma unroll
+      for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
+      fetch(eb[4], g, wv);
+#pragma unroll
+      for (int c = 0; c < C; ++c) lam[c] = ln[c] + jtvp(S1, wv, c);
+    } else {
     Run<T, C> X1, X, wv;
     T X2[C], X3[C], X4[C], ln[C], ad[C];
     // forward recomputation of the stage states
@@ -824,6 +965,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     fetch(eb[4], g, wv);
 #pragma unroll
     for (int c = 0; c < C; ++c) lam[c] = ln[c] + jtvp(X1, wv, c);
+    }
     if (t > b0) {
 #pragma unroll
       for (int c = 0; c < C; ++c) xr[c] = pf[c];
@@ -837,8 +979,10 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       read_halo(lam, mir, g);
       sync_cluster_or_block(clus);
     }
-    publish(eb[0], g, xr);
-    __syncthreads();
+    if (stg == nullptr) {  // the recomputation reads x_t's edges from buffer 0
+      publish(eb[0], g, xr);
+      __syncthreads();
+    }
   }
 
   if (a.ml) {  // multi-launch: the state goes to global memory; U_B follows in its own kernel
@@ -1364,9 +1508,9 @@ cudaError_t launch_warp(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t 
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-template <typename T, int C>
+template <typename T, int C, bool STG>
 cudaError_t launch_impl(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t s) {
-  auto kern = sweep_kernel<T, C>;
+  auto kern = sweep_kernel<T, C, STG>;
   // function attributes are set once (they are not stream work and must not
   // be issued while a stream is being captured)
   static bool attrs_set = false;
@@ -1594,11 +1738,12 @@ void obs_table(const SweepPlan& p, int n, int nos, const int* obs_ptr, const int
 template <typename T>
 cudaError_t launch_one(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t s) {
   if constexpr (sizeof(T) == 8) {
-    if (p.C == 4) return launch_impl<T, 4>(a, p, s);
-    if (p.C == 2) return launch_impl<T, 2>(a, p, s);
+    const bool stg = a.stages != nullptr && a.mode != MODE_NL;
+    if (p.C == 4) return stg ? launch_impl<T, 4, true>(a, p, s) : launch_impl<T, 4, false>(a, p, s);
+    if (p.C == 2) return stg ? launch_impl<T, 2, true>(a, p, s) : launch_impl<T, 2, false>(a, p, s);
   } else {
-    if (p.C == 8) return launch_impl<T, 8>(a, p, s);
-    if (p.C == 4) return launch_impl<T, 4>(a, p, s);
+    if (p.C == 8) return launch_impl<T, 8, false>(a, p, s);
+    if (p.C == 4) return launch_impl<T, 4, false>(a, p, s);
   }
   return cudaErrorInvalidValue;
 }

@@ -61,8 +61,11 @@ def test_twin_matches_oracle_without_spinup(spec):
     assert rel(y, y_o) < 1e-13
 
 
+@pytest.mark.parametrize("store", [1, 0], ids=["stored-stages", "recomputed-stages"])
 @pytest.mark.parametrize("spec", SMALL, ids=lambda s: s.name)
-def test_rhs_and_hvp_fp64(spec):
+def test_rhs_and_hvp_fp64(spec, store):
+    # the FP64 sweeps read the RK4 stage states stored with the trajectory,
+    # or recompute them (EDA_STAGE_STORE=0); FP32 sweeps always recompute
     taps, xb, y = problem(spec)
     traj, d, b = oracle_setup(spec, taps, xb, y)
     rng = np.random.default_rng(7)
@@ -71,15 +74,21 @@ def test_rhs_and_hvp_fp64(spec):
     V = rng.standard_normal((ncol, spec.n))
     ref = O.hvp(spec, traj[cols], V, taps)
     refA = O.hvp(spec, traj[cols], V, taps, identity=False)
-    with make(spec, taps) as h:
-        rhs = np.zeros_like(b)
-        h.eda_set_trajectory(xb, y, rhs)
-        assert rowrel(rhs, b).max() < 1e-11
-        HV = np.zeros_like(V)
-        h.eda_hvp(cols, V, HV, True)
-        assert rowrel(HV, ref).max() < 1e-11
-        h.eda_hvp(cols, V, HV, False)
-        assert rowrel(HV, refA).max() < 1e-10
+    with env(EDA_STAGE_STORE=store):
+        with make(spec, taps) as h:
+            rhs = np.zeros_like(b)
+            h.eda_set_trajectory(xb, y, rhs)
+            assert rowrel(rhs, b).max() < 1e-11
+            HV = np.zeros_like(V)
+            h.eda_hvp(cols, V, HV, True)
+            assert rowrel(HV, ref).max() < 1e-11
+            h.eda_hvp(cols, V, HV, False)
+            assert rowrel(HV, refA).max() < 1e-10
+        with make(spec, taps, precision=P.EDA_MIXED) as h:
+            h.eda_set_trajectory(xb, y)
+            HV = np.zeros_like(V)
+            h.eda_hvp(cols, V, HV, True)
+            assert rowrel(HV, ref).max() < 1e-4
 
 
 @pytest.mark.parametrize("cs", [2, 3, 5])
