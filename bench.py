@@ -479,7 +479,7 @@ def run_ours(args):
     if world > 1:
         torch.distributed.barrier()
     launches0 = P.kernel_launches()
-    hm.eda_trace(True)  # event-timed sweeps inside the timed steps (roofline)
+    hm.eda_trace(True, every=8)  # one sweep in 8 event-timed inside the timed steps (roofline)
     torch.cuda.profiler.start()  # ncu --profile-from-start off captures from here
     with Clocks(local) as clk:
         t_mixed, its_mixed = timed_steps(hm, args.steps, 0)

@@ -258,12 +258,13 @@ EDA_API long long eda_kernel_launches(void);
 
 /*
  * Tracing of the Hessian-product sweeps of one handle (eda_hvp, the sketch,
- * the PCG of eda_solve_batch, the FP64 true residuals): with enable != 0,
- * every later sweep is bracketed by a pair of CUDA events on the handle's
- * stream and the columns it computed (the active members, counted on the
- * device) are summed.  eda_trace(h, 1) starts a new record (zeroing the
- * totals); eda_trace(h, 0) stops recording and keeps them.  Each sweep adds
- * one one-thread kernel and two event records to the stream.
+ * the PCG of eda_solve_batch, the FP64 true residuals): with enable = e > 0,
+ * one later sweep in e (the first, then every e-th) is bracketed by a pair
+ * of CUDA events on the handle's stream and the columns it computed (the
+ * active members, counted on the device) are summed.  eda_trace(h, e) starts
+ * a new record (zeroing the totals); eda_trace(h, 0) stops recording and
+ * keeps them.  A traced sweep adds one one-thread kernel and two event
+ * records to the stream.  EDA_ERR_INVALID if enable < 0.
  */
 EDA_API int eda_trace(eda_handle* h, int enable);
 /*

@@ -303,9 +303,10 @@ class Handle:
         self._check(self._L.eda_set_lmp(self._h, _ptr(s_in, np.float64, self.k * self.n, "s_in"),
                                         _ptr(eigvals_in, np.float64, self.k, "eigvals_in")))
 
-    def eda_trace(self, enable=True):
-        """Starts (enable) or stops the sweep trace of this handle."""
-        self._check(self._L.eda_trace(self._h, 1 if enable else 0))
+    def eda_trace(self, enable=True, every=1):
+        """Starts (enable, tracing one sweep in `every`) or stops the sweep
+        trace of this handle."""
+        self._check(self._L.eda_trace(self._h, int(every) if enable else 0))
 
     def eda_trace_read(self, fp64=False):
         """(sweeps, columns, ms) recorded for the FP64 or the FP32 sweeps."""

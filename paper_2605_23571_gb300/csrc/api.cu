@@ -459,13 +459,14 @@ int hvp_dev(eda_handle* h, const int* dcols, int ncol, const double* V, double* 
   int rc = ensure_stash(h, ncol);
   if (rc) return rc;
   const bool sw64 = (h->precision == EDA_FP64 || force64);
-  if (h->trace_on) {
+  const bool traced = h->trace_on && (h->trace_seen++ % h->trace_every) == 0;
+  if (traced) {
     rc = trace_begin(h, sw64 ? 0 : 1, active, ncol);
     if (rc) return rc;
   }
   rc = hvp_launch(h, dcols, ncol, V, HV, ident, sw64, active, dot);
   if (rc) return rc;
-  return h->trace_on ? trace_end(h) : EDA_OK;
+  return traced ? trace_end(h) : EDA_OK;
 }
 
 int hvp_launch(eda_handle* h, const int* dcols, int ncol, const double* V, double* HV, int ident, bool sw64,
@@ -572,7 +573,10 @@ EDA_API long long eda_kernel_launches(void) { return eda::g_launches.load(std::m
 
 EDA_API int eda_trace(eda_handle* h, int enable) {
   if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (enable < 0) return fail(h, EDA_ERR_INVALID, "eda_trace: enable < 0");
   if (enable) {
+    h->trace_every = enable;
+    h->trace_seen = 0;
     int rc = trace_drain(h);
     if (rc) return rc;
     h->trace_ms[0] = h->trace_ms[1] = 0.0;

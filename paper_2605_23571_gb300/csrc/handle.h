@@ -106,6 +106,8 @@ struct eda_handle {
   // event pairs around each sweep on the handle's stream, drained into the
   // totals when the pool is full or on read; column counts on the device
   bool trace_on = false;
+  int trace_every = 1;     // trace one sweep in trace_every
+  long long trace_seen = 0;
   std::vector<cudaEvent_t> trace_ev;      // 2 per pair
   std::vector<int> trace_kind;            // precision index per pair
   int trace_used = 0;

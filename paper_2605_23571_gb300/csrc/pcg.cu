@@ -20,6 +20,32 @@ __device__ __forceinline__ double warp_sum(double v) {
 // 32 lanes reading one column of 32 consecutive rows hit 32 banks.
 __host__ __device__ __forceinline__ int odd_stride(int k) { return k | 1; }
 
+// Stages rows [row0, row0 + rows) of the k columns of S (column c at
+// S + c * n) into shared memory, sm[c * cs + i * rs] = S[c * n + row0 + i],
+// with 16 loads in flight per thread before their stores.
+template <typename TS>
+__device__ __forceinline__ void stage_S(const TS* S, int n, int k, int row0, int rows, TS* sm, int cs, int rs) {
+  constexpr int U = 16;
+  const int total = k * rows;
+  for (int base = 0; base < total; base += U * kThreads) {
+    TS v[U];
+    int dst[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int idx = base + (int)threadIdx.x + u * kThreads;
+      dst[u] = -1;
+      if (idx < total) {
+        const int c = idx / rows, i = idx - c * rows;
+        v[u] = S[(long long)c * n + row0 + i];
+        dst[u] = c * cs + i * rs;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (dst[u] >= 0) sm[dst[u]] = v[u];
+  }
+}
+
 template <typename TS>
 __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* tasks, const PcgProb* probs, int kmax,
                                                                const double* p, const double* q, double* x,
@@ -35,10 +61,7 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* ta
   TS* rsm = Ssm + (size_t)kmax * RBP;  // [kWarps][kPcgRows]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const TS* S = static_cast<const TS*>(P.S);
-  for (int idx = threadIdx.x; idx < k * tk.rows; idx += kThreads) {
-    const int c = idx / tk.rows, i = idx - c * tk.rows;
-    Ssm[c * RBP + i] = S[(long long)c * P.n + tk.row0 + i];
-  }
+  stage_S<TS>(S, P.n, k, tk.row0, tk.rows, Ssm, RBP, 1);
   // slot par^1 collects r.z in the precond launch that follows
   if (update && tk.first && blockIdx.y == 0)
     for (int m = threadIdx.x; m < P.M; m += kThreads) acc[P.item0 + m].rz[par ^ 1] = 0.0;
@@ -107,10 +130,7 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
   TS* wsm = Ssm + (size_t)kPcgRows * KP;   // [kWarps][kmax]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const TS* S = static_cast<const TS*>(P.S);
-  for (int idx = threadIdx.x; idx < k * tk.rows; idx += kThreads) {
-    const int c = idx / tk.rows, i = idx - c * tk.rows;
-    Ssm[i * KP + c] = S[(long long)c * P.n + tk.row0 + i];
-  }
+  stage_S<TS>(S, P.n, k, tk.row0, tk.rows, Ssm, 1, KP);
   // p^T q of the next sweep accumulates from zero
   if (tk.first && blockIdx.y == 0)
     for (int m = threadIdx.x; m < P.M; m += kThreads) acc[P.item0 + m].pq = 0.0;
