@@ -16,9 +16,35 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Row stride of the transposed S chunk in the precond kernel: odd, so that
-// 32 lanes reading one column of 32 consecutive rows hit 32 banks.
-__host__ __device__ __forceinline__ int odd_stride(int k) { return k | 1; }
+// 16-byte vectors of the LMP arithmetic type: VW values per load.
+template <typename TS>
+struct Vec16;
+template <>
+struct Vec16<float> {
+  using type = float4;
+  static constexpr int VW = 4;
+  __device__ static float dot(const float4& a, const float4& b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+};
+template <>
+struct Vec16<double> {
+  using type = double2;
+  static constexpr int VW = 2;
+  __device__ static double dot(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
+};
+
+// Stride (in values) of shared-memory rows read with 16-byte loads by
+// consecutive lanes: a multiple of the vector width whose eight consecutive
+// rows start in eight different 4-bank groups (4 mod 8 floats, 2 mod 4
+// doubles), at least len.
+template <typename TS>
+__host__ __device__ __forceinline__ int vec_stride(int len) {
+  constexpr int VW = 16 / (int)sizeof(TS);
+  int st = ((len + VW - 1) / VW) * VW;
+  while ((st / VW) % 2 == 0) st += VW;
+  return st;
+}
+
+static_assert(kPcgRows == 128, "stage_S indexes full chunks by shift and mask");
 
 // Stages rows [row0, row0 + rows) of the k columns of S (column c at
 // S + c * n) into shared memory, sm[c * cs + i * rs] = S[c * n + row0 + i],
@@ -27,6 +53,7 @@ template <typename TS>
 __device__ __forceinline__ void stage_S(const TS* S, int n, int k, int row0, int rows, TS* sm, int cs, int rs) {
   constexpr int U = 16;
   const int total = k * rows;
+  const bool full = rows == kPcgRows;  // a power of two: shift and mask
   for (int base = 0; base < total; base += U * kThreads) {
     TS v[U];
     int dst[U];
@@ -35,7 +62,8 @@ __device__ __forceinline__ void stage_S(const TS* S, int n, int k, int row0, int
       const int idx = base + (int)threadIdx.x + u * kThreads;
       dst[u] = -1;
       if (idx < total) {
-        const int c = idx / rows, i = idx - c * rows;
+        const int c = full ? (idx >> 7) : idx / rows;
+        const int i = idx - c * rows;
         v[u] = S[(long long)c * n + row0 + i];
         dst[u] = c * cs + i * rs;
       }
@@ -53,15 +81,22 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* ta
                                                                TS* Wk, int par, int update, int use_lmp,
                                                                int* nactive) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  constexpr int RBP = kPcgRows + 1;  // S chunk [c][RBP]: lane c reads column c
+  using V = typename Vec16<TS>::type;
+  constexpr int VW = Vec16<TS>::VW;
+  const int RBP = vec_stride<TS>(kPcgRows);  // S chunk [c][RBP]: lane c reads column c
   const PcgTask tk = tasks[blockIdx.x];
   const PcgProb P = probs[tk.prob];
   const int k = use_lmp ? P.k : 0;
+  const int rows_v = ((tk.rows + VW - 1) / VW) * VW;  // rows padded to whole vectors
   TS* Ssm = reinterpret_cast<TS*>(smraw);
   TS* rsm = Ssm + (size_t)kmax * RBP;  // [kWarps][kPcgRows]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const TS* S = static_cast<const TS*>(P.S);
   stage_S<TS>(S, P.n, k, tk.row0, tk.rows, Ssm, RBP, 1);
+  for (int idx = threadIdx.x; idx < k * (rows_v - tk.rows); idx += kThreads) {
+    const int c = idx / (rows_v - tk.rows);
+    Ssm[c * RBP + tk.rows + (idx - c * (rows_v - tk.rows))] = TS(0);
+  }
   // slot par^1 collects r.z in the precond launch that follows
   if (update && tk.first && blockIdx.y == 0)
     for (int m = threadIdx.x; m < P.M; m += kThreads) acc[P.item0 + m].rz[par ^ 1] = 0.0;
@@ -98,19 +133,19 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* ta
     } else {
       for (int i = lane; i < tk.rows; i += 32) rw[i] = (TS)r[off + i];
     }
+    if (lane < rows_v - tk.rows) rw[tk.rows + lane] = TS(0);
     __syncwarp();
     for (int c = lane; c < k; c += 32) {
-      const TS* Sc = Ssm + c * RBP;
-      TS s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      const V* Sc = reinterpret_cast<const V*>(Ssm + c * RBP);
+      const V* rv = reinterpret_cast<const V*>(rw);
+      TS s0 = 0, s1 = 0;
       int i = 0;
-      for (; i + 4 <= tk.rows; i += 4) {
-        s0 += Sc[i] * rw[i];
-        s1 += Sc[i + 1] * rw[i + 1];
-        s2 += Sc[i + 2] * rw[i + 2];
-        s3 += Sc[i + 3] * rw[i + 3];
+      for (; i + 2 <= rows_v / VW; i += 2) {
+        s0 += Vec16<TS>::dot(Sc[i], rv[i]);
+        s1 += Vec16<TS>::dot(Sc[i + 1], rv[i + 1]);
       }
-      for (; i < tk.rows; ++i) s0 += Sc[i] * rw[i];
-      atomicAdd(&Wk[(long long)item * kmax + c], (s0 + s1) + (s2 + s3));
+      if (i < rows_v / VW) s0 += Vec16<TS>::dot(Sc[i], rv[i]);
+      atomicAdd(&Wk[(long long)item * kmax + c], s0 + s1);
     }
   }
 }
@@ -122,21 +157,29 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
                                                                 const TS* Wk, int par, double tol, int maxit,
                                                                 int fixed, int use_lmp, int init, int* nactive) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  using V = typename Vec16<TS>::type;
+  constexpr int VW = Vec16<TS>::VW;
   const PcgTask tk = tasks[blockIdx.x];
   const PcgProb P = probs[tk.prob];
   const int k = use_lmp ? P.k : 0;
-  const int KP = odd_stride(k);
-  TS* Ssm = reinterpret_cast<TS*>(smraw);  // [row][KP]: lane = row reads a row
-  TS* wsm = Ssm + (size_t)kPcgRows * KP;   // [kWarps][kmax]
+  const int KP = vec_stride<TS>(k);               // row stride, zero beyond k
+  const int KW = vec_stride<TS>(kmax > 0 ? kmax : 1);
+  TS* Ssm = reinterpret_cast<TS*>(smraw);        // [row][KP]: lane = row reads a row
+  TS* wsm = Ssm + (size_t)kPcgRows * KW;         // [kWarps][KW]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const TS* S = static_cast<const TS*>(P.S);
   stage_S<TS>(S, P.n, k, tk.row0, tk.rows, Ssm, 1, KP);
+  if (k > 0)
+    for (int idx = threadIdx.x; idx < tk.rows * (KP - k); idx += kThreads) {
+      const int i = idx / (KP - k);
+      Ssm[i * KP + k + (idx - i * (KP - k))] = TS(0);
+    }
   // p^T q of the next sweep accumulates from zero
   if (tk.first && blockIdx.y == 0)
     for (int m = threadIdx.x; m < P.M; m += kThreads) acc[P.item0 + m].pq = 0.0;
   __syncthreads();
   const int slot = init ? 0 : (par ^ 1);
-  TS* wc = wsm + wid * kmax;
+  TS* wc = wsm + wid * KW;
   {
     const int m = blockIdx.y * kWarps + wid;  // one member per warp
     if (m >= P.M) return;
@@ -175,7 +218,7 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
       }
       if (stop) return;
     }
-    for (int c = lane; c < k; c += 32) wc[c] = (TS)(P.c[c] * (double)Wk[(long long)item * kmax + c]);
+    for (int c = lane; c < KP; c += 32) wc[c] = c < k ? (TS)(P.c[c] * (double)Wk[(long long)item * kmax + c]) : TS(0);
     __syncwarp();
     const long long off = P.off0 + (long long)m * P.n + tk.row0;
     double rz = 0.0;
@@ -183,14 +226,15 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
       const double rv = r[off + i];
       double zv = rv;
       if (k > 0) {
-        const TS* Srow = Ssm + i * KP;
+        const V* Srow = reinterpret_cast<const V*>(Ssm + i * KP);
+        const V* wv = reinterpret_cast<const V*>(wc);
         TS s0 = 0, s1 = 0;
         int c = 0;
-        for (; c + 2 <= k; c += 2) {
-          s0 += Srow[c] * wc[c];
-          s1 += Srow[c + 1] * wc[c + 1];
+        for (; c + 2 <= KP / VW; c += 2) {
+          s0 += Vec16<TS>::dot(Srow[c], wv[c]);
+          s1 += Vec16<TS>::dot(Srow[c + 1], wv[c + 1]);
         }
-        if (c < k) s0 += Srow[c] * wc[c];
+        if (c < KP / VW) s0 += Vec16<TS>::dot(Srow[c], wv[c]);
         zv += (double)(s0 + s1);
       }
       z[off + i] = zv;
@@ -313,7 +357,7 @@ cudaError_t pcg2_update(const PcgTask* tasks, int ntasks, const PcgProb* probs, 
                         const double* q, double* x, double* r, PcgScalars* sc, PcgAcc* acc, int* active, TS* Wk,
                         int par, int update, int use_lmp, int* nactive, cudaStream_t s) {
   if (ntasks <= 0 || mmax <= 0) return cudaSuccess;
-  const size_t smem = ((size_t)kmax * (kPcgRows + 1) + (size_t)kWarps * kPcgRows) * sizeof(TS);
+  const size_t smem = ((size_t)kmax * vec_stride<TS>(kPcgRows) + (size_t)kWarps * kPcgRows) * sizeof(TS);
   cudaError_t e = set_smem(pcg2_update_kernel<TS>, smem);
   if (e != cudaSuccess) return e;
   count_launch();
@@ -327,7 +371,8 @@ cudaError_t pcg2_precond(const PcgTask* tasks, int ntasks, const PcgProb* probs,
                          double* z, double* p, PcgScalars* sc, PcgAcc* acc, int* active, const TS* Wk, int par,
                          double tol, int maxit, int fixed, int use_lmp, int init, int* nactive, cudaStream_t s) {
   if (ntasks <= 0 || mmax <= 0) return cudaSuccess;
-  const size_t smem = ((size_t)kPcgRows * odd_stride(kmax) + (size_t)kWarps * (kmax > 0 ? kmax : 1)) * sizeof(TS);
+  const int KW = vec_stride<TS>(kmax > 0 ? kmax : 1);
+  const size_t smem = ((size_t)kPcgRows * KW + (size_t)kWarps * KW) * sizeof(TS);
   cudaError_t e = set_smem(pcg2_precond_kernel<TS>, smem);
   if (e != cudaSuccess) return e;
   count_launch();
