@@ -157,6 +157,15 @@ def workload(seed):
     return spec, dr
 
 
+def workload_config(spec, world):
+    """The config object of both arms' JSON lines."""
+    return {"workload": spec.name, "n": spec.n, "window": spec.nsteps, "members": spec.n_members,
+            "ell": spec.ell, "k": spec.k, "obs_per_step": int(spec.p // len(spec.obs_steps)),
+            "obs_steps": int(len(spec.obs_steps)), "tol": TOL, "precision": "mixed",
+            "l2": "flushed between timed steps (512 MB write)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def cpu_oracle_step(spec, xb, y, taps, iters_per_member, sample_iters=30):
     """The oracle on a bounded sample of one step: setup, RHS, Gamma sketch and
     LMP of every member, then ``sample_iters`` PCG iterations of one member;
@@ -219,8 +228,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": spec.name, "n": spec.n, "window": spec.nsteps,
-                                            "members": spec.n_members, "ell": spec.ell, "k": spec.k},
+            "data": "synthetic", "config": workload_config(spec, 1),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": r["sample"] + " (iteration count: the oracle's own, "
                                        "tests/golden/oracle_pcg_iters_n4096.json)"},
@@ -556,11 +564,7 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_mixed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": spec.name, "n": n, "window": spec.nsteps, "members": M,
-                       "ell": spec.ell, "k": spec.k, "obs_per_step": int(p // len(spec.obs_steps)),
-                       "obs_steps": int(len(spec.obs_steps)), "tol": TOL, "precision": "mixed",
-                       "l2": "flushed between timed steps (512 MB write)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": workload_config(spec, world),
             "fp64_path": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * t64 / max(1, args.fp64_steps),
                           "speedup_mixed_over_fp64": value / world / value64,
                           "iters_median": float(np.median(its_d))},
