@@ -1410,7 +1410,7 @@ EDA_API int eda_solve_batch(eda_handle* h, double tol, int maxit, const double* 
     if (rc) return rc;
     // FP64 residual replacement: true residual b - H x with FP64 sweeps;
     // members whose true residual misses the tolerance restart from it.
-    for (int rep = 0; rep < 64; ++rep) {
+    for (int round = 0; round < 64; ++round) {
       rc = hvp_dev(h, h->cols, M, h->x, h->q, 1, true, nullptr);
       if (rc) return rc;
       CU(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
