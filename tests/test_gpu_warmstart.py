@@ -95,3 +95,76 @@ def test_he_initialisation_matches_oracle():
         got = ws.eda_ws_get_params()
     ref = W.init_params(hidden, eta)
     np.testing.assert_allclose(got, ref.astype(np.float32), rtol=1e-6, atol=0)
+
+
+def test_warm_start_gain_on_held_out_problems():
+    # training triples (member RHS, control solution, member solution) from
+    # the plain FP64 solver on small problems, the network trained on the GPU,
+    # then a held-out problem solved from zero and from the network's guess
+    # to the same tolerance: the guess must beat the control solution as a
+    # guess, both solves converge and agree within the residual bound, and the
+    # iterations saved are reported
+    import torch
+    dev = torch.device("cuda:0")
+    n, N, members = 256, 16, 64
+
+    def problem_on_gpu(seed):
+        spec = S.spec_small(n, N, members + 1, every_var=2, every_step=2, length_scale=4.0, seed=seed)
+        taps = P.bhalf_gaussian(n, spec.length_scale, spec.sigma_b)
+        h = P.Handle.from_spec(spec, taps, precision=P.EDA_FP64)
+        dr = S.draws(spec)
+        M = spec.n_members
+        xb = torch.empty(M, n, dtype=torch.float64, device=dev)
+        y = torch.empty(M, spec.p, dtype=torch.float64, device=dev)
+        h.eda_twin(torch.tensor(spec.F + spec.spin_sigma * dr.eta_spin, device=dev), 300,
+                   torch.tensor(dr.eta_b, device=dev), torch.tensor(dr.eta_o, device=dev), xb, y)
+        b = torch.empty(M, n, dtype=torch.float64, device=dev)
+        h.eda_set_trajectory(xb, y, b)
+        h.eda_sketch()
+        h.eda_build_lmp()
+        return h, b
+
+    def solve(h, b, x0=None):
+        M = b.shape[0]
+        dz = torch.empty_like(b)
+        it = np.zeros(M, np.int32)
+        rr = np.zeros(M)
+        st = np.zeros(M, np.int32)
+        h.eda_solve_batch(1e-8, 5000, x0, True, dz, it, rr, st)
+        return dz, it, rr, st
+
+    R, C, Z = [], [], []
+    for e in range(12):
+        h, b = problem_on_gpu(100 + e)
+        dz, _, _, st = solve(h, b)
+        h.close()
+        assert (st == P.EDA_CONVERGED).all()
+        R.append(b[1:])
+        C.append(dz[0:1].expand(members, -1))
+        Z.append(dz[1:])
+    R, C, Z = (torch.cat(v).contiguous() for v in (R, C, Z))
+    with P.WarmStart(n, 32, max_batch=64) as ws:
+        ws.eda_ws_init(S.gaussian_matrix(1, ws.num_params, 5)[0])
+        order = np.concatenate([np.random.default_rng(e).permutation(R.shape[0]) for e in range(30)])
+        losses = ws.eda_ws_train(R, C, Z, epochs=30, batch=64, lr=2e-3, order=order.astype(np.int32))
+        assert losses[-1] < losses[0]
+        h, b = problem_on_gpu(900)
+        dz0, it0, rr0, st0 = solve(h, b)
+        ctrl = dz0[0:1].expand(members, -1).contiguous()
+        guess = torch.empty(members, n, dtype=torch.float64, device=dev)
+        ws.eda_ws_infer(b[1:].contiguous(), ctrl, guess)
+        x0 = torch.cat([dz0[0:1], guess]).contiguous()
+        dzw, itw, rrw, stw = solve(h, b, x0)
+        h.close()
+    ref = dz0[1:]
+    err_guess = (torch.linalg.norm(guess - ref, dim=1) / torch.linalg.norm(ref, dim=1)).cpu().numpy()
+    err_ctrl = (torch.linalg.norm(ctrl - ref, dim=1) / torch.linalg.norm(ref, dim=1)).cpu().numpy()
+    print("warm start: guess error median %.3f (control as guess %.3f); member iterations %d -> %d (%.1f %% saved)"
+          % (np.median(err_guess), np.median(err_ctrl), it0[1:].sum(), itw[1:].sum(),
+             100.0 * (1 - itw[1:].sum() / it0[1:].sum())))
+    assert np.median(err_guess) < np.median(err_ctrl)
+    assert (st0 == P.EDA_CONVERGED).all() and (stw == P.EDA_CONVERGED).all()
+    # both solutions are within their residuals of the exact one (lambda_min >= 1)
+    bn = torch.linalg.norm(b, dim=1).cpu().numpy()
+    diff = torch.linalg.norm(dzw - dz0, dim=1).cpu().numpy()
+    assert (diff <= (rr0 + rrw) * bn * (1 + 1e-6) + 1e-12).all()
