@@ -67,6 +67,21 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(t, device):
+    """The largest of every rank's t (the job's time: the slowest replica)."""
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_value(members, steps, world, t_max):
+    """Whole-job member solves/s of `world` independent replicas, each solving
+    `members` members per step for `steps` steps, over the slowest time."""
+    return world * members * steps / t_max
+
+
 class Clocks:
     """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
 
@@ -499,10 +514,8 @@ def run_ours(args):
     rr_mixed = relres.cpu().numpy()
     dz_mixed = dz.cpu().numpy()
     if world > 1:
-        tt = torch.tensor([t_mixed], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_mixed = float(tt.item())
-    value = world * M * args.steps / t_mixed
+        t_mixed = max_over_ranks(t_mixed, dev)
+    value = replica_value(M, args.steps, world, t_mixed)
 
     # ---- plain FP64 GPU path (comparison)
     t64, its64 = timed_steps(h64, max(1, args.fp64_steps), 1)
@@ -554,7 +567,7 @@ def run_ours(args):
     hm.close()
     h64.close()
     forms = None
-    if rank == 0 and not args.no_forms:
+    if rank == 0 and world == 1 and not args.no_forms:  # single-GPU measurements
         forms = {"scale": forms_scale(P, dev, peak), "uneven": forms_uneven(P, dev), "warm_start": forms_warm(P, dev)}
     if rank == 0:
         its_m = np.concatenate(its_mixed)
