@@ -314,6 +314,59 @@ def forms_scale(P, dev, hbm_peak):
     return out
 
 
+def forms_tiny(P, dev, problems=100):
+    """The tiny FP64 workload (n=40, 20-step window, 10 members + control,
+    k=10, PCG to 1e-6 within 100 iterations): the latency of one problem's
+    setup + sketch + LMP + solve on one handle, and the throughput of 100
+    seeded problems as one group."""
+    import torch
+    specs = [S.spec_tiny(seed=s_) for s_ in range(problems)]
+    hs, xbs, ys = [], [], []
+    for s_ in specs:
+        taps = P.bhalf_gaussian(s_.n, s_.length_scale, s_.sigma_b)
+        h = P.Handle.from_spec(s_, taps, precision=P.EDA_FP64)
+        dr = S.draws(s_)
+        xb = torch.empty(s_.n_members, s_.n, dtype=torch.float64, device=dev)
+        y = torch.empty(s_.n_members, s_.p, dtype=torch.float64, device=dev)
+        h.eda_twin(torch.tensor(s_.F + s_.spin_sigma * dr.eta_spin, device=dev), s_.spinup,
+                   torch.tensor(dr.eta_b, device=dev), torch.tensor(dr.eta_o, device=dev), xb, y)
+        hs.append(h)
+        xbs.append(xb)
+        ys.append(y)
+    M = specs[0].n_members
+    dz = torch.empty(M, specs[0].n, dtype=torch.float64, device=dev)
+    lat = []
+    for rep in range(6):  # one problem, end to end on its own handle (first run warms up)
+        h = hs[rep]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h.eda_set_trajectory(xbs[rep], ys[rep])
+        h.eda_sketch()
+        h.eda_build_lmp()
+        h.eda_solve_batch(TOL, 100, None, True, dz)
+        torch.cuda.synchronize()
+        lat.append(time.perf_counter() - t0)
+    with P.Group(hs) as g:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.eda_group_set_trajectories(xbs, ys)
+        g.eda_group_sketch()
+        g.eda_group_build_lmp()
+        T = g.total_members
+        it = np.zeros(T, np.int32)
+        st = np.zeros(T, np.int32)
+        g.eda_group_solve(TOL, 100, True, None, it, None, st)
+        torch.cuda.synchronize()
+        tg = time.perf_counter() - t0
+    for h in hs:
+        h.close()
+    return {"workload": "l96_n40_w20_m11 x %d seeds" % problems, "precision": "fp64",
+            "us_per_problem_single_handle": 1e6 * float(np.median(lat[1:])),
+            "group_member_solves_per_s": int((st == 0).sum()) / tg, "group_seconds": tg,
+            "group_converged": int((st == 0).sum()), "group_member_solves": T,
+            "iters_median": float(np.median(it)), "iters_max": int(it.max())}
+
+
 def forms_uneven(P, dev, count=256, maxit=3000):
     """Uneven batch: 256 independent problems in one group (mixed precision,
     graph-captured PCG, autotuned tiling), each member with a budget of
@@ -568,7 +621,8 @@ def run_ours(args):
     h64.close()
     forms = None
     if rank == 0 and world == 1 and not args.no_forms:  # single-GPU measurements
-        forms = {"scale": forms_scale(P, dev, peak), "uneven": forms_uneven(P, dev), "warm_start": forms_warm(P, dev)}
+        forms = {"tiny": forms_tiny(P, dev), "scale": forms_scale(P, dev, peak), "uneven": forms_uneven(P, dev),
+                 "warm_start": forms_warm(P, dev)}
     if rank == 0:
         its_m = np.concatenate(its_mixed)
         its_d = np.concatenate(its64)
