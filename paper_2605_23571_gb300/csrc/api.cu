@@ -1372,10 +1372,11 @@ EDA_API int eda_solve_batch(eda_handle* h, double tol, int maxit, const double* 
   In ix0;
   CU(h, ix0.init(x0, vb, h->st));
   CU(h, cudaMemsetAsync(h->nactive, 0, sizeof(int), h->st));
-  // x = x0 (or 0), r = b - H x0
+  // x = x0 (or 0), r = b - H x0: with the sweeps of the handle's precision
+  // (in EDA_MIXED the FP64 true residual at the end checks the result)
   if (x0) {
     CU(h, cudaMemcpyAsync(h->x, ix0.dev, vb, cudaMemcpyDeviceToDevice, h->st));
-    int rc = hvp_dev(h, h->cols, M, h->x, h->q, 1, true, nullptr);
+    int rc = hvp_dev(h, h->cols, M, h->x, h->q, 1, h->precision == EDA_FP64, nullptr);
     if (rc) return rc;
     eda::count_launch();
     sub_kernel<double><<<grid_for((long long)M * n), 256, 0, h->st>>>((long long)M * n, h->b, h->q, h->r);
