@@ -150,19 +150,28 @@ SWEEP_SRC = os.path.join(ROOT, "paper_2605_23571_gb300", "csrc", "sweep.cu")
 SWEEP_PROFILE = os.path.join(ROOT, "profiles", "sweep_kernel_f32_member_hvp_l96_n4096_w64_m51.md")
 
 
+def code_sha256(path):
+    """sha256 of a CUDA source with its comments and blank lines removed (the
+    code the counters were taken on; comment edits do not change it)."""
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    code = "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+    return hashlib.sha256(code.encode()).hexdigest()
+
+
 def sweep_traffic_per_launch():
     """DRAM bytes (read + write) per launch of the FP32 member-HVP sweep from
-    the committed ncu summary, or None when the sweep source has changed
+    the committed ncu summary, or None when the sweep's code has changed
     since those counters were taken (or there is no summary)."""
     if not os.path.exists(SWEEP_PROFILE):
         return None
     txt = open(SWEEP_PROFILE).read()
-    m_sha = re.search(r"sweep\.cu sha256: ([0-9a-f]{64})", txt)
+    m_sha = re.search(r"sweep\.cu code sha256: ([0-9a-f]{64})", txt)
     m_b = re.search(r"dram bytes per launch \(read \+ write\): ([0-9.eE+]+)", txt)
     if not (m_sha and m_b):
         return None
-    sha = hashlib.sha256(open(SWEEP_SRC, "rb").read()).hexdigest()
-    return float(m_b.group(1)) if sha == m_sha.group(1) else None
+    return float(m_b.group(1)) if code_sha256(SWEEP_SRC) == m_sha.group(1) else None
 
 
 # ---------------------------------------------------------------- workload

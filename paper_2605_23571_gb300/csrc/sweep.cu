@@ -3,7 +3,7 @@
 // right-hand side U_B^T G^T R^{-1} d (Section 2.3, Eq. (system with CVT);
 // the model and RK4 step of Section 4).
 //
-// Layout of one column (one vector on one member's trajectory):
+// Layout of one column (one vector on one member's trajectory), sweep_kernel:
 //  * the column is split over a thread-block cluster of CS CTAs; CTA r owns
 //    the global indices [r*Ttile, min((r+1)*Ttile, n));
 //  * each CTA computes on an extended region of E = A*C consecutive (periodic)
@@ -12,13 +12,22 @@
 //  * a stage of RK4 needs the neighbours i-2, i-1, i+1, i+2 of a thread's
 //    run: threads publish the first two and last two values of their run to
 //    a shared-memory edge buffer and read their neighbours' after a barrier;
-//  * the stencil wraps inside the extended region, so values within 8 s + 8
-//    of its ends are wrong after s steps; every K steps the halo is reloaded
-//    from its owners (distributed shared memory inside the cluster), and
-//    HL = 8K + 8 keeps the owned tile exact (for CS = 1 the owner is the CTA
-//    itself and the reload implements the periodic boundary);
-//  * trajectory states x_t are streamed from HBM into a double-buffered
-//    shared-memory stage (coalesced loads issued one step ahead).
+//  * the stencil wraps inside the extended region, so values near its ends
+//    go wrong (an error from outside travels at most 8 points per
+//    tangent-linear step and 11 per adjoint step, 8K + 3 over K steps);
+//    every K steps the halo is reloaded from its owners (distributed shared
+//    memory inside the cluster), and HL = 8K + 8 keeps the owned tile exact
+//    (for CS = 1 the owner is the CTA itself and the reload implements the
+//    periodic boundary);
+//  * trajectory runs are loaded straight into registers with 16-byte loads,
+//    one step ahead; the FP64 variant (STG) reads the RK4 stage states
+//    stored with the trajectory instead of recomputing them;
+//  * the Hessian-product epilogue applies U_B from the cluster's mirrors and
+//    adds v . (H v) of the column to the PCG accumulators.
+// Columns too long for one cluster run as chains of K-step launches whose
+// state passes through global buffers (multi-launch tiling, launch_sweep).
+// wsweep_kernel, the warp-tiled Hessian-product variant, is described where
+// it is defined.
 //
 // The tangent linear is the exact derivative of the discrete RK4 step and
 // the adjoint its exact transpose, computed stage by stage in reverse.

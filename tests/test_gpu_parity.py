@@ -610,3 +610,26 @@ def test_rank_deficient_sketch_uses_the_truncated_eigendecomposition():
         rr = np.zeros(spec.n_members)
         h.eda_solve_batch(1e-6, 500, None, True, dz, None, rr, st)
     assert (st == P.EDA_CONVERGED).all() and (rr <= 1e-6).all()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_control_only_problem_without_lmp(precision):
+    # a single member (no perturbed members, so no sketch and no LMP): the
+    # row-chunk PCG kernels run with no projections, the sketch is refused,
+    # and the solution matches the oracle's
+    spec = S.spec_small(97, 12, 1, every_var=3, every_step=3, length_scale=3.0, ell=0, k=0, seed=13)
+    taps, xb, y = problem(spec)
+    traj, d, b = oracle_setup(spec, taps, xb, y)
+    exact = O.pcg(lambda V: O.hvp(spec, traj, V, taps), b, tol=1e-13, maxit=2000)["x"]
+    prec = P.EDA_FP64 if precision == "fp64" else P.EDA_MIXED
+    with make(spec, taps, precision=prec) as h:
+        h.eda_set_trajectory(xb, y)
+        with pytest.raises(P.EdaError) as e:
+            h.eda_sketch()
+        assert e.value.code == P.EDA_ERR_INVALID
+        dz = np.zeros_like(b)
+        rr = np.zeros(1)
+        st = np.zeros(1, np.int32)
+        h.eda_solve_batch(1e-9, 2000, None, False, dz, None, rr, st)
+    assert st[0] == P.EDA_CONVERGED and rr[0] <= 1e-9
+    assert np.linalg.norm(dz - exact) <= rr[0] * np.linalg.norm(b) * (1 + 1e-6) + 1e-12
