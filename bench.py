@@ -150,6 +150,18 @@ SWEEP_SRC = os.path.join(ROOT, "paper_2605_23571_gb300", "csrc", "sweep.cu")
 SWEEP_PROFILE = os.path.join(ROOT, "profiles", "sweep_kernel_f32_member_hvp_l96_n4096_w64_m51.md")
 
 
+def sweep_kernel_name(plan, dtype="float"):
+    """The sweep kernel a tiling from eda_sweep_plan launches, with its shape."""
+    if plan["kind"] == "warp":
+        return "wsweep_kernel<%s,%d> (warp-tiled: %d CTAs per vector x %d threads, halo refresh every %d steps)" % (
+            dtype, plan["C"], plan["ctas_per_vector"], plan["threads"], plan["K"])
+    if plan["kind"] == "multi-launch":
+        return "sweep_kernel<%s,%d> (multi-launch: %d tiles per vector x %d threads, %d steps per launch)" % (
+            dtype, plan["C"], plan["ctas_per_vector"], plan["threads"], plan["K"])
+    return "sweep_kernel<%s,%d> (clusters of %d CTAs x %d threads, halo refresh every %d steps)" % (
+        dtype, plan["C"], plan["ctas_per_vector"], plan["threads"], plan["K"])
+
+
 def code_sha256(path):
     """sha256 of a CUDA source with its comments and blank lines removed (the
     code the counters were taken on; comment edits do not change it)."""
@@ -160,18 +172,26 @@ def code_sha256(path):
     return hashlib.sha256(code.encode()).hexdigest()
 
 
-def sweep_traffic_per_launch():
+def sweep_traffic_per_launch(plan=None):
     """DRAM bytes (read + write) per launch of the FP32 member-HVP sweep from
     the committed ncu summary, or None when the sweep's code has changed
-    since those counters were taken (or there is no summary)."""
+    since those counters were taken, when the tiling in use (plan, from
+    eda_sweep_plan) is not the captured one, or there is no summary."""
     if not os.path.exists(SWEEP_PROFILE):
         return None
     txt = open(SWEEP_PROFILE).read()
     m_sha = re.search(r"sweep\.cu code sha256: ([0-9a-f]{64})", txt)
     m_b = re.search(r"dram bytes per launch \(read \+ write\): ([0-9.eE+]+)", txt)
-    if not (m_sha and m_b):
+    m_p = re.search(r"captured plan: kind=(\S+) ctas_per_vector=(\d+) threads=(\d+) C=(\d+) K=(\d+)", txt)
+    if not (m_sha and m_b and m_p):
         return None
-    return float(m_b.group(1)) if code_sha256(SWEEP_SRC) == m_sha.group(1) else None
+    if code_sha256(SWEEP_SRC) != m_sha.group(1):
+        return None
+    if plan is not None:
+        cap = (m_p.group(1),) + tuple(int(v) for v in m_p.groups()[1:])
+        if cap != (plan["kind"], plan["ctas_per_vector"], plan["threads"], plan["C"], plan["K"]):
+            return None
+    return float(m_b.group(1))
 
 
 # ---------------------------------------------------------------- workload
@@ -556,6 +576,7 @@ def run_ours(args):
     tuned_ms_mixed = hm.eda_autotune(0)
     h64.eda_set_trajectory(xb, y)
     tuned_ms_64 = h64.eda_autotune(0)
+    plan32 = hm.eda_sweep_plan(fp64=False)
 
     # ---- timed region (headline: mixed precision)
     for _ in range(args.warmup):
@@ -596,7 +617,7 @@ def run_ours(args):
     bytes_per_col = 4 * n * (2 * spec.nsteps + 2)
     achieved = bytes_per_col * sw_cols / (sw_ms / 1e3) / 1e9
     peak, peak_kind = measured_peaks()
-    traffic = sweep_traffic_per_launch()
+    traffic = sweep_traffic_per_launch(plan32)
 
     # ---- end to end through the C ABI with host buffers
     xb_h = xb.cpu().pin_memory().numpy()
@@ -652,7 +673,7 @@ def run_ours(args):
                       "rel_diff_mixed_vs_fp64_max": diff64},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "sweep_kernel<float,8> (FP32 Hessian-product sweeps of the timed steps)",
+                         "kernel": sweep_kernel_name(plan32) + ": the FP32 Hessian-product sweeps of the timed steps",
                          "launches_timed": sw_calls, "columns": sw_cols,
                          "ms_per_launch": sw_ms / max(1, sw_calls),
                          "bytes_per_launch": bytes_per_col * sw_cols / max(1, sw_calls),

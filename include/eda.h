@@ -251,6 +251,18 @@ EDA_API int eda_hvp(eda_handle* h, const int* member_of_col, int ncol, const dou
 EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out);
 
 /*
+ * The tiling the Hessian-product sweeps of one precision (fp64 != 0: FP64,
+ * else FP32) use at this point (after eda_autotune, the autotuned one).
+ * info[8] (host, caller-owned) receives: [0] kind (0 thread-block cluster,
+ * 1 multi-launch tiles of K steps, 2 warp-tiled), [1] CTAs per state vector
+ * (cluster size or tiles), [2] threads per CTA, [3] values per thread (C),
+ * [4] halo refresh period K (steps), [5] halo width HL (points, each end),
+ * [6] owned points per CTA, [7] dynamic shared memory per CTA (bytes).
+ * EDA_ERR_INVALID if fp64 == 0 on an FP64 handle; no device work.
+ */
+EDA_API int eda_sweep_plan(eda_handle* h, int fp64, int* info);
+
+/*
  * Tracing: process-wide number of CUDA kernels the library has launched
  * (every handle, every entry point) since it was loaded.  No device work.
  */

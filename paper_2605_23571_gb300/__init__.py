@@ -36,7 +36,7 @@ EXPORTS = ["eda_version", "eda_last_error", "eda_create", "eda_destroy", "eda_tw
            "eda_ws_create", "eda_ws_destroy", "eda_ws_last_error", "eda_ws_num_params", "eda_ws_set_params",
            "eda_ws_get_params", "eda_ws_set_scales", "eda_ws_get_scales", "eda_ws_loss_grad", "eda_ws_train",
            "eda_ws_infer", "eda_hvp_noalloc", "eda_hvp_noalloc_capacity", "eda_lmp_info",
-           "eda_trace", "eda_trace_read", "eda_ws_init"]
+           "eda_trace", "eda_trace_read", "eda_ws_init", "eda_sweep_plan"]
 
 
 class EdaError(RuntimeError):
@@ -99,6 +99,8 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(d)]
     L.eda_lmp_info.restype = i
     L.eda_lmp_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)]
+    L.eda_sweep_plan.restype = i
+    L.eda_sweep_plan.argtypes = [vp, i, ctypes.POINTER(i)]
     L.eda_solve_batch.restype = i
     L.eda_solve_batch.argtypes = [vp, d, i, vp, i, vp, vp, vp, vp]
     L.eda_hvp.restype = i
@@ -321,6 +323,19 @@ class Handle:
         path, rank, shift = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
         self._check(self._L.eda_lmp_info(self._h, ctypes.byref(path), ctypes.byref(rank), ctypes.byref(shift)))
         return path.value, rank.value, shift.value
+
+    SWEEP_PLAN_KEYS = ("kind", "ctas_per_vector", "threads", "C", "K", "halo", "owned", "smem")
+    SWEEP_PLAN_KINDS = ("cluster", "multi-launch", "warp")
+
+    def eda_sweep_plan(self, fp64=False):
+        """The tiling of the FP64 or FP32 Hessian-product sweeps as a dict
+        (kind: cluster, multi-launch or warp; C values per thread, halo
+        refresh period K, ...)."""
+        info = (ctypes.c_int * 8)()
+        self._check(self._L.eda_sweep_plan(self._h, int(bool(fp64)), info))
+        out = dict(zip(self.SWEEP_PLAN_KEYS, list(info)))
+        out["kind"] = self.SWEEP_PLAN_KINDS[out["kind"]]
+        return out
 
     def eda_solve_batch(self, tol, maxit, x0, use_lmp, dz_out, iters_out=None, relres_out=None,
                         status_out=None):

@@ -1274,6 +1274,23 @@ EDA_API int eda_set_lmp(eda_handle* h, const double* s_in, const double* eigvals
   return EDA_OK;
 }
 
+EDA_API int eda_sweep_plan(eda_handle* h, int fp64, int* info) {
+  if (!h || !info) return fail(h, EDA_ERR_INVALID, "handle or info is NULL");
+  if (!fp64 && h->precision != EDA_MIXED) return fail(h, EDA_ERR_INVALID, "an FP64 handle has no FP32 sweep");
+  const int* ot = nullptr;
+  const int* wt = nullptr;
+  const eda::SweepPlan& p = eda::hvp_plan(h, fp64 != 0, &ot, &wt);
+  info[0] = p.warp ? 2 : (p.ml ? 1 : 0);
+  info[1] = p.CS;
+  info[2] = p.A;
+  info[3] = p.C;
+  info[4] = p.K;
+  info[5] = p.HL;
+  info[6] = p.Ttile;
+  info[7] = (int)p.smem;
+  return EDA_OK;
+}
+
 EDA_API int eda_lmp_info(eda_handle* h, int* path, int* rank, double* shift) {
   if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
   if (!h->have_lmp) return fail(h, EDA_ERR_STATE, "eda_lmp_info before eda_build_lmp or eda_set_lmp");

@@ -314,12 +314,24 @@ def test_autotuned_tiling_keeps_parity():
         HV = np.zeros_like(V)
         h.eda_hvp(cols, V, HV, True)
         assert rowrel(HV, ref).max() < 1e-4
+        for fp64, runs in ((False, (4, 8)), (True, (2, 4))):
+            plan = h.eda_sweep_plan(fp64)
+            assert plan["kind"] in ("cluster", "multi-launch", "warp") and plan["C"] in runs
+            assert plan["K"] >= 1 and plan["threads"] % 32 == 0 and plan["ctas_per_vector"] >= 1
+            if plan["kind"] != "warp":
+                # CTAs x owned points cover the state; each tile carries its
+                # halo of 8K + 8 points (the K-step reach) at both ends
+                assert plan["halo"] == 8 * plan["K"] + 8
+                assert plan["ctas_per_vector"] * plan["owned"] >= spec.n
+                assert plan["owned"] + 2 * plan["halo"] <= plan["threads"] * plan["C"]
     with make(spec, taps) as h:
         h.eda_set_trajectory(xb, y)
         assert h.eda_autotune(1) > 0
         HV = np.zeros_like(V)
         h.eda_hvp(cols, V, HV, True)
         assert rowrel(HV, ref).max() < 1e-11
+        with pytest.raises(P.EdaError):
+            h.eda_sweep_plan(False)  # an FP64 handle has no FP32 sweep
 
 
 def test_hvp_obs_at_window_ends():
