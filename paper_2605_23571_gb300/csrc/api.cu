@@ -1309,8 +1309,8 @@ namespace {
 // LMP arithmetic in FP64 or FP32 accordingly.  One iteration is the sweep
 // (with p.q in its epilogue) and the update, precond and dir launches over
 // row chunks of all members (pcg.h).  The host polls the active count
-// through a ring of pinned copies and runs at most kRing-1 iterations ahead
-// of the device.
+// through a ring of pinned host slots (the dir launch writes the count) and
+// runs at most kRing-1 iterations ahead of the device.
 template <typename TS>
 int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done, bool sweep64,
                int replace_every) {
@@ -1351,10 +1351,9 @@ int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int*
     }
     CU(h, eda::pcg2_precond<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->r, h->z, h->pv, h->sc, h->acc, h->active,
                                 Wk, par, tol, maxit, fixed, lmp, 0, h->nactive, h->st));
-    CU(h, eda::pcg2_dir<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->z, h->pv, h->sc, h->acc, h->active, Wk, par,
-                            h->st));
     const int slot = it % R;
-    CU(h, cudaMemcpyAsync(h->hring + slot, h->nactive, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    CU(h, eda::pcg2_dir<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->z, h->pv, h->sc, h->acc, h->active, Wk, par,
+                            h->st, h->nactive, h->hring + slot));
     CU(h, cudaEventRecord(h->ring_ev[slot], h->st));
     if (it - it0 >= R) {
       const int old = (it - R + 1) % R;

@@ -74,6 +74,15 @@ __device__ __forceinline__ void stage_S(const TS* S, int n, int k, int row0, int
   }
 }
 
+// Rows of a row chunk per lane (kPcgRows / 32): the warp of a member keeps
+// its rows of the PCG vectors in registers, loaded before the CTA stages S so
+// that both sets of global loads are in flight together.
+constexpr int kRowsPerLane = kPcgRows / 32;
+// LMP modes per lane in the precond launch: k <= 80 modes (the library's
+// limit on ell) pad to at most 96 = 3 x 32 values
+constexpr int kCwPerLane = 3;
+static_assert(32 * kCwPerLane >= 84 && 32 * kCwPerLane >= 82, "padded k of 80 LMP modes fits");
+
 template <typename TS>
 __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* tasks, const PcgProb* probs, int kmax,
                                                                const double* p, const double* q, double* x,
@@ -83,6 +92,7 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* ta
   extern __shared__ __align__(16) unsigned char smraw[];
   using V = typename Vec16<TS>::type;
   constexpr int VW = Vec16<TS>::VW;
+  constexpr int R = kRowsPerLane;
   const int RBP = vec_stride<TS>(kPcgRows);  // S chunk [c][RBP]: lane c reads column c
   const PcgTask tk = tasks[blockIdx.x];
   const PcgProb P = probs[tk.prob];
@@ -91,6 +101,31 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* ta
   TS* Ssm = reinterpret_cast<TS*>(smraw);
   TS* rsm = Ssm + (size_t)kmax * RBP;  // [kWarps][kPcgRows]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // this warp's member (one member per warp) and its rows, loaded first
+  const int m = blockIdx.y * kWarps + wid;
+  const int item = P.item0 + m;
+  const bool live = m < P.M && active[item] != 0;
+  const long long off = P.off0 + (long long)m * P.n + tk.row0;
+  double pv[R], qv[R], xv[R], rv[R];
+  double pq = 0.0, rzp = 0.0;
+  if (live) {
+    if (update) {
+      pq = acc[item].pq;
+      rzp = acc[item].rz[par];
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int i = lane + 32 * j;
+      if (i < tk.rows) {
+        rv[j] = r[off + i];
+        if (update) {
+          pv[j] = p[off + i];
+          qv[j] = q[off + i];
+          xv[j] = x[off + i];
+        }
+      }
+    }
+  }
   const TS* S = static_cast<const TS*>(P.S);
   stage_S<TS>(S, P.n, k, tk.row0, tk.rows, Ssm, RBP, 1);
   for (int idx = threadIdx.x; idx < k * (rows_v - tk.rows); idx += kThreads) {
@@ -99,54 +134,54 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* ta
   }
   // slot par^1 collects r.z in the precond launch that follows
   if (update && tk.first && blockIdx.y == 0)
-    for (int m = threadIdx.x; m < P.M; m += kThreads) acc[P.item0 + m].rz[par ^ 1] = 0.0;
+    for (int mm = threadIdx.x; mm < P.M; mm += kThreads) acc[P.item0 + mm].rz[par ^ 1] = 0.0;
   __syncthreads();
+  if (!live) return;
   TS* rw = rsm + wid * kPcgRows;
-  {
-    const int m = blockIdx.y * kWarps + wid;  // one member per warp
-    if (m >= P.M) return;
-    const int item = P.item0 + m;
-    if (!active[item]) return;
-    const long long off = P.off0 + (long long)m * P.n + tk.row0;
-    if (update) {
-      const double pq = acc[item].pq;
-      if (!(pq > 0.0)) {  // breakdown (or NaN): every CTA skips the member
-        if (tk.first && lane == 0) {
-          sc[item].status = isfinite(pq) ? EDA_BREAKDOWN : EDA_NAN;
-          active[item] = 0;
-          atomicSub(nactive, 1);
-        }
-        return;
+  if (update) {
+    if (!(pq > 0.0)) {  // breakdown (or NaN): every CTA skips the member
+      if (tk.first && lane == 0) {
+        sc[item].status = isfinite(pq) ? EDA_BREAKDOWN : EDA_NAN;
+        active[item] = 0;
+        atomicSub(nactive, 1);
       }
-      const double alpha = acc[item].rz[par] / pq;
-      double rr = 0.0;
-      for (int i = lane; i < tk.rows; i += 32) {
-        const double pv = p[off + i], qv = q[off + i];
-        x[off + i] += alpha * pv;
-        const double rv = r[off + i] - alpha * qv;
-        r[off + i] = rv;
-        rr += rv * rv;
-        rw[i] = (TS)rv;
-      }
-      rr = warp_sum(rr);
-      if (lane == 0) atomicAdd(&acc[item].rr, rr);
-    } else {
-      for (int i = lane; i < tk.rows; i += 32) rw[i] = (TS)r[off + i];
+      return;
     }
-    if (lane < rows_v - tk.rows) rw[tk.rows + lane] = TS(0);
-    __syncwarp();
-    for (int c = lane; c < k; c += 32) {
-      const V* Sc = reinterpret_cast<const V*>(Ssm + c * RBP);
-      const V* rv = reinterpret_cast<const V*>(rw);
-      TS s0 = 0, s1 = 0;
-      int i = 0;
-      for (; i + 2 <= rows_v / VW; i += 2) {
-        s0 += Vec16<TS>::dot(Sc[i], rv[i]);
-        s1 += Vec16<TS>::dot(Sc[i + 1], rv[i + 1]);
+    const double alpha = rzp / pq;
+    double rr = 0.0;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int i = lane + 32 * j;
+      if (i < tk.rows) {
+        x[off + i] = xv[j] + alpha * pv[j];
+        const double rn = rv[j] - alpha * qv[j];
+        r[off + i] = rn;
+        rr += rn * rn;
+        rw[i] = (TS)rn;
       }
-      if (i < rows_v / VW) s0 += Vec16<TS>::dot(Sc[i], rv[i]);
-      atomicAdd(&Wk[(long long)item * kmax + c], s0 + s1);
     }
+    rr = warp_sum(rr);
+    if (lane == 0) atomicAdd(&acc[item].rr, rr);
+  } else {
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int i = lane + 32 * j;
+      if (i < tk.rows) rw[i] = (TS)rv[j];
+    }
+  }
+  if (lane < rows_v - tk.rows) rw[tk.rows + lane] = TS(0);
+  __syncwarp();
+  for (int c = lane; c < k; c += 32) {
+    const V* Sc = reinterpret_cast<const V*>(Ssm + c * RBP);
+    const V* rvv = reinterpret_cast<const V*>(rw);
+    TS s0 = 0, s1 = 0;
+    int i = 0;
+    for (; i + 2 <= rows_v / VW; i += 2) {
+      s0 += Vec16<TS>::dot(Sc[i], rvv[i]);
+      s1 += Vec16<TS>::dot(Sc[i + 1], rvv[i + 1]);
+    }
+    if (i < rows_v / VW) s0 += Vec16<TS>::dot(Sc[i], rvv[i]);
+    atomicAdd(&Wk[(long long)item * kmax + c], s0 + s1);
   }
 }
 
@@ -159,6 +194,7 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
   extern __shared__ __align__(16) unsigned char smraw[];
   using V = typename Vec16<TS>::type;
   constexpr int VW = Vec16<TS>::VW;
+  constexpr int R = kRowsPerLane;
   const PcgTask tk = tasks[blockIdx.x];
   const PcgProb P = probs[tk.prob];
   const int k = use_lmp ? P.k : 0;
@@ -167,6 +203,36 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
   TS* Ssm = reinterpret_cast<TS*>(smraw);        // [row][KP]: lane = row reads a row
   TS* wsm = Ssm + (size_t)kPcgRows * KW;         // [kWarps][KW]
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // this warp's member, its rows of r, its stopping-test inputs and its
+  // scaled projections, loaded before the CTA stages S
+  const int m = blockIdx.y * kWarps + wid;
+  const int item = P.item0 + m;
+  const bool live = m < P.M && active[item] != 0;
+  const long long off = P.off0 + (long long)m * P.n + tk.row0;
+  double rv[R];
+  double bn = 0.0, rrv = 0.0, tolm = 0.0;
+  int itj = 0;
+  TS cw[kCwPerLane];  // c_c w_c for c = lane + 32 j
+#pragma unroll
+  for (int j = 0; j < kCwPerLane; ++j) cw[j] = TS(0);
+  if (live) {
+    if (!init) {
+      bn = sc[item].bnorm;
+      rrv = acc[item].rr;
+      itj = sc[item].iters + 1;
+      tolm = sc[item].tolm;
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int i = lane + 32 * j;
+      if (i < tk.rows) rv[j] = r[off + i];
+    }
+#pragma unroll
+    for (int j = 0; j < kCwPerLane; ++j) {
+      const int c = lane + 32 * j;
+      if (c < k) cw[j] = (TS)(P.c[c] * (double)Wk[(long long)item * kmax + c]);
+    }
+  }
   const TS* S = static_cast<const TS*>(P.S);
   stage_S<TS>(S, P.n, k, tk.row0, tk.rows, Ssm, 1, KP);
   if (k > 0)
@@ -176,55 +242,51 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
     }
   // p^T q of the next sweep accumulates from zero
   if (tk.first && blockIdx.y == 0)
-    for (int m = threadIdx.x; m < P.M; m += kThreads) acc[P.item0 + m].pq = 0.0;
+    for (int mm = threadIdx.x; mm < P.M; mm += kThreads) acc[P.item0 + mm].pq = 0.0;
   __syncthreads();
+  if (!live) return;
   const int slot = init ? 0 : (par ^ 1);
   TS* wc = wsm + wid * KW;
-  {
-    const int m = blockIdx.y * kWarps + wid;  // one member per warp
-    if (m >= P.M) return;
-    const int item = P.item0 + m;
-    if (!active[item]) return;
-    if (!init) {
-      // the stopping test, from values no CTA of this launch writes
-      const double bn = sc[item].bnorm;
-      const double rel = bn > 0.0 ? sqrt(acc[item].rr) / bn : 0.0;
-      const int itj = sc[item].iters + 1;
-      const double tolm = sc[item].tolm;
-      bool stop = false;
-      int st = EDA_MAXIT;
-      if (!isfinite(rel)) {
-        st = EDA_NAN;
-        stop = true;
-      } else if (fixed > 0) {
-        if (itj >= fixed) {
-          st = EDA_CONVERGED;
-          stop = true;
-        }
-      } else if (rel <= (tolm > 0.0 ? tolm : tol)) {
+  if (!init) {
+    // the stopping test, from values no CTA of this launch writes
+    const double rel = bn > 0.0 ? sqrt(rrv) / bn : 0.0;
+    bool stop = false;
+    int st = EDA_MAXIT;
+    if (!isfinite(rel)) {
+      st = EDA_NAN;
+      stop = true;
+    } else if (fixed > 0) {
+      if (itj >= fixed) {
         st = EDA_CONVERGED;
         stop = true;
-      } else if (maxit > 0 && itj >= maxit) {
-        stop = true;
       }
-      if (tk.first && lane == 0) {
-        sc[item].relres = rel;
-        acc[item].inc = 1;
-        if (stop) {
-          sc[item].status = st;
-          active[item] = 0;
-          atomicSub(nactive, 1);
-        }
-      }
-      if (stop) return;
+    } else if (rel <= (tolm > 0.0 ? tolm : tol)) {
+      st = EDA_CONVERGED;
+      stop = true;
+    } else if (maxit > 0 && itj >= maxit) {
+      stop = true;
     }
-    for (int c = lane; c < KP; c += 32) wc[c] = c < k ? (TS)(P.c[c] * (double)Wk[(long long)item * kmax + c]) : TS(0);
-    __syncwarp();
-    const long long off = P.off0 + (long long)m * P.n + tk.row0;
-    double rz = 0.0;
-    for (int i = lane; i < tk.rows; i += 32) {
-      const double rv = r[off + i];
-      double zv = rv;
+    if (tk.first && lane == 0) {
+      sc[item].relres = rel;
+      acc[item].inc = 1;
+      if (stop) {
+        sc[item].status = st;
+        active[item] = 0;
+        atomicSub(nactive, 1);
+      }
+    }
+    if (stop) return;
+  }
+#pragma unroll
+  for (int j = 0; j < kCwPerLane; ++j)
+    if (lane + 32 * j < KP) wc[lane + 32 * j] = cw[j];
+  __syncwarp();
+  double rz = 0.0;
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int i = lane + 32 * j;
+    if (i < tk.rows) {
+      double zv = rv[j];
       if (k > 0) {
         const V* Srow = reinterpret_cast<const V*>(Ssm + i * KP);
         const V* wv = reinterpret_cast<const V*>(wc);
@@ -239,20 +301,25 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
       }
       z[off + i] = zv;
       if (init) p[off + i] = zv;
-      rz += rv * zv;
+      rz += rv[j] * zv;
     }
-    rz = warp_sum(rz);
-    if (lane == 0) atomicAdd(&acc[item].rz[slot], rz);
   }
+  rz = warp_sum(rz);
+  if (lane == 0) atomicAdd(&acc[item].rz[slot], rz);
 }
 
 template <typename TS>
 __global__ void __launch_bounds__(kThreads) pcg2_dir_kernel(const PcgTask* tasks, const PcgProb* probs, int kmax,
                                                             const double* z, double* p, PcgScalars* sc, PcgAcc* acc,
-                                                            const int* active, TS* Wk, int par) {
+                                                            const int* active, TS* Wk, int par,
+                                                            const int* nactive, int* host_count) {
   const PcgTask tk = tasks[blockIdx.x];
   const PcgProb P = probs[tk.prob];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // the active count is final here (update and precond change it): one
+  // thread copies it to the host's ring slot (mapped pinned memory)
+  if (host_count != nullptr && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
+    *reinterpret_cast<volatile int*>(host_count) = *nactive;
   if (tk.first && blockIdx.y == 0) {
     // bookkeeping of the problem: iteration counts, and the accumulators
     // the next update launch fills
@@ -371,6 +438,7 @@ cudaError_t pcg2_precond(const PcgTask* tasks, int ntasks, const PcgProb* probs,
                          double* z, double* p, PcgScalars* sc, PcgAcc* acc, int* active, const TS* Wk, int par,
                          double tol, int maxit, int fixed, int use_lmp, int init, int* nactive, cudaStream_t s) {
   if (ntasks <= 0 || mmax <= 0) return cudaSuccess;
+  if (vec_stride<TS>(kmax) > 32 * kCwPerLane) return cudaErrorInvalidValue;  // more than 80 LMP modes
   const int KW = vec_stride<TS>(kmax > 0 ? kmax : 1);
   const size_t smem = ((size_t)kPcgRows * KW + (size_t)kWarps * KW) * sizeof(TS);
   cudaError_t e = set_smem(pcg2_precond_kernel<TS>, smem);
@@ -383,10 +451,13 @@ cudaError_t pcg2_precond(const PcgTask* tasks, int ntasks, const PcgProb* probs,
 
 template <typename TS>
 cudaError_t pcg2_dir(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* z, double* p,
-                     PcgScalars* sc, PcgAcc* acc, const int* active, TS* Wk, int par, cudaStream_t s) {
+                     PcgScalars* sc, PcgAcc* acc, const int* active, TS* Wk, int par, cudaStream_t s,
+                     const int* nactive, int* host_count) {
   if (ntasks <= 0 || mmax <= 0) return cudaSuccess;
   count_launch();
-  pcg2_dir_kernel<TS><<<dim3(ntasks, (mmax + kWarps - 1) / kWarps), kThreads, 0, s>>>(tasks, probs, kmax, z, p, sc, acc, active, Wk, par);
+  pcg2_dir_kernel<TS><<<dim3(ntasks, (mmax + kWarps - 1) / kWarps), kThreads, 0, s>>>(tasks, probs, kmax, z, p, sc, acc,
+                                                                                     active, Wk, par, nactive,
+                                                                                     host_count);
   return cudaGetLastError();
 }
 
@@ -425,8 +496,8 @@ template cudaError_t pcg2_precond<float>(const PcgTask*, int, const PcgProb*, in
                                          PcgScalars*, PcgAcc*, int*, const float*, int, double, int, int, int, int,
                                          int*, cudaStream_t);
 template cudaError_t pcg2_dir<double>(const PcgTask*, int, const PcgProb*, int, int, const double*, double*, PcgScalars*,
-                                      PcgAcc*, const int*, double*, int, cudaStream_t);
+                                      PcgAcc*, const int*, double*, int, cudaStream_t, const int*, int*);
 template cudaError_t pcg2_dir<float>(const PcgTask*, int, const PcgProb*, int, int, const double*, double*, PcgScalars*,
-                                     PcgAcc*, const int*, float*, int, cudaStream_t);
+                                     PcgAcc*, const int*, float*, int, cudaStream_t, const int*, int*);
 
 }  // namespace eda

@@ -78,9 +78,12 @@ cudaError_t pcg2_precond(const PcgTask* tasks, int ntasks, const PcgProb* probs,
                          double tol, int maxit, int fixed, int use_lmp, int init, int* nactive, cudaStream_t s);
 
 // p = z + beta p; counts the iteration and clears rr and the projections.
+// With host_count (pinned host memory) != NULL, one thread also copies the
+// active count *nactive there, which the host reads after an event.
 template <typename TS>
 cudaError_t pcg2_dir(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* z, double* p,
-                     PcgScalars* sc, PcgAcc* acc, const int* active, TS* Wk, int par, cudaStream_t s);
+                     PcgScalars* sc, PcgAcc* acc, const int* active, TS* Wk, int par, cudaStream_t s,
+                     const int* nactive = nullptr, int* host_count = nullptr);
 
 // Residual replacement: r = b - hx (hx = (I + A) x from an accurate sweep)
 // and ||r||^2 (cleared first) for the active members of T.
