@@ -223,6 +223,62 @@ def _subset_spec(n, seed):
                   name="l96_n%d_w13_m5_subset" % n)
 
 
+def _varied_spec(n, seed):
+    # a different observation set at every observation step (all variables,
+    # every third, random subsets, every second), including t = 0 and t = N
+    rng = np.random.default_rng(seed)
+    steps = np.array([0, 1, 4, 7, 12, 13], dtype=np.int32)
+    sets = [np.arange(n), np.arange(0, n, 3), np.sort(rng.choice(n, int(0.3 * n), replace=False)),
+            np.arange(n), np.sort(rng.choice(n, int(0.5 * n), replace=False)), np.arange(1, n, 2)]
+    ptr = np.concatenate([[0], np.cumsum([len(x) for x in sets])]).astype(np.int32)
+    return S.Spec(n=n, nsteps=13, obs_steps=steps, obs_ptr=ptr,
+                  obs_idx=np.concatenate(sets).astype(np.int32), sigma_o=0.8, sigma_b=1.0,
+                  length_scale=4.0, n_members=4, ell=3, k=3, spinup=5, seed=seed,
+                  name="l96_n%d_w13_m4_varied" % n)
+
+
+# (n, cluster size, refresh period, values per thread FP64, FP32): odd n puts
+# the wrap n-1 -> 0 of the last CTA's region inside a thread's run
+VARIED_OBS_CASES = [(997, 2, 4, 4, 8), (997, 3, 1, 2, 4), (1001, 3, 4, 4, 4), (1001, 2, 2, 2, 8)]
+
+
+@pytest.mark.parametrize("n,cs,K,c64,c32", VARIED_OBS_CASES)
+def test_cluster_plans_with_varied_observation_sets(n, cs, K, c64, c32):
+    # cluster plans over an observation network that changes from step to
+    # step (dense, sparse, random subsets, t = 0 and t = N) with a ragged n:
+    # the right-hand side and the products with and without the identity
+    # against the oracle, stage states stored or recomputed, and FP32
+    spec = _varied_spec(n, seed=n + cs)
+    taps = O.bhalf_taps(spec.n, spec.length_scale, spec.sigma_b)
+    _, xb, y = O.twin(spec, S.draws(spec), taps)
+    traj, d, b = oracle_setup(spec, taps, xb, y)
+    cols = np.array([0, 3, 1, 2, 0], dtype=np.int32)
+    V = np.random.default_rng(n * cs).standard_normal((len(cols), spec.n))
+    ref = O.hvp(spec, traj[cols], V, taps)
+    refA = O.hvp(spec, traj[cols], V, taps, identity=False)
+    with env(EDA_SWEEP_CS64=cs, EDA_SWEEP_CS32=cs, EDA_SWEEP_K=K, EDA_SWEEP_C64=c64, EDA_SWEEP_C32=c32):
+        for store in (1, 0):
+            with env(EDA_STAGE_STORE=store):
+                with make(spec, taps) as h:
+                    assert h.eda_sweep_plan(True)["kind"] == "cluster"
+                    rhs = np.zeros_like(b)
+                    h.eda_set_trajectory(xb, y, rhs)
+                    assert rowrel(rhs, b).max() < 1e-11, store
+                    HV = np.zeros_like(V)
+                    h.eda_hvp(cols, V, HV, True)
+                    assert rowrel(HV, ref).max() < 1e-11, store
+                    h.eda_hvp(cols, V, HV, False)
+                    assert rowrel(HV, refA).max() < 1e-10, store
+        with make(spec, taps, precision=P.EDA_MIXED) as h:
+            assert h.eda_sweep_plan(False)["kind"] == "cluster"
+            h.eda_set_trajectory(xb, y)
+            HV = np.zeros_like(V)
+            h.eda_hvp(cols, V, HV, True)
+            assert rowrel(HV, ref).max() < 1e-4
+            h.eda_hvp(cols, V, HV, False)
+            assert rowrel(HV, refA).max() < 1e-4
+
+
 # (n, cluster size, refresh period, values per lane FP64, FP32, observation network)
 WARP_CASES = [(1000, 2, 8, 4, 8, "regular"), (1000, 3, 4, 2, 4, "regular"),
               (997, 3, 8, 4, 4, "subset"), (2048, 5, 4, 2, 8, "subset")]
