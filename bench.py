@@ -33,6 +33,7 @@ for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
 import numpy as np
+from dataclasses import replace
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -437,6 +438,108 @@ def forms_uneven(P, dev, count=256, maxit=3000):
             "true_relres_max_converged": float(rr[st == 0].max()) if conv else None}
 
 
+def forms_sketch_study(P, dev, seeds=20, iters=(1, 2, 3, 5, 10, 20, 30)):
+    """The paper's experiment at its own size (Section 4: n=1500, 10-step
+    window, 50 variables observed at 3 steps, 20 members, ell=20) on the GPU
+    path: Algorithm 1 on the control member's Hessian with the five sketch
+    matrices Omega = Psi, A Psi (q=2), B Psi, U_B^T Psi and Gamma, each over
+    `seeds` realisations (Gaussian Psi; ensemble perturbations for Gamma, the
+    control member fixed).  Reports the median relative eigenvalue error
+    |lambda* - lambda| / lambda* of lambda_i(I + A) against the eigenvalues of
+    the dense operator (assembled from n products), the median quadratic-cost
+    reduction (J(dz_i) - J*) / (J(0) - J*) of the control member after i PCG
+    iterations with each LMP (theta = (lambda_k + 1)/2, k = 20), the same for
+    Omega = Gamma with theta in {lambda_k, (lambda_k + 1)/2, 1} and k in {15,
+    20}, and the GPU time of sketch + LMP per variant."""
+    import torch
+    spec0 = S.spec_paper()
+    n, M, ell = spec0.n, spec0.n_members, spec0.ell
+    taps = P.bhalf_gaussian(n, spec0.length_scale, spec0.sigma_b)
+
+    def twin(h, dr):
+        xb = torch.empty(M, n, dtype=torch.float64, device=dev)
+        y = torch.empty(M, spec0.p, dtype=torch.float64, device=dev)
+        h.eda_twin(torch.tensor(spec0.F + spec0.spin_sigma * dr.eta_spin, device=dev), spec0.spinup,
+                   torch.tensor(dr.eta_b, device=dev), torch.tensor(dr.eta_o, device=dev), xb, y)
+        return xb, y
+
+    configs = {"k20_mid": (20, S.THETA_MID), "k20_lamk": (20, S.THETA_LAMBDA_K), "k20_one": (20, S.THETA_GIVEN),
+               "k15_mid": (15, S.THETA_MID), "k15_lamk": (15, S.THETA_LAMBDA_K), "k15_one": (15, S.THETA_GIVEN)}
+    hs = {name: P.Handle.from_spec(replace(spec0, k=k, theta_mode=tm, theta=1.0), taps, precision=P.EDA_FP64)
+          for name, (k, tm) in configs.items()}
+    h = hs["k20_mid"]
+    # the control member's operator I + A, assembled from n products
+    xb, y = twin(h, S.ensemble_draws(spec0, 0, 0))
+    rhs = torch.empty(M, n, dtype=torch.float64, device=dev)
+    h.eda_set_trajectory(xb, y, rhs)
+    eye = torch.eye(n, dtype=torch.float64, device=dev)
+    Hd = torch.empty_like(eye)
+    h.eda_hvp(torch.zeros(n, dtype=torch.int32, device=dev), eye, Hd, True)
+    H = Hd.cpu().numpy()
+    H = 0.5 * (H + H.T)
+    lam_star = np.linalg.eigvalsh(H)[::-1][:ell]
+    b0 = rhs[0].cpu().numpy()
+    x_star = np.linalg.solve(H, b0)
+    J_star = -0.5 * float(b0 @ x_star)
+
+    def cost_reduction(hh, use_lmp):
+        dz = torch.empty(M, n, dtype=torch.float64, device=dev)
+        out = []
+        for i in iters:
+            hh.eda_solve_batch(0.0, i, None, use_lmp, dz)
+            z = dz[0].cpu().numpy()
+            J = 0.5 * float(z @ H @ z) - float(b0 @ z)
+            out.append((J - J_star) / (0.0 - J_star))
+        return out
+
+    variants = ("psi", "a_psi", "b_psi", "ubt_psi", "gamma")
+    err = {v: [] for v in variants}
+    red = {v: [] for v in variants}
+    ms = {v: [] for v in variants}
+    sens = {name: [] for name in configs}
+    red_none = []
+    for seed in range(seeds):
+        xb, y = twin(h, S.ensemble_draws(spec0, 0, 1000 + seed))
+        for hh in hs.values():
+            hh.eda_set_trajectory(xb, y)
+        psi = torch.tensor(S.gaussian_matrix(ell, n, 2000 + seed), device=dev)
+        ub = torch.empty_like(psi)
+        h.eda_bhalf_apply(psi, ub)
+        bpsi = torch.empty_like(psi)
+        h.eda_bhalf_apply(ub, bpsi)
+        phis = {"psi": (psi, 1), "a_psi": (psi, 2), "b_psi": (bpsi, 1), "ubt_psi": (ub, 1), "gamma": (None, 1)}
+        for v in variants:
+            phi, q = phis[v]
+            ev = np.zeros(spec0.k)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h.eda_sketch(phi, q)
+            h.eda_build_lmp(ev)
+            torch.cuda.synchronize()
+            ms[v].append(1e3 * (time.perf_counter() - t0))
+            err[v].append(np.abs(lam_star - ev) / lam_star)
+            red[v].append(cost_reduction(h, True))
+        for name, hh in hs.items():
+            hh.eda_sketch()
+            hh.eda_build_lmp()
+            sens[name].append(cost_reduction(hh, True))
+        red_none.append(cost_reduction(h, False))
+    for hh in hs.values():
+        hh.close()
+    pick = (0, 4, 9, 14, 19)
+    med = lambda a: np.median(np.asarray(a), axis=0)
+    return {
+        "workload": "%s, %d realisations" % (spec0.name, seeds),
+        "lambda_star_1_5_10_15_20": [float(lam_star[i]) for i in pick],
+        "median_rel_eig_error_modes_1_5_10_15_20": {v: [float(med(err[v])[i]) for i in pick] for v in variants},
+        "pcg_iters": list(iters),
+        "median_cost_reduction": dict({v: [float(x) for x in med(red[v])] for v in variants},
+                                      no_lmp=[float(x) for x in med(red_none)]),
+        "gamma_theta_k_cost_reduction": {name: [float(x) for x in med(sens[name])] for name in configs},
+        "ms_sketch_plus_lmp": {v: float(np.median(ms[v])) for v in variants},
+    }
+
+
 def forms_warm(P, dev, train_edas=80, test_edas=2, epochs=3, hidden=64):
     """Learned warm start (n=1024, 32-step window, 256 members): training
     triples (member RHS, control solution, member solution) from the plain
@@ -652,7 +755,7 @@ def run_ours(args):
     forms = None
     if rank == 0 and world == 1 and not args.no_forms:  # single-GPU measurements
         forms = {"tiny": forms_tiny(P, dev), "scale": forms_scale(P, dev, peak), "uneven": forms_uneven(P, dev),
-                 "warm_start": forms_warm(P, dev)}
+                 "warm_start": forms_warm(P, dev), "sketch_study": forms_sketch_study(P, dev)}
     if rank == 0:
         its_m = np.concatenate(its_mixed)
         its_d = np.concatenate(its64)

@@ -25,6 +25,11 @@ package is measured on):
                 trajectory checkpoints every 8 steps.
 * ``warm``    : n=1024, 32-step window, obs every 2nd variable every 2nd
                 step, length scale 4, 256 members + control.
+* ``paper``   : the size of the paper's own experiment (Section 4): n=1500,
+                10-step window, fifty variables (every 30th) observed at
+                three steps (4, 7, 10), sigma_o=0.05, sigma_b=0.8, length
+                scale 6 (the Daley length of its diffusion B), 20 members +
+                control, ell=k=20.
 """
 from __future__ import annotations
 
@@ -185,6 +190,29 @@ def gaussian_matrix(rows: int, cols: int, seed: int) -> np.ndarray:
     return np.random.default_rng([seed, rows, cols, 0x5EED]).standard_normal((rows, cols))
 
 
+def spec_paper(seed: int = 0, k: int = 20) -> Spec:
+    n, N = 1500, 10
+    steps = np.array([4, 7, 10], dtype=np.int32)
+    idx1 = np.arange(0, n, n // 50, dtype=np.int32)
+    ptr = (np.arange(len(steps) + 1) * len(idx1)).astype(np.int32)
+    return Spec(n=n, nsteps=N, obs_steps=steps, obs_ptr=ptr, obs_idx=np.tile(idx1, len(steps)),
+                sigma_o=0.05, sigma_b=0.8, length_scale=6.0, n_members=21, ell=20, k=k,
+                seed=seed, name="l96_n1500_w10_m21")
+
+
+def ensemble_draws(spec: Spec, control_seed: int, member_seed: int) -> Draws:
+    """Draws whose truth and control member come from ``control_seed`` and
+    whose perturbed members 1..L come from ``member_seed``: one twin
+    experiment (one control Hessian) under many ensemble realisations."""
+    base = draws(spec, control_seed)
+    mem = draws(spec, member_seed)
+    eta_b = mem.eta_b.copy()
+    eta_o = mem.eta_o.copy()
+    eta_b[0] = base.eta_b[0]
+    eta_o[0] = base.eta_o[0]
+    return Draws(eta_spin=base.eta_spin, eta_b=eta_b, eta_o=eta_o)
+
+
 def by_name(name: str, seed: int = 0) -> Spec:
     return {"tiny": spec_tiny, "batched": spec_batched, "scale": spec_scale,
-            "warm": spec_warm}[name](seed=seed)
+            "warm": spec_warm, "paper": spec_paper}[name](seed=seed)

@@ -229,6 +229,17 @@ EDA_API int eda_solve_batch(eda_handle* h, double tol, int maxit, const double* 
                             double* relres_out, int* status_out);
 
 /*
+ * Control-variable transform (Section 2.3, Eq. (system with CVT)): OUT[c] =
+ * U_B V[c] for c < ncol, U_B the handle's symmetric banded circulant square
+ * root of B (taps bhalf_coef).  Maps solutions dz_j of eda_solve_batch to
+ * analysis increments dx_j = U_B dz_j, and builds B-shaped sketch matrices
+ * (U_B Psi, B Psi = U_B U_B Psi).  V, OUT [ncol x n] FP64, host or device
+ * (caller-owned, not overlapping); a host OUT is complete on return.
+ * EDA_ERR_INVALID on ncol < 0 or a NULL buffer with ncol > 0.
+ */
+EDA_API int eda_bhalf_apply(eda_handle* h, int ncol, const double* V, double* OUT);
+
+/*
  * Batched Hessian-vector products (Section 2.3, Eq. (system with CVT)):
  * HV[c] = (include_identity ? V[c] : 0) + A_{m(c)} V[c] for c < ncol, with
  * m(c) = member_of_col[c] in [0, L] choosing the trajectory (the

@@ -36,7 +36,7 @@ EXPORTS = ["eda_version", "eda_last_error", "eda_create", "eda_destroy", "eda_tw
            "eda_ws_create", "eda_ws_destroy", "eda_ws_last_error", "eda_ws_num_params", "eda_ws_set_params",
            "eda_ws_get_params", "eda_ws_set_scales", "eda_ws_get_scales", "eda_ws_loss_grad", "eda_ws_train",
            "eda_ws_infer", "eda_hvp_noalloc", "eda_hvp_noalloc_capacity", "eda_lmp_info",
-           "eda_trace", "eda_trace_read", "eda_ws_init", "eda_sweep_plan"]
+           "eda_trace", "eda_trace_read", "eda_ws_init", "eda_sweep_plan", "eda_bhalf_apply"]
 
 
 class EdaError(RuntimeError):
@@ -101,6 +101,8 @@ def lib() -> ctypes.CDLL:
     L.eda_lmp_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(d)]
     L.eda_sweep_plan.restype = i
     L.eda_sweep_plan.argtypes = [vp, i, ctypes.POINTER(i)]
+    L.eda_bhalf_apply.restype = i
+    L.eda_bhalf_apply.argtypes = [vp, i, vp, vp]
     L.eda_solve_batch.restype = i
     L.eda_solve_batch.argtypes = [vp, d, i, vp, i, vp, vp, vp, vp]
     L.eda_hvp.restype = i
@@ -365,6 +367,12 @@ class Handle:
         ms = ctypes.c_double(0.0)
         self._check(self._L.eda_time_hvp_sweep(self._h, int(reps), 1 if fp64 else 0, ctypes.byref(ms)))
         return ms.value
+
+    def eda_bhalf_apply(self, V, OUT):
+        """OUT[c] = U_B V[c] (control-variable transform) for every row of V."""
+        ncol = int(V.shape[0])
+        self._check(self._L.eda_bhalf_apply(self._h, ncol, _ptr(V, np.float64, ncol * self.n, "V"),
+                                            _ptr(OUT, np.float64, ncol * self.n, "OUT")))
 
     def eda_hvp(self, member_of_col, V, HV, include_identity=True):
         ncol = int(np.asarray(member_of_col.shape[0] if hasattr(member_of_col, "shape") else len(member_of_col)))

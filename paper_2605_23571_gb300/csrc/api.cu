@@ -1103,6 +1103,24 @@ EDA_API int eda_hvp(eda_handle* h, const int* member_of_col, int ncol, const dou
   return EDA_OK;
 }
 
+EDA_API int eda_bhalf_apply(eda_handle* h, int ncol, const double* V, double* OUT) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (ncol < 0 || (ncol > 0 && (!V || !OUT))) return fail(h, EDA_ERR_INVALID, "eda_bhalf_apply: invalid argument");
+  if (ncol == 0) return EDA_OK;
+  const int n = h->n;
+  In iv;
+  CU(h, iv.init(V, (size_t)ncol * n * sizeof(double), h->st));
+  Out o;
+  CU(h, o.init(OUT, (size_t)ncol * n * sizeof(double), h->st));
+  eda::count_launch();
+  bhalf_apply_kernel<<<grid_for((long long)ncol * n), 256, 0, h->st>>>(n, h->w, h->bcoef, ncol, (const double*)iv.dev,
+                                                                     (double*)o.dev);
+  CU(h, cudaGetLastError());
+  CU(h, o.finish());
+  if (o.host) CU(h, cudaStreamSynchronize(h->st));
+  return EDA_OK;
+}
+
 EDA_API int eda_sketch(eda_handle* h, const double* phi, int q, double* y_out) {
   if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
   if (!h->have_traj) return fail(h, EDA_ERR_STATE, "eda_sketch before eda_set_trajectory");

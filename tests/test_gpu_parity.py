@@ -701,3 +701,72 @@ def test_control_only_problem_without_lmp(precision):
         h.eda_solve_batch(1e-9, 2000, None, False, dz, None, rr, st)
     assert st[0] == P.EDA_CONVERGED and rr[0] <= 1e-9
     assert np.linalg.norm(dz - exact) <= rr[0] * np.linalg.norm(b) * (1 + 1e-6) + 1e-12
+
+
+def test_bhalf_apply_matches_the_circulant():
+    # the control-variable transform dx = U_B dz (host and device buffers,
+    # empty batch) against the oracle's banded circulant
+    import torch
+    spec = S.spec_small(300, 8, 5, every_var=2, every_step=2, length_scale=8.0, seed=21)
+    taps = O.bhalf_taps(spec.n, spec.length_scale, spec.sigma_b)
+    V = np.random.default_rng(21).standard_normal((7, spec.n))
+    ref = O.bhalf_apply(V, taps)
+    with make(spec, taps) as h:
+        out = np.zeros_like(V)
+        h.eda_bhalf_apply(V, out)
+        assert rel(out, ref) < 1e-14
+        Vd = torch.tensor(V, device="cuda")
+        Od = torch.zeros_like(Vd)
+        h.eda_bhalf_apply(Vd, Od)
+        assert rel(Od.cpu().numpy(), ref) < 1e-14
+        h.eda_bhalf_apply(V[:0], out[:0])
+
+
+def _ctrl_apply(spec, traj, taps):
+    ctrl = traj[0:1]
+
+    def apply_ctrl(block):
+        tr = np.broadcast_to(ctrl, (block.shape[1],) + ctrl.shape[1:])
+        return O.apply_A(spec, tr, block.T.copy(), taps).T
+    return apply_ctrl
+
+
+@pytest.mark.parametrize("q", [1, 2])
+@pytest.mark.parametrize("kind", ["psi", "ub_psi", "b_psi"])
+def test_sketch_of_a_given_matrix_with_power_passes(kind, q):
+    # Algorithm 1 on a caller's sketch matrix: a Gaussian Psi, U_B Psi or
+    # B Psi (formed by eda_bhalf_apply on the GPU side, by the oracle's
+    # circulant on the other), with q - 1 power passes.  Eigenvalues within
+    # the oracle's own sensitivity to a 1e-15 perturbation of Phi; for q = 1
+    # also Y = A Phi itself
+    spec = S.spec_small(300, 16, 21, every_var=2, every_step=2, length_scale=8.0, seed=7)
+    spec = replace(spec, k=15)
+    taps, xb, y = problem(spec)
+    traj, d, b = oracle_setup(spec, taps, xb, y)
+    apply_ctrl = _ctrl_apply(spec, traj, taps)
+    rng = np.random.default_rng(100 + q)
+    psi = rng.standard_normal((spec.ell, spec.n))  # rows = columns of Psi
+    phi_o = psi.copy()
+    for _ in range({"psi": 0, "ub_psi": 1, "b_psi": 2}[kind]):
+        phi_o = O.bhalf_apply(phi_o, taps)
+    _, D, info = O.nystrom(apply_ctrl, phi_o.T, spec.k, q=q)
+    _, Dp, _ = O.nystrom(apply_ctrl, phi_o.T * (1 + 1e-15 * rng.standard_normal(phi_o.T.shape)), spec.k, q=q)
+    sens = np.abs(Dp - D) / np.maximum(D, 1e-300)
+    with make(spec, taps) as h:
+        h.eda_set_trajectory(xb, y)
+        phi_g = psi.copy()
+        for _ in range({"psi": 0, "ub_psi": 1, "b_psi": 2}[kind]):
+            tmp = np.zeros_like(phi_g)
+            h.eda_bhalf_apply(phi_g, tmp)
+            phi_g = tmp
+        assert rel(phi_g, phi_o) < 1e-13
+        Yg = np.zeros((spec.ell, spec.n))
+        h.eda_sketch(phi_g, q, Yg)
+        if q == 1:
+            assert rel(Yg, info["Y"].T) < 1e-11
+        ev = np.zeros(spec.k)
+        h.eda_build_lmp(ev)
+        path, rank, _ = h.eda_lmp_info()
+        top = D > 1e-10 * D[0]  # modes above the sketch's rounding floor
+        err = np.abs(ev - 1 - D) / (1 + D)
+        assert (err[top] <= np.maximum(1e-9, 100 * sens[top])).all(), (kind, q, path, err.max())
