@@ -287,6 +287,11 @@ def run_reference(args):
 # recomputation (60), counting each multiply and add (Lorenz-96 stencils of
 # the oracle's tl_step / adj_step)
 FLOPS_PER_ELEMENT_STEP = 117
+# the same for the FP64 sweep that reads the stored RK4 stage states: the
+# tangent-linear step (37) and the adjoint step (42) without recomputation
+FLOPS_PER_ELEMENT_STEP_STORED = 79
+# GB300 FP64 rate (nominal; no FP64 peak is measured on this part)
+FP64_PEAK_TFLOPS = 1.25
 
 
 def fp32_peak_tflops(sm_mhz):
@@ -713,6 +718,14 @@ def run_ours(args):
     ms64 = h64.eda_time_hvp_sweep(reps=3)
     hvps32 = M / (ms32 / 1e3)
     hvps64 = M / (ms64 / 1e3)
+    # FP64 sweep against the FP64 rate: the cluster tiling reads the stored
+    # stage states, the warp-tiled one recomputes them
+    plan64 = h64.eda_sweep_plan(fp64=True)
+    f64 = FLOPS_PER_ELEMENT_STEP if plan64["kind"] == "warp" else FLOPS_PER_ELEMENT_STEP_STORED
+    fp64_alu = {"achieved": f64 * M * n * spec.nsteps / (ms64 / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "flops_per_element_step": f64, "kernel": sweep_kernel_name(plan64, "double"),
+                "peak_kind": "nominal GB300 FP64 rate (not measured)"}
+    fp64_alu["frac"] = fp64_alu["achieved"] / FP64_PEAK_TFLOPS
     # roofline of the FP32 sweep from the timed steps: algorithmic bytes per
     # member-column HVP s*n*(2N+2) (trajectory forward and backward, vector
     # in and out), times the columns each traced launch computed, over the
@@ -769,7 +782,8 @@ def run_ours(args):
                           "speedup_mixed_over_fp64": value / world / value64,
                           "iters_median": float(np.median(its_d))},
             "hv_per_s": {"mixed_fp32_sweep": hvps32, "fp64_sweep": hvps64,
-                         "ms_per_batched_launch_fp32": ms32, "ms_per_batched_launch_fp64": ms64},
+                         "ms_per_batched_launch_fp32": ms32, "ms_per_batched_launch_fp64": ms64,
+                         "fp64_sweep_alu": fp64_alu},
             "solve": {"iters_min": int(its_m.min()), "iters_median": float(np.median(its_m)),
                       "iters_max": int(its_m.max()), "all_converged": bool((st_mixed == 0).all()),
                       "true_relres_max": float(rr_mixed.max()),

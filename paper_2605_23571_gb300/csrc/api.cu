@@ -884,11 +884,8 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
   CUC(dalloc(h, &h->acc, M));
   CUC(dalloc(h, &h->Wk, (size_t)M * std::max(kk, 1)));
   {
-    std::vector<eda::PcgTask> tasks;
-    eda::pcg_tasks(&n, 1, &tasks);
-    h->ntasks = (int)tasks.size();
-    CUC(dalloc(h, &h->tasks, tasks.size()));
-    CUC(cudaMemcpy(h->tasks, tasks.data(), tasks.size() * sizeof(eda::PcgTask), cudaMemcpyHostToDevice));
+    // the handle's solve is one problem: its row chunks and problem go to
+    // the PCG kernels by value (no task tables)
     eda::PcgProb pr{};
     pr.n = n;
     pr.M = M;
@@ -897,8 +894,7 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
     pr.off0 = 0;
     pr.S = (h->precision == EDA_MIXED) ? (const void*)h->S32 : (const void*)h->S;
     pr.c = h->cv;
-    CUC(dalloc(h, &h->probs, 1));
-    CUC(cudaMemcpy(h->probs, &pr, sizeof(pr), cudaMemcpyHostToDevice));
+    h->pgrid = eda::pcg_single(pr);
   }
   CUC(dalloc(h, &h->cols, mcols));
   CUC(dalloc(h, &h->zeros, mcols));
@@ -1339,9 +1335,9 @@ int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int*
   TS* Wk = reinterpret_cast<TS*>(h->Wk);
   // start: z = P r, p = z, r.z
   CU(h, eda::pcg2_reset(h->acc, M, Wk, (size_t)M * kmax * sizeof(TS), h->st));
-  CU(h, eda::pcg2_update<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->pv, h->q, h->x, h->r, h->sc, h->acc, h->active,
+  CU(h, eda::pcg2_update<TS>(h->pgrid, kmax, M, h->pv, h->q, h->x, h->r, h->sc, h->acc, h->active,
                              Wk, 0, 0, lmp, h->nactive, h->st));
-  CU(h, eda::pcg2_precond<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->r, h->z, h->pv, h->sc, h->acc, h->active, Wk,
+  CU(h, eda::pcg2_precond<TS>(h->pgrid, kmax, M, h->r, h->z, h->pv, h->sc, h->acc, h->active, Wk,
                               0, tol, maxit, fixed, lmp, 1, h->nactive, h->st));
   // the first update accumulates the projections of r_1 from zero
   CU(h, cudaMemsetAsync(Wk, 0, (size_t)M * kmax * sizeof(TS), h->st));
@@ -1354,7 +1350,7 @@ int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int*
     ++it;
     int rc = hvp_dev(h, h->cols, M, h->pv, h->q, 1, sweep64, h->active, reinterpret_cast<double*>(h->acc));
     if (rc) return rc;
-    CU(h, eda::pcg2_update<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->pv, h->q, h->x, h->r, h->sc, h->acc,
+    CU(h, eda::pcg2_update<TS>(h->pgrid, kmax, M, h->pv, h->q, h->x, h->r, h->sc, h->acc,
                                h->active, Wk, par, 1, lmp, h->nactive, h->st));
     if (replace_every > 0 && (it - it0) % replace_every == 0) {
       // residual replacement: the recurrence residual gives way to the FP64
@@ -1362,15 +1358,15 @@ int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int*
       // on with the same direction
       rc = hvp_dev(h, h->cols, M, h->x, h->q, 1, true, h->active);
       if (rc) return rc;
-      CU(h, eda::pcg2_replace(h->tasks, h->ntasks, h->probs, M, h->b, h->q, h->r, h->acc, M, h->active, h->st));
+      CU(h, eda::pcg2_replace(h->pgrid, M, h->b, h->q, h->r, h->acc, M, h->active, h->st));
       CU(h, cudaMemsetAsync(Wk, 0, (size_t)M * kmax * sizeof(TS), h->st));
-      CU(h, eda::pcg2_update<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->pv, h->q, h->x, h->r, h->sc, h->acc,
+      CU(h, eda::pcg2_update<TS>(h->pgrid, kmax, M, h->pv, h->q, h->x, h->r, h->sc, h->acc,
                                  h->active, Wk, par, 0, lmp, h->nactive, h->st));
     }
-    CU(h, eda::pcg2_precond<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->r, h->z, h->pv, h->sc, h->acc, h->active,
+    CU(h, eda::pcg2_precond<TS>(h->pgrid, kmax, M, h->r, h->z, h->pv, h->sc, h->acc, h->active,
                                 Wk, par, tol, maxit, fixed, lmp, 0, h->nactive, h->st));
     const int slot = it % R;
-    CU(h, eda::pcg2_dir<TS>(h->tasks, h->ntasks, h->probs, kmax, M, h->z, h->pv, h->sc, h->acc, h->active, Wk, par,
+    CU(h, eda::pcg2_dir<TS>(h->pgrid, kmax, M, h->z, h->pv, h->sc, h->acc, h->active, Wk, par,
                             h->st, h->nactive, h->hring + slot));
     CU(h, cudaEventRecord(h->ring_ev[slot], h->st));
     if (it - it0 >= R) {

@@ -65,6 +65,7 @@ struct eda_group {
   eda::PcgTask* tasks = nullptr;  // row chunks of every problem
   int ntasks = 0;
   eda::PcgProb* probs = nullptr;  // per problem: sizes, items, S (of the group's precision), c
+  eda::PcgGrid pgrid{};           // the two tables above as the PCG kernels' grid
   int* active = nullptr;
   int* nactive = nullptr;
   int* dflag = nullptr;
@@ -406,11 +407,11 @@ int group_iteration(eda_group* g, bool sweep64, bool use_lmp, double tol, int ma
   TS* Wk = reinterpret_cast<TS*>(g->Wk);
   int rc = group_sweep(g, sweep64, g->p, g->q, 1, false, reinterpret_cast<double*>(g->acc));
   if (rc) return rc;
-  GCU(g, eda::pcg2_update<TS>(g->tasks, g->ntasks, g->probs, kmax, g->mmax, g->p, g->q, g->x, g->r, g->sc, g->acc, g->active,
+  GCU(g, eda::pcg2_update<TS>(g->pgrid, kmax, g->mmax, g->p, g->q, g->x, g->r, g->sc, g->acc, g->active,
                               Wk, par, 1, lmp, g->nactive, g->st));
-  GCU(g, eda::pcg2_precond<TS>(g->tasks, g->ntasks, g->probs, kmax, g->mmax, g->r, g->z, g->p, g->sc, g->acc, g->active, Wk,
+  GCU(g, eda::pcg2_precond<TS>(g->pgrid, kmax, g->mmax, g->r, g->z, g->p, g->sc, g->acc, g->active, Wk,
                                par, tol, maxit, fixed, lmp, 0, g->nactive, g->st));
-  GCU(g, eda::pcg2_dir<TS>(g->tasks, g->ntasks, g->probs, kmax, g->mmax, g->z, g->p, g->sc, g->acc, g->active, Wk, par,
+  GCU(g, eda::pcg2_dir<TS>(g->pgrid, kmax, g->mmax, g->z, g->p, g->sc, g->acc, g->active, Wk, par,
                            g->st));
   return EDA_OK;
 }
@@ -422,9 +423,9 @@ int group_start(eda_group* g, bool use_lmp, double tol, int maxit, int fixed) {
   const int lmp = use_lmp ? 1 : 0;
   TS* Wk = reinterpret_cast<TS*>(g->Wk);
   GCU(g, eda::pcg2_reset(g->acc, g->T, Wk, (size_t)g->T * kmax * sizeof(TS), g->st));
-  GCU(g, eda::pcg2_update<TS>(g->tasks, g->ntasks, g->probs, kmax, g->mmax, g->p, g->q, g->x, g->r, g->sc, g->acc, g->active,
+  GCU(g, eda::pcg2_update<TS>(g->pgrid, kmax, g->mmax, g->p, g->q, g->x, g->r, g->sc, g->acc, g->active,
                               Wk, 0, 0, lmp, g->nactive, g->st));
-  GCU(g, eda::pcg2_precond<TS>(g->tasks, g->ntasks, g->probs, kmax, g->mmax, g->r, g->z, g->p, g->sc, g->acc, g->active, Wk,
+  GCU(g, eda::pcg2_precond<TS>(g->pgrid, kmax, g->mmax, g->r, g->z, g->p, g->sc, g->acc, g->active, Wk,
                                0, tol, maxit, fixed, lmp, 1, g->nactive, g->st));
   // the first update accumulates the projections of r_1 from zero
   GCU(g, cudaMemsetAsync(Wk, 0, (size_t)g->T * kmax * sizeof(TS), g->st));
@@ -605,6 +606,7 @@ EDA_API int eda_group_create(eda_handle* const* handles, int count, eda_group** 
     if (!e) e = galloc(g, &g->tasks, tasks.size());
     if (!e) e = cudaMemcpy(g->tasks, tasks.data(), tasks.size() * sizeof(eda::PcgTask), cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(g->probs, pr.data(), pr.size() * sizeof(eda::PcgProb), cudaMemcpyHostToDevice);
+    g->pgrid = eda::pcg_tables(g->tasks, g->ntasks, g->probs);
   }
   if (!e) e = cudaMallocHost((void**)&g->hring, 4 * sizeof(int));
   for (int i = 0; i < 4 && !e; ++i) e = cudaEventCreateWithFlags(&g->ev[i], cudaEventDisableTiming);

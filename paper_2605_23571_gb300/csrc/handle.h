@@ -67,9 +67,7 @@ struct eda_handle {
   PcgScalars* sc = nullptr;
   eda::PcgAcc* acc = nullptr;      // per-member accumulators of an iteration
   double* Wk = nullptr;            // M x max(k,1) LMP projections (FP64, or FP32 in the mixed solve)
-  eda::PcgTask* tasks = nullptr;   // row chunks of the state
-  int ntasks = 0;
-  eda::PcgProb* probs = nullptr;   // the handle as a one-problem batch
+  eda::PcgGrid pgrid{};            // the handle as a one-problem batch (by value)
   int* active = nullptr;
   int* nactive = nullptr;
   int* cols = nullptr;  // identity member map 0..max(M, ell)-1

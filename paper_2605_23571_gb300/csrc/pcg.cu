@@ -16,6 +16,18 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// The row chunk and problem of this CTA.
+__device__ __forceinline__ void grid_task(const PcgGrid& G, PcgTask* tk, PcgProb* P) {
+  if (G.single) {
+    *P = G.one;
+    const int r0 = (int)blockIdx.x * kPcgRows;
+    *tk = PcgTask{0, r0, min(kPcgRows, G.one.n - r0), blockIdx.x == 0 ? 1 : 0};
+  } else {
+    *tk = G.tasks[blockIdx.x];
+    *P = G.probs[tk->prob];
+  }
+}
+
 // 16-byte vectors of the LMP arithmetic type: VW values per load.
 template <typename TS>
 struct Vec16;
@@ -84,7 +96,7 @@ constexpr int kCwPerLane = 3;
 static_assert(32 * kCwPerLane >= 84 && 32 * kCwPerLane >= 82, "padded k of 80 LMP modes fits");
 
 template <typename TS>
-__global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* tasks, const PcgProb* probs, int kmax,
+__global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgGrid G, int kmax,
                                                                const double* p, const double* q, double* x,
                                                                double* r, PcgScalars* sc, PcgAcc* acc, int* active,
                                                                TS* Wk, int par, int update, int use_lmp,
@@ -94,8 +106,9 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* ta
   constexpr int VW = Vec16<TS>::VW;
   constexpr int R = kRowsPerLane;
   const int RBP = vec_stride<TS>(kPcgRows);  // S chunk [c][RBP]: lane c reads column c
-  const PcgTask tk = tasks[blockIdx.x];
-  const PcgProb P = probs[tk.prob];
+  PcgTask tk;
+  PcgProb P;
+  grid_task(G, &tk, &P);
   const int k = use_lmp ? P.k : 0;
   const int rows_v = ((tk.rows + VW - 1) / VW) * VW;  // rows padded to whole vectors
   TS* Ssm = reinterpret_cast<TS*>(smraw);
@@ -104,11 +117,14 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* ta
   // this warp's member (one member per warp) and its rows, loaded first
   const int m = blockIdx.y * kWarps + wid;
   const int item = P.item0 + m;
-  const bool live = m < P.M && active[item] != 0;
+  // the loads do not wait for the member's active flag (their addresses are
+  // valid for every member of the problem); inactive members drop them
+  const bool mine = m < P.M;
+  const bool live = mine && active[item] != 0;
   const long long off = P.off0 + (long long)m * P.n + tk.row0;
   double pv[R], qv[R], xv[R], rv[R];
   double pq = 0.0, rzp = 0.0;
-  if (live) {
+  if (mine) {
     if (update) {
       pq = acc[item].pq;
       rzp = acc[item].rz[par];
@@ -186,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgTask* ta
 }
 
 template <typename TS>
-__global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* tasks, const PcgProb* probs, int kmax,
+__global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgGrid G, int kmax,
                                                                 const double* r, double* z, double* p,
                                                                 PcgScalars* sc, PcgAcc* acc, int* active,
                                                                 const TS* Wk, int par, double tol, int maxit,
@@ -195,8 +211,9 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
   using V = typename Vec16<TS>::type;
   constexpr int VW = Vec16<TS>::VW;
   constexpr int R = kRowsPerLane;
-  const PcgTask tk = tasks[blockIdx.x];
-  const PcgProb P = probs[tk.prob];
+  PcgTask tk;
+  PcgProb P;
+  grid_task(G, &tk, &P);
   const int k = use_lmp ? P.k : 0;
   const int KP = vec_stride<TS>(k);               // row stride, zero beyond k
   const int KW = vec_stride<TS>(kmax > 0 ? kmax : 1);
@@ -207,7 +224,8 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
   // scaled projections, loaded before the CTA stages S
   const int m = blockIdx.y * kWarps + wid;
   const int item = P.item0 + m;
-  const bool live = m < P.M && active[item] != 0;
+  const bool mine = m < P.M;  // loads as in the update launch
+  const bool live = mine && active[item] != 0;
   const long long off = P.off0 + (long long)m * P.n + tk.row0;
   double rv[R];
   double bn = 0.0, rrv = 0.0, tolm = 0.0;
@@ -215,7 +233,7 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
   TS cw[kCwPerLane];  // c_c w_c for c = lane + 32 j
 #pragma unroll
   for (int j = 0; j < kCwPerLane; ++j) cw[j] = TS(0);
-  if (live) {
+  if (mine) {
     if (!init) {
       bn = sc[item].bnorm;
       rrv = acc[item].rr;
@@ -309,12 +327,13 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgTask* t
 }
 
 template <typename TS>
-__global__ void __launch_bounds__(kThreads) pcg2_dir_kernel(const PcgTask* tasks, const PcgProb* probs, int kmax,
+__global__ void __launch_bounds__(kThreads) pcg2_dir_kernel(const PcgGrid G, int kmax,
                                                             const double* z, double* p, PcgScalars* sc, PcgAcc* acc,
                                                             const int* active, TS* Wk, int par,
                                                             const int* nactive, int* host_count) {
-  const PcgTask tk = tasks[blockIdx.x];
-  const PcgProb P = probs[tk.prob];
+  PcgTask tk;
+  PcgProb P;
+  grid_task(G, &tk, &P);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   // the active count is final here (update and precond change it): one
   // thread copies it to the host's ring slot (mapped pinned memory)
@@ -338,19 +357,35 @@ __global__ void __launch_bounds__(kThreads) pcg2_dir_kernel(const PcgTask* tasks
     const int m = blockIdx.y * kWarps + wid;  // one member per warp
     if (m >= P.M) return;
     const int item = P.item0 + m;
-    if (!active[item]) return;
-    const double beta = acc[item].rz[par ^ 1] / acc[item].rz[par];
+    // every load in flight before the active flag is tested
+    constexpr int R = kRowsPerLane;
     const long long off = P.off0 + (long long)m * P.n + tk.row0;
-    for (int i = lane; i < tk.rows; i += 32) p[off + i] = z[off + i] + beta * p[off + i];
+    double zv[R], pv[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int i = lane + 32 * j;
+      if (i < tk.rows) {
+        zv[j] = z[off + i];
+        pv[j] = p[off + i];
+      }
+    }
+    const double rzn = acc[item].rz[par ^ 1], rzo = acc[item].rz[par];
+    if (!active[item]) return;
+    const double beta = rzn / rzo;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int i = lane + 32 * j;
+      if (i < tk.rows) p[off + i] = zv[j] + beta * pv[j];
+    }
   }
 }
 
 // r = b - hx and ||r||^2 for the active members (hx = (I + A) x).
-__global__ void __launch_bounds__(kThreads) pcg2_replace_kernel(const PcgTask* tasks, const PcgProb* probs,
-                                                                const double* b, const double* hx, double* r,
+__global__ void __launch_bounds__(kThreads) pcg2_replace_kernel(const PcgGrid G, const double* b, const double* hx, double* r,
                                                                 PcgAcc* acc, const int* active) {
-  const PcgTask tk = tasks[blockIdx.x];
-  const PcgProb P = probs[tk.prob];
+  PcgTask tk;
+  PcgProb P;
+  grid_task(G, &tk, &P);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int m = blockIdx.y * kWarps + wid;
   if (m >= P.M) return;
@@ -401,6 +436,22 @@ cudaError_t set_smem(K kern, size_t smem) {
 
 }  // namespace
 
+PcgGrid pcg_single(const PcgProb& prob) {
+  PcgGrid g{};
+  g.single = 1;
+  g.one = prob;
+  g.ntasks = (prob.n + kPcgRows - 1) / kPcgRows;
+  return g;
+}
+
+PcgGrid pcg_tables(const PcgTask* tasks, int ntasks, const PcgProb* probs) {
+  PcgGrid g{};
+  g.tasks = tasks;
+  g.probs = probs;
+  g.ntasks = ntasks;
+  return g;
+}
+
 void pcg_tasks(const int* n_of, int nprob, std::vector<PcgTask>* out) {
   out->clear();
   for (int pi = 0; pi < nprob; ++pi)
@@ -420,55 +471,55 @@ cudaError_t pcg2_reset(PcgAcc* acc, int T, void* Wk, size_t wk_bytes, cudaStream
 }
 
 template <typename TS>
-cudaError_t pcg2_update(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* p,
+cudaError_t pcg2_update(const PcgGrid& G, int kmax, int mmax, const double* p,
                         const double* q, double* x, double* r, PcgScalars* sc, PcgAcc* acc, int* active, TS* Wk,
                         int par, int update, int use_lmp, int* nactive, cudaStream_t s) {
-  if (ntasks <= 0 || mmax <= 0) return cudaSuccess;
+  if (G.ntasks <= 0 || mmax <= 0) return cudaSuccess;
   const size_t smem = ((size_t)kmax * vec_stride<TS>(kPcgRows) + (size_t)kWarps * kPcgRows) * sizeof(TS);
   cudaError_t e = set_smem(pcg2_update_kernel<TS>, smem);
   if (e != cudaSuccess) return e;
   count_launch();
-  pcg2_update_kernel<TS><<<dim3(ntasks, (mmax + kWarps - 1) / kWarps), kThreads, smem, s>>>(tasks, probs, kmax, p, q, x, r, sc, acc, active, Wk, par,
+  pcg2_update_kernel<TS><<<dim3(G.ntasks, (mmax + kWarps - 1) / kWarps), kThreads, smem, s>>>(G, kmax, p, q, x, r, sc, acc, active, Wk, par,
                                                         update, use_lmp, nactive);
   return cudaGetLastError();
 }
 
 template <typename TS>
-cudaError_t pcg2_precond(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* r,
+cudaError_t pcg2_precond(const PcgGrid& G, int kmax, int mmax, const double* r,
                          double* z, double* p, PcgScalars* sc, PcgAcc* acc, int* active, const TS* Wk, int par,
                          double tol, int maxit, int fixed, int use_lmp, int init, int* nactive, cudaStream_t s) {
-  if (ntasks <= 0 || mmax <= 0) return cudaSuccess;
+  if (G.ntasks <= 0 || mmax <= 0) return cudaSuccess;
   if (vec_stride<TS>(kmax) > 32 * kCwPerLane) return cudaErrorInvalidValue;  // more than 80 LMP modes
   const int KW = vec_stride<TS>(kmax > 0 ? kmax : 1);
   const size_t smem = ((size_t)kPcgRows * KW + (size_t)kWarps * KW) * sizeof(TS);
   cudaError_t e = set_smem(pcg2_precond_kernel<TS>, smem);
   if (e != cudaSuccess) return e;
   count_launch();
-  pcg2_precond_kernel<TS><<<dim3(ntasks, (mmax + kWarps - 1) / kWarps), kThreads, smem, s>>>(tasks, probs, kmax, r, z, p, sc, acc, active, Wk, par, tol,
+  pcg2_precond_kernel<TS><<<dim3(G.ntasks, (mmax + kWarps - 1) / kWarps), kThreads, smem, s>>>(G, kmax, r, z, p, sc, acc, active, Wk, par, tol,
                                                          maxit, fixed, use_lmp, init, nactive);
   return cudaGetLastError();
 }
 
 template <typename TS>
-cudaError_t pcg2_dir(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* z, double* p,
+cudaError_t pcg2_dir(const PcgGrid& G, int kmax, int mmax, const double* z, double* p,
                      PcgScalars* sc, PcgAcc* acc, const int* active, TS* Wk, int par, cudaStream_t s,
                      const int* nactive, int* host_count) {
-  if (ntasks <= 0 || mmax <= 0) return cudaSuccess;
+  if (G.ntasks <= 0 || mmax <= 0) return cudaSuccess;
   count_launch();
-  pcg2_dir_kernel<TS><<<dim3(ntasks, (mmax + kWarps - 1) / kWarps), kThreads, 0, s>>>(tasks, probs, kmax, z, p, sc, acc,
+  pcg2_dir_kernel<TS><<<dim3(G.ntasks, (mmax + kWarps - 1) / kWarps), kThreads, 0, s>>>(G, kmax, z, p, sc, acc,
                                                                                      active, Wk, par, nactive,
                                                                                      host_count);
   return cudaGetLastError();
 }
 
-cudaError_t pcg2_replace(const PcgTask* tasks, int ntasks, const PcgProb* probs, int mmax, const double* b,
+cudaError_t pcg2_replace(const PcgGrid& G, int mmax, const double* b,
                          const double* hx, double* r, PcgAcc* acc, int T, const int* active, cudaStream_t s) {
-  if (ntasks <= 0 || mmax <= 0) return cudaSuccess;
+  if (G.ntasks <= 0 || mmax <= 0) return cudaSuccess;
   // ||r||^2 of the replaced residual accumulates from zero
   cudaError_t e = cudaMemset2DAsync(&acc[0].rr, sizeof(PcgAcc), 0, sizeof(double), T, s);
   if (e != cudaSuccess) return e;
   count_launch();
-  pcg2_replace_kernel<<<dim3(ntasks, (mmax + kWarps - 1) / kWarps), kThreads, 0, s>>>(tasks, probs, b, hx, r, acc,
+  pcg2_replace_kernel<<<dim3(G.ntasks, (mmax + kWarps - 1) / kWarps), kThreads, 0, s>>>(G, b, hx, r, acc,
                                                                                       active);
   return cudaGetLastError();
 }
@@ -483,21 +534,21 @@ cudaError_t pcg2_col_dot(int n, int ncol, const double* v, const double* hv, con
   return cudaGetLastError();
 }
 
-template cudaError_t pcg2_update<double>(const PcgTask*, int, const PcgProb*, int, int, const double*, const double*,
+template cudaError_t pcg2_update<double>(const PcgGrid&, int, int, const double*, const double*,
                                          double*, double*, PcgScalars*, PcgAcc*, int*, double*, int, int, int, int*,
                                          cudaStream_t);
-template cudaError_t pcg2_update<float>(const PcgTask*, int, const PcgProb*, int, int, const double*, const double*,
+template cudaError_t pcg2_update<float>(const PcgGrid&, int, int, const double*, const double*,
                                         double*, double*, PcgScalars*, PcgAcc*, int*, float*, int, int, int, int*,
                                         cudaStream_t);
-template cudaError_t pcg2_precond<double>(const PcgTask*, int, const PcgProb*, int, int, const double*, double*, double*,
+template cudaError_t pcg2_precond<double>(const PcgGrid&, int, int, const double*, double*, double*,
                                           PcgScalars*, PcgAcc*, int*, const double*, int, double, int, int, int,
                                           int, int*, cudaStream_t);
-template cudaError_t pcg2_precond<float>(const PcgTask*, int, const PcgProb*, int, int, const double*, double*, double*,
+template cudaError_t pcg2_precond<float>(const PcgGrid&, int, int, const double*, double*, double*,
                                          PcgScalars*, PcgAcc*, int*, const float*, int, double, int, int, int, int,
                                          int*, cudaStream_t);
-template cudaError_t pcg2_dir<double>(const PcgTask*, int, const PcgProb*, int, int, const double*, double*, PcgScalars*,
+template cudaError_t pcg2_dir<double>(const PcgGrid&, int, int, const double*, double*, PcgScalars*,
                                       PcgAcc*, const int*, double*, int, cudaStream_t, const int*, int*);
-template cudaError_t pcg2_dir<float>(const PcgTask*, int, const PcgProb*, int, int, const double*, double*, PcgScalars*,
+template cudaError_t pcg2_dir<float>(const PcgGrid&, int, int, const double*, double*, PcgScalars*,
                                      PcgAcc*, const int*, float*, int, cudaStream_t, const int*, int*);
 
 }  // namespace eda

@@ -51,9 +51,26 @@ struct PcgTask {
 };
 constexpr int kPcgRows = 128;
 
+// Where the kernels find their row chunks and problems: the task and problem
+// tables (device memory; the group path), or, with single != 0, the one
+// problem `one` passed by value with row chunk blockIdx.x (a handle's solve:
+// no table loads ahead of the work).  ntasks: row chunks of the launch.
+struct PcgGrid {
+  const PcgTask* tasks;
+  const PcgProb* probs;
+  int ntasks;
+  int single;
+  PcgProb one;
+};
+
+// The grid of one problem of n rows.
+PcgGrid pcg_single(const PcgProb& prob);
+// The grid of the task and problem tables (ntasks row chunks).
+PcgGrid pcg_tables(const PcgTask* tasks, int ntasks, const PcgProb* probs);
+
 // Builds the row-chunk tasks of the given problem sizes.  Every kernel
-// below runs a grid of (tasks, ceil(mmax / 8)) CTAs of 8 warps, one member
-// per warp (mmax: the largest member count of the problems).
+// below runs a grid of (row chunks, ceil(mmax / 8)) CTAs of 8 warps, one
+// member per warp (mmax: the largest member count of the problems).
 void pcg_tasks(const int* n_of, int nprob, std::vector<PcgTask>* out);
 
 // Zeroes the accumulators of every member and its projections (start of a
@@ -64,7 +81,7 @@ cudaError_t pcg2_reset(PcgAcc* acc, int T, void* Wk, size_t wk_bytes, cudaStream
 // update = 0: projections of the current r only (start of a loop).
 // use_lmp = 0: no projections.
 template <typename TS>
-cudaError_t pcg2_update(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* p,
+cudaError_t pcg2_update(const PcgGrid& G, int kmax, int mmax, const double* p,
                         const double* q, double* x, double* r, PcgScalars* sc, PcgAcc* acc, int* active, TS* Wk,
                         int par, int update, int use_lmp, int* nactive, cudaStream_t s);
 
@@ -73,7 +90,7 @@ cudaError_t pcg2_update(const PcgTask* tasks, int ntasks, const PcgProb* probs, 
 // z, p = z and r.z into slot 0; the caller then clears the projections
 // before the first update.
 template <typename TS>
-cudaError_t pcg2_precond(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* r,
+cudaError_t pcg2_precond(const PcgGrid& G, int kmax, int mmax, const double* r,
                          double* z, double* p, PcgScalars* sc, PcgAcc* acc, int* active, const TS* Wk, int par,
                          double tol, int maxit, int fixed, int use_lmp, int init, int* nactive, cudaStream_t s);
 
@@ -81,13 +98,13 @@ cudaError_t pcg2_precond(const PcgTask* tasks, int ntasks, const PcgProb* probs,
 // With host_count (pinned host memory) != NULL, one thread also copies the
 // active count *nactive there, which the host reads after an event.
 template <typename TS>
-cudaError_t pcg2_dir(const PcgTask* tasks, int ntasks, const PcgProb* probs, int kmax, int mmax, const double* z, double* p,
+cudaError_t pcg2_dir(const PcgGrid& G, int kmax, int mmax, const double* z, double* p,
                      PcgScalars* sc, PcgAcc* acc, const int* active, TS* Wk, int par, cudaStream_t s,
                      const int* nactive = nullptr, int* host_count = nullptr);
 
 // Residual replacement: r = b - hx (hx = (I + A) x from an accurate sweep)
 // and ||r||^2 (cleared first) for the active members of T.
-cudaError_t pcg2_replace(const PcgTask* tasks, int ntasks, const PcgProb* probs, int mmax, const double* b,
+cudaError_t pcg2_replace(const PcgGrid& G, int mmax, const double* b,
                          const double* hx, double* r, PcgAcc* acc, int T, const int* active, cudaStream_t s);
 
 // acc[col].pq += v_col . hv_col for active columns of an [ncol][n] batch
