@@ -137,10 +137,10 @@ __device__ __forceinline__ void read_halo(T (&v)[C], T* mir, const Geo& g) {
   }
 }
 
-// Observation k-ranges of this CTA at observation step oj (see obs_table).
-__device__ __forceinline__ const int* obs_ranges(const int* tab, int nos, int rank, int oj) {
-  return tab + ((long long)rank * nos + oj) * 8;
-}
+// Observation k-ranges of a CTA at observation step oj (see obs_table), from
+// the CTA's rows of the table (tabp: shared memory, or global when they do
+// not fit).
+__device__ __forceinline__ const int* obs_ranges(const int* tabp, int oj) { return tabp + oj * 8; }
 
 // Own run <-> mirror, with 16-byte shared-memory accesses (C * sizeof(T) is a
 // multiple of 16 for every instantiated tile).
@@ -294,12 +294,11 @@ __device__ void bhalf_from_mirrors(const SweepArgs<T>& a, const Geo& g, T* mir, 
 // stash[k] = R^{-1}_k delta_t[obs_idx[k]] for the observations of the owned
 // tile at observation step oj; the owned values are in the mirror.
 template <typename T>
-__device__ __forceinline__ void gather_obs(const SweepArgs<T>& a, const Geo& g, int oj, const T* mir, T* stash) {
-  int k0 = a.obs_ptr[oj], k1 = a.obs_ptr[oj + 1];
-  if (a.obs_tab != nullptr) {
-    const int* tb = obs_ranges(a.obs_tab, a.nos, g.rank, oj);
-    k0 = tb[0];
-    k1 = tb[1];
+__device__ __forceinline__ void gather_obs(const SweepArgs<T>& a, const Geo& g, int oj, const int* tabp, const T* mir,
+                                           T* stash) {
+  if (tabp != nullptr) {
+    const int* tb = obs_ranges(tabp, oj);
+    const int k0 = tb[0], k1 = tb[1];
     const int off = g.HL - g.a0;
     for (int k = k0 + g.tid; k < k1; k += 4 * g.NT) {
       int ii[4];
@@ -315,6 +314,7 @@ __device__ __forceinline__ void gather_obs(const SweepArgs<T>& a, const Geo& g, 
         if (k + u * g.NT < k1) stash[k + u * g.NT] = rr[u] * mir[off + ii[u]];
     }
   } else {
+    const int k0 = a.obs_ptr[oj], k1 = a.obs_ptr[oj + 1];
     for (int k = k0 + g.tid; k < k1; k += g.NT) {
       const int gi = a.obs_idx[k];
       if (gi >= g.a0 && gi < g.a0 + g.Town) stash[k] = a.rinv[k] * mir[g.HL + gi - g.a0];
@@ -353,6 +353,7 @@ __device__ __forceinline__ void load_run(const T* row, const int (&gi)[C], bool 
 }
 
 constexpr int kObsMapCap = 1024;  // steps whose observation index is cached in smem
+constexpr int kObsTabCap = 2048;  // entries of a CTA's observation range rows cached in smem
 
 // STG: the kernel reads stored stage states when the arguments carry them
 // (instantiated for FP64 only: FP32 sweeps recompute, which costs them less
@@ -445,6 +446,18 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   if (omap_smem)
     for (int j = g.tid; j <= N; j += g.NT) omap[j] = a.obs_of_t[j];
   auto obs_at = [&](int t) { return omap_smem ? omap[t] : a.obs_of_t[t]; };
+  // this CTA's rows of the observation range table, in shared memory when
+  // they fit (every gather and injection reads them)
+  const int* tabp = nullptr;
+  if (a.obs_tab != nullptr) {
+    const int* rows = a.obs_tab + (long long)g.rank * a.nos * 8;
+    tabp = rows;
+    if (a.nos * 8 <= kObsTabCap) {
+      int* ot = omap + kObsMapCap;
+      for (int j = g.tid; j < a.nos * 8; j += g.NT) ot[j] = rows[j];
+      tabp = ot;
+    }
+  }
 
   // global indices of this thread's run, and whether 16-byte loads apply
   int gi[C];
@@ -561,11 +574,14 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
           for (int j = g.tid; j < g.Town; j += g.NT) dst[j] = mir[g.HL + j];
         }
         if (oj >= 0) {
-          int k0 = a.obs_ptr[oj], k1 = a.obs_ptr[oj + 1];
-          if (a.obs_tab != nullptr) {
-            const int* tb = obs_ranges(a.obs_tab, a.nos, g.rank, oj);
+          int k0, k1;
+          if (tabp != nullptr) {
+            const int* tb = obs_ranges(tabp, oj);
             k0 = tb[0];
             k1 = tb[1];
+          } else {
+            k0 = a.obs_ptr[oj];
+            k1 = a.obs_ptr[oj + 1];
           }
           for (int k = k0 + g.tid; k < k1; k += g.NT) {
             const int gk = a.obs_idx[k];
@@ -633,7 +649,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     if (obs_at(0) >= 0) {
       write_mirror(mir, g, dl);
       __syncthreads();
-      gather_obs(a, g, obs_at(0), mir, stash);
+      gather_obs(a, g, obs_at(0), tabp, mir, stash);
     }
     } else {
       // later launch of a multi-launch sweep: the state of the extended region
@@ -783,7 +799,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       if (oj >= 0 || refresh) {
         write_mirror(mir, g, dl);
         sync_cluster_or_block(refresh && clus);
-        if (oj >= 0) gather_obs(a, g, oj, mir, stash);
+        if (oj >= 0) gather_obs(a, g, oj, tabp, mir, stash);
         if (refresh) {
           read_halo(dl, mir, g);
           sync_cluster_or_block(clus);
@@ -807,8 +823,8 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   auto inject = [&](int oj) {
     write_mirror_zero<T, C>(mir, g);
     __syncthreads();
-    if (a.obs_tab != nullptr) {
-      const int* tb = obs_ranges(a.obs_tab, a.nos, g.rank, oj);
+    if (tabp != nullptr) {
+      const int* tb = obs_ranges(tabp, oj);
 #pragma unroll
       for (int sgm = 0; sgm < 2; ++sgm) {
         const int k0 = tb[2 + 3 * sgm], k1 = tb[3 + 3 * sgm], base = tb[4 + 3 * sgm];
@@ -1555,7 +1571,7 @@ size_t sweep_smem_bytes(int A, int C, int w, int elem_bytes) {
   int stage = kNumEdge * 4 * A;
   if (E + 2 * w + 2 > stage) stage = E + 2 * w + 2;
   const size_t elems = (size_t)E + (size_t)stage + (size_t)(w + 1);
-  return elems * (size_t)elem_bytes + (size_t)kObsMapCap * sizeof(int) + 16;
+  return elems * (size_t)elem_bytes + (size_t)(kObsMapCap + kObsTabCap) * sizeof(int) + 16;
 }
 
 bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* out, int C) {
