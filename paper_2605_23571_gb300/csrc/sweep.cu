@@ -322,6 +322,85 @@ __device__ __forceinline__ void gather_obs(const SweepArgs<T>& a, const Geo& g, 
   }
 }
 
+// Observation loads of one gather or injection issued a step ahead: the
+// first kObsPre observations of each thread's share (k = first + tid + u NT)
+// go to registers at the start of the step that ends with the gather or
+// injection, which then takes the rest with direct loads.
+constexpr int kObsPre = 2;
+
+template <typename T>
+struct ObsPre {
+  int idx[kObsPre];
+  T val[kObsPre];
+};
+
+// Gather of the owned tile at observation step oj: obs_idx and R^{-1}.
+template <typename T>
+__device__ __forceinline__ void gather_pre(const SweepArgs<T>& a, const Geo& g, const int* tb, ObsPre<T>& q) {
+#pragma unroll
+  for (int u = 0; u < kObsPre; ++u) {
+    const int k = tb[0] + g.tid + u * g.NT;
+    q.idx[u] = k < tb[1] ? __ldg(a.obs_idx + k) : 0;
+    q.val[u] = k < tb[1] ? __ldg(a.rinv + k) : T(0);
+  }
+}
+
+// stash[k] = R^{-1}_k delta[obs_idx[k]] (as gather_obs) from the prefetched
+// loads and direct loads for the rest.
+template <typename T>
+__device__ __forceinline__ void gather_use(const SweepArgs<T>& a, const Geo& g, const int* tb, const ObsPre<T>& q,
+                                           const T* mir, T* stash) {
+  const int off = g.HL - g.a0;
+#pragma unroll
+  for (int u = 0; u < kObsPre; ++u) {
+    const int k = tb[0] + g.tid + u * g.NT;
+    if (k < tb[1]) stash[k] = q.val[u] * mir[off + q.idx[u]];
+  }
+  for (int k = tb[0] + g.tid + kObsPre * g.NT; k < tb[1]; k += g.NT)
+    stash[k] = __ldg(a.rinv + k) * mir[off + __ldg(a.obs_idx + k)];
+}
+
+// Injection over the extended region at observation step oj: its two index
+// segments (k0, k1, base) as one sequence j = 0 .. cnt-1.
+__device__ __forceinline__ void inject_k(const int* tb, int j, int* k, int* base) {
+  const int ca = tb[3] - tb[2];
+  *k = j < ca ? tb[2] + j : tb[5] + (j - ca);
+  *base = j < ca ? tb[4] : tb[7];
+}
+
+template <typename T>
+__device__ __forceinline__ void inject_pre(const SweepArgs<T>& a, const Geo& g, const int* tb, const T* stash,
+                                           ObsPre<T>& q) {
+  const int cnt = (tb[3] - tb[2]) + (tb[6] - tb[5]);
+#pragma unroll
+  for (int u = 0; u < kObsPre; ++u) {
+    const int j = g.tid + u * g.NT;
+    int k, base;
+    inject_k(tb, j, &k, &base);
+    q.idx[u] = j < cnt ? __ldg(a.obs_idx + k) : 0;
+    q.val[u] = j < cnt ? stash[k] : T(0);
+  }
+}
+
+// mir[obs_idx[k] - base] = stash[k] (as scatter_obs over both segments).
+template <typename T>
+__device__ __forceinline__ void inject_use(const SweepArgs<T>& a, const Geo& g, const int* tb, const ObsPre<T>& q,
+                                           const T* stash, T* mir) {
+  const int cnt = (tb[3] - tb[2]) + (tb[6] - tb[5]);
+#pragma unroll
+  for (int u = 0; u < kObsPre; ++u) {
+    const int j = g.tid + u * g.NT;
+    int k, base;
+    inject_k(tb, j, &k, &base);
+    if (j < cnt) mir[q.idx[u] - base] = q.val[u];
+  }
+  for (int j = g.tid + kObsPre * g.NT; j < cnt; j += g.NT) {
+    int k, base;
+    inject_k(tb, j, &k, &base);
+    mir[__ldg(a.obs_idx + k) - base] = stash[k];
+  }
+}
+
 // Own run of the trajectory state at row `row` (C consecutive elements of the
 // extended region): one or two 16-byte vector loads when aligned, else scalar.
 template <typename T, int C>
@@ -661,9 +740,15 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     __syncthreads();
 
     // ------------------------------------------------ tangent linear, forward
+    // FP32 sweeps load the observations of x_{t+1} at the start of step t
+    constexpr bool kPre = sizeof(T) == 4;
     for (int t = f0; t < f1; ++t) {
       T pf[C];
       if (t + 1 < f1) load_run<T, C>(trj + (long long)(t + 1) * a.n, gi, vec_ok, pf);
+      const int oj = obs_at(t + 1);
+      ObsPre<T> qg;
+      if constexpr (kPre)
+        if (oj >= 0 && tabp != nullptr) gather_pre(a, g, obs_ranges(tabp, oj), qg);
       if (stg != nullptr) {
         // stage states from the store: only delta's edges are exchanged
         Run<T, C> X1, X2, X3, X4, e;
@@ -794,12 +879,16 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
 #pragma unroll
         for (int c = 0; c < C; ++c) xr[c] = pf[c];
       }
-      const int oj = obs_at(t + 1);
       const bool refresh = ((t + 1) % a.K == 0) && (t + 1 < N);
       if (oj >= 0 || refresh) {
         write_mirror(mir, g, dl);
         sync_cluster_or_block(refresh && clus);
-        if (oj >= 0) gather_obs(a, g, oj, tabp, mir, stash);
+        if (oj >= 0) {
+          if (kPre && tabp != nullptr)
+            gather_use(a, g, obs_ranges(tabp, oj), qg, mir, stash);
+          else
+            gather_obs(a, g, oj, tabp, mir, stash);
+        }
         if (refresh) {
           read_halo(dl, mir, g);
           sync_cluster_or_block(clus);
@@ -820,10 +909,12 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
 #pragma unroll
   for (int c = 0; c < C; ++c) lam[c] = T(0);
 
-  auto inject = [&](int oj) {
+  auto inject = [&](int oj, const ObsPre<T>* q) {
     write_mirror_zero<T, C>(mir, g);
     __syncthreads();
-    if (tabp != nullptr) {
+    if (q != nullptr) {
+      inject_use(a, g, obs_ranges(tabp, oj), *q, stash, mir);
+    } else if (tabp != nullptr) {
       const int* tb = obs_ranges(tabp, oj);
 #pragma unroll
       for (int sgm = 0; sgm < 2; ++sgm) {
@@ -844,16 +935,22 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   };
 
   if (b1 == N) {
-    if (obs_at(N) >= 0) inject(obs_at(N));
+    if (obs_at(N) >= 0) inject(obs_at(N), nullptr);
   } else {
     load_run<T, C>(a.st_in + (long long)col * a.n, gi, vec_ok, lam);
   }
   load_run<T, C>(trj + (long long)(b1 - 1) * a.n, gi, vec_ok, xr);
   publish(eb[0], g, xr);
   __syncthreads();
+  // FP32 sweeps load the injection of step t at its start
+  constexpr bool kPreA = sizeof(T) == 4;
   for (int t = b1 - 1; t >= b0; --t) {
     T pf[C];
     if (t > b0) load_run<T, C>(trj + (long long)(t - 1) * a.n, gi, vec_ok, pf);
+    const int oj = obs_at(t);
+    ObsPre<T> qa;
+    if constexpr (kPreA)
+      if (oj >= 0 && tabp != nullptr) inject_pre(a, g, obs_ranges(tabp, oj), stash, qa);
     if (stg != nullptr) {
       // stage states from the store: only the adjoint weights' edges are
       // exchanged, through edge buffers 3 and 4 in turn
@@ -995,8 +1092,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
 #pragma unroll
       for (int c = 0; c < C; ++c) xr[c] = pf[c];
     }
-    const int oj = obs_at(t);
-    if (oj >= 0) inject(oj);
+    if (oj >= 0) inject(oj, (kPreA && tabp != nullptr) ? &qa : nullptr);
     const bool refresh = ((N - t) % a.K == 0) && (t > 0);
     if (refresh) {
       write_mirror(mir, g, lam);
