@@ -740,15 +740,19 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     __syncthreads();
 
     // ------------------------------------------------ tangent linear, forward
-    // FP32 sweeps load the observations of x_{t+1} at the start of step t
-    constexpr bool kPre = sizeof(T) == 4;
+    // FP32 sweeps of four values per thread load the observations of
+    // x_{t+1} at the start of step t (the other instantiations keep their
+    // registers for the stages)
+    constexpr bool kPre = sizeof(T) == 4 && C == 4;
     for (int t = f0; t < f1; ++t) {
       T pf[C];
       if (t + 1 < f1) load_run<T, C>(trj + (long long)(t + 1) * a.n, gi, vec_ok, pf);
-      const int oj = obs_at(t + 1);
+      int oj_pre = -1;
       ObsPre<T> qg;
-      if constexpr (kPre)
-        if (oj >= 0 && tabp != nullptr) gather_pre(a, g, obs_ranges(tabp, oj), qg);
+      if constexpr (kPre) {
+        oj_pre = obs_at(t + 1);
+        if (oj_pre >= 0 && tabp != nullptr) gather_pre(a, g, obs_ranges(tabp, oj_pre), qg);
+      }
       if (stg != nullptr) {
         // stage states from the store: only delta's edges are exchanged
         Run<T, C> X1, X2, X3, X4, e;
@@ -879,6 +883,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
 #pragma unroll
         for (int c = 0; c < C; ++c) xr[c] = pf[c];
       }
+      const int oj = kPre ? oj_pre : obs_at(t + 1);
       const bool refresh = ((t + 1) % a.K == 0) && (t + 1 < N);
       if (oj >= 0 || refresh) {
         write_mirror(mir, g, dl);
@@ -942,15 +947,18 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   load_run<T, C>(trj + (long long)(b1 - 1) * a.n, gi, vec_ok, xr);
   publish(eb[0], g, xr);
   __syncthreads();
-  // FP32 sweeps load the injection of step t at its start
-  constexpr bool kPreA = sizeof(T) == 4;
+  // FP32 sweeps of four values per thread load the injection of step t at
+  // its start
+  constexpr bool kPreA = sizeof(T) == 4 && C == 4;
   for (int t = b1 - 1; t >= b0; --t) {
     T pf[C];
     if (t > b0) load_run<T, C>(trj + (long long)(t - 1) * a.n, gi, vec_ok, pf);
-    const int oj = obs_at(t);
+    int oj_pre = -1;
     ObsPre<T> qa;
-    if constexpr (kPreA)
-      if (oj >= 0 && tabp != nullptr) inject_pre(a, g, obs_ranges(tabp, oj), stash, qa);
+    if constexpr (kPreA) {
+      oj_pre = obs_at(t);
+      if (oj_pre >= 0 && tabp != nullptr) inject_pre(a, g, obs_ranges(tabp, oj_pre), stash, qa);
+    }
     if (stg != nullptr) {
       // stage states from the store: only the adjoint weights' edges are
       // exchanged, through edge buffers 3 and 4 in turn
@@ -1092,7 +1100,13 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
 #pragma unroll
       for (int c = 0; c < C; ++c) xr[c] = pf[c];
     }
-    if (oj >= 0) inject(oj, (kPreA && tabp != nullptr) ? &qa : nullptr);
+    const int oj = kPreA ? oj_pre : obs_at(t);
+    if (oj >= 0) {
+      if constexpr (kPreA)
+        inject(oj, tabp != nullptr ? &qa : nullptr);
+      else
+        inject(oj, nullptr);
+    }
     const bool refresh = ((N - t) % a.K == 0) && (t > 0);
     if (refresh) {
       write_mirror(mir, g, lam);
