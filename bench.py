@@ -653,11 +653,18 @@ def run_ours(args):
     status = torch.empty(M, dtype=torch.int32, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
 
-    def step(h, xb_, y_, dz_, it_, rr_, st_):
+    def step(h, xb_, y_, dz_, it_, rr_, st_, marks=None):
+        # marks: events recorded between the phases (setup | sketch + LMP | solve)
         h.eda_set_trajectory(xb_, y_)
+        if marks:
+            marks[0].record(stream)
         h.eda_sketch()
         h.eda_build_lmp()
+        if marks:
+            marks[1].record(stream)
         h.eda_solve_batch(TOL, MAXIT, None, True, dz_, it_, rr_, st_)
+
+    phase_ms = {}
 
     def timed_steps(h, k, warm):
         for _ in range(warm):
@@ -665,16 +672,20 @@ def run_ours(args):
         torch.cuda.synchronize()
         tot = 0.0
         its = []
+        ph = np.zeros(3)
         for _ in range(k):
             flush.fill_(1.0)  # L2 flush between timed steps (outside the events)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            marks = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
             e0.record(stream)
-            step(h, xb, y, dz, iters, relres, status)
+            step(h, xb, y, dz, iters, relres, status, marks)
             e1.record(stream)
             e1.synchronize()
             tot += e0.elapsed_time(e1) / 1e3
+            ph += [e0.elapsed_time(marks[0]), marks[0].elapsed_time(marks[1]), marks[1].elapsed_time(e1)]
             its.append(iters.cpu().numpy().copy())
+        phase_ms[id(h)] = ph / max(1, k)
         return tot, its
 
     hm = P.Handle.from_spec(spec, taps, precision=P.EDA_MIXED)
@@ -778,6 +789,8 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * t_mixed / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": workload_config(spec, world),
+            "step_ms": {name: {"setup": float(ph[0]), "sketch_lmp": float(ph[1]), "solve": float(ph[2])}
+                        for name, ph in (("mixed", phase_ms[id(hm)]), ("fp64", phase_ms[id(h64)]))},
             "fp64_path": {"value": value64, "unit": UNIT, "ms_per_step": 1e3 * t64 / max(1, args.fp64_steps),
                           "speedup_mixed_over_fp64": value / world / value64,
                           "iters_median": float(np.median(its_d))},
