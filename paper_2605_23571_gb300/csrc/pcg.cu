@@ -117,10 +117,14 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgGrid G, 
   // this warp's member (one member per warp) and its rows, loaded first
   const int m = blockIdx.y * kWarps + wid;
   const int item = P.item0 + m;
-  // the loads do not wait for the member's active flag (their addresses are
-  // valid for every member of the problem); inactive members drop them
-  const bool mine = m < P.M;
-  const bool live = mine && active[item] != 0;
+  // a handle's solve (one problem, at most a few hundred members) issues the
+  // loads without waiting for the member's active flag (their addresses are
+  // valid for every member; inactive members drop them); the group path,
+  // whose thousands of members are mostly inactive late in a solve, tests
+  // the flag first so that it does not stream their rows
+  const bool live_flag = m < P.M && active[item] != 0;
+  const bool mine = G.single ? m < P.M : live_flag;
+  const bool live = live_flag;
   const long long off = P.off0 + (long long)m * P.n + tk.row0;
   double pv[R], qv[R], xv[R], rv[R];
   double pq = 0.0, rzp = 0.0;
@@ -224,8 +228,9 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgGrid G,
   // scaled projections, loaded before the CTA stages S
   const int m = blockIdx.y * kWarps + wid;
   const int item = P.item0 + m;
-  const bool mine = m < P.M;  // loads as in the update launch
-  const bool live = mine && active[item] != 0;
+  const bool live_flag = m < P.M && active[item] != 0;  // loads as in the update launch
+  const bool mine = G.single ? m < P.M : live_flag;
+  const bool live = live_flag;
   const long long off = P.off0 + (long long)m * P.n + tk.row0;
   double rv[R];
   double bn = 0.0, rrv = 0.0, tolm = 0.0;
@@ -357,7 +362,9 @@ __global__ void __launch_bounds__(kThreads) pcg2_dir_kernel(const PcgGrid G, int
     const int m = blockIdx.y * kWarps + wid;  // one member per warp
     if (m >= P.M) return;
     const int item = P.item0 + m;
-    // every load in flight before the active flag is tested
+    // a handle's solve has every load in flight before the active flag is
+    // tested (see the update launch); the group path tests it first
+    if (!G.single && !active[item]) return;
     constexpr int R = kRowsPerLane;
     const long long off = P.off0 + (long long)m * P.n + tk.row0;
     double zv[R], pv[R];
