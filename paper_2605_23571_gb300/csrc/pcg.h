@@ -63,7 +63,8 @@ struct PcgGrid {
   PcgProb one;
 };
 
-// The grid of one problem of n rows.
+// The grid of one problem: ceil(prob.n / kPcgRows) row chunks, the problem
+// by value.
 PcgGrid pcg_single(const PcgProb& prob);
 // The grid of the task and problem tables (ntasks row chunks).
 PcgGrid pcg_tables(const PcgTask* tasks, int ntasks, const PcgProb* probs);
