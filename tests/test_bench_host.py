@@ -52,3 +52,21 @@ def test_kernel_names_follow_the_tiling():
     assert bench.sweep_kernel_name(PLAN).startswith("sweep_kernel<float,4> (clusters of 5 CTAs x 256 threads")
     assert bench.sweep_kernel_name(dict(PLAN, kind="warp", C=8)).startswith("wsweep_kernel<float,8>")
     assert "multi-launch" in bench.sweep_kernel_name(dict(PLAN, kind="multi-launch"), "double")
+
+
+def test_cpu_baseline_all_cores_sample():
+    # the oracle's PCG sample on several members at once in spawned workers
+    import numpy as np
+
+    import eda_synth as S
+    import oracle as O
+    spec = S.spec_small(200, 8, 5, every_var=2, every_step=2, length_scale=3.0, seed=3)
+    taps = O.bhalf_taps(spec.n, spec.length_scale, spec.sigma_b)
+    _, xb, y = O.twin(spec, S.draws(spec), taps)
+    r = bench.cpu_oracle_step(spec, xb, y, taps, np.full(spec.n_members, 50), sample_iters=4, cores=2)
+    ac = r["all_cores"]
+    assert ac["cores"] == 2 and ac["t_full_step_s"] > r["t_setup_sketch_lmp_s"]
+    # two members at once take less than twice one member's time per iteration
+    t_seq = r["t_full_step_s"] - r["t_setup_sketch_lmp_s"]
+    t_par = ac["t_full_step_s"] - r["t_setup_sketch_lmp_s"]
+    assert t_par < 1.5 * t_seq
