@@ -219,11 +219,12 @@ def cpu_oracle_parallel(spec, traj, b, Sk, c, taps, cores, sample_iters):
     from oracle.sample import pcg_member_sample
     m = max(1, min(cores, spec.n_members))
     ctx = mp.get_context("spawn")
-    with ctx.Pool(m) as pool:
-        pool.map(pcg_member_sample, [(spec, traj[:1], b[:1], Sk, c, taps, 1)] * m)  # workers import
+    with ctx.Pool(m) as pool:  # leaving the block terminates the workers
+        # bounded waits: a stuck pool raises instead of holding the benchmark
+        pool.map_async(pcg_member_sample, [(spec, traj[:1], b[:1], Sk, c, taps, 1)] * m).get(timeout=300)
         t0 = time.perf_counter()
-        pool.map(pcg_member_sample, [(spec, traj[j:j + 1], b[j:j + 1], Sk, c, taps, sample_iters)
-                                     for j in range(m)])
+        pool.map_async(pcg_member_sample, [(spec, traj[j:j + 1], b[j:j + 1], Sk, c, taps, sample_iters)
+                                           for j in range(m)]).get(timeout=300)
         wall = time.perf_counter() - t0
     return m, wall / sample_iters
 
