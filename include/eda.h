@@ -274,6 +274,19 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out);
 EDA_API int eda_sweep_plan(eda_handle* h, int fp64, int* info);
 
 /*
+ * Host-only planning query (no handle, no device work): the tiling the
+ * library would use for a Hessian-product sweep of state size n, FP64
+ * (fp64 != 0) or FP32, banded circulant half-width w and halo refresh period
+ * K.  kind 0: thread-block clusters of exactly cs CTAs with C values per
+ * thread (C = 0: the default run length); kind 1: multi-launch tiles of K
+ * steps with `threads` threads per CTA (0: the default; C must be 0); kind 2:
+ * warp-tiled, clusters of cs CTAs, C values per lane.  info[8] (host,
+ * caller-owned) as in eda_sweep_plan.  EDA_ERR_INVALID when no tiling of
+ * that shape fits (or an argument is out of range).
+ */
+EDA_API int eda_plan_tiling(int n, int fp64, int w, int kind, int cs, int threads, int K, int C, int* info);
+
+/*
  * Tracing: process-wide number of CUDA kernels the library has launched
  * (every handle, every entry point) since it was loaded.  No device work.
  */

@@ -36,7 +36,8 @@ EXPORTS = ["eda_version", "eda_last_error", "eda_create", "eda_destroy", "eda_tw
            "eda_ws_create", "eda_ws_destroy", "eda_ws_last_error", "eda_ws_num_params", "eda_ws_set_params",
            "eda_ws_get_params", "eda_ws_set_scales", "eda_ws_get_scales", "eda_ws_loss_grad", "eda_ws_train",
            "eda_ws_infer", "eda_hvp_noalloc", "eda_hvp_noalloc_capacity", "eda_lmp_info",
-           "eda_trace", "eda_trace_read", "eda_ws_init", "eda_sweep_plan", "eda_bhalf_apply"]
+           "eda_trace", "eda_trace_read", "eda_ws_init", "eda_sweep_plan", "eda_bhalf_apply",
+           "eda_plan_tiling"]
 
 
 class EdaError(RuntimeError):
@@ -103,6 +104,8 @@ def lib() -> ctypes.CDLL:
     L.eda_sweep_plan.argtypes = [vp, i, ctypes.POINTER(i)]
     L.eda_bhalf_apply.restype = i
     L.eda_bhalf_apply.argtypes = [vp, i, vp, vp]
+    L.eda_plan_tiling.restype = i
+    L.eda_plan_tiling.argtypes = [i, i, i, i, i, i, i, i, ctypes.POINTER(i)]
     L.eda_solve_batch.restype = i
     L.eda_solve_batch.argtypes = [vp, d, i, vp, i, vp, vp, vp, vp]
     L.eda_hvp.restype = i
@@ -190,6 +193,25 @@ def _ptr_impl(a, dtype, count, name):
             raise ValueError("%s has %d elements, needs %d" % (name, a.numel(), count))
         return a.data_ptr()
     raise TypeError("%s must be a numpy array or torch tensor" % name)
+
+
+PLAN_KINDS = ("cluster", "multi-launch", "warp")
+PLAN_KEYS = ("kind", "ctas_per_vector", "threads", "C", "K", "halo", "owned", "smem")
+
+
+def plan_tiling(n, fp64, w, kind, cs=0, threads=0, K=8, C=0):
+    """The sweep tiling the library would use (host only, no GPU): kind
+    'cluster' (cs CTAs per vector), 'multi-launch' (`threads` per CTA) or
+    'warp'; a dict as Handle.eda_sweep_plan returns, or None if it does not
+    fit."""
+    info = (ctypes.c_int * 8)()
+    rc = lib().eda_plan_tiling(int(n), int(bool(fp64)), int(w), PLAN_KINDS.index(kind), int(cs), int(threads),
+                               int(K), int(C), info)
+    if rc != EDA_OK:
+        return None
+    out = dict(zip(PLAN_KEYS, list(info)))
+    out["kind"] = PLAN_KINDS[out["kind"]]
+    return out
 
 
 def kernel_launches() -> int:
@@ -326,8 +348,6 @@ class Handle:
         self._check(self._L.eda_lmp_info(self._h, ctypes.byref(path), ctypes.byref(rank), ctypes.byref(shift)))
         return path.value, rank.value, shift.value
 
-    SWEEP_PLAN_KEYS = ("kind", "ctas_per_vector", "threads", "C", "K", "halo", "owned", "smem")
-    SWEEP_PLAN_KINDS = ("cluster", "multi-launch", "warp")
 
     def eda_sweep_plan(self, fp64=False):
         """The tiling of the FP64 or FP32 Hessian-product sweeps as a dict
@@ -335,8 +355,8 @@ class Handle:
         refresh period K, ...)."""
         info = (ctypes.c_int * 8)()
         self._check(self._L.eda_sweep_plan(self._h, int(bool(fp64)), info))
-        out = dict(zip(self.SWEEP_PLAN_KEYS, list(info)))
-        out["kind"] = self.SWEEP_PLAN_KINDS[out["kind"]]
+        out = dict(zip(PLAN_KEYS, list(info)))
+        out["kind"] = PLAN_KINDS[out["kind"]]
         return out
 
     def eda_solve_batch(self, tol, maxit, x0, use_lmp, dz_out, iters_out=None, relres_out=None,

@@ -1288,6 +1288,27 @@ EDA_API int eda_set_lmp(eda_handle* h, const double* s_in, const double* eigvals
   return EDA_OK;
 }
 
+EDA_API int eda_plan_tiling(int n, int fp64, int w, int kind, int cs, int threads, int K, int C, int* info) {
+  if (!info || n < 1 || w < 0 || K < 1 || kind < 0 || kind > 2)
+    return fail(nullptr, EDA_ERR_INVALID, "eda_plan_tiling: invalid argument");
+  const int eb = fp64 ? 8 : 4;
+  eda::SweepPlan p{};
+  bool ok = false;
+  if (kind == 0) ok = eda::plan_sweep_exact(n, eb, w, cs, K, &p, C);
+  if (kind == 1) ok = C == 0 && eda::plan_sweep_ml(n, eb, w, K, threads, &p);
+  if (kind == 2) ok = eda::plan_sweep_warp(n, eb, w, cs, K, C, &p);
+  if (!ok) return fail(nullptr, EDA_ERR_INVALID, "eda_plan_tiling: no tiling of that shape fits");
+  info[0] = p.warp ? 2 : (p.ml ? 1 : 0);
+  info[1] = p.CS;
+  info[2] = p.A;
+  info[3] = p.C;
+  info[4] = p.K;
+  info[5] = p.HL;
+  info[6] = p.Ttile;
+  info[7] = (int)p.smem;
+  return EDA_OK;
+}
+
 EDA_API int eda_sweep_plan(eda_handle* h, int fp64, int* info) {
   if (!h || !info) return fail(h, EDA_ERR_INVALID, "handle or info is NULL");
   if (!fp64 && h->precision != EDA_MIXED) return fail(h, EDA_ERR_INVALID, "an FP64 handle has no FP32 sweep");
