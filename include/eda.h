@@ -245,6 +245,10 @@ EDA_API int eda_bhalf_apply(eda_handle* h, int ncol, const double* V, double* OU
  * m(c) = member_of_col[c] in [0, L] choosing the trajectory (the
  * linearisation state).  V, HV are [ncol x n].  Requires
  * eda_set_trajectory.  Sweeps in FP64 (EDA_FP64) or FP32 (EDA_MIXED).
+ * A member index outside [0, L]: EDA_ERR_INVALID when member_of_col is
+ * host memory (checked before any work); when it is device memory the
+ * kernel checks it, reads no trajectory for that column and writes NaN to
+ * its row of HV.
  */
 EDA_API int eda_hvp(eda_handle* h, const int* member_of_col, int ncol, const double* V,
                     double* HV, int include_identity);
@@ -332,13 +336,16 @@ EDA_API int eda_time_hvp_sweep(eda_handle* h, int reps, int fp64, double* ms_out
  * the handle's observation stash and stages host arrays); this variant
  * computes the same products with no allocation at all:
  *  - member_of_col, V and HV must be device memory (EDA_ERR_INVALID otherwise);
+ *    a member index outside [0, L] gives a NaN row of HV (as in eda_hvp);
  *  - its scratch, the per-column observation stash, is a fixed 32 MiB
  *    __device__ array compiled into the library (held by every device that
  *    loads it until the process exits): ncol * p must not exceed
  *    eda_hvp_noalloc_capacity(precision == EDA_FP64) entries, or the call
  *    fails with EDA_ERR_INVALID before any work (split the columns);
  *  - the first call on a device looks up the array's device address (no
- *    allocation); make that first call before any stream capture;
+ *    allocation); make that first call before any stream capture.  Host
+ *    threads may make their first calls concurrently (the cached address
+ *    is published atomically);
  *  - every call on a device shares the array: calls that overlap on the GPU
  *    (other streams, other handles) race; calls on one stream do not.  The
  *    stash needs no clearing (each entry is written before it is read).

@@ -381,6 +381,7 @@ SweepArgs<T> base_args(eda_handle* h) {
     a.obs_tab = h->tab32_ok ? h->tab32 : nullptr;
   }
   a.traj_mstride = (long long)(h->N + 1) * h->n;
+  a.M = h->M;
   if constexpr (sizeof(T) == 8) a.stages = h->stg;
   a.stage_astride = (long long)h->M * (h->N + 1) * h->n;
   return a;
@@ -1289,7 +1290,7 @@ EDA_API int eda_set_lmp(eda_handle* h, const double* s_in, const double* eigvals
 }
 
 EDA_API int eda_plan_tiling(int n, int fp64, int w, int kind, int cs, int threads, int K, int C, int* info) {
-  if (!info || n < 1 || w < 0 || K < 1 || kind < 0 || kind > 2)
+  if (!info || n < 1 || w < 0 || K < 1 || K > eda::kMaxRefresh || kind < 0 || kind > 2)
     return fail(nullptr, EDA_ERR_INVALID, "eda_plan_tiling: invalid argument");
   const int eb = fp64 ? 8 : 4;
   eda::SweepPlan p{};

@@ -70,6 +70,9 @@ struct SweepArgs {
   // columns
   int ncol;
   const int* col_member; // [ncol] or nullptr (= column index)
+  int M;                 // members in the trajectory store: a column whose
+                         // col_member is outside [0, M) gets NaN outputs
+                         // (0: not checked; the group launch's items are)
   const int* col_active; // [ncol] or nullptr (= all active)
   const T* V;            // MODE_HVP input vectors [ncol][v_stride]
   long long v_stride;
@@ -121,6 +124,10 @@ struct SweepArgs {
   const SweepItem* items;
   const int* flags;
 };
+
+// Largest halo refresh period a tiling accepts (the halo 8K + 8 must stay
+// far from int overflow; windows are much shorter).
+constexpr int kMaxRefresh = 4096;
 
 struct SweepPlan {
   int CS, C, A, E, Ttile, HL, K;

@@ -15,6 +15,8 @@
 // device memory.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "handle.h"
 
 namespace {
@@ -25,9 +27,11 @@ constexpr long long kNoAllocScratchBytes = 32ll << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 // Device address of the scratch array per device, looked up once per device
-// (the array's name is only a host-side stand-in in host code).
+// (the array's name is only a host-side stand-in in host code).  Host threads
+// making their first call on one device at once may both look it up; they
+// find the same address, and the atomic slot makes the publication safe.
 constexpr int kMaxDevices = 64;
-void* g_scratch_ptr[kMaxDevices] = {};
+std::atomic<void*> g_scratch_ptr[kMaxDevices] = {};
 
 }  // namespace
 
@@ -64,12 +68,11 @@ EDA_API int eda_hvp_noalloc(eda_handle* h, const int* member_of_col, int ncol, c
   int dev = 0;
   CU(h, cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return eda::fail(h, EDA_ERR_INVALID, "eda_hvp_noalloc: device index too large");
-  if (g_scratch_ptr[dev] == nullptr) {
-    void* ptr = nullptr;
-    CU(h, cudaGetSymbolAddress(&ptr, g_noalloc_scratch));
-    g_scratch_ptr[dev] = ptr;
+  void* scratch = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (scratch == nullptr) {
+    CU(h, cudaGetSymbolAddress(&scratch, g_noalloc_scratch));
+    g_scratch_ptr[dev].store(scratch, std::memory_order_release);
   }
-  void* scratch = g_scratch_ptr[dev];
   // The stash needs no clearing: the tangent-linear sweep writes every
   // observation entry of a column before the adjoint sweep reads it.
   if (fp64) {
@@ -95,6 +98,7 @@ EDA_API int eda_hvp_noalloc(eda_handle* h, const int* member_of_col, int ncol, c
     a.mode = eda::MODE_HVP;
     a.ncol = ncol;
     a.col_member = member_of_col;
+    a.M = h->M;
     a.V = V;
     a.v_stride = h->n;
     a.OUT = HV;
@@ -124,6 +128,7 @@ EDA_API int eda_hvp_noalloc(eda_handle* h, const int* member_of_col, int ncol, c
     a.mode = eda::MODE_HVP;
     a.ncol = ncol;
     a.col_member = member_of_col;
+    a.M = h->M;
     a.V64 = V;
     a.v_stride = h->n;
     a.OUT64 = HV;

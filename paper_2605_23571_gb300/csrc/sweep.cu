@@ -431,6 +431,31 @@ __device__ __forceinline__ void load_run(const T* row, const int (&gi)[C], bool 
   }
 }
 
+// A column whose trajectory index lies outside the store [0, M) (M > 0):
+// the caller passed a bad member_of_col.  Its outputs become NaN and no
+// trajectory row is read.
+template <typename T>
+__device__ __forceinline__ bool bad_member(const SweepArgs<T>& a, int member) {
+  return a.M > 0 && (unsigned)member >= (unsigned)a.M;
+}
+
+// NaN over the owned tile of a column's output: the state buffer of a
+// multi-launch chain (its closing U_B kernel then writes NaN), else the
+// output vector.
+template <typename T>
+__device__ void nan_owned(const SweepArgs<T>& a, const Geo& g, int col, long long voff) {
+  const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+  if (a.ml) {
+    if (a.st_out != nullptr)
+      for (int j = g.tid; j < g.Town; j += g.NT) a.st_out[(long long)col * a.n + g.a0 + j] = (T)qnan;
+    return;
+  }
+  for (int j = g.tid; j < g.Town; j += g.NT) {
+    if (a.OUT64 != nullptr) a.OUT64[voff + g.a0 + j] = qnan;
+    else if (a.OUT != nullptr) a.OUT[voff + g.a0 + j] = (T)qnan;
+  }
+}
+
 constexpr int kObsMapCap = 1024;  // steps whose observation index is cached in smem
 constexpr int kObsTabCap = 2048;  // entries of a CTA's observation range rows cached in smem
 
@@ -508,6 +533,10 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   g.a0 = g.rank * a.Ttile;
   g.Town = min(a.Ttile, a.n - g.a0);
   g.gbase = ((g.a0 - a.HL) % a.n + a.n) % a.n;
+  if (a.items == nullptr && a.mode != MODE_NL && bad_member(a, member)) {
+    nan_owned(a, g, col, voff);  // uniform over the cluster: depends on col only
+    return;
+  }
 
   const int w = a.w;
   const int N = a.N;
@@ -1266,6 +1295,10 @@ __global__ void __launch_bounds__(kWarpMaxThreads) wsweep_kernel(const SweepArgs
   g.a0 = g.rank * a.Ttile;
   g.Town = min(a.Ttile, a.n - g.a0);
   g.gbase = ((g.a0 - a.HL) % a.n + a.n) % a.n;
+  if (bad_member(a, member)) {
+    nan_owned(a, g, col, voff);  // uniform over the cluster: depends on col only
+    return;
+  }
   const int E = a.E, w = a.w, N = a.N;
 
   // shared memory: mirrors [2][E] | stage [E + 2(HW + w)] | taps [w + 1] | obs-step map
@@ -1690,7 +1723,7 @@ bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* ou
   if (elem_bytes == 8 ? (C != 2 && C != 4) : (C != 4 && C != 8)) return false;
   out->ml = 0;
   out->warp = 0;
-  if (CS < 1 || CS > 16 || K < 1) return false;
+  if (CS < 1 || CS > 16 || K < 1 || K > kMaxRefresh) return false;
   const int Ttile = (n + CS - 1) / CS;
   if ((CS - 1) * Ttile >= n) return false;
   const int HL = 8 * K + 8;
@@ -1714,7 +1747,7 @@ bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* ou
 
 bool plan_sweep_warp(int n, int elem_bytes, int w, int CS, int K, int C, SweepPlan* out) {
   if (elem_bytes == 8 ? (C != 2 && C != 4) : (C != 4 && C != 8)) return false;
-  if (CS < 1 || CS > 16 || K < 1) return false;
+  if (CS < 1 || CS > 16 || K < 1 || K > kMaxRefresh) return false;
   const int LW = 32 * C - 2 * warp_halo(C);
   const int Ttile = (n + CS - 1) / CS;
   if ((CS - 1) * Ttile >= n) return false;
@@ -1798,7 +1831,7 @@ void warp_obs_table(const SweepPlan& p, int n, int nos, const int* obs_ptr, cons
 bool plan_sweep_ml(int n, int elem_bytes, int w, int K, int A, SweepPlan* out) {
   const int C = (elem_bytes == 8) ? 4 : 8;
   if (A <= 0) A = (elem_bytes == 8) ? 512 : 256;
-  if (A % 32 != 0 || A > kMaxThreads) return false;
+  if (A % 32 != 0 || A > kMaxThreads || K < 1 || K > kMaxRefresh) return false;
   const int E = A * C;
   const int HL = 8 * K + 8;
   const int Ttile = E - 2 * HL;

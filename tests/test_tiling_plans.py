@@ -81,3 +81,12 @@ def test_impossible_shapes_are_refused():
     assert P.plan_tiling(4096, False, 50, "cluster", cs=1, K=8, C=4) is None    # one CTA cannot hold it
     assert P.plan_tiling(4096, False, 50, "cluster", cs=17, K=8) is None        # cluster limit 16
     assert P.plan_tiling(0, False, 50, "cluster", cs=1, K=8) is None
+
+
+@pytest.mark.parametrize("kind", ["cluster", "multi-launch", "warp"])
+def test_refresh_period_is_bounded(kind):
+    # the halo 8K + 8 is an int: an absurd K is refused instead of wrapping
+    kw = {"cs": 5} if kind != "multi-launch" else {}
+    C = 0 if kind != "warp" else 8
+    for K in (4097, 1 << 28, (1 << 31) - 1):
+        assert P.plan_tiling(4096, False, 50, kind, K=K, C=C, **kw) is None

@@ -75,6 +75,34 @@ def test_noalloc_rejects_host_memory_and_oversized_batches():
         assert "exceed" in str(e.value)
 
 
+@pytest.mark.parametrize("entry", ["eda_hvp", "eda_hvp_noalloc"])
+def test_member_index_out_of_range_gives_nan_rows(entry):
+    # a device member_of_col is checked by the kernel: a bad index reads no
+    # trajectory row and turns that column's output into NaN; the other
+    # columns are computed as usual
+    import torch
+    dev = torch.device("cuda:0")
+    spec = S.spec_small(300, 16, 4, every_var=2, every_step=2, length_scale=6.0, seed=9)
+    taps, xb, y = problem(spec)
+    with P.Handle.from_spec(spec, taps, precision=P.EDA_FP64) as h:
+        h.eda_set_trajectory(torch.tensor(xb, device=dev), torch.tensor(y, device=dev))
+        V = torch.tensor(S.gaussian_matrix(4, spec.n, 5), device=dev)
+        good = torch.tensor([1, 2, 3, 0], dtype=torch.int32, device=dev)
+        bad = torch.tensor([1, spec.n_members, 3, -1], dtype=torch.int32, device=dev)
+        ref = torch.empty_like(V)
+        out = torch.zeros_like(V)
+        h.eda_hvp(good, V, ref, True)
+        getattr(h, entry)(bad, V, out, True)
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        assert np.isnan(o[1]).all() and np.isnan(o[3]).all()
+        assert rowrel(o[[0, 2]], ref.cpu().numpy()[[0, 2]]).max() < 1e-12
+        # a host member_of_col is checked before any work
+        with pytest.raises(P.EdaError) as e:
+            h.eda_hvp(bad.cpu().numpy(), V, out, True)
+        assert e.value.code == P.EDA_ERR_INVALID
+
+
 def test_noalloc_rejects_multi_launch_tilings():
     # multi-launch sweeps pass their state through buffers the handle
     # allocates, so the allocation-free entry point refuses them
