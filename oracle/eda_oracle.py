@@ -29,7 +29,33 @@ Parity status: every function here is pinned by a test in
 ``tests/test_oracle_*.py`` against something other than itself (closed forms,
 invariants, finite differences, brute force, library routines on tiny
 inputs).  The PCG iteration counts the paper only plots are "parity
-unpinned": the paper prints no numbers for them.
+unpinned": the paper prints no numbers for them.  Function -> pin:
+
+* l96_tendency ....... fixed point x = F (model), the paper's index form,
+                       energy identity of the advection term
+* rk4_step, trajectory  local error order 5 against scipy's DOP853
+* jac_apply, tl_step . Taylor test (remainder ratio -> 4)
+* jacT_apply, adj_step  entrywise transpose; dot-product tests per step and
+                       over the window (1e-12)
+* bhalf_taps/apply ... closed-form Gaussian taps (golden file); U_B U_B
+                       against the Gaussian correlation
+* twin, obs_gather ... enter every pin below through the observations;
+                       Gamma covariance A + A^2 on a linear twin
+* innovations, rhs ... minus the central-difference gradient of the
+                       nonlinear cost at dz = 0 (test_rhs_is_minus_...)
+* apply_A, hvp, dense_A  finite-difference Hessian of the nonlinear model,
+                       circulant closed form at the fixed point, symmetry,
+                       eigenvalues >= 1 and the unit cluster
+* cost_J ............. J(x) - J(x*) = 1/2 |x - x*|_H^2; history of pcg
+                       never increases and ends at J(x_K)
+* nystrom ............ full-rank recovery, exact low rank, Phi -> Phi G
+                       invariance, power pass, shift and truncated-EVD
+                       variants against dense A Phi (Phi^T A Phi)^+ Phi^T A
+* theta_value, lmp_coeffs, lmp_apply  exact eigenpairs map the k targeted
+                       eigenvalues to theta, the rest unchanged
+* pcg ................ dense direct solve (1e-10), with the LMP, from an
+                       initial guess x0 (and CG from x0 = x0 + CG on the
+                       shifted residual), a-priori bound |e| <= |r|
 
 Conventions (readings of the paper where it is silent):
 * states x_0..x_N on the window; observation steps are given explicitly and

@@ -117,6 +117,85 @@ def test_pcg_matches_dense_solve():
             <= np.linalg.norm(true_r, axis=1) * (1 + 1e-9)).all()
 
 
+def nonlinear_cost(spec, taps, xb0, y0, dz):
+    """Eq. (1) in the control variable (Section 2.3, CVT dx = U_B dz):
+    1/2 ||dz||^2 + 1/2 sum_t ||y_t - H_t M_{0->t}(x_b + U_B dz)||^2_{R^-1},
+    through the NONLINEAR model (no tangent linear, no adjoint)."""
+    x0 = xb0 + O.bhalf_apply(dz, taps)
+    dep = y0 - O.obs_gather(spec, O.trajectory(x0, spec.F, spec.dt, spec.nsteps))
+    return 0.5 * float(dz @ dz) + 0.5 * float(np.sum(spec.rinv * dep * dep))
+
+
+def test_rhs_is_minus_the_gradient_of_the_nonlinear_cost():
+    # b = U_B^T G^T R^{-1} d is minus the gradient of the cost at dz = 0
+    # (Section 2.3: the first Gauss-Newton step solves (I + A) dz = b).
+    # Central differences of the nonlinear cost catch a sign, a missing
+    # R^{-1} or U_B, or a wrong observation time in rhs(); sigma_o and
+    # sigma_b differ from 1 so that R^{-1} and the U_B scale are visible.
+    n, N = 32, 12
+    steps, ptr, idx = S.regular_obs(n, N, 3, 4)
+    spec = S.Spec(n=n, nsteps=N, obs_steps=steps, obs_ptr=ptr, obs_idx=idx, sigma_o=0.5,
+                  sigma_b=0.8, length_scale=2.5, n_members=2, ell=1, k=1, spinup=500)
+    taps = O.bhalf_taps(n, 2.5, 0.8)
+    _, xb, y = O.twin(spec, S.draws(spec), taps)
+    traj = O.member_trajectories(spec, xb)
+    b = O.rhs(spec, traj, O.innovations(spec, traj, y), taps)
+    eps = 1e-4
+    for m in range(2):
+        g = np.array([(nonlinear_cost(spec, taps, xb[m], y[m], eps * e)
+                       - nonlinear_cost(spec, taps, xb[m], y[m], -eps * e)) / (2 * eps) for e in np.eye(n)])
+        assert np.linalg.norm(g + b[m]) <= 1e-6 * np.linalg.norm(b[m])
+
+
+def test_pcg_from_an_initial_guess():
+    # the x0 branch of pcg: r_0 = b - H x0, converged to the dense solution,
+    # and CG from x0 on H x = b takes the same steps as CG from 0 on
+    # H e = b - H x0 (Section 2.3; x = x0 + e)
+    spec, taps, xb, y, traj = tiny_problem(seed=7)
+    b = O.rhs(spec, traj, O.innovations(spec, traj, y), taps)
+    Hd = [np.eye(spec.n) + O.dense_A(spec, traj[m], taps) for m in range(spec.n_members)]
+    ref = np.stack([np.linalg.solve(Hd[m], b[m]) for m in range(spec.n_members)])
+    x0 = np.random.default_rng(4).standard_normal(b.shape) * np.linalg.norm(ref, axis=1, keepdims=True) \
+        / np.sqrt(spec.n)
+    hv = lambda V: O.hvp(spec, traj, V, taps)
+    res = O.pcg(hv, b, tol=1e-13, maxit=300, x0=x0)
+    assert (np.linalg.norm(res["x"] - ref, axis=1) / np.linalg.norm(ref, axis=1)).max() <= 1e-10
+    # the same r_0 = b - H x0 both ways (CG amplifies a 1e-16 difference in
+    # it), so only the accumulation of x differs; and r_0 itself against
+    # the dense operator
+    r0 = b - hv(x0)
+    r0d = np.stack([b[m] - Hd[m] @ x0[m] for m in range(spec.n_members)])
+    assert np.abs(r0 - r0d).max() <= 1e-12 * np.abs(r0d).max()
+    for K in (1, 4, 9):
+        a = O.pcg(hv, b, tol=0, maxit=K, x0=x0, fixed_iters=K)["x"]
+        e = O.pcg(hv, r0, tol=0, maxit=K, fixed_iters=K)["x"]
+        assert (np.linalg.norm(a - (x0 + e), axis=1) / np.linalg.norm(a, axis=1)).max() <= 1e-12
+
+
+def test_cost_and_its_history_along_pcg():
+    # J(x) = 1/2 x^T H x - b^T x: J(x) - J(x*) = 1/2 (x - x*)^T H (x - x*) for
+    # any x (x* = H^{-1} b), and CG minimises J over nested Krylov spaces, so
+    # the history pcg records never increases and ends at J(x_K)
+    spec, taps, xb, y, traj = tiny_problem(seed=8)
+    b = O.rhs(spec, traj, O.innovations(spec, traj, y), taps)
+    H = np.eye(spec.n) + O.dense_A(spec, traj[0], taps)
+    H = 0.5 * (H + H.T)
+    xs = np.linalg.solve(H, b[0])
+    rng = np.random.default_rng(2)
+    for _ in range(3):
+        x = xs + rng.standard_normal(spec.n)
+        e = x - xs
+        lhs = O.cost_J(H @ x, x, b[0]) - O.cost_J(H @ xs, xs, b[0])
+        assert abs(lhs - 0.5 * e @ H @ e) <= 1e-10 * (0.5 * e @ H @ e)
+    res = O.pcg(lambda V: O.hvp(spec, traj[:1], V, taps), b[:1], tol=0, maxit=25, fixed_iters=25)
+    J = np.array(res["J"][0])
+    assert len(J) == 26 and J[0] == 0.0
+    assert (np.diff(J) <= 1e-12 * abs(J).max()).all()
+    xk = res["x"][0]
+    assert abs(J[-1] - O.cost_J(H @ xk, xk, b[0])) <= 1e-10 * abs(J[-1])
+    assert J[-1] >= O.cost_J(H @ xs, xs, b[0]) - 1e-10 * abs(J[-1])
+
+
 def test_pcg_with_lmp_matches_dense_solve():
     spec, taps, xb, y, traj = tiny_problem(seed=3)
     out = O.eda_pipeline(spec, xb, y, taps, tol=1e-13, maxit=200)
@@ -295,7 +374,12 @@ def test_nystrom_truncated_evd_when_the_sketch_is_rank_deficient():
     mu, V = np.linalg.eigh(0.5 * (W + W.T))
     keep = mu > 1e-12 * mu.max()
     # rank r of the approximation < k: the first r columns are orthonormal
-    # eigenvectors, the remaining ones (and their D) are zero
+    # eigenvectors, the remaining ones (and their D) are zero.  Reading of
+    # Appendix B (truncated eigendecomposition): A_N = Y W^+ Y^T has rank at
+    # most the number of kept eigenvalues of W, and of its nonzero
+    # eigenvalues only those above the truncation level carry information,
+    # so r can fall below keep.sum() when Y maps kept directions to
+    # negligible ones; hence r <= keep.sum(), not equality
     r = info["rank"]
     assert r <= keep.sum() < 31 and D[r - 1] > 1e-12 * D[0]
     np.testing.assert_allclose(Sk[:, :r].T @ Sk[:, :r], np.eye(r), atol=1e-12)
