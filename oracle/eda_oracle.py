@@ -56,6 +56,10 @@ unpinned": the paper prints no numbers for them.  Function -> pin:
 * pcg ................ dense direct solve (1e-10), with the LMP, from an
                        initial guess x0 (and CG from x0 = x0 + CG on the
                        shifted residual), a-priori bound |e| <= |r|
+* lmp_split_coeffs, pcg_split  U U = P_theta and U = U^T on dense matrices;
+                       the split iterates equal pcg's (nested Krylov spaces
+                       U K(U H U, U b) = K(P H, P b)) and converge to the
+                       dense solution
 
 Conventions (readings of the paper where it is silent):
 * states x_0..x_N on the window; observation steps are given explicitly and
@@ -230,7 +234,17 @@ def twin(spec, dr, taps):
     x = F + spec.spin_sigma * dr.eta_spin
     for _ in range(spec.spinup):
         x = rk4_step(x, F, dt)
-    xt0 = x
+    return twin_from_truth(spec, dr, taps, x)
+
+
+def twin_from_truth(spec, dr, taps, xt0):
+    """The twin of ``twin`` from a given spun-up truth x^t_0: truth over the
+    window, observations, control background and perturbed members.
+
+    Returns (x_truth0, xb (L+1, n), y (L+1, p)).
+    """
+    F, dt = spec.F, spec.dt
+    xt0 = np.asarray(xt0, dtype=np.float64)
     truth = trajectory(xt0, F, dt, spec.nsteps)
     sig_o = 1.0 / np.sqrt(spec.rinv)
     y0 = obs_gather(spec, truth) + sig_o * dr.eta_o[0]
@@ -438,6 +452,13 @@ def lmp_dense(S, c):
     return np.eye(S.shape[0]) + (S * c) @ S.T
 
 
+def lmp_split_coeffs(D, theta):
+    """s_i = sqrt(theta) (1 + lambda_i(A))^{-1/2} - 1: the factor
+    U_theta = U_theta^T = I + S_k diag(s) S_k^T of P_theta = U_theta U_theta^T
+    (Section 3.1, Eq. (lmp))."""
+    return np.sqrt(theta) / np.sqrt(1.0 + D) - 1.0
+
+
 # ---------------------------------------------------------------------------
 # Preconditioned CG (Section 2.3), all members at once
 # ---------------------------------------------------------------------------
@@ -517,6 +538,21 @@ def pcg(apply_h, b, precond=None, tol=1e-6, maxit=100, x0=None, fixed_iters=None
     if fixed_iters is not None:
         status[:] = np.where(status == BREAKDOWN, BREAKDOWN, CONVERGED)
     return {"x": x, "iters": iters, "relres": relres, "status": status, "J": Jhist}
+
+
+def pcg_split(apply_h, b, S, s, tol=1e-6, maxit=100, fixed_iters=None):
+    """CG on the split-preconditioned system U H U y = U b, x = U y, with the
+    symmetric factor U = I + S diag(s) S^T of P = U U^T (Section 3.1, Eq.
+    (lmp)).  In exact arithmetic x_i equals the i-th iterate of pcg with P.
+    The stopping test is CG's own: ||U (b - H x_i)|| / ||U b|| <= tol.
+    Returns pcg's dict with x mapped back (J is the same cost: 1/2 y^T U H U y
+    - (U b)^T y = J(U y))."""
+    U = lambda R: lmp_apply(S, s, R)
+    res = pcg(lambda V: U(apply_h(U(V))), U(np.asarray(b, dtype=np.float64)), None, tol=tol, maxit=maxit,
+              fixed_iters=fixed_iters)
+    res["y"] = res["x"]
+    res["x"] = U(res["y"])
+    return res
 
 
 # ---------------------------------------------------------------------------

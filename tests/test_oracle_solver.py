@@ -389,3 +389,33 @@ def test_nystrom_truncated_evd_when_the_sketch_is_rank_deficient():
     # and A_N <= A: no eigenvalue exceeds A's
     lamA = np.sort(np.linalg.eigvalsh(0.5 * (A + A.T)))[::-1]
     assert (D <= lamA[: len(D)] * (1 + 1e-8) + 1e-10 * lamA[0]).all()
+
+
+def test_split_preconditioner_factor_and_iterates():
+    # Section 3.1, Eq. (lmp): U_theta = U_theta^T with U U = P_theta, and CG
+    # on U H U y = U b gives x = U y equal to the PCG iterates with P_theta
+    # (U K_i(U H U, U b) = K_i(P H, P b), and the U H U-norm of y - y* is the
+    # H-norm of x - x*), so both minimise the same error on the same space
+    spec, taps, xb, y, traj = tiny_problem(seed=9)
+    b = O.rhs(spec, traj, O.innovations(spec, traj, y), taps)
+    f = control_apply(spec, traj, taps)
+    Sk, D, _ = O.nystrom(f, O.gamma(b)[:, : spec.ell], spec.k)
+    for mode in (0, 1, 2):
+        theta = O.theta_value(mode, D, 2.5)
+        c = O.lmp_coeffs(D, theta)
+        s = O.lmp_split_coeffs(D, theta)
+        U = O.lmp_dense(Sk, s)
+        Pm = O.lmp_dense(Sk, c)
+        assert np.abs(U - U.T).max() <= 1e-14
+        assert np.abs(U @ U - Pm).max() <= 1e-12 * np.abs(Pm).max()
+        hv = lambda V: O.hvp(spec, traj, V, taps)
+        for K in (1, 3, 6):
+            a = O.pcg(hv, b, lambda R: O.lmp_apply(Sk, c, R), tol=0, maxit=K, fixed_iters=K)
+            bsp = O.pcg_split(hv, b, Sk, s, tol=0, maxit=K, fixed_iters=K)
+            err = np.linalg.norm(bsp["x"] - a["x"], axis=1) / np.linalg.norm(a["x"], axis=1)
+            assert err.max() <= 1e-9, (mode, K, err.max())
+            np.testing.assert_allclose(np.array(bsp["J"]), np.array(a["J"]), rtol=1e-9, atol=1e-12)
+    ref = np.stack([np.linalg.solve(np.eye(spec.n) + O.dense_A(spec, traj[m], taps), b[m])
+                    for m in range(spec.n_members)])
+    res = O.pcg_split(hv, b, Sk, s, tol=1e-13, maxit=300)
+    assert (np.linalg.norm(res["x"] - ref, axis=1) / np.linalg.norm(ref, axis=1)).max() <= 1e-10
