@@ -229,6 +229,74 @@ EDA_API int eda_solve_batch(eda_handle* h, double tol, int maxit, const double* 
                             double* relres_out, int* status_out);
 
 /*
+ * Options of eda_solve.  Zero-initialise the struct, then set the fields you
+ * need; with every field 0 but maxit it runs exactly maxit iterations.
+ *
+ *  tol        stop member j when ||r_j|| / ||b_j|| <= tol on the recurrence
+ *             residual (the paper's system, Section 2.3); 0 = off.
+ *  err_tol    stop member j when ||r_j|| / (||x_j|| - ||r_j||) <= err_tol.
+ *             Since every eigenvalue of I + A is >= 1 (Section 2.3),
+ *             ||x - x*|| <= ||r|| and ||x*|| >= ||x|| - ||r||, so this is a
+ *             certified bound on the relative error ||x_j - x*_j|| /
+ *             ||x*_j||; the FP64 true residual b - (I + A) x confirms it at
+ *             exit (members whose true bound misses it go on).  0 = off.
+ *             With both tol and err_tol set, a member stops when both hold.
+ *  maxit      iteration budget per member (refinement rounds included).
+ *  use_lmp    precondition with the LMP (requires eda_build_lmp or
+ *             eda_set_lmp).
+ *  split      1: the split preconditioner P_theta = U_theta U_theta^T
+ *             (Section 3.1, Eq. (lmp)): CG on U H U y = U b, x = U y, which
+ *             has the same iterates as PCG with P_theta in exact arithmetic;
+ *             its stopping test is on its own residual U (b - H x) relative
+ *             to U b.  Requires use_lmp, EDA_FP64 and lmp_kind 0 (an error
+ *             in U v is multiplied by the leading eigenvalues of H before U
+ *             damps them again); err_tol must be 0.
+ *  lmp_kind   0: the LMP on CUDA cores, in FP64 (EDA_FP64) or FP32
+ *             (EDA_MIXED); 1: on tensor cores, S and the vectors split into
+ *             BF16 high and low parts, three products with FP32
+ *             accumulation (relative error of the LMP correction ~1e-5);
+ *             k <= 128.
+ *  x0         [(L+1) x n] initial guess (host or device), NULL = 0.
+ *  cost_out   [(L+1) x (maxit+1)] FP64 (host or device) or NULL: the
+ *             quadratic cost J(x_i) = 1/2 x_i^T (I + A) x_i - b^T x_i of every
+ *             iterate (Section 2, Eq. (2) up to its constant), i = 0 first,
+ *             from the recurrence residual (J = -x^T (b + r) / 2); NaN after
+ *             a member's last iteration.
+ */
+typedef struct {
+  double tol;
+  double err_tol;
+  int maxit;
+  int use_lmp;
+  int split;
+  int lmp_kind;
+  const double* x0;
+  double* cost_out;
+} eda_solve_opts;
+
+/*
+ * Batched PCG with options (see eda_solve_opts); otherwise as
+ * eda_solve_batch.  err_bound_out [L+1] (may be NULL) receives the certified
+ * bound ||r|| / (||x|| - ||r||) of the FP64 true residual at exit (NaN when
+ * no true residual was taken: EDA_FP64 with err_tol = 0 and err_bound_out
+ * NULL takes none); relres_out then holds the true relative residual.
+ * EDA_ERR_INVALID on a NULL opts or dz_out, a negative tolerance or maxit.
+ */
+EDA_API int eda_solve(eda_handle* h, const eda_solve_opts* opts, double* dz_out, int* iters_out,
+                      double* relres_out, double* err_bound_out, int* status_out);
+
+/*
+ * The LMP on caller vectors (Section 3.1): Z[c] = R[c] + S_k diag(coef)
+ * S_k^T R[c] for c < ncol with coef the coefficients of which = 0: P_theta
+ * (theta / (1 + lambda_i) - 1), 1: U_theta (sqrt(theta) (1 + lambda_i)^{-1/2}
+ * - 1), 2: U_theta^{-1} (1 / (1 + those) - 1).  kind as lmp_kind of
+ * eda_solve_opts.  R, Z [ncol x n] FP64, host or device (Z may equal R).
+ * Requires eda_build_lmp or eda_set_lmp.  EDA_ERR_TIMEOUT if a bounded wait
+ * on the tensor core gave up (outputs then incomplete).
+ */
+EDA_API int eda_lmp_apply(eda_handle* h, int which, int kind, int ncol, const double* R, double* Z);
+
+/*
  * Control-variable transform (Section 2.3, Eq. (system with CVT)): OUT[c] =
  * U_B V[c] for c < ncol, U_B the handle's symmetric banded circulant square
  * root of B (taps bhalf_coef).  Maps solutions dz_j of eda_solve_batch to

@@ -37,13 +37,22 @@ EXPORTS = ["eda_version", "eda_last_error", "eda_create", "eda_destroy", "eda_tw
            "eda_ws_get_params", "eda_ws_set_scales", "eda_ws_get_scales", "eda_ws_loss_grad", "eda_ws_train",
            "eda_ws_infer", "eda_hvp_noalloc", "eda_hvp_noalloc_capacity", "eda_lmp_info",
            "eda_trace", "eda_trace_read", "eda_ws_init", "eda_sweep_plan", "eda_bhalf_apply",
-           "eda_plan_tiling"]
+           "eda_plan_tiling", "eda_solve", "eda_lmp_apply"]
 
 
 class EdaError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__("eda error %d: %s" % (code, msg))
         self.code = code
+
+
+class EdaSolveOpts(ctypes.Structure):
+    """eda_solve_opts of include/eda.h."""
+    _fields_ = [
+        ("tol", ctypes.c_double), ("err_tol", ctypes.c_double), ("maxit", ctypes.c_int),
+        ("use_lmp", ctypes.c_int), ("split", ctypes.c_int), ("lmp_kind", ctypes.c_int),
+        ("x0", ctypes.c_void_p), ("cost_out", ctypes.c_void_p),
+    ]
 
 
 class EdaConfig(ctypes.Structure):
@@ -110,6 +119,10 @@ def lib() -> ctypes.CDLL:
     L.eda_solve_batch.argtypes = [vp, d, i, vp, i, vp, vp, vp, vp]
     L.eda_hvp.restype = i
     L.eda_hvp.argtypes = [vp, vp, i, vp, vp, i]
+    L.eda_lmp_apply.restype = i
+    L.eda_lmp_apply.argtypes = [vp, i, i, i, vp, vp]
+    L.eda_solve.restype = i
+    L.eda_solve.argtypes = [vp, ctypes.POINTER(EdaSolveOpts), vp, vp, vp, vp, vp]
     L.eda_kernel_launches.restype = ctypes.c_longlong
     L.eda_kernel_launches.argtypes = []
     L.eda_autotune.restype = i
@@ -366,6 +379,27 @@ class Handle:
             self._h, float(tol), int(maxit), _ptr(x0, np.float64, M * n, "x0"), 1 if use_lmp else 0,
             _ptr(dz_out, np.float64, M * n, "dz_out"), _ptr(iters_out, np.int32, M, "iters_out"),
             _ptr(relres_out, np.float64, M, "relres_out"), _ptr(status_out, np.int32, M, "status_out")))
+
+    def eda_solve(self, dz_out, tol=0.0, err_tol=0.0, maxit=100, use_lmp=True, split=False, lmp_kind=0,
+                  x0=None, cost_out=None, iters_out=None, relres_out=None, err_bound_out=None, status_out=None):
+        """Batched PCG with the options of eda_solve_opts (certified error
+        stopping err_tol, cost record cost_out [(L+1) x (maxit+1)])."""
+        n, M = self.n, self.M
+        o = EdaSolveOpts(float(tol), float(err_tol), int(maxit), 1 if use_lmp else 0, 1 if split else 0,
+                         int(lmp_kind), _ptr(x0, np.float64, M * n, "x0"),
+                         _ptr(cost_out, np.float64, M * (int(maxit) + 1), "cost_out"))
+        self._check(self._L.eda_solve(
+            self._h, ctypes.byref(o), _ptr(dz_out, np.float64, M * n, "dz_out"),
+            _ptr(iters_out, np.int32, M, "iters_out"), _ptr(relres_out, np.float64, M, "relres_out"),
+            _ptr(err_bound_out, np.float64, M, "err_bound_out"), _ptr(status_out, np.int32, M, "status_out")))
+
+    def eda_lmp_apply(self, R, Z, which=0, kind=0):
+        """Z = R + S diag(coef) S^T R for every row of R: which 0 P_theta,
+        1 U_theta, 2 U_theta^{-1}; kind 0 CUDA cores, 1 tensor cores."""
+        ncol = int(R.shape[0])
+        self._check(self._L.eda_lmp_apply(self._h, int(which), int(kind), ncol,
+                                          _ptr(R, np.float64, ncol * self.n, "R"),
+                                          _ptr(Z, np.float64, ncol * self.n, "Z")))
 
     def eda_autotune(self, which=0):
         """Times the sweep tilings on the stored trajectories, keeps the fastest."""

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "handle.h"
+#include "lmp.h"
 
 namespace eda {
 namespace {
@@ -292,17 +293,27 @@ __global__ void iota_kernel(int count, int* v, int value_mode) {
     v[i] = value_mode ? i : 0;
 }
 
-// first inner threshold of the mixed solve: max(tol, tau * relres0)
-__global__ void set_tolm_kernel(int M, PcgScalars* sc, double tol, double tau) {
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x)
-    sc[j].tolm = fmax(tol, tau * sc[j].relres);
+// Inner threshold of a refinement round of the mixed solve: the round
+// reduces its residual by tau, and needs no less than tol when tol is the
+// only criterion (with a certified error bound asked for, the bound may
+// need a residual below tol, so no floor then).
+__device__ __forceinline__ double inner_tol(double tol, double etol, double tau, double rel) {
+  return etol > 0.0 ? tau * rel : fmax(tol, tau * rel);
 }
 
-__global__ void export_kernel(int M, const PcgScalars* sc, int* iters, double* relres, int* status) {
+// first inner threshold of the mixed solve
+__global__ void set_tolm_kernel(int M, PcgScalars* sc, double tol, double etol, double tau) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x)
+    sc[j].tolm = inner_tol(tol, etol, tau, sc[j].relres);
+}
+
+__global__ void export_kernel(int M, const PcgScalars* sc, int* iters, double* relres, int* status,
+                              double* errb) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < M; j += gridDim.x * blockDim.x) {
     if (iters) iters[j] = sc[j].iters;
     if (relres) relres[j] = sc[j].relres;
     if (status) status[j] = sc[j].status;
+    if (errb) errb[j] = sc[j].errb;
   }
 }
 
@@ -314,21 +325,78 @@ __global__ void eig_kernel(int k, const double* D, double* out) {
 // FP64 true residual r = b - H x of every member; a member whose true
 // residual misses tol is reactivated with the next inner threshold
 // max(tol, tau * true relres).
-__global__ void true_res_kernel(int n, const double* b, const double* hx, float* r32, double* r64,
-                                PcgScalars* sc, int* active, double tol, int* nactive, int* need, double tau,
-                                int maxit) {
+// true-residual bookkeeping of the mixed solve (and of the FP64 solve when a
+// certified bound is asked for): FP64 true residual r = b - H x of every
+// member, its relative norm and the certified error bound
+// ||r|| / (||x|| - ||r||) >= ||x - x*|| / ||x*|| (lambda_min(I + A) >= 1,
+// Section 2.3).  A member that met its inner threshold but whose true
+// residual misses a requested criterion (tol > 0 on ||r||/||b||, etol > 0
+// on the bound) is reactivated, with the next inner threshold
+// inner_tol(tol, etol, tau, true relres) when tau > 0 (none otherwise).
+__global__ void true_res_kernel(int n, const double* b, const double* hx, const double* x, float* r32,
+                                double* r64, PcgScalars* sc, int* active, double tol, double etol, int* nactive,
+                                int* need, double tau, int maxit) {
   __shared__ double red[32];
+  __shared__ double redx[32];
   const int j = blockIdx.x;
   const double* bj = b + (long long)j * n;
   const double* hj = hx + (long long)j * n;
+  const double* xj = x + (long long)j * n;
   float* rj = r32 ? r32 + (long long)j * n : nullptr;
   double* rj64 = r64 + (long long)j * n;
-  double s = 0.0;
+  double s = 0.0, sx = 0.0;
   for (int g = threadIdx.x; g < n; g += blockDim.x) {
     const double rv = bj[g] - hj[g];
     if (rj) rj[g] = (float)rv;
     rj64[g] = rv;
     s += rv * rv;
+    sx += xj[g] * xj[g];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_down_sync(0xffffffffu, s, o);
+    sx += __shfl_down_sync(0xffffffffu, sx, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[threadIdx.x >> 5] = s;
+    redx[threadIdx.x >> 5] = sx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0, tx = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      t += red[i];
+      tx += redx[i];
+    }
+    const double bn = sc[j].bnorm;
+    const double rn = sqrt(t), xn = sqrt(tx);
+    const double rel = bn > 0.0 ? rn / bn : 0.0;
+    const double errb = (bn == 0.0) ? 0.0 : (xn > rn ? rn / (xn - rn) : __longlong_as_double(0x7ff0000000000000ll));
+    sc[j].relres = rel;
+    sc[j].errb = errb;
+    const bool ok = (bn == 0.0) || ((!(tol > 0.0) || rel <= tol) && (!(etol > 0.0) || errb <= etol));
+    if (sc[j].status == EDA_CONVERGED && !ok) {
+      // the inner solve met its threshold but the FP64 residual misses a
+      // criterion: next refinement round, while the member has iterations left
+      sc[j].status = EDA_MAXIT;
+      if (sc[j].iters < maxit) {
+        sc[j].tolm = tau > 0.0 ? inner_tol(tol, etol, tau, rel) : 0.0;
+        active[j] = 1;
+        atomicAdd(nactive, 1);
+        atomicAdd(need, 1);
+      }
+    }
+  }
+}
+
+// sc[j].bnorm = ||b_j|| (the split solve's true residual is relative to b)
+__global__ void bnorm_kernel(int n, const double* b, PcgScalars* sc) {
+  __shared__ double red[32];
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < n; g += blockDim.x) {
+    const double v = b[(long long)j * n + g];
+    s += v * v;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
@@ -337,21 +405,29 @@ __global__ void true_res_kernel(int n, const double* b, const double* hx, float*
   if (threadIdx.x == 0) {
     double t = 0.0;
     for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
-    const double bn = sc[j].bnorm;
-    const double rel = bn > 0.0 ? sqrt(t) / bn : 0.0;
-    sc[j].relres = rel;
-    const bool ok = (bn == 0.0) || (rel <= tol);
-    if (sc[j].status == EDA_CONVERGED && !ok) {
-      // the inner solve met its threshold but the FP64 residual misses tol:
-      // next refinement round, while the member has iterations left
-      sc[j].status = EDA_MAXIT;
-      if (sc[j].iters < maxit) {
-        sc[j].tolm = fmax(tol, tau * rel);
-        active[j] = 1;
-        atomicAdd(nactive, 1);
-        atomicAdd(need, 1);
-      }
-    }
+    sc[j].bnorm = sqrt(t);
+  }
+}
+
+// J(x0) = -x0^T (b + r0) / 2 into the first entry of each member's cost
+// record (the record is NaN elsewhere until the iterations fill it)
+__global__ void cost0_kernel(int n, const double* x, const double* b, const double* r, double* jhist,
+                             long long jstride) {
+  __shared__ double red[32];
+  const int j = blockIdx.x;
+  double s = 0.0;
+  for (int g = threadIdx.x; g < n; g += blockDim.x) {
+    const long long i = (long long)j * n + g;
+    s += x[i] * (b[i] + r[i]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    jhist[(long long)j * jstride] = -0.5 * t;
   }
 }
 
@@ -1248,6 +1324,7 @@ EDA_API int eda_build_lmp(eda_handle* h, double* eigvals_out, double* s_out) {
   CU(h, os.finish());
   if (oe.host || os.host) CU(h, cudaStreamSynchronize(h->st));
   h->have_lmp = true;
+  ++h->lmp_version;
   return EDA_OK;
 }
 
@@ -1286,6 +1363,7 @@ EDA_API int eda_set_lmp(eda_handle* h, const double* s_in, const double* eigvals
   h->lmp_rank = h->k;
   h->shift_used = 0.0;
   h->have_lmp = true;
+  ++h->lmp_version;
   return EDA_OK;
 }
 
@@ -1340,6 +1418,114 @@ EDA_API int eda_lmp_info(eda_handle* h, int* path, int* rank, double* shift) {
 
 namespace {
 
+// How a PCG loop applies the LMP (see pcg_loop_t).
+struct LoopMode {
+  bool split = false;  // CG on U H U with U = U_theta applied around each product
+  bool tc = false;     // the LMP on tensor cores (split-BF16) instead of CUDA cores
+};
+
+__global__ void ucoef_kernel(int k, const double* c, double* uv) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+    const double a = sqrt(1.0 + c[i]);  // 1 + c_i = theta / (1 + lambda_i) > 0
+    uv[i] = a - 1.0;
+    uv[k + i] = 1.0 / a - 1.0;
+  }
+}
+
+// Coefficients of U_theta (sqrt(theta) (1 + lambda_i)^{-1/2} - 1, Section
+// 3.1, Eq. (lmp)) and of its inverse, for the current LMP.
+int prep_ucoef(eda_handle* h) {
+  if (h->uv_version == h->lmp_version) return EDA_OK;
+  if (!h->uv) CU(h, dalloc(h, &h->uv, (size_t)2 * std::max(h->k, 1)));
+  eda::count_launch();
+  ucoef_kernel<<<1, 128, 0, h->st>>>(h->k, h->cv, h->uv);
+  CU(h, cudaGetLastError());
+  h->uv_version = h->lmp_version;
+  return EDA_OK;
+}
+
+// BF16 high/low copies of S for the tensor-core LMP, for the current LMP.
+int prep_bf16(eda_handle* h) {
+  if (h->bf_version == h->lmp_version) return EDA_OK;
+  const size_t one = (size_t)eda::lmp_tc_kt(h->k) * eda::lmp_tc_ns(h->n);
+  if (!h->Sbf) {
+    __nv_bfloat16* p = nullptr;
+    CU(h, dalloc(h, &p, 4 * one));
+    h->Sbf = p;
+  }
+  __nv_bfloat16* b = static_cast<__nv_bfloat16*>(h->Sbf);
+  CU(h, eda::split_bf16(h->n, h->k, h->S, b, b + one, b + 2 * one, b + 3 * one, h->st));
+  h->bf_version = h->lmp_version;
+  return EDA_OK;
+}
+
+// Z = R + S diag(coef) S^T R for ncol vectors (device memory, Z may alias
+// R; columns with active[c] == 0 untouched when active != nullptr): which 0
+// applies P_theta, 1 U_theta, 2 U_theta^{-1}; kind 0 on CUDA cores in the
+// handle's LMP precision (FP64, or FP32 in EDA_MIXED), kind 1 split-BF16 on
+// tensor cores.
+int lmp_apply_dev(eda_handle* h, int which, int kind, int ncol, const double* R, double* Z, const int* active) {
+  if (ncol <= 0) return EDA_OK;
+  const int n = h->n, k = h->k;
+  if (which != 0) {
+    int rc = prep_ucoef(h);
+    if (rc) return rc;
+  }
+  const double* coef = which == 0 ? h->cv : (which == 1 ? h->uv : h->uv + k);
+  if (kind == 0) {
+    const bool f64 = h->precision == EDA_FP64;
+    const long long need = (long long)ncol * std::max(k, 1) * (f64 ? 8 : 4);
+    if (need > h->wcc_cap) {
+      if (h->Wcc) cudaFree(h->Wcc);
+      for (auto& p : h->allocs)
+        if (p == h->Wcc) p = nullptr;
+      h->Wcc = nullptr;
+      h->wcc_cap = 0;
+      CU(h, cudaMalloc(&h->Wcc, (size_t)need));
+      h->wcc_cap = need;
+    }
+    if (f64)
+      CU(h, eda::lmp_apply_cc<double>(n, k, h->S, coef, ncol, R, Z, active, static_cast<double*>(h->Wcc), k, h->st));
+    else
+      CU(h, eda::lmp_apply_cc<float>(n, k, h->S32, coef, ncol, R, Z, active, static_cast<float*>(h->Wcc), k, h->st));
+    return EDA_OK;
+  }
+  int rc = prep_bf16(h);
+  if (rc) return rc;
+  const long long need = (long long)((ncol + 15) / 16 * 16) * eda::lmp_tc_kt(k);
+  if (need > h->wtc_cap) {
+    if (h->Wtc) cudaFree(h->Wtc);
+    for (auto& p : h->allocs)
+      if (p == (void*)h->Wtc) p = nullptr;
+    h->Wtc = nullptr;
+    h->wtc_cap = 0;
+    CU(h, cudaMalloc((void**)&h->Wtc, (size_t)need * sizeof(float)));
+    h->wtc_cap = need;
+  }
+  if (!h->tc_timeout) {
+    CU(h, dalloc(h, &h->tc_timeout, 1));
+    CU(h, cudaMemsetAsync(h->tc_timeout, 0, sizeof(int), h->st));
+  }
+  const size_t one = (size_t)eda::lmp_tc_kt(k) * eda::lmp_tc_ns(n);
+  const __nv_bfloat16* b = static_cast<const __nv_bfloat16*>(h->Sbf);
+  CU(h, eda::lmp_apply_tc(n, k, b, b + one, b + 2 * one, b + 3 * one, coef, ncol, R, Z, active, h->Wtc,
+                          h->tc_timeout, h->st));
+  return EDA_OK;
+}
+
+// A tensor-core wait that gave up (read after the stream synchronised).
+int check_tc_timeout(eda_handle* h) {
+  if (!h->tc_timeout) return EDA_OK;
+  int t = 0;
+  int rc = read_flag(h, h->tc_timeout, &t);
+  if (rc) return rc;
+  if (t) {
+    CU(h, cudaMemsetAsync(h->tc_timeout, 0, sizeof(int), h->st));
+    return fail(h, EDA_ERR_TIMEOUT, "tensor-core LMP: a bounded wait for the MMA gave up");
+  }
+  return EDA_OK;
+}
+
 // PCG iterations from the current (x, r) state (the caller has run
 // pcg_start): FP64 vectors and scalars; sweeps in FP64 (sweep64) or FP32,
 // LMP arithmetic in FP64 or FP32 accordingly.  One iteration is the sweep
@@ -1349,18 +1535,28 @@ namespace {
 // runs at most kRing-1 iterations ahead of the device.
 template <typename TS>
 int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done, bool sweep64,
-               int replace_every) {
+               int replace_every, const LoopMode& lm) {
   const int M = h->M;
-  const int fixed = (tol > 0.0) ? 0 : maxit;
-  const int lmp = use_lmp ? 1 : 0;
+  // no stopping criterion at all (tol = 0, no error bound): exactly maxit iterations
+  const int fixed = (tol > 0.0 || h->pgrid.one.etol > 0.0) ? 0 : maxit;
+  // the LMP inside the row-chunk kernels (CUDA cores), or z = P r by a
+  // separate tensor-core launch pair, or (split) no preconditioner in the
+  // kernels and U applied around every product
+  const int lmp = (use_lmp && !lm.split && !lm.tc) ? 1 : 0;
+  const bool zext = use_lmp && lm.tc && !lm.split;
+  const int kind = lm.tc ? 1 : 0;
   const int kmax = std::max(h->k, 1);
   TS* Wk = reinterpret_cast<TS*>(h->Wk);
   // start: z = P r, p = z, r.z
   CU(h, eda::pcg2_reset(h->acc, M, Wk, (size_t)M * kmax * sizeof(TS), h->st));
   CU(h, eda::pcg2_update<TS>(h->pgrid, kmax, M, h->pv, h->q, h->x, h->r, h->sc, h->acc, h->active,
                              Wk, 0, 0, lmp, h->nactive, h->st));
+  if (zext) {
+    int rc = lmp_apply_dev(h, 0, 1, M, h->r, h->z, h->active);
+    if (rc) return rc;
+  }
   CU(h, eda::pcg2_precond<TS>(h->pgrid, kmax, M, h->r, h->z, h->pv, h->sc, h->acc, h->active, Wk,
-                              0, tol, maxit, fixed, lmp, 1, h->nactive, h->st));
+                              0, tol, maxit, fixed, lmp, 1, h->nactive, h->st, zext ? h->z : nullptr));
   // the first update accumulates the projections of r_1 from zero
   CU(h, cudaMemsetAsync(Wk, 0, (size_t)M * kmax * sizeof(TS), h->st));
   constexpr int R = eda_handle::kRing;
@@ -1370,7 +1566,18 @@ int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int*
   while (it - it0 < maxit) {
     const int par = (it - it0) & 1;
     ++it;
-    int rc = hvp_dev(h, h->cols, M, h->pv, h->q, 1, sweep64, h->active, reinterpret_cast<double*>(h->acc));
+    int rc;
+    if (lm.split) {
+      // q^ = U H U p^ (U symmetric); the sweep's epilogue adds
+      // (U p^).(H U p^) = p^.q^ to the accumulators
+      rc = lmp_apply_dev(h, 1, kind, M, h->pv, h->tbuf, h->active);
+      if (rc) return rc;
+      rc = hvp_dev(h, h->cols, M, h->tbuf, h->q, 1, sweep64, h->active, reinterpret_cast<double*>(h->acc));
+      if (rc) return rc;
+      rc = lmp_apply_dev(h, 1, kind, M, h->q, h->q, h->active);
+    } else {
+      rc = hvp_dev(h, h->cols, M, h->pv, h->q, 1, sweep64, h->active, reinterpret_cast<double*>(h->acc));
+    }
     if (rc) return rc;
     CU(h, eda::pcg2_update<TS>(h->pgrid, kmax, M, h->pv, h->q, h->x, h->r, h->sc, h->acc,
                                h->active, Wk, par, 1, lmp, h->nactive, h->st));
@@ -1385,8 +1592,12 @@ int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int*
       CU(h, eda::pcg2_update<TS>(h->pgrid, kmax, M, h->pv, h->q, h->x, h->r, h->sc, h->acc,
                                  h->active, Wk, par, 0, lmp, h->nactive, h->st));
     }
+    if (zext) {
+      rc = lmp_apply_dev(h, 0, 1, M, h->r, h->z, h->active);
+      if (rc) return rc;
+    }
     CU(h, eda::pcg2_precond<TS>(h->pgrid, kmax, M, h->r, h->z, h->pv, h->sc, h->acc, h->active,
-                                Wk, par, tol, maxit, fixed, lmp, 0, h->nactive, h->st));
+                                Wk, par, tol, maxit, fixed, lmp, 0, h->nactive, h->st, zext ? h->z : nullptr));
     const int slot = it % R;
     CU(h, eda::pcg2_dir<TS>(h->pgrid, kmax, M, h->z, h->pv, h->sc, h->acc, h->active, Wk, par,
                             h->st, h->nactive, h->hring + slot));
@@ -1403,30 +1614,93 @@ int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int*
 }
 
 int pcg_loop(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int* it_done, bool sweep64,
-             int replace_every = 0) {
+             int replace_every = 0, LoopMode lm = LoopMode{}) {
   // the LMP arithmetic follows the sweeps: FP64, or FP32 with the FP32 copy of S
-  if (sweep64) return pcg_loop_t<double>(h, tol, maxit, it0, use_lmp, it_done, true, 0);
-  return pcg_loop_t<float>(h, tol, maxit, it0, use_lmp, it_done, false, replace_every);
+  if (sweep64) return pcg_loop_t<double>(h, tol, maxit, it0, use_lmp, it_done, true, 0, lm);
+  return pcg_loop_t<float>(h, tol, maxit, it0, use_lmp, it_done, false, replace_every, lm);
 }
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-EDA_API int eda_solve_batch(eda_handle* h, double tol, int maxit, const double* x0, int use_lmp, double* dz_out,
-                            int* iters_out, double* relres_out, int* status_out) {
+// Options of one batched solve (eda_solve; eda_solve_batch fills tol, maxit,
+// use_lmp and x0 only).
+struct SolveOpts {
+  double tol = 0.0, etol = 0.0;
+  int maxit = 0, use_lmp = 0, split = 0, lmp_kind = 0;
+  const double* x0 = nullptr;
+  double* cost = nullptr;
+};
+
+int solve_impl(eda_handle* h, const SolveOpts& o, double* dz_out, int* iters_out, double* relres_out,
+               double* errb_out, int* status_out) {
   if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
-  if (!h->have_traj) return fail(h, EDA_ERR_STATE, "eda_solve_batch before eda_set_trajectory");
-  if (use_lmp && !h->have_lmp) return fail(h, EDA_ERR_STATE, "eda_solve_batch with use_lmp before eda_build_lmp");
-  if (!dz_out || maxit < 0 || !(tol >= 0.0)) return fail(h, EDA_ERR_INVALID, "eda_solve_batch: invalid argument");
+  if (!h->have_traj) return fail(h, EDA_ERR_STATE, "solve before eda_set_trajectory");
+  if (o.use_lmp && !h->have_lmp) return fail(h, EDA_ERR_STATE, "solve with use_lmp before eda_build_lmp");
+  if (!dz_out || o.maxit < 0 || !(o.tol >= 0.0) || !(o.etol >= 0.0))
+    return fail(h, EDA_ERR_INVALID, "solve: invalid argument (dz_out NULL, maxit < 0 or a negative tolerance)");
+  if (o.lmp_kind != 0 && o.lmp_kind != 1) return fail(h, EDA_ERR_INVALID, "solve: lmp_kind must be 0 or 1");
+  if (o.lmp_kind == 1 && h->k > 128) return fail(h, EDA_ERR_INVALID, "solve: the tensor-core LMP takes k <= 128");
+  if (o.split != 0) {
+    if (!o.use_lmp) return fail(h, EDA_ERR_INVALID, "solve: the split preconditioner needs use_lmp");
+    if (h->precision != EDA_FP64) return fail(h, EDA_ERR_INVALID, "solve: the split preconditioner is FP64 only");
+    if (o.etol > 0.0) return fail(h, EDA_ERR_INVALID, "solve: err_tol is not available with the split preconditioner");
+    // an error e in U v reaches H's leading eigenvalues before U damps them
+    // again, so the split iteration needs an LMP accurate to working precision
+    if (o.lmp_kind != 0) return fail(h, EDA_ERR_INVALID, "solve: the split preconditioner takes lmp_kind 0");
+  }
   const int n = h->n, M = h->M;
   const size_t vb = (size_t)M * n * sizeof(double);
+  const LoopMode lm{o.split != 0, o.use_lmp && o.lmp_kind == 1};
+  if (lm.tc && h->tc_timeout) CU(h, cudaMemsetAsync(h->tc_timeout, 0, sizeof(int), h->st));
+  const long long jstride = (long long)o.maxit + 1;
   In ix0;
-  CU(h, ix0.init(x0, vb, h->st));
+  CU(h, ix0.init(o.x0, vb, h->st));
+  Out ocost;
+  CU(h, ocost.init(o.cost, o.cost ? (size_t)M * jstride * sizeof(double) : 0, h->st));
+  // the solve's options travel with the problem to the PCG kernels
+  h->pgrid.one.etol = o.etol;
+  h->pgrid.one.b = h->b;
+  h->pgrid.one.jhist = static_cast<double*>(ocost.dev);
+  h->pgrid.one.jstride = (int)jstride;
+  struct Reset {  // the handle's other solves run without them
+    eda_handle* h;
+    ~Reset() {
+      h->pgrid.one.etol = 0.0;
+      h->pgrid.one.jhist = nullptr;
+      h->pgrid.one.b = h->b;
+    }
+  } reset{h};
   CU(h, cudaMemsetAsync(h->nactive, 0, sizeof(int), h->st));
-  // x = x0 (or 0), r = b - H x0: with the sweeps of the handle's precision
-  // (in EDA_MIXED the FP64 true residual at the end checks the result)
-  if (x0) {
+  const double* bsys = h->b;  // right-hand side of the system CG runs on
+  if (lm.split) {
+    // CG on U H U y = U b (U = U_theta, Section 3.1, Eq. (lmp)); x = U y at
+    // the end.  b^ = U b; from x0: y0 = U^{-1} x0 and r^0 = U (b - H x0)
+    if (!h->bh) CU(h, dalloc(h, &h->bh, (size_t)M * n));
+    if (!h->tbuf) CU(h, dalloc(h, &h->tbuf, (size_t)M * n));
+    const int kind = o.lmp_kind;
+    int rc = lmp_apply_dev(h, 1, kind, M, h->b, h->bh, nullptr);
+    if (rc) return rc;
+    bsys = h->bh;
+    h->pgrid.one.b = h->bh;  // the cost record: J(U y) = -y^T (b^ + r^) / 2
+    if (o.x0) {
+      rc = hvp_dev(h, h->cols, M, static_cast<const double*>(ix0.dev), h->q, 1, true, nullptr);
+      if (rc) return rc;
+      eda::count_launch();
+      sub_kernel<double><<<grid_for((long long)M * n), 256, 0, h->st>>>((long long)M * n, h->b, h->q, h->tbuf);
+      CU(h, cudaGetLastError());
+      rc = lmp_apply_dev(h, 1, kind, M, h->tbuf, h->r, nullptr);
+      if (rc) return rc;
+      rc = lmp_apply_dev(h, 2, kind, M, static_cast<const double*>(ix0.dev), h->x, nullptr);
+      if (rc) return rc;
+    } else {
+      CU(h, cudaMemsetAsync(h->x, 0, vb, h->st));
+      CU(h, cudaMemcpyAsync(h->r, h->bh, vb, cudaMemcpyDeviceToDevice, h->st));
+    }
+  } else if (o.x0) {
+    // x = x0, r = b - H x0: with the sweeps of the handle's precision (in
+    // EDA_MIXED the FP64 true residual at the end checks the result)
     CU(h, cudaMemcpyAsync(h->x, ix0.dev, vb, cudaMemcpyDeviceToDevice, h->st));
     int rc = hvp_dev(h, h->cols, M, h->x, h->q, 1, h->precision == EDA_FP64, nullptr);
     if (rc) return rc;
@@ -1437,64 +1711,168 @@ EDA_API int eda_solve_batch(eda_handle* h, double tol, int maxit, const double* 
     CU(h, cudaMemcpyAsync(h->r, h->b, vb, cudaMemcpyDeviceToDevice, h->st));
   }
   CU(h, cudaGetLastError());
-  CU(h, eda::pcg_start<double>(n, M, h->b, h->r, h->sc, h->active, tol, h->nactive, h->st));
-  const bool lmp = use_lmp != 0;
+  if (o.cost) {
+    // NaN (all bits set) where no iterate is recorded; J(x0) first
+    CU(h, cudaMemsetAsync(ocost.dev, 0xff, (size_t)M * jstride * sizeof(double), h->st));
+    eda::count_launch();
+    cost0_kernel<<<M, 256, 0, h->st>>>(n, h->x, bsys, h->r, static_cast<double*>(ocost.dev), jstride);
+    CU(h, cudaGetLastError());
+  }
+  CU(h, eda::pcg_start<double>(n, M, bsys, h->r, h->sc, h->active, o.tol, h->nactive, h->st));
+  const bool lmp = o.use_lmp != 0;
+  const int maxit = o.maxit;
+  const double tol = o.tol, etol = o.etol;
   int it = 0;
-  if (h->precision == EDA_FP64) {
-    int rc = pcg_loop(h, tol, maxit, 0, lmp, &it, true);
+  if (lm.split) {
+    int rc = pcg_loop(h, tol, maxit, 0, lmp, &it, true, 0, lm);
     if (rc) return rc;
+    rc = lmp_apply_dev(h, 1, o.lmp_kind, M, h->x, h->x, nullptr);  // x = U y
+    if (rc) return rc;
+    if (errb_out != nullptr) {
+      // the certified bound of the mapped solution (no further rounds: the
+      // stopping test of the split iteration is on U r)
+      rc = hvp_dev(h, h->cols, M, h->x, h->q, 1, true, nullptr);
+      if (rc) return rc;
+      CU(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
+      CU(h, cudaMemsetAsync(h->active, 0, (size_t)M * sizeof(int), h->st));
+      eda::count_launch(2);
+      bnorm_kernel<<<M, 256, 0, h->st>>>(n, h->b, h->sc);
+      true_res_kernel<<<M, 256, 0, h->st>>>(n, h->b, h->q, h->x, nullptr, h->r, h->sc, h->active, 0.0, 0.0,
+                                           h->nactive, h->dstatus, 0.0, maxit);
+      CU(h, cudaGetLastError());
+    }
+  } else if (h->precision == EDA_FP64) {
+    int rc = pcg_loop(h, tol, maxit, 0, lmp, &it, true, 0, lm);
+    if (rc) return rc;
+    // with a certified bound asked for (as a criterion or an output): the
+    // FP64 true residual at exit, and further rounds for members whose
+    // true bound misses err_tol (the recurrence residual drifts from it)
+    if (etol > 0.0 || errb_out != nullptr) {
+      for (int round = 0; round < 64; ++round) {
+        rc = hvp_dev(h, h->cols, M, h->x, h->q, 1, true, nullptr);
+        if (rc) return rc;
+        CU(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
+        eda::count_launch();
+        true_res_kernel<<<M, 256, 0, h->st>>>(n, h->b, h->q, h->x, nullptr, h->r, h->sc, h->active, tol, etol,
+                                             h->nactive, h->dstatus, 0.0, maxit);
+        CU(h, cudaGetLastError());
+        int need = 0;
+        rc = read_flag(h, h->dstatus, &need);
+        if (rc) return rc;
+        if (need == 0) break;
+        rc = pcg_loop(h, tol, maxit, it, lmp, &it, true, 0, lm);
+        if (rc) return rc;
+      }
+    }
   } else {
     // FP32 sweeps and FP32 LMP arithmetic; CG vectors, scalars and x in FP64.
     // Iterative refinement: every inner PCG reduces its own residual by tau,
     // then the FP64 true residual b - (I + A) x restarts the members that
-    // miss tol.  EDA_MIXED_REPLACE = r > 0 instead replaces the recurrence
-    // residual by the FP64 true one every r iterations without a restart;
-    // on the batched workload that needs as many iterations and costs the
-    // extra FP64 sweeps, so restarts are the default.
+    // miss a requested criterion.  EDA_MIXED_REPLACE = r > 0 instead
+    // replaces the recurrence residual by the FP64 true one every r
+    // iterations without a restart; on the batched workload that needs as
+    // many iterations and costs the extra FP64 sweeps, so restarts are the
+    // default.
     const char* taus = std::getenv("EDA_MIXED_INNER_TOL");
     const double tau = (taus && *taus) ? std::atof(taus) : 1e-3;
     const int rep = env_int("EDA_MIXED_REPLACE", 0);
-    if (rep <= 0 && tol > 0.0 && tau > 0.0) {
+    const bool crit = tol > 0.0 || etol > 0.0;
+    if (rep <= 0 && crit && tau > 0.0) {
       eda::count_launch();
-      set_tolm_kernel<<<1, 128, 0, h->st>>>(M, h->sc, tol, tau);
+      set_tolm_kernel<<<1, 128, 0, h->st>>>(M, h->sc, tol, etol, tau);
       CU(h, cudaGetLastError());
     }
-    int rc = pcg_loop(h, tol, maxit, 0, lmp, &it, false, rep);
+    int rc = pcg_loop(h, tol, maxit, 0, lmp, &it, false, rep, lm);
     if (rc) return rc;
     // FP64 residual replacement: true residual b - H x with FP64 sweeps;
-    // members whose true residual misses the tolerance restart from it.
+    // members whose true residual misses a criterion restart from it.
     for (int round = 0; round < 64; ++round) {
       rc = hvp_dev(h, h->cols, M, h->x, h->q, 1, true, nullptr);
       if (rc) return rc;
       CU(h, cudaMemsetAsync(h->dstatus, 0, sizeof(int), h->st));
       eda::count_launch();
-      true_res_kernel<<<M, 256, 0, h->st>>>(n, h->b, h->q, nullptr, h->r, h->sc, h->active,
-                                           tol > 0.0 ? tol : 1e300, h->nactive, h->dstatus,
-                                           tau > 0.0 ? tau : 0.0, maxit);
+      true_res_kernel<<<M, 256, 0, h->st>>>(n, h->b, h->q, h->x, nullptr, h->r, h->sc, h->active, tol, etol,
+                                           h->nactive, h->dstatus, tau > 0.0 ? tau : 0.0, maxit);
       CU(h, cudaGetLastError());
       int need = 0;
       rc = read_flag(h, h->dstatus, &need);
       if (rc) return rc;
-      if (need == 0 || tol <= 0.0) break;
-      rc = pcg_loop(h, tol, maxit, it, lmp, &it, false, rep);
+      if (need == 0 || !crit) break;
+      rc = pcg_loop(h, tol, maxit, it, lmp, &it, false, rep, lm);
       if (rc) return rc;
     }
   }
-  Out odz, oit, orr, ost;
+  Out odz, oit, orr, ost, oeb;
   CU(h, odz.init(dz_out, vb, h->st));
   CU(h, oit.init(iters_out, (size_t)M * sizeof(int), h->st));
   CU(h, orr.init(relres_out, (size_t)M * sizeof(double), h->st));
   CU(h, ost.init(status_out, (size_t)M * sizeof(int), h->st));
+  CU(h, oeb.init(errb_out, (size_t)M * sizeof(double), h->st));
   CU(h, cudaMemcpyAsync(odz.dev, h->x, vb, cudaMemcpyDeviceToDevice, h->st));
   eda::count_launch();
-  export_kernel<<<1, 256, 0, h->st>>>(M, h->sc, (int*)oit.dev, (double*)orr.dev, (int*)ost.dev);
+  export_kernel<<<1, 256, 0, h->st>>>(M, h->sc, (int*)oit.dev, (double*)orr.dev, (int*)ost.dev,
+                                      (double*)oeb.dev);
   CU(h, cudaGetLastError());
   CU(h, odz.finish());
   CU(h, oit.finish());
   CU(h, orr.finish());
   CU(h, ost.finish());
-  if (odz.host || oit.host || orr.host || ost.host) CU(h, cudaStreamSynchronize(h->st));
+  CU(h, oeb.finish());
+  CU(h, ocost.finish());
+  if (odz.host || oit.host || orr.host || ost.host || oeb.host || ocost.host) CU(h, cudaStreamSynchronize(h->st));
+  if (lm.tc) return check_tc_timeout(h);
   return EDA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+EDA_API int eda_solve_batch(eda_handle* h, double tol, int maxit, const double* x0, int use_lmp, double* dz_out,
+                            int* iters_out, double* relres_out, int* status_out) {
+  SolveOpts o;
+  o.tol = tol;
+  o.maxit = maxit;
+  o.use_lmp = use_lmp;
+  o.x0 = x0;
+  return solve_impl(h, o, dz_out, iters_out, relres_out, nullptr, status_out);
+}
+
+EDA_API int eda_lmp_apply(eda_handle* h, int which, int kind, int ncol, const double* R, double* Z) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (!h->have_lmp) return fail(h, EDA_ERR_STATE, "eda_lmp_apply before eda_build_lmp / eda_set_lmp");
+  if (which < 0 || which > 2 || kind < 0 || kind > 1 || ncol < 0 || (ncol > 0 && (!R || !Z)))
+    return fail(h, EDA_ERR_INVALID, "eda_lmp_apply: invalid argument");
+  if (kind == 1 && h->k > 128) return fail(h, EDA_ERR_INVALID, "eda_lmp_apply: the tensor-core LMP takes k <= 128");
+  if (ncol == 0) return EDA_OK;
+  const size_t bytes = (size_t)ncol * h->n * sizeof(double);
+  In ir;
+  Out oz;
+  CU(h, ir.init(R, bytes, h->st));
+  CU(h, oz.init(Z, bytes, h->st));
+  if (kind == 1 && h->tc_timeout) CU(h, cudaMemsetAsync(h->tc_timeout, 0, sizeof(int), h->st));
+  int rc = lmp_apply_dev(h, which, kind, ncol, static_cast<const double*>(ir.dev), static_cast<double*>(oz.dev),
+                         nullptr);
+  if (rc) return rc;
+  CU(h, oz.finish());
+  if (oz.host) CU(h, cudaStreamSynchronize(h->st));
+  if (kind == 1) return check_tc_timeout(h);
+  return EDA_OK;
+}
+
+EDA_API int eda_solve(eda_handle* h, const eda_solve_opts* opts, double* dz_out, int* iters_out,
+                      double* relres_out, double* err_bound_out, int* status_out) {
+  if (!opts) return fail(h, EDA_ERR_INVALID, "eda_solve: opts is NULL");
+  SolveOpts o;
+  o.tol = opts->tol;
+  o.etol = opts->err_tol;
+  o.maxit = opts->maxit;
+  o.use_lmp = opts->use_lmp;
+  o.split = opts->split;
+  o.lmp_kind = opts->lmp_kind;
+  o.x0 = opts->x0;
+  o.cost = opts->cost_out;
+  return solve_impl(h, o, dz_out, iters_out, relres_out, err_bound_out, status_out);
 }
 
 }  // extern "C"

@@ -439,6 +439,7 @@ __global__ void pcg_start_kernel(int n, ItemGeo ig, const double* b, const T* r,
     sc[j].iters = 0;
     sc[j].status = EDA_MAXIT;
     sc[j].tolm = 0.0;
+    sc[j].errb = __longlong_as_double(0x7ff8000000000000ll);
     const bool done = (bn == 0.0) || (tol > 0.0 && sc[j].relres <= tol);
     if (done) sc[j].status = EDA_CONVERGED;
     active[j] = done ? 0 : 1;

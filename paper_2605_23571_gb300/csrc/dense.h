@@ -15,8 +15,9 @@ struct PcgScalars {
   double relres;  // ||r|| / ||b||
   int iters;
   int status;
-  double tolm;    // per-member stopping threshold on ||r||/||b|| (0: the call's tol)
-  double pad;
+  double tolm;    // per-member inner threshold of a refinement round on ||r||/||b|| (0: none)
+  double errb;    // certified relative-error bound ||r|| / (||x|| - ||r||) of the last
+                  // FP64 true residual (NaN until one is taken)
 };
 
 template <typename TA, typename TB>

@@ -89,6 +89,20 @@ struct eda_handle {
   double shift_used = 0.0;
   int nystrom_path = 0;  // 0 Cholesky, 1 Appendix B shift, 2 truncated eigendecomposition
   int lmp_rank = 0;      // informative LMP modes (k, or k_eff on path 2)
+  // the LMP applied outside the fused PCG kernels (eda_lmp_apply, the split
+  // preconditioner, the tensor-core LMP): coefficients of U_theta and
+  // U_theta^{-1} [2k], the BF16 copies of S (hi, lo, and transposed), FP32 /
+  // TS projection scratch, the tensor-core wait flag; versions follow the LMP
+  int lmp_version = 0, uv_version = -1, bf_version = -1;
+  double* uv = nullptr;
+  void* Sbf = nullptr;          // 4 arrays of kt x nS BF16: Shi | Slo | ShiT | SloT
+  float* Wtc = nullptr;
+  long long wtc_cap = 0;        // floats
+  void* Wcc = nullptr;
+  long long wcc_cap = 0;        // bytes
+  int* tc_timeout = nullptr;
+  double* bh = nullptr;         // split PCG: U b
+  double* tbuf = nullptr;       // split PCG: U p
   SweepPlan plan64{}, plan32{};
   // warp-tiled plans of the Hessian-product sweeps (warp = 0: none; the
   // plans above serve then) and their observation tables

@@ -1,0 +1,500 @@
+// Batched application of the scaled spectral LMP P_theta and of its
+// symmetric factor U_theta (Section 3.1, Eq. (lmp)) to every member's
+// vector: Z = R + S diag(coef) S^T R, the two dense contractions of the PCG
+// iteration (S: n x k orthonormal columns, R: n x M, k <= 80, M <= 257).
+//
+// Two implementations of the same two launches (projections W = S^T R over
+// row chunks, then the expansion Z = R + S (coef o W)):
+//  * CUDA cores (lmp_apply_cc) in FP64, or FP32 with the FP32 copy of S;
+//  * tensor cores (lmp_apply_tc): tcgen05.mma kind::f16 with BF16 operands
+//    and FP32 accumulators in tensor memory.  Each operand x is split as
+//    x = hi + lo with hi = bf16(x), lo = bf16(x - hi) (16 significant bits
+//    together), and each product is taken as hi.hi + hi.lo + lo.hi into one
+//    accumulator (the dropped lo.lo term is 2^-16 below it).  Operands are
+//    staged by the CTA's threads into shared memory in the canonical
+//    K-major, no-swizzle layout (core matrices of 8 rows x 16 bytes), one
+//    thread issues the MMAs, an mbarrier (bounded wait) signals completion,
+//    and the epilogue reads the accumulator with tcgen05.ld.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "eda_internal.h"
+#include "lmp.h"
+
+namespace eda {
+namespace {
+
+constexpr int kRows = 128;  // rows of n per CTA (a row chunk)
+
+// ----------------------------------------------------------------- CUDA cores
+constexpr int kCcThreads = 256;
+constexpr int kCcWarps = kCcThreads / 32;
+constexpr int kSmRow = kRows + 1;  // padded shared row: lanes reading one row per mode do not collide
+
+template <typename TS>
+__device__ __forceinline__ void stage_chunk(const TS* S, int n, int k, int row0, int rows, TS* sm) {
+  for (int idx = threadIdx.x; idx < k * kRows; idx += kCcThreads) {
+    const int c = idx / kRows, i = idx - c * kRows;
+    sm[c * kSmRow + i] = i < rows ? S[(long long)c * n + row0 + i] : TS(0);
+  }
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(kCcThreads) lmp_proj_cc_kernel(int n, int k, const TS* S, int M, const double* R,
+                                                                 const int* active, TS* W, int kpad) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TS* Ssm = reinterpret_cast<TS*>(smraw);
+  TS* rsm = Ssm + (size_t)k * kSmRow;  // [warp][kRows]
+  const int row0 = blockIdx.x * kRows;
+  const int rows = min(kRows, n - row0);
+  stage_chunk<TS>(S, n, k, row0, rows, Ssm);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int m = blockIdx.y * kCcWarps + wid;
+  const bool live = m < M && (active == nullptr || active[m] != 0);
+  TS* rw = rsm + wid * kRows;
+  for (int i = lane; i < kRows; i += 32) rw[i] = (live && i < rows) ? (TS)R[(long long)m * n + row0 + i] : TS(0);
+  __syncthreads();
+  if (!live) return;
+  for (int c = lane; c < k; c += 32) {
+    const TS* sc = Ssm + c * kSmRow;
+    TS s0 = 0, s1 = 0;
+    for (int i = 0; i < kRows; i += 2) {
+      s0 += sc[i] * rw[i];
+      s1 += sc[i + 1] * rw[i + 1];
+    }
+    atomicAdd(&W[(long long)m * kpad + c], s0 + s1);
+  }
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(kCcThreads) lmp_expand_cc_kernel(int n, int k, const TS* S, const double* coef,
+                                                                   int M, const double* R, double* Z,
+                                                                   const int* active, const TS* W, int kpad) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  TS* Ssm = reinterpret_cast<TS*>(smraw);
+  TS* csm = Ssm + (size_t)k * kSmRow;  // [warp][k]: coef o w of the warp's member
+  const int row0 = blockIdx.x * kRows;
+  const int rows = min(kRows, n - row0);
+  stage_chunk<TS>(S, n, k, row0, rows, Ssm);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int m = blockIdx.y * kCcWarps + wid;
+  const bool live = m < M && (active == nullptr || active[m] != 0);
+  TS* cw = csm + wid * k;
+  if (live)
+    for (int c = lane; c < k; c += 32) cw[c] = (TS)(coef[c] * (double)W[(long long)m * kpad + c]);
+  __syncthreads();
+  if (!live) return;
+  for (int i = lane; i < rows; i += 32) {
+    TS s0 = 0, s1 = 0;
+    int c = 0;
+    for (; c + 2 <= k; c += 2) {
+      s0 += Ssm[c * kSmRow + i] * cw[c];
+      s1 += Ssm[(c + 1) * kSmRow + i] * cw[c + 1];
+    }
+    if (c < k) s0 += Ssm[c * kSmRow + i] * cw[c];
+    const long long g = (long long)m * n + row0 + i;
+    Z[g] = R[g] + (double)(s0 + s1);
+  }
+}
+
+// --------------------------------------------------------------- tensor cores
+constexpr int kTcThreads = 128;  // four warps: warp w reads TMEM lanes 32w..32w+31
+constexpr int kWaitLimit = 1 << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor of a K-major operand without swizzling:
+// core matrices of 8 rows x 16 bytes stored contiguously (128 bytes), lbo =
+// byte distance between core matrices adjacent along K, sbo = between
+// core matrices adjacent along M (or N).  Bits 46-48 hold the fixed 0b001 of
+// the tcgen05 descriptor format.
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, M = 128, N = nd.
+__device__ __forceinline__ uint32_t idesc_bf16(int nd) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nd >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+               : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+  for (int it = 0; it < kWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
+  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+}
+
+// 8 values -> the 16-byte core-matrix rows of their BF16 high and low parts.
+template <typename T>
+__device__ __forceinline__ void split8(const T (&x)[8], uint4* hi, uint4* lo) {
+  __nv_bfloat16 h[8], l[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const float xf = (float)x[e];
+    h[e] = __float2bfloat16_rn(xf);
+    l[e] = __float2bfloat16_rn((float)(x[e] - (T)__bfloat162float(h[e])));
+  }
+  *hi = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+  *lo = make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
+}
+
+// Byte offset of core-matrix row (r, 8-element group kb) of a K-major
+// operand with kg groups of 8 along K: core matrix (r / 8, kb) at
+// ((r / 8) * kg + kb) * 128, row r % 8 at 16 (r % 8).
+__device__ __forceinline__ uint32_t kmaj_off(int r, int kb, int kg) {
+  return (uint32_t)((((r >> 3) * kg + kb) << 7) + ((r & 7) << 4));
+}
+
+struct TmemCta {
+  uint32_t base;
+  int ncols;
+};
+
+// Allocates ncols TMEM columns (warp 0), publishes the base through slot.
+__device__ __forceinline__ uint32_t tmem_alloc(uint32_t* slot, int ncols) {
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return *slot;
+}
+
+__device__ __forceinline__ void tmem_free(uint32_t base, int ncols) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ int tmem_cols(int mt) { return mt <= 32 ? 32 : (mt <= 64 ? 64 : (mt <= 128 ? 128 : 256)); }
+
+// Issues the kt/16 K-steps of hi.hi + hi.lo + lo.hi (thread 0), commits to
+// the mbarrier, and waits for it (every thread, bounded).  Operands K-major
+// with kg = K/8 core-matrix groups along K (lbo 128, sbo kg * 128).
+__device__ __forceinline__ bool mma_split3(uint32_t dt, const unsigned char* Ahi, const unsigned char* Alo,
+                                           const unsigned char* Bhi, const unsigned char* Blo, int kg, int nd,
+                                           uint32_t mbar, int* timeout) {
+  if (threadIdx.x == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t id = idesc_bf16(nd);
+    const uint32_t sbo = (uint32_t)kg * 128u;
+    for (int ks = 0; ks < kg / 2; ++ks) {
+      const uint32_t o = (uint32_t)ks * 256u;  // two core matrices along K per step of 16
+      const uint64_t ah = kmajor_desc(smem_u32(Ahi) + o, 128u, sbo);
+      const uint64_t al = kmajor_desc(smem_u32(Alo) + o, 128u, sbo);
+      const uint64_t bh = kmajor_desc(smem_u32(Bhi) + o, 128u, sbo);
+      const uint64_t bl = kmajor_desc(smem_u32(Blo) + o, 128u, sbo);
+      mma_bf16(dt, ah, bh, id, ks > 0 ? 1u : 0u);
+      mma_bf16(dt, ah, bl, id, 1u);
+      mma_bf16(dt, al, bh, id, 1u);
+    }
+    mma_commit(mbar);
+  }
+  __syncwarp();
+  bool ok = mbar_wait(mbar, 0);
+  // uniform over the CTA: the epilogue's tcgen05.ld is warp-collective
+  ok = __syncthreads_and(ok ? 1 : 0) != 0;
+  if (!ok) {
+    if (threadIdx.x == 0 && timeout != nullptr) atomicExch(timeout, 1);
+    // give the MMAs in flight a second bounded wait before the caller
+    // frees their tensor memory
+    mbar_wait(mbar, 0);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return ok;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+}
+
+// Projections W[m][c] += sum_{i in chunk} S[c][i] R[m][i]: D (128 modes x mt
+// members) = A (modes x 128 rows) B (128 rows x members), K = the chunk's rows.
+// Shared: A hi, lo [128 x 128] | B hi, lo [mt x 128] | mbarrier | TMEM slot.
+__global__ void __launch_bounds__(kTcThreads) lmp_proj_tc_kernel(int n, int nS, int k, const __nv_bfloat16* Shi,
+                                                                 const __nv_bfloat16* Slo, int M, int m0, int mt,
+                                                                 const double* R, const int* active, float* W,
+                                                                 int kt, int* timeout) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  constexpr int KG = kRows / 8;  // 16 groups of 8 rows along K
+  unsigned char* Ahi = sm;
+  unsigned char* Alo = Ahi + 128 * kRows * 2;
+  unsigned char* Bhi = Alo + 128 * kRows * 2;
+  unsigned char* Blo = Bhi + (size_t)mt * kRows * 2;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + (size_t)mt * kRows * 2);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int row0 = blockIdx.x * kRows;
+  const int rows = min(kRows, n - row0);
+  const int ncols = tmem_cols(mt);
+  mbar_init(mbar);
+  // A: 128 modes x 16 groups of 8 rows, zero for modes >= kt (S rows k..kt-1
+  // are zero in memory); one 16-byte load and store per core-matrix row
+  for (int idx = threadIdx.x; idx < 128 * KG; idx += kTcThreads) {
+    const int mo = idx / KG, kb = idx - mo * KG;
+    uint4 h = make_uint4(0, 0, 0, 0), l = h;
+    if (mo < kt) {
+      const long long g = (long long)mo * nS + row0 + 8 * kb;  // nS: padded to whole chunks
+      h = *reinterpret_cast<const uint4*>(Shi + g);
+      l = *reinterpret_cast<const uint4*>(Slo + g);
+    }
+    *reinterpret_cast<uint4*>(Ahi + kmaj_off(mo, kb, KG)) = h;
+    *reinterpret_cast<uint4*>(Alo + kmaj_off(mo, kb, KG)) = l;
+  }
+  // B: mt members x 16 groups of 8 rows of R, split on the fly
+  for (int idx = threadIdx.x; idx < mt * KG; idx += kTcThreads) {
+    const int j = idx / KG, kb = idx - j * KG;
+    const int m = m0 + j;
+    double x[8];
+    const bool live = m < M && (active == nullptr || active[m] != 0);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int i = 8 * kb + e;
+      x[e] = (live && i < rows) ? R[(long long)m * n + row0 + i] : 0.0;
+    }
+    uint4 h, l;
+    split8<double>(x, &h, &l);
+    *reinterpret_cast<uint4*>(Bhi + kmaj_off(j, kb, KG)) = h;
+    *reinterpret_cast<uint4*>(Blo + kmaj_off(j, kb, KG)) = l;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  const uint32_t tbase = tmem_alloc(slot, ncols);  // includes the block barrier
+  const bool ok = mma_split3(tbase, Ahi, Alo, Bhi, Blo, KG, mt, smem_u32(mbar), timeout);
+  if (ok) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mo = 32 * w + lane;  // TMEM lane = accumulator row = mode
+    for (int c0 = 0; c0 < mt; c0 += 16) {
+      float v[16];
+      tmem_ld16(tbase + ((uint32_t)(32 * w) << 16) + (uint32_t)c0, v);
+      if (mo < k) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int m = m0 + c0 + e;
+          if (m < M && (active == nullptr || active[m] != 0)) atomicAdd(&W[(long long)m * kt + mo], v[e]);
+        }
+      }
+    }
+  }
+  tmem_free(tbase, ncols);
+}
+
+// Expansion Z[m][i] = R[m][i] + sum_c S[c][i] coef[c] W[m][c]: D (128 rows x
+// mt members) = A (128 rows x kt modes) B (kt modes x members).  Shared: A
+// hi, lo [128 x kt] | B hi, lo [mt x kt] | mbarrier | TMEM slot.
+__global__ void __launch_bounds__(kTcThreads) lmp_expand_tc_kernel(int n, int nS, int k,
+                                                                   const __nv_bfloat16* ShiT,
+                                                                   const __nv_bfloat16* SloT, const double* coef,
+                                                                   int M, int m0, int mt, const double* R,
+                                                                   double* Z, const int* active, const float* W,
+                                                                   int kt, int* timeout) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int KG = kt / 8;
+  unsigned char* Ahi = sm;
+  unsigned char* Alo = Ahi + (size_t)128 * kt * 2;
+  unsigned char* Bhi = Alo + (size_t)128 * kt * 2;
+  unsigned char* Blo = Bhi + (size_t)mt * kt * 2;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + (size_t)mt * kt * 2);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int row0 = blockIdx.x * kRows;
+  const int rows = min(kRows, n - row0);
+  const int ncols = tmem_cols(mt);
+  mbar_init(mbar);
+  // A: 128 rows x KG groups of 8 modes from the transposed copy S^T [nS][kt]
+  for (int idx = threadIdx.x; idx < 128 * KG; idx += kTcThreads) {
+    const int i = idx / KG, kb = idx - i * KG;
+    const long long g = (long long)(row0 + i) * kt + 8 * kb;  // rows >= n are zero in the padded copy
+    *reinterpret_cast<uint4*>(Ahi + kmaj_off(i, kb, KG)) = *reinterpret_cast<const uint4*>(ShiT + g);
+    *reinterpret_cast<uint4*>(Alo + kmaj_off(i, kb, KG)) = *reinterpret_cast<const uint4*>(SloT + g);
+  }
+  // B: mt members x KG groups of 8 modes of coef o w, split on the fly
+  for (int idx = threadIdx.x; idx < mt * KG; idx += kTcThreads) {
+    const int j = idx / KG, kb = idx - j * KG;
+    const int m = m0 + j;
+    const bool live = m < M && (active == nullptr || active[m] != 0);
+    float x[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int c = 8 * kb + e;
+      x[e] = (live && c < k) ? (float)(coef[c] * (double)W[(long long)m * kt + c]) : 0.0f;
+    }
+    uint4 h, l;
+    split8<float>(x, &h, &l);
+    *reinterpret_cast<uint4*>(Bhi + kmaj_off(j, kb, KG)) = h;
+    *reinterpret_cast<uint4*>(Blo + kmaj_off(j, kb, KG)) = l;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  const uint32_t tbase = tmem_alloc(slot, ncols);
+  const bool ok = mma_split3(tbase, Ahi, Alo, Bhi, Blo, KG, mt, smem_u32(mbar), timeout);
+  if (ok) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = 32 * w + lane;  // TMEM lane = accumulator row = row of the chunk
+    for (int c0 = 0; c0 < mt; c0 += 16) {
+      float v[16];
+      tmem_ld16(tbase + ((uint32_t)(32 * w) << 16) + (uint32_t)c0, v);
+      if (i < rows) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int m = m0 + c0 + e;
+          if (m < M && (active == nullptr || active[m] != 0)) {
+            const long long g = (long long)m * n + row0 + i;
+            Z[g] = R[g] + (double)v[e];
+          }
+        }
+      }
+    }
+  }
+  tmem_free(tbase, ncols);
+}
+
+__global__ void split_bf16_kernel(int n, int nS, int k, int kt, const double* S, __nv_bfloat16* Shi,
+                                  __nv_bfloat16* Slo, __nv_bfloat16* ShiT, __nv_bfloat16* SloT) {
+  const long long total = (long long)kt * nS;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e / nS), i = (int)(e - (long long)c * nS);
+    const double x = (c < k && i < n) ? S[(long long)c * n + i] : 0.0;
+    const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
+    const __nv_bfloat16 l = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
+    Shi[e] = h;
+    Slo[e] = l;
+    ShiT[(long long)i * kt + c] = h;
+    SloT[(long long)i * kt + c] = l;
+  }
+}
+
+template <typename K>
+cudaError_t set_smem(K kern, size_t smem) {
+  if (smem <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
+}  // namespace
+
+int lmp_tc_kt(int k) { return ((k + 15) / 16) * 16; }
+int lmp_tc_ns(int n) { return ((n + kRows - 1) / kRows) * kRows; }
+
+template <typename TS>
+cudaError_t lmp_apply_cc(int n, int k, const TS* S, const double* coef, int M, const double* R, double* Z,
+                         const int* active, TS* W, int kpad, cudaStream_t s) {
+  if (M <= 0 || n <= 0) return cudaSuccess;
+  if (k <= 0) {
+    if (Z == R) return cudaSuccess;
+    return cudaMemcpyAsync(Z, R, (size_t)M * n * sizeof(double), cudaMemcpyDeviceToDevice, s);
+  }
+  cudaError_t e = cudaMemsetAsync(W, 0, (size_t)M * kpad * sizeof(TS), s);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((n + kRows - 1) / kRows, (M + kCcWarps - 1) / kCcWarps);
+  const size_t sm1 = ((size_t)k * kSmRow + (size_t)kCcWarps * kRows) * sizeof(TS);
+  const size_t sm2 = ((size_t)k * kSmRow + (size_t)kCcWarps * k) * sizeof(TS);
+  if ((e = set_smem(lmp_proj_cc_kernel<TS>, sm1)) != cudaSuccess) return e;
+  if ((e = set_smem(lmp_expand_cc_kernel<TS>, sm2)) != cudaSuccess) return e;
+  count_launch(2);
+  lmp_proj_cc_kernel<TS><<<grid, kCcThreads, sm1, s>>>(n, k, S, M, R, active, W, kpad);
+  lmp_expand_cc_kernel<TS><<<grid, kCcThreads, sm2, s>>>(n, k, S, coef, M, R, Z, active, W, kpad);
+  return cudaGetLastError();
+}
+
+cudaError_t lmp_apply_tc(int n, int k, const __nv_bfloat16* Shi, const __nv_bfloat16* Slo,
+                         const __nv_bfloat16* ShiT, const __nv_bfloat16* SloT, const double* coef, int M,
+                         const double* R, double* Z, const int* active, float* W, int* timeout, cudaStream_t s) {
+  if (M <= 0 || n <= 0) return cudaSuccess;
+  const int kt = lmp_tc_kt(k), nS = lmp_tc_ns(n);
+  if (k <= 0 || kt > 128) return cudaErrorInvalidValue;
+  const int Mp = ((M + 15) / 16) * 16;
+  cudaError_t e = cudaMemsetAsync(W, 0, (size_t)Mp * kt * sizeof(float), s);
+  if (e != cudaSuccess) return e;
+  const int chunks = nS / kRows;
+  // members in groups of at most 256 (the largest MMA N)
+  for (int m0 = 0; m0 < M; m0 += 256) {
+    const int mt = ((min(256, M - m0) + 15) / 16) * 16;
+    const size_t sm1 = (size_t)2 * 128 * kRows * 2 + (size_t)2 * mt * kRows * 2 + 16;
+    if ((e = set_smem(lmp_proj_tc_kernel, sm1)) != cudaSuccess) return e;
+    count_launch();
+    lmp_proj_tc_kernel<<<chunks, kTcThreads, sm1, s>>>(n, nS, k, Shi, Slo, M, m0, mt, R, active, W, kt, timeout);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  for (int m0 = 0; m0 < M; m0 += 256) {
+    const int mt = ((min(256, M - m0) + 15) / 16) * 16;
+    const size_t sm2 = (size_t)2 * 128 * kt * 2 + (size_t)2 * mt * kt * 2 + 16;
+    if ((e = set_smem(lmp_expand_tc_kernel, sm2)) != cudaSuccess) return e;
+    count_launch();
+    lmp_expand_tc_kernel<<<chunks, kTcThreads, sm2, s>>>(n, nS, k, ShiT, SloT, coef, M, m0, mt, R, Z, active, W,
+                                                         kt, timeout);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t split_bf16(int n, int k, const double* S, __nv_bfloat16* Shi, __nv_bfloat16* Slo, __nv_bfloat16* ShiT,
+                       __nv_bfloat16* SloT, cudaStream_t s) {
+  const int kt = lmp_tc_kt(k), nS = lmp_tc_ns(n);
+  count_launch();
+  long long blocks = ((long long)kt * nS + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, nS, k, kt, S, Shi, Slo, ShiT, SloT);
+  return cudaGetLastError();
+}
+
+template cudaError_t lmp_apply_cc<double>(int, int, const double*, const double*, int, const double*, double*,
+                                          const int*, double*, int, cudaStream_t);
+template cudaError_t lmp_apply_cc<float>(int, int, const float*, const double*, int, const double*, double*,
+                                         const int*, float*, int, cudaStream_t);
+
+}  // namespace eda

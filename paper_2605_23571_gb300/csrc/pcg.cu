@@ -126,8 +126,9 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgGrid G, 
   const bool mine = G.single ? m < P.M : live_flag;
   const bool live = live_flag;
   const long long off = P.off0 + (long long)m * P.n + tk.row0;
-  double pv[R], qv[R], xv[R], rv[R];
+  double pv[R], qv[R], xv[R], rv[R], bv[R];
   double pq = 0.0, rzp = 0.0;
+  const bool rec = update && P.jhist != nullptr;  // cost record: b is read too
   if (mine) {
     if (update) {
       pq = acc[item].pq;
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgGrid G, 
           qv[j] = q[off + i];
           xv[j] = x[off + i];
         }
+        if (rec) bv[j] = P.b[off + i];
       }
     }
   }
@@ -168,20 +170,31 @@ __global__ void __launch_bounds__(kThreads) pcg2_update_kernel(const PcgGrid G, 
       return;
     }
     const double alpha = rzp / pq;
-    double rr = 0.0;
+    double rr = 0.0, xx = 0.0, jx = 0.0;
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const int i = lane + 32 * j;
       if (i < tk.rows) {
-        x[off + i] = xv[j] + alpha * pv[j];
+        const double xn = xv[j] + alpha * pv[j];
+        x[off + i] = xn;
         const double rn = rv[j] - alpha * qv[j];
         r[off + i] = rn;
         rr += rn * rn;
+        xx += xn * xn;
+        if (rec) jx += xn * (bv[j] + rn);
         rw[i] = (TS)rn;
       }
     }
     rr = warp_sum(rr);
     if (lane == 0) atomicAdd(&acc[item].rr, rr);
+    if (P.etol > 0.0) {
+      xx = warp_sum(xx);
+      if (lane == 0) atomicAdd(&acc[item].xx, xx);
+    }
+    if (rec) {
+      jx = warp_sum(jx);
+      if (lane == 0) atomicAdd(&acc[item].jx, jx);
+    }
   } else {
 #pragma unroll
     for (int j = 0; j < R; ++j) {
@@ -210,7 +223,8 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgGrid G,
                                                                 const double* r, double* z, double* p,
                                                                 PcgScalars* sc, PcgAcc* acc, int* active,
                                                                 const TS* Wk, int par, double tol, int maxit,
-                                                                int fixed, int use_lmp, int init, int* nactive) {
+                                                                int fixed, int use_lmp, int init, int* nactive,
+                                                                const double* zpre) {
   extern __shared__ __align__(16) unsigned char smraw[];
   using V = typename Vec16<TS>::type;
   constexpr int VW = Vec16<TS>::VW;
@@ -232,8 +246,8 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgGrid G,
   const bool mine = G.single ? m < P.M : live_flag;
   const bool live = live_flag;
   const long long off = P.off0 + (long long)m * P.n + tk.row0;
-  double rv[R];
-  double bn = 0.0, rrv = 0.0, tolm = 0.0;
+  double rv[R], zp[R];
+  double bn = 0.0, rrv = 0.0, tolm = 0.0, xxv = 0.0, jxv = 0.0;
   int itj = 0;
   TS cw[kCwPerLane];  // c_c w_c for c = lane + 32 j
 #pragma unroll
@@ -244,11 +258,16 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgGrid G,
       rrv = acc[item].rr;
       itj = sc[item].iters + 1;
       tolm = sc[item].tolm;
+      if (P.etol > 0.0) xxv = acc[item].xx;
+      if (P.jhist != nullptr) jxv = acc[item].jx;
     }
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const int i = lane + 32 * j;
-      if (i < tk.rows) rv[j] = r[off + i];
+      if (i < tk.rows) {
+        rv[j] = r[off + i];
+        if (zpre != nullptr) zp[j] = zpre[off + i];
+      }
     }
 #pragma unroll
     for (int j = 0; j < kCwPerLane; ++j) {
@@ -283,14 +302,29 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgGrid G,
         st = EDA_CONVERGED;
         stop = true;
       }
-    } else if (rel <= (tolm > 0.0 ? tolm : tol)) {
-      st = EDA_CONVERGED;
-      stop = true;
-    } else if (maxit > 0 && itj >= maxit) {
-      stop = true;
+    } else {
+      // every requested criterion: the relative residual (tol > 0) and the
+      // certified error bound ||r|| / (||x|| - ||r||) (etol > 0); or the
+      // inner threshold tolm of a refinement round
+      bool fin = !(tol > 0.0) || rel <= tol;
+      if (P.etol > 0.0) {
+        const double rn = rel * bn, xn = sqrt(xxv);
+        fin = fin && xn > rn && rn <= P.etol * (xn - rn);
+      }
+      if (fin || (tolm > 0.0 && rel <= tolm)) {
+        st = EDA_CONVERGED;
+        stop = true;
+      } else if (maxit > 0 && itj >= maxit) {
+        stop = true;
+      }
     }
     if (tk.first && lane == 0) {
       sc[item].relres = rel;
+      if (P.jhist != nullptr) {
+        // this launch's only reader of jx: record, then clear for the next update
+        if (itj < P.jstride) P.jhist[(long long)m * P.jstride + itj] = -0.5 * jxv;
+        acc[item].jx = 0.0;
+      }
       acc[item].inc = 1;
       if (stop) {
         sc[item].status = st;
@@ -309,7 +343,7 @@ __global__ void __launch_bounds__(kThreads) pcg2_precond_kernel(const PcgGrid G,
   for (int j = 0; j < R; ++j) {
     const int i = lane + 32 * j;
     if (i < tk.rows) {
-      double zv = rv[j];
+      double zv = zpre != nullptr ? zp[j] : rv[j];
       if (k > 0) {
         const V* Srow = reinterpret_cast<const V*>(Ssm + i * KP);
         const V* wv = reinterpret_cast<const V*>(wc);
@@ -354,6 +388,7 @@ __global__ void __launch_bounds__(kThreads) pcg2_dir_kernel(const PcgGrid G, int
         acc[item].inc = 0;
       }
       acc[item].rr = 0.0;
+      acc[item].xx = 0.0;
     }
     for (int idx = threadIdx.x; idx < P.M * kmax; idx += kThreads)
       Wk[(long long)P.item0 * kmax + idx] = TS(0);
@@ -412,7 +447,7 @@ __global__ void __launch_bounds__(kThreads) pcg2_replace_kernel(const PcgGrid G,
 __global__ void pcg2_reset_kernel(PcgAcc* acc, int T) {
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < T; j += gridDim.x * blockDim.x) {
     PcgAcc a;
-    a.pq = a.rr = a.rz[0] = a.rz[1] = 0.0;
+    a.pq = a.rr = a.rz[0] = a.rz[1] = a.xx = a.jx = 0.0;
     a.inc = a.pad = 0;
     acc[j] = a;
   }
@@ -494,7 +529,8 @@ cudaError_t pcg2_update(const PcgGrid& G, int kmax, int mmax, const double* p,
 template <typename TS>
 cudaError_t pcg2_precond(const PcgGrid& G, int kmax, int mmax, const double* r,
                          double* z, double* p, PcgScalars* sc, PcgAcc* acc, int* active, const TS* Wk, int par,
-                         double tol, int maxit, int fixed, int use_lmp, int init, int* nactive, cudaStream_t s) {
+                         double tol, int maxit, int fixed, int use_lmp, int init, int* nactive, cudaStream_t s,
+                         const double* zpre) {
   if (G.ntasks <= 0 || mmax <= 0) return cudaSuccess;
   if (vec_stride<TS>(kmax) > 32 * kCwPerLane) return cudaErrorInvalidValue;  // more than 80 LMP modes
   const int KW = vec_stride<TS>(kmax > 0 ? kmax : 1);
@@ -503,7 +539,7 @@ cudaError_t pcg2_precond(const PcgGrid& G, int kmax, int mmax, const double* r,
   if (e != cudaSuccess) return e;
   count_launch();
   pcg2_precond_kernel<TS><<<dim3(G.ntasks, (mmax + kWarps - 1) / kWarps), kThreads, smem, s>>>(G, kmax, r, z, p, sc, acc, active, Wk, par, tol,
-                                                         maxit, fixed, use_lmp, init, nactive);
+                                                         maxit, fixed, use_lmp, init, nactive, zpre);
   return cudaGetLastError();
 }
 
@@ -549,10 +585,10 @@ template cudaError_t pcg2_update<float>(const PcgGrid&, int, int, const double*,
                                         cudaStream_t);
 template cudaError_t pcg2_precond<double>(const PcgGrid&, int, int, const double*, double*, double*,
                                           PcgScalars*, PcgAcc*, int*, const double*, int, double, int, int, int,
-                                          int, int*, cudaStream_t);
+                                          int, int*, cudaStream_t, const double*);
 template cudaError_t pcg2_precond<float>(const PcgGrid&, int, int, const double*, double*, double*,
                                          PcgScalars*, PcgAcc*, int*, const float*, int, double, int, int, int, int,
-                                         int*, cudaStream_t);
+                                         int*, cudaStream_t, const double*);
 template cudaError_t pcg2_dir<double>(const PcgGrid&, int, int, const double*, double*, PcgScalars*,
                                       PcgAcc*, const int*, double*, int, cudaStream_t, const int*, int*);
 template cudaError_t pcg2_dir<float>(const PcgGrid&, int, int, const double*, double*, PcgScalars*,

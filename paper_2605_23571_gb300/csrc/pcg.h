@@ -22,12 +22,14 @@
 
 namespace eda {
 
-// Per-member accumulators of one iteration (40 bytes: pq is the first
-// double, so the sweep epilogue adds p^T q at acc + 5 * member).
+// Per-member accumulators of one iteration (56 bytes: pq is the first
+// double, so the sweep epilogue adds p^T q at acc + kPcgAccStride * member).
 struct PcgAcc {
   double pq;     // p^T q of this iteration (sweep epilogue)
   double rr;     // ||r||^2 after the update
   double rz[2];  // r^T z by iteration parity
+  double xx;     // ||x||^2 after the update (certified error test)
+  double jx;     // x^T (b + r) after the update (cost record: J = -jx / 2)
   int inc;       // 1: the member iterated (set by precond, counted by dir)
   int pad;
 };
@@ -35,12 +37,21 @@ constexpr int kPcgAccStride = (int)(sizeof(PcgAcc) / sizeof(double));
 
 // One problem of the batch: members item0 .. item0+M-1, member m's vectors
 // at off0 + m * n of the concatenated layout; S is k x n column-major (TS),
-// c the k LMP coefficients (k = 0: no LMP).
+// c the k LMP coefficients (k = 0: no LMP).  Solve options of the problem:
+// etol > 0 adds the certified error test ||r|| / (||x|| - ||r||) <= etol to
+// the stopping rule (lambda_min(I + A) >= 1, Section 2.3, makes it a bound
+// on ||x - x*|| / ||x*||); jhist != nullptr records the quadratic cost
+// J(x_i) = 1/2 x^T H x - b^T x = -x^T (b + r) / 2 of every iterate at
+// jhist[m * jstride + i] (b: the right-hand sides, read only then).
 struct PcgProb {
   int n, M, k, item0;
   long long off0;
   const void* S;
   const double* c;
+  double etol;
+  const double* b;
+  double* jhist;
+  int jstride;
 };
 
 // A chunk of rows [row0, row0 + rows) of one problem (rows <= kPcgRows);
@@ -90,10 +101,13 @@ cudaError_t pcg2_update(const PcgGrid& G, int kmax, int mmax, const double* p,
 // par^1 for the members that go on.  init = 1 (start of a loop): no test;
 // z, p = z and r.z into slot 0; the caller then clears the projections
 // before the first update.
+// zpre != nullptr: z = P r was computed by a separate LMP launch (the
+// tensor-core LMP) and is read from zpre instead (use_lmp must be 0).
 template <typename TS>
 cudaError_t pcg2_precond(const PcgGrid& G, int kmax, int mmax, const double* r,
                          double* z, double* p, PcgScalars* sc, PcgAcc* acc, int* active, const TS* Wk, int par,
-                         double tol, int maxit, int fixed, int use_lmp, int init, int* nactive, cudaStream_t s);
+                         double tol, int maxit, int fixed, int use_lmp, int init, int* nactive, cudaStream_t s,
+                         const double* zpre = nullptr);
 
 // p = z + beta p; counts the iteration and clears rr and the projections.
 // With host_count (pinned host memory) != NULL, one thread also copies the

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libeda.so")
-SOURCES = ["sweep.cu", "dense.cu", "pcg.cu", "api.cu", "group.cu", "warm.cu", "noalloc.cu"]
+SOURCES = ["sweep.cu", "dense.cu", "pcg.cu", "api.cu", "group.cu", "warm.cu", "noalloc.cu", "lmp.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr",

@@ -1,0 +1,113 @@
+"""The batched workload at its full size (Lorenz-96 n = 4096, 64-step window,
+51 members, Gamma-sketch LMP with k = 49, PCG to relative residual 1e-6),
+solved through the C ABI and checked against reference solutions of the
+FP64 oracle (tests/golden/oracle_solutions_n4096.npz, written by
+write_oracle_solutions_n4096.py from the oracle alone).
+
+The inputs are rebuilt from the stored spun-up truth with the oracle's twin,
+and both sides use the oracle's LMP (eda_set_lmp), so that the comparison
+is of the solves.  Errors are stated against the certified bound
+||r|| / (||x|| - ||r||) >= ||x - x*|| / ||x*|| (lambda_min(I + A) >= 1,
+Section 2.3) of each side's FP64 true residual."""
+import os
+
+import numpy as np
+import pytest
+
+import eda_synth as S
+import oracle as O
+from helpers import rowrel
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2605_23571_gb300")
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_solutions_n4096.npz")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    P.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module")
+def workload():
+    G = dict(np.load(GOLDEN))
+    spec = S.spec_batched(seed=0)
+    taps = G["taps"]
+    np.testing.assert_allclose(taps, O.bhalf_taps(spec.n, spec.length_scale, spec.sigma_b), rtol=1e-15)
+    _, xb, y = O.twin_from_truth(spec, S.draws(spec), taps, G["xt0"])
+    traj = O.member_trajectories(spec, xb)
+    b = O.rhs(spec, traj, O.innovations(spec, traj, y), taps)
+    ctrl = traj[0:1]
+
+    def apply_ctrl(block):
+        tr = np.broadcast_to(ctrl, (block.shape[1],) + ctrl.shape[1:])
+        return O.apply_A(spec, tr, block.T.copy(), taps).T
+
+    Sk, D, _ = O.nystrom(apply_ctrl, O.gamma(b)[:, : spec.ell], spec.k)
+    np.testing.assert_allclose(1 + D, G["lmp_eigvals"], rtol=1e-12)
+    return spec, taps, xb, y, b, Sk, D, G
+
+
+def test_fp64_stopping_counts_at_1e6_match_the_oracle(workload):
+    spec, taps, xb, y, b, Sk, D, G = workload
+    mem = G["members"]
+    with P.Handle.from_spec(spec, taps, precision=P.EDA_FP64) as h:
+        rhs = np.zeros_like(b)
+        h.eda_set_trajectory(xb, y, rhs)
+        assert rowrel(rhs, b).max() < 1e-11
+        h.eda_set_lmp(np.ascontiguousarray(Sk.T), 1 + D)
+        M = spec.n_members
+        dz = np.zeros_like(b)
+        it = np.zeros(M, np.int32)
+        rr = np.zeros(M)
+        st = np.zeros(M, np.int32)
+        h.eda_solve_batch(1e-6, 10000, None, True, dz, it, rr, st)
+    assert (st == P.EDA_CONVERGED).all() and (rr <= 1e-6).all()
+    # the oracle's count, widened by its own spread under perturbations of b
+    # at 1e-16 (CG rounding) and 1e-13 (the level at which two FP64 Hessian
+    # products differ; the count moves by about 1 % there), and +-1
+    allc = np.concatenate([G["iters_1e6"][:, None], G["iters_1e6_pert"], G["iters_1e6_pert13"]], axis=1)
+    lo, hi = allc.min(axis=1), allc.max(axis=1)
+    print("stopping counts: gpu %s, oracle %s (perturbed %s..%s)" % (it[mem], G["iters_1e6"], lo, hi))
+    assert ((it[mem] >= lo - 1) & (it[mem] <= hi + 1)).all()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tight_solutions_match_the_oracle(workload, precision):
+    # FP64: solved to the attainable floor, the solution agrees with the
+    # oracle's to 1e-10, or to the sum of the two certified bounds where that
+    # is larger (neither side's residual can certify closer).  Mixed: solved
+    # to a certified error of 1e-6, its error against the oracle's solution
+    # is within that bound plus the oracle's.
+    spec, taps, xb, y, b, Sk, D, G = workload
+    mem = G["members"]
+    M = spec.n_members
+    prec = P.EDA_FP64 if precision == "fp64" else P.EDA_MIXED
+    with P.Handle.from_spec(spec, taps, precision=prec) as h:
+        h.eda_set_trajectory(xb, y)
+        h.eda_set_lmp(np.ascontiguousarray(Sk.T), 1 + D)
+        dz = np.zeros_like(b)
+        eb = np.zeros(M)
+        rr = np.zeros(M)
+        st = np.zeros(M, np.int32)
+        it = np.zeros(M, np.int32)
+        if precision == "fp64":
+            h.eda_solve(dz, tol=1e-13, maxit=6000, err_bound_out=eb, relres_out=rr, iters_out=it, status_out=st)
+        else:
+            h.eda_solve(dz, err_tol=1e-6, maxit=20000, err_bound_out=eb, relres_out=rr, iters_out=it,
+                        status_out=st)
+    err = rowrel(dz[mem], G["x_tight"])
+    bound = eb[mem] + G["tight_bound"]
+    print("%s: rel err vs oracle %s, gpu bound %s, oracle bound %s, iters %s, true relres %s"
+          % (precision, err, eb[mem], G["tight_bound"], it[mem], rr[mem]))
+    assert np.isfinite(eb).all()
+    if precision == "fp64":
+        assert (err <= np.maximum(1e-10, bound)).all()
+    else:
+        assert (st == P.EDA_CONVERGED).all() and (eb <= 1e-6).all()
+        assert (err <= bound * (1 + 1e-6)).all()
