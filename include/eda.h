@@ -92,8 +92,14 @@ typedef struct eda_handle eda_handle;
  *                  EDA_MIXED: tangent-linear/adjoint sweeps and LMP apply in
  *                  FP32, CG scalars, residual norms and the small Nystrom
  *                  factorisations in FP64, FP64 residual replacement.
- *  ckpt_every      0 stores the whole trajectory; c > 0 stores every c-th
- *                  state and recomputes the segments in the adjoint sweep.
+ *  ckpt_every      0 stores the whole trajectory; c in [1, 4096] stores the
+ *                  states x_0, x_c, x_2c, ... only, and every Hessian-product
+ *                  and right-hand-side sweep recomputes each c-step segment
+ *                  from its checkpoint on the chip (multi-launch tiles of c
+ *                  steps with a halo of 19c + 8; the FP64 stage-state store
+ *                  is off).  EDA_ERR_INVALID when no such tiling fits (c too
+ *                  large for shared memory).  Checkpointed handles are not
+ *                  grouped (eda_group_create).
  *  stream          a cudaStream_t (NULL = the legacy default stream).
  */
 typedef struct {
@@ -352,7 +358,9 @@ EDA_API int eda_sweep_plan(eda_handle* h, int fp64, int* info);
  * K.  kind 0: thread-block clusters of exactly cs CTAs with C values per
  * thread (C = 0: the default run length); kind 1: multi-launch tiles of K
  * steps with `threads` threads per CTA (0: the default; C must be 0); kind 2:
- * warp-tiled, clusters of cs CTAs, C values per lane.  info[8] (host,
+ * warp-tiled, clusters of cs CTAs, C values per lane; kind 3: multi-launch
+ * tiles for a trajectory checkpointed every K steps (ckpt_every = K; info[0]
+ * then reports kind 1).  info[8] (host,
  * caller-owned) as in eda_sweep_plan.  EDA_ERR_INVALID when no tiling of
  * that shape fits (or an argument is out of range).
  */

@@ -212,14 +212,14 @@ PLAN_KINDS = ("cluster", "multi-launch", "warp")
 PLAN_KEYS = ("kind", "ctas_per_vector", "threads", "C", "K", "halo", "owned", "smem")
 
 
-def plan_tiling(n, fp64, w, kind, cs=0, threads=0, K=8, C=0):
+def plan_tiling(n, fp64, w, kind, cs=0, threads=0, K=8, C=0, ckpt=False):
     """The sweep tiling the library would use (host only, no GPU): kind
-    'cluster' (cs CTAs per vector), 'multi-launch' (`threads` per CTA) or
-    'warp'; a dict as Handle.eda_sweep_plan returns, or None if it does not
-    fit."""
+    'cluster' (cs CTAs per vector), 'multi-launch' (`threads` per CTA; with
+    ckpt, for a trajectory checkpointed every K steps) or 'warp'; a dict as
+    Handle.eda_sweep_plan returns, or None if it does not fit."""
     info = (ctypes.c_int * 8)()
-    rc = lib().eda_plan_tiling(int(n), int(bool(fp64)), int(w), PLAN_KINDS.index(kind), int(cs), int(threads),
-                               int(K), int(C), info)
+    k = 3 if (ckpt and kind == "multi-launch") else PLAN_KINDS.index(kind)
+    rc = lib().eda_plan_tiling(int(n), int(bool(fp64)), int(w), k, int(cs), int(threads), int(K), int(C), info)
     if rc != EDA_OK:
         return None
     out = dict(zip(PLAN_KEYS, list(info)))

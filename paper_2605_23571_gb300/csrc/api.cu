@@ -456,7 +456,7 @@ SweepArgs<T> base_args(eda_handle* h) {
     a.bcoef = h->bcoef32;
     a.obs_tab = h->tab32_ok ? h->tab32 : nullptr;
   }
-  a.traj_mstride = (long long)(h->N + 1) * h->n;
+  a.traj_mstride = (long long)h->trows * h->n;
   a.M = h->M;
   if constexpr (sizeof(T) == 8) a.stages = h->stg;
   a.stage_astride = (long long)h->M * (h->N + 1) * h->n;
@@ -700,7 +700,14 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
     // candidates: single-launch cluster plans (CS 1..8, two run lengths),
     // then multi-launch plans where a column spans several tiles
     std::vector<SweepPlan> cands;
+    if (h->ckpt > 0) {  // checkpointed: multi-launch plans of K = ckpt_every steps only
+      for (int A : {128, 256, 512}) {
+        SweepPlan pl;
+        if (eda::plan_sweep_ml(h->n, fp64 ? 8 : 4, h->w, h->ckpt, A, &pl, true)) cands.push_back(pl);
+      }
+    }
     for (int C : {fp64 ? 4 : 8, fp64 ? 2 : 4})  // values per thread
+      if (h->ckpt == 0)
       for (int CS = 1; CS <= 8; ++CS)
         for (int K : Ks) {
           SweepPlan pl;
@@ -711,10 +718,12 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
     for (int A : {128, 256, 512})
       for (int K : Ks) {
         SweepPlan pl;
-        if (eda::plan_sweep_ml(h->n, fp64 ? 8 : 4, h->w, 2 * K, A, &pl) && pl.CS >= 2) cands.push_back(pl);
+        if (h->ckpt == 0 && eda::plan_sweep_ml(h->n, fp64 ? 8 : 4, h->w, 2 * K, A, &pl) && pl.CS >= 2)
+          cands.push_back(pl);
       }
     // warp-tiled plans (Hessian-product sweeps only)
     for (int C : {fp64 ? 4 : 8, fp64 ? 2 : 4})
+      if (h->ckpt == 0)
       for (int CS = 2; CS <= 16; ++CS)
         for (int K : {4, 8, 16}) {
           SweepPlan pl;
@@ -820,7 +829,8 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
   if (c.theta_mode < 0 || c.theta_mode > 2) return fail(nullptr, EDA_ERR_INVALID, "bad theta_mode");
   if (c.theta_mode == EDA_THETA_GIVEN && !(c.theta > 0.0)) return fail(nullptr, EDA_ERR_INVALID, "theta must be > 0");
   if (c.precision != EDA_FP64 && c.precision != EDA_MIXED) return fail(nullptr, EDA_ERR_INVALID, "bad precision");
-  if (c.ckpt_every != 0) return fail(nullptr, EDA_ERR_INVALID, "ckpt_every > 0 is not supported by this build");
+  if (c.ckpt_every < 0 || c.ckpt_every > eda::kMaxRefresh)
+    return fail(nullptr, EDA_ERR_INVALID, "ckpt_every must be in [0, 4096]");
   // observation network
   int prev = -1;
   for (int j = 0; j < c.n_obs_times; ++j) {
@@ -884,11 +894,17 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
   const int cs64 = env_int("EDA_SWEEP_CS64", 1), cs32 = env_int("EDA_SWEEP_CS32", 1);
   const int mlA = env_int("EDA_SWEEP_ML", 0);
   const int c64 = env_int("EDA_SWEEP_C64", 0), c32 = env_int("EDA_SWEEP_C32", 0);
+  // A checkpointed trajectory runs multi-launch plans of K = ckpt_every steps
+  // (each launch recomputes its segment from the checkpoint).
   const bool planned =
-      mlA > 0 ? (eda::plan_sweep_ml(h->n, 8, h->w, Kh > 0 ? Kh : 16, mlA, &h->plan64) &&
-                 eda::plan_sweep_ml(h->n, 4, h->w, Kh > 0 ? Kh : 16, mlA, &h->plan32))
-              : (eda::plan_sweep(h->n, 8, h->w, cs64, Kh, &h->plan64, c64) &&
-                 eda::plan_sweep(h->n, 4, h->w, cs32, Kh, &h->plan32, c32));
+      h->ckpt > 0 ? ((eda::plan_sweep_ml(h->n, 8, h->w, h->ckpt, mlA, &h->plan64, true) ||
+                      eda::plan_sweep_ml(h->n, 8, h->w, h->ckpt, 128, &h->plan64, true)) &&
+                     (eda::plan_sweep_ml(h->n, 4, h->w, h->ckpt, mlA, &h->plan32, true) ||
+                      eda::plan_sweep_ml(h->n, 4, h->w, h->ckpt, 128, &h->plan32, true)))
+      : mlA > 0   ? (eda::plan_sweep_ml(h->n, 8, h->w, Kh > 0 ? Kh : 16, mlA, &h->plan64) &&
+                   eda::plan_sweep_ml(h->n, 4, h->w, Kh > 0 ? Kh : 16, mlA, &h->plan32))
+                  : (eda::plan_sweep(h->n, 8, h->w, cs64, Kh, &h->plan64, c64) &&
+                     eda::plan_sweep(h->n, 4, h->w, cs32, Kh, &h->plan32, c32));
   if (!planned) {
     fail(nullptr, EDA_ERR_INVALID, "state size too large for the sweep tiling");
     return bail(EDA_ERR_INVALID);
@@ -898,7 +914,7 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
   // lane EDA_SWEEP_C64/C32), where such a tiling fits
   SweepPlan wp64{}, wp32{};
   bool want_w64 = false, want_w32 = false;
-  if (env_int("EDA_SWEEP_WARP", 0)) {
+  if (env_int("EDA_SWEEP_WARP", 0) && h->ckpt == 0) {
     const int Kw = Kh > 0 ? Kh : 8;
     for (int cs = std::max(cs64, 2); cs <= 16 && !want_w64; ++cs)
       want_w64 = eda::plan_sweep_warp(h->n, 8, h->w, cs, Kw, c64 ? c64 : 4, &wp64);
@@ -919,13 +935,15 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
   CUC(dalloc(h, &h->rinv32, p));
   CUC(dalloc(h, &h->bcoef, h->w + 1));
   CUC(dalloc(h, &h->bcoef32, h->w + 1));
-  CUC(dalloc(h, &h->traj, (size_t)M * (N + 1) * n));
-  if (h->precision == EDA_MIXED) CUC(dalloc(h, &h->traj32, (size_t)M * (N + 1) * n));
+  // trajectory store: states 0..N, or the checkpoints x_0, x_c, x_2c, ...
+  h->trows = h->ckpt > 0 ? N / h->ckpt + 1 : N + 1;
+  CUC(dalloc(h, &h->traj, (size_t)M * h->trows * n));
+  if (h->precision == EDA_MIXED) CUC(dalloc(h, &h->traj32, (size_t)M * h->trows * n));
   // stage-state store for the FP64 sweeps, which are bound by the FP64 pipe
   // and gain from not recomputing the stages (EDA_STAGE_STORE=0: recompute).
   // FP32 sweeps always recompute: streaming three more arrays costs them more
   // than the arithmetic saved.
-  if (env_int("EDA_STAGE_STORE", 1)) CUC(dalloc(h, &h->stg, (size_t)3 * M * (N + 1) * n));
+  if (env_int("EDA_STAGE_STORE", 1) && h->ckpt == 0) CUC(dalloc(h, &h->stg, (size_t)3 * M * (N + 1) * n));
   CUC(dalloc(h, &h->d, (size_t)M * p));
   CUC(dalloc(h, &h->rd, (size_t)M * p));
   CUC(dalloc(h, &h->b, (size_t)M * n));
@@ -1119,7 +1137,7 @@ EDA_API int eda_set_trajectory(eda_handle* h, const double* xb, const double* y,
     a.x0 = (const double*)ixb.dev;
     a.x0_stride = n;
     a.traj_out = h->traj;
-    a.traj_out_mstride = (long long)(N + 1) * n;
+    a.traj_out_mstride = (long long)h->trows * n;
     a.stage_out = h->stg;
     a.yobs = (const double*)iy.dev;
     a.d_out = h->d;
@@ -1127,7 +1145,7 @@ EDA_API int eda_set_trajectory(eda_handle* h, const double* xb, const double* y,
     CU(h, (eda::ensure_ml(h, a.ncol, true) == EDA_OK) ? eda::launch_sweep<double>(a, h->plan64, h->st, h->ml64[0], h->ml64[1]) : cudaErrorMemoryAllocation);
   }
   if (h->precision == EDA_MIXED) {
-    CU(h, eda::convert<double, float>((long long)M * (N + 1) * n, h->traj, h->traj32, h->st));
+    CU(h, eda::convert<double, float>((long long)M * h->trows * n, h->traj, h->traj32, h->st));
   }
   // right-hand sides b_j = U_B^T G_j^T R^{-1} d_j (FP64 adjoint sweep)
   {
@@ -1368,7 +1386,7 @@ EDA_API int eda_set_lmp(eda_handle* h, const double* s_in, const double* eigvals
 }
 
 EDA_API int eda_plan_tiling(int n, int fp64, int w, int kind, int cs, int threads, int K, int C, int* info) {
-  if (!info || n < 1 || w < 0 || K < 1 || K > eda::kMaxRefresh || kind < 0 || kind > 2)
+  if (!info || n < 1 || w < 0 || K < 1 || K > eda::kMaxRefresh || kind < 0 || kind > 3)
     return fail(nullptr, EDA_ERR_INVALID, "eda_plan_tiling: invalid argument");
   const int eb = fp64 ? 8 : 4;
   eda::SweepPlan p{};
@@ -1376,6 +1394,7 @@ EDA_API int eda_plan_tiling(int n, int fp64, int w, int kind, int cs, int thread
   if (kind == 0) ok = eda::plan_sweep_exact(n, eb, w, cs, K, &p, C);
   if (kind == 1) ok = C == 0 && eda::plan_sweep_ml(n, eb, w, K, threads, &p);
   if (kind == 2) ok = eda::plan_sweep_warp(n, eb, w, cs, K, C, &p);
+  if (kind == 3) ok = C == 0 && eda::plan_sweep_ml(n, eb, w, K, threads, &p, true);
   if (!ok) return fail(nullptr, EDA_ERR_INVALID, "eda_plan_tiling: no tiling of that shape fits");
   info[0] = p.warp ? 2 : (p.ml ? 1 : 0);
   info[1] = p.CS;

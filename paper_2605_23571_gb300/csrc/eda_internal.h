@@ -106,6 +106,13 @@ struct SweepArgs {
   T* stage_out;
   const T* stages;
   long long stage_astride;
+  // checkpointed trajectory (multi-launch plans only): ckpt > 0 means traj
+  // holds the states x_{j ckpt} only (row j); MODE_NL stores those rows, and
+  // the Hessian-product and right-hand-side launches recompute the states of
+  // their K = ckpt steps from the segment's checkpoint into shared memory at
+  // byte offset xseg_off
+  int ckpt;
+  int xseg_off;
   // plan
   int CS, Ttile, HL, E, K;
   // multi-launch mode (n too large for one cluster): CS tiles per column
@@ -134,6 +141,7 @@ struct SweepPlan {
   size_t smem;
   int ml;    // 1: multi-launch tiles of K steps (no cluster), CS = tiles per column
   int warp;  // 1: warp-tiled Hessian-product kernel (MODE_HVP only; needs a warp table)
+  int ckpt;  // > 0: checkpointed trajectory every ckpt = K steps (multi-launch only)
 };
 
 // Picks the tiling of a sweep for state size n (elem_bytes = sizeof(T)):
@@ -147,9 +155,18 @@ bool plan_sweep(int n, int elem_bytes, int w, int min_cs, int K_hint, SweepPlan*
 size_t sweep_smem_bytes(int A, int C, int w, int elem_bytes);
 
 // A multi-launch plan: tiles of A*C - 2HL owned points, K steps per launch,
-// A threads per CTA (A = 0: 512 for FP64, 256 for FP32; else a multiple of
-// 32 up to 512).
-bool plan_sweep_ml(int n, int elem_bytes, int w, int K, int A, SweepPlan* out);
+// A threads per CTA (A = 0: 512 for FP64, 256 for FP32, 256 checkpointed;
+// else a multiple of 32 up to 512).  ckpt: a checkpointed plan (K = the
+// checkpoint period, halo ckpt_halo(K), K states of the region in shared
+// memory).
+bool plan_sweep_ml(int n, int elem_bytes, int w, int K, int A, SweepPlan* out, bool ckpt = false);
+
+// Halo of a checkpointed multi-launch plan: a backward launch recomputes
+// its K states from the checkpoint (their edge errors reach 8 points per
+// step from the left end of the region and 4 from the right) and the
+// adjoint spreads errors 11 points per step both ways: 8(K-1) + 11K + 1 on
+// the left, rounded up to 19K + 8.
+inline int ckpt_halo(int K) { return 19 * K + 8; }
 
 // A warp-tiled Hessian-product plan with cluster size CS, refresh period K
 // and C values per lane (FP64 2 or 4, FP32 4 or 8): warps of 32*C points

@@ -513,6 +513,8 @@ EDA_API int eda_group_create(eda_handle* const* handles, int count, eda_group** 
   for (int i = 0; i < count; ++i) {
     if (handles[i]->precision != prec)
       return eda::fail(nullptr, EDA_ERR_INVALID, "eda_group_create: handles must share the precision");
+    if (handles[i]->ckpt != 0)
+      return eda::fail(nullptr, EDA_ERR_INVALID, "eda_group_create: checkpointed handles are not grouped");
     if (handles[i]->st != handles[0]->st)
       return eda::fail(nullptr, EDA_ERR_INVALID, "eda_group_create: handles must share the stream");
   }

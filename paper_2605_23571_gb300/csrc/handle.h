@@ -18,6 +18,7 @@ struct eda_handle {
   // problem
   int n = 0, N = 0, M = 0, p = 0, nos = 0, w = 0, ell = 0, k = 0;
   int theta_mode = 0, precision = 0, ckpt = 0;
+  int trows = 0;  // rows of each member's trajectory store (N + 1, or N / ckpt + 1 checkpoints)
   double F = 8.0, dt = 0.025, theta_given = 1.0;
   cudaStream_t st = nullptr;
   std::string err;

@@ -82,7 +82,7 @@ EDA_API int eda_hvp_noalloc(eda_handle* h, const int* member_of_col, int ncol, c
     a.F = h->F;
     a.dt = h->dt;
     a.traj = h->traj;
-    a.traj_mstride = (long long)(h->N + 1) * h->n;
+    a.traj_mstride = (long long)h->trows * h->n;
     a.stages = h->stg;
     a.stage_astride = (long long)h->M * (h->N + 1) * h->n;
     a.obs_of_t = h->obs_of_t;
@@ -114,7 +114,7 @@ EDA_API int eda_hvp_noalloc(eda_handle* h, const int* member_of_col, int ncol, c
     a.F = (float)h->F;
     a.dt = (float)h->dt;
     a.traj = h->traj32;
-    a.traj_mstride = (long long)(h->N + 1) * h->n;
+    a.traj_mstride = (long long)h->trows * h->n;
     a.obs_of_t = h->obs_of_t;
     a.obs_ptr = h->obs_ptr;
     a.obs_idx = h->obs_idx;

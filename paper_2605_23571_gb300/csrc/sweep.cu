@@ -462,7 +462,9 @@ constexpr int kObsTabCap = 2048;  // entries of a CTA's observation range rows c
 // STG: the kernel reads stored stage states when the arguments carry them
 // (instantiated for FP64 only: FP32 sweeps recompute, which costs them less
 // than streaming three more arrays).
-template <typename T, int C, bool STG>
+// CK: the kernel recomputes its launch's states from a checkpointed
+// trajectory (multi-launch plans with ckpt > 0; never with STG).
+template <typename T, int C, bool STG, bool CK>
 __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -599,7 +601,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       // x_f0: the initial state, or (later launches of a multi-launch sweep)
       // the state the previous launch stored in the trajectory
       const T* x0row = (f0 == 0)        ? a.x0 + voff
-                       : (tout != nullptr) ? tout + (long long)f0 * a.n
+                       : (tout != nullptr) ? tout + (long long)(a.ckpt ? f0 / a.ckpt : f0) * a.n
                                            : a.st_in + (long long)col * a.n;
       const bool x0_vec = vec_ok && ((reinterpret_cast<unsigned long long>(x0row) & 15ull) == 0);
       load_run<T, C>(x0row, gi, x0_vec, x);
@@ -669,12 +671,14 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       const bool fresh = (t > f0) || (f0 == 0);  // x_t not yet stored / observed
       const int oj = fresh ? obs_at(t) : -1;
       const bool refresh = (t > 0) && (t % a.K == 0) && (t < N);
-      const bool store = fresh && ((tout != nullptr) || (t == N && a.final_out != nullptr));
+      // a checkpointed store keeps the rows t = j * ckpt only
+      const bool trow = tout != nullptr && (a.ckpt == 0 || t % a.ckpt == 0);
+      const bool store = fresh && (trow || (t == N && a.final_out != nullptr));
       if (oj >= 0 || refresh || store) {
         write_mirror(mir, g, x);
         sync_cluster_or_block(refresh && clus);
-        if (tout != nullptr) {
-          T* dst = tout + (long long)t * a.n + g.a0;
+        if (trow) {
+          T* dst = tout + (long long)(a.ckpt ? t / a.ckpt : t) * a.n + g.a0;
           for (int j = g.tid; j < g.Town; j += g.NT) dst[j] = mir[g.HL + j];
         }
         if (t == N && a.final_out != nullptr) {
@@ -737,9 +741,90 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     load_run<T, C>(row, gi, vec_ok, X.v);
     load_halo(row, X);
   };
+  // checkpointed trajectory: the states of this launch's steps, recomputed
+  // from the segment's checkpoint over the extended region into shared
+  // memory (rows seg0 .. seg0 + cnt - 1); their edge errors are covered by
+  // the plan's wider halo
+  T* xseg = (CK && a.ckpt) ? reinterpret_cast<T*>(smem_raw + a.xseg_off) : nullptr;
+  int seg0 = 0;
+  auto recompute = [&](int s0, int cnt) {
+    seg0 = s0;
+    T x[C];
+    load_run<T, C>(trj + (long long)(s0 / a.ckpt) * a.n, gi, vec_ok, x);
+    for (int s_ = 0; s_ < cnt; ++s_) {
+      if (s_ > 0) {  // one RK4 step of the model, as the nonlinear sweep takes it
+        publish(eb[0], g, x);
+        __syncthreads();
+        Run<T, C> X;
+        T X1[C], acc[C], Xs[C];
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          X1[c] = x[c];
+          X.v[c] = x[c];
+        }
+        fetch(eb[0], g, X);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const T k = tend(X, c, F);
+          acc[c] = k;
+          Xs[c] = X1[c] + h2 * k;
+        }
+        publish(eb[1], g, Xs);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < C; ++c) X.v[c] = Xs[c];
+        fetch(eb[1], g, X);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const T k = tend(X, c, F);
+          acc[c] += T(2) * k;
+          Xs[c] = X1[c] + h2 * k;
+        }
+        publish(eb[2], g, Xs);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < C; ++c) X.v[c] = Xs[c];
+        fetch(eb[2], g, X);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const T k = tend(X, c, F);
+          acc[c] += T(2) * k;
+          Xs[c] = X1[c] + h * k;
+        }
+        publish(eb[1], g, Xs);
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < C; ++c) X.v[c] = Xs[c];
+        fetch(eb[1], g, X);
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const T k = tend(X, c, F);
+          acc[c] += k;
+          x[c] = X1[c] + h6 * acc[c];
+        }
+      }
+      write_mirror(xseg + (long long)s_ * g.E, g, x);
+    }
+    __syncthreads();
+  };
+  // own run of x_t: the recomputed segment, or the stored trajectory
+  auto xrow = [&](int t, T (&out)[C]) {
+    if constexpr (CK) {
+      if (xseg != nullptr) {
+        const T* src = xseg + (long long)(t - seg0) * g.E + g.l0;
+#pragma unroll
+        for (int c = 0; c < C; ++c) out[c] = src[c];
+        return;
+      }
+    }
+    load_run<T, C>(trj + (long long)t * a.n, gi, vec_ok, out);
+  };
 
   if (a.mode == MODE_HVP && f1 > f0) {
     T dl[C];
+    if constexpr (CK) {
+      if (xseg != nullptr) recompute(f0, f1 - f0);
+    }
     if (f0 == 0) {
     // delta_0 = U_B v on the extended region (v staged with a w-halo)
     {
@@ -752,7 +837,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       __syncthreads();
     }
     conv_run<T, C>(stage, g.l0, w, cf, dl);
-    load_run<T, C>(trj, gi, vec_ok, xr);
+    xrow(0, xr);
     __syncthreads();  // the stage area becomes the edge buffers
     if (obs_at(0) >= 0) {
       write_mirror(mir, g, dl);
@@ -762,7 +847,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     } else {
       // later launch of a multi-launch sweep: the state of the extended region
       load_run<T, C>(a.st_in + (long long)col * a.n, gi, vec_ok, dl);
-      load_run<T, C>(trj + (long long)f0 * a.n, gi, vec_ok, xr);
+      xrow(f0, xr);
     }
     publish(eb[0], g, dl);
     publish(eb[5], g, xr);
@@ -775,7 +860,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     constexpr bool kPre = sizeof(T) == 4 && C == 4;
     for (int t = f0; t < f1; ++t) {
       T pf[C];
-      if (t + 1 < f1) load_run<T, C>(trj + (long long)(t + 1) * a.n, gi, vec_ok, pf);
+      if (t + 1 < f1) xrow(t + 1, pf);
       int oj_pre = -1;
       ObsPre<T> qg;
       if constexpr (kPre) {
@@ -939,6 +1024,9 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   if (b1 <= b0) return;  // a forward-only launch of a multi-launch sweep
 
   // ------------------------------------------------------ adjoint, backward
+  if constexpr (CK) {
+    if (xseg != nullptr) recompute(b0, b1 - b0);
+  }
   T lam[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) lam[c] = T(0);
@@ -973,7 +1061,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   } else {
     load_run<T, C>(a.st_in + (long long)col * a.n, gi, vec_ok, lam);
   }
-  load_run<T, C>(trj + (long long)(b1 - 1) * a.n, gi, vec_ok, xr);
+  xrow(b1 - 1, xr);
   publish(eb[0], g, xr);
   __syncthreads();
   // FP32 sweeps of four values per thread load the injection of step t at
@@ -981,7 +1069,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   constexpr bool kPreA = sizeof(T) == 4 && C == 4;
   for (int t = b1 - 1; t >= b0; --t) {
     T pf[C];
-    if (t > b0) load_run<T, C>(trj + (long long)(t - 1) * a.n, gi, vec_ok, pf);
+    if (t > b0) xrow(t - 1, pf);
     int oj_pre = -1;
     ObsPre<T> qa;
     if constexpr (kPreA) {
@@ -1676,9 +1764,9 @@ cudaError_t launch_warp(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t 
   return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
-template <typename T, int C, bool STG>
+template <typename T, int C, bool STG, bool CK = false>
 cudaError_t launch_impl(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t s) {
-  auto kern = sweep_kernel<T, C, STG>;
+  auto kern = sweep_kernel<T, C, STG, CK>;
   // function attributes are set once (they are not stream work and must not
   // be issued while a stream is being captured)
   static bool attrs_set = false;
@@ -1742,6 +1830,7 @@ bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* ou
   out->HL = HL;
   out->K = K;
   out->smem = smem;
+  out->ckpt = 0;
   return true;
 }
 
@@ -1770,6 +1859,7 @@ bool plan_sweep_warp(int n, int elem_bytes, int w, int CS, int K, int C, SweepPl
   out->smem = smem;
   out->ml = 0;
   out->warp = 1;
+  out->ckpt = 0;
   return true;
 }
 
@@ -1828,16 +1918,21 @@ void warp_obs_table(const SweepPlan& p, int n, int nos, const int* obs_ptr, cons
   }
 }
 
-bool plan_sweep_ml(int n, int elem_bytes, int w, int K, int A, SweepPlan* out) {
+bool plan_sweep_ml(int n, int elem_bytes, int w, int K, int A, SweepPlan* out, bool ckpt) {
   const int C = (elem_bytes == 8) ? 4 : 8;
-  if (A <= 0) A = (elem_bytes == 8) ? 512 : 256;
+  // default threads: 512 (FP64) or 256 (FP32); checkpointed plans 256, whose
+  // shared memory also holds K recomputed states of the region
+  if (A <= 0) A = (elem_bytes == 8 && !ckpt) ? 512 : 256;
   if (A % 32 != 0 || A > kMaxThreads || K < 1 || K > kMaxRefresh) return false;
   const int E = A * C;
-  const int HL = 8 * K + 8;
+  const int HL = ckpt ? ckpt_halo(K) : 8 * K + 8;
   const int Ttile = E - 2 * HL;
   if (K < 1 || Ttile < 64) return false;
-  const size_t smem = sweep_smem_bytes(A, C, w, elem_bytes);
+  size_t smem = sweep_smem_bytes(A, C, w, elem_bytes);
+  // a checkpointed plan keeps the K recomputed states of its region
+  if (ckpt) smem = ((smem + 15) / 16) * 16 + (size_t)K * E * elem_bytes;
   if (smem > 227 * 1024) return false;
+  out->ckpt = ckpt ? K : 0;
   out->CS = (n + Ttile - 1) / Ttile;
   out->C = C;
   out->A = A;
@@ -1905,6 +2000,17 @@ void obs_table(const SweepPlan& p, int n, int nos, const int* obs_ptr, const int
 
 template <typename T>
 cudaError_t launch_one(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t s) {
+  // checkpointed launches (multi-launch plans: C = 4 FP64, 8 FP32); the
+  // nonlinear sweep only stores the checkpoint rows, which the general
+  // kernel does
+  if (a.ckpt > 0 && a.mode != MODE_NL) {
+    if constexpr (sizeof(T) == 8) {
+      if (p.C == 4) return launch_impl<T, 4, false, true>(a, p, s);
+    } else {
+      if (p.C == 8) return launch_impl<T, 8, false, true>(a, p, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   if constexpr (sizeof(T) == 8) {
     const bool stg = a.stages != nullptr && a.mode != MODE_NL;
     if (p.C == 4) return stg ? launch_impl<T, 4, true>(a, p, s) : launch_impl<T, 4, false>(a, p, s);
@@ -1924,7 +2030,10 @@ cudaError_t launch_sweep(const SweepArgs<T>& a0, const SweepPlan& p, cudaStream_
   a.HL = p.HL;
   a.E = p.E;
   a.K = p.K;
+  a.ckpt = p.ml ? p.ckpt : 0;
+  a.xseg_off = a.ckpt ? (int)(((sweep_smem_bytes(p.A, p.C, a0.w, (int)sizeof(T)) + 15) / 16) * 16) : 0;
   if (a.ncol <= 0) return cudaSuccess;
+  if (a.ckpt && a.stages != nullptr && a.mode != MODE_NL) return cudaErrorInvalidValue;
   if (p.warp) {
     if (a.mode != MODE_HVP || a.items != nullptr || a.wtab == nullptr) return cudaErrorInvalidValue;
     a.ml = 0;
@@ -1977,10 +2086,12 @@ cudaError_t launch_sweep(const SweepArgs<T>& a0, const SweepPlan& p, cudaStream_
       cur = 1 - cur;
     }
   }
-  for (int t1 = N; t1 > 0; t1 -= K) {
+  // backward in chunks of K steps (checkpointed: aligned on the checkpoints,
+  // the last chunk first, possibly shorter)
+  for (int t1 = N; t1 > 0; t1 = a.b0) {
     a.f0 = a.f1 = 0;
     a.b1 = t1;
-    a.b0 = (t1 - K > 0) ? t1 - K : 0;
+    a.b0 = a.ckpt ? ((t1 - 1) / K) * K : ((t1 - K > 0) ? t1 - K : 0);
     a.st_in = buf[cur];
     a.st_out = buf[1 - cur];
     cudaError_t e = launch_one<T>(a, p, s);

@@ -90,3 +90,17 @@ def test_refresh_period_is_bounded(kind):
     C = 0 if kind != "warp" else 8
     for K in (4097, 1 << 28, (1 << 31) - 1):
         assert P.plan_tiling(4096, False, 50, kind, K=K, C=C, **kw) is None
+
+
+@pytest.mark.parametrize("fp64", [True, False])
+def test_checkpointed_multi_launch_plans(fp64):
+    # the halo covers the recomputed states' edge errors plus the adjoint's
+    # reach (19K + 8), and K states of the region fit in shared memory
+    for K in (1, 2, 4, 6, 8):
+        p = P.plan_tiling(65536, fp64, 50, "multi-launch", K=K, ckpt=True)
+        assert p is not None and p["halo"] == 19 * K + 8 and p["K"] == K
+        assert p["owned"] == p["threads"] * p["C"] - 2 * p["halo"] and p["owned"] >= 64
+        assert p["smem"] <= SMEM_LIMIT
+        assert p["smem"] >= K * p["threads"] * p["C"] * (8 if fp64 else 4)
+    # too long a segment for shared memory (FP64) or for the tile
+    assert P.plan_tiling(65536, True, 50, "multi-launch", K=20, ckpt=True) is None
