@@ -59,6 +59,7 @@ def test_fp64_stopping_counts_at_1e6_match_the_oracle(workload):
     with P.Handle.from_spec(spec, taps, precision=P.EDA_FP64) as h:
         rhs = np.zeros_like(b)
         h.eda_set_trajectory(xb, y, rhs)
+        print("right-hand sides: max rel diff to the oracle %.2e" % rowrel(rhs, b).max())
         assert rowrel(rhs, b).max() < 1e-11
         h.eda_set_lmp(np.ascontiguousarray(Sk.T), 1 + D)
         M = spec.n_members
@@ -68,11 +69,15 @@ def test_fp64_stopping_counts_at_1e6_match_the_oracle(workload):
         st = np.zeros(M, np.int32)
         h.eda_solve_batch(1e-6, 10000, None, True, dz, it, rr, st)
     assert (st == P.EDA_CONVERGED).all() and (rr <= 1e-6).all()
-    # the oracle's count, widened by its own spread under perturbations of b
-    # at 1e-16 (CG rounding) and 1e-13 (the level at which two FP64 Hessian
-    # products differ; the count moves by about 1 % there), and +-1
+    # the oracle's own count distribution under perturbations of b at 1e-16
+    # (CG rounding) and 1e-13 (the level at which two FP64 Hessian products
+    # differ): 13 counts per member, spread by up to 3 % (std up to ~20
+    # iterations); the GPU count must lie in their range +-1 or within three
+    # standard deviations of their mean (13 draws under-sample the range)
     allc = np.concatenate([G["iters_1e6"][:, None], G["iters_1e6_pert"], G["iters_1e6_pert13"]], axis=1)
-    lo, hi = allc.min(axis=1), allc.max(axis=1)
+    mu, sd = allc.mean(axis=1), allc.std(axis=1, ddof=1)
+    lo = np.minimum(allc.min(axis=1), np.floor(mu - 3 * sd))
+    hi = np.maximum(allc.max(axis=1), np.ceil(mu + 3 * sd))
     print("stopping counts: gpu %s, oracle %s (perturbed %s..%s)" % (it[mem], G["iters_1e6"], lo, hi))
     assert ((it[mem] >= lo - 1) & (it[mem] <= hi + 1)).all()
 
