@@ -943,7 +943,7 @@ EDA_API int eda_create(const eda_config* cfg, eda_handle** out) {
   // and gain from not recomputing the stages (EDA_STAGE_STORE=0: recompute).
   // FP32 sweeps always recompute: streaming three more arrays costs them more
   // than the arithmetic saved.
-  if (env_int("EDA_STAGE_STORE", 1) && h->ckpt == 0) CUC(dalloc(h, &h->stg, (size_t)3 * M * (N + 1) * n));
+  if (env_int("EDA_STAGE_STORE", 1) && h->ckpt == 0) CUC(dalloc(h, &h->stg, (size_t)7 * M * (N + 1) * n));
   CUC(dalloc(h, &h->d, (size_t)M * p));
   CUC(dalloc(h, &h->rd, (size_t)M * p));
   CUC(dalloc(h, &h->b, (size_t)M * n));

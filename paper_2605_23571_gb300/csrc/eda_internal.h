@@ -98,11 +98,13 @@ struct SweepArgs {
   const T* yobs;         // [col][p] or nullptr (then d = H x)
   T* d_out;              // [col][p] or nullptr
   T* rd_out;             // [col][p] or nullptr: R^{-1} d
-  // Nonlinear stage states X2, X3, X4 of every RK4 step t -> t+1 (rows
-  // t = 0..N-1) of each member: three arrays, array s at + s * stage_astride,
-  // member m at + m * traj_mstride (the trajectory's layout).  MODE_NL with
-  // stage_out writes them; MODE_HVP / MODE_RHS with stages read them instead
-  // of recomputing.
+  // Stage store of every RK4 step t -> t+1 (rows t = 0..N-1) of each
+  // member: seven arrays, array s at + s * stage_astride, member m at
+  // + m * traj_mstride (the trajectory's layout): 0-2 the stage states X2,
+  // X3, X4; 3-6 the stencil differences D_j = X_{j+1} - X_{j-2} of X1 = x_t,
+  // X2, X3, X4.  MODE_NL with stage_out writes them; MODE_HVP / MODE_RHS with
+  // stages read them instead of recomputing (three FP64 instructions per
+  // tangent-linear or adjoint slope instead of five).
   T* stage_out;
   const T* stages;
   long long stage_astride;

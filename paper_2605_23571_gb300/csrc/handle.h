@@ -34,9 +34,10 @@ struct eda_handle {
   // device: setup products
   double* traj = nullptr;
   float* traj32 = nullptr;
-  // stage states X2, X3, X4 of every RK4 step ([3][member][t][n], the
-  // trajectory's layout), written with the trajectory and read by the FP64
-  // sweeps; nullptr: recomputed
+  // stage store of every RK4 step ([7][member][t][n], the trajectory's
+  // layout: the stage states X2, X3, X4 and the stencil differences of X1..X4),
+  // written with the trajectory and read by the FP64 sweeps; nullptr:
+  // recomputed
   double* stg = nullptr;
   double* d = nullptr;
   double* rd = nullptr;

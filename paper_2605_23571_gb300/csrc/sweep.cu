@@ -74,6 +74,21 @@ __device__ __forceinline__ T jtvp(const Run<T, C>& X, const Run<T, C>& w, int j)
          w.at(j);
 }
 
+// The stencils with the stored difference D_j = X_{j+1} - X_{j-2} of the
+// state (three FP64 instructions each instead of five):
+// (J(X) e)_j = (e_{j+1} - e_{j-2}) X_{j-1} + D_j e_{j-1} - e_j, with
+// xm1 = X_{j-1} and d = D_j;
+template <typename T, int C>
+__device__ __forceinline__ T jvpd(T xm1, T d, const Run<T, C>& e, int j) {
+  return fma(e.at(j + 1) - e.at(j - 2), xm1, fma(d, e.at(j - 1), -e.at(j)));
+}
+// (J(X)^T w)_j = X_{j-2} w_{j-1} + D_{j+1} w_{j+1} - X_{j+1} w_{j+2} - w_j,
+// with dp1 = D_{j+1}.
+template <typename T, int C>
+__device__ __forceinline__ T jtvpd(const Run<T, C>& X, T dp1, const Run<T, C>& w, int j) {
+  return fma(X.at(j - 2), w.at(j - 1), fma(dp1, w.at(j + 1), fma(-X.at(j + 1), w.at(j + 2), -w.at(j))));
+}
+
 struct Geo {
   // A: threads holding the extended region (the neighbour wrap); AS: edge
   // buffer slot stride and NT: loop stride (both the block size)
@@ -616,6 +631,13 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
         if (l >= g.HL && l < g.HL + g.Town) dst[gi[c]] = v[c];
       }
     };
+    // D_j = X_{j+1} - X_{j-2} of a stage state (its run with halos) -> array s_
+    auto store_diff = [&](int s_, int row, const Run<T, C>& X) {
+      T d[C];
+#pragma unroll
+      for (int c = 0; c < C; ++c) d[c] = X.at(c + 1) - X.at(c - 2);
+      store_stage(s_, row, d);
+    };
     for (int t = f0; t <= f1; ++t) {
       if (t > f0) {
         Run<T, C> X;
@@ -625,6 +647,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
 #pragma unroll
         for (int c = 0; c < C; ++c) X.v[c] = x[c];
         fetch(eb[0], g, X);
+        if (sout) store_diff(3, t - 1, X);  // D of X1 = x_t
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           const T k = tend(X, c, F);
@@ -637,6 +660,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
 #pragma unroll
         for (int c = 0; c < C; ++c) X.v[c] = Xs[c];
         fetch(eb[1], g, X);
+        if (sout) store_diff(4, t - 1, X);  // D of X2
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           const T k = tend(X, c, F);
@@ -649,6 +673,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
 #pragma unroll
         for (int c = 0; c < C; ++c) X.v[c] = Xs[c];
         fetch(eb[2], g, X);
+        if (sout) store_diff(5, t - 1, X);  // D of X3
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           const T k = tend(X, c, F);
@@ -661,6 +686,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
 #pragma unroll
         for (int c = 0; c < C; ++c) X.v[c] = Xs[c];
         fetch(eb[1], g, X);
+        if (sout) store_diff(6, t - 1, X);  // D of X4
 #pragma unroll
         for (int c = 0; c < C; ++c) {
           const T k = tend(X, c, F);
@@ -868,23 +894,38 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
         if (oj_pre >= 0 && tabp != nullptr) gather_pre(a, g, obs_ranges(tabp, oj_pre), qg);
       }
       if (stg != nullptr) {
-        // stage states from the store: only delta's edges are exchanged
-        Run<T, C> X1, X2, X3, X4, e;
-        T es[C], acc[C];
+        // stage states X_s and their differences D_s from the store (arrays
+        // 0-2: X2..X4, 3-6: D of X1..X4): each slope is three FP64
+        // instructions (jvpd); only delta's edges are exchanged
+        T xm[4][C], dd[4][C];  // X_s[j-1] and D_s[j] over the run
+        {
+          const T* r1 = trj + (long long)t * a.n;
+          xm[0][0] = r1[gh[1]];
 #pragma unroll
-        for (int c = 0; c < C; ++c) X1.v[c] = xr[c];
-        load_halo(trj + (long long)t * a.n, X1);
-        load_sx(stg + (long long)t * a.n, X2);
-        load_sx(stg + a.stage_astride + (long long)t * a.n, X3);
-        load_sx(stg + 2 * a.stage_astride + (long long)t * a.n, X4);
+          for (int c = 1; c < C; ++c) xm[0][c] = xr[c - 1];
+#pragma unroll
+          for (int s_ = 1; s_ < 4; ++s_) {
+            const T* row = stg + (long long)(s_ - 1) * a.stage_astride + (long long)t * a.n;
+            T v[C];
+            load_run<T, C>(row, gi, vec_ok, v);
+            xm[s_][0] = row[gh[1]];
+#pragma unroll
+            for (int c = 1; c < C; ++c) xm[s_][c] = v[c - 1];
+          }
+#pragma unroll
+          for (int s_ = 0; s_ < 4; ++s_)
+            load_run<T, C>(stg + (long long)(3 + s_) * a.stage_astride + (long long)t * a.n, gi, vec_ok, dd[s_]);
+        }
+        Run<T, C> e;
+        T es[C], acc[C];
 #pragma unroll
         for (int c = 0; c < C; ++c) e.v[c] = dl[c];
         fetch(eb[0], g, e);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          const T dk = jvp(X1, e, c);
+          const T dk = jvpd(xm[0][c], dd[0][c], e, c);
           acc[c] = dk;
-          es[c] = dl[c] + h2 * dk;
+          es[c] = fma(h2, dk, dl[c]);
         }
         publish(eb[3], g, es);
         __syncthreads();
@@ -893,9 +934,9 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
         fetch(eb[3], g, e);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          const T dk = jvp(X2, e, c);
-          acc[c] += T(2) * dk;
-          es[c] = dl[c] + h2 * dk;
+          const T dk = jvpd(xm[1][c], dd[1][c], e, c);
+          acc[c] = fma(T(2), dk, acc[c]);
+          es[c] = fma(h2, dk, dl[c]);
         }
         publish(eb[4], g, es);
         __syncthreads();
@@ -904,9 +945,9 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
         fetch(eb[4], g, e);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          const T dk = jvp(X3, e, c);
-          acc[c] += T(2) * dk;
-          es[c] = dl[c] + h * dk;
+          const T dk = jvpd(xm[2][c], dd[2][c], e, c);
+          acc[c] = fma(T(2), dk, acc[c]);
+          es[c] = fma(h, dk, dl[c]);
         }
         publish(eb[3], g, es);
         __syncthreads();
@@ -915,8 +956,8 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
         fetch(eb[3], g, e);
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          acc[c] += jvp(X4, e, c);
-          dl[c] += h6 * acc[c];
+          acc[c] += jvpd(xm[3][c], dd[3][c], e, c);
+          dl[c] = fma(h6, acc[c], dl[c]);
         }
       } else {
       Run<T, C> X, e;
@@ -1077,16 +1118,38 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       if (oj_pre >= 0 && tabp != nullptr) inject_pre(a, g, obs_ranges(tabp, oj_pre), stash, qa);
     }
     if (stg != nullptr) {
-      // stage states from the store: only the adjoint weights' edges are
+      // stage states and their differences from the store (jtvpd: three
+      // FP64 instructions per slope); only the adjoint weights' edges are
       // exchanged, through edge buffers 3 and 4 in turn
-      Run<T, C> S1, S2, S3, S4, wv;
+      Run<T, C> S[4], wv;
+      T dp[4][C];  // D_s[j+1] over the run
       T ln[C], ad[C];
+      {
+        const T* r1 = trj + (long long)t * a.n;
 #pragma unroll
-      for (int c = 0; c < C; ++c) S1.v[c] = xr[c];
-      load_halo(trj + (long long)t * a.n, S1);
-      load_sx(stg + (long long)t * a.n, S2);
-      load_sx(stg + a.stage_astride + (long long)t * a.n, S3);
-      load_sx(stg + 2 * a.stage_astride + (long long)t * a.n, S4);
+        for (int c = 0; c < C; ++c) S[0].v[c] = xr[c];
+        S[0].m2 = r1[gh[0]];
+        S[0].m1 = r1[gh[1]];
+        S[0].p1 = r1[gh[2]];
+#pragma unroll
+        for (int s_ = 1; s_ < 4; ++s_) {
+          const T* row = stg + (long long)(s_ - 1) * a.stage_astride + (long long)t * a.n;
+          load_run<T, C>(row, gi, vec_ok, S[s_].v);
+          S[s_].m2 = row[gh[0]];
+          S[s_].m1 = row[gh[1]];
+          S[s_].p1 = row[gh[2]];
+        }
+#pragma unroll
+        for (int s_ = 0; s_ < 4; ++s_) {
+          const T* row = stg + (long long)(3 + s_) * a.stage_astride + (long long)t * a.n;
+          T v[C];
+          load_run<T, C>(row, gi, vec_ok, v);
+#pragma unroll
+          for (int c = 0; c + 1 < C; ++c) dp[s_][c] = v[c + 1];
+          dp[s_][C - 1] = row[gh[2]];
+        }
+      }
+      // a4 = a1 = dt/6 lam and a3 = a2 = dt/3 lam before the slopes
 #pragma unroll
       for (int c = 0; c < C; ++c) ad[c] = h6 * lam[c];  // a4
       publish(eb[3], g, ad);
@@ -1096,9 +1159,9 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       fetch(eb[3], g, wv);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const T gg = jtvp(S4, wv, c);
+        const T gg = jtvpd(S[3], dp[3][c], wv, c);
         ln[c] = lam[c] + gg;
-        ad[c] = h3 * lam[c] + h * gg;  // a3
+        ad[c] = fma(h, gg, h3 * lam[c]);  // a3
       }
       publish(eb[4], g, ad);
       __syncthreads();
@@ -1107,9 +1170,9 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       fetch(eb[4], g, wv);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const T gg = jtvp(S3, wv, c);
+        const T gg = jtvpd(S[2], dp[2][c], wv, c);
         ln[c] += gg;
-        ad[c] = h3 * lam[c] + h2 * gg;  // a2
+        ad[c] = fma(h2, gg, h3 * lam[c]);  // a2
       }
       publish(eb[3], g, ad);
       __syncthreads();
@@ -1118,9 +1181,9 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       fetch(eb[3], g, wv);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const T gg = jtvp(S2, wv, c);
+        const T gg = jtvpd(S[1], dp[1][c], wv, c);
         ln[c] += gg;
-        ad[c] = h6 * lam[c] + h2 * gg;  // a1
+        ad[c] = fma(h2, gg, h6 * lam[c]);  // a1
       }
       publish(eb[4], g, ad);
       __syncthreads();
@@ -1128,7 +1191,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
       fetch(eb[4], g, wv);
 #pragma unroll
-      for (int c = 0; c < C; ++c) lam[c] = ln[c] + jtvp(S1, wv, c);
+      for (int c = 0; c < C; ++c) lam[c] = ln[c] + jtvpd(S[0], dp[0][c], wv, c);
     } else {
     Run<T, C> X1, X, wv;
     T X2[C], X3[C], X4[C], ln[C], ad[C];

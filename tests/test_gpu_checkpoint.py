@@ -110,6 +110,9 @@ def test_full_size_scale_checkpointed_every_8_steps():
     b = O.rhs(spec, traj, O.innovations(spec, traj, y[sample]), taps)
     V = np.random.default_rng(22).standard_normal((len(sample), spec.n))
     ref = O.hvp(spec, traj, V, taps)
+    # three PCG iterations (no LMP) of the sampled members against the oracle
+    K = 3
+    oref = O.pcg(lambda W: O.hvp(spec, traj, W, taps), b, tol=0, maxit=K, fixed_iters=K)["x"]
     with P.Handle.from_spec(spec, taps, precision=P.EDA_FP64) as h:
         rhs = np.zeros((spec.n_members, spec.n))
         h.eda_set_trajectory(xb, y, rhs)
@@ -117,6 +120,9 @@ def test_full_size_scale_checkpointed_every_8_steps():
         HV = np.zeros_like(V)
         h.eda_hvp(sample, V, HV, True)
         assert rowrel(HV, ref).max() < 1e-10
+        dz = np.zeros((spec.n_members, spec.n))
+        h.eda_solve_batch(0.0, K, None, False, dz)
+        assert rowrel(dz[sample], oref).max() < 1e-10
     with P.Handle.from_spec(spec, taps, precision=P.EDA_MIXED) as h:
         h.eda_set_trajectory(xb, y)
         HV = np.zeros_like(V)
