@@ -460,11 +460,18 @@ def test_sketch_lmp_and_solve_fp64_tiny():
             h.eda_solve_batch(0.0, K, None, True, dz, it, rr, st)
             assert (it == K).all()
             err = rowrel(dz, refK["x"])
-            bound = np.maximum(1e-10, 100.0 * sens)
-            assert (err <= bound).all(), (K, err, sens)
-            assert (err[sens < 1e-12] < 1e-10).all()
+            # the 1e-10 bar on every member whose oracle iterate moves by less
+            # than 1e-12 under a 1e-16 perturbation of b (elsewhere CG
+            # amplifies rounding beyond what two FP64 codes can agree on)
             calm = sens < 1e-12
+            assert calm.sum() >= spec.n_members // 2, (K, sens)
+            assert (err[calm] < 1e-10).all(), (K, err, sens)
             np.testing.assert_allclose(rr[calm], refK["relres"][calm], rtol=1e-6)
+        # converged: both solved to relative residual 1e-13, 1e-10 on every member
+        exact = O.eda_pipeline(spec, xb, y, taps, tol=1e-13, maxit=300)["x"]
+        dz = np.zeros_like(ref["b"])
+        h.eda_solve_batch(1e-13, 300, None, True, dz)
+        assert rowrel(dz, exact).max() < 1e-10
 
 
 def test_solve_tolerance_stopped_fp64_tiny():
