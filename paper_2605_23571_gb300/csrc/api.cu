@@ -1451,6 +1451,21 @@ __global__ void ucoef_kernel(int k, const double* c, double* uv) {
   }
 }
 
+// trace_cols[kind] += sign * (sum of the members' iteration counts): around
+// a persistent PCG launch, the member iterations (one swept column each) it ran
+__global__ void iters_delta_kernel(unsigned long long* acc, const eda::PcgScalars* sc, int M, int sign) {
+  __shared__ long long red[256];
+  long long s = 0;
+  for (int m = threadIdx.x; m < M; m += blockDim.x) s += sc[m].iters;
+  red[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    long long t = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) t += red[i];
+    *acc += (unsigned long long)(sign * t);
+  }
+}
+
 // Coefficients of U_theta (sqrt(theta) (1 + lambda_i)^{-1/2} - 1, Section
 // 3.1, Eq. (lmp)) and of its inverse, for the current LMP.
 int prep_ucoef(eda_handle* h) {
@@ -1578,6 +1593,84 @@ int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int*
                               0, tol, maxit, fixed, lmp, 1, h->nactive, h->st, zext ? h->z : nullptr));
   // the first update accumulates the projections of r_1 from zero
   CU(h, cudaMemsetAsync(Wk, 0, (size_t)M * kmax * sizeof(TS), h->st));
+  // the persistent PCG: the whole loop in one launch (one cluster per
+  // member) where the tiling is a cluster plan and nothing per iteration is
+  // asked of the host (no cost record, residual replacement or outside LMP)
+  const SweepPlan& gp = sweep64 ? h->plan64 : h->plan32;
+  const bool wplan = sweep64 ? h->wplan64.warp : h->wplan32.warp;
+  if (maxit >= 1 && env_int("EDA_PERSIST", 1) && !lm.split && !lm.tc && replace_every == 0 &&
+      h->pgrid.one.jhist == nullptr && !gp.ml && !gp.warp && !gp.ckpt && !wplan) {
+    int rc = ensure_stash(h, M);
+    if (rc) return rc;
+    if (!h->pacc) CU(h, dalloc(h, &h->pacc, (size_t)M));
+    if (!h->Wp) {
+      double* wp = nullptr;  // 8 bytes per entry serves both precisions
+      CU(h, dalloc(h, &wp, (size_t)2 * M * kmax));
+      h->Wp = wp;
+    }
+    CU(h, cudaMemsetAsync(h->pacc, 0, (size_t)M * sizeof(eda::PersistAcc), h->st));
+    CU(h, cudaMemsetAsync(h->Wp, 0, (size_t)2 * M * kmax * sizeof(TS), h->st));
+    eda::PersistArgs<TS> pa{};
+    pa.sw = base_args<TS>(h);
+    pa.sw.mode = eda::MODE_HVP;
+    pa.sw.ncol = M;
+    pa.sw.col_member = h->cols;
+    if constexpr (sizeof(TS) == 8) {
+      pa.sw.V = h->pv;
+      pa.sw.OUT = h->q;
+      pa.sw.stash = h->stash;
+      pa.sw.obs_tab = h->tab64_ok ? h->tab64 : nullptr;
+    } else {
+      pa.sw.V64 = h->pv;
+      pa.sw.OUT64 = h->q;
+      pa.sw.stash = h->stash32;
+      pa.sw.obs_tab = h->tab32_ok ? h->tab32 : nullptr;
+    }
+    pa.sw.v_stride = h->n;
+    pa.sw.out_stride = h->n;
+    pa.sw.stash_stride = h->p;
+    pa.n = h->n;
+    pa.M = M;
+    pa.k = h->k;
+    pa.kmax = kmax;
+    pa.x = h->x;
+    pa.r = h->r;
+    pa.z = h->z;
+    pa.p = h->pv;
+    pa.q = h->q;
+    pa.S = static_cast<const TS*>(h->pgrid.one.S);
+    pa.c = h->cv;
+    pa.sc = h->sc;
+    pa.acc = h->acc;
+    pa.active = h->active;
+    pa.nactive = h->nactive;
+    pa.tol = tol;
+    pa.etol = h->pgrid.one.etol;
+    pa.maxit = maxit;
+    pa.fixed = fixed;
+    pa.use_lmp = lmp;
+    pa.pacc = h->pacc;
+    pa.W = reinterpret_cast<TS*>(h->Wp);
+    const bool traced = h->trace_on;
+    if (traced) {
+      // every persistent launch is traced: its duration, and the columns its
+      // sweeps computed (the member iterations it ran)
+      rc = trace_begin(h, sweep64 ? 0 : 1, nullptr, 0);
+      if (rc) return rc;
+      eda::count_launch();
+      iters_delta_kernel<<<1, 256, 0, h->st>>>(h->trace_cols + (sweep64 ? 0 : 1), h->sc, M, -1);
+    }
+    CU(h, eda::launch_pcg_persist<TS>(pa, gp, h->st));
+    if (traced) {
+      rc = trace_end(h);
+      if (rc) return rc;
+      eda::count_launch();
+      iters_delta_kernel<<<1, 256, 0, h->st>>>(h->trace_cols + (sweep64 ? 0 : 1), h->sc, M, 1);
+    }
+    CU(h, cudaStreamSynchronize(h->st));
+    *it_done = it0 + maxit;
+    return EDA_OK;
+  }
   constexpr int R = eda_handle::kRing;
   // every member stops at convergence or at its own maxit-th iteration, so
   // no loop needs more than maxit iterations

@@ -103,6 +103,8 @@ struct eda_handle {
   void* Wcc = nullptr;
   long long wcc_cap = 0;        // bytes
   int* tc_timeout = nullptr;
+  eda::PersistAcc* pacc = nullptr;  // persistent PCG: per-member accumulators
+  void* Wp = nullptr;               // persistent PCG: projections [2][M][kmax] (FP64 or FP32)
   double* bh = nullptr;         // split PCG: U b
   double* tbuf = nullptr;       // split PCG: U p
   SweepPlan plan64{}, plan32{};

@@ -127,4 +127,40 @@ cudaError_t pcg2_replace(const PcgGrid& G, int mmax, const double* b,
 cudaError_t pcg2_col_dot(int n, int ncol, const double* v, const double* hv, const int* active, PcgAcc* acc,
                          cudaStream_t s);
 
+// ------------------------------------------------------------------------
+// Persistent PCG (one launch per solve phase): one thread-block cluster per
+// member runs the whole iteration -- the sweep q = (I + A) p of its column,
+// then alpha, x, r, ||r||^2, ||x||^2 and the LMP projections S^T r on each
+// CTA's tile, the stopping test, z = r + S (c o w), r.z, beta and p -- with
+// the reductions through per-member global accumulators (atomics, then a
+// cluster barrier) and no host involvement, until the member stops.
+
+// Accumulators of one member, by iteration parity (a slot is cleared one
+// iteration after it was read; zeroed before the launch).
+struct PersistAcc {
+  double pq[2], rr[2], xx[2], rz[2];
+};
+
+template <typename T>
+struct PersistArgs {
+  SweepArgs<T> sw;      // MODE_HVP of column m on member m: V = p, OUT = q, identity included
+  int n, M, k, kmax;
+  double *x, *r, *z, *p, *q;  // [M][n]
+  const T* S;           // k x n column-major, the LMP arithmetic type
+  const double* c;      // k coefficients
+  PcgScalars* sc;
+  const PcgAcc* acc;    // r.z of the loop start (slot 0, from pcg2_precond with init)
+  int* active;
+  int* nactive;
+  double tol, etol;
+  int maxit, fixed, use_lmp;
+  PersistAcc* pacc;     // [M]
+  T* W;                 // [2][M][kmax] projections by parity
+};
+
+// Launches the persistent PCG over the M members (a cluster tiling, not
+// multi-launch, not warp-tiled).  Returns a cudaError_t.
+template <typename T>
+cudaError_t launch_pcg_persist(const PersistArgs<T>& a, const SweepPlan& plan, cudaStream_t s);
+
 }  // namespace eda

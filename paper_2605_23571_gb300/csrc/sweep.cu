@@ -216,7 +216,7 @@ __device__ __forceinline__ void scatter_obs(const int* __restrict__ idx, const T
     for (int u = 0; u < 4; ++u) {
       const int kk = k + u * A;
       ii[u] = kk < k1 ? __ldg(idx + kk) : 0;
-      vv[u] = kk < k1 ? stash[kk] : T(0);
+      vv[u] = kk < k1 ? __ldcg(stash + kk) : T(0);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -393,7 +393,7 @@ __device__ __forceinline__ void inject_pre(const SweepArgs<T>& a, const Geo& g, 
     int k, base;
     inject_k(tb, j, &k, &base);
     q.idx[u] = j < cnt ? __ldg(a.obs_idx + k) : 0;
-    q.val[u] = j < cnt ? stash[k] : T(0);
+    q.val[u] = j < cnt ? __ldcg(stash + k) : T(0);
   }
 }
 
@@ -412,7 +412,7 @@ __device__ __forceinline__ void inject_use(const SweepArgs<T>& a, const Geo& g, 
   for (int j = g.tid + kObsPre * g.NT; j < cnt; j += g.NT) {
     int k, base;
     inject_k(tb, j, &k, &base);
-    mir[__ldg(a.obs_idx + k) - base] = stash[k];
+    mir[__ldg(a.obs_idx + k) - base] = __ldcg(stash + k);
   }
 }
 
@@ -479,8 +479,10 @@ constexpr int kObsTabCap = 2048;  // entries of a CTA's observation range rows c
 // than streaming three more arrays).
 // CK: the kernel recomputes its launch's states from a checkpointed
 // trajectory (multi-launch plans with ckpt > 0; never with STG).
+// One column's sweep by this CTA (the body of sweep_kernel and of the
+// persistent PCG kernel, which calls it once per iteration).
 template <typename T, int C, bool STG, bool CK>
-__global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a0) {
+__device__ __forceinline__ void sweep_body(const SweepArgs<T>& a0, const int col) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
 
@@ -488,7 +490,6 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
   Geo g;
   g.CS = a.CS;
   g.rank = (a.CS > 1) ? (a.ml ? (int)(blockIdx.x % a.CS) : (int)cg::this_cluster().block_rank()) : 0;
-  const int col = blockIdx.x / a.CS;
   if (col >= a.ncol) return;
   // launch-wide shared-memory layout (the group launch sizes it for its largest problem)
   const int Emax = (int)blockDim.x * C;
@@ -858,7 +859,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       for (int j = g.tid; j < cnt; j += g.NT) {
         int gk = (g.gbase - w + j) % g.n;
         if (gk < 0) gk += g.n;
-        stage[j] = V64 ? (T)V64[gk] : V[gk];
+        stage[j] = V64 ? (T)__ldcg(V64 + gk) : __ldcg(V + gk);
       }
       __syncthreads();
     }
@@ -1088,7 +1089,7 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
       const int k0 = a.obs_ptr[oj], k1 = a.obs_ptr[oj + 1];
       for (int k = k0 + g.tid; k < k1; k += g.NT) {
         const int gk = a.obs_idx[k];
-        const T val = stash[k];
+        const T val = __ldcg(stash + k);
         int l = ((gk - g.gbase) % g.n + g.n) % g.n;
         for (; l < g.E; l += g.n) mir[l] = val;
       }
@@ -1316,6 +1317,211 @@ __global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a
     bhalf_from_mirrors<T, C, T>(a, g, mir, stage, cf, a.OUT + voff, ident ? V64 : nullptr, ident ? V : nullptr,
                                 dot);
   }
+}
+
+template <typename T, int C, bool STG, bool CK>
+__global__ void __launch_bounds__(kMaxThreads) sweep_kernel(const SweepArgs<T> a0) {
+  sweep_body<T, C, STG, CK>(a0, (int)(blockIdx.x / a0.CS));
+}
+
+// Sum of v over the CTA (every thread gets it); red: 32 doubles of shared
+// memory that no other code uses in between.
+__device__ __forceinline__ double cta_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+  return t;
+}
+
+// Persistent PCG, one cluster per member (pcg.h).  Every decision to leave
+// the loop is taken by every CTA of the cluster from the same values (read
+// after the same cluster barrier), so the cluster's barriers stay matched;
+// every member stops by its iteration budget at the latest.  Values other
+// CTAs write during the launch (the accumulators, the projections, p's halo
+// in the sweep) are read past L1 (__ldcg).
+template <typename T, int C, bool STG>
+__global__ void __launch_bounds__(kMaxThreads) pcg_persist_kernel(const PersistArgs<T> P) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int CS = P.sw.CS;
+  const int col = (int)blockIdx.x / CS;
+  if (col >= P.M) return;             // uniform over the cluster
+  if (P.active[col] == 0) return;     // uniform: written before the launch
+  const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const int n = P.n, kmax = P.kmax;
+  const int a0 = rank * P.sw.Ttile;
+  const int town = min(P.sw.Ttile, n - a0);
+  const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = NT >> 5;
+  const long long vo = (long long)col * n + a0;
+  const int k = P.use_lmp ? P.k : 0;
+  // scratch between sweeps (the sweep re-initialises its shared memory)
+  double* red = reinterpret_cast<double*>(smem_raw);
+  T* cw = reinterpret_cast<T*>(red + 32);
+  T* rt = cw + ((kmax + 3) & ~3);
+  PersistAcc* pa = P.pacc + col;
+  auto csync = [&]() {
+    __threadfence();
+    if (CS > 1) cg::this_cluster().sync();
+    else __syncthreads();
+  };
+  double rz = __ldcg(&P.acc[col].rz[0]);
+  int it = P.sc[col].iters;
+  const double bn = P.sc[col].bnorm;
+  const double tolm = P.sc[col].tolm;
+  double rel = P.sc[col].relres;
+  int status = EDA_MAXIT;
+  int par = 0;
+  SweepArgs<T> a = P.sw;
+  a.dot_stride = (int)(sizeof(PersistAcc) / sizeof(double));
+  for (;;) {
+    // q = (I + A) p with p.q into this iteration's slot
+    a.dot_out = &P.pacc[0].pq[par];
+    sweep_body<T, C, STG, false>(a, col);
+    csync();
+    const double pq = __ldcg(&pa->pq[par]);
+    if (!(pq > 0.0)) {  // breakdown (or NaN): uniform
+      status = isfinite(pq) ? EDA_BREAKDOWN : EDA_NAN;
+      break;
+    }
+    const double alpha = rz / pq;
+    double rr = 0.0, xx = 0.0;
+    for (int j = tid; j < town; j += NT) {
+      const long long g = vo + j;
+      const double xn = P.x[g] + alpha * P.p[g];
+      const double rn = P.r[g] - alpha * P.q[g];
+      P.x[g] = xn;
+      P.r[g] = rn;
+      rr += rn * rn;
+      xx += xn * xn;
+      rt[j] = (T)rn;
+    }
+    __syncthreads();
+    // the LMP projections of the new r over this tile: warp w takes modes
+    // w, w + nw, ...
+    for (int c = wid; c < k; c += nw) {
+      const T* Sc = P.S + (long long)c * n + a0;
+      T s0 = T(0);
+      for (int j = lane; j < town; j += 32) s0 += Sc[j] * rt[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      if (lane == 0) atomicAdd(&P.W[((long long)par * P.M + col) * kmax + c], s0);
+    }
+    rr = cta_sum(rr, red);
+    xx = cta_sum(xx, red);
+    if (tid == 0) {
+      atomicAdd(&pa->rr[par], rr);
+      atomicAdd(&pa->xx[par], xx);
+    }
+    csync();
+    const double rrt = __ldcg(&pa->rr[par]), xxt = __ldcg(&pa->xx[par]);
+    ++it;
+    // the stopping test of pcg2_precond
+    rel = bn > 0.0 ? sqrt(rrt) / bn : 0.0;
+    bool stop = false;
+    if (!isfinite(rel)) {
+      status = EDA_NAN;
+      stop = true;
+    } else if (P.fixed > 0) {
+      if (it >= P.fixed) {
+        status = EDA_CONVERGED;
+        stop = true;
+      }
+    } else {
+      bool fin = !(P.tol > 0.0) || rel <= P.tol;
+      if (P.etol > 0.0) {
+        const double rn = rel * bn, xn = sqrt(xxt);
+        fin = fin && xn > rn && rn <= P.etol * (xn - rn);
+      }
+      if (fin || (tolm > 0.0 && rel <= tolm)) {
+        status = EDA_CONVERGED;
+        stop = true;
+      } else if (it >= P.maxit) {  // the host launches this loop with maxit >= 1
+        status = EDA_MAXIT;
+        stop = true;
+      }
+    }
+    if (stop) break;
+    // z = r + S (c o w), r.z
+    for (int c = tid; c < k; c += NT)
+      cw[c] = (T)(P.c[c] * (double)__ldcg(&P.W[((long long)par * P.M + col) * kmax + c]));
+    __syncthreads();
+    double rzp = 0.0;
+    for (int j = tid; j < town; j += NT) {
+      const long long g = vo + j;
+      T s0 = T(0), s1 = T(0);
+      int c = 0;
+      for (; c + 2 <= k; c += 2) {
+        s0 += P.S[(long long)c * n + a0 + j] * cw[c];
+        s1 += P.S[(long long)(c + 1) * n + a0 + j] * cw[c + 1];
+      }
+      if (c < k) s0 += P.S[(long long)c * n + a0 + j] * cw[c];
+      const double rv = P.r[g];
+      const double zv = rv + (double)(s0 + s1);
+      P.z[g] = zv;
+      rzp += rv * zv;
+    }
+    rzp = cta_sum(rzp, red);
+    if (tid == 0) atomicAdd(&pa->rz[par], rzp);
+    csync();
+    const double rzn = __ldcg(&pa->rz[par]);
+    const double beta = rzn / rz;
+    rz = rzn;
+    for (int j = tid; j < town; j += NT) {
+      const long long g = vo + j;
+      P.p[g] = P.z[g] + beta * P.p[g];
+    }
+    // the other parity's slots were read last iteration: clear them for the next
+    if (rank == 0) {
+      if (tid == 0) {
+        pa->pq[par ^ 1] = 0.0;
+        pa->rr[par ^ 1] = 0.0;
+        pa->xx[par ^ 1] = 0.0;
+        pa->rz[par ^ 1] = 0.0;
+      }
+      for (int c = tid; c < k; c += NT) P.W[((long long)(par ^ 1) * P.M + col) * kmax + c] = T(0);
+    }
+    csync();  // p complete (the next sweep reads its halo) and the slots cleared
+    par ^= 1;
+  }
+  if (rank == 0 && tid == 0) {
+    P.sc[col].iters = it;
+    P.sc[col].status = status;
+    P.sc[col].relres = rel;
+    P.active[col] = 0;
+    atomicSub(P.nactive, 1);
+  }
+}
+
+template <typename T, int C, bool STG>
+cudaError_t launch_persist_impl(const PersistArgs<T>& a, const SweepPlan& p, cudaStream_t s) {
+  auto kern = pcg_persist_kernel<T, C, STG>;
+  static bool attrs_set = false;
+  if (!attrs_set) {
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (err != cudaSuccess) return err;
+    attrs_set = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.M * p.CS), 1, 1);
+  cfg.blockDim = dim3((unsigned)p.A, 1, 1);
+  cfg.dynamicSmemBytes = p.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (p.CS > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)p.CS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, kern, a);
 }
 
 // out[col][i] = (ident ? v[col][i] : 0) + sum_{|d|<=w} coef[|d|] lam[col][(i+d) mod n]
@@ -2187,6 +2393,39 @@ cudaError_t launch_sweep(const SweepArgs<T>& a0, const SweepPlan& p, cudaStream_
   return pcg2_col_dot(a.n, a.ncol, vin, vout, a.col_active, reinterpret_cast<PcgAcc*>(a.dot_out), s);
 }
 
+template <typename T>
+cudaError_t launch_pcg_persist(const PersistArgs<T>& a0, const SweepPlan& p, cudaStream_t s) {
+  if (a0.M <= 0) return cudaSuccess;
+  if (p.ml || p.warp || p.ckpt) return cudaErrorInvalidValue;
+  PersistArgs<T> a = a0;
+  a.sw.CS = p.CS;
+  a.sw.Ttile = p.Ttile;
+  a.sw.HL = p.HL;
+  a.sw.E = p.E;
+  a.sw.K = p.K;
+  a.sw.ml = 0;
+  a.sw.ckpt = 0;
+  a.sw.mode = MODE_HVP;
+  a.sw.ncol = a.M;
+  a.sw.col_active = nullptr;
+  a.sw.include_identity = 1;
+  // the between-sweep scratch (reduction slots, c o w, the r tile) fits the
+  // sweep's own shared memory
+  const size_t scratch = 32 * sizeof(double) + (size_t)(((a.kmax + 3) & ~3) + p.Ttile) * sizeof(T);
+  if (scratch > p.smem) return cudaErrorInvalidValue;
+  if constexpr (sizeof(T) == 8) {
+    const bool stg = a.sw.stages != nullptr;
+    if (p.C == 4) return stg ? launch_persist_impl<T, 4, true>(a, p, s) : launch_persist_impl<T, 4, false>(a, p, s);
+    if (p.C == 2) return stg ? launch_persist_impl<T, 2, true>(a, p, s) : launch_persist_impl<T, 2, false>(a, p, s);
+  } else {
+    if (p.C == 8) return launch_persist_impl<T, 8, false>(a, p, s);
+    if (p.C == 4) return launch_persist_impl<T, 4, false>(a, p, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template cudaError_t launch_pcg_persist<double>(const PersistArgs<double>&, const SweepPlan&, cudaStream_t);
+template cudaError_t launch_pcg_persist<float>(const PersistArgs<float>&, const SweepPlan&, cudaStream_t);
 template cudaError_t launch_sweep<double>(const SweepArgs<double>&, const SweepPlan&, cudaStream_t, double*, double*);
 template cudaError_t launch_sweep<float>(const SweepArgs<float>&, const SweepPlan&, cudaStream_t, float*, float*);
 
