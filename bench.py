@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the scale, uneven-batch and warm-start measurements")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--profile-case", choices=["fp64", "mixed"], default=None,
+                    help="profiling case for ncu: the workload's setup, sketch and LMP, then one PCG solve of "
+                         "--profile-iters fixed iterations between cudaProfilerStart/Stop; prints one line")
+    ap.add_argument("--profile-iters", type=int, default=20)
     return ap.parse_args()
 
 
@@ -144,6 +148,27 @@ class Clocks:
                 "reasons": sorted(reasons)}
 
 
+def persist_traffic_per_launch(plan, dtype, cols_per_launch):
+    """DRAM bytes (read + write) per launch of the persistent PCG kernel:
+    the committed ncu summary's bytes per member-iteration (a 20-iteration
+    capture of the same kernel and workload; the per-iteration traffic of the
+    steady state) times the member-iterations a launch of the timed steps ran,
+    or None when the code or the tiling differs from the captured one."""
+    path = PERSIST_PROFILE[dtype]
+    if plan is None or not os.path.exists(path) or cols_per_launch <= 0:
+        return None
+    txt = open(path).read()
+    m_sha = re.search(r"sweep\.cu code sha256: ([0-9a-f]{64})", txt)
+    m_b = re.search(r"dram bytes per member-iteration \(read \+ write\): ([0-9.eE+]+)", txt)
+    m_p = re.search(r"captured plan: kind=(\S+) ctas_per_vector=(\d+) threads=(\d+) C=(\d+) K=(\d+)", txt)
+    if not (m_sha and m_b and m_p) or code_sha256(SWEEP_SRC) != m_sha.group(1):
+        return None
+    cap = (m_p.group(1),) + tuple(int(v) for v in m_p.groups()[1:])
+    if cap != (plan["kind"], plan["ctas_per_vector"], plan["threads"], plan["C"], plan["K"]):
+        return None
+    return float(m_b.group(1)) * cols_per_launch
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -154,7 +179,18 @@ def measured_peaks():
 
 SWEEP_SRC = os.path.join(ROOT, "paper_2605_23571_gb300", "csrc", "sweep.cu")
 SWEEP_PROFILE = os.path.join(ROOT, "profiles", "sweep_kernel_f32_member_hvp_l96_n4096_w64_m51.md")
-SWEEP_PROFILE_F64 = os.path.join(ROOT, "profiles", "sweep_kernel_f64_member_hvp_l96_n4096_w64_m51.md")
+PERSIST_PROFILE = {"double": os.path.join(ROOT, "profiles", "pcg_persist_kernel_f64_l96_n4096_w64_m51.md"),
+                   "float": os.path.join(ROOT, "profiles", "pcg_persist_kernel_f32_l96_n4096_w64_m51.md")}
+
+
+def persist_kernel_name(plan, dtype="double"):
+    """The persistent PCG kernel a cluster tiling launches (EDA_PERSIST unset
+    or 1), or None for tilings the per-iteration launches serve."""
+    if plan["kind"] != "cluster" or os.environ.get("EDA_PERSIST", "1") == "0":
+        return None
+    return ("pcg_persist_kernel<%s,%d> (one cluster of %d CTAs x %d threads per member, halo refresh every %d "
+            "steps: the member's sweeps, CG updates, LMP and stopping test for the whole solve)"
+            % (dtype, plan["C"], plan["ctas_per_vector"], plan["threads"], plan["K"]))
 
 
 def sweep_kernel_name(plan, dtype="float"):
@@ -922,8 +958,14 @@ def run_ours(args):
     hbm_peak, peak_kind = measured_peaks()
     bytes_per_col = 4 * n * (2 * spec.nsteps + 2)
     ach32 = bytes_per_col * sw32_cols / (sw32_ms / 1e3) / 1e9
-    traffic64 = sweep_traffic_per_launch(plan64, SWEEP_PROFILE_F64)
-    traffic32 = sweep_traffic_per_launch(plan32, SWEEP_PROFILE)
+    if persist_kernel_name(plan64) is not None:
+        traffic64 = persist_traffic_per_launch(plan64, "double", sw_cols / max(1, sw_calls))
+    else:
+        traffic64 = None
+    if persist_kernel_name(plan32) is not None:
+        traffic32 = persist_traffic_per_launch(plan32, "float", sw32_cols / max(1, sw32_calls))
+    else:
+        traffic32 = sweep_traffic_per_launch(plan32, SWEEP_PROFILE)
 
     # ---- end to end through the C ABI with host buffers (headline path)
     xb_h = xb.cpu().pin_memory().numpy()
@@ -987,8 +1029,10 @@ def run_ours(args):
                          "ms_per_batched_launch_fp64": ms64, "ms_per_batched_launch_fp32": ms32},
             "roofline": {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
                          "frac": ach64 / peak64, "traffic": traffic64,
-                         "kernel": sweep_kernel_name(plan64, "double") + ": the FP64 Hessian-product sweeps of "
-                                   "the timed steps",
+                         "kernel": (persist_kernel_name(plan64, "double") or sweep_kernel_name(plan64, "double")
+                                    + ": the FP64 Hessian-product sweeps of the timed steps"),
+                         "achieved_counts": "algorithmic flops of the sweeps only (79 per element-step) over the "
+                                            "whole kernel time (the CG vector work and LMP inside it included)",
                          "flops_per_element_step": f64, "launches_timed": sw_calls, "columns": sw_cols,
                          "ms_per_launch": sw_ms / max(1, sw_calls),
                          "bytes_per_launch": bytes64_col * sw_cols / max(1, sw_calls),
@@ -997,8 +1041,8 @@ def run_ours(args):
                                       "flops x 2070 MHz (no FP64 peak is measured)"},
             "roofline_fp32_sweep": {"bound": "hbm", "achieved": ach32, "peak": hbm_peak, "unit": "GB/s",
                                     "frac": ach32 / hbm_peak, "traffic": traffic32,
-                                    "kernel": sweep_kernel_name(plan32) + ": the FP32 Hessian-product sweeps of "
-                                              "the mixed form's timed steps",
+                                    "kernel": (persist_kernel_name(plan32, "float") or sweep_kernel_name(plan32)
+                                               + ": the FP32 Hessian-product sweeps of the mixed form's timed steps"),
                                     "launches_timed": sw32_calls, "columns": sw32_cols,
                                     "ms_per_launch": sw32_ms / max(1, sw32_calls),
                                     "bytes_per_launch": bytes_per_col * sw32_cols / max(1, sw32_calls),
@@ -1020,8 +1064,49 @@ def run_ours(args):
     return 0
 
 
+def run_profile_case(args):
+    """One fixed-iteration solve of the batched workload inside a profiler
+    range: a small case of the solve's kernels for ncu (the same kernels and
+    shapes as the timed steps, a few tens of milliseconds)."""
+    import torch
+    import paper_2605_23571_gb300 as P
+    P.build()
+    dev = torch.device("cuda", 0)
+    spec, dr = workload(args.seed)
+    G = golden(spec, args.seed)
+    taps = P.bhalf_gaussian(spec.n, spec.length_scale, spec.sigma_b)
+    M, n, p = spec.n_members, spec.n, spec.p
+    prec = P.EDA_FP64 if args.profile_case == "fp64" else P.EDA_MIXED
+    with P.Handle.from_spec(spec, taps, precision=prec) as h:
+        xb = torch.empty(M, n, dtype=torch.float64, device=dev)
+        y = torch.empty(M, p, dtype=torch.float64, device=dev)
+        x0 = G["xt0"] if G is not None else spec.F + spec.spin_sigma * dr.eta_spin
+        h.eda_twin(torch.tensor(x0, device=dev), 0 if G is not None else spec.spinup,
+                   torch.tensor(dr.eta_b, device=dev), torch.tensor(dr.eta_o, device=dev), xb, y)
+        h.eda_set_trajectory(xb, y)
+        h.eda_autotune(0)
+        h.eda_sketch()
+        h.eda_build_lmp()
+        dz = torch.empty(M, n, dtype=torch.float64, device=dev)
+        h.eda_solve_batch(0.0, args.profile_iters, None, True, dz)  # warm
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h.eda_solve_batch(0.0, args.profile_iters, None, True, dz)
+        e1.record()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        plan = h.eda_sweep_plan(fp64=args.profile_case == "fp64")
+    print(json.dumps({"profile_case": args.profile_case, "workload": spec.name, "iters": args.profile_iters,
+                      "ms": e0.elapsed_time(e1), "plan": plan}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
