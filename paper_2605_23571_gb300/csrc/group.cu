@@ -61,6 +61,11 @@ struct eda_group {
   float* stash32 = nullptr;
   PcgScalars* sc = nullptr;
   eda::PcgAcc* acc = nullptr;     // per-item accumulators of an iteration
+  eda::PersistAcc* pacc = nullptr;  // persistent PCG: per-item accumulators by parity
+  double* Wp = nullptr;             // persistent PCG: projections [2][T][kmax] (8 bytes an entry)
+  int* queue = nullptr;             // persistent PCG: one work-queue head per bucket
+  std::vector<cudaStream_t> bstreams;  // persistent PCG: one stream per bucket (they run concurrently)
+  std::vector<cudaEvent_t> bevents;
   double* Wk = nullptr;           // T x max(kmax,1) LMP projections
   eda::PcgTask* tasks = nullptr;  // row chunks of every problem
   int ntasks = 0;
@@ -432,6 +437,96 @@ int group_start(eda_group* g, bool use_lmp, double tol, int maxit, int fixed) {
   return EDA_OK;
 }
 
+// The whole PCG loop of the group as one persistent launch per bucket: the
+// bucket's clusters take its (problem, member) items, largest problems first,
+// from a device-side queue and run each member's PCG to its stop (pcg.h).
+template <typename TS>
+int group_persist(eda_group* g, bool sweep64, bool use_lmp, double tol, int maxit, int fixed, int* it_io) {
+  const int kmax = std::max(g->kmax, 1);
+  std::vector<Bucket>& bs = sweep64 ? g->b64 : g->b32;
+  if (!g->pacc) GCU(g, galloc(g, &g->pacc, (size_t)g->T));
+  if (!g->Wp) GCU(g, galloc(g, &g->Wp, (size_t)2 * g->T * kmax));
+  if (!g->queue) GCU(g, galloc(g, &g->queue, (size_t)64));
+  GCU(g, cudaMemsetAsync(g->pacc, 0, (size_t)g->T * sizeof(eda::PersistAcc), g->st));
+  GCU(g, cudaMemsetAsync(g->Wp, 0, (size_t)2 * g->T * kmax * sizeof(double), g->st));
+  GCU(g, cudaMemsetAsync(g->queue, 0, (size_t)64 * sizeof(int), g->st));
+  int qi = 0;
+  // every bucket on its own stream, forked from and joined back to the group's
+  while (g->bstreams.size() < bs.size()) {
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t ev2 = nullptr;
+    GCU(g, cudaStreamCreateWithFlags(&st2, cudaStreamNonBlocking));
+    g->bstreams.push_back(st2);
+    GCU(g, cudaEventCreateWithFlags(&ev2, cudaEventDisableTiming));
+    g->bevents.push_back(ev2);
+  }
+  GCU(g, cudaEventRecord(g->join, g->st));
+  size_t bi = 0;
+  for (Bucket& b : bs) {
+    const size_t mine = bi++;
+    if (b.items.empty()) continue;
+    cudaStream_t bst = g->bstreams[mine];
+    GCU(g, cudaStreamWaitEvent(bst, g->join, 0));
+    // the between-sweep scratch must fit the bucket's shared memory
+    int tmax = 0;
+    for (int pi : b.probs)
+      tmax = std::max(tmax, sweep64 ? g->prob64[pi].Ttile : g->prob32[pi].Ttile);
+    const size_t scratch = 32 * sizeof(double) + (size_t)(((kmax + 3) & ~3) + tmax) * sizeof(TS);
+    if (scratch > b.smem || qi >= 64) return gfail(g, EDA_ERR_INVALID, "group: persistent PCG scratch does not fit");
+    SweepPlan pl{};
+    pl.CS = b.CS;
+    pl.C = sweep64 ? 4 : 8;
+    pl.A = b.A;
+    pl.E = b.A * pl.C;
+    pl.K = b.K;
+    pl.smem = b.smem;
+    eda::PersistArgs<TS> pa{};
+    pa.sw.w = b.wmax;
+    if constexpr (sizeof(TS) == 8) {
+      pa.sw.V = g->p;
+      pa.sw.OUT = g->q;
+      pa.sw.stash = g->stash64;
+      pa.sw.probs = g->d_prob64;
+    } else {
+      pa.sw.V64 = g->p;
+      pa.sw.OUT64 = g->q;
+      pa.sw.stash = g->stash32;
+      pa.sw.probs = g->d_prob32;
+    }
+    pa.sw.items = b.d_items;
+    pa.sw.flags = g->active;
+    pa.sw.n = 1;
+    pa.n = 1;
+    pa.M = g->T;
+    pa.kmax = kmax;
+    pa.x = g->x;
+    pa.r = g->r;
+    pa.z = g->z;
+    pa.p = g->p;
+    pa.q = g->q;
+    pa.sc = g->sc;
+    pa.acc = g->acc;
+    pa.active = g->active;
+    pa.nactive = g->nactive;
+    pa.tol = tol;
+    pa.maxit = maxit;
+    pa.fixed = fixed;
+    pa.use_lmp = use_lmp ? 1 : 0;
+    pa.pacc = g->pacc;
+    pa.W = reinterpret_cast<TS*>(g->Wp);
+    pa.items = b.d_items;
+    pa.nitems = (int)b.items.size();
+    pa.pprobs = g->probs;
+    pa.queue = g->queue + qi++;
+    GCU(g, eda::launch_pcg_persist<TS>(pa, pl, bst));
+    GCU(g, cudaEventRecord(g->bevents[mine], bst));
+    GCU(g, cudaStreamWaitEvent(g->st, g->bevents[mine], 0));
+  }
+  GCU(g, cudaStreamSynchronize(g->st));
+  *it_io += maxit;
+  return EDA_OK;
+}
+
 // PCG iterations of the group from the current (x, r): replay of a graph of
 // two iterations (parities 0 and 1) with the active count polled through a
 // ring of pinned copies.
@@ -440,6 +535,7 @@ int group_pcg_loop_t(eda_group* g, bool sweep64, bool use_lmp, double tol, int m
   const int fixed = tol > 0.0 ? 0 : maxit;
   int rc = group_start<TS>(g, use_lmp, tol, maxit, fixed);
   if (rc) return rc;
+  if (maxit >= 1 && eda::env_int("EDA_PERSIST", 1)) return group_persist<TS>(g, sweep64, use_lmp, tol, maxit, fixed, it_io);
   const int key = (sweep64 ? 1 : 0) + (use_lmp ? 2 : 0) + (fixed ? 4 : 0);
   const bool use_graph = eda::env_int("EDA_GROUP_GRAPH", 1) != 0;
   // the graph bakes in tol and maxit as kernel arguments
@@ -639,6 +735,11 @@ EDA_API int eda_group_destroy(eda_group* g) {
   for (int i = 0; i < 4; ++i)
     if (g->ev[i]) cudaEventDestroy(g->ev[i]);
   if (g->join) cudaEventDestroy(g->join);
+  for (cudaEvent_t e : g->bevents) cudaEventDestroy(e);
+  for (cudaStream_t st2 : g->bstreams) {
+    cudaStreamSynchronize(st2);
+    cudaStreamDestroy(st2);
+  }
   if (g->st) cudaStreamDestroy(g->st);
   delete g;
   return EDA_OK;

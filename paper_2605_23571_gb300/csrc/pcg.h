@@ -156,10 +156,21 @@ struct PersistArgs {
   int maxit, fixed, use_lmp;
   PersistAcc* pacc;     // [M]
   T* W;                 // [2][M][kmax] projections by parity
+  // group mode (items != nullptr): the clusters take the launch's items
+  // (one member of one problem each, largest problems first) from a
+  // device-side queue; item i is sw.items[i], its PCG index (into sc, acc,
+  // active, pacc and W, with M the group's total) is items[i].flag, its
+  // problem's vector layout and LMP pprobs[items[i].prob]
+  const SweepItem* items;
+  int nitems;
+  const PcgProb* pprobs;
+  int* queue;           // next item to take (zeroed before the launch)
 };
 
 // Launches the persistent PCG over the M members (a cluster tiling, not
-// multi-launch, not warp-tiled).  Returns a cudaError_t.
+// multi-launch, not warp-tiled).  In group mode, plan describes the bucket
+// (cluster size, threads, run length, shared memory) and the grid holds as
+// many clusters as fit on the device at once.  Returns a cudaError_t.
 template <typename T>
 cudaError_t launch_pcg_persist(const PersistArgs<T>& a, const SweepPlan& plan, cudaStream_t s);
 

@@ -33,6 +33,9 @@
 // the adjoint its exact transpose, computed stage by stage in reverse.
 #include <cooperative_groups.h>
 
+#include <cstdio>
+#include <cstdlib>
+
 #include "eda_internal.h"
 #include "pcg.h"
 
@@ -1337,49 +1340,48 @@ __device__ __forceinline__ double cta_sum(double v, double* red) {
   return t;
 }
 
-// Persistent PCG, one cluster per member (pcg.h).  Every decision to leave
-// the loop is taken by every CTA of the cluster from the same values (read
-// after the same cluster barrier), so the cluster's barriers stay matched;
-// every member stops by its iteration budget at the latest.  Values other
-// CTAs write during the launch (the accumulators, the projections, p's halo
-// in the sweep) are read past L1 (__ldcg).
+// Persistent PCG (pcg.h): one member's whole PCG loop run by this cluster.
+// Every decision to leave the loop is taken by every CTA of the cluster from
+// the same values (read after the same cluster barrier), so the cluster's
+// barriers stay matched; every member stops by its iteration budget at the
+// latest.  Values other CTAs write during the launch (the accumulators, the
+// projections, p's halo in the sweep) are read past L1 (__ldcg).
+//   scol  the member's column for the sweep (index into sw.items in group
+//         mode); j its PCG index; n its state size; Ttile the tile of this
+//         plan; voff the offset of its vectors; S, cvec, k its LMP.
 template <typename T, int C, bool STG>
-__global__ void __launch_bounds__(kMaxThreads) pcg_persist_kernel(const PersistArgs<T> P) {
+__device__ __forceinline__ void persist_member(const PersistArgs<T>& P, SweepArgs<T>& a, int scol, int j, int n,
+                                               int Ttile, long long voff, const T* S, const double* cvec, int k,
+                                               int rank) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int CS = P.sw.CS;
-  const int col = (int)blockIdx.x / CS;
-  if (col >= P.M) return;             // uniform over the cluster
-  if (P.active[col] == 0) return;     // uniform: written before the launch
-  const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
-  const int n = P.n, kmax = P.kmax;
-  const int a0 = rank * P.sw.Ttile;
-  const int town = min(P.sw.Ttile, n - a0);
+  const int CS = P.sw.CS, kmax = P.kmax;
+  const int a0 = rank * Ttile;
+  const int town = min(Ttile, n - a0);
   const int tid = threadIdx.x, NT = blockDim.x, lane = tid & 31, wid = tid >> 5, nw = NT >> 5;
-  const long long vo = (long long)col * n + a0;
-  const int k = P.use_lmp ? P.k : 0;
+  const long long vo = voff + a0;
   // scratch between sweeps (the sweep re-initialises its shared memory)
   double* red = reinterpret_cast<double*>(smem_raw);
   T* cw = reinterpret_cast<T*>(red + 32);
   T* rt = cw + ((kmax + 3) & ~3);
-  PersistAcc* pa = P.pacc + col;
+  PersistAcc* pa = P.pacc + j;
+  T* Wj[2] = {P.W + (long long)j * kmax, P.W + ((long long)P.M + j) * kmax};
   auto csync = [&]() {
     __threadfence();
     if (CS > 1) cg::this_cluster().sync();
     else __syncthreads();
   };
-  double rz = __ldcg(&P.acc[col].rz[0]);
-  int it = P.sc[col].iters;
-  const double bn = P.sc[col].bnorm;
-  const double tolm = P.sc[col].tolm;
-  double rel = P.sc[col].relres;
+  double rz = __ldcg(&P.acc[j].rz[0]);
+  int it = P.sc[j].iters;
+  const double bn = P.sc[j].bnorm;
+  const double tolm = P.sc[j].tolm;
+  double rel = P.sc[j].relres;
   int status = EDA_MAXIT;
   int par = 0;
-  SweepArgs<T> a = P.sw;
   a.dot_stride = (int)(sizeof(PersistAcc) / sizeof(double));
   for (;;) {
     // q = (I + A) p with p.q into this iteration's slot
     a.dot_out = &P.pacc[0].pq[par];
-    sweep_body<T, C, STG, false>(a, col);
+    sweep_body<T, C, STG, false>(a, scol);
     csync();
     const double pq = __ldcg(&pa->pq[par]);
     if (!(pq > 0.0)) {  // breakdown (or NaN): uniform
@@ -1388,26 +1390,26 @@ __global__ void __launch_bounds__(kMaxThreads) pcg_persist_kernel(const PersistA
     }
     const double alpha = rz / pq;
     double rr = 0.0, xx = 0.0;
-    for (int j = tid; j < town; j += NT) {
-      const long long g = vo + j;
+    for (int i = tid; i < town; i += NT) {
+      const long long g = vo + i;
       const double xn = P.x[g] + alpha * P.p[g];
       const double rn = P.r[g] - alpha * P.q[g];
       P.x[g] = xn;
       P.r[g] = rn;
       rr += rn * rn;
       xx += xn * xn;
-      rt[j] = (T)rn;
+      rt[i] = (T)rn;
     }
     __syncthreads();
     // the LMP projections of the new r over this tile: warp w takes modes
     // w, w + nw, ...
     for (int c = wid; c < k; c += nw) {
-      const T* Sc = P.S + (long long)c * n + a0;
+      const T* Sc = S + (long long)c * n + a0;
       T s0 = T(0);
-      for (int j = lane; j < town; j += 32) s0 += Sc[j] * rt[j];
+      for (int i = lane; i < town; i += 32) s0 += Sc[i] * rt[i];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      if (lane == 0) atomicAdd(&P.W[((long long)par * P.M + col) * kmax + c], s0);
+      if (lane == 0) atomicAdd(&Wj[par][c], s0);
     }
     rr = cta_sum(rr, red);
     xx = cta_sum(xx, red);
@@ -1445,19 +1447,18 @@ __global__ void __launch_bounds__(kMaxThreads) pcg_persist_kernel(const PersistA
     }
     if (stop) break;
     // z = r + S (c o w), r.z
-    for (int c = tid; c < k; c += NT)
-      cw[c] = (T)(P.c[c] * (double)__ldcg(&P.W[((long long)par * P.M + col) * kmax + c]));
+    for (int c = tid; c < k; c += NT) cw[c] = (T)(cvec[c] * (double)__ldcg(&Wj[par][c]));
     __syncthreads();
     double rzp = 0.0;
-    for (int j = tid; j < town; j += NT) {
-      const long long g = vo + j;
+    for (int i = tid; i < town; i += NT) {
+      const long long g = vo + i;
       T s0 = T(0), s1 = T(0);
       int c = 0;
       for (; c + 2 <= k; c += 2) {
-        s0 += P.S[(long long)c * n + a0 + j] * cw[c];
-        s1 += P.S[(long long)(c + 1) * n + a0 + j] * cw[c + 1];
+        s0 += S[(long long)c * n + a0 + i] * cw[c];
+        s1 += S[(long long)(c + 1) * n + a0 + i] * cw[c + 1];
       }
-      if (c < k) s0 += P.S[(long long)c * n + a0 + j] * cw[c];
+      if (c < k) s0 += S[(long long)c * n + a0 + i] * cw[c];
       const double rv = P.r[g];
       const double zv = rv + (double)(s0 + s1);
       P.z[g] = zv;
@@ -1469,8 +1470,8 @@ __global__ void __launch_bounds__(kMaxThreads) pcg_persist_kernel(const PersistA
     const double rzn = __ldcg(&pa->rz[par]);
     const double beta = rzn / rz;
     rz = rzn;
-    for (int j = tid; j < town; j += NT) {
-      const long long g = vo + j;
+    for (int i = tid; i < town; i += NT) {
+      const long long g = vo + i;
       P.p[g] = P.z[g] + beta * P.p[g];
     }
     // the other parity's slots were read last iteration: clear them for the next
@@ -1481,26 +1482,73 @@ __global__ void __launch_bounds__(kMaxThreads) pcg_persist_kernel(const PersistA
         pa->xx[par ^ 1] = 0.0;
         pa->rz[par ^ 1] = 0.0;
       }
-      for (int c = tid; c < k; c += NT) P.W[((long long)(par ^ 1) * P.M + col) * kmax + c] = T(0);
+      for (int c = tid; c < k; c += NT) Wj[par ^ 1][c] = T(0);
     }
     csync();  // p complete (the next sweep reads its halo) and the slots cleared
     par ^= 1;
   }
   if (rank == 0 && tid == 0) {
-    P.sc[col].iters = it;
-    P.sc[col].status = status;
-    P.sc[col].relres = rel;
-    P.active[col] = 0;
+    P.sc[j].iters = it;
+    P.sc[j].status = status;
+    P.sc[j].relres = rel;
+    P.active[j] = 0;
     atomicSub(P.nactive, 1);
   }
 }
 
-template <typename T, int C, bool STG>
+// One member per cluster (a handle's solve), or, in group mode (GROUP), the
+// members of the launch's items taken in turn from the device-side queue.
+template <typename T, int C, bool STG, bool GROUP>
+__global__ void __launch_bounds__(kMaxThreads) pcg_persist_kernel(const PersistArgs<T> P) {
+  __shared__ int next_item;
+  const int CS = P.sw.CS;
+  const int rank = CS > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  SweepArgs<T> a = P.sw;
+  if constexpr (!GROUP) {
+    const int col = (int)blockIdx.x / CS;
+    if (col >= P.M) return;          // uniform over the cluster
+    if (P.active[col] == 0) return;  // uniform: written before the launch
+    persist_member<T, C, STG>(P, a, col, col, P.n, P.sw.Ttile, (long long)col * P.n, P.S, P.c,
+                              P.use_lmp ? P.k : 0, rank);
+    return;
+  } else {
+  for (;;) {
+    // rank 0 takes the next item for the cluster; the others read it from
+    // rank 0's shared memory between two cluster barriers
+    if (rank == 0 && threadIdx.x == 0) next_item = atomicAdd(P.queue, 1);
+    int idx;
+    if (CS > 1) {
+      cg::this_cluster().sync();
+      idx = *cg::this_cluster().map_shared_rank(&next_item, 0);
+      cg::this_cluster().sync();
+    } else {
+      __syncthreads();
+      idx = next_item;
+      __syncthreads();
+    }
+    if (idx >= P.nitems) return;  // uniform: every CTA read the same index
+    const SweepItem itm = P.items[idx];
+    const int j = itm.flag;
+    if (j < 0 || P.active[j] == 0) continue;  // uniform
+    const PcgProb pp = P.pprobs[itm.prob];
+    const SweepProb<T> sp = P.sw.probs[itm.prob];
+    persist_member<T, C, STG>(P, a, idx, j, sp.n, sp.Ttile, itm.voff, static_cast<const T*>(pp.S), pp.c,
+                              P.use_lmp ? pp.k : 0, rank);
+  }
+  }
+}
+
+template <typename T, int C, bool STG, bool GROUP = false>
 cudaError_t launch_persist_impl(const PersistArgs<T>& a, const SweepPlan& p, cudaStream_t s) {
-  auto kern = pcg_persist_kernel<T, C, STG>;
+  auto kern = pcg_persist_kernel<T, C, STG, GROUP>;
   static bool attrs_set = false;
   if (!attrs_set) {
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    // the group kernel's static shared memory (the queue slot) counts against the 227 KB
+    cudaFuncAttributes fa{};
+    cudaError_t err = cudaFuncGetAttributes(&fa, kern);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               227 * 1024 - (int)fa.sharedSizeBytes);
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (err != cudaSuccess) return err;
@@ -1519,6 +1567,31 @@ cudaError_t launch_persist_impl(const PersistArgs<T>& a, const SweepPlan& p, cud
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+  }
+  if (a.items != nullptr) {
+    // group mode: as many clusters as fit at once (they loop over the queue;
+    // clusters beyond what fits wait and then find the queue empty)
+    int dev = 0, sms = 152, per_sm = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, p.A, p.smem) != cudaSuccess || per_sm < 1) {
+      (void)cudaGetLastError();
+      per_sm = 1;
+    }
+    int clusters = 0;
+    if (p.CS > 1) {
+      if (cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        clusters = 0;
+      }
+    }
+    if (clusters < 1) clusters = per_sm * sms / (p.CS > 0 ? p.CS : 1);
+    if (clusters < 1) clusters = 1;
+    if (clusters > a.nitems) clusters = a.nitems;
+    cfg.gridDim = dim3((unsigned)(clusters * p.CS), 1, 1);
+    const char* vb = std::getenv("EDA_VERBOSE");
+    if (vb != nullptr && std::atoi(vb) != 0)
+      std::fprintf(stderr, "persistent group launch: CS=%d A=%d smem=%zu items=%d clusters=%d\n", p.CS, p.A,
+                   p.smem, a.nitems, clusters);
   }
   count_launch();
   return cudaLaunchKernelEx(&cfg, kern, a);
@@ -2395,7 +2468,7 @@ cudaError_t launch_sweep(const SweepArgs<T>& a0, const SweepPlan& p, cudaStream_
 
 template <typename T>
 cudaError_t launch_pcg_persist(const PersistArgs<T>& a0, const SweepPlan& p, cudaStream_t s) {
-  if (a0.M <= 0) return cudaSuccess;
+  if (a0.M <= 0 || (a0.items != nullptr && a0.nitems <= 0)) return cudaSuccess;
   if (p.ml || p.warp || p.ckpt) return cudaErrorInvalidValue;
   PersistArgs<T> a = a0;
   a.sw.CS = p.CS;
@@ -2406,13 +2479,22 @@ cudaError_t launch_pcg_persist(const PersistArgs<T>& a0, const SweepPlan& p, cud
   a.sw.ml = 0;
   a.sw.ckpt = 0;
   a.sw.mode = MODE_HVP;
-  a.sw.ncol = a.M;
+  a.sw.ncol = a.items != nullptr ? a.nitems : a.M;
   a.sw.col_active = nullptr;
   a.sw.include_identity = 1;
   // the between-sweep scratch (reduction slots, c o w, the r tile) fits the
-  // sweep's own shared memory
+  // sweep's own shared memory (group mode: the caller checks its largest tile)
   const size_t scratch = 32 * sizeof(double) + (size_t)(((a.kmax + 3) & ~3) + p.Ttile) * sizeof(T);
-  if (scratch > p.smem) return cudaErrorInvalidValue;
+  if (a.items == nullptr && scratch > p.smem) return cudaErrorInvalidValue;
+  if (a.items != nullptr) {  // group buckets: FP64 runs of 4, FP32 runs of 8, no stage store
+    if (a.sw.stages != nullptr) return cudaErrorInvalidValue;
+    if constexpr (sizeof(T) == 8) {
+      if (p.C == 4) return launch_persist_impl<T, 4, false, true>(a, p, s);
+    } else {
+      if (p.C == 8) return launch_persist_impl<T, 8, false, true>(a, p, s);
+    }
+    return cudaErrorInvalidValue;
+  }
   if constexpr (sizeof(T) == 8) {
     const bool stg = a.sw.stages != nullptr;
     if (p.C == 4) return stg ? launch_persist_impl<T, 4, true>(a, p, s) : launch_persist_impl<T, 4, false>(a, p, s);
