@@ -183,14 +183,17 @@ PERSIST_PROFILE = {"double": os.path.join(ROOT, "profiles", "pcg_persist_kernel_
                    "float": os.path.join(ROOT, "profiles", "pcg_persist_kernel_f32_l96_n4096_w64_m51.md")}
 
 
-def persist_kernel_name(plan, dtype="double"):
+def persist_kernel_name(plan, dtype="double", tails=()):
     """The persistent PCG kernel a cluster tiling launches (EDA_PERSIST unset
-    or 1), or None for tilings the per-iteration launches serve."""
+    or 1), or None for tilings the per-iteration launches serve; tails: the
+    (level, plan) tilings of the convergence tail (eda_tail_plans)."""
     if plan["kind"] != "cluster" or os.environ.get("EDA_PERSIST", "1") == "0":
         return None
+    tail = "".join("; at <= %d active members %d CTAs x %d threads, refresh every %d"
+                   % (lv, t["ctas_per_vector"], t["threads"], t["K"]) for lv, t in tails)
     return ("pcg_persist_kernel<%s,%d> (one cluster of %d CTAs x %d threads per member, halo refresh every %d "
-            "steps: the member's sweeps, CG updates, LMP and stopping test for the whole solve)"
-            % (dtype, plan["C"], plan["ctas_per_vector"], plan["threads"], plan["K"]))
+            "steps%s: the member's sweeps, CG updates, LMP and stopping test, one launch per phase of the solve)"
+            % (dtype, plan["C"], plan["ctas_per_vector"], plan["threads"], plan["K"], tail))
 
 
 def sweep_kernel_name(plan, dtype="float"):
@@ -546,8 +549,10 @@ def forms_tiny(P, dev, problems=100):
 
 def forms_uneven(P, dev, count=256, maxit=3000):
     """Uneven batch: 256 independent problems in one group (mixed precision,
-    graph-captured PCG, autotuned tiling), each member with a budget of
-    maxit iterations."""
+    autotuned tiling, the PCG as one persistent work-queue launch per tile
+    shape), each member with a budget of maxit iterations.  Reports, per
+    problem with members that miss the budget, its size, window and the
+    count that missed."""
     import torch
     specs = S.specs_uneven(count, seed=0)
     hs, xbs, ys = [], [], []
@@ -579,10 +584,24 @@ def forms_uneven(P, dev, count=256, maxit=3000):
     for h in hs:
         h.close()
     conv = int((st == 0).sum())
+    # members of problem i are rows off[i] .. off[i+1] of the group's outputs
+    off = np.cumsum([0] + [s_.n_members for s_ in specs])
+    missed = []
+    for i, s_ in enumerate(specs):
+        bad = int((st[off[i]:off[i + 1]] != 0).sum())
+        if bad:
+            missed.append({"problem": i, "n": s_.n, "window": s_.nsteps, "members": s_.n_members,
+                           "missed_budget": bad, "relres_median_missed":
+                           float(np.median(rr[off[i]:off[i + 1]][st[off[i]:off[i + 1]] != 0]))})
     return {"workload": "uneven_256_seed0", "problems": count, "member_solves": T, "converged": conv,
             "budget_per_member": maxit, "seconds": t, "converged_solves_per_s": conv / t,
             "iters_median": float(np.median(it)), "iters_p90": float(np.percentile(it, 90)),
-            "true_relres_max_converged": float(rr[st == 0].max()) if conv else None}
+            "true_relres_max_converged": float(rr[st == 0].max()) if conv else None,
+            "problems_missing_budget": missed,
+            "window_of_problems_missing_budget": {"min": min((m["window"] for m in missed), default=None),
+                                                  "max": max((m["window"] for m in missed), default=None)},
+            "window_all_problems": {"min": int(min(s_.nsteps for s_ in specs)),
+                                    "max": int(max(s_.nsteps for s_ in specs))}}
 
 
 def forms_sketch_study(P, dev, seeds=20, iters=(1, 2, 3, 5, 10, 20, 30)):
@@ -870,6 +889,8 @@ def run_ours(args):
     hm.eda_autotune(0)
     plan64 = h64.eda_sweep_plan(fp64=True)
     plan32 = hm.eda_sweep_plan(fp64=False)
+    tails64 = h64.eda_tail_plans(fp64=True)
+    tails32 = hm.eda_tail_plans(fp64=False)
 
     # ---- timed region (headline: the plain FP64 GPU path at the paper's precision)
     for _ in range(args.warmup):
@@ -1029,7 +1050,7 @@ def run_ours(args):
                          "ms_per_batched_launch_fp64": ms64, "ms_per_batched_launch_fp32": ms32},
             "roofline": {"bound": "alu", "achieved": ach64, "peak": peak64, "unit": "TFLOP/s",
                          "frac": ach64 / peak64, "traffic": traffic64,
-                         "kernel": (persist_kernel_name(plan64, "double") or sweep_kernel_name(plan64, "double")
+                         "kernel": (persist_kernel_name(plan64, "double", tails64) or sweep_kernel_name(plan64, "double")
                                     + ": the FP64 Hessian-product sweeps of the timed steps"),
                          "achieved_counts": "algorithmic flops of the sweeps only (79 per element-step) over the "
                                             "whole kernel time (the CG vector work and LMP inside it included)",
@@ -1041,7 +1062,7 @@ def run_ours(args):
                                       "flops x 2070 MHz (no FP64 peak is measured)"},
             "roofline_fp32_sweep": {"bound": "hbm", "achieved": ach32, "peak": hbm_peak, "unit": "GB/s",
                                     "frac": ach32 / hbm_peak, "traffic": traffic32,
-                                    "kernel": (persist_kernel_name(plan32, "float") or sweep_kernel_name(plan32)
+                                    "kernel": (persist_kernel_name(plan32, "float", tails32) or sweep_kernel_name(plan32)
                                                + ": the FP32 Hessian-product sweeps of the mixed form's timed steps"),
                                     "launches_timed": sw32_calls, "columns": sw32_cols,
                                     "ms_per_launch": sw32_ms / max(1, sw32_calls),

@@ -352,6 +352,34 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out);
 EDA_API int eda_sweep_plan(eda_handle* h, int fp64, int* info);
 
 /*
+ * Tilings of the persistent PCG's convergence tail (the solve of Section 2.3
+ * run as one launch per phase; not in the paper).  While many members are
+ * active the solve runs on the tiling above; a tail tiling of level R serves
+ * once at most R members remain active and spreads each over more CTAs: the
+ * running launch ends at the iteration boundary after the active count falls
+ * to R (every member's PCG state stays on the device) and the solve goes on
+ * in a launch on the tail tiling, with the same iterates up to the rounding
+ * order of the reductions.  eda_autotune chooses them (active counts L/2,
+ * L/4, ..., 1; a level is kept where its tiling's Hessian-product sweep beats
+ * the main tiling's by more than 7 %) and replaces any set before.
+ *
+ * eda_tail_plans: *count receives the number of tail tilings of one
+ * precision (fp64 != 0: FP64 sweeps, else FP32); levels[i] (may be NULL) and
+ * info[8i .. 8i+7] (may be NULL; as in eda_sweep_plan) describe the first
+ * min(cap, count), in decreasing level.  Host arrays, caller-owned.
+ *
+ * eda_set_tail_plan: level in [1, L+1] installs (or replaces, at an equal
+ * level) the thread-block cluster tiling of cs CTAs per member, halo refresh
+ * period K and C values per thread (0: the main tiling's); level 0 removes
+ * every tail tiling of that precision.  EDA_ERR_INVALID when the main tiling
+ * is not a cluster tiling (multi-launch, warp-tiled or checkpointed), no
+ * tiling of that shape fits, or the persistent PCG cannot run on it.
+ * Synchronises the stream.
+ */
+EDA_API int eda_tail_plans(eda_handle* h, int fp64, int cap, int* count, int* levels, int* info);
+EDA_API int eda_set_tail_plan(eda_handle* h, int fp64, int level, int cs, int K, int C);
+
+/*
  * Host-only planning query (no handle, no device work): the tiling the
  * library would use for a Hessian-product sweep of state size n, FP64
  * (fp64 != 0) or FP32, banded circulant half-width w and halo refresh period

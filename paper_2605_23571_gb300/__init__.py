@@ -37,7 +37,7 @@ EXPORTS = ["eda_version", "eda_last_error", "eda_create", "eda_destroy", "eda_tw
            "eda_ws_get_params", "eda_ws_set_scales", "eda_ws_get_scales", "eda_ws_loss_grad", "eda_ws_train",
            "eda_ws_infer", "eda_hvp_noalloc", "eda_hvp_noalloc_capacity", "eda_lmp_info",
            "eda_trace", "eda_trace_read", "eda_ws_init", "eda_sweep_plan", "eda_bhalf_apply",
-           "eda_plan_tiling", "eda_solve", "eda_lmp_apply"]
+           "eda_plan_tiling", "eda_solve", "eda_lmp_apply", "eda_tail_plans", "eda_set_tail_plan"]
 
 
 class EdaError(RuntimeError):
@@ -121,6 +121,10 @@ def lib() -> ctypes.CDLL:
     L.eda_hvp.argtypes = [vp, vp, i, vp, vp, i]
     L.eda_lmp_apply.restype = i
     L.eda_lmp_apply.argtypes = [vp, i, i, i, vp, vp]
+    L.eda_tail_plans.restype = i
+    L.eda_tail_plans.argtypes = [vp, i, i, ctypes.POINTER(i), vp, vp]
+    L.eda_set_tail_plan.restype = i
+    L.eda_set_tail_plan.argtypes = [vp, i, i, i, i, i]
     L.eda_solve.restype = i
     L.eda_solve.argtypes = [vp, ctypes.POINTER(EdaSolveOpts), vp, vp, vp, vp, vp]
     L.eda_kernel_launches.restype = ctypes.c_longlong
@@ -371,6 +375,27 @@ class Handle:
         out = dict(zip(PLAN_KEYS, list(info)))
         out["kind"] = PLAN_KINDS[out["kind"]]
         return out
+
+    def eda_tail_plans(self, fp64=True):
+        """The convergence tail's tilings of the persistent PCG: a list of
+        (level, plan dict), levels decreasing."""
+        cnt = ctypes.c_int(0)
+        self._check(self._L.eda_tail_plans(self._h, int(bool(fp64)), 0, ctypes.byref(cnt), None, None))
+        k = cnt.value
+        lev = (ctypes.c_int * max(1, k))()
+        info = (ctypes.c_int * max(8, 8 * k))()
+        self._check(self._L.eda_tail_plans(self._h, int(bool(fp64)), k, ctypes.byref(cnt), lev, info))
+        out = []
+        for i in range(k):
+            d = dict(zip(PLAN_KEYS, list(info[8 * i:8 * i + 8])))
+            d["kind"] = PLAN_KINDS[d["kind"]]
+            out.append((int(lev[i]), d))
+        return out
+
+    def eda_set_tail_plan(self, level, cs=0, K=0, C=0, fp64=True):
+        """Installs the cluster tiling of cs CTAs (refresh K) for at most
+        `level` active members; level 0 removes every tail tiling."""
+        self._check(self._L.eda_set_tail_plan(self._h, int(bool(fp64)), int(level), int(cs), int(K), int(C)))
 
     def eda_solve_batch(self, tol, maxit, x0, use_lmp, dz_out, iters_out=None, relres_out=None,
                         status_out=None):

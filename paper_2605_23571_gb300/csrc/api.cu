@@ -4,6 +4,7 @@
 
 #include <atomic>
 #include <cmath>
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -678,6 +679,118 @@ EDA_API int eda_trace_read(eda_handle* h, int fp64, long long* sweeps, long long
   return EDA_OK;
 }
 
+extern "C++" {
+// Drops the convergence-tail tilings of one precision (0 FP64, 1 FP32).
+void free_tails(eda_handle* h, int which) {
+  for (auto& t : h->tail[which])
+    if (t.tab) cudaFree(t.tab);
+  h->tail[which].clear();
+}
+
+// How many clusters of the persistent PCG on tiling pl fit on the device at
+// once (0: it cannot run there).
+template <typename TS>
+int persist_fits(eda_handle* h, const SweepPlan& pl) {
+  eda::PersistArgs<TS> pa{};
+  pa.sw = base_args<TS>(h);
+  pa.M = h->M;
+  pa.kmax = std::max(h->k, 1);
+  int q = 0;
+  if (eda::launch_pcg_persist<TS>(pa, pl, h->st, &q) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  return q;
+}
+
+// Tilings for the persistent PCG's convergence tail: at active counts
+// R = M/2, M/4, ..., 1 (rounded up), times the Hessian-product sweep of R
+// active columns on the chosen tiling and on clusters of more CTAs (up to
+// 16) with neighbouring refresh periods, and keeps a level's fastest tiling
+// where it beats the chosen one by more than 7 %.  The chosen tiling is
+// installed again at the end.
+int tune_tails(eda_handle* h, bool fp64, cudaEvent_t e0, cudaEvent_t e1) {
+  const int which = fp64 ? 0 : 1;
+  free_tails(h, which);
+  const SweepPlan main = fp64 ? h->plan64 : h->plan32;
+  const bool wp = fp64 ? h->wplan64.warp : h->wplan32.warp;
+  const int M = h->M;
+  if (main.ml || main.warp || main.ckpt || wp || M < 2 || !env_int("EDA_PERSIST", 1) || !env_int("EDA_TAIL", 1))
+    return EDA_OK;
+  int* mask = nullptr;
+  CU(h, cudaMalloc((void**)&mask, (size_t)M * sizeof(int)));
+  std::vector<int> hm((size_t)M);
+  const int reps = 3;
+  int rc = EDA_OK;
+  auto time_plan = [&](const SweepPlan& pl, float* ms) -> int {
+    int r = set_plan(h, fp64, pl);
+    for (int rep = -1; rep < reps && r == EDA_OK; ++rep) {
+      if (rep == 0) CU(h, cudaEventRecord(e0, h->st));
+      r = hvp_dev(h, h->cols, M, h->pv, h->q, 1, fp64, mask);
+    }
+    if (r) return r;
+    CU(h, cudaEventRecord(e1, h->st));
+    CU(h, cudaEventSynchronize(e1));
+    CU(h, cudaEventElapsedTime(ms, e0, e1));
+    *ms /= reps;
+    return EDA_OK;
+  };
+  for (int R = (M + 1) / 2; rc == EDA_OK; R = (R + 1) / 2) {
+    for (int i = 0; i < M; ++i) hm[(size_t)i] = i < R ? 1 : 0;
+    CU(h, cudaMemcpy(mask, hm.data(), (size_t)M * sizeof(int), cudaMemcpyHostToDevice));
+    float base_ms = 0.f;
+    rc = time_plan(main, &base_ms);
+    if (rc) break;
+    SweepPlan best = main;
+    float best_ms = base_ms;
+    for (int CS = main.CS + 1; CS <= 16 && rc == EDA_OK; ++CS)
+      for (int K : {main.K / 2, main.K, main.K * 2}) {
+        SweepPlan pl;
+        if (K < 2 || !eda::plan_sweep_exact(h->n, fp64 ? 8 : 4, h->w, CS, K, &pl, main.C)) continue;
+        if (pl.HL > h->n) continue;
+        if ((fp64 ? persist_fits<double>(h, pl) : persist_fits<float>(h, pl)) < 1) continue;
+        float ms = 0.f;
+        rc = time_plan(pl, &ms);
+        if (rc) break;
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = pl;
+        }
+      }
+    if (rc) break;
+    if (best_ms < 0.93f * base_ms) {
+      eda_handle::TailPlan t;
+      t.level = R;
+      t.plan = best;
+      std::vector<int> tab((size_t)best.CS * h->nos * 8);
+      bool ok = false;
+      eda::obs_table(best, h->n, h->nos, h->h_obs_ptr.data(), h->h_obs_idx.data(), tab.data(), &ok);
+      if (ok && !tab.empty()) {
+        cudaError_t e = cudaMalloc((void**)&t.tab, tab.size() * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemcpy(t.tab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+          if (t.tab) cudaFree(t.tab);
+          cudaFree(mask);
+          return fail(h, EDA_ERR_CUDA, cudaGetErrorString(e));
+        }
+      }
+      h->tail[which].push_back(t);
+      if (env_int("EDA_VERBOSE", 0))
+        std::fprintf(stderr, "eda_autotune: %s tail at <= %d active: CS=%d K=%d A=%d %.4f ms (chosen tiling %.4f)\n",
+                     fp64 ? "FP64" : "FP32", R, best.CS, best.K, best.A, best_ms, base_ms);
+    }
+    if (R == 1) break;
+  }
+  cudaFree(mask);
+  int r2 = set_plan(h, fp64, main);
+  if (rc) {
+    free_tails(h, which);
+    return rc;
+  }
+  return r2;
+}
+}  // extern "C++"
+
 EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
   if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
   if (!h->have_traj) return fail(h, EDA_ERR_STATE, "eda_autotune before eda_set_trajectory");
@@ -758,6 +871,8 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
       std::fprintf(stderr, "eda_autotune: %s sweep %s CS=%d K=%d A=%d E=%d C=%d %.4f ms\n", fp64 ? "FP64" : "FP32",
                    best.warp ? "warp-tiled" : (best.ml ? "multi-launch" : "cluster"), best.CS, best.K, best.A, best.E,
                    best.C, best_ms);
+    rc = tune_tails(h, fp64, e0, e1);
+    if (rc) return rc;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1040,6 +1155,9 @@ EDA_API int eda_destroy(eda_handle* h) {
   if (h->tab32) cudaFree(h->tab32);
   if (h->wtab64) cudaFree(h->wtab64);
   if (h->wtab32) cudaFree(h->wtab32);
+  for (auto& v : h->tail)
+    for (auto& t : v)
+      if (t.tab) cudaFree(t.tab);
   for (cudaEvent_t e : h->trace_ev)
     if (e) cudaEventDestroy(e);
   if (h->hflag) cudaFreeHost(h->hflag);
@@ -1424,6 +1542,77 @@ EDA_API int eda_sweep_plan(eda_handle* h, int fp64, int* info) {
   return EDA_OK;
 }
 
+EDA_API int eda_tail_plans(eda_handle* h, int fp64, int cap, int* count, int* levels, int* info) {
+  if (!h || !count || cap < 0) return fail(h, EDA_ERR_INVALID, "eda_tail_plans: invalid argument");
+  if (!fp64 && h->precision != EDA_MIXED) return fail(h, EDA_ERR_INVALID, "an FP64 handle has no FP32 sweep");
+  const std::vector<eda_handle::TailPlan>& t = h->tail[fp64 ? 0 : 1];
+  *count = (int)t.size();
+  for (int i = 0; i < (int)t.size() && i < cap; ++i) {
+    if (levels) levels[i] = t[(size_t)i].level;
+    if (info) {
+      const eda::SweepPlan& p = t[(size_t)i].plan;
+      int* o = info + 8 * (size_t)i;
+      o[0] = 0;
+      o[1] = p.CS;
+      o[2] = p.A;
+      o[3] = p.C;
+      o[4] = p.K;
+      o[5] = p.HL;
+      o[6] = p.Ttile;
+      o[7] = (int)p.smem;
+    }
+  }
+  return EDA_OK;
+}
+
+EDA_API int eda_set_tail_plan(eda_handle* h, int fp64, int level, int cs, int K, int C) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (!fp64 && h->precision != EDA_MIXED) return fail(h, EDA_ERR_INVALID, "an FP64 handle has no FP32 sweep");
+  const int which = fp64 ? 0 : 1;
+  if (level < 0 || level > h->M) return fail(h, EDA_ERR_INVALID, "eda_set_tail_plan: level outside [0, L+1]");
+  if (level == 0) {
+    CU(h, cudaStreamSynchronize(h->st));
+    free_tails(h, which);
+    return EDA_OK;
+  }
+  const eda::SweepPlan& main = fp64 ? h->plan64 : h->plan32;
+  const bool wp = fp64 ? h->wplan64.warp : h->wplan32.warp;
+  if (main.ml || main.warp || main.ckpt || wp)
+    return fail(h, EDA_ERR_INVALID, "eda_set_tail_plan: the chosen tiling is not a thread-block cluster tiling");
+  eda::SweepPlan pl;
+  if (!eda::plan_sweep_exact(h->n, fp64 ? 8 : 4, h->w, cs, K, &pl, C == 0 ? main.C : C) || (pl.HL > h->n && cs > 1))
+    return fail(h, EDA_ERR_INVALID, "eda_set_tail_plan: no cluster tiling of that shape fits");
+  if ((fp64 ? persist_fits<double>(h, pl) : persist_fits<float>(h, pl)) < 1)
+    return fail(h, EDA_ERR_INVALID, "eda_set_tail_plan: the persistent PCG cannot run on that tiling");
+  eda_handle::TailPlan t;
+  t.level = level;
+  t.plan = pl;
+  std::vector<int> tab((size_t)pl.CS * h->nos * 8);
+  bool ok = false;
+  eda::obs_table(pl, h->n, h->nos, h->h_obs_ptr.data(), h->h_obs_idx.data(), tab.data(), &ok);
+  if (ok && !tab.empty()) {
+    CU(h, cudaMalloc((void**)&t.tab, tab.size() * sizeof(int)));
+    cudaError_t e = cudaMemcpy(t.tab, tab.data(), tab.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(t.tab);
+      return fail(h, EDA_ERR_CUDA, cudaGetErrorString(e));
+    }
+  }
+  CU(h, cudaStreamSynchronize(h->st));
+  std::vector<eda_handle::TailPlan>& v = h->tail[which];
+  for (auto it = v.begin(); it != v.end(); ++it)
+    if (it->level == level) {
+      if (it->tab) cudaFree(it->tab);
+      v.erase(it);
+      break;
+    }
+  v.push_back(t);
+  std::sort(v.begin(), v.end(), [](const eda_handle::TailPlan& a, const eda_handle::TailPlan& b) {
+    return a.level > b.level;
+  });
+  return EDA_OK;
+}
+
 EDA_API int eda_lmp_info(eda_handle* h, int* path, int* rank, double* shift) {
   if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
   if (!h->have_lmp) return fail(h, EDA_ERR_STATE, "eda_lmp_info before eda_build_lmp or eda_set_lmp");
@@ -1619,12 +1808,10 @@ int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int*
       pa.sw.V = h->pv;
       pa.sw.OUT = h->q;
       pa.sw.stash = h->stash;
-      pa.sw.obs_tab = h->tab64_ok ? h->tab64 : nullptr;
     } else {
       pa.sw.V64 = h->pv;
       pa.sw.OUT64 = h->q;
       pa.sw.stash = h->stash32;
-      pa.sw.obs_tab = h->tab32_ok ? h->tab32 : nullptr;
     }
     pa.sw.v_stride = h->n;
     pa.sw.out_stride = h->n;
@@ -1651,21 +1838,63 @@ int pcg_loop_t(eda_handle* h, double tol, int maxit, int it0, bool use_lmp, int*
     pa.use_lmp = lmp;
     pa.pacc = h->pacc;
     pa.W = reinterpret_cast<TS*>(h->Wp);
+    // phases: the main tiling while many members are active, then the
+    // convergence tail's tilings (eda_autotune), each launch leaving early
+    // once the active count falls to the next level whose tiling differs
+    const std::vector<eda_handle::TailPlan>& tails = h->tail[sweep64 ? 0 : 1];
+    if (!tails.empty() && !h->brk) CU(h, dalloc(h, &h->brk, 1));
     const bool traced = h->trace_on;
-    if (traced) {
-      // every persistent launch is traced: its duration, and the columns its
-      // sweeps computed (the member iterations it ran)
-      rc = trace_begin(h, sweep64 ? 0 : 1, nullptr, 0);
-      if (rc) return rc;
-      eda::count_launch();
-      iters_delta_kernel<<<1, 256, 0, h->st>>>(h->trace_cols + (sweep64 ? 0 : 1), h->sc, M, -1);
-    }
-    CU(h, eda::launch_pcg_persist<TS>(pa, gp, h->st));
-    if (traced) {
-      rc = trace_end(h);
-      if (rc) return rc;
-      eda::count_launch();
-      iters_delta_kernel<<<1, 256, 0, h->st>>>(h->trace_cols + (sweep64 ? 0 : 1), h->sc, M, 1);
+    for (int phase = 0;; ++phase) {
+      int nact = M;
+      if (!tails.empty()) {
+        int rc = read_flag(h, h->nactive, &nact);
+        if (rc) return rc;
+        if (nact <= 0) break;
+      } else if (phase > 0) {
+        break;
+      }
+      // the tiling for nact active members: the last level at or above it
+      int li = -1;
+      for (int i = 0; i < (int)tails.size(); ++i)
+        if (tails[i].level >= nact) li = i;
+      const SweepPlan& pl = li < 0 ? gp : tails[li].plan;
+      const int* tab = li < 0 ? (sweep64 ? (h->tab64_ok ? h->tab64 : nullptr) : (h->tab32_ok ? h->tab32 : nullptr))
+                              : tails[li].tab;
+      int below = -1;  // leave when at most `below` members remain (-1: run to the end)
+      for (int i = li + 1; i < (int)tails.size(); ++i) {
+        const SweepPlan& q = tails[i].plan;
+        if (q.CS != pl.CS || q.K != pl.K || q.A != pl.A || q.C != pl.C) {
+          below = tails[i].level;
+          break;
+        }
+      }
+      if (phase > 0) {
+        CU(h, cudaMemsetAsync(h->pacc, 0, (size_t)M * sizeof(eda::PersistAcc), h->st));
+        CU(h, cudaMemsetAsync(h->Wp, 0, (size_t)2 * M * kmax * sizeof(TS), h->st));
+      }
+      if (h->brk) CU(h, cudaMemsetAsync(h->brk, 0, sizeof(int), h->st));
+      pa.sw.obs_tab = tab;
+      pa.exit_below = below;
+      pa.brk = below >= 0 ? h->brk : nullptr;
+      if (traced) {
+        // every persistent launch is traced: its duration, and the columns its
+        // sweeps computed (the member iterations it ran)
+        rc = trace_begin(h, sweep64 ? 0 : 1, nullptr, 0);
+        if (rc) return rc;
+        eda::count_launch();
+        iters_delta_kernel<<<1, 256, 0, h->st>>>(h->trace_cols + (sweep64 ? 0 : 1), h->sc, M, -1);
+      }
+      CU(h, eda::launch_pcg_persist<TS>(pa, pl, h->st));
+      if (traced) {
+        rc = trace_end(h);
+        if (rc) return rc;
+        eda::count_launch();
+        iters_delta_kernel<<<1, 256, 0, h->st>>>(h->trace_cols + (sweep64 ? 0 : 1), h->sc, M, 1);
+      }
+      if (env_int("EDA_VERBOSE", 0) > 1)
+        std::fprintf(stderr, "persistent PCG phase %d: %d active, CS=%d A=%d K=%d, leaves at %d\n", phase, nact,
+                     pl.CS, pl.A, pl.K, below);
+      if (below < 0) break;
     }
     CU(h, cudaStreamSynchronize(h->st));
     *it_done = it0 + maxit;

@@ -116,6 +116,17 @@ struct eda_handle {
   int* tab64 = nullptr;  // per-CTA observation ranges of plan64 / plan32
   int* tab32 = nullptr;
   bool tab64_ok = false, tab32_ok = false;
+  // tilings of the persistent PCG's convergence tail (eda_autotune): while at
+  // most `level` members are active, the solve relaunches on `plan`, which
+  // spreads each remaining member over more CTAs; levels decrease along the
+  // vector ([0] FP64 sweeps, [1] FP32); empty: one launch on plan64/plan32
+  struct TailPlan {
+    int level = 0;
+    SweepPlan plan{};
+    int* tab = nullptr;  // its observation table (nullptr: none fits)
+  };
+  std::vector<TailPlan> tail[2];
+  int* brk = nullptr;  // persistent PCG early-exit flag
   std::vector<int> h_obs_ptr, h_obs_idx;
   std::vector<void*> allocs;
   // tracing of the Hessian-product sweeps ([0] FP64 sweeps, [1] FP32):

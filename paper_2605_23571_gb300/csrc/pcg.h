@@ -139,6 +139,7 @@ cudaError_t pcg2_col_dot(int n, int ncol, const double* v, const double* hv, con
 // iteration after it was read; zeroed before the launch).
 struct PersistAcc {
   double pq[2], rr[2], xx[2], rz[2];
+  double ex[2];  // the launch's exit flag as rank 0 read it (1: leave at this iteration's end)
 };
 
 template <typename T>
@@ -149,13 +150,22 @@ struct PersistArgs {
   const T* S;           // k x n column-major, the LMP arithmetic type
   const double* c;      // k coefficients
   PcgScalars* sc;
-  const PcgAcc* acc;    // r.z of the loop start (slot 0, from pcg2_precond with init)
+  PcgAcc* acc;          // r.z of the loop start (slot 0, from pcg2_precond with init,
+                        // or saved there by a launch that left early)
   int* active;
   int* nactive;
   double tol, etol;
   int maxit, fixed, use_lmp;
   PersistAcc* pacc;     // [M]
   T* W;                 // [2][M][kmax] projections by parity
+  // early exit (re-tiling of the convergence tail): when a member's stop
+  // leaves at most exit_below members active, the stopping cluster sets
+  // *brk, and every other cluster leaves at the end of its current
+  // iteration with its PCG state saved (x, r, z, p in place; r.z in
+  // acc[j].rz[0], the iteration count and residual in sc[j]; still active)
+  // for a launch with another tiling.  brk == nullptr: no early exit.
+  int exit_below;
+  int* brk;
   // group mode (items != nullptr): the clusters take the launch's items
   // (one member of one problem each, largest problems first) from a
   // device-side queue; item i is sw.items[i], its PCG index (into sc, acc,
@@ -170,8 +180,11 @@ struct PersistArgs {
 // Launches the persistent PCG over the M members (a cluster tiling, not
 // multi-launch, not warp-tiled).  In group mode, plan describes the bucket
 // (cluster size, threads, run length, shared memory) and the grid holds as
-// many clusters as fit on the device at once.  Returns a cudaError_t.
+// many clusters as fit on the device at once.  With query != nullptr nothing
+// is launched: *query receives how many of the launch's clusters fit on the
+// device at once (0: the plan cannot run).  Returns a cudaError_t.
 template <typename T>
-cudaError_t launch_pcg_persist(const PersistArgs<T>& a, const SweepPlan& plan, cudaStream_t s);
+cudaError_t launch_pcg_persist(const PersistArgs<T>& a, const SweepPlan& plan, cudaStream_t s,
+                               int* query = nullptr);
 
 }  // namespace eda

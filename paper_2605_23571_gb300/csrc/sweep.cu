@@ -1481,10 +1481,23 @@ __device__ __forceinline__ void persist_member(const PersistArgs<T>& P, SweepArg
         pa->rr[par ^ 1] = 0.0;
         pa->xx[par ^ 1] = 0.0;
         pa->rz[par ^ 1] = 0.0;
+        // the launch's exit flag, published for the whole cluster (ex[par]
+        // was last read two barriers ago)
+        if (P.brk != nullptr) pa->ex[par] = *reinterpret_cast<volatile int*>(P.brk) != 0 ? 1.0 : 0.0;
       }
       for (int c = tid; c < k; c += NT) Wj[par ^ 1][c] = T(0);
     }
     csync();  // p complete (the next sweep reads its halo) and the slots cleared
+    if (P.brk != nullptr && __ldcg(&pa->ex[par]) != 0.0) {  // uniform: read after the same barrier
+      // leave with the state of a completed iteration: the next launch
+      // starts with the sweep of this p and reads r.z from acc[j].rz[0]
+      if (rank == 0 && tid == 0) {
+        P.sc[j].iters = it;
+        P.sc[j].relres = rel;
+        P.acc[j].rz[0] = rz;
+      }
+      return;
+    }
     par ^= 1;
   }
   if (rank == 0 && tid == 0) {
@@ -1492,7 +1505,8 @@ __device__ __forceinline__ void persist_member(const PersistArgs<T>& P, SweepArg
     P.sc[j].status = status;
     P.sc[j].relres = rel;
     P.active[j] = 0;
-    atomicSub(P.nactive, 1);
+    const int left = atomicSub(P.nactive, 1) - 1;
+    if (P.brk != nullptr && left <= P.exit_below) atomicExch(P.brk, 1);
   }
 }
 
@@ -1539,7 +1553,7 @@ __global__ void __launch_bounds__(kMaxThreads) pcg_persist_kernel(const PersistA
 }
 
 template <typename T, int C, bool STG, bool GROUP = false>
-cudaError_t launch_persist_impl(const PersistArgs<T>& a, const SweepPlan& p, cudaStream_t s) {
+cudaError_t launch_persist_impl(const PersistArgs<T>& a, const SweepPlan& p, cudaStream_t s, int* query) {
   auto kern = pcg_persist_kernel<T, C, STG, GROUP>;
   static bool attrs_set = false;
   if (!attrs_set) {
@@ -1567,6 +1581,25 @@ cudaError_t launch_persist_impl(const PersistArgs<T>& a, const SweepPlan& p, cud
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+  }
+  if (query != nullptr) {
+    // how many of this launch's clusters fit on the device at once (0: none)
+    *query = 0;
+    if (p.CS > 1) {
+      if (cudaOccupancyMaxActiveClusters(query, kern, &cfg) != cudaSuccess) {
+        (void)cudaGetLastError();
+        *query = 0;
+      }
+    } else {
+      int dev = 0, sms = 0, per_sm = 0;
+      if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
+                                                    cudaSuccess &&
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, p.A, p.smem) == cudaSuccess)
+        *query = per_sm * sms;
+      else
+        (void)cudaGetLastError();
+    }
+    return cudaSuccess;
   }
   if (a.items != nullptr) {
     // group mode: as many clusters as fit at once (they loop over the queue;
@@ -2467,7 +2500,7 @@ cudaError_t launch_sweep(const SweepArgs<T>& a0, const SweepPlan& p, cudaStream_
 }
 
 template <typename T>
-cudaError_t launch_pcg_persist(const PersistArgs<T>& a0, const SweepPlan& p, cudaStream_t s) {
+cudaError_t launch_pcg_persist(const PersistArgs<T>& a0, const SweepPlan& p, cudaStream_t s, int* query) {
   if (a0.M <= 0 || (a0.items != nullptr && a0.nitems <= 0)) return cudaSuccess;
   if (p.ml || p.warp || p.ckpt) return cudaErrorInvalidValue;
   PersistArgs<T> a = a0;
@@ -2489,25 +2522,25 @@ cudaError_t launch_pcg_persist(const PersistArgs<T>& a0, const SweepPlan& p, cud
   if (a.items != nullptr) {  // group buckets: FP64 runs of 4, FP32 runs of 8, no stage store
     if (a.sw.stages != nullptr) return cudaErrorInvalidValue;
     if constexpr (sizeof(T) == 8) {
-      if (p.C == 4) return launch_persist_impl<T, 4, false, true>(a, p, s);
+      if (p.C == 4) return launch_persist_impl<T, 4, false, true>(a, p, s, query);
     } else {
-      if (p.C == 8) return launch_persist_impl<T, 8, false, true>(a, p, s);
+      if (p.C == 8) return launch_persist_impl<T, 8, false, true>(a, p, s, query);
     }
     return cudaErrorInvalidValue;
   }
   if constexpr (sizeof(T) == 8) {
     const bool stg = a.sw.stages != nullptr;
-    if (p.C == 4) return stg ? launch_persist_impl<T, 4, true>(a, p, s) : launch_persist_impl<T, 4, false>(a, p, s);
-    if (p.C == 2) return stg ? launch_persist_impl<T, 2, true>(a, p, s) : launch_persist_impl<T, 2, false>(a, p, s);
+    if (p.C == 4) return stg ? launch_persist_impl<T, 4, true>(a, p, s, query) : launch_persist_impl<T, 4, false>(a, p, s, query);
+    if (p.C == 2) return stg ? launch_persist_impl<T, 2, true>(a, p, s, query) : launch_persist_impl<T, 2, false>(a, p, s, query);
   } else {
-    if (p.C == 8) return launch_persist_impl<T, 8, false>(a, p, s);
-    if (p.C == 4) return launch_persist_impl<T, 4, false>(a, p, s);
+    if (p.C == 8) return launch_persist_impl<T, 8, false>(a, p, s, query);
+    if (p.C == 4) return launch_persist_impl<T, 4, false>(a, p, s, query);
   }
   return cudaErrorInvalidValue;
 }
 
-template cudaError_t launch_pcg_persist<double>(const PersistArgs<double>&, const SweepPlan&, cudaStream_t);
-template cudaError_t launch_pcg_persist<float>(const PersistArgs<float>&, const SweepPlan&, cudaStream_t);
+template cudaError_t launch_pcg_persist<double>(const PersistArgs<double>&, const SweepPlan&, cudaStream_t, int*);
+template cudaError_t launch_pcg_persist<float>(const PersistArgs<float>&, const SweepPlan&, cudaStream_t, int*);
 template cudaError_t launch_sweep<double>(const SweepArgs<double>&, const SweepPlan&, cudaStream_t, double*, double*);
 template cudaError_t launch_sweep<float>(const SweepArgs<float>&, const SweepPlan&, cudaStream_t, float*, float*);
 

@@ -1,0 +1,126 @@
+"""The persistent PCG's convergence tail on other tilings (eda_set_tail_plan,
+eda_tail_plans, eda_autotune): the solve leaves the running launch at an
+iteration boundary once few members remain and goes on with each member
+spread over more CTAs.  The iterates are those of PCG (Section 2.3) up to
+the rounding order of the reductions, so the solutions stopped by the
+certified bound ||r|| / (||x|| - ||r||) (every eigenvalue of I + A is at
+least 1) must agree with the oracle's within the two certified bounds, and
+the iteration counts with the single-tiling solve within rounding."""
+import numpy as np
+import pytest
+
+import eda_synth as S
+import oracle as O
+from helpers import problem, rowrel
+
+pytestmark = pytest.mark.gpu
+
+P = pytest.importorskip("paper_2605_23571_gb300")
+
+ETOL = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    P.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module")
+def case():
+    spec = S.spec_small(1500, 16, 12, every_var=2, every_step=4, length_scale=4.0, seed=41)
+    taps, xb, y = problem(spec)
+    ref = O.eda_pipeline(spec, xb, y, taps, tol=1e-12, maxit=5000)
+    # the oracle's own certified relative error, from its true residual
+    rn = np.linalg.norm(ref["b"] - O.hvp(spec, ref["traj"], ref["x"], taps), axis=1)
+    xn = np.linalg.norm(ref["x"], axis=1)
+    assert (xn > rn).all()
+    bound = rn / (xn - rn)
+    assert (bound < 1e-9).all()
+    return spec, taps, xb, y, ref["x"], bound
+
+
+def solve(h, spec, trace=False):
+    M, n = spec.n_members, spec.n
+    dz = np.zeros((M, n))
+    it = np.zeros(M, np.int32)
+    eb = np.zeros(M)
+    st = np.zeros(M, np.int32)
+    if trace:
+        h.eda_trace(True)
+    h.eda_solve(dz, tol=0.0, err_tol=ETOL, maxit=20000, iters_out=it, err_bound_out=eb, status_out=st)
+    launches = None
+    if trace:
+        launches = h.eda_trace_read(fp64=True)[0]
+        h.eda_trace(False)
+    assert (st == 0).all()
+    assert (eb <= ETOL).all()
+    return dz, it, eb, launches
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_tail_tilings_keep_the_solution_and_the_iterations(case, precision):
+    spec, taps, xb, y, x_or, b_or = case
+    prec = P.EDA_FP64 if precision == "fp64" else P.EDA_MIXED
+    fp64 = precision == "fp64"
+    with P.Handle.from_spec(spec, taps, precision=prec) as h:
+        h.eda_set_trajectory(xb, y)
+        h.eda_sketch()
+        h.eda_build_lmp()
+        assert h.eda_sweep_plan(fp64=fp64)["kind"] == "cluster"
+        h.eda_set_tail_plan(0, fp64=fp64)
+        assert h.eda_tail_plans(fp64=fp64) == []
+        dz1, it1, eb1, n1 = solve(h, spec, trace=fp64)
+        # two tail tilings: 3 CTAs per member at <= 6 active, 6 at <= 2
+        h.eda_set_tail_plan(2, cs=6, K=2, fp64=fp64)
+        h.eda_set_tail_plan(6, cs=3, K=2, fp64=fp64)
+        tails = h.eda_tail_plans(fp64=fp64)
+        assert [lv for lv, _ in tails] == [6, 2]
+        assert [pl["ctas_per_vector"] for _, pl in tails] == [3, 6]
+        dz2, it2, eb2, n2 = solve(h, spec, trace=fp64)
+    # each solution within the certified bounds of the oracle's
+    lim = eb1 + b_or
+    assert (rowrel(dz1, x_or) <= 2 * lim).all()
+    assert (rowrel(dz2, x_or) <= 2 * (eb2 + b_or)).all()
+    # the same iterates up to the reductions' rounding order (FP32 sweeps
+    # in the mixed form round at 6e-8, and its counts follow that further)
+    slack = 2 if fp64 else np.maximum(3, 0.03 * it1)
+    assert (np.abs(it2.astype(int) - it1) <= slack).all()
+    if fp64:
+        # the persistent launches: one per PCG round without tail tilings (the
+        # certified stop checks the true residual after a round and may run
+        # another); with them one per phase, at most one per level and round,
+        # and more than without when the six longest members need clearly
+        # more iterations than the rest (each member's cluster runs its own
+        # iterations, so the order in which members stop is not exactly that
+        # of their counts)
+        assert n1 >= 1
+        assert n1 <= n2 <= 3 * n1
+        srt = np.sort(it2)[::-1]
+        if srt[6] < 0.95 * srt[0]:
+            assert n2 > n1
+
+
+def test_tail_plan_refusals_and_autotune(case):
+    spec, taps, xb, y, _, _ = case
+    with P.Handle.from_spec(spec, taps, precision=P.EDA_FP64) as h:
+        h.eda_set_trajectory(xb, y)
+        with pytest.raises(P.EdaError):
+            h.eda_set_tail_plan(spec.n_members + 1, cs=3, K=2)  # level above L + 1
+        with pytest.raises(P.EdaError):
+            h.eda_set_tail_plan(4, cs=200, K=2)  # no tiling of that shape
+        with pytest.raises(P.EdaError):
+            h.eda_set_tail_plan(4, cs=3, K=2, fp64=False)  # an FP64 handle has no FP32 sweep
+        h.eda_set_tail_plan(4, cs=3, K=2)
+        h.eda_set_tail_plan(4, cs=6, K=2)  # same level: replaced
+        t = h.eda_tail_plans()
+        assert len(t) == 1 and t[0][0] == 4 and t[0][1]["ctas_per_vector"] == 6
+        h.eda_autotune(0)
+        t = h.eda_tail_plans()
+        lv = [x for x, _ in t]
+        assert lv == sorted(lv, reverse=True) and all(1 <= x <= spec.n_members // 2 + 1 for x in lv)
+        main = h.eda_sweep_plan(fp64=True)
+        for _, pl in t:
+            assert pl["kind"] == "cluster" and pl["ctas_per_vector"] > main["ctas_per_vector"]
