@@ -61,10 +61,13 @@ def parse():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the scale, uneven-batch and warm-start measurements")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--profile-case", choices=["fp64", "mixed"], default=None,
-                    help="profiling case for ncu: the workload's setup, sketch and LMP, then one PCG solve of "
-                         "--profile-iters fixed iterations between cudaProfilerStart/Stop; prints one line")
+    ap.add_argument("--profile-case", choices=["fp64", "mixed", "scale"], default=None,
+                    help="profiling case for ncu: fp64 / mixed: the workload's setup, sketch and LMP, then one "
+                         "PCG solve of --profile-iters fixed iterations between cudaProfilerStart/Stop; scale: "
+                         "one batched FP32 Hessian product of --profile-members members of the scale workload "
+                         "(its multi-launch chain) in that range; prints one line")
     ap.add_argument("--profile-iters", type=int, default=20)
+    ap.add_argument("--profile-members", type=int, default=9)
     return ap.parse_args()
 
 
@@ -1085,10 +1088,57 @@ def run_ours(args):
     return 0
 
 
+def run_profile_scale(args):
+    """The scale workload's batched FP32 Hessian product for a reduced number
+    of members (the trajectory still far larger than L2), on the autotuned
+    tiling, once inside a profiler range: a small case of the multi-launch
+    chain for ncu."""
+    import torch
+    import paper_2605_23571_gb300 as P
+    P.build()
+    # the FP32 product reads no FP64 stage states: leave the store out, so
+    # that the device holds under a gigabyte for the profiler
+    os.environ["EDA_STAGE_STORE"] = "0"
+    dev = torch.device("cuda", 0)
+    spec = replace(S.spec_scale(seed=0), n_members=args.profile_members, ckpt_every=0)
+    spec = replace(spec, ell=min(spec.ell, spec.n_members - 1), k=min(spec.k, spec.n_members - 2))
+    taps = P.bhalf_gaussian(spec.n, spec.length_scale, spec.sigma_b)
+    dr = S.draws(spec)
+    M, n, p = spec.n_members, spec.n, spec.p
+    xb = torch.empty(M, n, dtype=torch.float64, device=dev)
+    y = torch.empty(M, p, dtype=torch.float64, device=dev)
+    with P.Handle.from_spec(spec, taps, precision=P.EDA_FP64) as hg:
+        hg.eda_twin(torch.tensor(spec.F + spec.spin_sigma * dr.eta_spin, device=dev), spec.spinup,
+                    torch.tensor(dr.eta_b, device=dev), torch.tensor(dr.eta_o, device=dev), xb, y)
+    cols = torch.arange(M, dtype=torch.int32, device=dev)
+    V = torch.tensor(S.gaussian_matrix(M, n, 31), device=dev)
+    hv = torch.empty_like(V)
+    with P.Handle.from_spec(spec, taps, precision=P.EDA_MIXED) as h:
+        h.eda_set_trajectory(xb, y)
+        h.eda_autotune(2)
+        ms = h.eda_time_hvp_sweep(reps=3)
+        h.eda_hvp(cols, V, hv, True)  # warm
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        h.eda_time_hvp_sweep(reps=1)
+        e1.record()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        plan = h.eda_sweep_plan(fp64=False)
+    print(json.dumps({"profile_case": "scale", "workload": "l96_n65536_w96_m%d" % M, "members": M,
+                      "ms_product": ms, "ms_profiled": e0.elapsed_time(e1), "plan": plan,
+                      "algorithmic_bytes": M * 4 * n * (2 * spec.nsteps + 2)}))
+    return 0
+
+
 def run_profile_case(args):
     """One fixed-iteration solve of the batched workload inside a profiler
     range: a small case of the solve's kernels for ncu (the same kernels and
     shapes as the timed steps, a few tens of milliseconds)."""
+    if args.profile_case == "scale":
+        return run_profile_scale(args)
     import torch
     import paper_2605_23571_gb300 as P
     P.build()
