@@ -485,9 +485,14 @@ EDA_API int eda_group_set_trajectories(eda_group* g, const double* const* xb, co
 EDA_API int eda_group_sketch(eda_group* g);
 /* The rest of Algorithm 1 and the LMP of every problem (eda_build_lmp). */
 EDA_API int eda_group_build_lmp(eda_group* g);
-/* Autotuner: times the group's batched member sweep for halo refresh periods
- * K in {2, 4, 8, 16} per bucket, keeps the fastest per problem.
- * *best_ms_out (may be NULL) = mean time of the tuned batched sweep (ms). */
+/* Autotuner of the group's tile shapes: for every problem, tiles of 1 or 2
+ * times the fewest CTAs per member that fit, and halo refresh periods K in
+ * {2, 4, 8, 16}.  Times the batched member sweep of every resulting bucket
+ * (problems of one cluster size and power-of-two CTA size, launched
+ * together) alone on the device, charges each problem its share of its
+ * bucket's time (by members x n x window), and keeps each problem's cheapest
+ * shape and period.  *best_ms_out (may be NULL) = mean time of the tuned
+ * batched sweep (ms). */
 EDA_API int eda_group_autotune(eda_group* g, double* best_ms_out);
 /* Batched PCG of every member of every problem (as eda_solve_batch, x0 = 0;
  * maxit is a budget per member, so one hard problem does not cut the others

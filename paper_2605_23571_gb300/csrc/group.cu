@@ -222,7 +222,11 @@ SweepProb<T> make_prob(eda_handle* h, const SweepPlan& pl, int* tab) {
 
 // Plans every problem for one precision with refresh period K (per bucket
 // later), groups problems into buckets by cluster size and thread count.
-int plan_group(eda_group* g, bool fp64, const std::vector<int>& Kp) {
+// Tilings and buckets of every problem: halo refresh period Kp[pi] and a
+// tile shape of mult[pi] (1 or 2) times the fewest CTAs per member that fit
+// (mult empty: 1), falling back to the fewest where the wider shape does not
+// fit.
+int plan_group(eda_group* g, bool fp64, const std::vector<int>& Kp, const std::vector<int>& mult = {}) {
   const int eb = fp64 ? 8 : 4;
   std::vector<Bucket>& bs = fp64 ? g->b64 : g->b32;
   std::map<std::pair<int, int>, int> key2b;
@@ -233,6 +237,11 @@ int plan_group(eda_group* g, bool fp64, const std::vector<int>& Kp) {
     SweepPlan pl;
     bool ok = false;
     for (int CS = 1; CS <= 16 && !ok; ++CS) ok = eda::plan_sweep_exact(h->n, eb, h->w, CS, Kp[pi], &pl);
+    if (ok && !mult.empty() && mult[pi] > 1) {
+      SweepPlan wide;
+      const int cs2 = pl.CS * mult[pi];
+      if (cs2 <= 16 && eda::plan_sweep_exact(h->n, eb, h->w, cs2, Kp[pi], &wide) && wide.HL <= h->n) pl = wide;
+    }
     if (!ok && !eda::plan_sweep(h->n, eb, h->w, 1, 0, &pl))
       return gfail(g, EDA_ERR_INVALID, "group: a problem does not fit the sweep tiling");
     if (pl.ml)
@@ -461,12 +470,23 @@ int group_persist(eda_group* g, bool sweep64, bool use_lmp, double tol, int maxi
     g->bevents.push_back(ev2);
   }
   GCU(g, cudaEventRecord(g->join, g->st));
+  // EDA_VERBOSE: each bucket's launch timed on its stream, printed at the end
+  const bool verbose = eda::env_int("EDA_VERBOSE", 0) != 0;
+  std::vector<cudaEvent_t> tev;
   size_t bi = 0;
   for (Bucket& b : bs) {
     const size_t mine = bi++;
     if (b.items.empty()) continue;
     cudaStream_t bst = g->bstreams[mine];
     GCU(g, cudaStreamWaitEvent(bst, g->join, 0));
+    if (verbose) {
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      GCU(g, cudaEventCreate(&e0));
+      GCU(g, cudaEventCreate(&e1));
+      tev.push_back(e0);
+      tev.push_back(e1);
+      GCU(g, cudaEventRecord(e0, bst));
+    }
     // the between-sweep scratch must fit the bucket's shared memory
     int tmax = 0;
     for (int pi : b.probs)
@@ -519,10 +539,26 @@ int group_persist(eda_group* g, bool sweep64, bool use_lmp, double tol, int maxi
     pa.pprobs = g->probs;
     pa.queue = g->queue + qi++;
     GCU(g, eda::launch_pcg_persist<TS>(pa, pl, bst));
+    if (verbose) GCU(g, cudaEventRecord(tev.back(), bst));
     GCU(g, cudaEventRecord(g->bevents[mine], bst));
     GCU(g, cudaStreamWaitEvent(g->st, g->bevents[mine], 0));
   }
   GCU(g, cudaStreamSynchronize(g->st));
+  if (verbose) {
+    size_t j = 0;
+    for (const Bucket& b : bs) {
+      if (b.items.empty()) continue;
+      float ms = 0.f;
+      GCU(g, cudaEventElapsedTime(&ms, tev[j], tev[j + 1]));
+      long long work = 0;  // member x n x window of the bucket
+      for (int pi : b.probs) work += (long long)g->hs[pi]->M * g->hs[pi]->n * g->hs[pi]->N;
+      std::fprintf(stderr, "persistent group bucket CS=%d A=%d K=%d problems=%zu items=%zu work=%lld: %.1f ms\n",
+                   b.CS, b.A, b.K, b.probs.size(), b.items.size(), work, ms);
+      cudaEventDestroy(tev[j]);
+      cudaEventDestroy(tev[j + 1]);
+      j += 2;
+    }
+  }
   *it_io += maxit;
   return EDA_OK;
 }
@@ -814,20 +850,26 @@ EDA_API int eda_group_autotune(eda_group* g, double* best_ms_out) {
   for (int pi = 0; pi < g->P; ++pi)
     if (!g->hs[pi]->have_traj) return gfail(g, EDA_ERR_STATE, "eda_group_autotune before eda_group_set_trajectories");
   const bool fp64 = g->prec == EDA_FP64;
-  // time the batched member sweep of every bucket for K in {2, 4, 8, 16};
-  // keep the fastest K per problem's bucket
+  // tile shapes (1 or 2 times the fewest CTAs per member) x halo refresh
+  // periods K in {2, 4, 8, 16}: time the batched member sweep of every
+  // bucket alone and charge each problem its share of the bucket's time (by
+  // members x n x window); keep each problem's cheapest shape and period
   const int Ks[] = {2, 4, 8, 16};
-  std::vector<int> bestK(g->P, 4);
-  std::vector<float> bestT(g->P, 1e30f);
+  std::vector<int> bestK(g->P, 4), bestM(g->P, 1);
+  std::vector<double> bestT(g->P, 1e300);
+  std::vector<double> work(g->P);
+  for (int pi = 0; pi < g->P; ++pi)
+    work[pi] = (double)g->hs[pi]->M * g->hs[pi]->n * std::max(g->hs[pi]->N, 1);
   cudaEvent_t e0, e1;
   GCU(g, cudaEventCreate(&e0));
   GCU(g, cudaEventCreate(&e1));
   GCU(g, cudaMemcpyAsync(g->p, g->b, (size_t)g->vtot * sizeof(double), cudaMemcpyDeviceToDevice, g->st));
   GCU(g, cudaMemsetAsync(g->active, 0xFF, (size_t)g->T * sizeof(int), g->st));  // all flags nonzero
   double total = 0.0;
+  for (int m : {1, 2})
   for (int K : Ks) {
-    std::vector<int> Kp(g->P, K);
-    int rc = plan_group(g, fp64, Kp);
+    std::vector<int> Kp(g->P, K), Mp(g->P, m);
+    int rc = plan_group(g, fp64, Kp, Mp);
     if (rc) return rc;
     rc = set_items(g, fp64, false);
     if (rc) return rc;
@@ -847,14 +889,19 @@ EDA_API int eda_group_autotune(eda_group* g, double* best_ms_out) {
       GCU(g, cudaEventSynchronize(e1));
       GCU(g, cudaEventElapsedTime(&ms, e0, e1));
       std::swap(bs, only);
-      for (int pi : b.probs)
-        if (ms < bestT[pi]) {
-          bestT[pi] = ms;
+      double bw = 0.0;
+      for (int pi : b.probs) bw += work[pi];
+      for (int pi : b.probs) {
+        const double cost = (double)ms * work[pi] / std::max(bw, 1.0);
+        if (cost < bestT[pi]) {
+          bestT[pi] = cost;
           bestK[pi] = K;
+          bestM[pi] = m;
         }
+      }
     }
   }
-  int rc = plan_group(g, fp64, bestK);
+  int rc = plan_group(g, fp64, bestK, bestM);
   if (rc) return rc;
   rc = set_items(g, fp64, false);
   if (rc) return rc;

@@ -99,11 +99,12 @@ def test_he_initialisation_matches_oracle():
 
 def test_warm_start_gain_on_held_out_problems():
     # training triples (member RHS, control solution, member solution) from
-    # the plain FP64 solver on small problems, the network trained on the GPU,
-    # then a held-out problem solved from zero and from the network's guess
-    # to the same tolerance: the guess must beat the control solution as a
-    # guess, both solves converge and agree within the residual bound, and the
-    # iterations saved are reported
+    # the plain FP64 solver on small problems, the network trained on the GPU
+    # (AdamW, cosine learning-rate schedule), then a held-out problem solved
+    # from zero and from the network's guess to the same tolerance: the guess
+    # must beat the control solution as a guess, the warm-started solve must
+    # need fewer member iterations in all, both solves converge and agree
+    # within the residual bound, and the iterations saved are reported
     import torch
     dev = torch.device("cuda:0")
     n, N, members = 256, 16, 64
@@ -145,8 +146,11 @@ def test_warm_start_gain_on_held_out_problems():
     R, C, Z = (torch.cat(v).contiguous() for v in (R, C, Z))
     with P.WarmStart(n, 32, max_batch=64) as ws:
         ws.eda_ws_init(S.gaussian_matrix(1, ws.num_params, 5)[0])
-        order = np.concatenate([np.random.default_rng(e).permutation(R.shape[0]) for e in range(30)])
-        losses = ws.eda_ws_train(R, C, Z, epochs=30, batch=64, lr=2e-3, order=order.astype(np.int32))
+        losses = []
+        for e in range(30):
+            order = np.random.default_rng(e).permutation(R.shape[0]).astype(np.int32)
+            lr = 0.5 * 2e-3 * (1 + np.cos(np.pi * e / 30))
+            losses.append(ws.eda_ws_train(R, C, Z, epochs=1, batch=64, lr=lr, order=order)[0])
         assert losses[-1] < losses[0]
         h, b = problem_on_gpu(900)
         dz0, it0, rr0, st0 = solve(h, b)
@@ -164,6 +168,9 @@ def test_warm_start_gain_on_held_out_problems():
              100.0 * (1 - itw[1:].sum() / it0[1:].sum())))
     assert np.median(err_guess) < np.median(err_ctrl)
     assert (st0 == P.EDA_CONVERGED).all() and (stw == P.EDA_CONVERGED).all()
+    # CG's count falls only with the logarithm of the initial error (about
+    # 1 % here for a guess at 0.6 of the solution), but it must fall
+    assert itw[1:].sum() < it0[1:].sum()
     # both solutions are within their residuals of the exact one (lambda_min >= 1)
     bn = torch.linalg.norm(b, dim=1).cpu().numpy()
     diff = torch.linalg.norm(dzw - dz0, dim=1).cpu().numpy()

@@ -109,3 +109,32 @@ def test_training_reduces_loss_on_a_linear_target():
         loss, g = W.loss_and_grad(theta, hidden, rhs, ctrl, sol, 1.0, 1.0)
         theta, m, v = W.adamw_step(theta, g, m, v, t, lr=3e-3, wd=0.0)
     assert loss < 0.2 * l0
+
+
+def test_pcg_iterations_fall_only_logarithmically_with_the_guess_error():
+    # what any warm start can gain: the oracle's PCG (Section 2.3, with the
+    # spectral LMP of Section 3.1) from initial iterates x* + e with smooth
+    # errors |e| = eps |x*| needs fewer iterations as eps falls, but only in
+    # proportion to log(1 / eps): a guess at 1 % of the solution still needs
+    # most of the iterations of a start from zero
+    import eda_synth as S
+    import oracle as O
+    spec = S.spec_small(128, 12, 17, every_var=2, every_step=2, length_scale=4.0, seed=77)
+    taps = O.bhalf_taps(spec.n, spec.length_scale, spec.sigma_b)
+    _, xb, y = O.twin(spec, S.draws(spec), taps)
+    ref = O.eda_pipeline(spec, xb, y, taps, tol=1e-10, maxit=2000)
+    x, b = ref["x"], ref["b"]
+
+    def iters(x0):
+        r = O.pcg(lambda V: O.hvp(spec, ref["traj"], V, taps), b, lambda R: O.lmp_apply(ref["S"], ref["c"], R),
+                  tol=1e-8, maxit=2000, x0=x0)
+        assert (r["status"] == 0).all()
+        return int(r["iters"].sum())
+
+    rng = np.random.default_rng(3)
+    noise = np.stack([O.bhalf_apply(v, taps) for v in rng.standard_normal(x.shape)])
+    noise *= np.linalg.norm(x, axis=1, keepdims=True) / np.linalg.norm(noise, axis=1, keepdims=True)
+    n0 = iters(None)
+    counts = [iters(x + eps * noise) for eps in (0.5, 0.1, 0.01)]
+    assert n0 >= counts[0] >= counts[1] >= counts[2]
+    assert counts[2] > 0.5 * n0, (n0, counts)
