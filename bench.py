@@ -1166,6 +1166,9 @@ def run_profile_case(args):
     shapes as the timed steps, a few tens of milliseconds)."""
     if args.profile_case == "scale":
         return run_profile_scale(args)
+    # one launch on the main tiling: no relaunch on the convergence tail's
+    # tilings, whose members stop together after the fixed iterations
+    os.environ["EDA_TAIL"] = "0"
     import torch
     import paper_2605_23571_gb300 as P
     P.build()
