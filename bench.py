@@ -61,11 +61,13 @@ def parse():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the scale, uneven-batch and warm-start measurements")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--profile-case", choices=["fp64", "mixed", "scale"], default=None,
+    ap.add_argument("--profile-case", choices=["fp64", "mixed", "scale", "lmp"], default=None,
                     help="profiling case for ncu: fp64 / mixed: the workload's setup, sketch and LMP, then one "
                          "PCG solve of --profile-iters fixed iterations between cudaProfilerStart/Stop; scale: "
                          "one batched FP32 Hessian product of --profile-members members of the scale workload "
-                         "(its multi-launch chain) in that range; prints one line")
+                         "(its multi-launch chain) in that range; lmp: the LMP apply on CUDA and tensor cores "
+                         "timed at the batched and the scale sizes, the batched size's tensor-core apply in that "
+                         "range; prints one line")
     ap.add_argument("--profile-iters", type=int, default=20)
     ap.add_argument("--profile-members", type=int, default=9)
     return ap.parse_args()
@@ -1160,12 +1162,62 @@ def run_profile_scale(args):
     return 0
 
 
+def run_profile_lmp(args):
+    """The LMP apply Z = R + S diag(c) S^T R of every member (Section 3.1) on
+    CUDA cores (FP32 arithmetic, the mixed form's) and as split-BF16
+    tensor-core products, timed with CUDA events at the batched size (n=4096,
+    k=49, 51 members) and the scale size (n=65536, k=79, 81 members), on an
+    orthonormal S with a decreasing spectrum loaded by eda_set_lmp; then one
+    tensor-core apply at the batched size inside a profiler range."""
+    import torch
+    import paper_2605_23571_gb300 as P
+    P.build()
+    os.environ["EDA_STAGE_STORE"] = "0"
+    dev = torch.device("cuda", 0)
+    out = {"profile_case": "lmp"}
+    for key, spec in (("scale", replace(S.spec_scale(seed=0), ckpt_every=0)), ("batched", S.spec_batched(seed=0))):
+        n, k, M = spec.n, spec.k, spec.n_members
+        taps = P.bhalf_gaussian(n, spec.length_scale, spec.sigma_b)
+        Sk = np.linalg.qr(S.gaussian_matrix(n, k, 7))[0]
+        ev = np.logspace(5, 1, k)
+        R = torch.tensor(S.gaussian_matrix(M, n, 8), device=dev)
+        Z = torch.empty_like(R)
+        with P.Handle.from_spec(spec, taps, precision=P.EDA_MIXED) as h:
+            h.eda_set_lmp(np.ascontiguousarray(Sk.T), ev)
+            res = {"n": n, "k": k, "members": M, "flops_per_apply": 4 * n * k * M}
+            for kind, name in ((0, "cuda_cores_fp32"), (1, "tensor_cores_split_bf16")):
+                for _ in range(3):
+                    h.eda_lmp_apply(R, Z, 0, kind)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(20):
+                    h.eda_lmp_apply(R, Z, 0, kind)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / 20
+                res[name] = {"ms": ms, "tflops": 4 * n * k * M / (ms / 1e3) / 1e12}
+            if key == "batched":
+                torch.cuda.synchronize()
+                torch.cuda.profiler.start()
+                h.eda_lmp_apply(R, Z, 0, 1)
+                torch.cuda.synchronize()
+                torch.cuda.profiler.stop()
+        out[key] = res
+        del R, Z
+        torch.cuda.synchronize()
+    print(json.dumps(out))
+    return 0
+
+
 def run_profile_case(args):
     """One fixed-iteration solve of the batched workload inside a profiler
     range: a small case of the solve's kernels for ncu (the same kernels and
     shapes as the timed steps, a few tens of milliseconds)."""
     if args.profile_case == "scale":
         return run_profile_scale(args)
+    if args.profile_case == "lmp":
+        return run_profile_lmp(args)
     # one launch on the main tiling: no relaunch on the convergence tail's
     # tilings, whose members stop together after the fixed iterations
     os.environ["EDA_TAIL"] = "0"
