@@ -1165,47 +1165,57 @@ def run_profile_scale(args):
 def run_profile_lmp(args):
     """The LMP apply Z = R + S diag(c) S^T R of every member (Section 3.1) on
     CUDA cores (FP32 arithmetic, the mixed form's) and as split-BF16
-    tensor-core products, timed with CUDA events at the batched size (n=4096,
-    k=49, 51 members) and the scale size (n=65536, k=79, 81 members), on an
-    orthonormal S with a decreasing spectrum loaded by eda_set_lmp; then one
-    tensor-core apply at the batched size inside a profiler range."""
+    tensor-core products, timed with CUDA events at the scale size (n=65536,
+    k=79, 81 members) and the batched size (n=4096, k=49, 51 members), on an
+    orthonormal S with a decreasing spectrum loaded by eda_set_lmp (the apply
+    does not read the trajectory, so the handles carry a 2-step window);
+    then one tensor-core apply of each size inside a profiler range."""
     import torch
     import paper_2605_23571_gb300 as P
     P.build()
     os.environ["EDA_STAGE_STORE"] = "0"
     dev = torch.device("cuda", 0)
     out = {"profile_case": "lmp"}
-    for key, spec in (("scale", replace(S.spec_scale(seed=0), ckpt_every=0)), ("batched", S.spec_batched(seed=0))):
+    cases = (("scale", S.spec_small(65536, 2, 81, ell=80, k=79, length_scale=8.0, seed=5)),
+             ("batched", S.spec_small(4096, 2, 51, ell=50, k=49, length_scale=8.0, seed=6)))
+    hs = []
+    for key, spec in cases:
         n, k, M = spec.n, spec.k, spec.n_members
         taps = P.bhalf_gaussian(n, spec.length_scale, spec.sigma_b)
         Sk = np.linalg.qr(S.gaussian_matrix(n, k, 7))[0]
         ev = np.logspace(5, 1, k)
         R = torch.tensor(S.gaussian_matrix(M, n, 8), device=dev)
         Z = torch.empty_like(R)
-        with P.Handle.from_spec(spec, taps, precision=P.EDA_MIXED) as h:
-            h.eda_set_lmp(np.ascontiguousarray(Sk.T), ev)
-            res = {"n": n, "k": k, "members": M, "flops_per_apply": 4 * n * k * M}
-            for kind, name in ((0, "cuda_cores_fp32"), (1, "tensor_cores_split_bf16")):
-                for _ in range(3):
-                    h.eda_lmp_apply(R, Z, 0, kind)
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                for _ in range(20):
-                    h.eda_lmp_apply(R, Z, 0, kind)
-                e1.record()
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / 20
-                res[name] = {"ms": ms, "tflops": 4 * n * k * M / (ms / 1e3) / 1e12}
-            if key == "batched":
-                torch.cuda.synchronize()
-                torch.cuda.profiler.start()
-                h.eda_lmp_apply(R, Z, 0, 1)
-                torch.cuda.synchronize()
-                torch.cuda.profiler.stop()
+        h = P.Handle.from_spec(spec, taps, precision=P.EDA_MIXED)
+        h.eda_set_lmp(np.ascontiguousarray(Sk.T), ev)
+        # algorithmic bytes of one apply: R read by both launches, Z written,
+        # S read once in each of its two tiled BF16 forms (high and low parts)
+        nS, kt = -(-n // 128) * 128, -(-k // 16) * 16
+        res = {"n": n, "k": k, "members": M, "flops_per_apply": 4 * n * k * M,
+               "bytes_per_apply_tc": 3 * 8 * n * M + 2 * 2 * nS * (128 + kt)}
+        for kind, name in ((0, "cuda_cores_fp32"), (1, "tensor_cores_split_bf16")):
+            for _ in range(3):
+                h.eda_lmp_apply(R, Z, 0, kind)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(20):
+                h.eda_lmp_apply(R, Z, 0, kind)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 20
+            res[name] = {"ms": ms, "tflops": 4 * n * k * M / (ms / 1e3) / 1e12}
+        res["tensor_cores_split_bf16"]["gbs"] = res["bytes_per_apply_tc"] / (res["tensor_cores_split_bf16"]["ms"] / 1e3) / 1e9
         out[key] = res
-        del R, Z
-        torch.cuda.synchronize()
+        hs.append((h, R, Z))
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    for h, R, Z in hs:
+        h.eda_lmp_apply(R, Z, 0, 1)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    for h, _, _ in hs:
+        h.close()
     print(json.dumps(out))
     return 0
 

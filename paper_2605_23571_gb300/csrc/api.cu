@@ -1670,14 +1670,12 @@ int prep_ucoef(eda_handle* h) {
 // BF16 high/low copies of S for the tensor-core LMP, for the current LMP.
 int prep_bf16(eda_handle* h) {
   if (h->bf_version == h->lmp_version) return EDA_OK;
-  const size_t one = (size_t)eda::lmp_tc_kt(h->k) * eda::lmp_tc_ns(h->n);
   if (!h->Sbf) {
     __nv_bfloat16* p = nullptr;
-    CU(h, dalloc(h, &p, 4 * one));
+    CU(h, dalloc(h, &p, eda::lmp_tc_elems(h->n, h->k)));
     h->Sbf = p;
   }
-  __nv_bfloat16* b = static_cast<__nv_bfloat16*>(h->Sbf);
-  CU(h, eda::split_bf16(h->n, h->k, h->S, b, b + one, b + 2 * one, b + 3 * one, h->st));
+  CU(h, eda::split_bf16(h->n, h->k, h->S, static_cast<__nv_bfloat16*>(h->Sbf), h->st));
   h->bf_version = h->lmp_version;
   return EDA_OK;
 }
@@ -1729,9 +1727,7 @@ int lmp_apply_dev(eda_handle* h, int which, int kind, int ncol, const double* R,
     CU(h, dalloc(h, &h->tc_timeout, 1));
     CU(h, cudaMemsetAsync(h->tc_timeout, 0, sizeof(int), h->st));
   }
-  const size_t one = (size_t)eda::lmp_tc_kt(k) * eda::lmp_tc_ns(n);
-  const __nv_bfloat16* b = static_cast<const __nv_bfloat16*>(h->Sbf);
-  CU(h, eda::lmp_apply_tc(n, k, b, b + one, b + 2 * one, b + 3 * one, coef, ncol, R, Z, active, h->Wtc,
+  CU(h, eda::lmp_apply_tc(n, k, static_cast<const __nv_bfloat16*>(h->Sbf), coef, ncol, R, Z, active, h->Wtc,
                           h->tc_timeout, h->st));
   return EDA_OK;
 }

@@ -97,7 +97,7 @@ struct eda_handle {
   // TS projection scratch, the tensor-core wait flag; versions follow the LMP
   int lmp_version = 0, uv_version = -1, bf_version = -1;
   double* uv = nullptr;
-  void* Sbf = nullptr;          // 4 arrays of kt x nS BF16: Shi | Slo | ShiT | SloT
+  void* Sbf = nullptr;          // tiled BF16 copies of S (lmp.h: lmp_tc_elems)
   float* Wtc = nullptr;
   long long wtc_cap = 0;        // floats
   void* Wcc = nullptr;

@@ -10,14 +10,19 @@
 //    and FP32 accumulators in tensor memory.  Each operand x is split as
 //    x = hi + lo with hi = bf16(x), lo = bf16(x - hi) (16 significant bits
 //    together), and each product is taken as hi.hi + hi.lo + lo.hi into one
-//    accumulator (the dropped lo.lo term is 2^-16 below it).  Operands are
-//    staged by the CTA's threads into shared memory in the canonical
-//    K-major, no-swizzle layout (core matrices of 8 rows x 16 bytes), one
-//    thread issues the MMAs, an mbarrier (bounded wait) signals completion,
-//    and the epilogue reads the accumulator with tcgen05.ld.
+//    accumulator (the dropped lo.lo term is 2^-16 below it).  Shared-memory
+//    operands use the canonical K-major, no-swizzle layout (core matrices of
+//    8 rows x 16 bytes).  The S operand of each row chunk is stored in global
+//    memory already in that layout (split_bf16), so one bulk asynchronous
+//    copy per part (cp.async.bulk, completion counted on an mbarrier) moves
+//    it while the CTA's threads split the member vectors into the other
+//    operand.  One thread issues the MMAs and commits to a second mbarrier;
+//    every wait is bounded; the epilogue reads the accumulator with
+//    tcgen05.ld.  The grid covers row chunks x member tiles.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "eda_internal.h"
@@ -100,7 +105,7 @@ __global__ void __launch_bounds__(kCcThreads) lmp_expand_cc_kernel(int n, int k,
 }
 
 // --------------------------------------------------------------- tensor cores
-constexpr int kTcThreads = 128;  // four warps: warp w reads TMEM lanes 32w..32w+31
+constexpr int kTcThreads = 256;  // eight warps: warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31
 constexpr int kWaitLimit = 1 << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -223,106 +228,169 @@ __device__ __forceinline__ void tmem_free(uint32_t base, int ncols) {
 
 __device__ __forceinline__ int tmem_cols(int mt) { return mt <= 32 ? 32 : (mt <= 64 ? 64 : (mt <= 128 ? 128 : 256)); }
 
-// Issues the kt/16 K-steps of hi.hi + hi.lo + lo.hi (thread 0), commits to
-// the mbarrier, and waits for it (every thread, bounded).  Operands K-major
-// with kg = K/8 core-matrix groups along K (lbo 128, sbo kg * 128).
+// Bulk asynchronous copy of `bytes` (a multiple of 16, both addresses
+// 16-byte aligned) from global to this CTA's shared memory, its completion
+// counted on the mbarrier at mbar.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// Issues the kg/2 K-steps of hi.hi + hi.lo + lo.hi (thread 0) once the bulk
+// copies counted on `tma` have landed (bounded wait; tma == 0: nothing to
+// wait for), commits them to `mma`, and waits for it (every thread,
+// bounded).  If the copies' wait gives up, thread 0 arrives on `mma` itself
+// so that the CTA's wait ends.  Operands K-major with kg = K/8 core-matrix
+// groups along K (lbo 128, sbo kg * 128).  Returns false (uniformly) when a
+// wait gave up: *timeout is set, and the copies and MMAs in flight get a
+// second bounded wait before the caller frees tensor memory.
 __device__ __forceinline__ bool mma_split3(uint32_t dt, const unsigned char* Ahi, const unsigned char* Alo,
                                            const unsigned char* Bhi, const unsigned char* Blo, int kg, int nd,
-                                           uint32_t mbar, int* timeout) {
+                                           uint32_t tma, uint32_t mma, int* flag, int* timeout) {
   if (threadIdx.x == 0) {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t id = idesc_bf16(nd);
-    const uint32_t sbo = (uint32_t)kg * 128u;
-    for (int ks = 0; ks < kg / 2; ++ks) {
-      const uint32_t o = (uint32_t)ks * 256u;  // two core matrices along K per step of 16
-      const uint64_t ah = kmajor_desc(smem_u32(Ahi) + o, 128u, sbo);
-      const uint64_t al = kmajor_desc(smem_u32(Alo) + o, 128u, sbo);
-      const uint64_t bh = kmajor_desc(smem_u32(Bhi) + o, 128u, sbo);
-      const uint64_t bl = kmajor_desc(smem_u32(Blo) + o, 128u, sbo);
-      mma_bf16(dt, ah, bh, id, ks > 0 ? 1u : 0u);
-      mma_bf16(dt, ah, bl, id, 1u);
-      mma_bf16(dt, al, bh, id, 1u);
+    const bool have = tma == 0u || mbar_wait(tma, 0);
+    *flag = have ? 1 : 0;
+    if (have) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t id = idesc_bf16(nd);
+      const uint32_t sbo = (uint32_t)kg * 128u;
+      for (int ks = 0; ks < kg / 2; ++ks) {
+        const uint32_t o = (uint32_t)ks * 256u;  // two core matrices along K per step of 16
+        const uint64_t ah = kmajor_desc(smem_u32(Ahi) + o, 128u, sbo);
+        const uint64_t al = kmajor_desc(smem_u32(Alo) + o, 128u, sbo);
+        const uint64_t bh = kmajor_desc(smem_u32(Bhi) + o, 128u, sbo);
+        const uint64_t bl = kmajor_desc(smem_u32(Blo) + o, 128u, sbo);
+        mma_bf16(dt, ah, bh, id, ks > 0 ? 1u : 0u);
+        mma_bf16(dt, ah, bl, id, 1u);
+        mma_bf16(dt, al, bh, id, 1u);
+      }
+      mma_commit(mma);
+    } else {
+      mbar_arrive(mma);
     }
-    mma_commit(mbar);
   }
   __syncwarp();
-  bool ok = mbar_wait(mbar, 0);
-  // uniform over the CTA: the epilogue's tcgen05.ld is warp-collective
+  bool ok = mbar_wait(mma, 0);
+  // uniform over the CTA (the epilogue's tcgen05.ld is warp-collective); the
+  // barrier also publishes thread 0's flag
   ok = __syncthreads_and(ok ? 1 : 0) != 0;
-  if (!ok) {
+  if (!ok || *flag == 0) {
     if (threadIdx.x == 0 && timeout != nullptr) atomicExch(timeout, 1);
-    // give the MMAs in flight a second bounded wait before the caller
-    // frees their tensor memory
-    mbar_wait(mbar, 0);
+    if (tma != 0u) mbar_wait(tma, 0);
+    mbar_wait(mma, 0);
+    ok = false;
   }
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   return ok;
 }
 
-__device__ __forceinline__ void mbar_init(uint64_t* mbar) {
+// Shared-memory layout of both kernels: A hi | A lo (bulk-copied) | B hi |
+// B lo | two mbarriers (bulk copies, MMAs) | TMEM slot | flag.
+struct TcSmem {
+  unsigned char *Ahi, *Alo, *Bhi, *Blo;
+  uint32_t tma, mma;
+  uint32_t* slot;
+  int* flag;
+};
+
+__device__ __forceinline__ TcSmem tc_smem(unsigned char* sm, uint32_t a_bytes, uint32_t b_bytes) {
+  TcSmem t;
+  t.Ahi = sm;
+  t.Alo = sm + a_bytes;
+  t.Bhi = t.Alo + a_bytes;
+  t.Blo = t.Bhi + b_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(t.Blo + b_bytes);
+  t.tma = smem_u32(bars);
+  t.mma = smem_u32(bars + 1);
+  t.slot = reinterpret_cast<uint32_t*>(bars + 2);
+  t.flag = reinterpret_cast<int*>(t.slot + 1);
+  return t;
+}
+
+// Thread 0: initialises both mbarriers and starts the bulk copies of the
+// two parts of A (a_bytes each) from hi and lo.
+__device__ __forceinline__ void start_a(const TcSmem& t, const __nv_bfloat16* hi, const __nv_bfloat16* lo,
+                                        uint32_t a_bytes) {
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(t.tma) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(t.mma) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(t.tma), "r"(2u * a_bytes)
+                 : "memory");
+    bulk_g2s(smem_u32(t.Ahi), hi, a_bytes, t.tma);
+    bulk_g2s(smem_u32(t.Alo), lo, a_bytes, t.tma);
   }
 }
 
 // Projections W[m][c] += sum_{i in chunk} S[c][i] R[m][i]: D (128 modes x mt
-// members) = A (modes x 128 rows) B (128 rows x members), K = the chunk's rows.
-// Shared: A hi, lo [128 x 128] | B hi, lo [mt x 128] | mbarrier | TMEM slot.
-__global__ void __launch_bounds__(kTcThreads) lmp_proj_tc_kernel(int n, int nS, int k, const __nv_bfloat16* Shi,
-                                                                 const __nv_bfloat16* Slo, int M, int m0, int mt,
-                                                                 const double* R, const int* active, float* W,
-                                                                 int kt, int* timeout) {
+// members) = A (modes x 128 rows) B (128 rows x members), K = the chunk's
+// rows.  A comes from the chunk's tile of the projection copies (modes >= k
+// zero); B is R of the tile's members, split on the fly, four core-matrix
+// rows in flight per thread (16-byte loads where R's rows allow them).
+__global__ void __launch_bounds__(kTcThreads) lmp_proj_tc_kernel(int n, int k, const __nv_bfloat16* Ph,
+                                                                 const __nv_bfloat16* Pl, int M, int mt,
+                                                                 const double* R, int vec, const int* active,
+                                                                 float* W, int kt, int* timeout) {
   extern __shared__ __align__(1024) unsigned char sm[];
   constexpr int KG = kRows / 8;  // 16 groups of 8 rows along K
-  unsigned char* Ahi = sm;
-  unsigned char* Alo = Ahi + 128 * kRows * 2;
-  unsigned char* Bhi = Alo + 128 * kRows * 2;
-  unsigned char* Blo = Bhi + (size_t)mt * kRows * 2;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + (size_t)mt * kRows * 2);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 1);
-  const int row0 = blockIdx.x * kRows;
+  constexpr uint32_t kA = 128u * kRows * 2u;
+  const TcSmem t = tc_smem(sm, kA, (uint32_t)mt * kRows * 2u);
+  const int chunk = blockIdx.x, m0 = blockIdx.y * mt;
+  const int row0 = chunk * kRows;
   const int rows = min(kRows, n - row0);
   const int ncols = tmem_cols(mt);
-  mbar_init(mbar);
-  // A: 128 modes x 16 groups of 8 rows, zero for modes >= kt (S rows k..kt-1
-  // are zero in memory); one 16-byte load and store per core-matrix row
-  for (int idx = threadIdx.x; idx < 128 * KG; idx += kTcThreads) {
-    const int mo = idx / KG, kb = idx - mo * KG;
-    uint4 h = make_uint4(0, 0, 0, 0), l = h;
-    if (mo < kt) {
-      const long long g = (long long)mo * nS + row0 + 8 * kb;  // nS: padded to whole chunks
-      h = *reinterpret_cast<const uint4*>(Shi + g);
-      l = *reinterpret_cast<const uint4*>(Slo + g);
-    }
-    *reinterpret_cast<uint4*>(Ahi + kmaj_off(mo, kb, KG)) = h;
-    *reinterpret_cast<uint4*>(Alo + kmaj_off(mo, kb, KG)) = l;
-  }
-  // B: mt members x 16 groups of 8 rows of R, split on the fly
-  for (int idx = threadIdx.x; idx < mt * KG; idx += kTcThreads) {
-    const int j = idx / KG, kb = idx - j * KG;
-    const int m = m0 + j;
-    double x[8];
-    const bool live = m < M && (active == nullptr || active[m] != 0);
+  start_a(t, Ph + (long long)chunk * 128 * kRows, Pl + (long long)chunk * 128 * kRows, kA);
+  const int items = mt * KG;
+  for (int base = threadIdx.x; base < items; base += 4 * kTcThreads) {
+    double x[4][8];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int i = 8 * kb + e;
-      x[e] = (live && i < rows) ? R[(long long)m * n + row0 + i] : 0.0;
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * kTcThreads;
+      const int j = idx / KG, kb = idx - j * KG;
+      const int m = m0 + j;
+      const int i0 = 8 * kb;
+      const bool live = idx < items && m < M && (active == nullptr || active[m] != 0);
+      const double* src = R + (long long)m * n + row0 + i0;
+      if (live && vec && i0 + 8 <= rows) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const double2 v = reinterpret_cast<const double2*>(src)[e];
+          x[u][2 * e] = v.x;
+          x[u][2 * e + 1] = v.y;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) x[u][e] = (live && i0 + e < rows) ? src[e] : 0.0;
+      }
     }
-    uint4 h, l;
-    split8<double>(x, &h, &l);
-    *reinterpret_cast<uint4*>(Bhi + kmaj_off(j, kb, KG)) = h;
-    *reinterpret_cast<uint4*>(Blo + kmaj_off(j, kb, KG)) = l;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * kTcThreads;
+      if (idx < items) {
+        const int j = idx / KG, kb = idx - j * KG;
+        uint4 h, l;
+        split8<double>(x[u], &h, &l);
+        *reinterpret_cast<uint4*>(t.Bhi + kmaj_off(j, kb, KG)) = h;
+        *reinterpret_cast<uint4*>(t.Blo + kmaj_off(j, kb, KG)) = l;
+      }
+    }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  const uint32_t tbase = tmem_alloc(slot, ncols);  // includes the block barrier
-  const bool ok = mma_split3(tbase, Ahi, Alo, Bhi, Blo, KG, mt, smem_u32(mbar), timeout);
+  const uint32_t tbase = tmem_alloc(t.slot, ncols);  // includes the block barrier
+  const bool ok = mma_split3(tbase, t.Ahi, t.Alo, t.Bhi, t.Blo, KG, mt, t.tma, t.mma, t.flag, timeout);
   if (ok) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mo = 32 * w + lane;  // TMEM lane = accumulator row = mode
-    for (int c0 = 0; c0 < mt; c0 += 16) {
+    // warp w reads TMEM lanes 32 (w % 4) ... (modes), column blocks of 16
+    // members alternating between the two warps of a lane quarter
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, q = w & 3;
+    const int mo = 32 * q + lane;
+    for (int c0 = 16 * (w >> 2); c0 < mt; c0 += 32) {
       float v[16];
-      tmem_ld16(tbase + ((uint32_t)(32 * w) << 16) + (uint32_t)c0, v);
+      tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
       if (mo < k) {
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
@@ -336,34 +404,23 @@ __global__ void __launch_bounds__(kTcThreads) lmp_proj_tc_kernel(int n, int nS, 
 }
 
 // Expansion Z[m][i] = R[m][i] + sum_c S[c][i] coef[c] W[m][c]: D (128 rows x
-// mt members) = A (128 rows x kt modes) B (kt modes x members).  Shared: A
-// hi, lo [128 x kt] | B hi, lo [mt x kt] | mbarrier | TMEM slot.
-__global__ void __launch_bounds__(kTcThreads) lmp_expand_tc_kernel(int n, int nS, int k,
-                                                                   const __nv_bfloat16* ShiT,
-                                                                   const __nv_bfloat16* SloT, const double* coef,
-                                                                   int M, int m0, int mt, const double* R,
-                                                                   double* Z, const int* active, const float* W,
-                                                                   int kt, int* timeout) {
+// mt members) = A (128 rows x kt modes) B (kt modes x members).  A comes from
+// the chunk's tile of the expansion copies; B is coef o w of the tile's
+// members, split on the fly.
+__global__ void __launch_bounds__(kTcThreads) lmp_expand_tc_kernel(int n, int k, const __nv_bfloat16* Eh,
+                                                                   const __nv_bfloat16* El, const double* coef,
+                                                                   int M, int mt, const double* R, double* Z,
+                                                                   const int* active, const float* W, int kt,
+                                                                   int* timeout) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int KG = kt / 8;
-  unsigned char* Ahi = sm;
-  unsigned char* Alo = Ahi + (size_t)128 * kt * 2;
-  unsigned char* Bhi = Alo + (size_t)128 * kt * 2;
-  unsigned char* Blo = Bhi + (size_t)mt * kt * 2;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(Blo + (size_t)mt * kt * 2);
-  uint32_t* slot = reinterpret_cast<uint32_t*>(mbar + 1);
-  const int row0 = blockIdx.x * kRows;
+  const uint32_t kA = 128u * (uint32_t)kt * 2u;
+  const TcSmem t = tc_smem(sm, kA, (uint32_t)mt * (uint32_t)kt * 2u);
+  const int chunk = blockIdx.x, m0 = blockIdx.y * mt;
+  const int row0 = chunk * kRows;
   const int rows = min(kRows, n - row0);
   const int ncols = tmem_cols(mt);
-  mbar_init(mbar);
-  // A: 128 rows x KG groups of 8 modes from the transposed copy S^T [nS][kt]
-  for (int idx = threadIdx.x; idx < 128 * KG; idx += kTcThreads) {
-    const int i = idx / KG, kb = idx - i * KG;
-    const long long g = (long long)(row0 + i) * kt + 8 * kb;  // rows >= n are zero in the padded copy
-    *reinterpret_cast<uint4*>(Ahi + kmaj_off(i, kb, KG)) = *reinterpret_cast<const uint4*>(ShiT + g);
-    *reinterpret_cast<uint4*>(Alo + kmaj_off(i, kb, KG)) = *reinterpret_cast<const uint4*>(SloT + g);
-  }
-  // B: mt members x KG groups of 8 modes of coef o w, split on the fly
+  start_a(t, Eh + (long long)chunk * 128 * kt, El + (long long)chunk * 128 * kt, kA);
   for (int idx = threadIdx.x; idx < mt * KG; idx += kTcThreads) {
     const int j = idx / KG, kb = idx - j * KG;
     const int m = m0 + j;
@@ -376,46 +433,61 @@ __global__ void __launch_bounds__(kTcThreads) lmp_expand_tc_kernel(int n, int nS
     }
     uint4 h, l;
     split8<float>(x, &h, &l);
-    *reinterpret_cast<uint4*>(Bhi + kmaj_off(j, kb, KG)) = h;
-    *reinterpret_cast<uint4*>(Blo + kmaj_off(j, kb, KG)) = l;
+    *reinterpret_cast<uint4*>(t.Bhi + kmaj_off(j, kb, KG)) = h;
+    *reinterpret_cast<uint4*>(t.Blo + kmaj_off(j, kb, KG)) = l;
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  const uint32_t tbase = tmem_alloc(slot, ncols);
-  const bool ok = mma_split3(tbase, Ahi, Alo, Bhi, Blo, KG, mt, smem_u32(mbar), timeout);
+  const uint32_t tbase = tmem_alloc(t.slot, ncols);
+  const bool ok = mma_split3(tbase, t.Ahi, t.Alo, t.Bhi, t.Blo, KG, mt, t.tma, t.mma, t.flag, timeout);
   if (ok) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int i = 32 * w + lane;  // TMEM lane = accumulator row = row of the chunk
-    for (int c0 = 0; c0 < mt; c0 += 16) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, q = w & 3;
+    const int i = 32 * q + lane;  // TMEM lane = accumulator row = row of the chunk
+    for (int c0 = 16 * (w >> 2); c0 < mt; c0 += 32) {
       float v[16];
-      tmem_ld16(tbase + ((uint32_t)(32 * w) << 16) + (uint32_t)c0, v);
+      tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
       if (i < rows) {
+        // all sixteen loads of R first, then the stores (Z may alias R: each
+        // element is read before this thread writes it)
+        double rv[16];
+        bool on[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const int m = m0 + c0 + e;
-          if (m < M && (active == nullptr || active[m] != 0)) {
-            const long long g = (long long)m * n + row0 + i;
-            Z[g] = R[g] + (double)v[e];
-          }
+          on[e] = m < M && (active == nullptr || active[m] != 0);
+          rv[e] = on[e] ? R[(long long)m * n + row0 + i] : 0.0;
         }
+#pragma unroll
+        for (int e = 0; e < 16; ++e)
+          if (on[e]) Z[(long long)(m0 + c0 + e) * n + row0 + i] = rv[e] + (double)v[e];
       }
     }
   }
   tmem_free(tbase, ncols);
 }
 
-__global__ void split_bf16_kernel(int n, int nS, int k, int kt, const double* S, __nv_bfloat16* Shi,
-                                  __nv_bfloat16* Slo, __nv_bfloat16* ShiT, __nv_bfloat16* SloT) {
-  const long long total = (long long)kt * nS;
+// The tiled BF16 copies of S [k x n] (column-major FP64): for every chunk of
+// 128 rows, the projection operand (128 modes x 128 rows, K-major along the
+// rows) and the expansion operand (128 rows x kt modes, K-major along the
+// modes), each as high and low parts in the core-matrix layout shared memory
+// takes; zero outside k x n.
+__global__ void split_bf16_kernel(int n, int nS, int k, int kt, const double* S, __nv_bfloat16* Ph,
+                                  __nv_bfloat16* Pl, __nv_bfloat16* Eh, __nv_bfloat16* El) {
+  const long long total = 128LL * nS;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
        e += (long long)gridDim.x * blockDim.x) {
-    const int c = (int)(e / nS), i = (int)(e - (long long)c * nS);
-    const double x = (c < k && i < n) ? S[(long long)c * n + i] : 0.0;
+    const int c = (int)(e / nS), gi = (int)(e - (long long)c * nS);
+    const double x = (c < k && gi < n) ? S[(long long)c * n + gi] : 0.0;
     const __nv_bfloat16 h = __float2bfloat16_rn((float)x);
     const __nv_bfloat16 l = __float2bfloat16_rn((float)(x - (double)__bfloat162float(h)));
-    Shi[e] = h;
-    Slo[e] = l;
-    ShiT[(long long)i * kt + c] = h;
-    SloT[(long long)i * kt + c] = l;
+    const int q = gi / kRows, r = gi - q * kRows;
+    const long long pe = (long long)q * 128 * kRows + (kmaj_off(c, r >> 3, kRows / 8) >> 1) + (r & 7);
+    Ph[pe] = h;
+    Pl[pe] = l;
+    if (c < kt) {
+      const long long ee = (long long)q * 128 * kt + (kmaj_off(r, c >> 3, kt >> 3) >> 1) + (c & 7);
+      Eh[ee] = h;
+      El[ee] = l;
+    }
   }
 }
 
@@ -429,6 +501,10 @@ cudaError_t set_smem(K kern, size_t smem) {
 
 int lmp_tc_kt(int k) { return ((k + 15) / 16) * 16; }
 int lmp_tc_ns(int n) { return ((n + kRows - 1) / kRows) * kRows; }
+size_t lmp_tc_elems(int n, int k) {
+  const size_t nS = (size_t)lmp_tc_ns(n);
+  return 2 * nS * 128 + 2 * nS * (size_t)lmp_tc_kt(k);
+}
 
 template <typename TS>
 cudaError_t lmp_apply_cc(int n, int k, const TS* S, const double* coef, int M, const double* R, double* Z,
@@ -451,44 +527,59 @@ cudaError_t lmp_apply_cc(int n, int k, const TS* S, const double* coef, int M, c
   return cudaGetLastError();
 }
 
-cudaError_t lmp_apply_tc(int n, int k, const __nv_bfloat16* Shi, const __nv_bfloat16* Slo,
-                         const __nv_bfloat16* ShiT, const __nv_bfloat16* SloT, const double* coef, int M,
-                         const double* R, double* Z, const int* active, float* W, int* timeout, cudaStream_t s) {
+cudaError_t lmp_apply_tc(int n, int k, const __nv_bfloat16* tiles, const double* coef, int M, const double* R,
+                         double* Z, const int* active, float* W, int* timeout, cudaStream_t s) {
   if (M <= 0 || n <= 0) return cudaSuccess;
   const int kt = lmp_tc_kt(k), nS = lmp_tc_ns(n);
   if (k <= 0 || kt > 128) return cudaErrorInvalidValue;
+  const __nv_bfloat16* Ph = tiles;
+  const __nv_bfloat16* Pl = Ph + (size_t)nS * 128;
+  const __nv_bfloat16* Eh = Pl + (size_t)nS * 128;
+  const __nv_bfloat16* El = Eh + (size_t)nS * kt;
   const int Mp = ((M + 15) / 16) * 16;
   cudaError_t e = cudaMemsetAsync(W, 0, (size_t)Mp * kt * sizeof(float), s);
   if (e != cudaSuccess) return e;
   const int chunks = nS / kRows;
-  // members in groups of at most 256 (the largest MMA N)
-  for (int m0 = 0; m0 < M; m0 += 256) {
-    const int mt = ((min(256, M - m0) + 15) / 16) * 16;
-    const size_t sm1 = (size_t)2 * 128 * kRows * 2 + (size_t)2 * mt * kRows * 2 + 16;
-    if ((e = set_smem(lmp_proj_tc_kernel, sm1)) != cudaSuccess) return e;
-    count_launch();
-    lmp_proj_tc_kernel<<<chunks, kTcThreads, sm1, s>>>(n, nS, k, Shi, Slo, M, m0, mt, R, active, W, kt, timeout);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // member tiles (multiples of 16, at most 256 members: the MMA's N): where
+  // the row chunks alone give fewer than two CTAs per SM, split the members
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess) {
+      (void)cudaGetLastError();
+      sms = 152;
+    }
   }
-  for (int m0 = 0; m0 < M; m0 += 256) {
-    const int mt = ((min(256, M - m0) + 15) / 16) * 16;
-    const size_t sm2 = (size_t)2 * 128 * kt * 2 + (size_t)2 * mt * kt * 2 + 16;
-    if ((e = set_smem(lmp_expand_tc_kernel, sm2)) != cudaSuccess) return e;
-    count_launch();
-    lmp_expand_tc_kernel<<<chunks, kTcThreads, sm2, s>>>(n, nS, k, ShiT, SloT, coef, M, m0, mt, R, Z, active, W,
-                                                         kt, timeout);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  int mtiles = (2 * sms + chunks - 1) / chunks;
+  mtiles = std::max(mtiles, (Mp + 255) / 256);
+  mtiles = std::min(mtiles, Mp / 16);
+  const int mt = (((Mp + mtiles - 1) / mtiles + 15) / 16) * 16;  // <= 256
+  mtiles = (Mp + mt - 1) / mt;
+  // 16-byte loads of R where every row starts on a 16-byte boundary
+  const int vec = ((reinterpret_cast<uintptr_t>(R) & 15u) == 0 && (n & 1) == 0) ? 1 : 0;
+  const size_t sm1 = (size_t)2 * 128 * kRows * 2 + (size_t)2 * mt * kRows * 2 + 32;
+  const size_t sm2 = (size_t)2 * 128 * kt * 2 + (size_t)2 * mt * kt * 2 + 32;
+  if ((e = set_smem(lmp_proj_tc_kernel, sm1)) != cudaSuccess) return e;
+  if ((e = set_smem(lmp_expand_tc_kernel, sm2)) != cudaSuccess) return e;
+  const dim3 grid((unsigned)chunks, (unsigned)mtiles);
+  count_launch(2);
+  lmp_proj_tc_kernel<<<grid, kTcThreads, sm1, s>>>(n, k, Ph, Pl, M, mt, R, vec, active, W, kt, timeout);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  lmp_expand_tc_kernel<<<grid, kTcThreads, sm2, s>>>(n, k, Eh, El, coef, M, mt, R, Z, active, W, kt, timeout);
+  return cudaGetLastError();
 }
 
-cudaError_t split_bf16(int n, int k, const double* S, __nv_bfloat16* Shi, __nv_bfloat16* Slo, __nv_bfloat16* ShiT,
-                       __nv_bfloat16* SloT, cudaStream_t s) {
+cudaError_t split_bf16(int n, int k, const double* S, __nv_bfloat16* tiles, cudaStream_t s) {
   const int kt = lmp_tc_kt(k), nS = lmp_tc_ns(n);
+  __nv_bfloat16* Ph = tiles;
+  __nv_bfloat16* Pl = Ph + (size_t)nS * 128;
+  __nv_bfloat16* Eh = Pl + (size_t)nS * 128;
+  __nv_bfloat16* El = Eh + (size_t)nS * kt;
   count_launch();
-  long long blocks = ((long long)kt * nS + 255) / 256;
+  long long blocks = (128LL * nS + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, nS, k, kt, S, Shi, Slo, ShiT, SloT);
+  split_bf16_kernel<<<(unsigned)blocks, 256, 0, s>>>(n, nS, k, kt, S, Ph, Pl, Eh, El);
   return cudaGetLastError();
 }
 
