@@ -2,18 +2,22 @@
 // member count, observation network and B) solved together.  Every sweep of
 // the group -- all members of all problems in the PCG, all sketch columns of
 // all problems -- runs as one launch per thread-block shape ("bucket"), with
-// per-problem tilings carried by the work items; the PCG vector updates and
-// the LMP apply run as batched launches over all (problem, member) items; one
-// PCG iteration of the whole group is captured once in a CUDA graph and
-// replayed until every member has converged.  Tilings (refresh period per
-// bucket) are chosen by the group autotuner.  Not in the paper: the paper
-// solves one EDA at a time.
+// per-problem tilings carried by the work items.  The PCG runs as one
+// persistent launch per bucket whose clusters take (problem, member) items
+// from a device-side queue, the buckets on concurrent streams, the whole
+// solve phase captured once in a CUDA graph and replayed; without the
+// persistent kernel (EDA_PERSIST=0), one PCG iteration of the whole group is
+// a captured graph replayed until every member has converged.  Tilings
+// (tile shape and refresh period per problem) are chosen by the group
+// autotuner.  Not in the paper: the paper solves one EDA at a time.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <string>
 #include <vector>
@@ -91,6 +95,10 @@ struct eda_group {
   float* sk_stash32 = nullptr;
   // captured PCG iteration
   cudaGraphExec_t gexec = nullptr;
+  // the persistent solve phase (memsets, every bucket's launch on its stream,
+  // the join) captured once and replayed while its signature holds
+  cudaGraphExec_t pexec = nullptr;
+  std::vector<long long> psig;
   int g_key = -1;
   double g_tol = -1.0;
   int g_maxit = -1;
@@ -456,11 +464,7 @@ int group_persist(eda_group* g, bool sweep64, bool use_lmp, double tol, int maxi
   if (!g->pacc) GCU(g, galloc(g, &g->pacc, (size_t)g->T));
   if (!g->Wp) GCU(g, galloc(g, &g->Wp, (size_t)2 * g->T * kmax));
   if (!g->queue) GCU(g, galloc(g, &g->queue, (size_t)64));
-  GCU(g, cudaMemsetAsync(g->pacc, 0, (size_t)g->T * sizeof(eda::PersistAcc), g->st));
-  GCU(g, cudaMemsetAsync(g->Wp, 0, (size_t)2 * g->T * kmax * sizeof(double), g->st));
-  GCU(g, cudaMemsetAsync(g->queue, 0, (size_t)64 * sizeof(int), g->st));
-  int qi = 0;
-  // every bucket on its own stream, forked from and joined back to the group's
+  // every bucket on its own stream, forked from and joined to the group's
   while (g->bstreams.size() < bs.size()) {
     cudaStream_t st2 = nullptr;
     cudaEvent_t ev2 = nullptr;
@@ -469,38 +473,33 @@ int group_persist(eda_group* g, bool sweep64, bool use_lmp, double tol, int maxi
     GCU(g, cudaEventCreateWithFlags(&ev2, cudaEventDisableTiming));
     g->bevents.push_back(ev2);
   }
-  GCU(g, cudaEventRecord(g->join, g->st));
-  // EDA_VERBOSE: each bucket's launch timed on its stream, printed at the end
-  const bool verbose = eda::env_int("EDA_VERBOSE", 0) != 0;
-  std::vector<cudaEvent_t> tev;
-  size_t bi = 0;
-  for (Bucket& b : bs) {
-    const size_t mine = bi++;
+  // the launches: one persistent PCG per non-empty bucket
+  struct Launch {
+    eda::PersistArgs<TS> pa;
+    SweepPlan pl;
+    size_t bucket;
+  };
+  std::vector<Launch> ls;
+  std::vector<long long> sig = {sweep64 ? 1 : 0, use_lmp ? 1 : 0, fixed, maxit, 0};
+  std::memcpy(&sig[4], &tol, sizeof(double));
+  int qi = 0;
+  for (size_t bi = 0; bi < bs.size(); ++bi) {
+    const Bucket& b = bs[bi];
     if (b.items.empty()) continue;
-    cudaStream_t bst = g->bstreams[mine];
-    GCU(g, cudaStreamWaitEvent(bst, g->join, 0));
-    if (verbose) {
-      cudaEvent_t e0 = nullptr, e1 = nullptr;
-      GCU(g, cudaEventCreate(&e0));
-      GCU(g, cudaEventCreate(&e1));
-      tev.push_back(e0);
-      tev.push_back(e1);
-      GCU(g, cudaEventRecord(e0, bst));
-    }
     // the between-sweep scratch must fit the bucket's shared memory
     int tmax = 0;
-    for (int pi : b.probs)
-      tmax = std::max(tmax, sweep64 ? g->prob64[pi].Ttile : g->prob32[pi].Ttile);
+    for (int pi : b.probs) tmax = std::max(tmax, sweep64 ? g->prob64[pi].Ttile : g->prob32[pi].Ttile);
     const size_t scratch = 32 * sizeof(double) + (size_t)(((kmax + 3) & ~3) + tmax) * sizeof(TS);
     if (scratch > b.smem || qi >= 64) return gfail(g, EDA_ERR_INVALID, "group: persistent PCG scratch does not fit");
-    SweepPlan pl{};
-    pl.CS = b.CS;
-    pl.C = sweep64 ? 4 : 8;
-    pl.A = b.A;
-    pl.E = b.A * pl.C;
-    pl.K = b.K;
-    pl.smem = b.smem;
-    eda::PersistArgs<TS> pa{};
+    Launch L{};
+    L.bucket = bi;
+    L.pl.CS = b.CS;
+    L.pl.C = sweep64 ? 4 : 8;
+    L.pl.A = b.A;
+    L.pl.E = b.A * L.pl.C;
+    L.pl.K = b.K;
+    L.pl.smem = b.smem;
+    eda::PersistArgs<TS>& pa = L.pa;
     pa.sw.w = b.wmax;
     if constexpr (sizeof(TS) == 8) {
       pa.sw.V = g->p;
@@ -538,25 +537,78 @@ int group_persist(eda_group* g, bool sweep64, bool use_lmp, double tol, int maxi
     pa.nitems = (int)b.items.size();
     pa.pprobs = g->probs;
     pa.queue = g->queue + qi++;
-    GCU(g, eda::launch_pcg_persist<TS>(pa, pl, bst));
-    if (verbose) GCU(g, cudaEventRecord(tev.back(), bst));
-    GCU(g, cudaEventRecord(g->bevents[mine], bst));
-    GCU(g, cudaStreamWaitEvent(g->st, g->bevents[mine], 0));
+    ls.push_back(L);
+    for (long long v : {(long long)reinterpret_cast<uintptr_t>(b.d_items), (long long)b.items.size(),
+                        (long long)b.CS, (long long)b.A, (long long)b.K, (long long)b.smem, (long long)bi})
+      sig.push_back(v);
+  }
+  // EDA_VERBOSE: each bucket's launch timed on its stream (no graph)
+  const bool verbose = eda::env_int("EDA_VERBOSE", 0) != 0;
+  const bool use_graph = eda::env_int("EDA_GROUP_GRAPH", 1) != 0 && !verbose;
+  std::vector<cudaEvent_t> tev;
+  auto record = [&]() -> int {
+    GCU(g, cudaMemsetAsync(g->pacc, 0, (size_t)g->T * sizeof(eda::PersistAcc), g->st));
+    GCU(g, cudaMemsetAsync(g->Wp, 0, (size_t)2 * g->T * kmax * sizeof(double), g->st));
+    GCU(g, cudaMemsetAsync(g->queue, 0, (size_t)64 * sizeof(int), g->st));
+    GCU(g, cudaEventRecord(g->join, g->st));
+    for (const Launch& L : ls) {
+      cudaStream_t bst = g->bstreams[L.bucket];
+      GCU(g, cudaStreamWaitEvent(bst, g->join, 0));
+      if (verbose) {
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        GCU(g, cudaEventCreate(&e0));
+        GCU(g, cudaEventCreate(&e1));
+        tev.push_back(e0);
+        tev.push_back(e1);
+        GCU(g, cudaEventRecord(e0, bst));
+      }
+      GCU(g, eda::launch_pcg_persist<TS>(L.pa, L.pl, bst));
+      if (verbose) GCU(g, cudaEventRecord(tev.back(), bst));
+      GCU(g, cudaEventRecord(g->bevents[L.bucket], bst));
+      GCU(g, cudaStreamWaitEvent(g->st, g->bevents[L.bucket], 0));
+    }
+    return EDA_OK;
+  };
+  if (use_graph) {
+    if (g->pexec == nullptr || g->psig != sig) {
+      if (g->pexec) {
+        cudaGraphExecDestroy(g->pexec);
+        g->pexec = nullptr;
+      }
+      // function attributes and grid sizes are settled outside the capture
+      for (const Launch& L : ls) {
+        int fit = 0;
+        GCU(g, eda::launch_pcg_persist<TS>(L.pa, L.pl, g->st, &fit));
+      }
+      cudaGraph_t graph;
+      GCU(g, cudaStreamBeginCapture(g->st, cudaStreamCaptureModeRelaxed));
+      const int rc = record();
+      cudaError_t ce = cudaStreamEndCapture(g->st, &graph);
+      if (rc) return rc;
+      GCU(g, ce);
+      ce = cudaGraphInstantiate(&g->pexec, graph, 0);
+      cudaGraphDestroy(graph);
+      GCU(g, ce);
+      g->psig = sig;
+    }
+    eda::count_launch((int)ls.size());
+    GCU(g, cudaGraphLaunch(g->pexec, g->st));
+  } else {
+    const int rc = record();
+    if (rc) return rc;
   }
   GCU(g, cudaStreamSynchronize(g->st));
   if (verbose) {
-    size_t j = 0;
-    for (const Bucket& b : bs) {
-      if (b.items.empty()) continue;
+    for (size_t j = 0; j < ls.size(); ++j) {
+      const Bucket& b = bs[ls[j].bucket];
       float ms = 0.f;
-      GCU(g, cudaEventElapsedTime(&ms, tev[j], tev[j + 1]));
+      GCU(g, cudaEventElapsedTime(&ms, tev[2 * j], tev[2 * j + 1]));
       long long work = 0;  // member x n x window of the bucket
       for (int pi : b.probs) work += (long long)g->hs[pi]->M * g->hs[pi]->n * g->hs[pi]->N;
       std::fprintf(stderr, "persistent group bucket CS=%d A=%d K=%d problems=%zu items=%zu work=%lld: %.1f ms\n",
                    b.CS, b.A, b.K, b.probs.size(), b.items.size(), work, ms);
-      cudaEventDestroy(tev[j]);
-      cudaEventDestroy(tev[j + 1]);
-      j += 2;
+      cudaEventDestroy(tev[2 * j]);
+      cudaEventDestroy(tev[2 * j + 1]);
     }
   }
   *it_io += maxit;
@@ -761,6 +813,7 @@ EDA_API int eda_group_destroy(eda_group* g) {
   if (!g) return EDA_OK;
   if (g->st) cudaStreamSynchronize(g->st);
   if (g->gexec) cudaGraphExecDestroy(g->gexec);
+  if (g->pexec) cudaGraphExecDestroy(g->pexec);
   for (void* p : g->allocs) cudaFree(p);
   for (int* t : g->tabs) cudaFree(t);
   for (Bucket& b : g->b64)
