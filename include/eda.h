@@ -331,7 +331,8 @@ EDA_API int eda_hvp(eda_handle* h, const int* member_of_col, int ncol, const dou
  * Autotuner of the sweep tiling: for the stored trajectories, times the
  * batched member Hessian-vector sweep (all L+1 members) for every tiling
  * that fits -- thread-block cluster size 1..8 (CTAs per vector) and halo
- * refresh period K in {2, 4, 8, 16} steps -- and keeps the fastest for all
+ * refresh period K in {2, 4, 8, 16} steps (FP64 sweeps also K = 1), run
+ * lengths, warp-tiled and multi-launch tilings -- and keeps the fastest for all
  * later sweeps of the handle.  which: bit 0 tunes the FP64 sweep, bit 1 the
  * FP32 sweep (EDA_MIXED only); 0 = the sweeps of the handle's precision.
  * *best_ms_out (may be NULL) = sum of the chosen tilings' mean times (ms).

@@ -746,7 +746,7 @@ int tune_tails(eda_handle* h, bool fp64, cudaEvent_t e0, cudaEvent_t e1) {
     for (int CS = main.CS + 1; CS <= 16 && rc == EDA_OK; ++CS)
       for (int K : {main.K / 2, main.K, main.K * 2}) {
         SweepPlan pl;
-        if (K < 2 || !eda::plan_sweep_exact(h->n, fp64 ? 8 : 4, h->w, CS, K, &pl, main.C)) continue;
+        if (K < 1 || !eda::plan_sweep_exact(h->n, fp64 ? 8 : 4, h->w, CS, K, &pl, main.C)) continue;
         if (pl.HL > h->n) continue;
         if ((fp64 ? persist_fits<double>(h, pl) : persist_fits<float>(h, pl)) < 1) continue;
         float ms = 0.f;
@@ -819,10 +819,14 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
         if (eda::plan_sweep_ml(h->n, fp64 ? 8 : 4, h->w, h->ckpt, A, &pl, true)) cands.push_back(pl);
       }
     }
+    // FP64 sweeps are bound by the FP64 pipe: a refresh every step (K = 1)
+    // trades a cluster barrier per step for a narrower halo of redundant work
+    std::vector<int> Kc(std::begin(Ks), std::end(Ks));
+    if (fp64) Kc.insert(Kc.begin(), 1);
     for (int C : {fp64 ? 4 : 8, fp64 ? 2 : 4})  // values per thread
       if (h->ckpt == 0)
       for (int CS = 1; CS <= 8; ++CS)
-        for (int K : Ks) {
+        for (int K : Kc) {
           SweepPlan pl;
           if (!eda::plan_sweep_exact(h->n, fp64 ? 8 : 4, h->w, CS, K, &pl, C)) continue;
           if (pl.HL > h->n && CS > 1) continue;
