@@ -70,6 +70,8 @@ def parse():
                          "range; prints one line")
     ap.add_argument("--profile-iters", type=int, default=20)
     ap.add_argument("--profile-members", type=int, default=9)
+    ap.add_argument("--profile-ckpt", type=int, default=0,
+                    help="scale profiling case: the trajectory checkpointed every this many steps (0: stored)")
     return ap.parse_args()
 
 
@@ -1129,14 +1131,14 @@ def run_profile_scale(args):
     # that the device holds under a gigabyte for the profiler
     os.environ["EDA_STAGE_STORE"] = "0"
     dev = torch.device("cuda", 0)
-    spec = replace(S.spec_scale(seed=0), n_members=args.profile_members, ckpt_every=0)
+    spec = replace(S.spec_scale(seed=0), n_members=args.profile_members, ckpt_every=args.profile_ckpt)
     spec = replace(spec, ell=min(spec.ell, spec.n_members - 1), k=min(spec.k, spec.n_members - 2))
     taps = P.bhalf_gaussian(spec.n, spec.length_scale, spec.sigma_b)
     dr = S.draws(spec)
     M, n, p = spec.n_members, spec.n, spec.p
     xb = torch.empty(M, n, dtype=torch.float64, device=dev)
     y = torch.empty(M, p, dtype=torch.float64, device=dev)
-    with P.Handle.from_spec(spec, taps, precision=P.EDA_FP64) as hg:
+    with P.Handle.from_spec(replace(spec, ckpt_every=0), taps, precision=P.EDA_FP64) as hg:
         hg.eda_twin(torch.tensor(spec.F + spec.spin_sigma * dr.eta_spin, device=dev), spec.spinup,
                     torch.tensor(dr.eta_b, device=dev), torch.tensor(dr.eta_o, device=dev), xb, y)
     cols = torch.arange(M, dtype=torch.int32, device=dev)
@@ -1157,8 +1159,8 @@ def run_profile_scale(args):
         torch.cuda.profiler.stop()
         plan = h.eda_sweep_plan(fp64=False)
     print(json.dumps({"profile_case": "scale", "workload": "l96_n65536_w96_m%d" % M, "members": M,
-                      "ms_product": ms, "ms_profiled": e0.elapsed_time(e1), "plan": plan,
-                      "algorithmic_bytes": M * 4 * n * (2 * spec.nsteps + 2)}))
+                      "ckpt_every": spec.ckpt_every, "ms_product": ms, "ms_profiled": e0.elapsed_time(e1),
+                      "plan": plan, "algorithmic_bytes_full_trajectory": M * 4 * n * (2 * spec.nsteps + 2)}))
     return 0
 
 
