@@ -18,7 +18,10 @@
 //    it while the CTA's threads split the member vectors into the other
 //    operand.  One thread issues the MMAs and commits to a second mbarrier;
 //    every wait is bounded; the epilogue reads the accumulator with
-//    tcgen05.ld.  The grid covers row chunks x member tiles.
+//    tcgen05.ld.  One CTA per SM and member tile works through every
+//    gridDim.x-th row chunk in a two-stage pipeline (the projections
+//    accumulate in tensor memory across the CTA's chunks; the expansion
+//    double-buffers its accumulator to overlap its MMAs and epilogue).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -105,6 +108,9 @@ __global__ void __launch_bounds__(kCcThreads) lmp_expand_cc_kernel(int n, int k,
 }
 
 // --------------------------------------------------------------- tensor cores
+// core-matrix rows of R each thread loads at once (a 96-member tile of a
+// chunk is 6 per thread: one round of loads in flight)
+constexpr int kStageRows = 6;
 constexpr int kTcThreads = 256;  // eight warps: warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31
 constexpr int kWaitLimit = 1 << 24;
 
@@ -178,15 +184,47 @@ __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
   return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
 }
 
-// 8 values -> the 16-byte core-matrix rows of their BF16 high and low parts.
+// FP64 -> FP32 by truncating the significand to 24 bits, in integer
+// arithmetic (GB300's FP64 pipe, which its conversions use, runs at 1/64 of
+// the FP32 rate).  Magnitudes below the FP32 normal range give a signed
+// zero, above it (and NaN) a signed infinity.  The split below keeps 16
+// significant bits, so truncation instead of rounding at bit 24 is of no
+// consequence.
+__device__ __forceinline__ float f64_to_f32_trunc(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned int hw = (unsigned int)(b >> 32), lw = (unsigned int)b;
+  const unsigned int sign = hw & 0x80000000u;
+  const int e = (int)((hw >> 20) & 0x7FFu) - 1023 + 127;
+  if (e <= 0) return __uint_as_float(sign);
+  if (e >= 255) return __uint_as_float(sign | 0x7F800000u);
+  return __uint_as_float(sign | ((unsigned int)e << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29));
+}
+
+// FP32 -> FP64, exactly, in integer arithmetic (FP32 subnormals give a
+// signed zero; infinities and NaN keep their class).
+__device__ __forceinline__ double f32_to_f64_exact(float f) {
+  const unsigned int u = __float_as_uint(f);
+  const unsigned int sign = u & 0x80000000u, e = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  if (e == 0u) return __hiloint2double((int)sign, 0);
+  const unsigned int ed = e == 0xFFu ? 0x7FFu : e - 127u + 1023u;
+  return __hiloint2double((int)(sign | (ed << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// 8 values -> the 16-byte core-matrix rows of their BF16 high and low parts:
+// hi = bf16(x), lo = bf16(x - hi), in FP32 arithmetic (x - hi is exact there:
+// x carries 24 significant bits and hi its leading 8).
 template <typename T>
 __device__ __forceinline__ void split8(const T (&x)[8], uint4* hi, uint4* lo) {
   __nv_bfloat16 h[8], l[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
-    const float xf = (float)x[e];
+    float xf;
+    if constexpr (sizeof(T) == 8)
+      xf = f64_to_f32_trunc(x[e]);
+    else
+      xf = x[e];
     h[e] = __float2bfloat16_rn(xf);
-    l[e] = __float2bfloat16_rn((float)(x[e] - (T)__bfloat162float(h[e])));
+    l[e] = __float2bfloat16_rn(xf - __bfloat162float(h[e]));
   }
   *hi = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
   *lo = make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
@@ -226,7 +264,7 @@ __device__ __forceinline__ void tmem_free(uint32_t base, int ncols) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
 }
 
-__device__ __forceinline__ int tmem_cols(int mt) { return mt <= 32 ? 32 : (mt <= 64 ? 64 : (mt <= 128 ? 128 : 256)); }
+__device__ __forceinline__ int tmem_cols(int c) { return c <= 32 ? 32 : (c <= 64 ? 64 : (c <= 128 ? 128 : (c <= 256 ? 256 : 512))); }
 
 // Bulk asynchronous copy of `bytes` (a multiple of 16, both addresses
 // 16-byte aligned) from global to this CTA's shared memory, its completion
@@ -241,156 +279,208 @@ __device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
-// Issues the kg/2 K-steps of hi.hi + hi.lo + lo.hi (thread 0) once the bulk
-// copies counted on `tma` have landed (bounded wait; tma == 0: nothing to
-// wait for), commits them to `mma`, and waits for it (every thread,
-// bounded).  If the copies' wait gives up, thread 0 arrives on `mma` itself
-// so that the CTA's wait ends.  Operands K-major with kg = K/8 core-matrix
-// groups along K (lbo 128, sbo kg * 128).  Returns false (uniformly) when a
-// wait gave up: *timeout is set, and the copies and MMAs in flight get a
-// second bounded wait before the caller frees tensor memory.
-__device__ __forceinline__ bool mma_split3(uint32_t dt, const unsigned char* Ahi, const unsigned char* Alo,
-                                           const unsigned char* Bhi, const unsigned char* Blo, int kg, int nd,
-                                           uint32_t tma, uint32_t mma, int* flag, int* timeout) {
-  if (threadIdx.x == 0) {
-    const bool have = tma == 0u || mbar_wait(tma, 0);
-    *flag = have ? 1 : 0;
-    if (have) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t id = idesc_bf16(nd);
-      const uint32_t sbo = (uint32_t)kg * 128u;
-      for (int ks = 0; ks < kg / 2; ++ks) {
-        const uint32_t o = (uint32_t)ks * 256u;  // two core matrices along K per step of 16
-        const uint64_t ah = kmajor_desc(smem_u32(Ahi) + o, 128u, sbo);
-        const uint64_t al = kmajor_desc(smem_u32(Alo) + o, 128u, sbo);
-        const uint64_t bh = kmajor_desc(smem_u32(Bhi) + o, 128u, sbo);
-        const uint64_t bl = kmajor_desc(smem_u32(Blo) + o, 128u, sbo);
-        mma_bf16(dt, ah, bh, id, ks > 0 ? 1u : 0u);
-        mma_bf16(dt, ah, bl, id, 1u);
-        mma_bf16(dt, al, bh, id, 1u);
-      }
-      mma_commit(mma);
-    } else {
-      mbar_arrive(mma);
-    }
-  }
-  __syncwarp();
-  bool ok = mbar_wait(mma, 0);
-  // uniform over the CTA (the epilogue's tcgen05.ld is warp-collective); the
-  // barrier also publishes thread 0's flag
-  ok = __syncthreads_and(ok ? 1 : 0) != 0;
-  if (!ok || *flag == 0) {
-    if (threadIdx.x == 0 && timeout != nullptr) atomicExch(timeout, 1);
-    if (tma != 0u) mbar_wait(tma, 0);
-    mbar_wait(mma, 0);
-    ok = false;
-  }
+// Thread 0: the kg/2 K-steps of hi.hi + hi.lo + lo.hi into the accumulator
+// at dt (accumulate: add to what it holds), committed to the mbarrier at
+// mma.  Operands K-major with kg = K/8 core-matrix groups along K (lbo 128,
+// sbo kg * 128).
+__device__ __forceinline__ void mma_split3_issue(uint32_t dt, const unsigned char* Ahi, const unsigned char* Alo,
+                                                 const unsigned char* Bhi, const unsigned char* Blo, int kg, int nd,
+                                                 bool accumulate, uint32_t mma) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  return ok;
+  const uint32_t id = idesc_bf16(nd);
+  const uint32_t sbo = (uint32_t)kg * 128u;
+  for (int ks = 0; ks < kg / 2; ++ks) {
+    const uint32_t o = (uint32_t)ks * 256u;  // two core matrices along K per step of 16
+    const uint64_t ah = kmajor_desc(smem_u32(Ahi) + o, 128u, sbo);
+    const uint64_t al = kmajor_desc(smem_u32(Alo) + o, 128u, sbo);
+    const uint64_t bh = kmajor_desc(smem_u32(Bhi) + o, 128u, sbo);
+    const uint64_t bl = kmajor_desc(smem_u32(Blo) + o, 128u, sbo);
+    mma_bf16(dt, ah, bh, id, (accumulate || ks > 0) ? 1u : 0u);
+    mma_bf16(dt, ah, bl, id, 1u);
+    mma_bf16(dt, al, bh, id, 1u);
+  }
+  mma_commit(mma);
 }
 
-// Shared-memory layout of both kernels: A hi | A lo (bulk-copied) | B hi |
-// B lo | two mbarriers (bulk copies, MMAs) | TMEM slot | flag.
-struct TcSmem {
+// Shared memory of the two kernels: two stages of A hi | A lo (bulk-copied
+// S tiles) and, for the projections, B hi | B lo (split R tiles); then the
+// mbarriers (bulk copies and MMAs of each stage), the TMEM slot and the
+// abort flag.
+struct TcStage {
   unsigned char *Ahi, *Alo, *Bhi, *Blo;
-  uint32_t tma, mma;
-  uint32_t* slot;
-  int* flag;
 };
 
-__device__ __forceinline__ TcSmem tc_smem(unsigned char* sm, uint32_t a_bytes, uint32_t b_bytes) {
-  TcSmem t;
-  t.Ahi = sm;
-  t.Alo = sm + a_bytes;
-  t.Bhi = t.Alo + a_bytes;
-  t.Blo = t.Bhi + b_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(t.Blo + b_bytes);
-  t.tma = smem_u32(bars);
-  t.mma = smem_u32(bars + 1);
-  t.slot = reinterpret_cast<uint32_t*>(bars + 2);
-  t.flag = reinterpret_cast<int*>(t.slot + 1);
-  return t;
+struct TcPipe {
+  TcStage st[2];
+  uint32_t tma[2], mma[2];
+  uint32_t* slot;
+  int* abort;
+};
+
+__device__ __forceinline__ TcPipe tc_pipe(unsigned char* sm, uint32_t a_bytes, uint32_t b_bytes) {
+  TcPipe p;
+  unsigned char* c = sm;
+  for (int s = 0; s < 2; ++s) {
+    p.st[s].Ahi = c;
+    p.st[s].Alo = c + a_bytes;
+    p.st[s].Bhi = c + 2 * a_bytes;
+    p.st[s].Blo = c + 2 * a_bytes + b_bytes;
+    c += 2 * (a_bytes + b_bytes);
+  }
+  uint64_t* bars = reinterpret_cast<uint64_t*>(c);
+  for (int s = 0; s < 2; ++s) {
+    p.tma[s] = smem_u32(bars + s);
+    p.mma[s] = smem_u32(bars + 2 + s);
+  }
+  p.slot = reinterpret_cast<uint32_t*>(bars + 4);
+  p.abort = reinterpret_cast<int*>(p.slot + 1);
+  return p;
 }
 
-// Thread 0: initialises both mbarriers and starts the bulk copies of the
-// two parts of A (a_bytes each) from hi and lo.
-__device__ __forceinline__ void start_a(const TcSmem& t, const __nv_bfloat16* hi, const __nv_bfloat16* lo,
-                                        uint32_t a_bytes) {
+// Thread 0: the four mbarriers (count 1) and the abort flag.
+__device__ __forceinline__ void tc_pipe_init(const TcPipe& p) {
   if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(t.tma) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(t.mma) : "memory");
+    for (int s = 0; s < 2; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(p.tma[s]) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(p.mma[s]) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(t.tma), "r"(2u * a_bytes)
-                 : "memory");
-    bulk_g2s(smem_u32(t.Ahi), hi, a_bytes, t.tma);
-    bulk_g2s(smem_u32(t.Alo), lo, a_bytes, t.tma);
+    *p.abort = 0;
   }
 }
 
-// Projections W[m][c] += sum_{i in chunk} S[c][i] R[m][i]: D (128 modes x mt
-// members) = A (modes x 128 rows) B (128 rows x members), K = the chunk's
-// rows.  A comes from the chunk's tile of the projection copies (modes >= k
-// zero); B is R of the tile's members, split on the fly, four core-matrix
-// rows in flight per thread (16-byte loads where R's rows allow them).
+// Thread 0: the bulk copies of the two parts of A (a_bytes each) into stage s.
+__device__ __forceinline__ void tc_load_a(const TcPipe& p, int s, const __nv_bfloat16* hi, const __nv_bfloat16* lo,
+                                          uint32_t a_bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(p.tma[s]), "r"(2u * a_bytes)
+               : "memory");
+  bulk_g2s(smem_u32(p.st[s].Ahi), hi, a_bytes, p.tma[s]);
+  bulk_g2s(smem_u32(p.st[s].Alo), lo, a_bytes, p.tma[s]);
+}
+
+// Thread 0, once stage s's bulk copies (use u of the stage) have landed:
+// the MMAs of the stage into dt, committed to the stage's MMA barrier.  If
+// the wait gives up (or an earlier one did), the CTA is marked aborted and
+// thread 0 arrives on the barrier itself, so that every later wait on it
+// still ends.
+__device__ __forceinline__ void tc_mma_stage(const TcPipe& p, int s, int u, uint32_t dt, int kg, int nd,
+                                             bool accumulate) {
+  if (*p.abort == 0 && !mbar_wait(p.tma[s], (uint32_t)(u & 1))) *p.abort = 1;
+  if (*p.abort == 0)
+    mma_split3_issue(dt, p.st[s].Ahi, p.st[s].Alo, p.st[s].Bhi, p.st[s].Blo, kg, nd, accumulate, p.mma[s]);
+  else
+    mbar_arrive(p.mma[s]);
+}
+
+// Every thread: waits (bounded) for use u of stage s's MMA barrier; true in
+// every thread when it completed in all of them and nothing aborted.  A
+// barrier completes in use order, so parity u & 1 names use u.
+__device__ __forceinline__ bool tc_wait_mma(const TcPipe& p, int s, int u) {
+  const bool ok = mbar_wait(p.mma[s], (uint32_t)(u & 1));
+  return __syncthreads_and((ok && *p.abort == 0) ? 1 : 0) != 0;
+}
+
+// After a wait gave up: *timeout set, and every stage's outstanding bulk
+// copies and MMAs given a second bounded wait before tensor memory is freed.
+__device__ __forceinline__ void tc_drain(const TcPipe& p, int uses0, int uses1, int* timeout) {
+  if (threadIdx.x == 0 && timeout != nullptr) atomicExch(timeout, 1);
+  const int uses[2] = {uses0, uses1};
+  for (int s = 0; s < 2; ++s)
+    if (uses[s] > 0) {
+      mbar_wait(p.tma[s], (uint32_t)((uses[s] - 1) & 1));
+      mbar_wait(p.mma[s], (uint32_t)((uses[s] - 1) & 1));
+    }
+  __syncthreads();
+}
+
+// Projections W[m][c] += sum_i S[c][i] R[m][i] over the CTA's row chunks q =
+// blockIdx.x, blockIdx.x + gridDim.x, ...: D (128 modes x mt members) =
+// A (modes x rows) B (rows x members) accumulates in tensor memory across
+// the chunks (K = 128 rows each) and is added into W once per CTA.  A is the
+// chunk's tile of the projection copies (modes >= k zero), bulk-copied; B is
+// R of the tile's members, split on the fly, six core-matrix rows in flight
+// per thread (16-byte loads where R's rows allow them).  Two stages: chunk
+// i + 1 is staged while the MMAs of chunk i run.
 __global__ void __launch_bounds__(kTcThreads) lmp_proj_tc_kernel(int n, int k, const __nv_bfloat16* Ph,
-                                                                 const __nv_bfloat16* Pl, int M, int mt,
+                                                                 const __nv_bfloat16* Pl, int M, int mt, int chunks,
                                                                  const double* R, int vec, const int* active,
                                                                  float* W, int kt, int* timeout) {
   extern __shared__ __align__(1024) unsigned char sm[];
   constexpr int KG = kRows / 8;  // 16 groups of 8 rows along K
   constexpr uint32_t kA = 128u * kRows * 2u;
-  const TcSmem t = tc_smem(sm, kA, (uint32_t)mt * kRows * 2u);
-  const int chunk = blockIdx.x, m0 = blockIdx.y * mt;
-  const int row0 = chunk * kRows;
-  const int rows = min(kRows, n - row0);
+  const TcPipe p = tc_pipe(sm, kA, (uint32_t)mt * kRows * 2u);
+  const int m0 = blockIdx.y * mt;
+  const int nq = (chunks - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
   const int ncols = tmem_cols(mt);
-  start_a(t, Ph + (long long)chunk * 128 * kRows, Pl + (long long)chunk * 128 * kRows, kA);
+  tc_pipe_init(p);
+  const uint32_t tbase = tmem_alloc(p.slot, ncols);  // includes the block barrier
   const int items = mt * KG;
-  for (int base = threadIdx.x; base < items; base += 4 * kTcThreads) {
-    double x[4][8];
+  bool ok = true;
+  int uses[2] = {0, 0};
+  for (int i = 0; i < nq && ok; ++i) {
+    const int s = i & 1;
+    const int q = (int)blockIdx.x + i * (int)gridDim.x;
+    const int row0 = q * kRows;
+    const int rows = min(kRows, n - row0);
+    // the stage's buffers were read by the MMAs of chunk i - 2
+    if (i >= 2) ok = tc_wait_mma(p, s, uses[s] - 1);
+    if (!ok) break;
+    if (threadIdx.x == 0)
+      tc_load_a(p, s, Ph + (long long)q * 128 * kRows, Pl + (long long)q * 128 * kRows, kA);
+    for (int base = threadIdx.x; base < items; base += kStageRows * kTcThreads) {
+      double x[kStageRows][8];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int idx = base + u * kTcThreads;
-      const int j = idx / KG, kb = idx - j * KG;
-      const int m = m0 + j;
-      const int i0 = 8 * kb;
-      const bool live = idx < items && m < M && (active == nullptr || active[m] != 0);
-      const double* src = R + (long long)m * n + row0 + i0;
-      if (live && vec && i0 + 8 <= rows) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const double2 v = reinterpret_cast<const double2*>(src)[e];
-          x[u][2 * e] = v.x;
-          x[u][2 * e + 1] = v.y;
-        }
-      } else {
-#pragma unroll
-        for (int e = 0; e < 8; ++e) x[u][e] = (live && i0 + e < rows) ? src[e] : 0.0;
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int idx = base + u * kTcThreads;
-      if (idx < items) {
+      for (int u = 0; u < kStageRows; ++u) {
+        const int idx = base + u * kTcThreads;
         const int j = idx / KG, kb = idx - j * KG;
-        uint4 h, l;
-        split8<double>(x[u], &h, &l);
-        *reinterpret_cast<uint4*>(t.Bhi + kmaj_off(j, kb, KG)) = h;
-        *reinterpret_cast<uint4*>(t.Blo + kmaj_off(j, kb, KG)) = l;
+        const int m = m0 + j;
+        const int i0 = 8 * kb;
+        const bool live = idx < items && m < M && (active == nullptr || active[m] != 0);
+        const double* src = R + (long long)m * n + row0 + i0;
+        if (live && vec && i0 + 8 <= rows) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const double2 v = reinterpret_cast<const double2*>(src)[e];
+            x[u][2 * e] = v.x;
+            x[u][2 * e + 1] = v.y;
+          }
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) x[u][e] = (live && i0 + e < rows) ? src[e] : 0.0;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kStageRows; ++u) {
+        const int idx = base + u * kTcThreads;
+        if (idx < items) {
+          const int j = idx / KG, kb = idx - j * KG;
+          uint4 h, l;
+          split8<double>(x[u], &h, &l);
+          *reinterpret_cast<uint4*>(p.st[s].Bhi + kmaj_off(j, kb, KG)) = h;
+          *reinterpret_cast<uint4*>(p.st[s].Blo + kmaj_off(j, kb, KG)) = l;
+        }
       }
     }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) tc_mma_stage(p, s, uses[s], tbase, KG, mt, i > 0);
+    ++uses[s];
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  const uint32_t tbase = tmem_alloc(t.slot, ncols);  // includes the block barrier
-  const bool ok = mma_split3(tbase, t.Ahi, t.Alo, t.Bhi, t.Blo, KG, mt, t.tma, t.mma, t.flag, timeout);
+  // the last commit follows every earlier MMA of this thread
+  if (ok) {
+    const int sl = (nq - 1) & 1;
+    ok = tc_wait_mma(p, sl, uses[sl] - 1);
+  }
+  if (!ok) tc_drain(p, uses[0], uses[1], timeout);
   if (ok) {
     // warp w reads TMEM lanes 32 (w % 4) ... (modes), column blocks of 16
     // members alternating between the two warps of a lane quarter
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, q = w & 3;
-    const int mo = 32 * q + lane;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, qd = w & 3;
+    const int mo = 32 * qd + lane;
     for (int c0 = 16 * (w >> 2); c0 < mt; c0 += 32) {
       float v[16];
-      tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
+      tmem_ld16(tbase + ((uint32_t)(32 * qd) << 16) + (uint32_t)c0, v);
       if (mo < k) {
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
@@ -403,24 +493,37 @@ __global__ void __launch_bounds__(kTcThreads) lmp_proj_tc_kernel(int n, int k, c
   tmem_free(tbase, ncols);
 }
 
-// Expansion Z[m][i] = R[m][i] + sum_c S[c][i] coef[c] W[m][c]: D (128 rows x
-// mt members) = A (128 rows x kt modes) B (kt modes x members).  A comes from
-// the chunk's tile of the expansion copies; B is coef o w of the tile's
-// members, split on the fly.
+// Expansion Z[m][i] = R[m][i] + sum_c S[c][i] coef[c] W[m][c] over the CTA's
+// row chunks: D (128 rows x mt members) = A (128 rows x kt modes) B (kt
+// modes x members).  B, coef o w of the tile's members split on the fly, is
+// the same for every chunk and staged once; A, the chunk's tile of the
+// expansion copies, is bulk-copied two chunks ahead into two stages, and D
+// is double-buffered in tensor memory, so the copy of chunk i + 2 and the
+// MMAs of chunk i + 1 run while the epilogue of chunk i reads R and writes Z.
 __global__ void __launch_bounds__(kTcThreads) lmp_expand_tc_kernel(int n, int k, const __nv_bfloat16* Eh,
                                                                    const __nv_bfloat16* El, const double* coef,
-                                                                   int M, int mt, const double* R, double* Z,
-                                                                   const int* active, const float* W, int kt,
-                                                                   int* timeout) {
+                                                                   int M, int mt, int chunks, const double* R,
+                                                                   double* Z, const int* active, const float* W,
+                                                                   int kt, int* timeout) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const int KG = kt / 8;
   const uint32_t kA = 128u * (uint32_t)kt * 2u;
-  const TcSmem t = tc_smem(sm, kA, (uint32_t)mt * (uint32_t)kt * 2u);
-  const int chunk = blockIdx.x, m0 = blockIdx.y * mt;
-  const int row0 = chunk * kRows;
-  const int rows = min(kRows, n - row0);
-  const int ncols = tmem_cols(mt);
-  start_a(t, Eh + (long long)chunk * 128 * kt, El + (long long)chunk * 128 * kt, kA);
+  const uint32_t kB = (uint32_t)mt * (uint32_t)kt * 2u;
+  // one B for both stages: stage 1 reads stage 0's B buffers
+  TcPipe p = tc_pipe(sm, kA, kB);
+  p.st[1].Bhi = p.st[0].Bhi;
+  p.st[1].Blo = p.st[0].Blo;
+  const int m0 = blockIdx.y * mt;
+  const int nq = (chunks - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int ncols = tmem_cols(2 * mt);  // two accumulators of mt columns
+  auto chunk_of = [&](int i) { return (int)blockIdx.x + i * (int)gridDim.x; };
+  int uses[2] = {0, 0};  // bulk copies (and MMAs) started per stage
+  tc_pipe_init(p);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2 && i < nq; ++i)
+      tc_load_a(p, i, Eh + (long long)chunk_of(i) * 128 * kt, El + (long long)chunk_of(i) * 128 * kt, kA);
+  }
+  for (int i = 0; i < 2 && i < nq; ++i) ++uses[i];
   for (int idx = threadIdx.x; idx < mt * KG; idx += kTcThreads) {
     const int j = idx / KG, kb = idx - j * KG;
     const int m = m0 + j;
@@ -429,39 +532,72 @@ __global__ void __launch_bounds__(kTcThreads) lmp_expand_tc_kernel(int n, int k,
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int c = 8 * kb + e;
-      x[e] = (live && c < k) ? (float)(coef[c] * (double)W[(long long)m * kt + c]) : 0.0f;
+      x[e] = (live && c < k) ? f64_to_f32_trunc(coef[c]) * W[(long long)m * kt + c] : 0.0f;
     }
     uint4 h, l;
     split8<float>(x, &h, &l);
-    *reinterpret_cast<uint4*>(t.Bhi + kmaj_off(j, kb, KG)) = h;
-    *reinterpret_cast<uint4*>(t.Blo + kmaj_off(j, kb, KG)) = l;
+    *reinterpret_cast<uint4*>(p.st[0].Bhi + kmaj_off(j, kb, KG)) = h;
+    *reinterpret_cast<uint4*>(p.st[0].Blo + kmaj_off(j, kb, KG)) = l;
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  const uint32_t tbase = tmem_alloc(t.slot, ncols);
-  const bool ok = mma_split3(tbase, t.Ahi, t.Alo, t.Bhi, t.Blo, KG, mt, t.tma, t.mma, t.flag, timeout);
-  if (ok) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, q = w & 3;
-    const int i = 32 * q + lane;  // TMEM lane = accumulator row = row of the chunk
-    for (int c0 = 16 * (w >> 2); c0 < mt; c0 += 32) {
-      float v[16];
-      tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
-      if (i < rows) {
-        // all sixteen loads of R first, then the stores (Z may alias R: each
-        // element is read before this thread writes it)
-        double rv[16];
-        bool on[16];
+  const uint32_t tbase = tmem_alloc(p.slot, ncols);  // includes the block barrier
+  if (threadIdx.x == 0) tc_mma_stage(p, 0, 0, tbase, KG, mt, false);
+  bool ok = true;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, qd = w & 3;
+  const int il = 32 * qd + lane;  // TMEM lane = accumulator row = row of the chunk
+  for (int i = 0; i < nq && ok; ++i) {
+    const int s = i & 1, s1 = s ^ 1;
+    // chunk i's MMAs (use i / 2 of stage s) are done: its accumulator is
+    // ready and stage s's A is free
+    ok = tc_wait_mma(p, s, i >> 1);
+    if (!ok) break;
+    if (threadIdx.x == 0) {
+      if (i + 2 < nq)
+        tc_load_a(p, s, Eh + (long long)chunk_of(i + 2) * 128 * kt, El + (long long)chunk_of(i + 2) * 128 * kt,
+                  kA);
+      // chunk i + 1 into the other accumulator (read by the epilogue of
+      // chunk i - 1, which ended at the last block barrier)
+      if (i + 1 < nq) tc_mma_stage(p, s1, (i + 1) >> 1, tbase + (uint32_t)(s1 * mt), KG, mt, false);
+    }
+    if (i + 2 < nq) ++uses[s];
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int row0 = chunk_of(i) * kRows;
+    const int rows = min(kRows, n - row0);
+    // the warp's column groups of 16 (groups w / 4, w / 4 + 2, w / 4 + 4 of
+    // the at most six): every load of R first, then the stores (Z may alias
+    // R: each element is read before this thread writes it)
+    float v[3][16];
+    double rv[3][16];
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-          const int m = m0 + c0 + e;
-          on[e] = m < M && (active == nullptr || active[m] != 0);
-          rv[e] = on[e] ? R[(long long)m * n + row0 + i] : 0.0;
-        }
+    for (int gg = 0; gg < 3; ++gg) {
+      const int c0 = 16 * ((w >> 2) + 2 * gg);
+      if (c0 < mt) tmem_ld16(tbase + ((uint32_t)(32 * qd) << 16) + (uint32_t)(s * mt + c0), v[gg]);
+    }
 #pragma unroll
-        for (int e = 0; e < 16; ++e)
-          if (on[e]) Z[(long long)(m0 + c0 + e) * n + row0 + i] = rv[e] + (double)v[e];
+    for (int gg = 0; gg < 3; ++gg) {
+      const int c0 = 16 * ((w >> 2) + 2 * gg);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int m = m0 + c0 + e;
+        const bool on = c0 < mt && il < rows && m < M && (active == nullptr || active[m] != 0);
+        rv[gg][e] = on ? R[(long long)m * n + row0 + il] : 0.0;
       }
     }
+#pragma unroll
+    for (int gg = 0; gg < 3; ++gg) {
+      const int c0 = 16 * ((w >> 2) + 2 * gg);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int m = m0 + c0 + e;
+        if (c0 < mt && il < rows && m < M && (active == nullptr || active[m] != 0))
+          Z[(long long)m * n + row0 + il] = rv[gg][e] + f32_to_f64_exact(v[gg][e]);
+      }
+    }
+    // accumulator s is read: the MMAs of chunk i + 2 may write it
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
   }
+  if (!ok) tc_drain(p, uses[0], uses[1], timeout);
   tmem_free(tbase, ncols);
 }
 
@@ -540,8 +676,6 @@ cudaError_t lmp_apply_tc(int n, int k, const __nv_bfloat16* tiles, const double*
   cudaError_t e = cudaMemsetAsync(W, 0, (size_t)Mp * kt * sizeof(float), s);
   if (e != cudaSuccess) return e;
   const int chunks = nS / kRows;
-  // member tiles (multiples of 16, at most 256 members: the MMA's N): where
-  // the row chunks alone give fewer than two CTAs per SM, split the members
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
@@ -551,22 +685,28 @@ cudaError_t lmp_apply_tc(int n, int k, const __nv_bfloat16* tiles, const double*
       sms = 152;
     }
   }
-  int mtiles = (2 * sms + chunks - 1) / chunks;
-  mtiles = std::max(mtiles, (Mp + 255) / 256);
-  mtiles = std::min(mtiles, Mp / 16);
-  const int mt = (((Mp + mtiles - 1) / mtiles + 15) / 16) * 16;  // <= 256
+  // member tiles: multiples of 16 and at most 96 members (two pipeline
+  // stages of the projection's operands then fit shared memory); more tiles
+  // where the row chunks alone would leave SMs idle
+  int mtiles = std::max((Mp + 95) / 96, std::min(Mp / 16, (sms + chunks - 1) / chunks));
+  const int mt = (((Mp + mtiles - 1) / mtiles + 15) / 16) * 16;
   mtiles = (Mp + mt - 1) / mt;
+  // one CTA per SM (the stages take most of its shared memory), each
+  // working through every gridDim.x-th row chunk
+  const int nblk = std::max(1, std::min(chunks, sms / mtiles));
   // 16-byte loads of R where every row starts on a 16-byte boundary
   const int vec = ((reinterpret_cast<uintptr_t>(R) & 15u) == 0 && (n & 1) == 0) ? 1 : 0;
-  const size_t sm1 = (size_t)2 * 128 * kRows * 2 + (size_t)2 * mt * kRows * 2 + 32;
-  const size_t sm2 = (size_t)2 * 128 * kt * 2 + (size_t)2 * mt * kt * 2 + 32;
+  const size_t aP = (size_t)128 * kRows * 2, bP = (size_t)mt * kRows * 2;
+  const size_t aE = (size_t)128 * kt * 2, bE = (size_t)mt * kt * 2;
+  const size_t sm1 = 4 * (aP + bP) + 48, sm2 = 4 * (aE + bE) + 48;
   if ((e = set_smem(lmp_proj_tc_kernel, sm1)) != cudaSuccess) return e;
   if ((e = set_smem(lmp_expand_tc_kernel, sm2)) != cudaSuccess) return e;
-  const dim3 grid((unsigned)chunks, (unsigned)mtiles);
+  const dim3 grid((unsigned)nblk, (unsigned)mtiles);
   count_launch(2);
-  lmp_proj_tc_kernel<<<grid, kTcThreads, sm1, s>>>(n, k, Ph, Pl, M, mt, R, vec, active, W, kt, timeout);
+  lmp_proj_tc_kernel<<<grid, kTcThreads, sm1, s>>>(n, k, Ph, Pl, M, mt, chunks, R, vec, active, W, kt, timeout);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  lmp_expand_tc_kernel<<<grid, kTcThreads, sm2, s>>>(n, k, Eh, El, coef, M, mt, R, Z, active, W, kt, timeout);
+  lmp_expand_tc_kernel<<<grid, kTcThreads, sm2, s>>>(n, k, Eh, El, coef, M, mt, chunks, R, Z, active, W, kt,
+                                                     timeout);
   return cudaGetLastError();
 }
 
