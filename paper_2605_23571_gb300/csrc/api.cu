@@ -823,7 +823,8 @@ EDA_API int eda_autotune(eda_handle* h, int which, double* best_ms_out) {
     // trades a cluster barrier per step for a narrower halo of redundant work
     std::vector<int> Kc(std::begin(Ks), std::end(Ks));
     if (fp64) Kc.insert(Kc.begin(), 1);
-    for (int C : {fp64 ? 4 : 8, fp64 ? 2 : 4})  // values per thread
+    std::vector<int> Cc = fp64 ? std::vector<int>{4, 2} : std::vector<int>{8, 4, 2};  // values per thread
+    for (int C : Cc)
       if (h->ckpt == 0)
       for (int CS = 1; CS <= 8; ++CS)
         for (int K : Kc) {

@@ -181,8 +181,8 @@ bool plan_sweep_warp(int n, int elem_bytes, int w, int CS, int K, int C, SweepPl
 void warp_obs_table(const SweepPlan& p, int n, int nos, const int* obs_ptr, const int* obs_idx, int* tab);
 
 // The plan with exactly cluster size CS, refresh period K and C values per
-// thread (C = 0: 4 for FP64, 8 for FP32; else FP64 2 or 4, FP32 4 or 8), if
-// it fits.
+// thread (C = 0: 4 for FP64, 8 for FP32; else FP64 2 or 4, FP32 2, 4 or 8),
+// if it fits.
 bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* out, int C = 0);
 
 // Per-CTA observation ranges of a plan: for CTA r and observation step j,

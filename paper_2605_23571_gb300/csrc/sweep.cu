@@ -160,12 +160,16 @@ __device__ __forceinline__ void read_halo(T (&v)[C], T* mir, const Geo& g) {
 // not fit).
 __device__ __forceinline__ const int* obs_ranges(const int* tabp, int oj) { return tabp + oj * 8; }
 
-// Own run <-> mirror, with 16-byte shared-memory accesses (C * sizeof(T) is a
-// multiple of 16 for every instantiated tile).
+// Own run <-> mirror, with 16-byte shared-memory accesses (8-byte ones for a
+// run of two FP32 values).
 template <typename T, int C>
 __device__ __forceinline__ void write_mirror(T* mir, const Geo& g, const T (&v)[C]) {
-  static_assert((C * sizeof(T)) % 16 == 0, "run must be a whole number of 16-byte chunks");
-  if constexpr (sizeof(T) == 4) {
+  static_assert((C * sizeof(T)) % 8 == 0, "run must be a whole number of 8-byte chunks");
+  if constexpr (sizeof(T) == 4 && C % 4 != 0) {
+    float2* p = reinterpret_cast<float2*>(mir + g.l0);
+#pragma unroll
+    for (int q = 0; q < C / 2; ++q) p[q] = make_float2(v[2 * q], v[2 * q + 1]);
+  } else if constexpr (sizeof(T) == 4) {
     float4* p = reinterpret_cast<float4*>(mir + g.l0);
 #pragma unroll
     for (int q = 0; q < C / 4; ++q) p[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
@@ -186,7 +190,15 @@ __device__ __forceinline__ void write_mirror_zero(T* mir, const Geo& g) {
 
 template <typename T, int C>
 __device__ __forceinline__ void add_mirror(const T* mir, const Geo& g, T (&v)[C]) {
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4 && C % 4 != 0) {
+    const float2* p = reinterpret_cast<const float2*>(mir + g.l0);
+#pragma unroll
+    for (int q = 0; q < C / 2; ++q) {
+      const float2 u = p[q];
+      v[2 * q] += u.x;
+      v[2 * q + 1] += u.y;
+    }
+  } else if constexpr (sizeof(T) == 4) {
     const float4* p = reinterpret_cast<const float4*>(mir + g.l0);
 #pragma unroll
     for (int q = 0; q < C / 4; ++q) {
@@ -424,7 +436,15 @@ __device__ __forceinline__ void inject_use(const SweepArgs<T>& a, const Geo& g, 
 template <typename T, int C>
 __device__ __forceinline__ void load_run(const T* row, const int (&gi)[C], bool vec_ok, T (&out)[C]) {
   if (vec_ok) {
-    if constexpr (sizeof(T) == 4) {
+    if constexpr (sizeof(T) == 4 && C % 4 != 0) {
+      const float2* p = reinterpret_cast<const float2*>(row + gi[0]);
+#pragma unroll
+      for (int v = 0; v < C / 2; ++v) {
+        const float2 q = __ldg(p + v);
+        out[2 * v] = q.x;
+        out[2 * v + 1] = q.y;
+      }
+    } else if constexpr (sizeof(T) == 4) {
       const float4* p = reinterpret_cast<const float4*>(row + gi[0]);
 #pragma unroll
       for (int v = 0; v < C / 4; ++v) {
@@ -588,14 +608,15 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T>& a0, const int col
     }
   }
 
-  // global indices of this thread's run, and whether 16-byte loads apply
+  // global indices of this thread's run, and whether vector loads apply (16
+  // bytes, or 8 for a run of two FP32 values)
   int gi[C];
   {
     const int g0 = (g.gbase + g.l0) % g.n;
 #pragma unroll
     for (int c = 0; c < C; ++c) gi[c] = (g0 + c) % g.n;
   }
-  constexpr int kVec = 16 / (int)sizeof(T);
+  constexpr int kVec = (C * (int)sizeof(T) >= 16) ? 16 / (int)sizeof(T) : C;
   const bool vec_ok = (g.n % kVec == 0) && (gi[0] % kVec == 0) && (gi[0] + C <= g.n);
 
   const T F = a.F, h = a.dt;
@@ -622,7 +643,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T>& a0, const int col
       const T* x0row = (f0 == 0)        ? a.x0 + voff
                        : (tout != nullptr) ? tout + (long long)(a.ckpt ? f0 / a.ckpt : f0) * a.n
                                            : a.st_in + (long long)col * a.n;
-      const bool x0_vec = vec_ok && ((reinterpret_cast<unsigned long long>(x0row) & 15ull) == 0);
+      const bool x0_vec =
+          vec_ok && ((reinterpret_cast<unsigned long long>(x0row) & (unsigned long long)(kVec * sizeof(T) - 1)) == 0);
       load_run<T, C>(x0row, gi, x0_vec, x);
     }
     // owned positions of a run -> row of a stage array
@@ -2182,8 +2204,8 @@ size_t sweep_smem_bytes(int A, int C, int w, int elem_bytes) {
 
 bool plan_sweep_exact(int n, int elem_bytes, int w, int CS, int K, SweepPlan* out, int C) {
   if (C == 0) C = (elem_bytes == 8) ? 4 : 8;
-  // instantiated runs: FP64 2 or 4 values per thread, FP32 4 or 8
-  if (elem_bytes == 8 ? (C != 2 && C != 4) : (C != 4 && C != 8)) return false;
+  // instantiated runs: FP64 2 or 4 values per thread, FP32 2, 4 or 8
+  if (elem_bytes == 8 ? (C != 2 && C != 4) : (C != 2 && C != 4 && C != 8)) return false;
   out->ml = 0;
   out->warp = 0;
   if (CS < 1 || CS > 16 || K < 1 || K > kMaxRefresh) return false;
@@ -2393,6 +2415,7 @@ cudaError_t launch_one(const SweepArgs<T>& a, const SweepPlan& p, cudaStream_t s
   } else {
     if (p.C == 8) return launch_impl<T, 8, false>(a, p, s);
     if (p.C == 4) return launch_impl<T, 4, false>(a, p, s);
+    if (p.C == 2) return launch_impl<T, 2, false>(a, p, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -2535,6 +2558,7 @@ cudaError_t launch_pcg_persist(const PersistArgs<T>& a0, const SweepPlan& p, cud
   } else {
     if (p.C == 8) return launch_persist_impl<T, 8, false>(a, p, s, query);
     if (p.C == 4) return launch_persist_impl<T, 4, false>(a, p, s, query);
+    if (p.C == 2) return launch_persist_impl<T, 2, false>(a, p, s, query);
   }
   return cudaErrorInvalidValue;
 }

@@ -112,7 +112,7 @@ def test_hvp_fp64_cluster_split(cs):
                 assert rowrel(HV, ref).max() < 1e-11, (cs, K)
 
 
-@pytest.mark.parametrize("c64,c32", [(2, 4), (4, 8)])
+@pytest.mark.parametrize("c64,c32", [(2, 4), (4, 8), (4, 2)])
 def test_hvp_with_each_run_length(c64, c32):
     # every instantiated run length (values per thread) of the sweep kernel,
     # alone and split over a cluster, FP64 against the oracle and the FP32
@@ -239,7 +239,7 @@ def _varied_spec(n, seed):
 
 # (n, cluster size, refresh period, values per thread FP64, FP32): odd n puts
 # the wrap n-1 -> 0 of the last CTA's region inside a thread's run
-VARIED_OBS_CASES = [(997, 2, 4, 4, 8), (997, 3, 1, 2, 4), (1001, 3, 4, 4, 4), (1001, 2, 2, 2, 8)]
+VARIED_OBS_CASES = [(997, 2, 4, 4, 8), (997, 3, 1, 2, 4), (1001, 3, 4, 4, 4), (1001, 2, 2, 2, 8), (998, 3, 2, 4, 2)]
 
 
 @pytest.mark.parametrize("n,cs,K,c64,c32", VARIED_OBS_CASES)

@@ -22,7 +22,7 @@ def _built():
 
 @pytest.mark.parametrize("fp64", [True, False])
 def test_cluster_plans_cover_the_state_with_the_halo(fp64):
-    runs = (2, 4) if fp64 else (4, 8)
+    runs = (2, 4) if fp64 else (2, 4, 8)
     seen = 0
     for n, cs, K, C, w in itertools.product((40, 97, 300, 997, 4096, 30000), range(1, 17), (1, 2, 4, 8, 16),
                                             (0,) + runs, (2, 50)):
@@ -76,7 +76,7 @@ def test_warp_plans(fp64):
 
 
 def test_impossible_shapes_are_refused():
-    assert P.plan_tiling(4096, False, 50, "cluster", cs=5, K=8, C=2) is None    # FP32 runs are 4 or 8
+    assert P.plan_tiling(4096, False, 50, "cluster", cs=5, K=8, C=16) is None   # FP32 runs are 2, 4 or 8
     assert P.plan_tiling(4096, True, 50, "cluster", cs=5, K=8, C=8) is None     # FP64 runs are 2 or 4
     assert P.plan_tiling(4096, False, 50, "cluster", cs=1, K=8, C=4) is None    # one CTA cannot hold it
     assert P.plan_tiling(4096, False, 50, "cluster", cs=17, K=8) is None        # cluster limit 16
