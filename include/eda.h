@@ -360,9 +360,10 @@ EDA_API int eda_sweep_plan(eda_handle* h, int fp64, int* info);
  * running launch ends at the iteration boundary after the active count falls
  * to R (every member's PCG state stays on the device) and the solve goes on
  * in a launch on the tail tiling, with the same iterates up to the rounding
- * order of the reductions.  eda_autotune chooses them (active counts L/2,
- * L/4, ..., 1; a level is kept where its tiling's Hessian-product sweep beats
- * the main tiling's by more than 7 %) and replaces any set before.
+ * order of the reductions.  eda_autotune chooses them (active counts falling
+ * by a quarter at a time from 3(L+1)/4 to 1; a level is kept where its
+ * tiling's Hessian-product sweep beats the main tiling's by more than 7 %)
+ * and replaces any set before.
  *
  * eda_tail_plans: *count receives the number of tail tilings of one
  * precision (fp64 != 0: FP64 sweeps, else FP32); levels[i] (may be NULL) and

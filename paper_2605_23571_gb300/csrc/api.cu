@@ -703,8 +703,8 @@ int persist_fits(eda_handle* h, const SweepPlan& pl) {
   return q;
 }
 
-// Tilings for the persistent PCG's convergence tail: at active counts
-// R = M/2, M/4, ..., 1 (rounded up), times the Hessian-product sweep of R
+// Tilings for the persistent PCG's convergence tail: at active counts R
+// falling by a quarter at a time from 3M/4 to 1, times the Hessian-product sweep of R
 // active columns on the chosen tiling and on clusters of more CTAs (up to
 // 16) with neighbouring refresh periods, and keeps a level's fastest tiling
 // where it beats the chosen one by more than 7 %.  The chosen tiling is
@@ -735,7 +735,7 @@ int tune_tails(eda_handle* h, bool fp64, cudaEvent_t e0, cudaEvent_t e1) {
     *ms /= reps;
     return EDA_OK;
   };
-  for (int R = (M + 1) / 2; rc == EDA_OK; R = (R + 1) / 2) {
+  for (int R = M - std::max(1, M / 4); rc == EDA_OK && R >= 1; R -= std::max(1, R / 4)) {
     for (int i = 0; i < M; ++i) hm[(size_t)i] = i < R ? 1 : 0;
     CU(h, cudaMemcpy(mask, hm.data(), (size_t)M * sizeof(int), cudaMemcpyHostToDevice));
     float base_ms = 0.f;
@@ -779,7 +779,6 @@ int tune_tails(eda_handle* h, bool fp64, cudaEvent_t e0, cudaEvent_t e1) {
         std::fprintf(stderr, "eda_autotune: %s tail at <= %d active: CS=%d K=%d A=%d %.4f ms (chosen tiling %.4f)\n",
                      fp64 ? "FP64" : "FP32", R, best.CS, best.K, best.A, best_ms, base_ms);
     }
-    if (R == 1) break;
   }
   cudaFree(mask);
   int r2 = set_plan(h, fp64, main);
