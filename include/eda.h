@@ -518,7 +518,11 @@ EDA_API int eda_group_solve(eda_group* g, double tol, int maxit, int use_lmp, do
  * [b_j / s_b, dz_0 / s_z] with s_b, s_z the training-set RMS of b and dz_0;
  * guess = dz_0 + s_z * out.  Parameters: FP32 masters, flat, per layer the
  * weights [out][in][5] then the biases; every product uses the weights
- * rounded to BF16, activations and accumulation are FP32.  Training: mean
+ * rounded to BF16, activations and accumulation are FP32 (with 64 hidden
+ * channels the 64 -> 64 convolutions run on the tensor cores, each FP32
+ * activation split exactly into three BF16 parts; EDA_WS_TC=0 keeps them on
+ * CUDA cores; EDA_ERR_TIMEOUT if a bounded wait for the tensor cores gives
+ * up).  Training: mean
  * squared error of (guess - dz_j) / s_z, AdamW (beta 0.9/0.999, eps 1e-8,
  * decoupled weight decay).  Samples are [count x n] FP64 arrays (host or
  * device).  Calls on one network are not thread-safe.

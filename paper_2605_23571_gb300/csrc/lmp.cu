@@ -30,9 +30,12 @@
 
 #include "eda_internal.h"
 #include "lmp.h"
+#include "tc.h"
 
 namespace eda {
 namespace {
+
+using namespace tc;
 
 constexpr int kRows = 128;  // rows of n per CTA (a row chunk)
 
@@ -112,78 +115,6 @@ __global__ void __launch_bounds__(kCcThreads) lmp_expand_cc_kernel(int n, int k,
 // chunk is 6 per thread: one round of loads in flight)
 constexpr int kStageRows = 6;
 constexpr int kTcThreads = 256;  // eight warps: warp w reads TMEM lanes 32 (w % 4) .. 32 (w % 4) + 31
-constexpr int kWaitLimit = 1 << 24;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Shared-memory matrix descriptor of a K-major operand without swizzling:
-// core matrices of 8 rows x 16 bytes stored contiguously (128 bytes), lbo =
-// byte distance between core matrices adjacent along K, sbo = between
-// core matrices adjacent along M (or N).  Bits 46-48 hold the fixed 0b001 of
-// the tcgen05 descriptor format.
-__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
-// K-major, M = 128, N = nd.
-__device__ __forceinline__ uint32_t idesc_bf16(int nd) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(nd >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accum) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-// Bounded wait for phase `parity` of an mbarrier; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-  for (int it = 0; it < kWaitLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 a, __nv_bfloat16 b) {
-  return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-}
-
 // FP64 -> FP32 by truncating the significand to 24 bits, in integer
 // arithmetic (GB300's FP64 pipe, which its conversions use, runs at 1/64 of
 // the FP32 rate).  Magnitudes below the FP32 normal range give a signed
@@ -228,55 +159,6 @@ __device__ __forceinline__ void split8(const T (&x)[8], uint4* hi, uint4* lo) {
   }
   *hi = make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
   *lo = make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
-}
-
-// Byte offset of core-matrix row (r, 8-element group kb) of a K-major
-// operand with kg groups of 8 along K: core matrix (r / 8, kb) at
-// ((r / 8) * kg + kb) * 128, row r % 8 at 16 (r % 8).
-__device__ __forceinline__ uint32_t kmaj_off(int r, int kb, int kg) {
-  return (uint32_t)((((r >> 3) * kg + kb) << 7) + ((r & 7) << 4));
-}
-
-struct TmemCta {
-  uint32_t base;
-  int ncols;
-};
-
-// Allocates ncols TMEM columns (warp 0), publishes the base through slot.
-__device__ __forceinline__ uint32_t tmem_alloc(uint32_t* slot, int ncols) {
-  if ((threadIdx.x >> 5) == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-                 "r"(ncols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  return *slot;
-}
-
-__device__ __forceinline__ void tmem_free(uint32_t base, int ncols) {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if ((threadIdx.x >> 5) == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
-}
-
-__device__ __forceinline__ int tmem_cols(int c) { return c <= 32 ? 32 : (c <= 64 ? 64 : (c <= 128 ? 128 : (c <= 256 ? 256 : 512))); }
-
-// Bulk asynchronous copy of `bytes` (a multiple of 16, both addresses
-// 16-byte aligned) from global to this CTA's shared memory, its completion
-// counted on the mbarrier at mbar.
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
 // Thread 0: the kg/2 K-steps of hi.hi + hi.lo + lo.hi into the accumulator

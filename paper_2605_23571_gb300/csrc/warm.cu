@@ -8,7 +8,8 @@
 // training-set RMS of b and dz_0; guess = dz_0 + s_z * out.  Weights are FP32
 // masters used as BF16 in every product, activations and accumulation FP32.
 // Hand-written kernels: forward convolution (register-blocked 4 channels x 4
-// positions per thread), the data gradient as a forward convolution with the
+// positions per thread, or, for the 64 -> 64 layers, an implicit GEMM on the
+// tcgen05 tensor cores), the data gradient as a forward convolution with the
 // transposed and flipped kernel, the weight gradient by per-CTA partial sums,
 // GELU, MSE and AdamW.
 #include <cuda_bf16.h>
@@ -20,6 +21,7 @@
 #include <vector>
 
 #include "handle.h"
+#include "tc.h"
 
 namespace {
 
@@ -93,6 +95,157 @@ __global__ void __launch_bounds__(256) conv_fwd_kernel(int n, int cin, int cout,
       if (pre) pre[idx] = z;
       out[idx] = act ? gelu_f(z) : z;
     }
+  }
+}
+
+// ------------------------------------------------ tensor-core convolution
+// The 64 -> 64 layers as an implicit GEMM on the tensor cores: for a tile of
+// 128 positions, D (128 positions x 64 output channels) = sum over the five
+// taps t of A_t (positions x 64 input channels) B_t (64 x 64).  The input
+// tile is staged once, 132 rows (positions i0 - 2 .. i0 + 129, periodic),
+// each row's 64 channels as eight 16-byte groups, and kept row-contiguous
+// within each group of 8 channels: A_t is then A_0 shifted by t rows, a
+// descriptor start 16 t bytes further.  Activations stay FP32 in value: each
+// is split exactly into three BF16 parts (hi = bf16(x), mid = bf16(x - hi),
+// lo = bf16(x - hi - mid); 3 x 8 significant bits), so that the three MMAs
+// per step multiply FP32 activations by the BF16 weights exactly, with FP32
+// accumulation.  The weights arrive pre-tiled (weights_tile_kernel) by one
+// bulk asynchronous copy.
+constexpr int kTcPos = 128;               // positions per tile (the MMA's M)
+constexpr int kTcRows = kTcPos + KS - 1;  // staged rows
+constexpr int kTcRowsP = 136;             // staged rows rounded up to whole core matrices
+constexpr int kTcCh = 64;                 // channels in and out
+constexpr uint32_t kTcGroup = kTcRowsP * 16;             // bytes of one 8-channel group of a part
+constexpr uint32_t kTcPart = (kTcCh / 8) * kTcGroup;      // bytes of one BF16 part of the tile
+constexpr uint32_t kTcTap = kTcCh * kTcCh * 2;           // bytes of one tap's weight tile
+constexpr size_t kTcSmem = 3 * (size_t)kTcPart + KS * (size_t)kTcTap + 32;
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b, __nv_bfloat16* ra, __nv_bfloat16* rb) {
+  *ra = __float2bfloat16_rn(a);
+  *rb = __float2bfloat16_rn(b);
+  return (uint32_t)__bfloat16_as_ushort(*ra) | ((uint32_t)__bfloat16_as_ushort(*rb) << 16);
+}
+
+// out[s][o][i] = bias[o] + sum_{c,t} W[o][c][t] x[s][c][(i + t - 2) mod n]
+// (pre and GELU as conv_fwd_kernel) for cin = cout = 64.  Grid (S,
+// ceil(n / 128)); 128 threads (warp w reads TMEM lanes 32w.., the tile's
+// positions).  Shared: three parts of the staged tile | the five tap tiles
+// | two mbarriers (weights copy, MMAs) | TMEM slot.  A bounded wait that
+// gives up sets *timeout and the CTA skips its outputs.
+__global__ void __launch_bounds__(128) conv_tc_kernel(int n, const float* __restrict__ x,
+                                                      const __nv_bfloat16* __restrict__ Wtile,
+                                                      const float* __restrict__ bias, float* pre, float* out, int act,
+                                                      int* timeout) {
+  using namespace eda::tc;
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char* Apart = tsm;  // part q at q * kTcPart
+  unsigned char* Bt = tsm + 3 * kTcPart;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(Bt + KS * kTcTap);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(bars + 2);
+  const uint32_t bw = smem_u32(bars), bm = smem_u32(bars + 1);
+  const int s = blockIdx.x, i0 = blockIdx.y * kTcPos;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bw) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bm) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bw), "r"((uint32_t)(KS * kTcTap))
+                 : "memory");
+    bulk_g2s(smem_u32(Bt), Wtile, KS * kTcTap, bw);
+  }
+  // the tile: item (group g of 8 channels, row j) -> one 16-byte row of each part
+  const float* xs = x + (long long)s * kTcCh * n;
+  for (int idx = threadIdx.x; idx < (kTcCh / 8) * kTcRows; idx += blockDim.x) {
+    const int g = idx / kTcRows, j = idx - g * kTcRows;
+    int p = i0 + j - KS / 2;
+    p = (p % n + n) % n;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) v[e] = xs[(long long)(8 * g + e) * n + p];
+    uint32_t w3[3][4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      __nv_bfloat16 h0, h1, m0, m1, l0, l1;
+      w3[0][e / 2] = pack_bf16(v[e], v[e + 1], &h0, &h1);
+      const float r0 = v[e] - __bfloat162float(h0), r1 = v[e + 1] - __bfloat162float(h1);
+      w3[1][e / 2] = pack_bf16(r0, r1, &m0, &m1);
+      w3[2][e / 2] = pack_bf16(r0 - __bfloat162float(m0), r1 - __bfloat162float(m1), &l0, &l1);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+      *reinterpret_cast<uint4*>(Apart + q * kTcPart + g * kTcGroup + j * 16) =
+          make_uint4(w3[q][0], w3[q][1], w3[q][2], w3[q][3]);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  const uint32_t tbase = tmem_alloc(slot, kTcCh);  // includes the block barrier
+  if (threadIdx.x == 0) {
+    bool have = mbar_wait(bw, 0);
+    if (have) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t id = idesc_bf16(kTcCh);
+      bool first = true;
+      for (int t = 0; t < KS; ++t)
+        for (int ks = 0; ks < kTcCh / 16; ++ks) {
+          // B_t: 64 output channels x 64 input channels, K-major core matrices
+          // (lbo 128 along K, sbo 1024 along N)
+          const uint64_t bd = kmajor_desc(smem_u32(Bt + t * kTcTap) + ks * 256u, 128u, 1024u);
+          for (int q = 0; q < 3; ++q) {
+            // A_t: rows shifted by t; groups of 8 channels kTcGroup apart
+            const uint64_t ad = kmajor_desc(smem_u32(Apart + q * kTcPart) + 2u * ks * kTcGroup + 16u * t, kTcGroup,
+                                            128u);
+            mma_bf16(tbase, ad, bd, id, first ? 0u : 1u);
+            first = false;
+          }
+        }
+      mma_commit(bm);
+    } else {
+      mbar_arrive(bm);
+      if (timeout != nullptr) atomicExch(timeout, 1);
+    }
+    slot[1] = have ? 1u : 0u;
+  }
+  __syncwarp();
+  bool ok = mbar_wait(bm, 0);
+  ok = __syncthreads_and(ok ? 1 : 0) != 0 && slot[1] != 0u;
+  if (!ok) {
+    if (threadIdx.x == 0 && timeout != nullptr) atomicExch(timeout, 1);
+    mbar_wait(bw, 0);
+    mbar_wait(bm, 0);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = i0 + 32 * w + lane;  // TMEM lane = row = position
+    for (int c0 = 0; c0 < kTcCh; c0 += 16) {
+      float v[16];
+      tmem_ld16(tbase + ((uint32_t)(32 * w) << 16) + (uint32_t)c0, v);
+      if (i < n) {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const int o = c0 + e;
+          const float z = v[e] + (bias ? bias[o] : 0.f);
+          const long long idx = ((long long)s * kTcCh + o) * n + i;
+          if (pre) pre[idx] = z;
+          out[idx] = act ? gelu_f(z) : z;
+        }
+      }
+    }
+  }
+  tmem_free(tbase, kTcCh);
+}
+
+// Tap tiles of a 64 x 64 layer for conv_tc_kernel: forward Tf[t] = W[.][.][t]
+// (rows output channel o, K input channel c) and the data gradient's
+// Tb[t'] = W[.][.][4 - t'] transposed (rows c, K o), BF16, each tap a 64 x 64
+// block of K-major core matrices (core (r / 8, k / 8) at ((r / 8) * 8 +
+// k / 8) * 128 bytes, row r % 8 at 16 (r % 8)).
+__global__ void weights_tile_kernel(const float* W, __nv_bfloat16* Tf, __nv_bfloat16* Tb) {
+  const int total = KS * kTcCh * kTcCh;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int o = e / (kTcCh * KS), c = (e / KS) % kTcCh, t = e % KS;
+    const __nv_bfloat16 b = __float2bfloat16_rn(W[e]);
+    auto at = [](int r, int k) { return ((((r >> 3) * 8 + (k >> 3)) << 7) + ((r & 7) << 4)) / 2 + (k & 7); };
+    Tf[t * kTcCh * kTcCh + at(o, c)] = b;
+    Tb[(KS - 1 - t) * kTcCh * kTcCh + at(c, o)] = b;
   }
 }
 
@@ -266,6 +419,11 @@ struct eda_ws {
   long long woff[4], boff[4], nparam = 0;
   float *theta = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
   __nv_bfloat16 *Wb = nullptr, *Wt = nullptr;  // per layer at woff
+  // tensor-core tap tiles of the 64 -> 64 layers (forward, data gradient),
+  // layer l at l * 5 * 64 * 64; tc: those layers run on the tensor cores
+  __nv_bfloat16 *Tf = nullptr, *Tb = nullptr;
+  bool tc = false;
+  int* tout = nullptr;  // set by a tensor-core wait that gave up
   float* act[5] = {};                           // act[0] features, act[l] output of layer l
   float* pre[4] = {};                           // pre-activations of layers 1..3
   float* gbuf[2] = {};                          // gradient ping-pong (max channels)
@@ -298,36 +456,70 @@ cudaError_t walloc(eda_ws* w, T** p, size_t count) {
   return e;
 }
 
+// The tensor-core tap tiles of layer l (nullptr: the layer runs on CUDA cores).
+const __nv_bfloat16* tile_f(const eda_ws* w, int l) {
+  return w->tc && w->cin[l] == kTcCh && w->cout_[l] == kTcCh ? w->Tf + (long long)l * KS * kTcCh * kTcCh : nullptr;
+}
+const __nv_bfloat16* tile_b(const eda_ws* w, int l) {
+  return w->tc && w->cin[l] == kTcCh && w->cout_[l] == kTcCh ? w->Tb + (long long)l * KS * kTcCh * kTcCh : nullptr;
+}
+
 int refresh_bf16(eda_ws* w) {
   for (int l = 0; l < 4; ++l) {
     eda::count_launch();
     weights_bf16_kernel<<<64, 256, 0, w->st>>>(w->cout_[l], w->cin[l], w->theta + w->woff[l], w->Wb + w->woff[l],
                                                w->Wt + w->woff[l]);
+    if (tile_f(w, l) != nullptr) {
+      eda::count_launch();
+      weights_tile_kernel<<<80, 256, 0, w->st>>>(w->theta + w->woff[l], w->Tf + (long long)l * KS * kTcCh * kTcCh,
+                                                 w->Tb + (long long)l * KS * kTcCh * kTcCh);
+    }
   }
   WCU(w, cudaGetLastError());
   return EDA_OK;
 }
 
-int conv(eda_ws* w, int S, int cin, int cout, const float* x, const __nv_bfloat16* W, const float* b, float* pre,
-         float* out, int act) {
+// One convolution of S samples; tile != nullptr (a 64 -> 64 layer's tap
+// tiles) runs it on the tensor cores.
+int conv(eda_ws* w, int S, int cin, int cout, const float* x, const __nv_bfloat16* W, const __nv_bfloat16* tile,
+         const float* b, float* pre, float* out, int act) {
   static bool attr = false;
   if (!attr) {
     WCU(w, cudaFuncSetAttribute(conv_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 MAXC * (TP + KS - 1) * 4 + MAXC * MAXC * KS * 2));
+    WCU(w, cudaFuncSetAttribute(conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
     attr = true;
   }
-  const size_t smem = (size_t)cin * (TP + KS - 1) * sizeof(float) + (size_t)cout * cin * KS * sizeof(__nv_bfloat16);
   eda::count_launch();
-  conv_fwd_kernel<<<dim3(S, (w->n + TP - 1) / TP), 256, smem, w->st>>>(w->n, cin, cout, x, W, b, pre, out, act);
+  if (tile != nullptr) {
+    conv_tc_kernel<<<dim3(S, (w->n + kTcPos - 1) / kTcPos), 128, kTcSmem, w->st>>>(w->n, x, tile, b, pre, out, act,
+                                                                                   w->tout);
+  } else {
+    const size_t smem =
+        (size_t)cin * (TP + KS - 1) * sizeof(float) + (size_t)cout * cin * KS * sizeof(__nv_bfloat16);
+    conv_fwd_kernel<<<dim3(S, (w->n + TP - 1) / TP), 256, smem, w->st>>>(w->n, cin, cout, x, W, b, pre, out, act);
+  }
   WCU(w, cudaGetLastError());
+  return EDA_OK;
+}
+
+// After the stream synchronised: EDA_ERR_TIMEOUT if a tensor-core wait gave up.
+int check_tout(eda_ws* w) {
+  if (!w->tc) return EDA_OK;
+  int t = 0;
+  WCU(w, cudaMemcpy(&t, w->tout, sizeof(int), cudaMemcpyDeviceToHost));
+  if (t) {
+    WCU(w, cudaMemset(w->tout, 0, sizeof(int)));
+    return wfail(w, EDA_ERR_TIMEOUT, "warm start: a bounded wait for the tensor cores gave up");
+  }
   return EDA_OK;
 }
 
 // Forward of S samples whose features are in act[0].
 int forward(eda_ws* w, int S) {
   for (int l = 0; l < 4; ++l) {
-    const int rc = conv(w, S, w->cin[l], w->cout_[l], w->act[l], w->Wb + w->woff[l], w->theta + w->boff[l],
-                        l < 3 ? w->pre[l] : nullptr, w->act[l + 1], l < 3 ? 1 : 0);
+    const int rc = conv(w, S, w->cin[l], w->cout_[l], w->act[l], w->Wb + w->woff[l], tile_f(w, l),
+                        w->theta + w->boff[l], l < 3 ? w->pre[l] : nullptr, w->act[l + 1], l < 3 ? 1 : 0);
     if (rc) return rc;
   }
   return EDA_OK;
@@ -358,7 +550,8 @@ int forward_backward(eda_ws* w, int S) {
         w->n, S, w->cin[l], w->cout_[l], w->act[l], g, w->grad + w->woff[l], w->grad + w->boff[l]);
     WCU(w, cudaGetLastError());
     if (l > 0) {
-      rc = conv(w, S, w->cout_[l], w->cin[l], g, w->Wt + w->woff[l], nullptr, nullptr, w->gbuf[1 - cur], 0);
+      rc = conv(w, S, w->cout_[l], w->cin[l], g, w->Wt + w->woff[l], tile_b(w, l), nullptr, nullptr,
+                w->gbuf[1 - cur], 0);
       if (rc) return rc;
       cur = 1 - cur;
     }
@@ -400,6 +593,13 @@ EDA_API int eda_ws_create(int n, int hidden, int max_batch, void* stream, eda_ws
     if (ok && l < 3) ok = !walloc(w, &w->pre[l], B * co[l] * n);
   }
   for (int i = 0; i < 2 && ok; ++i) ok = !walloc(w, &w->gbuf[i], B * (long long)hidden * n);
+  // the 64 -> 64 layers on the tensor cores (EDA_WS_TC=0: CUDA cores)
+  w->tc = hidden == kTcCh && eda::env_int("EDA_WS_TC", 1) != 0;
+  if (ok && w->tc) {
+    const size_t tiles = (size_t)4 * KS * kTcCh * kTcCh;
+    ok = !walloc(w, &w->Tf, tiles) && !walloc(w, &w->Tb, tiles) && !walloc(w, &w->tout, 1);
+    if (ok) ok = cudaMemset(w->tout, 0, sizeof(int)) == cudaSuccess;
+  }
   if (ok) ok = cudaMallocHost((void**)&w->hpin, 2 * sizeof(double)) == cudaSuccess;
   if (!ok) {
     eda_ws_destroy(w);
@@ -513,6 +713,8 @@ EDA_API int eda_ws_loss_grad(eda_ws* w, const double* rhs, const double* ctrl, c
   WCU(w, cudaFreeAsync(dc, w->st));
   WCU(w, cudaFreeAsync(ds, w->st));
   WCU(w, cudaStreamSynchronize(w->st));
+  rc = check_tout(w);
+  if (rc) return rc;
   if (loss_out) *loss_out = w->hpin[0];
   return EDA_OK;
 }
@@ -597,6 +799,8 @@ EDA_API int eda_ws_train(eda_ws* w, const double* rhs, const double* ctrl, const
     WCU(w, cudaFreeAsync(ds, w->st));
   }
   WCU(w, cudaStreamSynchronize(w->st));
+  rc = check_tout(w);
+  if (rc) return rc;
   if (loss_out) std::memcpy(loss_out, eloss.data(), epochs * sizeof(double));
   return EDA_OK;
 }
@@ -644,8 +848,8 @@ EDA_API int eda_ws_infer(eda_ws* w, const double* rhs, const double* ctrl, int c
   if (t1) WCU(w, cudaFreeAsync(t1, w->st));
   if (t2) WCU(w, cudaFreeAsync(t2, w->st));
   if (t3) WCU(w, cudaFreeAsync(t3, w->st));
-  if (host_out) WCU(w, cudaStreamSynchronize(w->st));
-  return EDA_OK;
+  if (host_out || w->tc) WCU(w, cudaStreamSynchronize(w->st));
+  return check_tout(w);
 }
 
 }  // extern "C"

@@ -1,6 +1,7 @@
 """The learned warm start's hand-written kernels against the FP64 oracle of
 the network (same BF16-rounded weights): loss, gradients, inference and one
-AdamW step; and the end-to-end use as PCG initial iterate."""
+AdamW step, on CUDA cores and with the tensor-core convolutions; and the
+end-to-end use as PCG initial iterate."""
 import numpy as np
 import pytest
 
@@ -36,8 +37,10 @@ def net_case(hidden=8, n=96, S_=6, seed=0):
     return rhs, ctrl, sol, theta
 
 
-@pytest.mark.parametrize("hidden,n", [(8, 96), (64, 128), (5, 37)])
+@pytest.mark.parametrize("hidden,n", [(8, 96), (64, 128), (5, 37), (64, 1000)])
 def test_loss_gradient_and_inference_match_oracle(hidden, n):
+    # hidden = 64 takes the tensor-core convolutions for the 64 -> 64 layers
+    # (n = 1000: eight position tiles, the last one ragged)
     rhs, ctrl, sol, theta = net_case(hidden, n)
     sb, sz = 2.9, 0.55
     loss_o, grad_o = W.loss_and_grad(theta, hidden, rhs, ctrl, sol, sb, sz)
@@ -175,3 +178,28 @@ def test_warm_start_gain_on_held_out_problems():
     bn = torch.linalg.norm(b, dim=1).cpu().numpy()
     diff = torch.linalg.norm(dzw - dz0, dim=1).cpu().numpy()
     assert (diff <= (rr0 + rrw) * bn * (1 + 1e-6) + 1e-12).all()
+
+
+def test_tensor_core_and_cuda_core_convolutions_agree():
+    # the same network and batch with the 64 -> 64 layers on the tensor cores
+    # and on CUDA cores (EDA_WS_TC=0): both take FP32 activations times BF16
+    # weights with FP32 accumulation, which the tensor cores sum in another
+    # order and round differently; held to each other by the bars both keep
+    # against the FP64 oracle (measured loss difference 5e-6 relative)
+    from helpers import env
+    hidden, n = 64, 700
+    rhs, ctrl, sol, theta = net_case(hidden, n, S_=5, seed=9)
+    res = {}
+    for tc in (1, 0):
+        with env(EDA_WS_TC=tc):
+            with P.WarmStart(n, hidden, max_batch=8) as ws:
+                ws.eda_ws_set_params(theta.astype(np.float32))
+                ws.eda_ws_set_scales(2.5, 0.6)
+                loss, grad = ws.eda_ws_loss_grad(rhs, ctrl, sol)
+                out = np.zeros_like(rhs)
+                ws.eda_ws_infer(rhs, ctrl, out)
+                res[tc] = (loss, grad, out)
+    (l1, g1, o1), (l0, g0, o0) = res[1], res[0]
+    assert abs(l1 - l0) <= 2e-5 * l0
+    assert np.abs(g1 - g0).max() <= 2e-4 * np.abs(g0).max()
+    assert rowrel(o1, o0).max() < 2e-5
