@@ -24,6 +24,8 @@ assimilations with randomized preconditioning"):
 * scaled spectral LMP ..................... Section 3.1 (P_theta, choices of
   theta)
 * preconditioned CG ....................... Section 2.3 (CG on the SPD system)
+* Ritz pairs from CG (Lanczos) ............ Section 3 (spectral LMPs from the
+  Ritz pairs of an earlier CG run)
 
 Parity status: every function here is pinned by a test in
 ``tests/test_oracle_*.py`` against something other than itself (closed forms,
@@ -60,6 +62,9 @@ unpinned": the paper prints no numbers for them.  Function -> pin:
                        the split iterates equal pcg's (nested Krylov spaces
                        U K(U H U, U b) = K(P H, P b)) and converge to the
                        dense solution
+* lanczos_cg ......... V^T V = I and V^T H V = T on an explicit H; with
+                       iters = n the Ritz values are eigh(H)'s; the Lanczos
+                       residual identity |H s - theta s| = eta |y_last|
 
 Conventions (readings of the paper where it is silent):
 * states x_0..x_N on the window; observation steps are given explicitly and
@@ -538,6 +543,50 @@ def pcg(apply_h, b, precond=None, tol=1e-6, maxit=100, x0=None, fixed_iters=None
     if fixed_iters is not None:
         status[:] = np.where(status == BREAKDOWN, BREAKDOWN, CONVERGED)
     return {"x": x, "iters": iters, "relres": relres, "status": status, "J": Jhist}
+
+
+def lanczos_cg(apply_h, b, iters):
+    """Ritz pairs of H from conjugate gradients (Section 3: spectral LMPs
+    built from the Ritz pairs of an earlier CG run; the CG-Lanczos relation).
+
+    CG without preconditioner from x0 = 0 on H x = b (b one vector) for
+    ``iters`` iterations.  Its residuals, normalised with alternating signs,
+    v_j = (-1)^j r_j / |r_j|, are the Lanczos basis V of the Krylov space
+    K_iters(H, b), and its coefficients give the tridiagonal T = V^T H V:
+      T[j, j]   = 1/alpha_j + beta_{j-1}/alpha_{j-1}   (no second term at j = 0)
+      T[j, j+1] = sqrt(beta_j) / alpha_j
+    with alpha_j = |r_j|^2 / p_j^T H p_j and beta_j = |r_{j+1}|^2 / |r_j|^2.
+    The eigenpairs (theta_i, y_i) of T give the Ritz pairs (theta_i, V y_i).
+    Returns dict(V [n x iters], T, alpha, beta, theta (descending), S = the
+    Ritz vectors [n x iters] in the same order, eta = T's next off-diagonal
+    sqrt(beta_{iters-1}) / alpha_{iters-1}: |H s_i - theta_i s_i| = eta |y_i[-1]|)."""
+    b = np.asarray(b, dtype=np.float64).ravel()
+    n = b.shape[0]
+    r = b.copy()
+    p = r.copy()
+    rr = float(r @ r)
+    V = np.zeros((n, iters))
+    alpha = np.zeros(iters)
+    beta = np.zeros(iters)
+    for j in range(iters):
+        V[:, j] = (-1.0) ** j * r / np.sqrt(rr)
+        q = np.asarray(apply_h(p[None, :]), dtype=np.float64).ravel()
+        alpha[j] = rr / float(p @ q)
+        r = r - alpha[j] * q
+        rr_new = float(r @ r)
+        beta[j] = rr_new / rr
+        p = r + beta[j] * p
+        rr = rr_new
+    T = np.zeros((iters, iters))
+    for j in range(iters):
+        T[j, j] = 1.0 / alpha[j] + (beta[j - 1] / alpha[j - 1] if j > 0 else 0.0)
+        if j + 1 < iters:
+            T[j, j + 1] = T[j + 1, j] = np.sqrt(beta[j]) / alpha[j]
+    theta, Y = np.linalg.eigh(T)
+    order = np.argsort(theta)[::-1]
+    theta, Y = theta[order], Y[:, order]
+    return {"V": V, "T": T, "alpha": alpha, "beta": beta, "theta": theta, "S": V @ Y, "Y": Y,
+            "eta": np.sqrt(beta[-1]) / alpha[-1]}
 
 
 def pcg_split(apply_h, b, S, s, tol=1e-6, maxit=100, fixed_iters=None):

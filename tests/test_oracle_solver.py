@@ -419,3 +419,59 @@ def test_split_preconditioner_factor_and_iterates():
                     for m in range(spec.n_members)])
     res = O.pcg_split(hv, b, Sk, s, tol=1e-13, maxit=300)
     assert (np.linalg.norm(res["x"] - ref, axis=1) / np.linalg.norm(ref, axis=1)).max() <= 1e-10
+
+
+def test_lanczos_cg_relations_and_ritz_pairs():
+    # Ritz pairs from CG (Section 3: spectral LMPs from the Ritz pairs of an
+    # earlier CG run), pinned on an explicit SPD matrix with eigenvalues >= 1
+    # (the spectrum class of I + A): the alternating-sign normalised
+    # residuals are orthonormal, V^T H V is CG's tridiagonal, with as many
+    # iterations as unknowns the Ritz values are the eigenvalues, and every
+    # Ritz pair satisfies the Lanczos residual identity
+    rng = np.random.default_rng(12)
+    n = 12
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = 1.0 + np.geomspace(1e2, 1e-2, n)
+    H = (Q * lam) @ Q.T
+    b = rng.standard_normal(n)
+    apply_h = lambda X: X @ H.T
+    k = 6
+    L = O.lanczos_cg(apply_h, b, k)
+    V, T = L["V"], L["T"]
+    np.testing.assert_allclose(V.T @ V, np.eye(k), atol=1e-12)
+    np.testing.assert_allclose(V.T @ H @ V, T, rtol=0, atol=1e-10 * np.abs(T).max())
+    for i in range(k):
+        s, th = L["S"][:, i], L["theta"][i]
+        res = np.linalg.norm(H @ s - th * s)
+        assert abs(res - L["eta"] * abs(L["Y"][-1, i])) <= 1e-9 * lam.max()
+    assert (np.diff(L["theta"]) <= 0).all() and L["theta"][-1] >= 1.0 - 1e-12
+    # as many iterations as unknowns, on a well-conditioned H (so that the
+    # finite-precision Lanczos basis stays orthogonal): the Ritz values are
+    # the eigenvalues and the Ritz vectors the eigenvectors (up to sign)
+    m = 8
+    Q2, _ = np.linalg.qr(rng.standard_normal((m, m)))
+    lam2 = 1.0 + np.linspace(4.0, 0.1, m)
+    H2 = (Q2 * lam2) @ Q2.T
+    full = O.lanczos_cg(lambda X: X @ H2.T, rng.standard_normal(m), m)
+    np.testing.assert_allclose(full["theta"], np.sort(lam2)[::-1], rtol=1e-9)
+    for i in range(m):
+        v = Q2[:, np.argsort(lam2)[::-1][i]]
+        assert abs(abs(full["S"][:, i] @ v) - 1.0) < 1e-8
+
+
+def test_lanczos_cg_on_the_control_hessian():
+    # the same relations through the oracle's Hessian products of the tiny
+    # EDA problem's control member (batch interface of hvp)
+    spec = S.spec_tiny(seed=3)
+    taps = O.bhalf_taps(spec.n, spec.length_scale, spec.sigma_b)
+    _, xb, y = O.twin(spec, S.draws(spec), taps)
+    traj = O.member_trajectories(spec, xb)
+    b = O.rhs(spec, traj, O.innovations(spec, traj, y), taps)
+    Hd = np.eye(spec.n) + O.dense_A(spec, traj[0], taps)
+    L = O.lanczos_cg(lambda X: O.hvp(spec, traj[0:1], X, taps), b[0], 8)
+    np.testing.assert_allclose(L["V"].T @ L["V"], np.eye(8), atol=1e-10)
+    np.testing.assert_allclose(L["V"].T @ Hd @ L["V"], L["T"], rtol=0, atol=1e-9 * np.abs(L["T"]).max())
+    ev = np.linalg.eigvalsh(Hd)
+    assert L["theta"][0] <= ev[-1] * (1 + 1e-12) and L["theta"][-1] >= ev[0] * (1 - 1e-12)
+    # the largest Ritz value converges first: within 1e-3 of lambda_max
+    assert abs(L["theta"][0] - ev[-1]) <= 1e-3 * ev[-1]
