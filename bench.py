@@ -619,8 +619,9 @@ def forms_sketch_study(P, dev, seeds=20, iters=(1, 2, 3, 5, 10, 20, 30)):
     """The paper's experiment at its own size (Section 4: n=1500, 10-step
     window, 50 variables observed at 3 steps, 20 members, ell=20) on the GPU
     path: Algorithm 1 on the control member's Hessian with the five sketch
-    matrices Omega = Psi, A Psi (q=2), B Psi, U_B^T Psi and Gamma, each over
-    `seeds` realisations (Gaussian Psi; ensemble perturbations for Gamma, the
+    matrices Omega = Psi, A Psi (q=2), B Psi, U_B^T Psi and Gamma, and the
+    Ritz LMP of ell CG iterations on the control member's Hessian from member
+    1's right-hand side, each over `seeds` realisations (Gaussian Psi; ensemble perturbations for Gamma, the
     control member fixed).  Reports the median relative eigenvalue error
     |lambda* - lambda| / lambda* of lambda_i(I + A) against the eigenvalues of
     the dense operator (assembled from n products), the median quadratic-cost
@@ -669,7 +670,10 @@ def forms_sketch_study(P, dev, seeds=20, iters=(1, 2, 3, 5, 10, 20, 30)):
             out.append((J - J_star) / (0.0 - J_star))
         return out
 
-    variants = ("psi", "a_psi", "b_psi", "ubt_psi", "gamma")
+    # ritz_cg: the spectral LMP from the Ritz pairs of ell CG iterations on
+    # the control member's Hessian, run from another right-hand side (member
+    # 1's b, standing in for an earlier CG run of the same system)
+    variants = ("psi", "a_psi", "b_psi", "ubt_psi", "gamma", "ritz_cg")
     err = {v: [] for v in variants}
     red = {v: [] for v in variants}
     ms = {v: [] for v in variants}
@@ -677,21 +681,26 @@ def forms_sketch_study(P, dev, seeds=20, iters=(1, 2, 3, 5, 10, 20, 30)):
     red_none = []
     for seed in range(seeds):
         xb, y = twin(h, S.ensemble_draws(spec0, 0, 1000 + seed))
+        rhs_s = torch.empty(M, n, dtype=torch.float64, device=dev)
         for hh in hs.values():
-            hh.eda_set_trajectory(xb, y)
+            hh.eda_set_trajectory(xb, y, rhs_s)
         psi = torch.tensor(S.gaussian_matrix(ell, n, 2000 + seed), device=dev)
         ub = torch.empty_like(psi)
         h.eda_bhalf_apply(psi, ub)
         bpsi = torch.empty_like(psi)
         h.eda_bhalf_apply(ub, bpsi)
-        phis = {"psi": (psi, 1), "a_psi": (psi, 2), "b_psi": (bpsi, 1), "ubt_psi": (ub, 1), "gamma": (None, 1)}
+        phis = {"psi": (psi, 1), "a_psi": (psi, 2), "b_psi": (bpsi, 1), "ubt_psi": (ub, 1), "gamma": (None, 1),
+                "ritz_cg": (None, 0)}
         for v in variants:
             phi, q = phis[v]
             ev = np.zeros(spec0.k)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            h.eda_sketch(phi, q)
-            h.eda_build_lmp(ev)
+            if v == "ritz_cg":
+                ev[:] = h.eda_ritz_lmp(member=0, iters=ell, b=rhs_s[1])[:spec0.k]
+            else:
+                h.eda_sketch(phi, q)
+                h.eda_build_lmp(ev)
             torch.cuda.synchronize()
             ms[v].append(1e3 * (time.perf_counter() - t0))
             err[v].append(np.abs(lam_star - ev) / lam_star)

@@ -303,6 +303,28 @@ EDA_API int eda_solve(eda_handle* h, const eda_solve_opts* opts, double* dz_out,
 EDA_API int eda_lmp_apply(eda_handle* h, int which, int kind, int ncol, const double* R, double* Z);
 
 /*
+ * A spectral LMP from Ritz pairs of one member's Hessian (Section 3: the
+ * limited-memory preconditioners built from the Ritz pairs of an earlier CG
+ * run, the design the paper's randomized LMP is set against).  Runs `iters`
+ * iterations of CG without preconditioner from x0 = 0 on (I + A_m) x = b,
+ * A_m the Hessian term of member m = `member` (FP64 sweeps, one Hessian
+ * product per iteration, a host round trip per iteration); b [n] FP64, host
+ * or device (caller-owned, read only), or NULL for member m's own right-hand
+ * side from eda_set_trajectory.  Takes the Lanczos basis v_j = (-1)^j r_j /
+ * |r_j| and the tridiagonal T = V^T (I + A_m) V from CG's coefficients
+ * (T[j][j] = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T[j][j+1] = sqrt(beta_j) /
+ * alpha_j), its eigenpairs (theta_i, y_i), and installs the k leading Ritz
+ * pairs (theta_i, V y_i) as the handle's LMP, as eda_set_lmp would (theta
+ * mode of the handle; Ritz values below 1 by rounding taken as 1).  The
+ * basis is not reorthogonalised.  ritz_out (host, may be NULL) receives all
+ * `iters` Ritz values in descending order.  Requires eda_set_trajectory;
+ * EDA_ERR_INVALID unless 0 <= member < L+1 and k <= iters <= min(256, n);
+ * EDA_ERR_NUMERIC on a zero or non-finite b, a CG breakdown, or if CG
+ * converges first.  Synchronises the stream.
+ */
+EDA_API int eda_ritz_lmp(eda_handle* h, int member, int iters, const double* b, double* ritz_out);
+
+/*
  * Control-variable transform (Section 2.3, Eq. (system with CVT)): OUT[c] =
  * U_B V[c] for c < ncol, U_B the handle's symmetric banded circulant square
  * root of B (taps bhalf_coef).  Maps solutions dz_j of eda_solve_batch to

@@ -37,7 +37,8 @@ EXPORTS = ["eda_version", "eda_last_error", "eda_create", "eda_destroy", "eda_tw
            "eda_ws_get_params", "eda_ws_set_scales", "eda_ws_get_scales", "eda_ws_loss_grad", "eda_ws_train",
            "eda_ws_infer", "eda_hvp_noalloc", "eda_hvp_noalloc_capacity", "eda_lmp_info",
            "eda_trace", "eda_trace_read", "eda_ws_init", "eda_sweep_plan", "eda_bhalf_apply",
-           "eda_plan_tiling", "eda_solve", "eda_lmp_apply", "eda_tail_plans", "eda_set_tail_plan"]
+           "eda_plan_tiling", "eda_solve", "eda_lmp_apply", "eda_tail_plans", "eda_set_tail_plan",
+           "eda_ritz_lmp"]
 
 
 class EdaError(RuntimeError):
@@ -125,6 +126,8 @@ def lib() -> ctypes.CDLL:
     L.eda_tail_plans.argtypes = [vp, i, i, ctypes.POINTER(i), vp, vp]
     L.eda_set_tail_plan.restype = i
     L.eda_set_tail_plan.argtypes = [vp, i, i, i, i, i]
+    L.eda_ritz_lmp.restype = i
+    L.eda_ritz_lmp.argtypes = [vp, i, i, vp, vp]
     L.eda_solve.restype = i
     L.eda_solve.argtypes = [vp, ctypes.POINTER(EdaSolveOpts), vp, vp, vp, vp, vp]
     L.eda_kernel_launches.restype = ctypes.c_longlong
@@ -374,6 +377,16 @@ class Handle:
         self._check(self._L.eda_sweep_plan(self._h, int(bool(fp64)), info))
         out = dict(zip(PLAN_KEYS, list(info)))
         out["kind"] = PLAN_KINDS[out["kind"]]
+        return out
+
+    def eda_ritz_lmp(self, member=0, iters=None, b=None):
+        """Installs the LMP of the k leading Ritz pairs from `iters` CG
+        iterations (default k) on member's Hessian, right-hand side b [n]
+        (default the member's own); returns all Ritz values (descending)."""
+        iters = self.k if iters is None else int(iters)
+        out = np.zeros(iters)
+        self._check(self._L.eda_ritz_lmp(self._h, int(member), iters, _ptr(b, np.float64, self.n, "b"),
+                                         out.ctypes.data))
         return out
 
     def eda_tail_plans(self, fp64=True):

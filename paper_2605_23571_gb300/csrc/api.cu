@@ -1507,6 +1507,206 @@ EDA_API int eda_set_lmp(eda_handle* h, const double* s_in, const double* eigvals
   return EDA_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// One block: *out = a . b over n values (FP64).
+__global__ void dot1_kernel(int n, const double* a, const double* b, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += a[i] * b[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    *out = t;
+  }
+}
+
+// v = f * r (the next Lanczos vector)
+__global__ void lanczos_vec_kernel(int n, const double* r, double f, double* v) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = f * r[i];
+}
+
+// r -= alpha q
+__global__ void lanczos_r_kernel(int n, double alpha, const double* q, double* r) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) r[i] -= alpha * q[i];
+}
+
+// p = r + beta p
+__global__ void lanczos_p_kernel(int n, double beta, const double* r, double* p) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = r[i] + beta * p[i];
+}
+
+// S[c][i] = sum_j Y[j][c] V[j][i] for the k leading Ritz vectors (Y [m x k]
+// row-major, V [m][n]).
+__global__ void ritz_vec_kernel(int n, int m, int k, const double* Y, const double* V, double* S) {
+  const long long total = (long long)k * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(e / n), i = (int)(e - (long long)c * n);
+    double acc = 0.0;
+    for (int j = 0; j < m; ++j) acc += Y[(long long)j * k + c] * V[(long long)j * n + i];
+    S[e] = acc;
+  }
+}
+
+// Eigenpairs of a symmetric m x m matrix (row-major, overwritten) by cyclic
+// Jacobi rotations: eigenvalues on A's diagonal, eigenvectors in the columns
+// of Q.  Each rotation annihilates A[p][q] with tan = sign(z) / (|z| +
+// sqrt(z^2 + 1)), z = (A[q][q] - A[p][p]) / (2 A[p][q]).
+void jacobi_eigh(int m, std::vector<double>& A, std::vector<double>& Q) {
+  Q.assign((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) Q[(size_t)i * m + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < m; ++i) {
+      diag += A[(size_t)i * m + i] * A[(size_t)i * m + i];
+      for (int j = i + 1; j < m; ++j) off += A[(size_t)i * m + j] * A[(size_t)i * m + j];
+    }
+    if (off <= 1e-32 * diag) break;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double apq = A[(size_t)p * m + q];
+        if (apq == 0.0) continue;
+        const double z = (A[(size_t)q * m + q] - A[(size_t)p * m + p]) / (2.0 * apq);
+        const double t = (z >= 0.0 ? 1.0 : -1.0) / (std::fabs(z) + std::sqrt(z * z + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int r = 0; r < m; ++r) {  // columns p, q
+          const double arp = A[(size_t)r * m + p], arq = A[(size_t)r * m + q];
+          A[(size_t)r * m + p] = c * arp - sn * arq;
+          A[(size_t)r * m + q] = sn * arp + c * arq;
+        }
+        for (int r = 0; r < m; ++r) {  // rows p, q
+          const double apr = A[(size_t)p * m + r], aqr = A[(size_t)q * m + r];
+          A[(size_t)p * m + r] = c * apr - sn * aqr;
+          A[(size_t)q * m + r] = sn * apr + c * aqr;
+        }
+        for (int r = 0; r < m; ++r) {
+          const double qrp = Q[(size_t)r * m + p], qrq = Q[(size_t)r * m + q];
+          Q[(size_t)r * m + p] = c * qrp - sn * qrq;
+          Q[(size_t)r * m + q] = sn * qrp + c * qrq;
+        }
+      }
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+EDA_API int eda_ritz_lmp(eda_handle* h, int member, int iters, const double* b, double* ritz_out) {
+  if (!h) return fail(nullptr, EDA_ERR_INVALID, "handle is NULL");
+  if (!h->have_traj) return fail(h, EDA_ERR_STATE, "eda_ritz_lmp before eda_set_trajectory");
+  const int n = h->n, k = h->k;
+  if (k < 1) return fail(h, EDA_ERR_INVALID, "eda_ritz_lmp: the handle has no LMP rank (ell = 0)");
+  if (member < 0 || member >= h->M || iters < k || iters > 256 || iters > n)
+    return fail(h, EDA_ERR_INVALID, "eda_ritz_lmp: member outside [0, L+1) or iters outside [k, min(256, n)]");
+  // CG without preconditioner from x0 = 0 on member's Hessian, FP64 sweeps;
+  // v_j = (-1)^j r_j / |r_j| and CG's coefficients (Section 3; the
+  // CG-Lanczos relation)
+  double *V = nullptr, *r = nullptr, *pv = nullptr, *q = nullptr, *d = nullptr, *Yd = nullptr, *Sd = nullptr;
+  int* col = nullptr;
+  struct Frees {
+    std::vector<void*> ps;
+    ~Frees() {
+      for (void* p : ps)
+        if (p) cudaFree(p);
+    }
+  } frees;
+  auto dal = [&](double** p, size_t cnt) -> cudaError_t {
+    cudaError_t e = cudaMalloc((void**)p, cnt * sizeof(double));
+    if (e == cudaSuccess) frees.ps.push_back(*p);
+    return e;
+  };
+  CU(h, dal(&V, (size_t)iters * n));
+  CU(h, dal(&r, n));
+  CU(h, dal(&pv, n));
+  CU(h, dal(&q, n));
+  CU(h, dal(&d, 2));
+  CU(h, cudaMalloc((void**)&col, sizeof(int)));
+  frees.ps.push_back(col);
+  CU(h, cudaMemcpyAsync(col, &member, sizeof(int), cudaMemcpyHostToDevice, h->st));
+  In ib;
+  CU(h, ib.init(b, (size_t)n * sizeof(double), h->st));
+  const double* bm = b ? (const double*)ib.dev : h->b + (long long)member * n;
+  CU(h, cudaMemcpyAsync(r, bm, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  CU(h, cudaMemcpyAsync(pv, bm, (size_t)n * sizeof(double), cudaMemcpyDeviceToDevice, h->st));
+  auto dot = [&](const double* a, const double* b2, double* out) -> int {
+    eda::count_launch();
+    dot1_kernel<<<1, 1024, 0, h->st>>>(n, a, b2, d);
+    CU(h, cudaGetLastError());
+    double hv = 0.0;
+    CU(h, cudaMemcpyAsync(&hv, d, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    CU(h, cudaStreamSynchronize(h->st));
+    *out = hv;
+    return EDA_OK;
+  };
+  double rr = 0.0;
+  int rc = dot(r, r, &rr);
+  if (rc) return rc;
+  if (!(rr > 0.0) || !std::isfinite(rr)) return fail(h, EDA_ERR_NUMERIC, "eda_ritz_lmp: the right-hand side is zero or not finite");
+  std::vector<double> alpha((size_t)iters), beta((size_t)iters);
+  const unsigned gb = grid_for(n);
+  for (int j = 0; j < iters; ++j) {
+    eda::count_launch();
+    lanczos_vec_kernel<<<gb, 256, 0, h->st>>>(n, r, ((j & 1) ? -1.0 : 1.0) / std::sqrt(rr), V + (long long)j * n);
+    CU(h, cudaGetLastError());
+    rc = hvp_dev(h, col, 1, pv, q, 1, true, nullptr);
+    if (rc) return rc;
+    double pq = 0.0;
+    rc = dot(pv, q, &pq);
+    if (rc) return rc;
+    if (!(pq > 0.0) || !std::isfinite(pq)) return fail(h, EDA_ERR_NUMERIC, "eda_ritz_lmp: CG breakdown (p.Hp <= 0)");
+    alpha[(size_t)j] = rr / pq;
+    eda::count_launch();
+    lanczos_r_kernel<<<gb, 256, 0, h->st>>>(n, alpha[(size_t)j], q, r);
+    CU(h, cudaGetLastError());
+    double rr_new = 0.0;
+    rc = dot(r, r, &rr_new);
+    if (rc) return rc;
+    if (!(rr_new > 0.0) && j + 1 < iters)
+      return fail(h, EDA_ERR_NUMERIC, "eda_ritz_lmp: CG converged before the requested iterations");
+    beta[(size_t)j] = rr_new / rr;
+    eda::count_launch();
+    lanczos_p_kernel<<<gb, 256, 0, h->st>>>(n, beta[(size_t)j], r, pv);
+    CU(h, cudaGetLastError());
+    rr = rr_new;
+  }
+  // T = V^T H V from CG's coefficients, its eigenpairs on the host
+  const int m = iters;
+  std::vector<double> T((size_t)m * m, 0.0), Q;
+  for (int j = 0; j < m; ++j) {
+    T[(size_t)j * m + j] = 1.0 / alpha[(size_t)j] + (j > 0 ? beta[(size_t)j - 1] / alpha[(size_t)j - 1] : 0.0);
+    if (j + 1 < m) T[(size_t)j * m + j + 1] = T[(size_t)(j + 1) * m + j] = std::sqrt(beta[(size_t)j]) / alpha[(size_t)j];
+  }
+  jacobi_eigh(m, T, Q);
+  std::vector<int> order((size_t)m);
+  for (int i = 0; i < m; ++i) order[(size_t)i] = i;
+  std::sort(order.begin(), order.end(),
+            [&](int a, int b2) { return T[(size_t)a * m + a] > T[(size_t)b2 * m + b2]; });
+  std::vector<double> theta((size_t)m), Y((size_t)m * k);
+  for (int i = 0; i < m; ++i) theta[(size_t)i] = T[(size_t)order[(size_t)i] * m + order[(size_t)i]];
+  for (int j = 0; j < m; ++j)
+    for (int c = 0; c < k; ++c) Y[(size_t)j * k + c] = Q[(size_t)j * m + order[(size_t)c]];
+  if (ritz_out) std::memcpy(ritz_out, theta.data(), (size_t)m * sizeof(double));
+  // the k leading Ritz vectors S = V Y, installed as the LMP's eigenpairs
+  CU(h, dal(&Yd, (size_t)m * k));
+  CU(h, dal(&Sd, (size_t)k * n));
+  CU(h, cudaMemcpyAsync(Yd, Y.data(), (size_t)m * k * sizeof(double), cudaMemcpyHostToDevice, h->st));
+  eda::count_launch();
+  ritz_vec_kernel<<<grid_for((long long)k * n), 256, 0, h->st>>>(n, m, k, Yd, V, Sd);
+  CU(h, cudaGetLastError());
+  std::vector<double> lead(theta.begin(), theta.begin() + k);
+  for (double& v : lead)
+    if (v < 1.0) v = 1.0;  // Ritz values of I + A lie above 1 up to rounding
+  return eda_set_lmp(h, Sd, lead.data());
+}
+
 EDA_API int eda_plan_tiling(int n, int fp64, int w, int kind, int cs, int threads, int K, int C, int* info) {
   if (!info || n < 1 || w < 0 || K < 1 || K > eda::kMaxRefresh || kind < 0 || kind > 3)
     return fail(nullptr, EDA_ERR_INVALID, "eda_plan_tiling: invalid argument");
