@@ -92,6 +92,16 @@ __device__ __forceinline__ T jtvpd(const Run<T, C>& X, T dp1, const Run<T, C>& w
   return fma(X.at(j - 2), w.at(j - 1), fma(dp1, w.at(j + 1), fma(-X.at(j + 1), w.at(j + 2), -w.at(j))));
 }
 
+// Reverse RK4 step.  The TL step is e' = e + h/6 (k1 + 2 k2 + 2 k3 + k4),
+// k_s = J_s e_s, e_1 = e, e_2 = e + h/2 k1, e_3 = e + h/2 k2, e_4 = e + h k3.
+// Its adjoint maps lam (the weight of e') to
+//   lam + h/6 u4 + h/3 u3 + h/3 u2 + h/6 u1,   u_s = J_s^T b_s,
+//   b4 = lam, b3 = lam + h/2 u4, b2 = lam + h/2 u3, b1 = lam + h u2,
+// which is the textbook recursion (stage weights a4 = h/6 lam,
+// a3 = h/3 lam + h J4^T a4, a2 = h/3 lam + h/2 J3^T a3,
+// a1 = h/6 lam + h/2 J2^T a2) with a_s = h/6 b4, h/3 b3, h/3 b2, h/6 b1
+// factored out by linearity: one FMA per weight and per accumulated slope.
+
 struct Geo {
   // A: threads holding the extended region (the neighbour wrap); AS: edge
   // buffer slot stride and NT: loop stride (both the block size)
@@ -1175,19 +1185,17 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T>& a0, const int col
           dp[s_][C - 1] = row[gh[2]];
         }
       }
-      // a4 = a1 = dt/6 lam and a3 = a2 = dt/3 lam before the slopes
+      // the reverse RK4 step (u_s = J_s^T b_s, b4 = lam) on the stored stages
 #pragma unroll
-      for (int c = 0; c < C; ++c) ad[c] = h6 * lam[c];  // a4
-      publish(eb[3], g, ad);
+      for (int c = 0; c < C; ++c) wv.v[c] = lam[c];
+      publish(eb[3], g, lam);
       __syncthreads();
-#pragma unroll
-      for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
       fetch(eb[3], g, wv);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const T gg = jtvpd(S[3], dp[3][c], wv, c);
-        ln[c] = lam[c] + gg;
-        ad[c] = fma(h, gg, h3 * lam[c]);  // a3
+        const T u = jtvpd(S[3], dp[3][c], wv, c);
+        ln[c] = fma(h6, u, lam[c]);
+        ad[c] = fma(h2, u, lam[c]);  // b3
       }
       publish(eb[4], g, ad);
       __syncthreads();
@@ -1196,9 +1204,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T>& a0, const int col
       fetch(eb[4], g, wv);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const T gg = jtvpd(S[2], dp[2][c], wv, c);
-        ln[c] += gg;
-        ad[c] = fma(h2, gg, h3 * lam[c]);  // a2
+        const T u = jtvpd(S[2], dp[2][c], wv, c);
+        ln[c] = fma(h3, u, ln[c]);
+        ad[c] = fma(h2, u, lam[c]);  // b2
       }
       publish(eb[3], g, ad);
       __syncthreads();
@@ -1207,9 +1215,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T>& a0, const int col
       fetch(eb[3], g, wv);
 #pragma unroll
       for (int c = 0; c < C; ++c) {
-        const T gg = jtvpd(S[1], dp[1][c], wv, c);
-        ln[c] += gg;
-        ad[c] = fma(h2, gg, h6 * lam[c]);  // a1
+        const T u = jtvpd(S[1], dp[1][c], wv, c);
+        ln[c] = fma(h3, u, ln[c]);
+        ad[c] = fma(h, u, lam[c]);  // b1
       }
       publish(eb[4], g, ad);
       __syncthreads();
@@ -1217,7 +1225,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T>& a0, const int col
       for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
       fetch(eb[4], g, wv);
 #pragma unroll
-      for (int c = 0; c < C; ++c) lam[c] = ln[c] + jtvpd(S[0], dp[0][c], wv, c);
+      for (int c = 0; c < C; ++c) lam[c] = fma(h6, jtvpd(S[0], dp[0][c], wv, c), ln[c]);
     } else {
     Run<T, C> X1, X, wv;
     T X2[C], X3[C], X4[C], ln[C], ad[C];
@@ -1228,7 +1236,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T>& a0, const int col
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       X2[c] = xr[c] + h2 * tend(X1, c, F);
-      ad[c] = h6 * lam[c];
+      ad[c] = lam[c];  // b4
     }
     publish(eb[1], g, X2);
     publish(eb[3], g, ad);
@@ -1247,7 +1255,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T>& a0, const int col
     for (int c = 0; c < C; ++c) X4[c] = xr[c] + h * tend(X, c, F);
     publish(eb[5], g, X4);
     __syncthreads();
-    // reverse stage 4: g4 = J4^T a4, a4 = h/6 lam
+    // reverse stage 4: u4 = J4^T b4, b4 = lam (the reverse RK4 step)
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       X.v[c] = X4[c];
@@ -1257,9 +1265,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T>& a0, const int col
     fetch(eb[3], g, wv);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const T gg = jtvp(X, wv, c);
-      ln[c] = lam[c] + gg;
-      ad[c] = h3 * lam[c] + h * gg;  // a3
+      const T u = jtvp(X, wv, c);
+      ln[c] = fma(h6, u, lam[c]);
+      ad[c] = fma(h2, u, lam[c]);  // b3
     }
     publish(eb[4], g, ad);
     __syncthreads();
@@ -1273,9 +1281,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T>& a0, const int col
     fetch(eb[4], g, wv);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const T gg = jtvp(X, wv, c);
-      ln[c] += gg;
-      ad[c] = h3 * lam[c] + h2 * gg;  // a2
+      const T u = jtvp(X, wv, c);
+      ln[c] = fma(h3, u, ln[c]);
+      ad[c] = fma(h2, u, lam[c]);  // b2
     }
     publish(eb[3], g, ad);
     __syncthreads();
@@ -1289,9 +1297,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T>& a0, const int col
     fetch(eb[3], g, wv);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const T gg = jtvp(X, wv, c);
-      ln[c] += gg;
-      ad[c] = h6 * lam[c] + h2 * gg;  // a1
+      const T u = jtvp(X, wv, c);
+      ln[c] = fma(h3, u, ln[c]);
+      ad[c] = fma(h, u, lam[c]);  // b1
     }
     publish(eb[4], g, ad);
     __syncthreads();
@@ -1300,7 +1308,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs<T>& a0, const int col
     for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
     fetch(eb[4], g, wv);
 #pragma unroll
-    for (int c = 0; c < C; ++c) lam[c] = ln[c] + jtvp(X1, wv, c);
+    for (int c = 0; c < C; ++c) lam[c] = fma(h6, jtvp(X1, wv, c), ln[c]);
     }
     if (t > b0) {
 #pragma unroll
@@ -2066,7 +2074,7 @@ __global__ void __launch_bounds__(kWarpMaxThreads) wsweep_kernel(const SweepArgs
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       X2.v[c] = xr[c] + h2 * tend(X1, c, F);
-      ad[c] = h6 * lam[c];
+      ad[c] = lam[c];  // b4
     }
     shfl_all<T, C>(X2);
 #pragma unroll
@@ -2075,15 +2083,15 @@ __global__ void __launch_bounds__(kWarpMaxThreads) wsweep_kernel(const SweepArgs
 #pragma unroll
     for (int c = 0; c < C; ++c) X4.v[c] = xr[c] + h * tend(X3, c, F);
     shfl_all<T, C>(X4);
-    // reverse stage 4: g4 = J4^T a4, a4 = h/6 lam
+    // reverse stage 4: u4 = J4^T b4, b4 = lam (the reverse RK4 step)
 #pragma unroll
     for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
     shfl_m1p1p2<T, C>(wv);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const T gg = jtvp(X4, wv, c);
-      ln[c] = lam[c] + gg;
-      ad[c] = h3 * lam[c] + h * gg;  // a3
+      const T u = jtvp(X4, wv, c);
+      ln[c] = fma(h6, u, lam[c]);
+      ad[c] = fma(h2, u, lam[c]);  // b3
     }
     // reverse stage 3
 #pragma unroll
@@ -2091,9 +2099,9 @@ __global__ void __launch_bounds__(kWarpMaxThreads) wsweep_kernel(const SweepArgs
     shfl_m1p1p2<T, C>(wv);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const T gg = jtvp(X3, wv, c);
-      ln[c] += gg;
-      ad[c] = h3 * lam[c] + h2 * gg;  // a2
+      const T u = jtvp(X3, wv, c);
+      ln[c] = fma(h3, u, ln[c]);
+      ad[c] = fma(h2, u, lam[c]);  // b2
     }
     // reverse stage 2
 #pragma unroll
@@ -2101,16 +2109,16 @@ __global__ void __launch_bounds__(kWarpMaxThreads) wsweep_kernel(const SweepArgs
     shfl_m1p1p2<T, C>(wv);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
-      const T gg = jtvp(X2, wv, c);
-      ln[c] += gg;
-      ad[c] = h6 * lam[c] + h2 * gg;  // a1
+      const T u = jtvp(X2, wv, c);
+      ln[c] = fma(h3, u, ln[c]);
+      ad[c] = fma(h, u, lam[c]);  // b1
     }
     // reverse stage 1
 #pragma unroll
     for (int c = 0; c < C; ++c) wv.v[c] = ad[c];
     shfl_m1p1p2<T, C>(wv);
 #pragma unroll
-    for (int c = 0; c < C; ++c) lam[c] = ln[c] + jtvp(X1, wv, c);
+    for (int c = 0; c < C; ++c) lam[c] = fma(h6, jtvp(X1, wv, c), ln[c]);
     if (t > 0) {
 #pragma unroll
       for (int c = 0; c < C; ++c) xr[c] = pf[c];
