@@ -67,6 +67,27 @@ def test_ritz_pairs_and_lmp_match_the_oracle(member, iters, b_from):
     assert it_p.sum() < it_0.sum()
 
 
+def test_ritz_lmp_on_a_mixed_handle():
+    # the CG runs on the FP64 sweeps of a mixed handle; the installed LMP is
+    # applied in FP32 (its S and arithmetic), to 1e-5 of the correction
+    spec = S.spec_small(400, 12, 9, every_var=2, every_step=2, length_scale=4.0, ell=8, k=8, seed=21)
+    taps, xb, y = problem(spec)
+    traj = O.member_trajectories(spec, xb)
+    b = O.rhs(spec, traj, O.innovations(spec, traj, y), taps)
+    L = O.lanczos_cg(lambda X: O.hvp(spec, traj[0:1], X, taps), b[0], 8)
+    D = L["theta"][:spec.k] - 1.0
+    c = O.lmp_coeffs(D, O.theta_value(spec.theta_mode, D, spec.theta))
+    R = np.random.default_rng(5).standard_normal((spec.n_members, spec.n))
+    ref = O.lmp_apply(L["S"][:, :spec.k], c, R)
+    with P.Handle.from_spec(spec, taps, precision=P.EDA_MIXED) as h:
+        h.eda_set_trajectory(xb, y)
+        theta = h.eda_ritz_lmp(member=0, iters=8)
+        Z = np.zeros_like(R)
+        h.eda_lmp_apply(R, Z, 0, 0)
+    np.testing.assert_allclose(theta, L["theta"], rtol=1e-8)
+    assert (np.linalg.norm(Z - ref, axis=1) / np.linalg.norm(ref - R, axis=1)).max() < 1e-5
+
+
 def test_ritz_lmp_refusals():
     spec = S.spec_small(200, 8, 5, every_var=2, every_step=2, length_scale=3.0, ell=4, k=4, seed=22)
     taps, xb, y = problem(spec)
