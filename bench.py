@@ -61,13 +61,15 @@ def parse():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the scale, uneven-batch and warm-start measurements")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--profile-case", choices=["fp64", "mixed", "scale", "lmp"], default=None,
+    ap.add_argument("--profile-case", choices=["fp64", "mixed", "scale", "lmp", "hvp32"], default=None,
                     help="profiling case for ncu: fp64 / mixed: the workload's setup, sketch and LMP, then one "
                          "PCG solve of --profile-iters fixed iterations between cudaProfilerStart/Stop; scale: "
                          "one batched FP32 Hessian product of --profile-members members of the scale workload "
                          "(its multi-launch chain) in that range; lmp: the LMP apply on CUDA and tensor cores "
                          "timed at the batched and the scale sizes, the batched size's tensor-core apply in that "
-                         "range; prints one line")
+                         "range; hvp32: the batched workload's FP32 member Hessian products through eda_hvp (one "
+                         "column per member, each on its own trajectory), three of them in that range; prints one "
+                         "line")
     ap.add_argument("--profile-iters", type=int, default=20)
     ap.add_argument("--profile-members", type=int, default=9)
     ap.add_argument("--profile-ckpt", type=int, default=0,
@@ -1239,6 +1241,47 @@ def run_profile_lmp(args):
     return 0
 
 
+def run_profile_hvp32(args):
+    """The batched FP32 member Hessian product of the mixed form outside the
+    persistent PCG: eda_hvp of all members (column j on member j's
+    trajectory) on the autotuned tiling, twice untimed, then three times
+    inside the profiler range, timed by CUDA events."""
+    import torch
+    import paper_2605_23571_gb300 as P
+    P.build()
+    dev = torch.device("cuda", 0)
+    spec, dr = workload(args.seed)
+    G = golden(spec, args.seed)
+    taps = P.bhalf_gaussian(spec.n, spec.length_scale, spec.sigma_b)
+    M, n, p = spec.n_members, spec.n, spec.p
+    with P.Handle.from_spec(spec, taps, precision=P.EDA_MIXED) as h:
+        xb = torch.empty(M, n, dtype=torch.float64, device=dev)
+        y = torch.empty(M, p, dtype=torch.float64, device=dev)
+        x0 = G["xt0"] if G is not None else spec.F + spec.spin_sigma * dr.eta_spin
+        h.eda_twin(torch.tensor(x0, device=dev), 0 if G is not None else spec.spinup,
+                   torch.tensor(dr.eta_b, device=dev), torch.tensor(dr.eta_o, device=dev), xb, y)
+        rhs = torch.empty(M, n, dtype=torch.float64, device=dev)
+        h.eda_set_trajectory(xb, y, rhs)
+        h.eda_autotune(0)
+        cols = torch.arange(M, dtype=torch.int32, device=dev)
+        out = torch.empty_like(rhs)
+        for _ in range(2):
+            h.eda_hvp(cols, rhs, out, True)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            h.eda_hvp(cols, rhs, out, True)
+        e1.record()
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        plan = h.eda_sweep_plan(fp64=False)
+    print(json.dumps({"profile_case": "hvp32", "workload": spec.name, "members": M,
+                      "ms_per_product": e0.elapsed_time(e1) / 3, "plan": plan}))
+    return 0
+
+
 def run_profile_case(args):
     """One fixed-iteration solve of the batched workload inside a profiler
     range: a small case of the solve's kernels for ncu (the same kernels and
@@ -1247,6 +1290,8 @@ def run_profile_case(args):
         return run_profile_scale(args)
     if args.profile_case == "lmp":
         return run_profile_lmp(args)
+    if args.profile_case == "hvp32":
+        return run_profile_hvp32(args)
     # one launch on the main tiling: no relaunch on the convergence tail's
     # tilings, whose members stop together after the fixed iterations
     os.environ["EDA_TAIL"] = "0"
