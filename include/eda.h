@@ -383,7 +383,7 @@ EDA_API int eda_sweep_plan(eda_handle* h, int fp64, int* info);
  * to R (every member's PCG state stays on the device) and the solve goes on
  * in a launch on the tail tiling, with the same iterates up to the rounding
  * order of the reductions.  eda_autotune chooses them (active counts falling
- * by a quarter at a time from 3(L+1)/4 to 1; a level is kept where its
+ * by an eighth at a time from 7(L+1)/8 to 1; a level is kept where its
  * tiling's Hessian-product sweep beats the main tiling's by more than 7 %)
  * and replaces any set before.
  *

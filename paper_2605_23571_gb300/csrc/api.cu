@@ -704,7 +704,8 @@ int persist_fits(eda_handle* h, const SweepPlan& pl) {
 }
 
 // Tilings for the persistent PCG's convergence tail: at active counts R
-// falling by a quarter at a time from 3M/4 to 1, times the Hessian-product sweep of R
+// falling by an eighth at a time from 7M/8 to 1 (EDA_TAIL_DIV=d: by R/d from
+// M - M/d), times the Hessian-product sweep of R
 // active columns on the chosen tiling and on clusters of more CTAs (up to
 // 16) with neighbouring refresh periods, and keeps a level's fastest tiling
 // where it beats the chosen one by more than 7 %.  The chosen tiling is
@@ -735,7 +736,8 @@ int tune_tails(eda_handle* h, bool fp64, cudaEvent_t e0, cudaEvent_t e1) {
     *ms /= reps;
     return EDA_OK;
   };
-  for (int R = M - std::max(1, M / 4); rc == EDA_OK && R >= 1; R -= std::max(1, R / 4)) {
+  const int div = std::max(2, env_int("EDA_TAIL_DIV", 8));  // levels fall by R / div
+  for (int R = M - std::max(1, M / div); rc == EDA_OK && R >= 1; R -= std::max(1, R / div)) {
     for (int i = 0; i < M; ++i) hm[(size_t)i] = i < R ? 1 : 0;
     CU(h, cudaMemcpy(mask, hm.data(), (size_t)M * sizeof(int), cudaMemcpyHostToDevice));
     float base_ms = 0.f;

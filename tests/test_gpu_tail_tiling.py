@@ -122,7 +122,7 @@ def test_tail_plan_refusals_and_autotune(case):
         h.eda_autotune(0)
         t = h.eda_tail_plans()
         lv = [x for x, _ in t]
-        top = spec.n_members - max(1, spec.n_members // 4)  # the first level: 3/4 of the members
+        top = spec.n_members - max(1, spec.n_members // 8)  # the first level: 7/8 of the members
         assert lv == sorted(lv, reverse=True) and all(1 <= x <= top for x in lv)
         main = h.eda_sweep_plan(fp64=True)
         for _, pl in t:
