@@ -533,7 +533,7 @@ EDA_API int eda_group_solve(eda_group* g, double tol, int maxit, int use_lmp, do
  * network mapping (member right-hand side b_j, control solution dz_0) to a
  * guess of the member solution dz_j, used only as the initial iterate x0 of
  * eda_solve_batch, which still runs to the same tolerance (so the plain
- * solve remains the judge of the error).
+ * solve still decides the error).
  *
  * Network: channels 2 -> H -> H -> H -> 1, kernel 5 with periodic wrap (tap t
  * reads position i + t - 2 mod n), GELU (erf form) after layers 1-3; inputs
