@@ -51,7 +51,7 @@ MAXIT = 6000
 MAXIT_ERR = 20000  # budget of the certified-error forms (deeper than relres 1e-6)
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -74,7 +74,7 @@ def parse():
     ap.add_argument("--profile-members", type=int, default=9)
     ap.add_argument("--profile-ckpt", type=int, default=0,
                     help="scale profiling case: the trajectory checkpointed every this many steps (0: stored)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def dist_env():

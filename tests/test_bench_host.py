@@ -70,3 +70,21 @@ def test_cpu_baseline_all_cores_sample():
     t_seq = r["t_full_step_s"] - r["t_setup_sketch_lmp_s"]
     t_par = ac["t_full_step_s"] - r["t_setup_sketch_lmp_s"]
     assert t_par < 1.5 * t_seq
+
+
+def test_profile_commands_run_on_this_bench():
+    # every ncu summary under profiles/ names the bench.py command it was
+    # taken with; each must still parse with this bench's options
+    import glob
+    import shlex
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    found = 0
+    for path in glob.glob(os.path.join(root, "profiles", "*.md")):
+        text = open(path).read().replace("\\\n", " ")
+        for line in text.splitlines():
+            if "python bench.py" not in line:
+                continue
+            args = shlex.split(line.split("python bench.py", 1)[1])
+            bench.parse(args)  # raises SystemExit on an unknown option
+            found += 1
+    assert found >= 6
